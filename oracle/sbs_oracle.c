@@ -1,0 +1,717 @@
+/*
+ * FP64 CPU oracle for the sample-based stochastic (SBS) predictive controller
+ * of Turrisi et al., "On the Benefits of GPU Sample-Based Stochastic Predictive
+ * Controllers for Legged Locomotion" (IROS 2024).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU path computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant generator with the CUDA library; the two meet only
+ * through seeded inputs made by the workload module.
+ *
+ * Everything is double precision except the one place where floating point
+ * decides an integer (the quantised step frequency, Sec. IV-C), which is taken
+ * in single precision, the precision of the GPU path.
+ *
+ * Paper passages followed (section / equation / algorithm of the paper):
+ *   sampling theta_k ~ N(theta, C), C diagonal ........ Alg. 1 (Sampling)
+ *   rollout loop, cost charged on the pre-step state .. Alg. 2
+ *   SRBD continuous dynamics ........................... Eq. (1), Sec. IV-A
+ *   discrete dynamics x_{j+1} = f(x_j, u_j) ............ Sec. IV-A (explicit Euler)
+ *   GRF spline policy Gamma = sigma(t_knot, theta_2, t)  Sec. IV-B
+ *   gait: T_st = D_f / f_s, contact sequence ........... Sec. IV-C
+ *   quadratic cost and step-frequency regulariser ..... Sec. V (cost equations)
+ *   MPPI weights and weighted mean ..................... Sec. III-C, Alg. 5
+ *   elite mean / covariance refit ...................... Alg. 1 (Update), Alg. 4
+ *   Naive optimiser (best sample, covariance frozen) ... Sec. III-B, Alg. 3
+ *   one warm-started iteration per control tick ........ Sec. III-A
+ *
+ * Random numbers: Philox4x32-10 from Salmon, Moraes, Dror, Shaw, "Parallel
+ * Random Numbers: As Easy as 1, 2, 3" (SC'11), written from that description;
+ * normals by the Box-Muller transform (Box & Muller, 1958).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NX 12
+#define NU 12
+#define PHASE_ONE 1000000000u /* one gait cycle in units of 1e-9 cycle */
+
+enum { ORC_MPPI = 0, ORC_ELITE = 1, ORC_NAIVE = 2 };
+enum { ORC_OK = 0, ORC_DIVERGED = -6 };
+
+typedef struct {
+    int32_t K, H, P;         /* samples, horizon steps, spline knots (0 = one force per step) */
+    int32_t method;          /* ORC_MPPI / ORC_ELITE / ORC_NAIVE */
+    int32_t iterations;      /* sampling iterations per solve */
+    int32_t elite_count;     /* K_e */
+    int32_t adaptive;        /* 1: the step frequency is a decision variable */
+    uint32_t dt_us;          /* time step in microseconds */
+    uint32_t q_init;         /* nominal / initial step frequency in mHz */
+    uint32_t seed, ctrl;     /* Philox key */
+    double lambda;           /* MPPI temperature */
+    double mass, inertia[3], foot[12], gravity[3];
+    double Q[NX], R[3], w_fc, mu, rho, f_nominal;
+    double f_min, f_max;
+    double sigma_init, sigma_min, sigma_f_init, sigma_f_min;
+} orc_params;
+
+typedef struct {
+    uint32_t offset[4];      /* per-leg phase offset, 1e-9 cycle */
+    uint32_t duty;           /* duty factor D_f, 1e-9 cycle */
+    uint32_t phase0;         /* gait phase at t = 0 of the horizon, 1e-9 cycle */
+} orc_gait;
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11, Sec. 4): ten rounds of two 32x32->64  */
+/* multiplies whose high halves are XORed with the other counter words and a */
+/* Weyl-sequence key.                                                         */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t MUL0 = 0xD2511F53u, MUL1 = 0xCD9E8D57u;
+    const uint32_t WEYL0 = 0x9E3779B9u, WEYL1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)MUL0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)MUL1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += WEYL0; k1 += WEYL1;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Box-Muller on two 32-bit words.  The top 24 bits of each word give an exact
+ * uniform: u1 in (0, 1], u2 in [0, 1). */
+void orc_box_muller(uint32_t x, uint32_t y, double* z0, double* z1)
+{
+    const double two_m24 = 1.0 / 16777216.0;
+    double u1 = (double)((x >> 8) + 1u) * two_m24;
+    double u2 = (double)(y >> 8) * two_m24;
+    double r = sqrt(-2.0 * log(u1));
+    *z0 = r * cos(2.0 * M_PI * u2);
+    *z1 = r * sin(2.0 * M_PI * u2);
+}
+
+/* The counter layout of one sample's normals.
+ *   key     = (seed, controller id)
+ *   counter = (sample k, draw d, iteration low word, iteration high word)
+ *   draw 0  : the step-frequency normal (first Box-Muller output of words 0,1)
+ *   draw d>0: normals n = 4(d-1) .. 4(d-1)+3; words (0,1) give n%4 = 0 (cos), 1 (sin),
+ *             words (2,3) give n%4 = 2 (cos), 3 (sin).
+ * Force normal n of step j, leg i, axis a is n = 12 j + 3 i + a (knot p instead of j
+ * for the spline policy). */
+double orc_normal(uint32_t seed, uint32_t ctrl, uint32_t k, uint32_t n, uint64_t iter)
+{
+    uint32_t ctr[4] = {k, 1u + n / 4u, (uint32_t)iter, (uint32_t)(iter >> 32)};
+    uint32_t key[2] = {seed, ctrl};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double z0, z1;
+    unsigned slot = n % 4u;
+    if (slot < 2) orc_box_muller(w[0], w[1], &z0, &z1);
+    else orc_box_muller(w[2], w[3], &z0, &z1);
+    return (slot % 2u == 0) ? z0 : z1;
+}
+
+double orc_freq_normal(uint32_t seed, uint32_t ctrl, uint32_t k, uint64_t iter)
+{
+    uint32_t ctr[4] = {k, 0u, (uint32_t)iter, (uint32_t)(iter >> 32)};
+    uint32_t key[2] = {seed, ctrl};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double z0, z1;
+    orc_box_muller(w[0], w[1], &z0, &z1);
+    return z0;
+}
+
+/* Step frequency of one sample (Sec. IV-C, frequency as decision variable theta_1):
+ * f = clip(mu_f + sigma_f z, f_min, f_max), quantised to integer mHz.  This is the
+ * one float-to-integer decision of the path, so it is taken in single precision
+ * (the precision of the GPU path).  *margin receives |1000 f - nearest half-integer|
+ * evaluated in double; a small margin marks a sample whose rounding is ambiguous
+ * between the two precisions. */
+uint32_t orc_quantise_freq(double mu_f, double sigma_f, double z, double f_min, double f_max,
+                           double* margin)
+{
+    float zf = (float)z;
+    float ff = fmaf((float)sigma_f, zf, (float)mu_f);
+    if (ff < (float)f_min) ff = (float)f_min;
+    if (ff > (float)f_max) ff = (float)f_max;
+    float t = 1000.0f * ff;
+    uint32_t q = (uint32_t)floorf(t + 0.5f);
+    if (margin) {
+        double fd = mu_f + sigma_f * z;
+        if (fd < f_min) fd = f_min;
+        if (fd > f_max) fd = f_max;
+        double td = 1000.0 * fd;
+        double frac = td - floor(td);
+        *margin = fabs(frac - 0.5);
+    }
+    return q;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gait (Sec. IV-C).  A leg's phase advances at the step frequency f_s; the   */
+/* leg is in stance for the first D_f of each cycle, so T_st = D_f / f_s and  */
+/* T_sw = (1 - D_f) / f_s.  Phases are integers in units of 1e-9 cycle, so the */
+/* schedule is exact: at step j (time j dt) the phase advance is               */
+/* j * (q mHz) * (dt_us us) = j q dt_us * 1e-9 cycle.                          */
+/* ------------------------------------------------------------------------- */
+int orc_stance(const orc_gait* g, int leg, uint32_t q_mhz, uint32_t dt_us, int j)
+{
+    uint64_t adv = (uint64_t)j * (uint64_t)q_mhz * (uint64_t)dt_us;
+    uint64_t ph = ((uint64_t)g->phase0 + (uint64_t)g->offset[leg] + adv) % (uint64_t)PHASE_ONE;
+    return ph < (uint64_t)g->duty ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Model (Sec. IV-A, Eq. (1)).  State x = [p (world), Phi = (roll, pitch, yaw), */
+/* v (world), omega (body)].  Ground reaction forces Gamma_i are world-frame, */
+/* foot lever arms p_cf,i are constant in the body frame.                     */
+/* ------------------------------------------------------------------------- */
+
+/* Body-to-world rotation R = Rz(yaw) Ry(pitch) Rx(roll), row-major. */
+void orc_rotation(const double rpy[3], double Rm[9])
+{
+    double Rx[9] = {1, 0, 0, 0, cos(rpy[0]), -sin(rpy[0]), 0, sin(rpy[0]), cos(rpy[0])};
+    double Ry[9] = {cos(rpy[1]), 0, sin(rpy[1]), 0, 1, 0, -sin(rpy[1]), 0, cos(rpy[1])};
+    double Rz[9] = {cos(rpy[2]), -sin(rpy[2]), 0, sin(rpy[2]), cos(rpy[2]), 0, 0, 0, 1};
+    double T[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0;
+            for (int m = 0; m < 3; ++m) s += Ry[3 * r + m] * Rx[3 * m + c];
+            T[3 * r + c] = s;
+        }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0;
+            for (int m = 0; m < 3; ++m) s += Rz[3 * r + m] * T[3 * m + c];
+            Rm[3 * r + c] = s;
+        }
+}
+
+/* E'^{-1}(Phi): body angular velocity -> roll/pitch/yaw rates for the ZYX
+ * convention above. */
+void orc_euler_rates(const double rpy[3], const double w[3], double rates[3])
+{
+    double sr = sin(rpy[0]), cr = cos(rpy[0]);
+    double tp = tan(rpy[1]), cp = cos(rpy[1]);
+    rates[0] = w[0] + sr * tp * w[1] + cr * tp * w[2];
+    rates[1] = cr * w[1] - sr * w[2];
+    rates[2] = (sr * w[1] + cr * w[2]) / cp;
+}
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Right-hand side of Eq. (1).  gamma: 4 legs x 3 world-frame force components,
+ * already multiplied by the contact flags. f_ext: external world force (may be NULL). */
+void orc_srbd_deriv(const orc_params* P, const double x[NX], const double gamma[NU],
+                    const double* f_ext, double xdot[NX])
+{
+    const double* rpy = x + 3;
+    const double* v = x + 6;
+    const double* w = x + 9;
+    double Rm[9];
+    orc_rotation(rpy, Rm);
+    /* translational: p_dot = v, v_dot = (1/m) sum Gamma_i + g (+ f_ext / m) */
+    double F[3] = {0, 0, 0};
+    for (int i = 0; i < 4; ++i)
+        for (int a = 0; a < 3; ++a) F[a] += gamma[3 * i + a];
+    for (int a = 0; a < 3; ++a) {
+        xdot[a] = v[a];
+        double fe = f_ext ? f_ext[a] : 0.0;
+        xdot[6 + a] = (F[a] + fe) / P->mass + P->gravity[a];
+    }
+    /* rotational: tau_B = sum p_cf,i x (R^T Gamma_i); omega_dot = I^{-1}(tau_B - omega x I omega) */
+    double tau[3] = {0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+        double gb[3];
+        for (int r = 0; r < 3; ++r)
+            gb[r] = Rm[0 * 3 + r] * gamma[3 * i + 0] + Rm[1 * 3 + r] * gamma[3 * i + 1] +
+                    Rm[2 * 3 + r] * gamma[3 * i + 2];
+        double t[3];
+        cross3(P->foot + 3 * i, gb, t);
+        for (int a = 0; a < 3; ++a) tau[a] += t[a];
+    }
+    double Iw[3] = {P->inertia[0] * w[0], P->inertia[1] * w[1], P->inertia[2] * w[2]};
+    double wxIw[3];
+    cross3(w, Iw, wxIw);
+    for (int a = 0; a < 3; ++a) xdot[9 + a] = (tau[a] - wxIw[a]) / P->inertia[a];
+    double rates[3];
+    orc_euler_rates(rpy, w, rates);
+    for (int a = 0; a < 3; ++a) xdot[3 + a] = rates[a];
+}
+
+/* Discrete dynamics x_{j+1} = x_j + dt * f(x_j, u_j) (explicit Euler). */
+void orc_srbd_step(const orc_params* P, const double x[NX], const double gamma[NU],
+                   const double* f_ext, double dt, double xn[NX])
+{
+    double xd[NX];
+    orc_srbd_deriv(P, x, gamma, f_ext, xd);
+    for (int c = 0; c < NX; ++c) xn[c] = x[c] + dt * xd[c];
+}
+
+/* Stage cost r(u_j, x_j, x^r_j) (Sec. V): diagonal quadratic state tracking,
+ * diagonal quadratic force cost with u^r = 0, and a friction-cone penalty
+ * (mu) on stance legs: max(0, |Gamma_xy| - mu Gamma_z)^2 + max(0, -Gamma_z)^2. */
+double orc_stage_cost(const orc_params* P, const double x[NX], const double xr[NX],
+                      const double gamma[NU], const int stance[4])
+{
+    double J = 0;
+    for (int c = 0; c < NX; ++c) {
+        double e = x[c] - xr[c];
+        J += P->Q[c] * e * e;
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int a = 0; a < 3; ++a) J += P->R[a] * gamma[3 * i + a] * gamma[3 * i + a];
+    for (int i = 0; i < 4; ++i) {
+        if (!stance[i]) continue;
+        double gx = gamma[3 * i], gy = gamma[3 * i + 1], gz = gamma[3 * i + 2];
+        double slip = sqrt(gx * gx + gy * gy) - P->mu * gz;
+        double pen = 0;
+        if (slip > 0) pen += slip * slip;
+        if (gz < 0) pen += gz * gz;
+        J += P->w_fc * pen;
+    }
+    return J;
+}
+
+/* ------------------------------------------------------------------------- */
+/* GRF spline (Sec. IV-B): natural cubic spline through P knots at            */
+/* t_p = p T / (P - 1), T = (H - 1) dt, evaluated at t_j = j dt.  The map from */
+/* knot values to samples is linear, so it is a fixed H x P basis B.           */
+/* ------------------------------------------------------------------------- */
+static double natural_spline_eval(int P, const double* tk, const double* y, double t)
+{
+    /* second derivatives M: M_0 = M_{P-1} = 0; interior rows of the standard
+     * tridiagonal system, solved by the Thomas algorithm. */
+    double M[64] = {0};
+    if (P > 2) {
+        int n = P - 2;
+        double a[64], b[64], c[64], d[64];
+        for (int i = 1; i <= n; ++i) {
+            double h0 = tk[i] - tk[i - 1], h1 = tk[i + 1] - tk[i];
+            a[i - 1] = h0;
+            b[i - 1] = 2.0 * (h0 + h1);
+            c[i - 1] = h1;
+            d[i - 1] = 6.0 * ((y[i + 1] - y[i]) / h1 - (y[i] - y[i - 1]) / h0);
+        }
+        for (int i = 1; i < n; ++i) {
+            double m = a[i] / b[i - 1];
+            b[i] -= m * c[i - 1];
+            d[i] -= m * d[i - 1];
+        }
+        M[n] = d[n - 1] / b[n - 1];
+        for (int i = n - 1; i >= 1; --i) M[i] = (d[i - 1] - c[i - 1] * M[i + 1]) / b[i - 1];
+    }
+    int s = 0;
+    while (s < P - 2 && t > tk[s + 1]) ++s;
+    double h = tk[s + 1] - tk[s];
+    double A = tk[s + 1] - t, Bt = t - tk[s];
+    return M[s] * A * A * A / (6.0 * h) + M[s + 1] * Bt * Bt * Bt / (6.0 * h) +
+           (y[s] / h - M[s] * h / 6.0) * A + (y[s + 1] / h - M[s + 1] * h / 6.0) * Bt;
+}
+
+void orc_knot_times(int H, int P, double dt, double* tk)
+{
+    double T = (H - 1) * dt;
+    for (int p = 0; p < P; ++p) tk[p] = T * (double)p / (double)(P - 1);
+}
+
+/* Evaluate the spline with knot values y at an arbitrary time t in [0, T]. */
+double orc_spline_at(int H, int P, double dt, const double* y, double t)
+{
+    double tk[64];
+    orc_knot_times(H, P, dt, tk);
+    return natural_spline_eval(P, tk, y, t);
+}
+
+/* B[j][p]: the spline's value at t_j when knot p is 1 and the others 0. */
+void orc_spline_basis(int H, int P, double dt, double* B)
+{
+    double tk[64], e[64];
+    orc_knot_times(H, P, dt, tk);
+    for (int p = 0; p < P; ++p) {
+        for (int q = 0; q < P; ++q) e[q] = (q == p) ? 1.0 : 0.0;
+        for (int j = 0; j < H; ++j) B[j * P + p] = natural_spline_eval(P, tk, e, j * dt);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Decision vector layout: theta = [force part (12 H per-step values, or 12 P  */
+/* knot values), step frequency (adaptive only)], so D = 12 H (+1) or 12 P (+1). */
+/* ------------------------------------------------------------------------- */
+int orc_dim(const orc_params* P)
+{
+    int nf = 12 * (P->P > 0 ? P->P : P->H);
+    return nf + (P->adaptive ? 1 : 0);
+}
+
+static double weight_z(const orc_params* P) { return P->mass * (-P->gravity[2]); }
+
+/* Initial distribution (reset).  Per-step policy: at each step j every leg's mean
+ * force is (0, 0, m|g| / n_j) with n_j the number of stance legs at step j of the
+ * nominal schedule (q_init), 0 when no leg is in stance.  Spline policy: every
+ * knot is (0, 0, m|g| / (4 D_f)).  Variances sigma_init^2; frequency mean
+ * q_init / 1000 Hz with variance sigma_f_init^2. */
+static void init_step(const orc_params* P, const orc_gait* g, int j, double* mu, double* var)
+{
+    int n = 0;
+    for (int i = 0; i < 4; ++i) n += orc_stance(g, i, P->q_init, P->dt_us, j);
+    double fz = n > 0 ? weight_z(P) / n : 0.0;
+    for (int i = 0; i < 4; ++i) {
+        mu[3 * i] = 0; mu[3 * i + 1] = 0; mu[3 * i + 2] = fz;
+        for (int a = 0; a < 3; ++a) var[3 * i + a] = P->sigma_init * P->sigma_init;
+    }
+}
+
+void orc_init_dist(const orc_params* P, const orc_gait* g, double* mean, double* var)
+{
+    int nt = P->P > 0 ? P->P : P->H;
+    if (P->P > 0) {
+        double fz = weight_z(P) / (4.0 * (double)g->duty / (double)PHASE_ONE);
+        for (int p = 0; p < nt; ++p)
+            for (int i = 0; i < 4; ++i) {
+                mean[12 * p + 3 * i] = 0; mean[12 * p + 3 * i + 1] = 0; mean[12 * p + 3 * i + 2] = fz;
+                for (int a = 0; a < 3; ++a) var[12 * p + 3 * i + a] = P->sigma_init * P->sigma_init;
+            }
+    } else {
+        for (int j = 0; j < nt; ++j) init_step(P, g, j, mean + 12 * j, var + 12 * j);
+    }
+    if (P->adaptive) {
+        mean[12 * nt] = P->q_init / 1000.0;
+        var[12 * nt] = P->sigma_f_init * P->sigma_f_init;
+    }
+}
+
+/* Warm start (Sec. III-A): the previous solution, moved forward by `shift` steps
+ * to the new tick.  Per-step policy: entry j takes entry j + shift; the last
+ * `shift` steps are reset by the initial rule for the new gait phase.  Spline
+ * policy: the new knots are the old spline evaluated at t_p + shift dt (held at
+ * its end value past the horizon); variances are kept. */
+void orc_warm_shift(const orc_params* P, const orc_gait* g, int shift, double* mean, double* var)
+{
+    if (shift <= 0) return;
+    if (P->P > 0) {
+        double dt = P->dt_us * 1e-6, T = (P->H - 1) * dt, tk[64], y[64];
+        orc_knot_times(P->H, P->P, dt, tk);
+        for (int c = 0; c < 12; ++c) {
+            double nv[64];
+            for (int p = 0; p < P->P; ++p) y[p] = mean[12 * p + c];
+            for (int p = 0; p < P->P; ++p) {
+                double t = tk[p] + shift * dt;
+                if (t > T) t = T;
+                nv[p] = orc_spline_at(P->H, P->P, dt, y, t);
+            }
+            for (int p = 0; p < P->P; ++p) mean[12 * p + c] = nv[p];
+        }
+        return;
+    }
+    int H = P->H;
+    for (int j = 0; j < H; ++j) {
+        if (j + shift < H) {
+            for (int c = 0; c < 12; ++c) {
+                mean[12 * j + c] = mean[12 * (j + shift) + c];
+                var[12 * j + c] = var[12 * (j + shift) + c];
+            }
+        } else {
+            init_step(P, g, j, mean + 12 * j, var + 12 * j);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Rollout(theta_k) (Alg. 2), for sample k of iteration `iter`:               */
+/*   theta_k = mean + sqrt(var) * eps_k (Alg. 1 Sampling, diagonal C);         */
+/*   u_j = pi(theta_k, t_j): contact flags from the sample's frequency and     */
+/*         forces from the per-step values or the spline, zeroed on swing legs */
+/*         (Alg. 4, function pi);                                              */
+/*   J  += r(u_j, x_j, x^r_j); x_{j+1} = f(x_j, u_j).                          */
+/* After the loop, adaptive gaits add rho (theta_1 - f_nominal)^2 (Sec. V).    */
+/* A non-finite cost is +inf.  q_override >= 0 replaces the sample's quantised */
+/* frequency (used to evaluate both candidates of an ambiguous rounding).      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const orc_params* P;
+    const orc_gait* g;
+    const double* x0;
+    const double* xref;
+    const double* f_ext;
+    const double* mean;
+    const double* var;
+    const double* B; /* H x P spline basis, or NULL */
+    uint64_t iter;
+} rollout_ctx;
+
+static double rollout_one(const rollout_ctx* c, uint32_t k, int64_t q_override, double* theta,
+                          uint32_t* q_out, double* margin_out)
+{
+    const orc_params* P = c->P;
+    int H = P->H, nt = P->P > 0 ? P->P : H;
+    int D = orc_dim(P);
+    double dt = P->dt_us * 1e-6;
+    /* Sampling */
+    for (int n = 0; n < 12 * nt; ++n)
+        theta[n] = c->mean[n] + sqrt(c->var[n]) * orc_normal(P->seed, P->ctrl, k, (uint32_t)n, c->iter);
+    uint32_t q = P->q_init;
+    double margin = 1.0;
+    if (P->adaptive) {
+        double z = orc_freq_normal(P->seed, P->ctrl, k, c->iter);
+        q = orc_quantise_freq(c->mean[D - 1], sqrt(c->var[D - 1]), z, P->f_min, P->f_max, &margin);
+    }
+    if (q_override >= 0) q = (uint32_t)q_override;
+    if (P->adaptive) theta[D - 1] = q / 1000.0;
+    if (q_out) *q_out = q;
+    if (margin_out) *margin_out = margin;
+
+    double x[NX], xn[NX];
+    memcpy(x, c->x0, sizeof(x));
+    double J = 0;
+    for (int j = 0; j < H; ++j) {
+        int st[4];
+        for (int i = 0; i < 4; ++i) st[i] = orc_stance(c->g, i, q, P->dt_us, j);
+        double u[NU];
+        for (int n = 0; n < NU; ++n) {
+            double val;
+            if (P->P > 0) {
+                val = 0;
+                for (int p = 0; p < P->P; ++p) val += c->B[j * P->P + p] * theta[12 * p + n];
+            } else {
+                val = theta[12 * j + n];
+            }
+            u[n] = st[n / 3] ? val : 0.0;
+        }
+        J += orc_stage_cost(P, x, c->xref + NX * j, u, st);
+        orc_srbd_step(P, x, u, c->f_ext, dt, xn);
+        memcpy(x, xn, sizeof(x));
+    }
+    if (P->adaptive) {
+        double d = q / 1000.0 - P->f_nominal;
+        J += P->rho * d * d;
+    }
+    if (!isfinite(J)) J = INFINITY;
+    return J;
+}
+
+/* Evaluate all K samples.  theta (K x D) and margin (K) may be NULL.
+ * nthreads > 1 runs samples in parallel (each sample is computed identically). */
+void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
+                 const double* f_ext, const double* mean, const double* var, uint64_t iter,
+                 double* J, uint32_t* q, double* theta, double* margin, int nthreads)
+{
+    int D = orc_dim(P);
+    double* B = NULL;
+    if (P->P > 0) {
+        B = (double*)malloc(sizeof(double) * P->H * P->P);
+        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
+    }
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter};
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int k = 0; k < P->K; ++k) {
+        double* th = theta ? theta + (size_t)k * D : (double*)malloc(sizeof(double) * D);
+        uint32_t qk;
+        double mk;
+        J[k] = rollout_one(&c, (uint32_t)k, -1, th, &qk, &mk);
+        if (q) q[k] = qk;
+        if (margin) margin[k] = mk;
+        if (!theta) free(th);
+    }
+    free(B);
+}
+
+/* One sample with an optional forced frequency (q_override < 0: its own). */
+double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* x0,
+                          const double* xref, const double* f_ext, const double* mean,
+                          const double* var, uint64_t iter, uint32_t k, int64_t q_override,
+                          double* theta)
+{
+    double* B = NULL;
+    if (P->P > 0) {
+        B = (double*)malloc(sizeof(double) * P->H * P->P);
+        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
+    }
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter};
+    double J = rollout_one(&c, k, q_override, theta, NULL, NULL);
+    free(B);
+    return J;
+}
+
+/* ------------------------------------------------------------------------- */
+/* MPPI UpdateMean (Sec. III-C, Alg. 5): beta = best cost,                    */
+/* w~_i = exp(-(J_i - beta) / lambda), Omega = sum w~, w_i = w~_i / Omega,    */
+/* theta_new = sum_i w_i theta_i.  Covariance unchanged.  Also returns the     */
+/* effective sample size 1 / sum w_i^2 and beta.  Returns ORC_DIVERGED (mean   */
+/* untouched) when no cost is finite.                                          */
+/* ------------------------------------------------------------------------- */
+int orc_mppi(const double* J, const double* theta, int K, int D, double lambda, double* mean_out,
+             double* ess, double* beta_out)
+{
+    double beta = INFINITY;
+    for (int i = 0; i < K; ++i)
+        if (J[i] < beta) beta = J[i];
+    if (!isfinite(beta)) return ORC_DIVERGED;
+    double* w = (double*)malloc(sizeof(double) * K);
+    double Omega = 0;
+    for (int i = 0; i < K; ++i) {
+        w[i] = isfinite(J[i]) ? exp(-(J[i] - beta) / lambda) : 0.0;
+        Omega += w[i];
+    }
+    double s2 = 0;
+    for (int i = 0; i < K; ++i) {
+        w[i] /= Omega;
+        s2 += w[i] * w[i];
+    }
+    for (int d = 0; d < D; ++d) {
+        double s = 0;
+        for (int i = 0; i < K; ++i) s += w[i] * theta[(size_t)i * D + d];
+        mean_out[d] = s;
+    }
+    if (ess) *ess = 1.0 / s2;
+    if (beta_out) *beta_out = beta;
+    free(w);
+    return ORC_OK;
+}
+
+/* Sorting (Alg. 1): order samples by (cost ascending, index ascending) and keep
+ * the first K_e.  qsort over (J, k) pairs. */
+typedef struct { double J; int32_t k; } cost_key;
+static int cmp_cost_key(const void* a, const void* b)
+{
+    const cost_key* x = (const cost_key*)a;
+    const cost_key* y = (const cost_key*)b;
+    if (x->J < y->J) return -1;
+    if (x->J > y->J) return 1;
+    return (x->k > y->k) - (x->k < y->k);
+}
+
+void orc_elite_select(const double* J, int K, int Ke, int32_t* idx)
+{
+    cost_key* v = (cost_key*)malloc(sizeof(cost_key) * K);
+    for (int i = 0; i < K; ++i) {
+        v[i].J = isnan(J[i]) ? INFINITY : J[i];
+        v[i].k = i;
+    }
+    qsort(v, K, sizeof(cost_key), cmp_cost_key);
+    for (int e = 0; e < Ke; ++e) idx[e] = v[e].k;
+    free(v);
+}
+
+/* Elite UpdateMean / UpdateCov (Alg. 1 Update, Alg. 4): mean and biased (maximum
+ * likelihood) diagonal variance of the elite samples about the new mean, floored
+ * at var_floor. */
+void orc_elite_refit(const double* theta, int D, const int32_t* idx, int Ke, const double* var_floor,
+                     double* mean_out, double* var_out)
+{
+    for (int d = 0; d < D; ++d) {
+        double s = 0;
+        for (int e = 0; e < Ke; ++e) s += theta[(size_t)idx[e] * D + d];
+        double m = s / Ke;
+        double v = 0;
+        for (int e = 0; e < Ke; ++e) {
+            double t = theta[(size_t)idx[e] * D + d] - m;
+            v += t * t;
+        }
+        v /= Ke;
+        if (v < var_floor[d]) v = var_floor[d];
+        mean_out[d] = m;
+        if (var_out) var_out[d] = v;
+    }
+}
+
+/* First control of a distribution: the mean's forces at t_0, zeroed on legs not in
+ * stance at t_0 (the contact flags at step 0 do not depend on the frequency). */
+void orc_first_control(const orc_params* P, const orc_gait* g, const double* mean, double u0[NU])
+{
+    for (int n = 0; n < NU; ++n) {
+        int st = orc_stance(g, n / 3, P->q_init, P->dt_us, 0);
+        u0[n] = st ? mean[n] : 0.0; /* knot 0 of an interpolating spline is its value at t_0 */
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* One solve (Alg. 4 with Alg. 1 repeated `iterations` times): warm shift,    */
+/* then per iteration sample / evaluate / sort / update.  The distribution     */
+/* (mean, var) is updated in place; iter0 is the Philox iteration counter of   */
+/* the first iteration (iteration i uses iter0 + i).                           */
+/* Outputs (any may be NULL): u0[12]; info[4] = {beta, ess, mean frequency,    */
+/* status}; J_last, q_last (K) of the last iteration; elite_last (K_e) of the  */
+/* last elite iteration; mppi_mean (D): with the elite/naive method, the MPPI  */
+/* mean from the first iteration's samples.                                    */
+/* ------------------------------------------------------------------------- */
+int orc_solve(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
+              const double* f_ext, int shift, uint64_t iter0, double* mean, double* var, double* u0,
+              double* info, double* J_last, uint32_t* q_last, int32_t* elite_last,
+              double* mppi_mean, int nthreads)
+{
+    int K = P->K, D = orc_dim(P);
+    orc_warm_shift(P, g, shift, mean, var);
+    double* theta = (double*)malloc(sizeof(double) * (size_t)K * D);
+    double* J = (double*)malloc(sizeof(double) * K);
+    uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * K);
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (P->elite_count > 0 ? P->elite_count : 1));
+    double* floor_ = (double*)malloc(sizeof(double) * D);
+    for (int d = 0; d < D; ++d) floor_[d] = P->sigma_min * P->sigma_min;
+    if (P->adaptive) floor_[D - 1] = P->sigma_f_min * P->sigma_f_min;
+    int status = ORC_OK;
+    double beta = INFINITY, ess = 0;
+    for (int it = 0; it < P->iterations; ++it) {
+        orc_rollout(P, g, x0, xref, f_ext, mean, var, iter0 + (uint64_t)it, J, q, theta, NULL, nthreads);
+        double b = INFINITY;
+        for (int k = 0; k < K; ++k)
+            if (J[k] < b) b = J[k];
+        if (!isfinite(b)) { status = ORC_DIVERGED; break; }
+        if (P->method == ORC_MPPI) {
+            orc_mppi(J, theta, K, D, P->lambda, mean, &ess, &beta);
+        } else {
+            if (it == 0 && mppi_mean) orc_mppi(J, theta, K, D, P->lambda, mppi_mean, NULL, NULL);
+            int Ke = P->method == ORC_NAIVE ? 1 : P->elite_count;
+            orc_elite_select(J, K, Ke, idx);
+            if (P->method == ORC_NAIVE) {
+                for (int d = 0; d < D; ++d) mean[d] = theta[(size_t)idx[0] * D + d];
+            } else {
+                orc_elite_refit(theta, D, idx, Ke, floor_, mean, var);
+            }
+            if (elite_last) memcpy(elite_last, idx, sizeof(int32_t) * Ke);
+            beta = b;
+            ess = Ke;
+        }
+        if (J_last) memcpy(J_last, J, sizeof(double) * K);
+        if (q_last) memcpy(q_last, q, sizeof(uint32_t) * K);
+    }
+    if (u0) orc_first_control(P, g, mean, u0);
+    if (info) {
+        info[0] = beta;
+        info[1] = ess;
+        info[2] = P->adaptive ? mean[D - 1] : P->q_init / 1000.0;
+        info[3] = status;
+    }
+    free(theta); free(J); free(q); free(idx); free(floor_);
+    return status;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
