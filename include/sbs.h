@@ -1,0 +1,239 @@
+/*
+ * sbs.h - C ABI of the B300 sample-based stochastic (SBS) predictive controller.
+ *
+ * The library implements the data-parallel hot path of the SBS locomotion
+ * controller of Turrisi et al., "On the Benefits of GPU Sample-Based Stochastic
+ * Predictive Controllers for Legged Locomotion" (IROS 2024):
+ *   - batched forward rollout of K sampled foot-force sequences over H steps
+ *     through the single-rigid-body model (Eq. (1), Alg. 2), each sample with its
+ *     own step frequency and contact schedule (Sec. IV-C);
+ *   - per-step tracking, force and friction-cone cost (Sec. V, Sec. IV-B);
+ *   - the distribution update: MPPI weighted mean (Sec. III-C, Alg. 5), elite
+ *     mean and diagonal variance refit (Alg. 1, Alg. 4) and the Naive best-sample
+ *     rule (Sec. III-B, Alg. 3);
+ *   - one warm-started iteration per control tick (Sec. III-A).
+ * Every step runs in the library's own CUDA kernels (sm_103a).
+ *
+ * Conventions
+ *   State x = [p (3, world, m), roll/pitch/yaw (3, rad, ZYX), v (3, world, m/s),
+ *              omega (3, body, rad/s)].
+ *   Forces: 4 legs (FL, FR, RL, RR) x 3 world-frame components, N.
+ *   Decision vector theta (length D): the force part first (12 values per step,
+ *   step-major, for the per-step policy; 12 values per knot, knot-major, for the
+ *   spline policy), then the step frequency in Hz when the gait is adaptive.
+ *   Gait phases are integers in units of 1e-9 cycle (1e9 = one cycle).
+ *   Random numbers: Philox4x32-10 keyed by (seed, controller_id), counter
+ *   (sample, draw, iteration low, iteration high); draw 0 is the frequency,
+ *   draw 1 + n/4 holds force normal n (Box-Muller on word pairs (0,1), (2,3)).
+ *
+ * Errors: every call returns an int status (SBS_OK = 0, negative on error).  No
+ * C++ exception crosses the boundary.  A call that fails validation leaves the
+ * handle unchanged.  Errors found on the device (all costs non-finite) are
+ * reported in sbs_result.status.  A handle must not be used by two host threads
+ * at once.
+ *
+ * Memory: the library owns its device state (mean, variance, costs, partial
+ * sums, counters), allocated at creation through the caller's allocator (or
+ * cudaMalloc when none is given) and released by sbs_destroy.  Input and output
+ * buffers belong to the caller; the library keeps no pointer to them after the
+ * work it enqueued has run.
+ */
+#ifndef SBS_H
+#define SBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define SBS_OK 0
+#define SBS_PENDING 1
+#define SBS_ERR_INVALID_ARG (-1)
+#define SBS_ERR_OOM (-2)
+#define SBS_ERR_BUDGET (-3)
+#define SBS_ERR_CUDA (-4)
+#define SBS_ERR_TIMEOUT (-5)
+#define SBS_ERR_DIVERGED (-6)
+
+/* ---------------------------------------------------------------- methods */
+#define SBS_MPPI 0  /* weighted mean, covariance unchanged (Alg. 5) */
+#define SBS_ELITE 1 /* elite mean + diagonal variance refit (Alg. 1 Update) */
+#define SBS_NAIVE 2 /* best sample as the new mean, covariance unchanged (Alg. 3) */
+
+/* ---------------------------------------------------------------- limits */
+#define SBS_MAX_H 128         /* horizon steps */
+#define SBS_MAX_K (1 << 24)   /* samples per controller */
+#define SBS_MAX_TILE 256      /* samples per tile (threads per block) */
+
+/* ---------------------------------------------------------------- buffers for sbs_read */
+#define SBS_BUF_MEAN 0      /* float[D]  current mean */
+#define SBS_BUF_VAR 1       /* float[D]  current diagonal variance */
+#define SBS_BUF_COST 2      /* float[K]  costs of the last iteration (+inf when not finite) */
+#define SBS_BUF_FREQ 3      /* int32[K]  quantised step frequency of each sample, mHz */
+#define SBS_BUF_ELITE 4     /* int32[K_e] elite sample indices of the last elite iteration, ascending */
+#define SBS_BUF_MPPI_MEAN 5 /* float[D]  MPPI mean from the first iteration's samples (compare_mppi) */
+
+/* Single rigid body model of Eq. (1). */
+typedef struct sbs_model {
+    float mass;         /* kg, > 0 */
+    float inertia[3];   /* principal body inertia (diagonal tensor), kg m^2, > 0 */
+    float foot[4][3];   /* body-frame foot positions relative to the CoM, m */
+    float gravity[3];   /* world gravity, m/s^2 (e.g. 0, 0, -9.81) */
+} sbs_model;
+
+/* Stage cost r(u, x, x_ref) (Sec. V) plus the friction-cone penalty and the
+ * step-frequency regulariser:
+ *   r = sum_c Q_c (x_c - xref_c)^2 + sum_legs sum_a R_a Gamma_a^2
+ *     + w_fc sum_stance [max(0, |Gamma_xy| - mu Gamma_z)^2 + max(0, -Gamma_z)^2]
+ *   J = sum_{j<H} r(u_j, x_j, xref_j) (+ rho (f - f_nominal)^2 when adaptive). */
+typedef struct sbs_cost {
+    float Q[12];
+    float R[3];
+    float w_fc;
+    float mu;
+    float rho;
+    float f_nominal; /* Hz */
+} sbs_cost;
+
+typedef struct sbs_config {
+    int32_t K;            /* samples, 1..SBS_MAX_K */
+    int32_t H;            /* horizon steps, 1..SBS_MAX_H */
+    int32_t P;            /* 0: one force per step; 2..8: spline knots per force axis (Sec. IV-B) */
+    int32_t method;       /* SBS_MPPI / SBS_ELITE / SBS_NAIVE */
+    int32_t iterations;   /* sampling iterations per solve, >= 1 */
+    int32_t elite_count;  /* K_e for SBS_ELITE, 1..K */
+    int32_t adaptive;     /* 1: the step frequency is sampled (Sec. IV-C) */
+    int32_t compare_mppi; /* 1: elite/naive solves also form the MPPI mean of iteration 0 */
+    uint32_t dt_us;       /* time step, microseconds */
+    uint32_t q_init;      /* initial / fixed step frequency, mHz */
+    uint32_t seed;        /* Philox key word 0 */
+    uint32_t controller_id; /* Philox key word 1 */
+    float lambda;         /* MPPI temperature, > 0 */
+    float f_min, f_max;   /* step-frequency clip, Hz */
+    float sigma_init;     /* initial force standard deviation, N */
+    float sigma_min;      /* elite force standard-deviation floor, N */
+    float sigma_f_init;   /* initial frequency standard deviation, Hz */
+    float sigma_f_min;    /* elite frequency standard-deviation floor, Hz */
+    int32_t tile;         /* samples per tile (64..SBS_MAX_TILE, multiple of 32); 0: default 128 */
+    sbs_model model;
+    sbs_cost cost;
+} sbs_config;
+
+/* Periodic gait (Sec. IV-C): leg i is in stance while its phase
+ * (phase0 + offset[i] + f t) mod 1 is below the duty factor. */
+typedef struct sbs_gait {
+    uint32_t offset[4]; /* per-leg phase offset, 1e-9 cycle, < 1e9 */
+    uint32_t duty;      /* duty factor D_f, 1e-9 cycle, <= 1e9 */
+    uint32_t phase0;    /* gait phase at the first step of the horizon, 1e-9 cycle, < 1e9 */
+} sbs_gait;
+
+/* One solve's inputs.  host_memory = 0: x0, xref, f_ext and the result are device
+ * pointers read/written by the enqueued kernels (they must stay valid until the
+ * stream reaches the work).  host_memory = 1: they are host pointers; inputs are
+ * copied to the device before the call returns (pinned memory makes the copy
+ * asynchronous) and the result is copied back on the stream (synchronize before
+ * reading it). */
+typedef struct sbs_problem {
+    const float* x0;    /* [12] current state estimate */
+    const float* xref;  /* [H][12] reference states x^r_0 .. x^r_{H-1} */
+    const float* f_ext; /* [3] known external world force on the body, or NULL (zero) */
+    sbs_gait gait;
+    int32_t shift;      /* warm start: steps elapsed since the previous solve (0 = none) */
+    int32_t host_memory;
+} sbs_problem;
+
+/* Result of a solve, written by the device. */
+typedef struct sbs_result {
+    float u0[12];      /* first control of the new mean: forces at t_0, zero on swing legs */
+    float cost_min;    /* best sample cost of the last iteration */
+    float ess;         /* MPPI effective sample size 1 / sum w^2 (K_e for elite/naive) */
+    float f_mean;      /* mean step frequency after the update, Hz */
+    int32_t q_freq;    /* that frequency quantised to mHz */
+    int32_t status;    /* SBS_OK or SBS_ERR_DIVERGED (no finite cost; mean kept) */
+    int32_t n_finite;  /* samples with a finite cost in the last iteration */
+    uint32_t iter_lo;  /* Philox iteration counter of the last iteration */
+    uint32_t iter_hi;
+} sbs_result;
+
+/* Caller-supplied device allocator (e.g. a framework's caching allocator). */
+typedef struct sbs_allocator {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+} sbs_allocator;
+
+typedef struct sbs_handle sbs_handle;
+typedef struct sbs_batch sbs_batch;
+
+/* Create a controller.  Validates cfg (SBS_ERR_INVALID_ARG), allocates its device
+ * state through alloc (NULL: cudaMalloc; SBS_ERR_OOM on failure) on the current
+ * device.  The distribution is initialised on the first solve (or sbs_reset). */
+int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** out);
+void sbs_destroy(sbs_handle* h);
+
+/* Decision-vector length D = 12 (H or P) + adaptive. */
+int sbs_dim(const sbs_handle* h);
+
+/* Bytes of device memory the handle holds. */
+size_t sbs_device_bytes(const sbs_handle* h);
+
+/* Reset the distribution to its initial value for the given gait (hover forces
+ * m|g| / n_stance per step, sigma_init; frequency q_init, sigma_f_init) and the
+ * iteration counter to iter. Enqueued on stream (a cudaStream_t; NULL = default). */
+int sbs_reset(sbs_handle* h, const sbs_gait* gait, uint64_t iter, void* stream);
+
+/* One controller tick (Alg. 4): warm shift by prob->shift steps, then
+ * `iterations` rounds of sample / roll out / evaluate / update, enqueued on
+ * stream.  The first solve after creation resets the distribution with the
+ * problem's gait and ignores the shift. */
+int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* stream);
+
+/* Copy a device buffer of the handle (SBS_BUF_*) to dst (host_dst: host memory),
+ * bytes must equal the buffer's size.  Enqueued on stream. */
+int sbs_read(const sbs_handle* h, int which, void* dst, size_t bytes, int host_dst, void* stream);
+
+/* Checkpoint: the distribution and iteration counter as an opaque byte blob.
+ * sbs_state_size gives its size; get/set synchronize the stream. */
+size_t sbs_state_size(const sbs_handle* h);
+int sbs_get_state(const sbs_handle* h, void* buf, size_t bytes, void* stream);
+int sbs_set_state(sbs_handle* h, const void* buf, size_t bytes, void* stream);
+
+/* ---------------------------------------------------------------- batching
+ * Many controllers of uneven K and H solved in one persistent launch that pulls
+ * (controller, tile) items from a device work queue; the tick is captured in a
+ * CUDA graph and replayed.  Every controller's result equals its own sbs_solve
+ * (same tile size), bit for bit. */
+int sbs_batch_create(int max_instances, int max_tiles, const sbs_allocator* alloc, sbs_batch** out);
+void sbs_batch_destroy(sbs_batch* b);
+
+/* Solve n controllers (each one iteration; elite/naive controllers with
+ * iterations > 1 are rejected) on stream.  probs[i] must use device memory
+ * (host_memory = 0) and results is a device array of n sbs_result. */
+int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                    sbs_result* results, void* stream);
+
+/* ---------------------------------------------------------------- utilities */
+const char* sbs_status_str(int status);
+
+/* Philox4x32-10 blocks (Salmon et al., SC'11): out[4i..4i+3] = Philox(ctr[4i..],
+ * key[2i..]) for i < n.  Device arrays; enqueued on stream. */
+int sbs_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream);
+
+/* The standard normals the controller with key (seed, ctrl) draws in iteration
+ * iter (Alg. 1 Sampling): for samples k0 .. k0 + nk - 1, out[i (nn + 1)] is the
+ * frequency normal (draw 0) and out[i (nn + 1) + 1 + n] force normal n < nn
+ * (draw 1 + n/4).  Device output of nk (nn + 1) floats; enqueued on stream. */
+int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
+
+/* Measure the FP32 FMA throughput of the current device with a register-resident
+ * FMA chain kernel; returns FLOP/s (2 per FMA) in *flops, or an error. */
+int sbs_fp32_peak(double* flops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBS_H */

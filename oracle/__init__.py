@@ -75,6 +75,8 @@ def lib():
             "orc_solve": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, u64, vp, vp, vp, vp, vp, vp, vp,
                                     vp, C.c_int]),
             "orc_max_threads": (C.c_int, []),
+            "orc_cost_condition": (d, [vp, vp, vp, vp, vp, vp, vp, u64, u32, d, vp]),
+            "orc_cost_condition_all": (None, [vp, vp, vp, vp, vp, vp, vp, u64, d, vp, C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -317,6 +319,34 @@ def solve(params, gait, x0, xref, f_ext, shift, iter0, mean, var, nthreads=1):
                          _p(mppi_mean), nthreads)
     return {"status": st, "mean": mean, "var": var, "u0": u0, "beta": info[0], "ess": info[1],
             "f_mean": info[2], "J": J, "q": q, "elite": elite, "mppi_mean": mppi_mean}
+
+
+EPS_FP32 = 2.0 ** -23
+
+
+def cost_condition(params, gait, x0, xref, f_ext, mean, var, it, k, eps=EPS_FP32):
+    """Relative change of sample k's cost under rounding-sized perturbations."""
+    D = dim(params)
+    x0 = _f64(x0, 12)
+    xref = _f64(xref, 12 * params.H)
+    fe = None if f_ext is None else _f64(f_ext, 3)
+    mean, var = _f64(mean, D), _f64(var, D)
+    J = C.c_double()
+    kap = lib().orc_cost_condition(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(mean),
+                                   _p(var), it, k, eps, C.byref(J))
+    return kap, J.value
+
+
+def cost_condition_all(params, gait, x0, xref, f_ext, mean, var, it, eps=EPS_FP32, nthreads=1):
+    D = dim(params)
+    x0 = _f64(x0, 12)
+    xref = _f64(xref, 12 * params.H)
+    fe = None if f_ext is None else _f64(f_ext, 3)
+    mean, var = _f64(mean, D), _f64(var, D)
+    kap = np.zeros(params.K)
+    lib().orc_cost_condition_all(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(mean),
+                                 _p(var), it, eps, _p(kap), nthreads)
+    return kap
 
 
 def max_threads():

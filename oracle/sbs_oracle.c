@@ -460,8 +460,30 @@ typedef struct {
     uint64_t iter;
 } rollout_ctx;
 
+/* Sign of a perturbation: a fixed integer hash of (key, a, b) mapped to +-1.
+ * (Only used by the conditioning estimate below, never by the method.) */
+static double pert_sign(uint64_t key, uint64_t a, uint64_t b)
+{
+    uint64_t z = key * 0x9E3779B97F4A7C15ull + a * 0xBF58476D1CE4E5B9ull + b * 0x94D049BB133111EBull;
+    z ^= z >> 31; z *= 0xD6E8D07A4F2C6F35ull; z ^= z >> 29;
+    return (z & 1ull) ? 1.0 : -1.0;
+}
+
+static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override, double* theta,
+                           uint32_t* q_out, double* margin_out, double eps, uint64_t pkey);
+
 static double rollout_one(const rollout_ctx* c, uint32_t k, int64_t q_override, double* theta,
                           uint32_t* q_out, double* margin_out)
+{
+    return rollout_core(c, k, q_override, theta, q_out, margin_out, 0.0, 0);
+}
+
+/* The rollout of Alg. 2.  With eps > 0 (conditioning estimate only) every force
+ * and every state component is multiplied by (1 +- eps) after it is formed, the
+ * signs fixed by pkey: a model of the per-operation rounding of a
+ * lower-precision evaluation. */
+static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override, double* theta,
+                           uint32_t* q_out, double* margin_out, double eps, uint64_t pkey)
 {
     const orc_params* P = c->P;
     int H = P->H, nt = P->P > 0 ? P->P : H;
@@ -497,10 +519,13 @@ static double rollout_one(const rollout_ctx* c, uint32_t k, int64_t q_override, 
                 val = theta[12 * j + n];
             }
             u[n] = st[n / 3] ? val : 0.0;
+            if (eps > 0) u[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j, (uint64_t)n);
         }
         J += orc_stage_cost(P, x, c->xref + NX * j, u, st);
         orc_srbd_step(P, x, u, c->f_ext, dt, xn);
         memcpy(x, xn, sizeof(x));
+        if (eps > 0)
+            for (int n = 0; n < NX; ++n) x[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j + 1, (uint64_t)n);
     }
     if (P->adaptive) {
         double d = q / 1000.0 - P->f_nominal;
@@ -552,6 +577,51 @@ double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* 
     double J = rollout_one(&c, k, q_override, theta, NULL, NULL);
     free(B);
     return J;
+}
+
+/* Conditioning estimate of sample k's cost (test infrastructure): the relative
+ * change of J when the rollout is repeated with every force and state component
+ * perturbed by a relative eps per step (two sign patterns, the larger change).
+ * A cost that moves by more than the parity tolerance under rounding-sized
+ * perturbations cannot be reproduced to that tolerance by any single-precision
+ * evaluation; such samples are ill-conditioned. */
+double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
+                          const double* f_ext, const double* mean, const double* var, uint64_t iter,
+                          uint32_t k, double eps, double* J_out)
+{
+    double* B = NULL;
+    if (P->P > 0) {
+        B = (double*)malloc(sizeof(double) * P->H * P->P);
+        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
+    }
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter};
+    double* th = (double*)malloc(sizeof(double) * orc_dim(P));
+    uint32_t q;
+    double J = rollout_core(&c, k, -1, th, &q, NULL, 0.0, 0);
+    double worst = 0.0;
+    for (uint64_t key = 1; key <= 2; ++key) {
+        double Jp = rollout_core(&c, k, (int64_t)q, th, NULL, NULL, eps, key * 1000003ull + k);
+        double d;
+        if (isinf(J) && isinf(Jp)) d = 0.0;
+        else if (isinf(J) || isinf(Jp)) d = INFINITY;
+        else d = fabs(Jp - J) / fmax(fabs(J), 1e-300);
+        if (d > worst) worst = d;
+    }
+    if (J_out) *J_out = J;
+    free(th);
+    free(B);
+    return worst;
+}
+
+/* Conditioning of all K samples (parallel over samples). */
+void orc_cost_condition_all(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
+                            const double* f_ext, const double* mean, const double* var, uint64_t iter,
+                            double eps, double* kappa, int nthreads)
+{
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int k = 0; k < P->K; ++k)
+        kappa[k] = orc_cost_condition(P, g, x0, xref, f_ext, mean, var, iter, (uint32_t)k, eps, NULL);
 }
 
 /* ------------------------------------------------------------------------- */

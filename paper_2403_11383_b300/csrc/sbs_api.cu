@@ -1,0 +1,782 @@
+// Host side of the C ABI declared in include/sbs.h: validation, device-state
+// layout, the plain per-solve launch sequence, batched graph-captured ticks,
+// checkpoints and the FP32 peak microbenchmark.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sbs_internal.h"
+
+using namespace sbs;
+
+struct sbs_handle {
+    sbs_config cfg;
+    InstParams hP;         // host copy (device pointers filled in)
+    InstParams* dP;        // device copy
+    char* dev_base;
+    size_t dev_bytes;
+    sbs_allocator alloc;
+    bool has_alloc;
+    int device;
+    int cur;               // current state buffer
+    uint64_t iter;         // Philox iteration counter of the next iteration
+    bool initialized;
+    float* dev_in;         // device staging of host inputs: x0 (12) | f_ext (3) | pad | xref (12 H)
+    sbs_result* res_dev;   // device result for host-memory solves
+    float* pin_in;         // pinned host staging of inputs
+    cudaEvent_t in_done;   // last copy out of pin_in has run
+    bool in_pending;
+};
+
+namespace {
+
+constexpr uint32_t kStateMagic = 0x53425331u;  // "SBS1"
+
+bool finite_all(const float* p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int validate(const sbs_config* c)
+{
+    if (!c) return SBS_ERR_INVALID_ARG;
+    if (c->K < 1 || c->K > SBS_MAX_K) return SBS_ERR_INVALID_ARG;
+    if (c->H < 1 || c->H > SBS_MAX_H) return SBS_ERR_INVALID_ARG;
+    if (!(c->P == 0 || c->P == 2 || c->P == 3 || c->P == 4 || c->P == 6 || c->P == 8)) return SBS_ERR_INVALID_ARG;
+    if (c->P > 0 && c->H < 2) return SBS_ERR_INVALID_ARG;
+    if (c->method < SBS_MPPI || c->method > SBS_NAIVE) return SBS_ERR_INVALID_ARG;
+    if (c->iterations < 1 || c->iterations > 1000) return SBS_ERR_INVALID_ARG;
+    if (c->method == SBS_ELITE && (c->elite_count < 1 || c->elite_count > c->K)) return SBS_ERR_INVALID_ARG;
+    if (c->dt_us < 1 || c->dt_us > 1000000) return SBS_ERR_INVALID_ARG;
+    if (!(c->lambda > 0.0f) || !std::isfinite(c->lambda)) return SBS_ERR_INVALID_ARG;
+    if (!(c->f_min > 0.0f) || !(c->f_max >= c->f_min) || !std::isfinite(c->f_max)) return SBS_ERR_INVALID_ARG;
+    // the per-step phase advance q * dt_us must stay below one cycle
+    const double qmax = std::max<double>(c->q_init, std::floor(1000.0 * c->f_max + 0.5) + 1.0);
+    if (qmax * c->dt_us >= 1e9) return SBS_ERR_INVALID_ARG;
+    if (c->q_init < 1) return SBS_ERR_INVALID_ARG;
+    if (!(c->sigma_init >= 0.0f) || !(c->sigma_min >= 0.0f) || !(c->sigma_f_init >= 0.0f) || !(c->sigma_f_min >= 0.0f))
+        return SBS_ERR_INVALID_ARG;
+    if (c->tile != 0 && (c->tile < 64 || c->tile > SBS_MAX_TILE || c->tile % 32 != 0)) return SBS_ERR_INVALID_ARG;
+    const sbs_model& m = c->model;
+    if (!(m.mass > 0.0f)) return SBS_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(m.inertia[a] > 0.0f)) return SBS_ERR_INVALID_ARG;
+    if (!finite_all(&m.foot[0][0], 12) || !finite_all(m.gravity, 3)) return SBS_ERR_INVALID_ARG;
+    const sbs_cost& k = c->cost;
+    if (!finite_all(k.Q, 12) || !finite_all(k.R, 3)) return SBS_ERR_INVALID_ARG;
+    for (int i = 0; i < 12; ++i)
+        if (k.Q[i] < 0) return SBS_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (k.R[i] < 0) return SBS_ERR_INVALID_ARG;
+    if (!(k.w_fc >= 0) || !(k.mu >= 0) || !(k.rho >= 0) || !std::isfinite(k.f_nominal)) return SBS_ERR_INVALID_ARG;
+    return SBS_OK;
+}
+
+int validate_gait(const sbs_gait* g)
+{
+    if (!g) return SBS_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (g->offset[i] >= kPhaseOne) return SBS_ERR_INVALID_ARG;
+    if (g->duty > kPhaseOne || g->phase0 >= kPhaseOne) return SBS_ERR_INVALID_ARG;
+    return SBS_OK;
+}
+
+// ---------------------------------------------------------------- natural cubic spline (Sec. IV-B)
+// Knots at t_p = p T / (P - 1), T = (H - 1) dt.  The second derivatives M solve
+// the natural-spline system; here the system is assembled in full (end rows
+// M_0 = M_{P-1} = 0) and solved for the P x P matrix X with M = X y by Gaussian
+// elimination with partial pivoting.
+struct Spline {
+    int P;
+    double h;
+    std::vector<double> tk, X;  // X: P x P
+
+    Spline(int H, int P_, double dt) : P(P_), tk(P_), X((size_t)P_ * P_, 0.0)
+    {
+        const double T = (H - 1) * dt;
+        h = T / (P - 1);
+        for (int p = 0; p < P; ++p) tk[p] = T * p / (P - 1);
+        std::vector<double> A((size_t)P * P, 0.0), Rhs((size_t)P * P, 0.0);
+        A[0] = 1.0;
+        A[(size_t)(P - 1) * P + P - 1] = 1.0;
+        for (int i = 1; i < P - 1; ++i) {
+            A[(size_t)i * P + i - 1] = h;
+            A[(size_t)i * P + i] = 4.0 * h;
+            A[(size_t)i * P + i + 1] = h;
+            Rhs[(size_t)i * P + i - 1] = 6.0 / h;
+            Rhs[(size_t)i * P + i] = -12.0 / h;
+            Rhs[(size_t)i * P + i + 1] = 6.0 / h;
+        }
+        // solve A X = Rhs
+        for (int col = 0; col < P; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < P; ++r)
+                if (std::fabs(A[(size_t)r * P + col]) > std::fabs(A[(size_t)piv * P + col])) piv = r;
+            if (piv != col)
+                for (int c = 0; c < P; ++c) {
+                    std::swap(A[(size_t)piv * P + c], A[(size_t)col * P + c]);
+                    std::swap(Rhs[(size_t)piv * P + c], Rhs[(size_t)col * P + c]);
+                }
+            for (int r = 0; r < P; ++r) {
+                if (r == col) continue;
+                const double f = A[(size_t)r * P + col] / A[(size_t)col * P + col];
+                if (f == 0.0) continue;
+                for (int c = 0; c < P; ++c) {
+                    A[(size_t)r * P + c] -= f * A[(size_t)col * P + c];
+                    Rhs[(size_t)r * P + c] -= f * Rhs[(size_t)col * P + c];
+                }
+            }
+        }
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) X[(size_t)r * P + c] = Rhs[(size_t)r * P + c] / A[(size_t)r * P + r];
+    }
+
+    // weight of knot value y_p in the spline's value at time t (clamped to [0, T])
+    double weight(double t, int p) const
+    {
+        t = std::min(std::max(t, tk[0]), tk[P - 1]);
+        int s = (int)std::floor((t - tk[0]) / h);
+        s = std::min(std::max(s, 0), P - 2);
+        const double a = tk[s + 1] - t, b = t - tk[s];
+        const double Ms = X[(size_t)s * P + p], Ms1 = X[(size_t)(s + 1) * P + p];
+        const double ys = (p == s) ? 1.0 : 0.0, ys1 = (p == s + 1) ? 1.0 : 0.0;
+        return Ms * a * a * a / (6.0 * h) + Ms1 * b * b * b / (6.0 * h) + (ys / h - Ms * h / 6.0) * a +
+               (ys1 / h - Ms1 * h / 6.0) * b;
+    }
+};
+
+// ---------------------------------------------------------------- allocation
+void* dev_alloc(const sbs_allocator* a, bool has, size_t bytes)
+{
+    if (has) return a->alloc(bytes, a->ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(const sbs_allocator* a, bool has, void* p)
+{
+    if (!p) return;
+    if (has) a->free(p, a->ctx);
+    else cudaFree(p);
+}
+
+TickArgs make_tick(const sbs_handle* h, const sbs_gait& g)
+{
+    TickArgs t;
+    std::memset(&t, 0, sizeof(t));
+    for (int i = 0; i < 4; ++i) t.offset[i] = g.offset[i];
+    t.duty = g.duty;
+    t.phase0 = g.phase0;
+    t.src = h->cur;
+    t.iter = h->iter;
+    return t;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* sbs_status_str(int s)
+{
+    switch (s) {
+        case SBS_OK: return "ok";
+        case SBS_PENDING: return "pending";
+        case SBS_ERR_INVALID_ARG: return "invalid argument";
+        case SBS_ERR_OOM: return "out of device memory";
+        case SBS_ERR_BUDGET: return "over the device-memory budget";
+        case SBS_ERR_CUDA: return "CUDA error";
+        case SBS_ERR_TIMEOUT: return "timed out";
+        case SBS_ERR_DIVERGED: return "no finite cost (diverged)";
+        default: return "unknown status";
+    }
+}
+
+int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** out)
+{
+    if (!out) return SBS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int st = validate(cfg);
+    if (st) return st;
+    if (alloc && (!alloc->alloc || !alloc->free)) return SBS_ERR_INVALID_ARG;
+    sbs_handle* h = new (std::nothrow) sbs_handle();
+    if (!h) return SBS_ERR_OOM;
+    h->cfg = *cfg;
+    h->has_alloc = alloc != nullptr;
+    if (alloc) h->alloc = *alloc;
+    cudaGetDevice(&h->device);
+
+    InstParams& P = h->hP;
+    std::memset(&P, 0, sizeof(P));
+    P.K = cfg->K;
+    P.H = cfg->H;
+    P.P = cfg->P;
+    P.nt = cfg->P > 0 ? cfg->P : cfg->H;
+    P.nf = 12 * P.nt;
+    P.adaptive = cfg->adaptive ? 1 : 0;
+    P.D = P.nf + P.adaptive;
+    P.method = cfg->method;
+    P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
+    P.T = cfg->tile ? cfg->tile : 128;
+    P.ntiles = (cfg->K + P.T - 1) / P.T;
+    P.compare_mppi = cfg->compare_mppi ? 1 : 0;
+    P.part_stride = kPartHeader + P.nf;
+    P.dt_us = cfg->dt_us;
+    P.q_init = cfg->q_init;
+    P.seed = cfg->seed;
+    P.ctrl = cfg->controller_id;
+    P.dt = (float)(cfg->dt_us * 1e-6);
+    P.lambda = cfg->lambda;
+    P.inv_lambda = 1.0f / cfg->lambda;
+    P.inv_mass = 1.0f / cfg->model.mass;
+    P.weight_z = cfg->model.mass * -cfg->model.gravity[2];
+    for (int a = 0; a < 3; ++a) {
+        P.inertia[a] = cfg->model.inertia[a];
+        P.inv_inertia[a] = 1.0f / cfg->model.inertia[a];
+        P.gravity[a] = cfg->model.gravity[a];
+        P.R[a] = cfg->cost.R[a];
+    }
+    std::memcpy(P.foot, &cfg->model.foot[0][0], sizeof(P.foot));
+    std::memcpy(P.Q, cfg->cost.Q, sizeof(P.Q));
+    P.w_fc = cfg->cost.w_fc;
+    P.mu = cfg->cost.mu;
+    P.rho = cfg->cost.rho;
+    P.f_nominal = cfg->cost.f_nominal;
+    P.f_min = cfg->f_min;
+    P.f_max = cfg->f_max;
+    P.var_init = cfg->sigma_init * cfg->sigma_init;
+    P.var_min = cfg->sigma_min * cfg->sigma_min;
+    P.var_f_init = cfg->sigma_f_init * cfg->sigma_f_init;
+    P.var_f_min = cfg->sigma_f_min * cfg->sigma_f_min;
+
+    // device layout (256-byte aligned pieces)
+    const size_t D = P.D;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_params = take(sizeof(InstParams));
+    const size_t o_state0 = take(2 * D * sizeof(float));
+    const size_t o_state1 = take(2 * D * sizeof(float));
+    const size_t o_J = take((size_t)P.K * sizeof(float));
+    const size_t o_q = take((size_t)P.K * sizeof(int32_t));
+    const size_t o_part = take((size_t)P.ntiles * P.part_stride * sizeof(float));
+    const size_t o_elite = take((size_t)std::max(P.Ke, 1) * sizeof(int32_t));
+    const size_t o_counter = take(16);
+    const size_t o_mppi = take(D * sizeof(float));
+    const size_t o_B = take(P.P > 0 ? (size_t)P.H * P.P * sizeof(float) : 0);
+    const size_t o_S = take(P.P > 0 ? (size_t)P.P * P.P * sizeof(float) : 0);
+    const size_t o_res = take(sizeof(sbs_result));
+    const size_t in_floats = 16 + 12 * (size_t)P.H;
+    const size_t o_in = take(in_floats * sizeof(float));
+    h->dev_bytes = off;
+    h->dev_base = (char*)dev_alloc(&h->alloc, h->has_alloc, off);
+    if (!h->dev_base) {
+        delete h;
+        return SBS_ERR_OOM;
+    }
+    char* b = h->dev_base;
+    h->dP = (InstParams*)(b + o_params);
+    P.state[0] = (float*)(b + o_state0);
+    P.state[1] = (float*)(b + o_state1);
+    P.J = (float*)(b + o_J);
+    P.q = (int32_t*)(b + o_q);
+    P.part = (float*)(b + o_part);
+    P.elite = (int32_t*)(b + o_elite);
+    P.counter = (unsigned*)(b + o_counter);
+    P.mppi_mean = (float*)(b + o_mppi);
+    P.Bsp = P.P > 0 ? (const float*)(b + o_B) : nullptr;
+    P.Ssp = P.P > 0 ? (const float*)(b + o_S) : nullptr;
+    h->res_dev = (sbs_result*)(b + o_res);
+    h->dev_in = (float*)(b + o_in);
+
+    cudaError_t e = cudaMemset(b, 0, off);
+    if (e == cudaSuccess && P.P > 0) {
+        // spline basis B[j][p] = weight of knot p at t_j, and the one-step shift map
+        // S[p][r] = weight of knot r at t_p + dt (held at the horizon end)
+        Spline sp(P.H, P.P, cfg->dt_us * 1e-6);
+        std::vector<float> B((size_t)P.H * P.P), S((size_t)P.P * P.P);
+        const double dt = cfg->dt_us * 1e-6;
+        for (int j = 0; j < P.H; ++j)
+            for (int p = 0; p < P.P; ++p) B[(size_t)j * P.P + p] = (float)sp.weight(j * dt, p);
+        for (int p = 0; p < P.P; ++p)
+            for (int r = 0; r < P.P; ++r) S[(size_t)p * P.P + r] = (float)sp.weight(sp.tk[p] + dt, r);
+        e = cudaMemcpy((void*)P.Bsp, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy((void*)P.Ssp, S.data(), S.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h->dP, &P, sizeof(P), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&h->pin_in, in_floats * sizeof(float), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->in_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->pin_in) cudaFreeHost(h->pin_in);
+        dev_free(&h->alloc, h->has_alloc, h->dev_base);
+        delete h;
+        return SBS_ERR_CUDA;
+    }
+    h->cur = 0;
+    h->iter = 0;
+    h->initialized = false;
+    *out = h;
+    return SBS_OK;
+}
+
+void sbs_destroy(sbs_handle* h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    if (h->in_done) cudaEventDestroy(h->in_done);
+    if (h->pin_in) cudaFreeHost(h->pin_in);
+    dev_free(&h->alloc, h->has_alloc, h->dev_base);
+    delete h;
+}
+
+int sbs_dim(const sbs_handle* h) { return h ? h->hP.D : SBS_ERR_INVALID_ARG; }
+
+size_t sbs_device_bytes(const sbs_handle* h) { return h ? h->dev_bytes : 0; }
+
+int sbs_reset(sbs_handle* h, const sbs_gait* gait, uint64_t iter, void* stream)
+{
+    if (!h) return SBS_ERR_INVALID_ARG;
+    int st = validate_gait(gait);
+    if (st) return st;
+    h->iter = iter;
+    TickArgs t = make_tick(h, *gait);
+    st = launch_init(h->dP, h->hP, t, stream);
+    if (st) return st;
+    h->initialized = true;
+    return SBS_OK;
+}
+
+int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* stream)
+{
+    if (!h || !prob || !result || !prob->x0 || !prob->xref) return SBS_ERR_INVALID_ARG;
+    int st = validate_gait(&prob->gait);
+    if (st) return st;
+    const InstParams& P = h->hP;
+    if (prob->shift < 0) return SBS_ERR_INVALID_ARG;
+    if (P.P > 0 && prob->shift > 1) return SBS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float *x0 = prob->x0, *xref = prob->xref, *fext = prob->f_ext;
+    sbs_result* res = result;
+    if (prob->host_memory) {
+        if (!finite_all(x0, 12) || !finite_all(xref, 12 * P.H) || (fext && !finite_all(fext, 3)))
+            return SBS_ERR_INVALID_ARG;
+        if (h->in_pending && cudaEventSynchronize(h->in_done) != cudaSuccess) return SBS_ERR_CUDA;
+        std::memcpy(h->pin_in, x0, 12 * sizeof(float));
+        if (fext) std::memcpy(h->pin_in + 12, fext, 3 * sizeof(float));
+        else std::memset(h->pin_in + 12, 0, 3 * sizeof(float));
+        h->pin_in[15] = 0.0f;
+        std::memcpy(h->pin_in + 16, xref, 12 * (size_t)P.H * sizeof(float));
+        if (cudaMemcpyAsync(h->dev_in, h->pin_in, (16 + 12 * (size_t)P.H) * sizeof(float), cudaMemcpyHostToDevice,
+                            s) != cudaSuccess)
+            return SBS_ERR_CUDA;
+        if (cudaEventRecord(h->in_done, s) != cudaSuccess) return SBS_ERR_CUDA;
+        h->in_pending = true;
+        x0 = h->dev_in;
+        fext = h->dev_in + 12;
+        xref = h->dev_in + 16;
+        res = h->res_dev;
+    }
+    int shift = prob->shift;
+    if (!h->initialized) {
+        TickArgs t0 = make_tick(h, prob->gait);
+        st = launch_init(h->dP, P, t0, stream);
+        if (st) return st;
+        h->initialized = true;
+        shift = 0;
+    }
+    for (int it = 0; it < h->cfg.iterations; ++it) {
+        TickArgs t = make_tick(h, prob->gait);
+        t.x0 = x0;
+        t.xref = xref;
+        t.fext = fext;
+        t.shift = it == 0 ? shift : 0;
+        t.partials = (P.method == SBS_MPPI || (P.compare_mppi && it == 0)) ? 1 : 0;
+        t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
+        t.result = res;
+        st = launch_rollout(h->dP, P, t, stream);
+        if (st) return st;
+        if (P.method != SBS_MPPI) {
+            st = launch_refit(h->dP, P, t, stream);
+            if (st) return st;
+        }
+        h->cur ^= 1;
+        h->iter += 1;
+    }
+    if (prob->host_memory) {
+        if (cudaMemcpyAsync(result, h->res_dev, sizeof(sbs_result), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SBS_ERR_CUDA;
+    }
+    return SBS_OK;
+}
+
+int sbs_read(const sbs_handle* h, int which, void* dst, size_t bytes, int host_dst, void* stream)
+{
+    if (!h || !dst) return SBS_ERR_INVALID_ARG;
+    const InstParams& P = h->hP;
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (which) {
+        case SBS_BUF_MEAN: src = P.state[h->cur]; n = P.D * sizeof(float); break;
+        case SBS_BUF_VAR: src = P.state[h->cur] + P.D; n = P.D * sizeof(float); break;
+        case SBS_BUF_COST: src = P.J; n = (size_t)P.K * sizeof(float); break;
+        case SBS_BUF_FREQ: src = P.q; n = (size_t)P.K * sizeof(int32_t); break;
+        case SBS_BUF_ELITE: src = P.elite; n = (size_t)P.Ke * sizeof(int32_t); break;
+        case SBS_BUF_MPPI_MEAN: src = P.mppi_mean; n = P.D * sizeof(float); break;
+        default: return SBS_ERR_INVALID_ARG;
+    }
+    if (bytes != n) return SBS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(dst, src, n, host_dst ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? SBS_OK : SBS_ERR_CUDA;
+}
+
+size_t sbs_state_size(const sbs_handle* h)
+{
+    return h ? 32 + 2 * (size_t)h->hP.D * sizeof(float) : 0;
+}
+
+int sbs_get_state(const sbs_handle* h, void* buf, size_t bytes, void* stream)
+{
+    if (!h || !buf || bytes != sbs_state_size(h)) return SBS_ERR_INVALID_ARG;
+    uint32_t* w = (uint32_t*)buf;
+    std::memset(buf, 0, 32);
+    w[0] = kStateMagic;
+    w[1] = (uint32_t)h->hP.D;
+    w[2] = (uint32_t)h->iter;
+    w[3] = (uint32_t)(h->iter >> 32);
+    w[4] = h->initialized ? 1u : 0u;
+    if (h->initialized) {
+        cudaStream_t s = (cudaStream_t)stream;
+        if (cudaMemcpyAsync((char*)buf + 32, h->hP.state[h->cur], 2 * h->hP.D * sizeof(float), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess)
+            return SBS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SBS_ERR_CUDA;
+    }
+    return SBS_OK;
+}
+
+int sbs_set_state(sbs_handle* h, const void* buf, size_t bytes, void* stream)
+{
+    if (!h || !buf || bytes != sbs_state_size(h)) return SBS_ERR_INVALID_ARG;
+    const uint32_t* w = (const uint32_t*)buf;
+    if (w[0] != kStateMagic || w[1] != (uint32_t)h->hP.D) return SBS_ERR_INVALID_ARG;
+    const uint64_t iter = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+    const bool init = w[4] != 0;
+    if (init) {
+        const float* f = (const float*)((const char*)buf + 32);
+        if (!finite_all(f, 2 * h->hP.D)) return SBS_ERR_INVALID_ARG;
+        cudaStream_t s = (cudaStream_t)stream;
+        if (cudaMemcpyAsync(h->hP.state[h->cur], f, 2 * h->hP.D * sizeof(float), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return SBS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SBS_ERR_CUDA;
+    }
+    h->iter = iter;
+    h->initialized = init;
+    return SBS_OK;
+}
+
+int sbs_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return SBS_ERR_INVALID_ARG;
+    return launch_philox(ctr, key, out, n, stream);
+}
+
+int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream)
+{
+    if (k0 < 0 || nk < 0 || nn < 0 || (nk > 0 && !out)) return SBS_ERR_INVALID_ARG;
+    return launch_normals(seed, ctrl, iter, k0, nk, nn, out, stream);
+}
+
+int sbs_fp32_peak(double* flops, void* stream)
+{
+    if (!flops) return SBS_ERR_INVALID_ARG;
+    int dev, sms;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SBS_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SBS_ERR_CUDA;
+    float* out = nullptr;
+    if (cudaMalloc(&out, 16) != cudaSuccess) return SBS_ERR_OOM;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = 256, blocks = sms * 8, iters = 4096;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int st = launch_fma_peak(out, 64, blocks, threads, stream);
+    float best = 1e30f;
+    for (int rep = 0; rep < 5 && st == SBS_OK; ++rep) {
+        cudaEventRecord(a, s);
+        st = launch_fma_peak(out, iters, blocks, threads, stream);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (st) return st;
+    *flops = 2.0 * 8.0 * 16.0 * (double)iters * threads * blocks / (best * 1e-3);
+    return SBS_OK;
+}
+
+// =====================================================================================
+// Batched ticks
+// =====================================================================================
+struct sbs_batch_slot {
+    char* pin;            // [counts (16 B) | records]
+    char* dev;            // device mirror
+    int* heads;           // device queue heads (2)
+    cudaEvent_t done;
+    bool used;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaGraphNode_t copy_node;
+    size_t key_smem;
+    int key_T;
+    int key_P;
+    int grid1, grid2;
+};
+
+struct sbs_batch {
+    int max_inst, max_tiles;
+    sbs_allocator alloc;
+    bool has_alloc;
+    size_t bytes;
+    sbs_batch_slot slot[2];
+    int next;
+    bool use_graph;
+};
+
+extern "C" int sbs_batch_create(int max_instances, int max_tiles, const sbs_allocator* alloc, sbs_batch** out)
+{
+    if (!out || max_instances < 1 || max_tiles < 1) return SBS_ERR_INVALID_ARG;
+    *out = nullptr;
+    sbs_batch* b = new (std::nothrow) sbs_batch();
+    if (!b) return SBS_ERR_OOM;
+    b->max_inst = max_instances;
+    b->max_tiles = max_tiles;
+    b->has_alloc = alloc != nullptr;
+    if (alloc) b->alloc = *alloc;
+    b->bytes = 16 + (size_t)max_instances * sizeof(InstRec);
+    const char* ng = std::getenv("SBS_NO_GRAPH");
+    b->use_graph = !(ng && ng[0] == '1');
+    for (int i = 0; i < 2; ++i) {
+        sbs_batch_slot& sl = b->slot[i];
+        sl.dev = (char*)dev_alloc(&b->alloc, b->has_alloc, align_up(b->bytes, 256) + 256);
+        if (!sl.dev || cudaHostAlloc((void**)&sl.pin, b->bytes, cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            sbs_batch_destroy(b);
+            return SBS_ERR_OOM;
+        }
+        sl.heads = (int*)(sl.dev + align_up(b->bytes, 256));
+        if (cudaMemset(sl.heads, 0, 16) != cudaSuccess) {
+            sbs_batch_destroy(b);
+            return SBS_ERR_CUDA;
+        }
+    }
+    *out = b;
+    return SBS_OK;
+}
+
+extern "C" void sbs_batch_destroy(sbs_batch* b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i) {
+        sbs_batch_slot& sl = b->slot[i];
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.graph) cudaGraphDestroy(sl.graph);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.pin) cudaFreeHost(sl.pin);
+        dev_free(&b->alloc, b->has_alloc, sl.dev);
+    }
+    delete b;
+}
+
+static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, int T)
+{
+    if (sl.exec) {
+        cudaGraphExecDestroy(sl.exec);
+        sl.exec = nullptr;
+    }
+    if (sl.graph) {
+        cudaGraphDestroy(sl.graph);
+        sl.graph = nullptr;
+    }
+    int st = batch_grid(P, smem, T, &sl.grid1, &sl.grid2);
+    if (st) return st;
+    cudaGraph_t g;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return SBS_ERR_CUDA;
+    cudaGraphNode_t n_cp, n_ms, n_k1, n_k2;
+    bool ok = cudaGraphAddMemcpyNode1D(&n_cp, g, nullptr, 0, sl.dev, sl.pin, b->bytes, cudaMemcpyHostToDevice) ==
+              cudaSuccess;
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.dst = sl.heads;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 2;
+    mp.height = 1;
+    ok = ok && cudaGraphAddMemsetNode(&n_ms, g, &n_cp, 1, &mp) == cudaSuccess;
+    const InstRec* recs = (const InstRec*)(sl.dev + 16);
+    const int* counts = (const int*)sl.dev;
+    int* heads = sl.heads;
+    void* args[] = {(void*)&recs, (void*)&counts, (void*)&heads};
+    cudaKernelNodeParams k1;
+    std::memset(&k1, 0, sizeof(k1));
+    k1.func = (void*)batch_rollout_fn(P);
+    k1.gridDim = dim3(sl.grid1);
+    k1.blockDim = dim3(T);
+    k1.sharedMemBytes = (unsigned)smem;
+    k1.kernelParams = args;
+    ok = ok && cudaGraphAddKernelNode(&n_k1, g, &n_ms, 1, &k1) == cudaSuccess;
+    cudaKernelNodeParams k2 = k1;
+    k2.func = (void*)batch_refit_fn();
+    k2.gridDim = dim3(sl.grid2);
+    k2.blockDim = dim3(kRefitThreads);
+    k2.sharedMemBytes = 0;
+    ok = ok && cudaGraphAddKernelNode(&n_k2, g, &n_k1, 1, &k2) == cudaSuccess;
+    cudaGraphExec_t ex = nullptr;
+    ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return SBS_ERR_CUDA;
+    }
+    sl.graph = g;
+    sl.exec = ex;
+    sl.copy_node = n_cp;
+    sl.key_smem = smem;
+    sl.key_T = T;
+    sl.key_P = P;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                               sbs_result* results, void* stream)
+{
+    if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int T = handles[0] ? handles[0]->hP.T : 0;
+    const int Pk = handles[0] ? handles[0]->hP.P : 0;
+    size_t smem = 0;
+    long long items = 0;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) {
+        const sbs_handle* h = handles[i];
+        const sbs_problem* p = &probs[i];
+        if (!h || !p->x0 || !p->xref || p->host_memory || h->hP.T != T || h->hP.P != Pk) return SBS_ERR_INVALID_ARG;
+        if (h->hP.method != SBS_MPPI && h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
+        if (h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
+        if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
+        smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T));
+        items += h->hP.ntiles;
+        order[i] = i;
+    }
+    if (items > b->max_tiles) return SBS_ERR_INVALID_ARG;
+    {
+        std::vector<const sbs_handle*> u(handles, handles + n);
+        std::sort(u.begin(), u.end());
+        if (std::adjacent_find(u.begin(), u.end()) != u.end()) return SBS_ERR_INVALID_ARG;
+    }
+    // heavier tiles first (longer horizon, then more tiles) so the tail is short
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const InstParams &A = handles[a]->hP, &C = handles[c]->hP;
+        if (A.H != C.H) return A.H > C.H;
+        return A.ntiles > C.ntiles;
+    });
+    sbs_batch_slot& sl = b->slot[b->next];
+    b->next ^= 1;
+    if (sl.used && cudaEventSynchronize(sl.done) != cudaSuccess) return SBS_ERR_CUDA;
+    // controllers solved for the first time start from their initial distribution
+    for (int i = 0; i < n; ++i) {
+        sbs_handle* h = handles[i];
+        if (!h->initialized) {
+            TickArgs t0 = make_tick(h, probs[i].gait);
+            int st = launch_init(h->dP, h->hP, t0, stream);
+            if (st) return st;
+        }
+    }
+    int* counts = (int*)sl.pin;
+    InstRec* recs = (InstRec*)(sl.pin + 16);
+    int tile_begin = 0, refit_begin = 0;
+    for (int r = 0; r < n; ++r) {
+        const int i = order[r];
+        sbs_handle* h = handles[i];
+        const InstParams& P = h->hP;
+        InstRec& R = recs[r];
+        R.t = make_tick(h, probs[i].gait);
+        R.t.x0 = probs[i].x0;
+        R.t.xref = probs[i].xref;
+        R.t.fext = probs[i].f_ext;
+        R.t.shift = h->initialized ? probs[i].shift : 0;
+        R.t.partials = (P.method == SBS_MPPI || P.compare_mppi) ? 1 : 0;
+        R.t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
+        R.t.result = results + i;
+        R.dP = h->dP;
+        R.tile_begin = tile_begin;
+        R.refit_begin = refit_begin;
+        tile_begin += P.ntiles;
+        if (P.method != SBS_MPPI) refit_begin += P.nt + P.adaptive;
+    }
+    counts[0] = n;
+    counts[1] = tile_begin;
+    counts[2] = refit_begin;
+    counts[3] = 0;
+    const size_t used = 16 + (size_t)n * sizeof(InstRec);
+    int st = SBS_OK;
+    if (b->use_graph) {
+        if (!sl.exec || sl.key_smem != smem || sl.key_T != T || sl.key_P != Pk) {
+            st = build_graph(b, sl, Pk, smem, T);
+            if (st) return st;
+        }
+        if (cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.pin, used,
+                                               cudaMemcpyHostToDevice) != cudaSuccess)
+            return SBS_ERR_CUDA;
+        if (cudaGraphLaunch(sl.exec, s) != cudaSuccess) return SBS_ERR_CUDA;
+    } else {
+        if (sl.key_smem != smem || sl.key_T != T || sl.key_P != Pk) {
+            st = batch_grid(Pk, smem, T, &sl.grid1, &sl.grid2);
+            if (st) return st;
+            sl.key_smem = smem;
+            sl.key_T = T;
+            sl.key_P = Pk;
+            if (sl.exec) {
+                cudaGraphExecDestroy(sl.exec);
+                sl.exec = nullptr;
+            }
+        }
+        if (cudaMemcpyAsync(sl.dev, sl.pin, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return SBS_ERR_CUDA;
+        if (cudaMemsetAsync(sl.heads, 0, 8, s) != cudaSuccess) return SBS_ERR_CUDA;
+        st = launch_batch(Pk, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, T, sl.grid1, sl.grid2,
+                          stream);
+        if (st) return st;
+    }
+    if (cudaEventRecord(sl.done, s) != cudaSuccess) return SBS_ERR_CUDA;
+    sl.used = true;
+    for (int i = 0; i < n; ++i) {
+        sbs_handle* h = handles[i];
+        h->initialized = true;
+        h->cur ^= 1;
+        h->iter += 1;
+    }
+    return SBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// Device building blocks of the SBS controller: counter-based random numbers,
+// the single-rigid-body model step, the stage cost and block reductions.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "sbs_internal.h"
+
+namespace sbs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies; the high halves are XORed with the other counter words and the
+// round key, which advances by the Weyl constants each round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += W0;
+        k1 += W1;
+    }
+    return c;
+}
+
+// Box-Muller on two words: the top 24 bits give exact uniforms u1 in (0, 1]
+// and u2 in [0, 1).
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
+{
+    const float two_m24 = 5.9604644775390625e-8f;
+    const float u1 = __uint2float_rn((a >> 8) + 1u) * two_m24;
+    const float u2 = __uint2float_rn(b >> 8) * two_m24;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// The four normals of one draw: counter (k, draw, iter lo, iter hi), key (seed, ctrl).
+__device__ __forceinline__ float4 normals4(uint32_t k, uint32_t draw, uint64_t iter, uint32_t seed,
+                                           uint32_t ctrl)
+{
+    const uint4 w = philox4x32_10(make_uint4(k, draw, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
+    const float2 a = box_muller(w.x, w.y);
+    const float2 b = box_muller(w.z, w.w);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// The 12 normals of step (or knot) j: draws 1 + 3j .. 3 + 3j.
+__device__ __forceinline__ void normals12(uint32_t k, int j, uint64_t iter, uint32_t seed, uint32_t ctrl,
+                                          float e[12])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float4 z = normals4(k, 1u + 3u * (uint32_t)j + (uint32_t)d, iter, seed, ctrl);
+        e[4 * d + 0] = z.x;
+        e[4 * d + 1] = z.y;
+        e[4 * d + 2] = z.z;
+        e[4 * d + 3] = z.w;
+    }
+}
+
+// Step frequency of sample k (Sec. IV-C): clip(mu_f + sigma_f z, f_min, f_max)
+// quantised to integer mHz.  The exact single-precision sequence (one fused
+// multiply-add, one multiply, one add, floor) defines the rounding.
+__device__ __forceinline__ uint32_t sample_freq(uint32_t k, uint64_t iter, uint32_t seed, uint32_t ctrl,
+                                                float mu_f, float sig_f, float f_min, float f_max)
+{
+    const uint4 w = philox4x32_10(make_uint4(k, 0u, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
+    const float z = box_muller(w.x, w.y).x;
+    float f = __fmaf_rn(sig_f, z, mu_f);
+    if (f < f_min) f = f_min;
+    if (f > f_max) f = f_max;
+    const float t = __fmul_rn(1000.0f, f);
+    return (uint32_t)floorf(__fadd_rn(t, 0.5f));
+}
+
+__device__ __forceinline__ uint32_t quantise_mhz(float f, float f_min, float f_max)
+{
+    if (f < f_min) f = f_min;
+    if (f > f_max) f = f_max;
+    return (uint32_t)floorf(__fadd_rn(__fmul_rn(1000.0f, f), 0.5f));
+}
+
+// Contact flag of one leg at step j for frequency q (mHz); 64-bit exact phase.
+__device__ __forceinline__ int stance_at(const TickArgs& t, int leg, uint32_t q, uint32_t dt_us, int j)
+{
+    const uint64_t ph = ((uint64_t)t.phase0 + t.offset[leg] + (uint64_t)j * q * dt_us) % kPhaseOne;
+    return ph < (uint64_t)t.duty ? 1 : 0;
+}
+
+// Kahan-compensated accumulation.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// ---------------------------------------------------------------------------
+// One explicit-Euler step of Eq. (1) plus the stage cost of the pre-step state
+// (Alg. 2 charges r(u_i, x_i, x^r_i) before x_{i+1} = f(x_i, u_i)).
+// G: world-frame forces already zeroed on swing legs.  fe: f_ext / m.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float stage_cost(const InstParams& P, const float x[12], const float* xr,
+                                            const float G[12])
+{
+    float r = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const float e = x[c] - xr[c];
+        r = fmaf(P.Q[c] * e, e, r);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
+        r = fmaf(P.R[0] * gx, gx, r);
+        r = fmaf(P.R[1] * gy, gy, r);
+        r = fmaf(P.R[2] * gz, gz, r);
+        // friction cone on stance legs; a swing leg's zero force adds nothing
+        const float slip = sqrtf(fmaf(gx, gx, gy * gy)) - P.mu * gz;
+        float pen = slip > 0.0f ? slip * slip : 0.0f;
+        pen += gz < 0.0f ? gz * gz : 0.0f;
+        r = fmaf(P.w_fc, pen, r);
+    }
+    return r;
+}
+
+// sin and cos of an attitude angle.  Beyond 1e5 rad (a rollout that has long left
+// any meaningful attitude) the argument reduction of the accurate routine would
+// take its slow path; the hardware approximation is used there instead.
+__device__ __forceinline__ void angle_sincos(float a, float* s, float* c)
+{
+    if (fabsf(a) <= 1.0e5f) sincosf(a, s, c);
+    else __sincosf(a, s, c);
+}
+
+__device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], const float G[12],
+                                          const float fe[3])
+{
+    float sr, cr, sp, cp, sy, cy;
+    angle_sincos(x[3], &sr, &cr);
+    angle_sincos(x[4], &sp, &cp);
+    angle_sincos(x[5], &sy, &cy);
+    // body-to-world R = Rz(yaw) Ry(pitch) Rx(roll)
+    const float R00 = cy * cp, R01 = cy * sp * sr - sy * cr, R02 = cy * sp * cr + sy * sr;
+    const float R10 = sy * cp, R11 = sy * sp * sr + cy * cr, R12 = sy * sp * cr - cy * sr;
+    const float R20 = -sp, R21 = cp * sr, R22 = cp * cr;
+    float F0 = 0.f, F1 = 0.f, F2 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
+        F0 += gx;
+        F1 += gy;
+        F2 += gz;
+        // body-frame force R^T Gamma_i, then the lever arm cross product
+        const float bx = R00 * gx + R10 * gy + R20 * gz;
+        const float by = R01 * gx + R11 * gy + R21 * gz;
+        const float bz = R02 * gx + R12 * gy + R22 * gz;
+        const float rx = P.foot[3 * i], ry = P.foot[3 * i + 1], rz = P.foot[3 * i + 2];
+        t0 += ry * bz - rz * by;
+        t1 += rz * bx - rx * bz;
+        t2 += rx * by - ry * bx;
+    }
+    const float w0 = x[9], w1 = x[10], w2 = x[11];
+    const float L0 = P.inertia[0] * w0, L1 = P.inertia[1] * w1, L2 = P.inertia[2] * w2;
+    const float wd0 = (t0 - (w1 * L2 - w2 * L1)) * P.inv_inertia[0];
+    const float wd1 = (t1 - (w2 * L0 - w0 * L2)) * P.inv_inertia[1];
+    const float wd2 = (t2 - (w0 * L1 - w1 * L0)) * P.inv_inertia[2];
+    // E'^{-1}(Phi) omega for the ZYX angles
+    const float ic = __frcp_rn(cp);
+    const float a = sr * w1 + cr * w2;
+    const float rd = w0 + sp * ic * a;
+    const float pd = cr * w1 - sr * w2;
+    const float yd = a * ic;
+    const float dt = P.dt;
+    const float vd0 = fmaf(F0 + fe[0], P.inv_mass, P.gravity[0]);
+    const float vd1 = fmaf(F1 + fe[1], P.inv_mass, P.gravity[1]);
+    const float vd2 = fmaf(F2 + fe[2], P.inv_mass, P.gravity[2]);
+    x[0] = fmaf(dt, x[6], x[0]);
+    x[1] = fmaf(dt, x[7], x[1]);
+    x[2] = fmaf(dt, x[8], x[2]);
+    x[3] = fmaf(dt, rd, x[3]);
+    x[4] = fmaf(dt, pd, x[4]);
+    x[5] = fmaf(dt, yd, x[5]);
+    x[6] = fmaf(dt, vd0, x[6]);
+    x[7] = fmaf(dt, vd1, x[7]);
+    x[8] = fmaf(dt, vd2, x[8]);
+    x[9] = fmaf(dt, wd0, w0);
+    x[10] = fmaf(dt, wd1, w1);
+    x[11] = fmaf(dt, wd2, w2);
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Sum of 12 per-lane values over a warp.  On return, lane l holds the warp
+// totals of components c0 + 0..2 with c0 = 6 (l & 16 ? 1 : 0) + 3 (l & 8 ? 1 : 0);
+// lanes with (l & 7) == 0 are the designated writers.  18 shuffles in place of
+// 60 for twelve independent butterflies.
+__device__ __forceinline__ int warp_sum12(const float v[12], float out[3])
+{
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    float a[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float send = h16 ? v[i] : v[i + 6];
+        const float keep = h16 ? v[i + 6] : v[i];
+        a[i] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float send = h8 ? a[i] : a[i + 3];
+        const float keep = h8 ? a[i + 3] : a[i];
+        out[i] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) out[i] += __shfl_xor_sync(kFull, out[i], o);
+    }
+    return (h16 ? 6 : 0) + (h8 ? 3 : 0);
+}
+
+// Order-preserving map of a float cost to an unsigned key (NaN never occurs:
+// non-finite costs are stored as +inf).
+__device__ __forceinline__ uint32_t cost_key(float J)
+{
+    const uint32_t b = __float_as_uint(J);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+}  // namespace sbs

@@ -1,0 +1,358 @@
+"""Python binding of libsbs (include/sbs.h): argument marshalling only.
+
+Every step of the controller runs in the library's CUDA kernels.  PyTorch
+provides device memory (through the allocator callbacks below) and streams.
+The binding fails loudly when the compiled library is missing; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+OK, PENDING = 0, 1
+ERR_INVALID_ARG, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_DIVERGED = -1, -2, -3, -4, -5, -6
+MPPI, ELITE, NAIVE = 0, 1, 2
+BUF_MEAN, BUF_VAR, BUF_COST, BUF_FREQ, BUF_ELITE, BUF_MPPI_MEAN = 0, 1, 2, 3, 4, 5
+MAX_H, MAX_K, MAX_TILE = 128, 1 << 24, 256
+
+
+class Model(C.Structure):
+    _fields_ = [("mass", C.c_float), ("inertia", C.c_float * 3), ("foot", (C.c_float * 3) * 4),
+                ("gravity", C.c_float * 3)]
+
+
+class Cost(C.Structure):
+    _fields_ = [("Q", C.c_float * 12), ("R", C.c_float * 3), ("w_fc", C.c_float), ("mu", C.c_float),
+                ("rho", C.c_float), ("f_nominal", C.c_float)]
+
+
+class Config(C.Structure):
+    _fields_ = [("K", C.c_int32), ("H", C.c_int32), ("P", C.c_int32), ("method", C.c_int32),
+                ("iterations", C.c_int32), ("elite_count", C.c_int32), ("adaptive", C.c_int32),
+                ("compare_mppi", C.c_int32), ("dt_us", C.c_uint32), ("q_init", C.c_uint32),
+                ("seed", C.c_uint32), ("controller_id", C.c_uint32), ("lam", C.c_float),
+                ("f_min", C.c_float), ("f_max", C.c_float), ("sigma_init", C.c_float),
+                ("sigma_min", C.c_float), ("sigma_f_init", C.c_float), ("sigma_f_min", C.c_float),
+                ("tile", C.c_int32), ("model", Model), ("cost", Cost)]
+
+
+class Gait(C.Structure):
+    _fields_ = [("offset", C.c_uint32 * 4), ("duty", C.c_uint32), ("phase0", C.c_uint32)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("x0", C.c_void_p), ("xref", C.c_void_p), ("f_ext", C.c_void_p), ("gait", Gait),
+                ("shift", C.c_int32), ("host_memory", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("u0", C.c_float * 12), ("cost_min", C.c_float), ("ess", C.c_float), ("f_mean", C.c_float),
+                ("q_freq", C.c_int32), ("status", C.c_int32), ("n_finite", C.c_int32),
+                ("iter_lo", C.c_uint32), ("iter_hi", C.c_uint32)]
+
+
+RESULT_BYTES = C.sizeof(Result)
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class SBSError(RuntimeError):
+    def __init__(self, status, what=""):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes); the complete exported ABI of include/sbs.h
+ABI = {
+    "sbs_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_destroy": (None, [C.c_void_p]),
+    "sbs_dim": (C.c_int, [C.c_void_p]),
+    "sbs_device_bytes": (C.c_size_t, [C.c_void_p]),
+    "sbs_reset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
+    "sbs_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
+    "sbs_state_size": (C.c_size_t, [C.c_void_p]),
+    "sbs_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sbs_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sbs_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sbs_batch_destroy": (None, [C.c_void_p]),
+    "sbs_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_status_str": (C.c_char_p, [C.c_int]),
+    "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sbs_normals": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                              C.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libsbs.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsbs.so not built ({path}); run `python -m paper_2403_11383_b300.build`")
+        L = C.CDLL(path)
+        for name, (res, args) in ABI.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(s: int) -> str:
+    return lib().sbs_status_str(s).decode()
+
+
+def check(status: int, what: str = "sbs"):
+    if status != OK:
+        raise SBSError(status, what)
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def make_config(cfg: dict, tile: int = 0) -> Config:
+    """Config from a workload dict (see workloads.py)."""
+    c = Config()
+    c.K, c.H, c.P = cfg["K"], cfg["H"], cfg.get("P", 0)
+    c.method = {"mppi": MPPI, "elite": ELITE, "naive": NAIVE}[cfg["method"]]
+    c.iterations = cfg.get("iterations", 1)
+    c.elite_count = cfg.get("elite_count", 1)
+    c.adaptive = 1 if cfg.get("adaptive") else 0
+    c.compare_mppi = 1 if cfg.get("compare_mppi") else 0
+    c.dt_us, c.q_init = cfg["dt_us"], cfg["q_init"]
+    c.seed, c.controller_id = cfg["seed"], cfg.get("ctrl", 0)
+    c.lam = cfg["lam"]
+    c.f_min, c.f_max = cfg["f_min"], cfg["f_max"]
+    c.sigma_init, c.sigma_min = cfg["sigma_init"], cfg["sigma_min"]
+    c.sigma_f_init, c.sigma_f_min = cfg["sigma_f_init"], cfg["sigma_f_min"]
+    c.tile = tile or cfg.get("tile", 0)
+    m = cfg["model"]
+    c.model.mass = m["mass"]
+    c.model.inertia[:] = list(m["inertia"])
+    for i in range(4):
+        c.model.foot[i][:] = list(m["foot"][i])
+    c.model.gravity[:] = list(m["gravity"])
+    k = cfg["cost"]
+    c.cost.Q[:] = list(k["Q"])
+    c.cost.R[:] = list(k["R"])
+    c.cost.w_fc, c.cost.mu, c.cost.rho, c.cost.f_nominal = k["w_fc"], k["mu"], k["rho"], k["f_nominal"]
+    return c
+
+
+def make_gait(g: dict) -> Gait:
+    out = Gait()
+    out.offset[:] = list(g["offset"])
+    out.duty, out.phase0 = g["duty"], g["phase0"]
+    return out
+
+
+def parse_result(buf) -> dict:
+    """Decode one sbs_result from bytes / a uint8 array of RESULT_BYTES."""
+    r = Result.from_buffer_copy(bytes(np.asarray(buf, dtype=np.uint8).tobytes()[:RESULT_BYTES]))
+    return {"u0": np.array(r.u0[:], dtype=np.float32), "cost_min": r.cost_min, "ess": r.ess,
+            "f_mean": r.f_mean, "q_freq": r.q_freq, "status": r.status, "n_finite": r.n_finite,
+            "iter": r.iter_lo | (r.iter_hi << 32)}
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self):
+        self._live = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+        self.struct = Allocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, ctx):
+        import torch
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        except RuntimeError:
+            return None
+        p = t.data_ptr()
+        self._live[p] = t
+        return p
+
+    def _do_free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+
+_TORCH_ALLOC = None
+
+
+def torch_allocator() -> TorchAllocator:
+    global _TORCH_ALLOC
+    if _TORCH_ALLOC is None:
+        _TORCH_ALLOC = TorchAllocator()
+    return _TORCH_ALLOC
+
+
+class Controller:
+    """One controller instance (sbs_create ... sbs_destroy)."""
+
+    def __init__(self, cfg: dict, tile: int = 0, use_torch_allocator: bool = True):
+        self.cfg = cfg
+        self._c = make_config(cfg, tile)
+        self._h = C.c_void_p()
+        alloc = C.byref(torch_allocator().struct) if use_torch_allocator else None
+        check(lib().sbs_create(C.byref(self._c), alloc, C.byref(self._h)), "sbs_create")
+        self.D = lib().sbs_dim(self._h)
+        self.K, self.H = cfg["K"], cfg["H"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        return lib().sbs_device_bytes(self._h)
+
+    def close(self):
+        if self._h:
+            lib().sbs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, gait: dict, it: int = 0, stream=None):
+        g = make_gait(gait)
+        check(lib().sbs_reset(self._h, C.byref(g), it, _stream_ptr(stream)), "sbs_reset")
+
+    def problem(self, x0, xref, gait, f_ext=None, shift=0, host=False) -> Problem:
+        p = Problem()
+        p.x0 = x0.data_ptr() if hasattr(x0, "data_ptr") else x0.ctypes.data
+        p.xref = xref.data_ptr() if hasattr(xref, "data_ptr") else xref.ctypes.data
+        if f_ext is None:
+            p.f_ext = None
+        else:
+            p.f_ext = f_ext.data_ptr() if hasattr(f_ext, "data_ptr") else f_ext.ctypes.data
+        p.gait = make_gait(gait)
+        p.shift = shift
+        p.host_memory = 1 if host else 0
+        return p
+
+    def solve(self, x0, xref, gait, f_ext=None, shift=0, result=None, stream=None):
+        """Device solve: x0 [12], xref [H,12], f_ext [3] float32 CUDA tensors.
+        Returns the device result buffer (uint8 tensor of RESULT_BYTES)."""
+        import torch
+        if result is None:
+            result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        p = self.problem(x0, xref, gait, f_ext, shift, host=False)
+        check(lib().sbs_solve(self._h, C.byref(p), C.c_void_p(result.data_ptr()), _stream_ptr(stream)),
+              "sbs_solve")
+        return result
+
+    def solve_host(self, x0, xref, gait, f_ext=None, shift=0, result: Optional[Result] = None, stream=None):
+        """Host-memory solve: numpy/pinned-CPU float32 inputs; the result struct is
+        written on the stream (synchronize before reading)."""
+        if result is None:
+            result = Result()
+        p = self.problem(x0, xref, gait, f_ext, shift, host=True)
+        check(lib().sbs_solve(self._h, C.byref(p), C.byref(result), _stream_ptr(stream)), "sbs_solve")
+        return result
+
+    def read(self, which: int, stream=None):
+        import torch
+        n = {BUF_MEAN: self.D, BUF_VAR: self.D, BUF_COST: self.K, BUF_FREQ: self.K,
+             BUF_ELITE: self.cfg.get("elite_count", 1) if self.cfg["method"] == "elite" else 1,
+             BUF_MPPI_MEAN: self.D}[which]
+        dt = torch.int32 if which in (BUF_FREQ, BUF_ELITE) else torch.float32
+        out = torch.empty(n, dtype=dt, device="cuda")
+        check(lib().sbs_read(self._h, which, C.c_void_p(out.data_ptr()), out.numel() * 4, 0, _stream_ptr(stream)),
+              "sbs_read")
+        return out
+
+    def get_state(self, stream=None) -> bytes:
+        n = lib().sbs_state_size(self._h)
+        buf = (C.c_uint8 * n)()
+        check(lib().sbs_get_state(self._h, buf, n, _stream_ptr(stream)), "sbs_get_state")
+        return bytes(buf)
+
+    def set_state(self, blob: bytes, stream=None):
+        buf = (C.c_uint8 * len(blob)).from_buffer_copy(blob)
+        check(lib().sbs_set_state(self._h, buf, len(blob), _stream_ptr(stream)), "sbs_set_state")
+
+
+class Batch:
+    """Many controllers per persistent, graph-captured launch (sbs_batch_*)."""
+
+    def __init__(self, max_instances: int, max_tiles: int, use_torch_allocator: bool = True):
+        self._b = C.c_void_p()
+        alloc = C.byref(torch_allocator().struct) if use_torch_allocator else None
+        check(lib().sbs_batch_create(max_instances, max_tiles, alloc, C.byref(self._b)), "sbs_batch_create")
+
+    def close(self):
+        if self._b:
+            lib().sbs_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, controllers, problems, results, stream=None):
+        """controllers: list of Controller; problems: list of Problem (device
+        memory); results: uint8 CUDA tensor of n * RESULT_BYTES."""
+        n = len(controllers)
+        hs = (C.c_void_p * n)(*[c.handle.value for c in controllers])
+        ps = (Problem * n)(*problems)
+        check(lib().sbs_batch_solve(self._b, n, hs, ps, C.c_void_p(results.data_ptr()), _stream_ptr(stream)),
+              "sbs_batch_solve")
+
+
+def philox(ctr, key, stream=None):
+    """Philox4x32-10 on the device: ctr (n, 4), key (n, 2) int32 CUDA tensors -> (n, 4)."""
+    import torch
+    n = ctr.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    check(lib().sbs_philox4x32_10(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()),
+                                  C.c_void_p(out.data_ptr()), n, _stream_ptr(stream)), "sbs_philox4x32_10")
+    return out
+
+
+def normals(seed, ctrl, it, k0, nk, nn, stream=None):
+    """The controller's normals (frequency, then nn force normals) for nk samples."""
+    import torch
+    out = torch.empty((nk, nn + 1), dtype=torch.float32, device="cuda")
+    check(lib().sbs_normals(seed, ctrl, it, k0, nk, nn, C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+          "sbs_normals")
+    return out
+
+
+def fp32_peak(stream=None) -> float:
+    f = C.c_double()
+    check(lib().sbs_fp32_peak(C.byref(f), _stream_ptr(stream)), "sbs_fp32_peak")
+    return f.value
