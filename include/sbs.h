@@ -177,8 +177,12 @@ void sbs_destroy(sbs_handle* h);
 /* Decision-vector length D = 12 (H or P) + adaptive. */
 int sbs_dim(const sbs_handle* h);
 
-/* Bytes of device memory the handle holds. */
+/* Bytes of device memory the handle holds (state, tables and its own workspace). */
 size_t sbs_device_bytes(const sbs_handle* h);
+
+/* Bytes of scratch one solve of this controller needs in a batch workspace
+ * (costs, sampled deviations, partial sums, elite indices). */
+size_t sbs_workspace_bytes(const sbs_handle* h);
 
 /* Reset the distribution to its initial value for the given gait (hover forces
  * m|g| / n_stance per step, sigma_init; frequency q_init, sigma_f_init) and the
@@ -206,14 +210,28 @@ int sbs_set_state(sbs_handle* h, const void* buf, size_t bytes, void* stream);
  * (controller, tile) items from a device work queue; the tick is captured in a
  * CUDA graph and replayed.  Every controller's result equals its own sbs_solve
  * (same tile size), bit for bit. */
-int sbs_batch_create(int max_instances, int max_tiles, const sbs_allocator* alloc, sbs_batch** out);
+/* A batch context for up to max_instances controllers per tick with a device
+ * workspace of workspace_bytes shared by the controllers of one tick (the
+ * device-memory budget of in-flight solves).  Two ticks may be in flight per
+ * batch object; use one object per stream. */
+int sbs_batch_create(int max_instances, size_t workspace_bytes, const sbs_allocator* alloc, sbs_batch** out);
 void sbs_batch_destroy(sbs_batch* b);
 
-/* Solve n controllers (each one iteration; elite/naive controllers with
+/* Solve n controllers (one iteration each; controllers configured with
  * iterations > 1 are rejected) on stream.  probs[i] must use device memory
- * (host_memory = 0) and results is a device array of n sbs_result. */
+ * (host_memory = 0) and results is a device array of n sbs_result.  All
+ * controllers must share the tile size and the policy (P).  Returns
+ * SBS_ERR_BUDGET, with nothing enqueued, when their workspaces together exceed
+ * the batch workspace. */
 int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                     sbs_result* results, void* stream);
+
+/* Tracing: with profiling on, a batch launches its three stages (rollout,
+ * selection, refit) as separate kernels bracketed by CUDA events instead of
+ * replaying its graph; sbs_batch_stage_ms waits for the last tick and gives the
+ * three stage durations in milliseconds. */
+int sbs_batch_set_profiling(sbs_batch* b, int on);
+int sbs_batch_stage_ms(sbs_batch* b, float ms[3]);
 
 /* ---------------------------------------------------------------- utilities */
 const char* sbs_status_str(int status);

@@ -27,6 +27,8 @@ struct sbs_handle {
     int cur;               // current state buffer
     uint64_t iter;         // Philox iteration counter of the next iteration
     bool initialized;
+    WsLayout wsl;          // layout of one solve's workspace
+    Workspace ws;          // the handle's own workspace (plain solves)
     float* dev_in;         // device staging of host inputs: x0 (12) | f_ext (3) | pad | xref (12 H)
     sbs_result* res_dev;   // device result for host-memory solves
     float* pin_in;         // pinned host staging of inputs
@@ -233,6 +235,7 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
     P.T = cfg->tile ? cfg->tile : 128;
     P.ntiles = (cfg->K + P.T - 1) / P.T;
+    P.ngroups = (P.ntiles + kGroup - 1) / kGroup;
     P.compare_mppi = cfg->compare_mppi ? 1 : 0;
     P.part_stride = kPartHeader + P.nf;
     P.dt_us = cfg->dt_us;
@@ -264,23 +267,21 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     P.var_f_min = cfg->sigma_f_min * cfg->sigma_f_min;
 
     // device layout (256-byte aligned pieces)
+    h->wsl = ws_layout(P.K, P.H, P.P, P.T, P.Ke);
     const size_t D = P.D;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     const size_t o_params = take(sizeof(InstParams));
     const size_t o_state0 = take(2 * D * sizeof(float));
     const size_t o_state1 = take(2 * D * sizeof(float));
-    const size_t o_J = take((size_t)P.K * sizeof(float));
-    const size_t o_q = take((size_t)P.K * sizeof(int32_t));
-    const size_t o_part = take((size_t)P.ntiles * P.part_stride * sizeof(float));
-    const size_t o_elite = take((size_t)std::max(P.Ke, 1) * sizeof(int32_t));
-    const size_t o_counter = take(16);
     const size_t o_mppi = take(D * sizeof(float));
     const size_t o_B = take(P.P > 0 ? (size_t)P.H * P.P * sizeof(float) : 0);
     const size_t o_S = take(P.P > 0 ? (size_t)P.P * P.P * sizeof(float) : 0);
     const size_t o_res = take(sizeof(sbs_result));
     const size_t in_floats = 16 + 12 * (size_t)P.H;
     const size_t o_in = take(in_floats * sizeof(float));
+    const size_t o_cnt = take((size_t)h->wsl.counters * sizeof(unsigned));
+    const size_t o_ws = take(h->wsl.bytes);
     h->dev_bytes = off;
     h->dev_base = (char*)dev_alloc(&h->alloc, h->has_alloc, off);
     if (!h->dev_base) {
@@ -291,16 +292,12 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     h->dP = (InstParams*)(b + o_params);
     P.state[0] = (float*)(b + o_state0);
     P.state[1] = (float*)(b + o_state1);
-    P.J = (float*)(b + o_J);
-    P.q = (int32_t*)(b + o_q);
-    P.part = (float*)(b + o_part);
-    P.elite = (int32_t*)(b + o_elite);
-    P.counter = (unsigned*)(b + o_counter);
     P.mppi_mean = (float*)(b + o_mppi);
     P.Bsp = P.P > 0 ? (const float*)(b + o_B) : nullptr;
     P.Ssp = P.P > 0 ? (const float*)(b + o_S) : nullptr;
     h->res_dev = (sbs_result*)(b + o_res);
     h->dev_in = (float*)(b + o_in);
+    h->ws = ws_at(h->wsl, b + o_ws, (unsigned*)(b + o_cnt));
 
     cudaError_t e = cudaMemset(b, 0, off);
     if (e == cudaSuccess && P.P > 0) {
@@ -346,6 +343,8 @@ void sbs_destroy(sbs_handle* h)
 int sbs_dim(const sbs_handle* h) { return h ? h->hP.D : SBS_ERR_INVALID_ARG; }
 
 size_t sbs_device_bytes(const sbs_handle* h) { return h ? h->dev_bytes : 0; }
+
+size_t sbs_workspace_bytes(const sbs_handle* h) { return h ? h->wsl.bytes : 0; }
 
 int sbs_reset(sbs_handle* h, const sbs_gait* gait, uint64_t iter, void* stream)
 {
@@ -407,9 +406,12 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         t.partials = (P.method == SBS_MPPI || (P.compare_mppi && it == 0)) ? 1 : 0;
         t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
         t.result = res;
+        t.ws = h->ws;
         st = launch_rollout(h->dP, P, t, stream);
         if (st) return st;
         if (P.method != SBS_MPPI) {
+            st = launch_select(h->dP, P, t, stream);
+            if (st) return st;
             st = launch_refit(h->dP, P, t, stream);
             if (st) return st;
         }
@@ -432,9 +434,9 @@ int sbs_read(const sbs_handle* h, int which, void* dst, size_t bytes, int host_d
     switch (which) {
         case SBS_BUF_MEAN: src = P.state[h->cur]; n = P.D * sizeof(float); break;
         case SBS_BUF_VAR: src = P.state[h->cur] + P.D; n = P.D * sizeof(float); break;
-        case SBS_BUF_COST: src = P.J; n = (size_t)P.K * sizeof(float); break;
-        case SBS_BUF_FREQ: src = P.q; n = (size_t)P.K * sizeof(int32_t); break;
-        case SBS_BUF_ELITE: src = P.elite; n = (size_t)P.Ke * sizeof(int32_t); break;
+        case SBS_BUF_COST: src = h->ws.J; n = (size_t)P.K * sizeof(float); break;
+        case SBS_BUF_FREQ: src = h->ws.q; n = (size_t)P.K * sizeof(int32_t); break;
+        case SBS_BUF_ELITE: src = h->ws.elite; n = (size_t)P.Ke * sizeof(int32_t); break;
         case SBS_BUF_MPPI_MEAN: src = P.mppi_mean; n = P.D * sizeof(float); break;
         default: return SBS_ERR_INVALID_ARG;
     }
@@ -540,36 +542,44 @@ int sbs_fp32_peak(double* flops, void* stream)
 struct sbs_batch_slot {
     char* pin;            // [counts (16 B) | records]
     char* dev;            // device mirror
-    int* heads;           // device queue heads (2)
+    int* heads;           // device queue heads (4)
+    char* arena;          // workspace arena of this slot's ticks
+    unsigned* counters;   // counter arena (zero while idle)
     cudaEvent_t done;
     bool used;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaGraphNode_t copy_node;
-    size_t key_smem;
-    int key_T;
-    int key_P;
-    int grid1, grid2;
+    size_t key_smem, key_sel;
+    int key_T, key_P;
+    int grids[3];
 };
 
 struct sbs_batch {
-    int max_inst, max_tiles;
+    int max_inst;
+    size_t arena_bytes;
+    int counter_words;
     sbs_allocator alloc;
     bool has_alloc;
     size_t bytes;
     sbs_batch_slot slot[2];
     int next;
     bool use_graph;
+    bool profiling;
+    cudaEvent_t ev[4];
+    bool ev_valid;
 };
 
-extern "C" int sbs_batch_create(int max_instances, int max_tiles, const sbs_allocator* alloc, sbs_batch** out)
+extern "C" int sbs_batch_create(int max_instances, size_t workspace_bytes, const sbs_allocator* alloc,
+                                sbs_batch** out)
 {
-    if (!out || max_instances < 1 || max_tiles < 1) return SBS_ERR_INVALID_ARG;
+    if (!out || max_instances < 1 || workspace_bytes < 256) return SBS_ERR_INVALID_ARG;
     *out = nullptr;
     sbs_batch* b = new (std::nothrow) sbs_batch();
     if (!b) return SBS_ERR_OOM;
     b->max_inst = max_instances;
-    b->max_tiles = max_tiles;
+    b->arena_bytes = align_up(workspace_bytes, 256);
+    b->counter_words = 4 * max_instances + (int)std::min<size_t>(b->arena_bytes / 8192, 1 << 24) + 1024;
     b->has_alloc = alloc != nullptr;
     if (alloc) b->alloc = *alloc;
     b->bytes = 16 + (size_t)max_instances * sizeof(InstRec);
@@ -577,15 +587,20 @@ extern "C" int sbs_batch_create(int max_instances, int max_tiles, const sbs_allo
     b->use_graph = !(ng && ng[0] == '1');
     for (int i = 0; i < 2; ++i) {
         sbs_batch_slot& sl = b->slot[i];
-        sl.dev = (char*)dev_alloc(&b->alloc, b->has_alloc, align_up(b->bytes, 256) + 256);
+        const size_t rec_bytes = align_up(b->bytes, 256);
+        const size_t cnt_bytes = align_up((size_t)b->counter_words * 4, 256);
+        const size_t total = rec_bytes + 256 + cnt_bytes + b->arena_bytes;
+        sl.dev = (char*)dev_alloc(&b->alloc, b->has_alloc, total);
         if (!sl.dev || cudaHostAlloc((void**)&sl.pin, b->bytes, cudaHostAllocDefault) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             sbs_batch_destroy(b);
             return SBS_ERR_OOM;
         }
-        sl.heads = (int*)(sl.dev + align_up(b->bytes, 256));
-        if (cudaMemset(sl.heads, 0, 16) != cudaSuccess) {
+        sl.heads = (int*)(sl.dev + rec_bytes);
+        sl.counters = (unsigned*)(sl.dev + rec_bytes + 256);
+        sl.arena = sl.dev + rec_bytes + 256 + cnt_bytes;
+        if (cudaMemset(sl.dev, 0, rec_bytes + 256 + cnt_bytes) != cudaSuccess) {
             sbs_batch_destroy(b);
             return SBS_ERR_CUDA;
         }
@@ -594,10 +609,33 @@ extern "C" int sbs_batch_create(int max_instances, int max_tiles, const sbs_allo
     return SBS_OK;
 }
 
+extern "C" int sbs_batch_set_profiling(sbs_batch* b, int on)
+{
+    if (!b) return SBS_ERR_INVALID_ARG;
+    if (on && !b->ev[0]) {
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&b->ev[i]) != cudaSuccess) return SBS_ERR_CUDA;
+    }
+    b->profiling = on != 0;
+    b->ev_valid = false;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_stage_ms(sbs_batch* b, float ms[3])
+{
+    if (!b || !ms || !b->ev_valid) return SBS_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(b->ev[3]) != cudaSuccess) return SBS_ERR_CUDA;
+    for (int i = 0; i < 3; ++i)
+        if (cudaEventElapsedTime(&ms[i], b->ev[i], b->ev[i + 1]) != cudaSuccess) return SBS_ERR_CUDA;
+    return SBS_OK;
+}
+
 extern "C" void sbs_batch_destroy(sbs_batch* b)
 {
     if (!b) return;
     cudaDeviceSynchronize();
+    for (int i = 0; i < 4; ++i)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
     for (int i = 0; i < 2; ++i) {
         sbs_batch_slot& sl = b->slot[i];
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
@@ -609,7 +647,7 @@ extern "C" void sbs_batch_destroy(sbs_batch* b)
     delete b;
 }
 
-static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, int T)
+static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, size_t sel_smem, int T)
 {
     if (sl.exec) {
         cudaGraphExecDestroy(sl.exec);
@@ -619,11 +657,11 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, int
         cudaGraphDestroy(sl.graph);
         sl.graph = nullptr;
     }
-    int st = batch_grid(P, smem, T, &sl.grid1, &sl.grid2);
+    int st = batch_grid(P, smem, sel_smem, T, sl.grids);
     if (st) return st;
     cudaGraph_t g;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return SBS_ERR_CUDA;
-    cudaGraphNode_t n_cp, n_ms, n_k1, n_k2;
+    cudaGraphNode_t n_cp, n_ms, n_k1, n_k2, n_k3;
     bool ok = cudaGraphAddMemcpyNode1D(&n_cp, g, nullptr, 0, sl.dev, sl.pin, b->bytes, cudaMemcpyHostToDevice) ==
               cudaSuccess;
     cudaMemsetParams mp;
@@ -631,7 +669,7 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, int
     mp.dst = sl.heads;
     mp.value = 0;
     mp.elementSize = 4;
-    mp.width = 2;
+    mp.width = 4;
     mp.height = 1;
     ok = ok && cudaGraphAddMemsetNode(&n_ms, g, &n_cp, 1, &mp) == cudaSuccess;
     const InstRec* recs = (const InstRec*)(sl.dev + 16);
@@ -641,17 +679,23 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, int
     cudaKernelNodeParams k1;
     std::memset(&k1, 0, sizeof(k1));
     k1.func = (void*)batch_rollout_fn(P);
-    k1.gridDim = dim3(sl.grid1);
+    k1.gridDim = dim3(sl.grids[0]);
     k1.blockDim = dim3(T);
     k1.sharedMemBytes = (unsigned)smem;
     k1.kernelParams = args;
     ok = ok && cudaGraphAddKernelNode(&n_k1, g, &n_ms, 1, &k1) == cudaSuccess;
     cudaKernelNodeParams k2 = k1;
-    k2.func = (void*)batch_refit_fn();
-    k2.gridDim = dim3(sl.grid2);
-    k2.blockDim = dim3(kRefitThreads);
-    k2.sharedMemBytes = 0;
+    k2.func = (void*)batch_select_fn();
+    k2.gridDim = dim3(sl.grids[1]);
+    k2.blockDim = dim3(kSelectThreads);
+    k2.sharedMemBytes = (unsigned)sel_smem;
     ok = ok && cudaGraphAddKernelNode(&n_k2, g, &n_k1, 1, &k2) == cudaSuccess;
+    cudaKernelNodeParams k3 = k1;
+    k3.func = (void*)batch_refit_fn();
+    k3.gridDim = dim3(sl.grids[2]);
+    k3.blockDim = dim3(kRefitThreads);
+    k3.sharedMemBytes = 0;
+    ok = ok && cudaGraphAddKernelNode(&n_k3, g, &n_k2, 1, &k3) == cudaSuccess;
     cudaGraphExec_t ex = nullptr;
     ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
     if (!ok) {
@@ -662,9 +706,6 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, int
     sl.graph = g;
     sl.exec = ex;
     sl.copy_node = n_cp;
-    sl.key_smem = smem;
-    sl.key_T = T;
-    sl.key_P = P;
     return SBS_OK;
 }
 
@@ -673,23 +714,25 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
 {
     if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    int T = handles[0] ? handles[0]->hP.T : 0;
-    const int Pk = handles[0] ? handles[0]->hP.P : 0;
-    size_t smem = 0;
-    long long items = 0;
+    if (!handles[0]) return SBS_ERR_INVALID_ARG;
+    const int T = handles[0]->hP.T;
+    const int Pk = handles[0]->hP.P;
+    size_t smem = 0, sel_smem = 0, arena = 0;
+    long long counters = 0;
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) {
         const sbs_handle* h = handles[i];
         const sbs_problem* p = &probs[i];
         if (!h || !p->x0 || !p->xref || p->host_memory || h->hP.T != T || h->hP.P != Pk) return SBS_ERR_INVALID_ARG;
-        if (h->hP.method != SBS_MPPI && h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         if (h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
         smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T));
-        items += h->hP.ntiles;
+        if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
+        arena += align_up(h->wsl.bytes, 256);
+        counters += h->wsl.counters;
         order[i] = i;
     }
-    if (items > b->max_tiles) return SBS_ERR_INVALID_ARG;
+    if (arena > b->arena_bytes || counters > b->counter_words) return SBS_ERR_BUDGET;
     {
         std::vector<const sbs_handle*> u(handles, handles + n);
         std::sort(u.begin(), u.end());
@@ -715,12 +758,15 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     }
     int* counts = (int*)sl.pin;
     InstRec* recs = (InstRec*)(sl.pin + 16);
-    int tile_begin = 0, refit_begin = 0;
+    int tile_begin = 0, select_begin = 0, refit_begin = 0;
+    size_t aoff = 0;
+    unsigned* cnt = sl.counters;
     for (int r = 0; r < n; ++r) {
         const int i = order[r];
         sbs_handle* h = handles[i];
         const InstParams& P = h->hP;
         InstRec& R = recs[r];
+        std::memset(&R, 0, sizeof(R));
         R.t = make_tick(h, probs[i].gait);
         R.t.x0 = probs[i].x0;
         R.t.xref = probs[i].xref;
@@ -729,21 +775,30 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         R.t.partials = (P.method == SBS_MPPI || P.compare_mppi) ? 1 : 0;
         R.t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
         R.t.result = results + i;
+        R.t.ws = ws_at(h->wsl, sl.arena + aoff, cnt);
+        aoff += align_up(h->wsl.bytes, 256);
+        cnt += h->wsl.counters;
         R.dP = h->dP;
         R.tile_begin = tile_begin;
+        R.select_begin = select_begin;
         R.refit_begin = refit_begin;
         tile_begin += P.ntiles;
-        if (P.method != SBS_MPPI) refit_begin += P.nt + P.adaptive;
+        if (P.method != SBS_MPPI) {
+            select_begin += 1;
+            refit_begin += P.nt + P.adaptive;
+        }
     }
     counts[0] = n;
     counts[1] = tile_begin;
-    counts[2] = refit_begin;
-    counts[3] = 0;
+    counts[2] = select_begin;
+    counts[3] = refit_begin;
+    if (sel_smem == 0) sel_smem = 256;
     const size_t used = 16 + (size_t)n * sizeof(InstRec);
     int st = SBS_OK;
-    if (b->use_graph) {
-        if (!sl.exec || sl.key_smem != smem || sl.key_T != T || sl.key_P != Pk) {
-            st = build_graph(b, sl, Pk, smem, T);
+    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_P != Pk;
+    if (b->use_graph && !b->profiling) {
+        if (!sl.exec || rekey) {
+            st = build_graph(b, sl, Pk, smem, sel_smem, T);
             if (st) return st;
         }
         if (cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.pin, used,
@@ -751,23 +806,25 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
             return SBS_ERR_CUDA;
         if (cudaGraphLaunch(sl.exec, s) != cudaSuccess) return SBS_ERR_CUDA;
     } else {
-        if (sl.key_smem != smem || sl.key_T != T || sl.key_P != Pk) {
-            st = batch_grid(Pk, smem, T, &sl.grid1, &sl.grid2);
+        if (rekey || !sl.grids[0]) {
+            st = batch_grid(Pk, smem, sel_smem, T, sl.grids);
             if (st) return st;
-            sl.key_smem = smem;
-            sl.key_T = T;
-            sl.key_P = Pk;
-            if (sl.exec) {
+            if (sl.exec) {  // the graph's launch shapes no longer match
                 cudaGraphExecDestroy(sl.exec);
                 sl.exec = nullptr;
             }
         }
         if (cudaMemcpyAsync(sl.dev, sl.pin, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return SBS_ERR_CUDA;
-        if (cudaMemsetAsync(sl.heads, 0, 8, s) != cudaSuccess) return SBS_ERR_CUDA;
-        st = launch_batch(Pk, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, T, sl.grid1, sl.grid2,
-                          stream);
+        if (cudaMemsetAsync(sl.heads, 0, 16, s) != cudaSuccess) return SBS_ERR_CUDA;
+        st = launch_batch(Pk, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, sel_smem, T,
+                          sl.grids, stream, b->profiling ? (void* const*)b->ev : nullptr);
         if (st) return st;
+        b->ev_valid = b->profiling;
     }
+    sl.key_smem = smem;
+    sl.key_sel = sel_smem;
+    sl.key_T = T;
+    sl.key_P = Pk;
     if (cudaEventRecord(sl.done, s) != cudaSuccess) return SBS_ERR_CUDA;
     sl.used = true;
     for (int i = 0; i < n; ++i) {

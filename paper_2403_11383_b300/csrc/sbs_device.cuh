@@ -33,7 +33,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // Box-Muller on two words: the top 24 bits give exact uniforms u1 in (0, 1]
-// and u2 in [0, 1).
+// and u2 in [0, 1).  The radius uses the accurate logarithm (its argument is
+// often within a few ulp of 1); the angle uses the hardware sine/cosine, whose
+// absolute error (about 4e-7 on [0, 2 pi)) moves a normal by at most 3e-6.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {
     const float two_m24 = 5.9604644775390625e-8f;
@@ -41,7 +43,7 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
     const float u2 = __uint2float_rn(b >> 8) * two_m24;
     const float r = sqrtf(-2.0f * logf(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    __sincosf(6.28318530717958648f * u2, &s, &c);
     return make_float2(r * c, r * s);
 }
 

@@ -4,38 +4,47 @@
 #include <cstddef>
 #include <cstdint>
 
-#include "../../include/sbs.h"
+#include "sbs.h"  // include/ is on the include path
 
 namespace sbs {
 
 constexpr uint32_t kPhaseOne = 1000000000u;  // one gait cycle in 1e-9 cycle
 constexpr int kMaxKnots = 8;
 constexpr int kPartHeader = 8;               // floats ahead of the per-dimension sums in a partial row
+constexpr int kGroup = 16;                   // tiles whose partial rows one block combines
 constexpr int kRefitThreads = 256;
+constexpr int kSelectThreads = 1024;
+constexpr int kSelectSmemMaxK = 32768;       // costs staged in shared memory up to this K
 
-// Per-controller constants and device buffers.  Lives in device memory; every
-// kernel copies it into shared memory before use.
+// Per-controller constants and persistent device state.  Lives in device
+// memory; every kernel copies it into shared memory before use.
 struct InstParams {
     int32_t K, H, P, D;
     int32_t nt;        // H (per-step policy) or P (spline knots)
     int32_t nf;        // 12 * nt: length of the force part of theta
-    int32_t method, adaptive, Ke, T, ntiles, compare_mppi;
+    int32_t method, adaptive, Ke, T, ntiles, ngroups, compare_mppi;
     int32_t part_stride;  // floats per partial row: kPartHeader + nf
+    int32_t pad0;
     uint32_t dt_us, q_init, seed, ctrl;
     float dt, lambda, inv_lambda, inv_mass, weight_z;
     float inertia[3], inv_inertia[3], foot[12], gravity[3];
     float Q[12], R[3], w_fc, mu, rho, f_nominal, f_min, f_max;
     float var_init, var_min, var_f_init, var_f_min;
-    // device buffers owned by the handle
     float* state[2];   // ping-pong distribution: mean[D] then var[D]
-    float* J;          // [K]
-    int32_t* q;        // [K]
-    float* part;       // [ntiles][part_stride]
-    int32_t* elite;    // [max(Ke, 1)]
-    unsigned* counter; // tiles finished in the current launch
     float* mppi_mean;  // [D]
     const float* Bsp;  // [H][P] spline basis
     const float* Ssp;  // [P][P] spline shift-by-one-step map
+};
+
+// Scratch of one in-flight solve.  Counters are zero whenever no launch uses them.
+struct Workspace {
+    float* J;          // [K] costs
+    int32_t* q;        // [K] quantised step frequencies
+    float* theta;      // [nt][K][12] sampled deviations sigma * eps of every sample
+    float* part;       // [ntiles][part_stride] tile partial sums (MPPI)
+    float* gpart;      // [ngroups][part_stride] group partial sums
+    int32_t* elite;    // [Ke] elite indices, ascending
+    unsigned* counters;  // [ngroups + 1]
 };
 
 // Per-solve, per-iteration arguments.
@@ -51,15 +60,18 @@ struct TickArgs {
     int32_t partials;    // 1: this iteration forms MPPI partial sums
     int32_t mppi_to_state;  // 1: the MPPI combine is the update; 0: it goes to mppi_mean
     sbs_result* result;
+    Workspace ws;
 };
 
 // One controller of a batched tick: its tick arguments, its parameters and the
-// first item of its tiles / refit blocks in the launch's item numbering.
+// first item of its tiles / selection / refit blocks in the launch's numbering.
 struct InstRec {
     TickArgs t;
     const InstParams* dP;
     int32_t tile_begin;
+    int32_t select_begin;
     int32_t refit_begin;
+    int32_t pad;
 };
 
 static_assert(sizeof(InstRec) % 16 == 0, "InstRec must be a multiple of 16 bytes");
@@ -75,19 +87,61 @@ inline size_t rollout_smem_bytes(int H, int P, int T)
     size_t floats = 3 * (size_t)nf   // mean, variance, standard deviation (shifted)
                   + 12 * (size_t)H   // reference
                   + (P > 0 ? (size_t)H * P + 12 * (size_t)H : 0)  // spline basis, mean forces
-                  + (size_t)T         // weights
-                  + (size_t)nwarps * nf;  // per-warp partial sums
+                  + (size_t)nwarps * nf;  // per-warp partial sums / combined row
     return floats * sizeof(float);
+}
+
+inline size_t select_smem_bytes(int K) { return 4 * (size_t)(K < kSelectSmemMaxK ? K : kSelectSmemMaxK); }
+
+// Byte layout of a workspace inside one allocation (256-byte aligned pieces).
+struct WsLayout {
+    size_t J, q, theta, part, gpart, elite, bytes;
+    int ntiles, ngroups, counters;
+};
+
+inline WsLayout ws_layout(int K, int H, int P, int T, int Ke)
+{
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const int nt = P > 0 ? P : H, nf = 12 * nt;
+    WsLayout L;
+    L.ntiles = (K + T - 1) / T;
+    L.ngroups = (L.ntiles + kGroup - 1) / kGroup;
+    L.counters = L.ngroups + 1;
+    const size_t PS = kPartHeader + nf;
+    size_t o = 0;
+    L.J = o; o = up(o + 4 * (size_t)K);
+    L.q = o; o = up(o + 4 * (size_t)K);
+    L.theta = o; o = up(o + 4 * (size_t)K * nf);
+    L.part = o; o = up(o + 4 * (size_t)L.ntiles * PS);
+    L.gpart = o; o = up(o + 4 * (size_t)L.ngroups * PS);
+    L.elite = o; o = up(o + 4 * (size_t)(Ke > 0 ? Ke : 1));
+    L.bytes = o;
+    return L;
+}
+
+inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
+{
+    Workspace w;
+    w.J = (float*)(base + L.J);
+    w.q = (int32_t*)(base + L.q);
+    w.theta = (float*)(base + L.theta);
+    w.part = (float*)(base + L.part);
+    w.gpart = (float*)(base + L.gpart);
+    w.elite = (int32_t*)(base + L.elite);
+    w.counters = counters;
+    return w;
 }
 
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
+int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
-int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem, int T, int grid1,
-                 int grid2, void* stream);
-int batch_grid(int P, size_t smem, int T, int* grid1, int* grid2);
+int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem, size_t sel_smem,
+                 int T, const int grids[3], void* stream, void* const* events);
+int batch_grid(int P, size_t smem, size_t sel_smem, int T, int grids[3]);
 const void* batch_rollout_fn(int P);
+const void* batch_select_fn();
 const void* batch_refit_fn();
 int launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream);
 int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);

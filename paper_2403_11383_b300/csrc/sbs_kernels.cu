@@ -1,19 +1,21 @@
 // Kernels of the SBS controller hot path (sm_103a).
 //
-//  k_rollout     one block per tile of T samples: stage the (warm-shifted) mean,
-//                deviation and reference in shared memory, roll every sample
-//                out in registers (Alg. 2 with Eq. (1)), accumulate its cost with
-//                Kahan compensation, and - for MPPI - form the tile's max-shifted
-//                partial sums of w and w (theta - mean).  The last tile to finish
-//                combines the partials in tile order (MPPI, Alg. 5) or selects the
-//                elite set by radix select (Alg. 1 Sorting).
-//  k_refit       one block per step (or knot) of an elite/naive controller:
-//                elite mean and diagonal variance (Alg. 1 Update) from the
-//                elite samples' regenerated noise.
-//  k_batch_*     the same work for many controllers, pulled as (controller, tile)
-//                items from a device queue by persistent blocks.
-//  k_init        the initial distribution.
-//  k_fma_peak    FP32 FMA-chain microbenchmark for the roofline denominator.
+//  k_rollout   one block per tile of T samples: stage the (warm-shifted) mean,
+//              deviation and reference in shared memory, roll every sample out
+//              in registers (Alg. 2 with Eq. (1)), accumulate its cost with Kahan
+//              compensation and store its sampled deviations sigma * eps.  For
+//              MPPI the tile forms max-shifted partial sums of w and
+//              w (theta - mean); the last tile of each group of 16 combines the
+//              group, the last group the whole controller (Alg. 5).
+//  k_select    one 1024-thread block per elite/naive controller: radix select of
+//              the K_e lowest (cost, index) pairs (Alg. 1 Sorting).
+//  k_refit     one block per step (or knot): elite mean and diagonal variance
+//              (Alg. 1 Update) or the best sample (Alg. 3) from the stored
+//              deviations.
+//  k_batch_*   the same three stages for many controllers, pulled as items from
+//              device queues by persistent blocks.
+//  k_init      the initial distribution.
+//  k_fma_peak  FP32 FMA-chain microbenchmark for the roofline denominator.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -22,6 +24,8 @@
 
 namespace sbs {
 
+constexpr float kInf = __builtin_huge_valf();
+
 struct __align__(16) BlockShared {
     InstParams P;
     TickArgs t;
@@ -29,22 +33,20 @@ struct __align__(16) BlockShared {
     float fe[3];
     float mu_f, var_f, sig_f;
     float red[32][4];
-    float m;
     int item;
     int last;
     int hist[256];
     int wtot[32];
-    int wtot2[32];
     int digit, below;
-    float mu12[12], vr12[12], sd12[12], ebar[12];
-    float wacc[8][12];
+    float mu12[12], vr12[12], dbar[12];
+    float wacc[32][12];
 };
 
 struct Views {
-    float *mu, *vr, *sd, *xr, *Bs, *Mb, *w, *acc;
+    float *mu, *vr, *sd, *xr, *Bs, *Mb, *acc;
 };
 
-__device__ __forceinline__ Views carve(float* base, int H, int P, int nf, int T)
+__device__ __forceinline__ Views carve(float* base, int H, int P, int nf)
 {
     Views v;
     v.mu = base;
@@ -60,8 +62,6 @@ __device__ __forceinline__ Views carve(float* base, int H, int P, int nf, int T)
     } else {
         v.Bs = v.Mb = nullptr;
     }
-    v.w = p;
-    p += T;
     v.acc = p;
     return v;
 }
@@ -80,8 +80,8 @@ __device__ __forceinline__ void load_tick(const TickArgs* src, BlockShared& sh)
     for (int i = threadIdx.x; i < (int)(sizeof(TickArgs) / 8); i += blockDim.x) d[i] = s[i];
 }
 
-// Initial value of force entry idx (Sec. III-A warm start, reset rule): every
-// leg's mean force at step j is (0, 0, m|g| / n_j) with n_j the stance legs of
+// Initial value of force entry idx (reset rule of the warm start, Sec. III-A):
+// every leg's mean force at step j is (0, 0, m|g| / n_j), n_j the stance legs of
 // the nominal schedule; spline knots carry m|g| / (4 D_f).
 __device__ __forceinline__ void init_entry(const InstParams& P, const TickArgs& t, int idx, float& m,
                                            float& v)
@@ -100,7 +100,7 @@ __device__ __forceinline__ void init_entry(const InstParams& P, const TickArgs& 
     v = P.var_init;
 }
 
-// Force entry idx of the distribution after the warm shift of this tick.
+// Force entry idx of the distribution after this tick's warm shift.
 __device__ __forceinline__ void shifted_entry(const InstParams& P, const TickArgs& t, const float* sm,
                                               const float* sv, int idx, float& m, float& v)
 {
@@ -207,37 +207,372 @@ __device__ __forceinline__ int block_scan(BlockShared& sh, int v, int* total)
     return off + incl - v;
 }
 
-// ---------------------------------------------------------------------------
-// Elite selection (Alg. 1 Sorting): the Ke smallest (cost, index) pairs by a
-// 4-pass 8-bit radix select on the order-preserving cost key, then an ordered
-// compaction that takes ties at the threshold key by ascending index.
-// Output: indices in ascending order.  Also returns the best cost and the
-// number of finite costs.
-// ---------------------------------------------------------------------------
-__device__ void radix_select(BlockShared& sh, const float* J, int K, int Ke, int32_t* out, float* beta,
-                             int* nfin)
+// Sum of 12 per-thread values over the block in a fixed order: warp transpose
+// sums, then the warps' totals in warp order.  Threads < 12 receive component
+// threadIdx.x in *out_c.
+__device__ __forceinline__ float block_sum12(BlockShared& sh, const float v[12])
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float o[3];
+    const int c0 = warp_sum12(v, o);
+    __syncthreads();
+    if ((lane & 7) == 0) {
+        sh.wacc[warp][c0] = o[0];
+        sh.wacc[warp][c0 + 1] = o[1];
+        sh.wacc[warp][c0 + 2] = o[2];
+    }
+    __syncthreads();
+    float tot = 0.0f;
+    if (threadIdx.x < 12)
+        for (int w = 0; w < nw; ++w) tot += sh.wacc[w][threadIdx.x];
+    __syncthreads();
+    return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Combine nrows partial rows (stride PS) in row order (Alg. 5 with max shift):
+// m = min_t m_t; each row scaled by exp(-(m_t - m) / lambda) (squared for the
+// sum of squared weights, none for the finite count); Kahan sums per column.
+// out (nf + kPartHeader floats, shared memory) gets the combined row.
+// ---------------------------------------------------------------------------
+__device__ void combine_rows(BlockShared& sh, const float* rows, int nrows, int PS, int nf, float inv_lambda,
+                             float* out)
+{
+    const int tid = threadIdx.x, T = blockDim.x;
+    float m = kInf;
+    for (int i = tid; i < nrows; i += T) m = fminf(m, __ldcg(rows + (size_t)i * PS));
+    m = block_min(sh, m);
+    const int ncol = nf + 4;
+    for (int col = tid; col < ncol; col += T) {
+        const int off = col < 4 ? 1 + col : kPartHeader + (col - 4);
+        float s = 0.0f, c = 0.0f;
+        for (int i0 = 0; i0 < nrows; i0 += 8) {
+            float mt[8], x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+                mt[u] = i < nrows ? __ldcg(rows + (size_t)i * PS) : kInf;
+                x[u] = i < nrows ? __ldcg(rows + (size_t)i * PS + off) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (i0 + u < nrows) {
+                    const float sc = mt[u] < kInf ? expf(-(mt[u] - m) * inv_lambda) : 0.0f;
+                    const float term = col == 3 ? x[u] : (col == 1 ? x[u] * sc * sc : x[u] * sc);
+                    kahan_add(s, c, term);
+                }
+            }
+        }
+        out[off] = s;
+    }
+    if (tid == 0) {
+        out[0] = m;
+        out[5] = out[6] = out[7] = 0.0f;
+    }
+    __syncthreads();
+}
+
+// The MPPI update from the combined row: mean = mu + A / S, variance kept
+// (Alg. 5: the covariance is unchanged), and the result record.
+__device__ void mppi_finish(BlockShared& sh, const Views& v, const float* row, bool to_state)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const float m = row[0], S = row[1];
+    const bool ok = S > 0.0f && m < kInf;
+    const float invS = ok ? 1.0f / S : 0.0f;
+    float* out_mean = to_state ? P.state[1 - t.src] : P.mppi_mean;
+    float* out_var = P.state[1 - t.src] + P.D;
+    for (int d = tid; d < P.nf; d += T) {
+        out_mean[d] = ok ? v.mu[d] + row[kPartHeader + d] * invS : v.mu[d];
+        if (to_state) out_var[d] = v.vr[d];
+    }
+    const float fmean = P.adaptive ? (ok ? row[3] * invS : sh.mu_f) : sh.mu_f;
+    if (tid == 0 && P.adaptive) {
+        out_mean[P.D - 1] = fmean;
+        if (to_state) out_var[P.D - 1] = sh.var_f;
+    }
+    if (to_state) {
+        sbs_result* r = t.result;
+        if (tid < 12) {
+            const uint32_t ph = (t.phase0 + t.offset[tid / 3]) % kPhaseOne;
+            const float md = ok ? v.mu[tid] + row[kPartHeader + tid] * invS : v.mu[tid];
+            r->u0[tid] = ph < t.duty ? md : 0.0f;
+        }
+        if (tid == 0) {
+            r->cost_min = m;
+            r->ess = ok ? S * S / row[2] : 0.0f;
+            r->f_mean = fmean;
+            r->q_freq = (int32_t)quantise_mhz(fmean, P.f_min, P.f_max);
+            r->status = ok ? SBS_OK : SBS_ERR_DIVERGED;
+            r->n_finite = (int32_t)row[4];
+            r->iter_lo = (uint32_t)t.iter;
+            r->iter_hi = (uint32_t)(t.iter >> 32);
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// One tile of T samples.  NP = 0: per-step forces; NP > 0: NP spline knots.
+// ---------------------------------------------------------------------------
+template <int NP>
+__device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    const Views v = carve(dyn, P.H, NP, P.nf);
+    stage(sh, v, NP);
+
+    const int K = P.K;
+    const uint32_t k = (uint32_t)tile * (uint32_t)T + (uint32_t)tid;
+    const bool valid = k < (uint32_t)K;
+    const uint32_t seed = P.seed, ctrl = P.ctrl;
+    const uint64_t iter = t.iter;
+    float* theta = t.ws.theta;
+    uint32_t q = P.q_init;
+    if (P.adaptive) q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
+
+    float x[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) x[c] = sh.x0[c];
+    const float fe[3] = {sh.fe[0], sh.fe[1], sh.fe[2]};
+    uint32_t ph[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t p0 = t.phase0 + t.offset[i];
+        ph[i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
+    }
+    const uint32_t step = q * P.dt_us;
+    const uint32_t duty = t.duty;
+
+    constexpr int ND = NP > 0 ? 12 * NP : 1;
+    float dth[ND];
+    if constexpr (NP > 0) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float e[12];
+            normals12(k, p, iter, seed, ctrl, e);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) dth[12 * p + c] = v.sd[12 * p + c] * e[c];
+            if (valid) {
+                float4* o = reinterpret_cast<float4*>(theta + ((size_t)p * K + k) * 12);
+                o[0] = make_float4(dth[12 * p + 0], dth[12 * p + 1], dth[12 * p + 2], dth[12 * p + 3]);
+                o[1] = make_float4(dth[12 * p + 4], dth[12 * p + 5], dth[12 * p + 6], dth[12 * p + 7]);
+                o[2] = make_float4(dth[12 * p + 8], dth[12 * p + 9], dth[12 * p + 10], dth[12 * p + 11]);
+            }
+        }
+    }
+
+    float J = 0.0f, Jc = 0.0f;
+    for (int j = 0; j < P.H; ++j) {
+        float G[12];
+        if constexpr (NP == 0) {
+            float e[12];
+            normals12(k, j, iter, seed, ctrl, e);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                e[c] = v.sd[12 * j + c] * e[c];  // deviation sigma * eps
+                G[c] = v.mu[12 * j + c] + e[c];
+            }
+            if (valid) {
+                float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
+                o[0] = make_float4(e[0], e[1], e[2], e[3]);
+                o[1] = make_float4(e[4], e[5], e[6], e[7]);
+                o[2] = make_float4(e[8], e[9], e[10], e[11]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                float s = v.Mb[12 * j + c];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) s = fmaf(v.Bs[j * NP + p], dth[12 * p + c], s);
+                G[c] = s;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (ph[i] >= duty) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
+        kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G));
+        srbd_step(P, x, G, fe);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ph[i] += step;
+            if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
+        }
+    }
+    if (P.adaptive) {
+        const float d = (float)q / 1000.0f - P.f_nominal;
+        kahan_add(J, Jc, P.rho * d * d);
+    }
+    if (!isfinite(J)) J = kInf;
+    if (valid) {
+        t.ws.J[k] = J;
+        t.ws.q[k] = (int32_t)q;
+    }
+    if (!t.partials) return;
+
+    // ---- MPPI partial sums of this tile, shifted by the tile's best cost
+    const bool fin = valid && J < kInf;
+    const float mt = block_min(sh, fin ? J : kInf);
+    const float w = (fin && mt < kInf) ? expf(-(J - mt) * P.inv_lambda) : 0.0f;
+    const float f = (float)q / 1000.0f;
+    {
+        const float s0 = warp_sum(w), s1 = warp_sum(w * w), s2 = warp_sum(w * f), s3 = warp_sum(fin ? 1.0f : 0.0f);
+        if (lane == 0) {
+            sh.red[warp][0] = s0;
+            sh.red[warp][1] = s1;
+            sh.red[warp][2] = s2;
+            sh.red[warp][3] = s3;
+        }
+    }
+    // A warp whose weights all underflowed to zero contributes exact zeros.
+    const bool warp_live = __any_sync(kFull, w != 0.0f);
+    if (!warp_live) {
+        for (int d = lane; d < P.nf; d += 32) v.acc[warp * P.nf + d] = 0.0f;
+    } else if constexpr (NP == 0) {
+#pragma unroll 4
+        for (int j = 0; j < P.H; ++j) {
+            float vv[12], o[3];
+            if (valid) {
+                const float4* src = reinterpret_cast<const float4*>(theta + ((size_t)j * K + k) * 12);
+                const float4 a = src[0], b = src[1], c = src[2];
+                vv[0] = w * a.x; vv[1] = w * a.y; vv[2] = w * a.z; vv[3] = w * a.w;
+                vv[4] = w * b.x; vv[5] = w * b.y; vv[6] = w * b.z; vv[7] = w * b.w;
+                vv[8] = w * c.x; vv[9] = w * c.y; vv[10] = w * c.z; vv[11] = w * c.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) vv[c] = 0.0f;
+            }
+            const int c0 = warp_sum12(vv, o);
+            if ((lane & 7) == 0) {
+                float* a = v.acc + warp * P.nf + 12 * j + c0;
+                a[0] = o[0];
+                a[1] = o[1];
+                a[2] = o[2];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float vv[12], o[3];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) vv[c] = w * dth[12 * p + c];
+            const int c0 = warp_sum12(vv, o);
+            if ((lane & 7) == 0) {
+                float* a = v.acc + warp * P.nf + 12 * p + c0;
+                a[0] = o[0];
+                a[1] = o[1];
+                a[2] = o[2];
+            }
+        }
+    }
+    __syncthreads();
+    const int PS = P.part_stride;
+    float* row = t.ws.part + (size_t)tile * PS;
+    for (int d = tid; d < P.nf; d += T) {
+        float s = 0.0f;
+        for (int ww = 0; ww < nw; ++ww) s += v.acc[ww * P.nf + d];
+        row[kPartHeader + d] = s;
+    }
+    if (tid == 0) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int ww = 0; ww < nw; ++ww) {
+            a0 += sh.red[ww][0];
+            a1 += sh.red[ww][1];
+            a2 += sh.red[ww][2];
+            a3 += sh.red[ww][3];
+        }
+        row[0] = mt;
+        row[1] = a0;
+        row[2] = a1;
+        row[3] = a2;
+        row[4] = a3;
+    }
+
+    // ---- hierarchical combine: the last tile of a group of kGroup tiles combines
+    // the group's rows in tile order; the last group combines the group rows.
+    const int g = tile / kGroup;
+    const int gsize = min(kGroup, P.ntiles - g * kGroup);
+    unsigned* counters = t.ws.counters;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(&counters[g], 1u);
+        sh.last = prev == (unsigned)gsize - 1u;
+    }
+    __syncthreads();
+    if (!sh.last) return;
+    __threadfence();
+    float* comb = v.acc;  // nf + kPartHeader floats (blockDim >= 64 leaves room)
+    const float* src_rows = t.ws.part + (size_t)g * kGroup * PS;
+    combine_rows(sh, src_rows, gsize, PS, P.nf, P.inv_lambda, comb);
+    if (P.ngroups > 1) {
+        float* grow = t.ws.gpart + (size_t)g * PS;
+        for (int i = tid; i < PS; i += T) grow[i] = comb[i];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            counters[g] = 0u;
+            const unsigned prev = atomicAdd(&counters[P.ngroups], 1u);
+            sh.last = prev == (unsigned)P.ngroups - 1u;
+        }
+        __syncthreads();
+        if (!sh.last) return;
+        __threadfence();
+        combine_rows(sh, t.ws.gpart, P.ngroups, PS, P.nf, P.inv_lambda, comb);
+        if (tid == 0) counters[P.ngroups] = 0u;
+    } else if (tid == 0) {
+        counters[g] = 0u;
+    }
+    mppi_finish(sh, v, comb, t.mppi_to_state != 0);
+}
+
+// ---------------------------------------------------------------------------
+// Elite selection (Alg. 1 Sorting) by one block: the Ke smallest (cost, index)
+// pairs.  4-pass 8-bit radix select on the order-preserving cost key (costs
+// staged in shared memory when K <= kSelectSmemMaxK), then an ordered
+// compaction that takes ties at the threshold key by ascending index.
+// ---------------------------------------------------------------------------
+__device__ void select_block(BlockShared& sh, uint32_t* skeys)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    const int K = P.K;
+    const int Ke = P.method == SBS_NAIVE ? 1 : P.Ke;
+    const float* J = t.ws.J;
+    const bool in_smem = K <= kSelectSmemMaxK;
+    if (in_smem) {
+        for (int i = tid; i < K; i += T) skeys[i] = cost_key(__ldcg(J + i));
+        __syncthreads();
+    }
     uint32_t prefix = 0, mask = 0;
     int rank = Ke;  // 1-based rank of the threshold key among the keys matching prefix
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         for (int i = tid; i < 256; i += T) sh.hist[i] = 0;
         __syncthreads();
-        for (int base = 0; base < K; base += T) {
-            const int k = base + tid;
-            bool match = false;
-            uint32_t dig = 0;
-            if (k < K) {
-                const uint32_t key = cost_key(__ldcg(J + k));
-                match = (key & mask) == prefix;
-                dig = (key >> shift) & 255u;
+        for (int base = 0; base < K; base += 8 * T) {
+            uint32_t keys[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = base + u * T + tid;
+                keys[u] = i < K ? (in_smem ? skeys[i] : cost_key(__ldcg(J + i))) : 0u;
             }
-            // warp-aggregated histogram update: one atomic per distinct digit
-            const unsigned act = __ballot_sync(kFull, match);
-            if (match) {
-                const unsigned peers = __match_any_sync(act, dig);
-                if (lane == __ffs(peers) - 1) atomicAdd(&sh.hist[dig], __popc(peers));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = base + u * T + tid;
+                const bool match = i < K && (keys[u] & mask) == prefix;
+                const uint32_t dig = (keys[u] >> shift) & 255u;
+                // warp-aggregated histogram update: one atomic per distinct digit
+                const unsigned act = __ballot_sync(kFull, match);
+                if (match) {
+                    const unsigned peers = __match_any_sync(act, dig);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&sh.hist[dig], __popc(peers));
+                }
             }
         }
         __syncthreads();
@@ -273,9 +608,9 @@ __device__ void radix_select(BlockShared& sh, const float* J, int K, int Ke, int
     }
     const uint32_t thr = prefix;
     const int need_eq = rank;  // keys equal to thr taken in index order
-    // ordered compaction, 8 consecutive keys per thread per chunk
+    int32_t* out = t.ws.elite;
     int pos = 0, eq_seen = 0, nf = 0;
-    float bmin = __int_as_float(0x7f800000);
+    float bmin = kInf;
     for (int base = 0; base < K; base += 8 * T) {
         const int k0 = base + 8 * tid;
         uint32_t keys[8];
@@ -285,9 +620,9 @@ __device__ void radix_select(BlockShared& sh, const float* J, int K, int Ke, int
             const int k = k0 + i;
             if (k < K) {
                 const float Jk = __ldcg(J + k);
-                keys[i] = cost_key(Jk);
+                keys[i] = in_smem ? skeys[k] : cost_key(Jk);
                 bmin = fminf(bmin, Jk);
-                nf += Jk < __int_as_float(0x7f800000) ? 1 : 0;
+                nf += Jk < kInf ? 1 : 0;
             } else {
                 keys[i] = 0xffffffffu;
             }
@@ -318,264 +653,25 @@ __device__ void radix_select(BlockShared& sh, const float* J, int K, int Ke, int
         pos += take_tot;
         eq_seen += eq_tot;
     }
-    *beta = block_min(sh, bmin);
-    int tot;
-    block_scan(sh, nf, &tot);
-    *nfin = tot;
-}
-
-// ---------------------------------------------------------------------------
-// MPPI combine (Alg. 5 UpdateMean): global best cost beta = min over tile
-// minima m_t; each tile's sums are rescaled by exp(-(m_t - beta) / lambda) and
-// added in tile order with Kahan compensation; mean = mu + A / S.
-// Writes mean (and, when to_state, the unchanged variance) of all D entries.
-// ---------------------------------------------------------------------------
-__device__ void mppi_combine(BlockShared& sh, const Views& v, float* out_mean, float* out_var, bool to_state)
-{
-    const InstParams& P = sh.P;
-    const TickArgs& t = sh.t;
-    const int tid = threadIdx.x, T = blockDim.x, nt = P.ntiles, PS = P.part_stride;
-    float* part = P.part;
-    float m = __int_as_float(0x7f800000);
-    for (int i = tid; i < nt; i += T) m = fminf(m, __ldcg(part + (size_t)i * PS));
-    m = block_min(sh, m);
-    for (int i = tid; i < nt; i += T) {
-        const float mt = __ldcg(part + (size_t)i * PS);
-        part[(size_t)i * PS + 5] = mt < __int_as_float(0x7f800000) ? expf(-(mt - m) * P.inv_lambda) : 0.0f;
-    }
-    __syncthreads();
-    float* combo = v.acc;  // nf + 4 floats (blockDim >= 64 guarantees room)
-    const int ncol = P.nf + 4;
-    for (int col = tid; col < ncol; col += T) {
-        const int off = col < 4 ? 1 + col : kPartHeader + (col - 4);
-        float s = 0.0f, c = 0.0f;
-        for (int i = 0; i < nt; ++i) {
-            const float* row = part + (size_t)i * PS;
-            const float sc = __ldcg(row + 5);
-            const float x = __ldcg(row + off);
-            const float term = col == 3 ? x : (col == 1 ? x * sc * sc : x * sc);
-            kahan_add(s, c, term);
-        }
-        combo[col] = s;
-    }
-    __syncthreads();
-    const float S = combo[0];
-    const bool ok = S > 0.0f && m < __int_as_float(0x7f800000);
-    const float invS = ok ? 1.0f / S : 0.0f;
-    for (int d = tid; d < P.nf; d += T) {
-        out_mean[d] = ok ? v.mu[d] + combo[4 + d] * invS : v.mu[d];
-        if (to_state) out_var[d] = v.vr[d];
-    }
-    const float fmean = P.adaptive ? (ok ? combo[2] * invS : sh.mu_f) : sh.mu_f;
-    if (tid == 0 && P.adaptive) {
-        out_mean[P.D - 1] = fmean;
-        if (to_state) out_var[P.D - 1] = sh.var_f;
-    }
-    if (to_state) {
-        sbs_result* r = t.result;
-        if (tid < 12) {
-            const uint32_t ph = (t.phase0 + t.offset[tid / 3]) % kPhaseOne;
-            const float md = ok ? v.mu[tid] + combo[4 + tid] * invS : v.mu[tid];
-            r->u0[tid] = ph < t.duty ? md : 0.0f;
-        }
-        if (tid == 0) {
-            r->cost_min = m;
-            r->ess = ok ? S * S / combo[1] : 0.0f;
-            r->f_mean = fmean;
-            r->q_freq = (int32_t)quantise_mhz(fmean, P.f_min, P.f_max);
-            r->status = ok ? SBS_OK : SBS_ERR_DIVERGED;
-            r->n_finite = (int32_t)combo[3];
-            r->iter_lo = (uint32_t)t.iter;
-            r->iter_hi = (uint32_t)(t.iter >> 32);
-        }
-    }
-    __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// One tile of T samples.  NP = 0: per-step forces; NP > 0: NP spline knots.
-// ---------------------------------------------------------------------------
-template <int NP>
-__device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
-{
-    const InstParams& P = sh.P;
-    const TickArgs& t = sh.t;
-    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    const Views v = carve(dyn, P.H, NP, P.nf, T);
-    stage(sh, v, NP);
-
-    const uint32_t k = (uint32_t)tile * (uint32_t)T + (uint32_t)tid;
-    const bool valid = k < (uint32_t)P.K;
-    const uint32_t seed = P.seed, ctrl = P.ctrl;
-    const uint64_t iter = t.iter;
-    uint32_t q = P.q_init;
-    if (P.adaptive) q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
-
-    float x[12];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) x[c] = sh.x0[c];
-    const float fe[3] = {sh.fe[0], sh.fe[1], sh.fe[2]};
-    uint32_t ph[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        uint32_t p0 = t.phase0 + t.offset[i];
-        ph[i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
-    }
-    const uint32_t step = q * P.dt_us;
-    const uint32_t duty = t.duty;
-
-    constexpr int ND = NP > 0 ? 12 * NP : 1;
-    float dth[ND];
-    if constexpr (NP > 0) {
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float e[12];
-            normals12(k, p, iter, seed, ctrl, e);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) dth[12 * p + c] = v.sd[12 * p + c] * e[c];
-        }
-    }
-
-    float J = 0.0f, Jc = 0.0f;
-    for (int j = 0; j < P.H; ++j) {
-        float G[12];
-        if constexpr (NP == 0) {
-            float e[12];
-            normals12(k, j, iter, seed, ctrl, e);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) G[c] = fmaf(v.sd[12 * j + c], e[c], v.mu[12 * j + c]);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                float s = v.Mb[12 * j + c];
-#pragma unroll
-                for (int p = 0; p < NP; ++p) s = fmaf(v.Bs[j * NP + p], dth[12 * p + c], s);
-                G[c] = s;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (ph[i] >= duty) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
-        kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G));
-        srbd_step(P, x, G, fe);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ph[i] += step;
-            if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
-        }
-    }
-    if (P.adaptive) {
-        const float d = (float)q / 1000.0f - P.f_nominal;
-        kahan_add(J, Jc, P.rho * d * d);
-    }
-    if (!isfinite(J)) J = __int_as_float(0x7f800000);
-    if (valid) {
-        P.J[k] = J;
-        P.q[k] = (int32_t)q;
-    }
-
-    if (t.partials) {
-        const float inf = __int_as_float(0x7f800000);
-        const bool fin = valid && J < inf;
-        const float mt = block_min(sh, fin ? J : inf);
-        const float w = (fin && mt < inf) ? expf(-(J - mt) * P.inv_lambda) : 0.0f;
-        const float f = (float)q / 1000.0f;
-        const float s0 = warp_sum(w), s1 = warp_sum(w * w), s2 = warp_sum(w * f), s3 = warp_sum(fin ? 1.0f : 0.0f);
-        if (lane == 0) {
-            sh.red[warp][0] = s0;
-            sh.red[warp][1] = s1;
-            sh.red[warp][2] = s2;
-            sh.red[warp][3] = s3;
-        }
-        // per-dimension sums of w (theta - mu)
-        if constexpr (NP == 0) {
-            for (int j = 0; j < P.H; ++j) {
-                float e[12], vv[12], o[3];
-                normals12(k, j, iter, seed, ctrl, e);
-#pragma unroll
-                for (int c = 0; c < 12; ++c) vv[c] = w * (v.sd[12 * j + c] * e[c]);
-                const int c0 = warp_sum12(vv, o);
-                if ((lane & 7) == 0) {
-                    float* a = v.acc + warp * P.nf + 12 * j + c0;
-                    a[0] = o[0];
-                    a[1] = o[1];
-                    a[2] = o[2];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float vv[12], o[3];
-#pragma unroll
-                for (int c = 0; c < 12; ++c) vv[c] = w * dth[12 * p + c];
-                const int c0 = warp_sum12(vv, o);
-                if ((lane & 7) == 0) {
-                    float* a = v.acc + warp * P.nf + 12 * p + c0;
-                    a[0] = o[0];
-                    a[1] = o[1];
-                    a[2] = o[2];
-                }
-            }
-        }
-        __syncthreads();
-        float* row = P.part + (size_t)tile * P.part_stride;
-        for (int d = tid; d < P.nf; d += T) {
-            float s = 0.0f;
-            for (int ww = 0; ww < nw; ++ww) s += v.acc[ww * P.nf + d];
-            row[kPartHeader + d] = s;
-        }
-        if (tid == 0) {
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            for (int ww = 0; ww < nw; ++ww) {
-                a0 += sh.red[ww][0];
-                a1 += sh.red[ww][1];
-                a2 += sh.red[ww][2];
-                a3 += sh.red[ww][3];
-            }
-            row[0] = mt;
-            row[1] = a0;
-            row[2] = a1;
-            row[3] = a2;
-            row[4] = a3;
-        }
-    }
-
-    // completion: the last tile of this controller finalises the update
-    __threadfence();
-    __syncthreads();
+    const float beta = block_min(sh, bmin);
+    int nfin;
+    block_scan(sh, nf, &nfin);
     if (tid == 0) {
-        const unsigned prev = atomicAdd(P.counter, 1u);
-        sh.last = prev == (unsigned)P.ntiles - 1u;
+        sbs_result* r = t.result;
+        r->cost_min = beta;
+        r->ess = (float)Ke;
+        r->status = nfin > 0 ? SBS_OK : SBS_ERR_DIVERGED;
+        r->n_finite = nfin;
+        r->iter_lo = (uint32_t)t.iter;
+        r->iter_hi = (uint32_t)(t.iter >> 32);
     }
-    __syncthreads();
-    if (!sh.last) return;
-    __threadfence();
-    if (P.method == SBS_MPPI) {
-        mppi_combine(sh, v, P.state[1 - t.src], P.state[1 - t.src] + P.D, true);
-    } else {
-        if (t.partials) mppi_combine(sh, v, P.mppi_mean, nullptr, false);
-        const int Ke = P.method == SBS_NAIVE ? 1 : P.Ke;
-        float beta;
-        int nfin;
-        radix_select(sh, P.J, P.K, Ke, P.elite, &beta, &nfin);
-        if (tid == 0) {
-            sbs_result* r = t.result;
-            r->cost_min = beta;
-            r->ess = (float)Ke;
-            r->status = nfin > 0 ? SBS_OK : SBS_ERR_DIVERGED;
-            r->n_finite = nfin;
-            r->iter_lo = (uint32_t)t.iter;
-            r->iter_hi = (uint32_t)(t.iter >> 32);
-        }
-    }
-    if (tid == 0) *P.counter = 0u;
 }
 
 // ---------------------------------------------------------------------------
 // Elite / Naive refit of one step (or knot) b, or of the frequency (b == nt).
-// Elite (Alg. 1 Update): mean = mu + sd * mean(eps_e), var = sd^2 * mean((eps_e -
-// mean eps)^2) floored (two passes over regenerated noise); Naive (Alg. 3): the
-// best sample, variance kept.
+// With d = theta - mu the stored deviations of the elites: mean = mu + mean(d),
+// var = mean((d - mean(d))^2) floored (Alg. 1 Update, two passes); Naive
+// (Alg. 3): the best sample, variance kept.
 // ---------------------------------------------------------------------------
 __device__ void refit_block(BlockShared& sh, int b)
 {
@@ -586,7 +682,9 @@ __device__ void refit_block(BlockShared& sh, int b)
     const float* sv = sm + P.D;
     float* dm = P.state[1 - t.src];
     float* dv = dm + P.D;
+    const int K = P.K;
     const int Ke = P.method == SBS_NAIVE ? 1 : P.Ke;
+    const int32_t* elite = t.ws.elite;
     sbs_result* r = t.result;
     const bool diverged = __ldcg(&r->status) != SBS_OK;
     if (b < P.nt) {
@@ -595,7 +693,6 @@ __device__ void refit_block(BlockShared& sh, int b)
             shifted_entry(P, t, sm, sv, 12 * b + tid, m, var);
             sh.mu12[tid] = m;
             sh.vr12[tid] = var;
-            sh.sd12[tid] = sqrtf(var);
         }
         __syncthreads();
         float mean_c = 0.0f, var_c = 0.0f;  // valid in threads < 12
@@ -606,10 +703,8 @@ __device__ void refit_block(BlockShared& sh, int b)
             }
         } else if (P.method == SBS_NAIVE) {
             if (tid < 12) {
-                const uint32_t kb = (uint32_t)__ldcg(P.elite);
-                const float4 z = normals4(kb, 1u + 3u * (uint32_t)b + (uint32_t)(tid / 4), t.iter, P.seed, P.ctrl);
-                const float e = (tid % 4 == 0) ? z.x : (tid % 4 == 1) ? z.y : (tid % 4 == 2) ? z.z : z.w;
-                mean_c = fmaf(sh.sd12[tid], e, sh.mu12[tid]);
+                const int kb = __ldcg(elite);
+                mean_c = sh.mu12[tid] + __ldcg(t.ws.theta + ((size_t)b * K + kb) * 12 + tid);
                 var_c = sh.vr12[tid];
             }
         } else {
@@ -618,36 +713,27 @@ __device__ void refit_block(BlockShared& sh, int b)
 #pragma unroll
                 for (int c = 0; c < 12; ++c) s[c] = 0.0f;
                 for (int e = tid; e < Ke; e += blockDim.x) {
-                    const uint32_t kb = (uint32_t)__ldcg(P.elite + e);
-                    float z[12];
-                    normals12(kb, b, t.iter, P.seed, P.ctrl, z);
+                    const int kb = __ldcg(elite + e);
+                    const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
+                    const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
+                    const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
                     for (int c = 0; c < 12; ++c) {
                         if (pass == 0) {
-                            s[c] += z[c];
+                            s[c] += d[c];
                         } else {
-                            const float d = z[c] - sh.ebar[c];
-                            s[c] = fmaf(d, d, s[c]);
+                            const float q = d[c] - sh.dbar[c];
+                            s[c] = fmaf(q, q, s[c]);
                         }
                     }
                 }
-                float o[3];
-                const int c0 = warp_sum12(s, o);
-                if ((lane & 7) == 0) {
-                    sh.wacc[warp][c0] = o[0];
-                    sh.wacc[warp][c0 + 1] = o[1];
-                    sh.wacc[warp][c0 + 2] = o[2];
-                }
-                __syncthreads();
+                const float tot = block_sum12(sh, s);
                 if (tid < 12) {
-                    float tot = 0.0f;
-                    for (int w = 0; w < nw; ++w) tot += sh.wacc[w][tid];
                     if (pass == 0) {
-                        sh.ebar[tid] = tot / (float)Ke;
+                        sh.dbar[tid] = tot / (float)Ke;
                     } else {
-                        const float sd = sh.sd12[tid];
-                        var_c = fmaxf(sd * sd * (tot / (float)Ke), P.var_min);
-                        mean_c = fmaf(sd, sh.ebar[tid], sh.mu12[tid]);
+                        var_c = fmaxf(tot / (float)Ke, P.var_min);
+                        mean_c = sh.mu12[tid] + sh.dbar[tid];
                     }
                 }
                 __syncthreads();
@@ -671,20 +757,20 @@ __device__ void refit_block(BlockShared& sh, int b)
         float mean_f = mu_f, vf = var_f;
         if (!diverged) {
             if (P.method == SBS_NAIVE) {
-                mean_f = (float)__ldcg(P.q + __ldcg(P.elite)) / 1000.0f;
+                mean_f = (float)__ldcg(t.ws.q + __ldcg(elite)) / 1000.0f;
             } else {
                 float s = 0.0f;
-                for (int e = tid; e < Ke; e += blockDim.x) s += (float)__ldcg(P.q + __ldcg(P.elite + e)) / 1000.0f;
+                for (int e = tid; e < Ke; e += blockDim.x) s += (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f;
                 s = warp_sum(s);
+                __syncthreads();
                 if (lane == 0) sh.red[warp][0] = s;
                 __syncthreads();
                 float tot = 0.0f;
                 for (int w = 0; w < nw; ++w) tot += sh.red[w][0];
                 mean_f = tot / (float)Ke;
-                __syncthreads();
                 float s2 = 0.0f;
                 for (int e = tid; e < Ke; e += blockDim.x) {
-                    const float d = (float)__ldcg(P.q + __ldcg(P.elite + e)) / 1000.0f - mean_f;
+                    const float d = (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f - mean_f;
                     s2 = fmaf(d, d, s2);
                 }
                 s2 = warp_sum(s2);
@@ -718,6 +804,16 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __re
     rollout_tile<NP>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
 }
 
+__global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    load_params(dP, sh);
+    if (threadIdx.x == 0) sh.t = t;
+    __syncthreads();
+    select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
+}
+
 __global__ void __launch_bounds__(kRefitThreads) k_refit(const InstParams* __restrict__ dP, TickArgs t)
 {
     __shared__ BlockShared sh;
@@ -744,19 +840,21 @@ __global__ void k_init(const InstParams* __restrict__ dP, TickArgs t)
 }
 
 // Item it of a batched launch belongs to the last controller whose first item
-// is <= it (records are in item order).
-__device__ __forceinline__ int find_rec(const InstRec* recs, int n, int it, bool refit)
+// is <= it (records are in item order).  which: 0 tiles, 1 selections, 2 refits.
+__device__ __forceinline__ int find_rec(const InstRec* recs, int n, int it, int which)
 {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int b = refit ? recs[mid].refit_begin : recs[mid].tile_begin;
-        if (b <= it) lo = mid; else hi = mid - 1;
+        const int b =
+            which == 0 ? recs[mid].tile_begin : (which == 1 ? recs[mid].select_begin : recs[mid].refit_begin);
+        if (b <= it) lo = mid;
+        else hi = mid - 1;
     }
     return lo;
 }
 
-// counts = {controllers, rollout items, refit items}; heads = {rollout, refit} queue heads.
+// counts = {controllers, tile items, selection items, refit items}; heads = queue heads.
 // Every controller of one launch uses the same policy (NP).
 template <int NP>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* __restrict__ recs,
@@ -770,7 +868,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* _
         __syncthreads();
         const int it = sh.item;
         if (it >= nitems) break;
-        const int i = find_rec(recs, n, it, false);
+        const int i = find_rec(recs, n, it, 0);
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
@@ -779,9 +877,10 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* _
     }
 }
 
-__global__ void __launch_bounds__(kRefitThreads) k_batch_refit(const InstRec* __restrict__ recs,
-                                                              const int* __restrict__ counts, int* heads)
+__global__ void __launch_bounds__(kSelectThreads) k_batch_select(const InstRec* __restrict__ recs,
+                                                                const int* __restrict__ counts, int* heads)
 {
+    extern __shared__ float4 dyn4[];
     __shared__ BlockShared sh;
     const int n = counts[0], nitems = counts[2];
     for (;;) {
@@ -789,7 +888,26 @@ __global__ void __launch_bounds__(kRefitThreads) k_batch_refit(const InstRec* __
         __syncthreads();
         const int it = sh.item;
         if (it >= nitems) break;
-        const int i = find_rec(recs, n, it, true);
+        const int i = find_rec(recs, n, it, 1);
+        load_params(recs[i].dP, sh);
+        load_tick(&recs[i].t, sh);
+        __syncthreads();
+        select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRefitThreads) k_batch_refit(const InstRec* __restrict__ recs,
+                                                              const int* __restrict__ counts, int* heads)
+{
+    __shared__ BlockShared sh;
+    const int n = counts[0], nitems = counts[3];
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&heads[2], 1);
+        __syncthreads();
+        const int it = sh.item;
+        if (it >= nitems) break;
+        const int i = find_rec(recs, n, it, 2);
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
@@ -856,13 +974,6 @@ static int ensure_smem_attr(const void* fn, size_t smem)
     return status_of(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 }
 
-int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
-{
-    (void)hP;
-    k_init<<<1, 256, 0, (cudaStream_t)stream>>>(dP, t);
-    return status_of(cudaGetLastError());
-}
-
 template <int NP>
 static const void* rollout_fn()
 {
@@ -901,6 +1012,16 @@ const void* batch_rollout_fn(int P)
     }
 }
 
+const void* batch_select_fn() { return (const void*)k_batch_select; }
+const void* batch_refit_fn() { return (const void*)k_batch_refit; }
+
+int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
+{
+    (void)hP;
+    k_init<<<1, 256, 0, (cudaStream_t)stream>>>(dP, t);
+    return status_of(cudaGetLastError());
+}
+
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T);
@@ -914,6 +1035,15 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
     return status_of(cudaLaunchKernel(fn, dim3(hP.ntiles), dim3(hP.T), args, smem, (cudaStream_t)stream));
 }
 
+int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
+{
+    const size_t smem = select_smem_bytes(hP.K);
+    int st = ensure_smem_attr((const void*)k_select, smem);
+    if (st) return st;
+    k_select<<<1, kSelectThreads, smem, (cudaStream_t)stream>>>(dP, t);
+    return status_of(cudaGetLastError());
+}
+
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
     const int grid = hP.nt + (hP.adaptive ? 1 : 0);
@@ -921,26 +1051,32 @@ int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, 
     return status_of(cudaGetLastError());
 }
 
-int batch_grid(int P, size_t smem, int T, int* grid1, int* grid2)
+int batch_grid(int P, size_t smem, size_t sel_smem, int T, int grids[3])
 {
-    int dev, sms, b1 = 0, b2 = 0;
+    int dev, sms, b1 = 0, b2 = 0, b3 = 0;
     const void* fn = batch_rollout_fn(P);
     if (!fn) return SBS_ERR_INVALID_ARG;
     if (cudaGetDevice(&dev) != cudaSuccess) return SBS_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SBS_ERR_CUDA;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;
+    st = ensure_smem_attr((const void*)k_batch_select, sel_smem);
+    if (st) return st;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, T, smem) != cudaSuccess) return SBS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_batch_refit, kRefitThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_batch_select, kSelectThreads, sel_smem) != cudaSuccess)
         return SBS_ERR_CUDA;
-    if (b1 < 1 || b2 < 1) return SBS_ERR_INVALID_ARG;
-    *grid1 = sms * b1;
-    *grid2 = sms * b2;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_batch_refit, kRefitThreads, 0) != cudaSuccess)
+        return SBS_ERR_CUDA;
+    if (b1 < 1 || b2 < 1 || b3 < 1) return SBS_ERR_INVALID_ARG;
+    grids[0] = sms * b1;
+    grids[1] = sms * b2;
+    grids[2] = sms * b3;
     return SBS_OK;
 }
 
-int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem, int T, int grid1,
-                 int grid2, void* stream)
+// events: null, or four CUDA events recorded before and after each stage.
+int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem, size_t sel_smem,
+                 int T, const int grids[3], void* stream, void* const* events)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const void* fn = batch_rollout_fn(P);
@@ -949,12 +1085,16 @@ int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, s
     const int* c = dCounts;
     int* hd = dHeads;
     void* args[] = {(void*)&r, (void*)&c, (void*)&hd};
-    if (cudaLaunchKernel(fn, dim3(grid1), dim3(T), args, smem, s) != cudaSuccess) return SBS_ERR_CUDA;
-    k_batch_refit<<<grid2, kRefitThreads, 0, s>>>(dRecs, dCounts, dHeads);
+    if (events) cudaEventRecord((cudaEvent_t)events[0], s);
+    if (cudaLaunchKernel(fn, dim3(grids[0]), dim3(T), args, smem, s) != cudaSuccess) return SBS_ERR_CUDA;
+    if (events) cudaEventRecord((cudaEvent_t)events[1], s);
+    k_batch_select<<<grids[1], kSelectThreads, sel_smem, s>>>(dRecs, dCounts, dHeads);
+    if (cudaGetLastError() != cudaSuccess) return SBS_ERR_CUDA;
+    if (events) cudaEventRecord((cudaEvent_t)events[2], s);
+    k_batch_refit<<<grids[2], kRefitThreads, 0, s>>>(dRecs, dCounts, dHeads);
+    if (events) cudaEventRecord((cudaEvent_t)events[3], s);
     return status_of(cudaGetLastError());
 }
-
-const void* batch_refit_fn() { return (const void*)k_batch_refit; }
 
 int launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream)
 {

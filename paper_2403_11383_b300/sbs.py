@@ -81,16 +81,19 @@ ABI = {
     "sbs_destroy": (None, [C.c_void_p]),
     "sbs_dim": (C.c_int, [C.c_void_p]),
     "sbs_device_bytes": (C.c_size_t, [C.c_void_p]),
+    "sbs_workspace_bytes": (C.c_size_t, [C.c_void_p]),
     "sbs_reset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "sbs_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
     "sbs_state_size": (C.c_size_t, [C.c_void_p]),
     "sbs_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "sbs_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
-    "sbs_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sbs_batch_create": (C.c_int, [C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
     "sbs_batch_destroy": (None, [C.c_void_p]),
     "sbs_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_status_str": (C.c_char_p, [C.c_int]),
+    "sbs_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_batch_stage_ms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_normals": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_void_p,
@@ -99,7 +102,8 @@ ABI = {
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The in-tree library, or the one named by SBS_LIB (an alternative build)."""
+    return os.environ.get("SBS_LIB") or _build.LIB
 
 
 def lib():
@@ -167,7 +171,8 @@ def make_gait(g: dict) -> Gait:
 
 def parse_result(buf) -> dict:
     """Decode one sbs_result from bytes / a uint8 array of RESULT_BYTES."""
-    r = Result.from_buffer_copy(bytes(np.asarray(buf, dtype=np.uint8).tobytes()[:RESULT_BYTES]))
+    raw = bytes(buf) if isinstance(buf, (bytes, bytearray, memoryview)) else np.asarray(buf, dtype=np.uint8).tobytes()
+    r = Result.from_buffer_copy(raw[:RESULT_BYTES])
     return {"u0": np.array(r.u0[:], dtype=np.float32), "cost_min": r.cost_min, "ess": r.ess,
             "f_mean": r.f_mean, "q_freq": r.q_freq, "status": r.status, "n_finite": r.n_finite,
             "iter": r.iter_lo | (r.iter_hi << 32)}
@@ -233,6 +238,9 @@ class Controller:
 
     def device_bytes(self) -> int:
         return lib().sbs_device_bytes(self._h)
+
+    def workspace_bytes(self) -> int:
+        return lib().sbs_workspace_bytes(self._h)
 
     def close(self):
         if self._h:
@@ -307,10 +315,10 @@ class Controller:
 class Batch:
     """Many controllers per persistent, graph-captured launch (sbs_batch_*)."""
 
-    def __init__(self, max_instances: int, max_tiles: int, use_torch_allocator: bool = True):
+    def __init__(self, max_instances: int, workspace_bytes: int, use_torch_allocator: bool = True):
         self._b = C.c_void_p()
         alloc = C.byref(torch_allocator().struct) if use_torch_allocator else None
-        check(lib().sbs_batch_create(max_instances, max_tiles, alloc, C.byref(self._b)), "sbs_batch_create")
+        check(lib().sbs_batch_create(max_instances, workspace_bytes, alloc, C.byref(self._b)), "sbs_batch_create")
 
     def close(self):
         if self._b:
@@ -322,6 +330,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_profiling(self, on: bool):
+        check(lib().sbs_batch_set_profiling(self._b, 1 if on else 0), "sbs_batch_set_profiling")
+
+    def stage_ms(self):
+        """(rollout, selection, refit) milliseconds of the last profiled tick."""
+        ms = (C.c_float * 3)()
+        check(lib().sbs_batch_stage_ms(self._b, ms), "sbs_batch_stage_ms")
+        return list(ms)
 
     def solve(self, controllers, problems, results, stream=None):
         """controllers: list of Controller; problems: list of Problem (device

@@ -1,0 +1,180 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path and the FP64 oracle
+on the same seeded inputs and compare with the tolerances below.
+
+Tolerances (derived from the arithmetic):
+  * integers (Philox words, quantised frequencies, contact flags): exact; a
+    frequency whose FP64 value lies within 2e-3 mHz of a rounding boundary may
+    round either way in single precision and is checked against both candidates.
+  * costs: relative error <= max(1e-4, 100 kappa) where kappa is the oracle's
+    conditioning estimate of that sample (relative cost change under per-step
+    rounding-sized perturbations); samples with kappa > 1e-4 are chaotic
+    (tumbling rollouts) and only reported.
+  * MPPI mean: 1e-4 m|g| plus the first-order propagation of those cost
+    tolerances through the weights: (1/lambda) sum_i w_i |theta_i - m| tol_i J_i.
+  * elite set: identical except samples whose cost is within its tolerance band
+    of the threshold cost.
+"""
+import math
+
+import numpy as np
+
+import oracle as orc
+from paper_2403_11383_b300 import sbs as S
+from paper_2403_11383_b300 import workloads as W
+
+MG = 21.0 * 9.81
+MEAN_ATOL = 1e-4 * MG
+Q_MARGIN = 2e-3
+KAPPA_STRICT = 1e-6
+KAPPA_GATED = 1e-4
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+class GpuRun:
+    """One controller on the GPU with device-resident inputs."""
+
+    def __init__(self, cfg, prob, tile=0):
+        import torch
+        self.cfg, self.prob = cfg, prob
+        self.ctl = S.Controller(cfg, tile=tile)
+        self.x0 = dev(prob["x0"])
+        self.xref = dev(prob["xref"])
+        self.fext = dev(prob["f_ext"])
+        self.torch = torch
+
+    def solve(self, shift=0, gait=None, x0=None):
+        res = self.ctl.solve(self.x0 if x0 is None else x0, self.xref, gait or self.prob["gait"], self.fext, shift)
+        self.torch.cuda.synchronize()
+        return S.parse_result(res.cpu().numpy())
+
+    def read(self, which):
+        out = self.ctl.read(which).cpu().numpy()
+        self.torch.cuda.synchronize()
+        return out
+
+    def state(self):
+        return self.read(S.BUF_MEAN), self.read(S.BUF_VAR)
+
+    def close(self):
+        self.ctl.close()
+
+
+class OracleRun:
+    """The oracle on the same (single-precision-rounded) inputs."""
+
+    def __init__(self, cfg, prob):
+        self.cfg, self.prob = cfg, prob
+        self.P = orc.make_params(cfg)
+        self.g = orc.make_gait(prob["gait"])
+        self.x0 = np.float64(f32(prob["x0"]))
+        self.xref = np.float64(f32(prob["xref"]))
+        self.fext = np.float64(f32(prob["f_ext"]))
+        self.mean, self.var = orc.init_dist(self.P, self.g)
+        self.iter = 0
+
+    def rollout(self, want_theta=True, kappa=True, nthreads=8):
+        J, q, th, margin = orc.rollout(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
+                                       self.iter, want_theta=want_theta, nthreads=nthreads)
+        kap = None
+        if kappa:
+            kap = orc.cost_condition_all(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
+                                         self.iter, nthreads=nthreads)
+        return J, q, th, margin, kap
+
+    def sample(self, k, q_override=-1):
+        return orc.rollout_sample(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
+                                  self.iter, k, q_override)
+
+    def kappa(self, k):
+        return orc.cost_condition(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
+                                  self.iter, k)[0]
+
+    def solve(self, shift=0, nthreads=8):
+        r = orc.solve(self.P, self.g, self.x0, self.xref, self.fext, shift, self.iter, self.mean, self.var,
+                      nthreads=nthreads)
+        self.mean, self.var = r["mean"], r["var"]
+        self.iter += self.P.iterations
+        return r
+
+
+def alt_frequency(o, k):
+    """The other rounding of sample k's frequency (from the oracle's FP64 value)."""
+    z = orc.freq_normal(o.P.seed, o.P.ctrl, k, o.iter)
+    f = min(o.P.f_max, max(o.P.f_min, o.mean[-1] + math.sqrt(o.var[-1]) * z))
+    lo = math.floor(1000.0 * f)
+    q, _ = orc.quantise_freq(o.mean[-1], math.sqrt(o.var[-1]), z, o.P.f_min, o.P.f_max)
+    return lo + 1 if q == lo else lo
+
+
+def cost_tolerance(kap):
+    return np.maximum(1e-4, 100.0 * kap)
+
+
+def check_frequencies(q_gpu, q_orc, margin):
+    """Exact except at ambiguous roundings, where either neighbour is valid."""
+    amb = margin < Q_MARGIN
+    assert np.array_equal(q_gpu[~amb], q_orc[~amb])
+    d = np.abs(q_gpu[amb].astype(np.int64) - q_orc[amb].astype(np.int64))
+    assert np.all(d <= 1)
+    return amb
+
+
+def check_costs(J_gpu, J_orc, kap, skip=None):
+    """Cost parity gated by conditioning; returns a report dict."""
+    Jg = J_gpu.astype(np.float64)
+    fin = np.isfinite(J_orc) & (J_orc < 3.0e38)
+    sel = np.ones(J_orc.size, bool) if skip is None else ~skip
+    strict = sel & fin & (kap <= KAPPA_STRICT)
+    gated = sel & fin & (kap <= KAPPA_GATED)
+    rel = np.abs(Jg - J_orc) / np.maximum(np.abs(J_orc), 1e-30)
+    tol = cost_tolerance(kap)
+    bad = gated & ~(rel <= tol)
+    assert not bad.any(), f"{bad.sum()} costs outside tolerance: rel {rel[bad][:5]} kappa {kap[bad][:5]}"
+    if strict.any():
+        assert rel[strict].max() <= 1e-4
+    # a sample the oracle finds finite and well conditioned is finite on the GPU too
+    assert np.all(np.isfinite(Jg[gated]))
+    return {"n": J_orc.size, "strict": int(strict.sum()), "gated": int(gated.sum()),
+            "max_rel_strict": float(rel[strict].max()) if strict.any() else 0.0,
+            "max_rel_gated": float(rel[gated].max()) if gated.any() else 0.0}
+
+
+def mppi_tolerance(J, th, kap, lam, mean_ref):
+    """Per-dimension tolerance of the MPPI mean: accumulation term plus the
+    first-order effect of the cost tolerances through the weights."""
+    fin = np.isfinite(J)
+    beta = J[fin].min()
+    w = np.where(fin, np.exp(-(np.where(fin, J, beta) - beta) / lam), 0.0)
+    w /= w.sum()
+    tolJ = cost_tolerance(kap) * np.where(fin, np.abs(J), 0.0)
+    prop = (w * tolJ)[:, None] * np.abs(th - mean_ref[None, :]) / lam
+    return MEAN_ATOL + prop.sum(axis=0)
+
+
+def elite_band_ok(gpu_set, orc_J, Ke, kap, alt_J=None):
+    """The GPU elite set equals the oracle's except for samples within their
+    tolerance band of the threshold cost (or with an ambiguous frequency whose
+    alternative cost crosses the threshold)."""
+    key = np.where(np.isnan(orc_J), np.inf, orc_J)
+    order = np.lexsort((np.arange(key.size), key))
+    orc_set = set(order[:Ke].tolist())
+    thr = key[order[Ke - 1]]
+    nxt = key[order[Ke]] if Ke < key.size else np.inf
+    diff = orc_set ^ set(int(i) for i in gpu_set)
+    tol = cost_tolerance(kap)
+    for i in diff:
+        lo, hi = min(thr, nxt), max(thr, nxt)
+        band = tol[i] * max(abs(key[i]), abs(lo)) * 2
+        near = (key[i] >= lo - band) and (key[i] <= hi + band)
+        if alt_J is not None and i in alt_J:
+            near = near or alt_J[i] <= hi + band
+        assert near, f"sample {i} cost {key[i]} far from threshold {thr} (tol {tol[i]})"
+    return len(diff)

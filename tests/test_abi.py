@@ -1,0 +1,98 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/sbs.h declares; configuration validation needs no device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2403_11383_b300 import build as B
+from paper_2403_11383_b300 import sbs as S
+from paper_2403_11383_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "sbs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbs_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert len(names) >= 18
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (sbs_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # and the Python binding marshals every one of them
+    assert set(names) == set(S.ABI), set(names) ^ set(S.ABI)
+    for n in names:
+        getattr(lib, n)
+
+
+def test_struct_sizes_match_header():
+    # gcc computes the sizes of the ABI structs from the header itself
+    code = r'''
+#include <stdio.h>
+#include "sbs.h"
+int main(void) { printf("%zu %zu %zu %zu %zu %zu\n", sizeof(sbs_config), sizeof(sbs_problem),
+  sizeof(sbs_result), sizeof(sbs_gait), sizeof(sbs_model), sizeof(sbs_cost)); return 0; }
+'''
+    tmp = os.path.join(B.OUT_DIR, "abi_sizes")
+    os.makedirs(B.OUT_DIR, exist_ok=True)
+    with open(tmp + ".c", "w") as f:
+        f.write(code)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", tmp, tmp + ".c"], check=True)
+    got = [int(v) for v in subprocess.run([tmp], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(S.Config), C.sizeof(S.Problem), C.sizeof(S.Result), C.sizeof(S.Gait), C.sizeof(S.Model),
+            C.sizeof(S.Cost)]
+    assert got == want
+
+
+def test_status_strings(lib):
+    for s in (0, 1, -1, -2, -3, -4, -5, -6):
+        assert S.status_str(s) not in ("", "unknown status")
+
+
+@pytest.mark.parametrize("field,value", [("K", 0), ("H", 0), ("H", 129), ("P", 5), ("P", 1), ("method", 7),
+                                         ("iterations", 0), ("elite_count", 0), ("dt_us", 0), ("lam", 0.0),
+                                         ("f_max", 0.5), ("tile", 48), ("tile", 512), ("q_init", 0)])
+def test_invalid_config_rejected_without_device(lib, field, value):
+    c = S.make_config(W.config("adaptive_elite_k8192_h25"))
+    setattr(c, field, value)
+    h = C.c_void_p()
+    assert lib.sbs_create(C.byref(c), None, C.byref(h)) == S.ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_invalid_model_rejected_without_device(lib):
+    cfg = W.config("plain_mppi_k512_h12")
+    c = S.make_config(cfg)
+    c.model.mass = -1.0
+    h = C.c_void_p()
+    assert lib.sbs_create(C.byref(c), None, C.byref(h)) == S.ERR_INVALID_ARG
+    c = S.make_config(cfg)
+    c.cost.Q[3] = -1.0
+    assert lib.sbs_create(C.byref(c), None, C.byref(h)) == S.ERR_INVALID_ARG
+    # a phase step of a full cycle per time step is rejected
+    cfg2 = dict(cfg, dt_us=300000, f_max=4.0)
+    c = S.make_config(cfg2)
+    assert lib.sbs_create(C.byref(c), None, C.byref(h)) == S.ERR_INVALID_ARG
+
+
+def test_null_arguments(lib):
+    assert lib.sbs_create(None, None, None) == S.ERR_INVALID_ARG
+    assert lib.sbs_solve(None, None, None, None) == S.ERR_INVALID_ARG
+    assert lib.sbs_batch_solve(None, 0, None, None, None, None) == S.ERR_INVALID_ARG
+    assert lib.sbs_dim(None) == S.ERR_INVALID_ARG
+    lib.sbs_destroy(None)
+    lib.sbs_batch_destroy(None)

@@ -1,0 +1,386 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.  Tolerances are documented in gpu_helpers."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from gpu_helpers import (MEAN_ATOL, GpuRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
+                         elite_band_ok, f32, mppi_tolerance)
+from paper_2403_11383_b300 import sbs as S
+from paper_2403_11383_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    S.lib()
+    return torch
+
+
+def golden_kat():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            rows.append(v)
+    return rows
+
+
+# ------------------------------------------------------------------ random numbers
+
+def test_philox_gpu_known_answers_and_oracle(cuda):
+    torch = cuda
+    rows = golden_kat()
+    rng = np.random.default_rng(0)
+    extra = rng.integers(0, 2 ** 32, size=(4093, 6), dtype=np.uint64)
+    allv = np.array([r[:6] for r in rows] + extra.tolist(), dtype=np.uint64)
+    ctr = torch.tensor(allv[:, :4].astype(np.uint32).view(np.int32), device="cuda")
+    key = torch.tensor(allv[:, 4:6].astype(np.uint32).view(np.int32), device="cuda")
+    out = S.philox(ctr, key).cpu().numpy().view(np.uint32)
+    for i, r in enumerate(rows):
+        assert out[i].tolist() == r[6:10]
+    for i in range(len(rows), allv.shape[0], 7):
+        want = orc.philox4x32_10(allv[i, :4].astype(np.uint32), allv[i, 4:6].astype(np.uint32))
+        assert out[i].tolist() == want.tolist()
+
+
+def test_normals_gpu_vs_oracle(cuda):
+    seed, ctrl, it = 11, 3, (1 << 32) + 7
+    nk, nn = 1024, 50
+    z = S.normals(seed, ctrl, it, 5, nk, nn).cpu().numpy()
+    ref = np.array([[orc.freq_normal(seed, ctrl, 5 + i, it)] +
+                    [orc.normal(seed, ctrl, 5 + i, n, it) for n in range(nn)] for i in range(nk)])
+    np.testing.assert_allclose(z, ref, rtol=2e-6, atol=3e-6)
+
+
+# ------------------------------------------------------------------ single solves
+
+def _mppi_parity(cfg, prob, name):
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    r = g.solve()
+    Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
+    amb = check_frequencies(qg, q, margin)
+    rep = check_costs(Jg, J, kap, skip=amb)
+    st, mo, esso, beta = orc.mppi(J, th, cfg["lam"])
+    mg, vg = g.state()
+    tol = mppi_tolerance(J, th, kap, cfg["lam"], mo)
+    assert np.all(np.abs(mg - mo) <= tol), (name, np.max(np.abs(mg - mo) - tol))
+    np.testing.assert_array_equal(vg, f32(o.var))  # MPPI keeps the covariance
+    assert r["status"] == S.OK
+    assert r["cost_min"] == float(np.min(Jg))  # its value is covered by the cost parity above
+    assert r["n_finite"] == int(np.sum(np.isfinite(J) & (J < 3e38)))
+    u0 = orc.first_control(o.P, o.g, mo)
+    np.testing.assert_allclose(r["u0"], u0, atol=float(np.max(tol[:12])))
+    g.close()
+    return rep
+
+
+def test_plain_mppi_single_solve(cuda):
+    cfg = W.config("plain_mppi_k512_h12")
+    rep = _mppi_parity(cfg, W.problem(cfg), "c1")
+    assert rep["gated"] == cfg["K"]
+
+
+@pytest.mark.parametrize("K,H,gait,tile", [(1000, 7, "trot", 128), (77, 3, "pace", 64), (1, 5, "crawl", 128),
+                                           (3001, 20, "crawl", 256)])
+def test_mppi_ragged_and_small(cuda, K, H, gait, tile):
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(K=K, H=H, gait=gait, tile=tile, seed=K)
+    _mppi_parity(cfg, W.problem(cfg), f"K{K}")
+
+
+def test_mppi_k1_returns_its_sample(cuda):
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg["K"] = 1
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    g.solve()
+    mg, _ = g.state()
+    np.testing.assert_allclose(mg, th[0], atol=1e-4, rtol=1e-6)
+    g.close()
+
+
+def test_mppi_many_tiles_hierarchical_combine(cuda):
+    # 40 000 samples = 313 tiles = 20 groups of 16: exercises the two-level combine
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(K=40000, seed=9)
+    _mppi_parity(cfg, W.problem(cfg), "K40000")
+
+
+def test_adaptive_elite_iteration0_full_size(cuda):
+    # the adaptive elite workload (K=8192, H=25, 60 N push): iteration 0
+    cfg = W.config("adaptive_elite_k8192_h25")
+    cfg["iterations"] = 1
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    r = g.solve()
+    Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
+    amb = check_frequencies(qg, q, margin)
+    check_costs(Jg, J, kap, skip=amb)
+    Ke = cfg["elite_count"]
+    eg = g.read(S.BUF_ELITE)
+    assert np.all(np.diff(eg) > 0) and eg.size == Ke
+    alt = {}
+    for i in np.nonzero(amb)[0]:
+        alt[int(i)] = o.sample(int(i), alt_frequency(o, int(i)))[0]
+    elite_band_ok(eg, J, Ke, kap, alt)
+    # the refit is the elite mean / biased variance of the selected samples
+    mg, vg = g.state()
+    thg = th.copy()
+    thg[:, -1] = qg / 1000.0
+    sel = thg[eg]
+    np.testing.assert_allclose(mg, sel.mean(axis=0), atol=MEAN_ATOL, rtol=1e-5)
+    vref = np.maximum(sel.var(axis=0), np.r_[np.full(thg.shape[1] - 1, cfg["sigma_min"] ** 2),
+                                             cfg["sigma_f_min"] ** 2])
+    np.testing.assert_allclose(vg, vref, rtol=2e-4, atol=1e-6)
+    assert r["cost_min"] == pytest.approx(float(np.min(Jg)), rel=0)
+    # MPPI on the same noise
+    mm = g.read(S.BUF_MPPI_MEAN)
+    st, mo, _, _ = orc.mppi(J, th, cfg["lam"])
+    tol = mppi_tolerance(J, th, kap, cfg["lam"], mo)
+    assert np.all(np.abs(mm[:-1] - mo[:-1]) <= tol[:-1])
+    g.close()
+
+
+def _well_conditioned_elite():
+    cfg = W.config("adaptive_elite_k8192_h25")
+    cfg.update(H=12, K=4096, elite_count=W.elite_count(0.05, 4096), seed=21, iterations=1)
+    return cfg
+
+
+def test_elite_iterations_track_oracle(cuda):
+    # five warm-started elite iterations compared iteration by iteration while the
+    # elite sets agree (a swap at a near tie ends the comparison)
+    cfg = _well_conditioned_elite()
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    compared = 0
+    for it in range(5):
+        J, q, th, margin, kap = o.rollout()
+        r = g.solve()
+        Jg, qg, eg = g.read(S.BUF_COST), g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
+        amb = check_frequencies(qg, q, margin)
+        check_costs(Jg, J, kap, skip=amb)
+        ro = o.solve()
+        mg, vg = g.state()
+        if not np.array_equal(np.sort(ro["elite"]), eg):
+            elite_band_ok(eg, J, cfg["elite_count"], kap)
+            break
+        np.testing.assert_allclose(mg, ro["mean"], atol=MEAN_ATOL, rtol=1e-5)
+        np.testing.assert_allclose(vg, ro["var"], rtol=2e-4, atol=1e-6)
+        np.testing.assert_allclose(r["u0"], ro["u0"], atol=MEAN_ATOL)
+        assert r["q_freq"] == pytest.approx(round(1000 * min(4.0, max(1.0, ro["f_mean"]))), abs=1)
+        compared += 1
+    assert compared >= 1
+    g.close()
+
+
+def test_naive_is_best_sample(cuda):
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(method="naive", K=1500, seed=5)
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    r = g.solve()
+    Jg = g.read(S.BUF_COST)
+    check_costs(Jg, J, kap)
+    best = int(np.lexsort((np.arange(J.size), J))[0])
+    kb = int(np.lexsort((np.arange(Jg.size), Jg))[0])
+    assert kb == best or abs(J[kb] - J[best]) <= 2e-4 * abs(J[best])
+    mg, vg = g.state()
+    np.testing.assert_allclose(mg, th[kb], atol=MEAN_ATOL)
+    np.testing.assert_array_equal(vg, f32(o.var))
+    g.close()
+
+
+def test_iterations_compose_on_gpu(cuda):
+    # one solve with I iterations equals I single-iteration solves, bit for bit
+    cfg = W.config("adaptive_elite_k8192_h25")
+    cfg.update(K=2048, seed=7)
+    prob = W.problem(cfg)
+    g5 = GpuRun(cfg, prob)
+    r5 = g5.solve()
+    m5, v5 = g5.state()
+    c1 = dict(cfg, iterations=1)
+    g1 = GpuRun(c1, prob)
+    for _ in range(5):
+        r1 = g1.solve()
+    m1, v1 = g1.state()
+    np.testing.assert_array_equal(m5, m1)
+    np.testing.assert_array_equal(v5, v1)
+    np.testing.assert_array_equal(r5["u0"], r1["u0"])
+    assert r5["iter"] == r1["iter"] == 4
+    g5.close()
+    g1.close()
+
+
+def test_warm_start_two_ticks(cuda):
+    # second tick shifted by one step from the first tick's solution
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg["seed"] = 3
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g.solve()
+    o.solve()
+    gait2 = dict(prob["gait"])
+    gait2["phase0"] = (gait2["phase0"] + 2000 * 20000) % W.PHASE_ONE
+    o.g = orc.make_gait(gait2)
+    J, q, th, margin, kap = None, None, None, None, None
+    m_shift, v_shift = orc.warm_shift(o.P, o.g, 1, o.mean, o.var)
+    o.mean, o.var = m_shift, v_shift
+    J, q, th, margin, kap = o.rollout()
+    g.solve(shift=1, gait=gait2)
+    Jg = g.read(S.BUF_COST)
+    check_costs(Jg, J, kap)
+    st, mo, _, _ = orc.mppi(J, th, cfg["lam"])
+    mg, vg = g.state()
+    tol = mppi_tolerance(J, th, kap, cfg["lam"], mo)
+    # the first tick's GPU/oracle means differ within their tolerance; that difference
+    # enters the second tick's sampling mean linearly
+    assert np.all(np.abs(mg - mo) <= tol + 2 * MEAN_ATOL)
+    np.testing.assert_allclose(vg, v_shift, rtol=1e-6)
+    g.close()
+
+
+def test_spline_full_size_sampled(cuda):
+    # the spline workload at full size (K=262144, H=100, 4 knots): sampled costs
+    cfg = W.config("spline_k262144_h100")
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    r = g.solve()
+    Jg, qg, eg = g.read(S.BUF_COST), g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
+    rng = np.random.default_rng(1)
+    ks = np.r_[rng.choice(cfg["K"], 150, replace=False), eg[:50]]
+    J = np.array([o.sample(int(k))[0] for k in ks])
+    kap = np.array([o.kappa(int(k)) for k in ks])
+    qo = np.array([orc.quantise_freq(o.mean[-1], np.sqrt(o.var[-1]), orc.freq_normal(cfg["seed"], 0, int(k), 0),
+                                     cfg["f_min"], cfg["f_max"]) for k in ks])
+    amb = check_frequencies(qg[ks], qo[:, 0].astype(np.uint32), qo[:, 1])
+    check_costs(Jg[ks], J, kap, skip=amb)
+    assert eg.size == cfg["elite_count"] and np.all(np.diff(eg) > 0)
+    # every elite's cost is at most every non-elite's (on the GPU's own costs)
+    mask = np.zeros(cfg["K"], bool)
+    mask[eg] = True
+    assert Jg[mask].max() <= Jg[~mask].min()
+    g.close()
+
+
+def test_spline_small_mppi_parity(cuda):
+    cfg = W.config("spline_k262144_h100")
+    cfg.update(K=3000, H=25, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=8)
+    _mppi_parity(cfg, W.problem(cfg), "spline-small")
+
+
+def test_spline_warm_shift(cuda):
+    cfg = W.config("spline_k262144_h100")
+    cfg.update(K=512, H=25, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=12)
+    prob = W.problem(cfg)
+    g = GpuRun(cfg, prob)
+    g.solve()
+    mg1, vg1 = g.state()
+    r = g.solve(shift=1)
+    # MPPI keeps the covariance, and a spline shift keeps the knot variances
+    mg2, vg2 = g.state()
+    np.testing.assert_allclose(vg2, vg1)
+    assert r["status"] == S.OK
+    g.close()
+
+
+# ------------------------------------------------------------------ boundary behaviour
+
+def test_host_memory_path_equals_device_path(cuda):
+    cfg = W.config("adaptive_elite_k8192_h25")
+    cfg.update(K=1024, iterations=2, seed=4)
+    prob = W.problem(cfg)
+    g = GpuRun(cfg, prob)
+    rd = g.solve()
+    md, vd = g.state()
+    c2 = S.Controller(cfg)
+    res = c2.solve_host(f32(prob["x0"]), f32(prob["xref"]), prob["gait"], f32(prob["f_ext"]), 0)
+    cuda.cuda.synchronize()
+    rh = S.parse_result(bytes(res))
+    np.testing.assert_array_equal(rd["u0"], rh["u0"])
+    assert rd["cost_min"] == rh["cost_min"]
+    np.testing.assert_array_equal(md, c2.read(S.BUF_MEAN).cpu().numpy())
+    np.testing.assert_array_equal(vd, c2.read(S.BUF_VAR).cpu().numpy())
+    g.close()
+    c2.close()
+
+
+def test_checkpoint_resume_bit_exact(cuda):
+    cfg = W.config("plain_mppi_k512_h12")
+    prob = W.problem(cfg)
+    g = GpuRun(cfg, prob)
+    g.solve()
+    blob = g.ctl.get_state()
+    r1 = g.solve(shift=1)
+    m1, _ = g.state()
+    g.ctl.set_state(blob)
+    r2 = g.solve(shift=1)
+    m2, _ = g.state()
+    np.testing.assert_array_equal(m1, m2)
+    np.testing.assert_array_equal(r1["u0"], r2["u0"])
+    fresh = S.Controller(cfg)
+    fresh.set_state(blob)
+    res = fresh.solve(g.x0, g.xref, prob["gait"], g.fext, 1)
+    cuda.cuda.synchronize()
+    np.testing.assert_array_equal(S.parse_result(res.cpu().numpy())["u0"], r1["u0"])
+    g.close()
+    fresh.close()
+
+
+def test_all_costs_nonfinite_reports_divergence(cuda):
+    cfg = W.config("plain_mppi_k512_h12")
+    prob = W.problem(cfg)
+    g = GpuRun(cfg, prob)
+    g.solve()
+    m0, v0 = g.state()
+    x0 = g.x0.clone()
+    x0[0] = float("nan")
+    r = g.solve(shift=0, x0=x0)
+    assert r["status"] == S.ERR_DIVERGED and r["n_finite"] == 0
+    m1, v1 = g.state()
+    np.testing.assert_array_equal(m0, m1)
+    np.testing.assert_array_equal(v0, v1)
+    cfg2 = dict(cfg, method="elite", elite_count=10)
+    g2 = GpuRun(cfg2, prob)
+    g2.solve()
+    m0, v0 = g2.state()
+    r = g2.solve(shift=0, x0=x0)
+    assert r["status"] == S.ERR_DIVERGED
+    m1, v1 = g2.state()
+    np.testing.assert_array_equal(m0, m1)
+    np.testing.assert_array_equal(v0, v1)
+    g.close()
+    g2.close()
+
+
+def test_host_input_validation(cuda):
+    cfg = W.config("plain_mppi_k512_h12")
+    prob = W.problem(cfg)
+    c = S.Controller(cfg)
+    x0 = f32(prob["x0"]).copy()
+    x0[3] = np.inf
+    with pytest.raises(S.SBSError) as e:
+        c.solve_host(x0, f32(prob["xref"]), prob["gait"], None, 0)
+    assert e.value.status == S.ERR_INVALID_ARG
+    bad = dict(prob["gait"], phase0=W.PHASE_ONE)
+    with pytest.raises(S.SBSError):
+        c.solve_host(f32(prob["x0"]), f32(prob["xref"]), bad, None, 0)
+    c.close()
+
+
+def test_fp32_peak_is_plausible(cuda):
+    f = S.fp32_peak()
+    assert 1e12 < f < 2e14
