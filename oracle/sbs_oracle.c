@@ -581,7 +581,7 @@ double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* 
 
 /* Conditioning estimate of sample k's cost (test infrastructure): the relative
  * change of J when the rollout is repeated with every force and state component
- * perturbed by a relative eps per step (two sign patterns, the larger change).
+ * perturbed by a relative eps per step (four sign patterns, the largest change).
  * A cost that moves by more than the parity tolerance under rounding-sized
  * perturbations cannot be reproduced to that tolerance by any single-precision
  * evaluation; such samples are ill-conditioned. */
@@ -599,7 +599,7 @@ double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* 
     uint32_t q;
     double J = rollout_core(&c, k, -1, th, &q, NULL, 0.0, 0);
     double worst = 0.0;
-    for (uint64_t key = 1; key <= 2; ++key) {
+    for (uint64_t key = 1; key <= 4; ++key) {
         double Jp = rollout_core(&c, k, (int64_t)q, th, NULL, NULL, eps, key * 1000003ull + k);
         double d;
         if (isinf(J) && isinf(Jp)) d = 0.0;

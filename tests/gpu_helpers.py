@@ -5,10 +5,10 @@ Tolerances (derived from the arithmetic):
   * integers (Philox words, quantised frequencies, contact flags): exact; a
     frequency whose FP64 value lies within 2e-3 mHz of a rounding boundary may
     round either way in single precision and is checked against both candidates.
-  * costs: relative error <= max(1e-4, 100 kappa) where kappa is the oracle's
-    conditioning estimate of that sample (relative cost change under per-step
-    rounding-sized perturbations); samples with kappa > 1e-4 are chaotic
-    (tumbling rollouts) and only reported.
+  * costs: relative error <= 1e-4 for samples whose conditioning estimate
+    kappa (the oracle's relative cost change under per-step rounding-sized
+    perturbations) is <= 1e-6, and <= max(1e-4, 100 kappa) up to kappa = 1e-5;
+    samples above that are chaotic (tumbling rollouts) and only reported.
   * MPPI mean: 1e-4 m|g| plus the first-order propagation of those cost
     tolerances through the weights: (1/lambda) sum_i w_i |theta_i - m| tol_i J_i.
   * elite set: identical except samples whose cost is within its tolerance band
@@ -26,7 +26,7 @@ MG = 21.0 * 9.81
 MEAN_ATOL = 1e-4 * MG
 Q_MARGIN = 2e-3
 KAPPA_STRICT = 1e-6
-KAPPA_GATED = 1e-4
+KAPPA_GATED = 1e-5
 
 
 def dev(a):
