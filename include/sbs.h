@@ -205,6 +205,35 @@ size_t sbs_state_size(const sbs_handle* h);
 int sbs_get_state(const sbs_handle* h, void* buf, size_t bytes, void* stream);
 int sbs_set_state(sbs_handle* h, const void* buf, size_t bytes, void* stream);
 
+/* ---------------------------------------------------------------- allocation-free solve
+ * The paper has no counterpart to this entry point; it serves callers that may
+ * not allocate device memory when they solve (a real-time control thread that
+ * must not block on an allocator, a host application or plug-in that owns all
+ * device memory).  It runs one MPPI iteration of the per-step policy
+ * (method SBS_MPPI, P = 0, iterations = 1) with all of its per-solve scratch in
+ * one file-scope device array of SBS_STATIC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc or
+ * cudaFree and creates no handle.
+ *   cfg        validated like sbs_create.
+ *   prob       device pointers only (host_memory = 0); shift is the warm-start
+ *              shift applied to state_in.
+ *   state_in   device [mean (D) | variance (D)] of the distribution to sample;
+ *              D = 12 H (+1 when adaptive).  Use sbs_reset / sbs_read of a
+ *              handle, or your own initial values, for the first call.
+ *   state_out  device [mean | variance] written with the updated distribution;
+ *              must not alias state_in.
+ *   iter       the Philox iteration counter of this solve.
+ *   result     device sbs_result.
+ * Returns SBS_ERR_BUDGET when the solve's scratch exceeds the array.  The first
+ * call on a device looks the array's device address up (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the previous call's contents (the completion counters are
+ * cleared by every call): calls whose work overlaps on the GPU - on different
+ * streams, or from different threads - race and corrupt each other. */
+#define SBS_STATIC_SCRATCH_BYTES (64u << 20)
+int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* prob, const float* state_in,
+                          float* state_out, uint64_t iter, sbs_result* result, void* stream);
+
 /* ---------------------------------------------------------------- batching
  * Many controllers of uneven K and H solved in one persistent launch that pulls
  * (controller, tile) items from a device work queue; the tick is captured in a

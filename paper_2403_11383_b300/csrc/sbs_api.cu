@@ -49,7 +49,11 @@ bool finite_all(const float* p, int n)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int validate(const sbs_config* c)
+}  // namespace
+
+namespace sbs {
+
+int validate_config(const sbs_config* c)
 {
     if (!c) return SBS_ERR_INVALID_ARG;
     if (c->K < 1 || c->K > SBS_MAX_K) return SBS_ERR_INVALID_ARG;
@@ -92,6 +96,58 @@ int validate_gait(const sbs_gait* g)
     if (g->duty > kPhaseOne || g->phase0 >= kPhaseOne) return SBS_ERR_INVALID_ARG;
     return SBS_OK;
 }
+
+// Sizes and constants of a validated configuration (device pointers left null).
+void fill_params(const sbs_config* cfg, InstParams* out)
+{
+    InstParams& P = *out;
+    std::memset(&P, 0, sizeof(P));
+    P.K = cfg->K;
+    P.H = cfg->H;
+    P.P = cfg->P;
+    P.nt = cfg->P > 0 ? cfg->P : cfg->H;
+    P.nf = 12 * P.nt;
+    P.adaptive = cfg->adaptive ? 1 : 0;
+    P.D = P.nf + P.adaptive;
+    P.method = cfg->method;
+    P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
+    P.T = cfg->tile ? cfg->tile : 128;
+    P.ntiles = (cfg->K + P.T - 1) / P.T;
+    P.ngroups = (P.ntiles + kGroup - 1) / kGroup;
+    P.compare_mppi = cfg->compare_mppi ? 1 : 0;
+    P.part_stride = kPartHeader + P.nf;
+    P.dt_us = cfg->dt_us;
+    P.q_init = cfg->q_init;
+    P.seed = cfg->seed;
+    P.ctrl = cfg->controller_id;
+    P.dt = (float)(cfg->dt_us * 1e-6);
+    P.lambda = cfg->lambda;
+    P.inv_lambda = 1.0f / cfg->lambda;
+    P.inv_mass = 1.0f / cfg->model.mass;
+    P.weight_z = cfg->model.mass * -cfg->model.gravity[2];
+    for (int a = 0; a < 3; ++a) {
+        P.inertia[a] = cfg->model.inertia[a];
+        P.inv_inertia[a] = 1.0f / cfg->model.inertia[a];
+        P.gravity[a] = cfg->model.gravity[a];
+        P.R[a] = cfg->cost.R[a];
+    }
+    std::memcpy(P.foot, &cfg->model.foot[0][0], sizeof(P.foot));
+    std::memcpy(P.Q, cfg->cost.Q, sizeof(P.Q));
+    P.w_fc = cfg->cost.w_fc;
+    P.mu = cfg->cost.mu;
+    P.rho = cfg->cost.rho;
+    P.f_nominal = cfg->cost.f_nominal;
+    P.f_min = cfg->f_min;
+    P.f_max = cfg->f_max;
+    P.var_init = cfg->sigma_init * cfg->sigma_init;
+    P.var_min = cfg->sigma_min * cfg->sigma_min;
+    P.var_f_init = cfg->sigma_f_init * cfg->sigma_f_init;
+    P.var_f_min = cfg->sigma_f_min * cfg->sigma_f_min;
+}
+
+}  // namespace sbs
+
+namespace {
 
 // ---------------------------------------------------------------- natural cubic spline (Sec. IV-B)
 // Knots at t_p = p T / (P - 1), T = (H - 1) dt.  The second derivatives M solve
@@ -212,7 +268,7 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
 {
     if (!out) return SBS_ERR_INVALID_ARG;
     *out = nullptr;
-    int st = validate(cfg);
+    int st = validate_config(cfg);
     if (st) return st;
     if (alloc && (!alloc->alloc || !alloc->free)) return SBS_ERR_INVALID_ARG;
     sbs_handle* h = new (std::nothrow) sbs_handle();
@@ -223,48 +279,7 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     cudaGetDevice(&h->device);
 
     InstParams& P = h->hP;
-    std::memset(&P, 0, sizeof(P));
-    P.K = cfg->K;
-    P.H = cfg->H;
-    P.P = cfg->P;
-    P.nt = cfg->P > 0 ? cfg->P : cfg->H;
-    P.nf = 12 * P.nt;
-    P.adaptive = cfg->adaptive ? 1 : 0;
-    P.D = P.nf + P.adaptive;
-    P.method = cfg->method;
-    P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
-    P.T = cfg->tile ? cfg->tile : 128;
-    P.ntiles = (cfg->K + P.T - 1) / P.T;
-    P.ngroups = (P.ntiles + kGroup - 1) / kGroup;
-    P.compare_mppi = cfg->compare_mppi ? 1 : 0;
-    P.part_stride = kPartHeader + P.nf;
-    P.dt_us = cfg->dt_us;
-    P.q_init = cfg->q_init;
-    P.seed = cfg->seed;
-    P.ctrl = cfg->controller_id;
-    P.dt = (float)(cfg->dt_us * 1e-6);
-    P.lambda = cfg->lambda;
-    P.inv_lambda = 1.0f / cfg->lambda;
-    P.inv_mass = 1.0f / cfg->model.mass;
-    P.weight_z = cfg->model.mass * -cfg->model.gravity[2];
-    for (int a = 0; a < 3; ++a) {
-        P.inertia[a] = cfg->model.inertia[a];
-        P.inv_inertia[a] = 1.0f / cfg->model.inertia[a];
-        P.gravity[a] = cfg->model.gravity[a];
-        P.R[a] = cfg->cost.R[a];
-    }
-    std::memcpy(P.foot, &cfg->model.foot[0][0], sizeof(P.foot));
-    std::memcpy(P.Q, cfg->cost.Q, sizeof(P.Q));
-    P.w_fc = cfg->cost.w_fc;
-    P.mu = cfg->cost.mu;
-    P.rho = cfg->cost.rho;
-    P.f_nominal = cfg->cost.f_nominal;
-    P.f_min = cfg->f_min;
-    P.f_max = cfg->f_max;
-    P.var_init = cfg->sigma_init * cfg->sigma_init;
-    P.var_min = cfg->sigma_min * cfg->sigma_min;
-    P.var_f_init = cfg->sigma_f_init * cfg->sigma_f_init;
-    P.var_f_min = cfg->sigma_f_min * cfg->sigma_f_min;
+    fill_params(cfg, &P);
 
     // device layout (256-byte aligned pieces)
     h->wsl = ws_layout(P.K, P.H, P.P, P.T, P.Ke);

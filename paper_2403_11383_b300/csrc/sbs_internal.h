@@ -132,6 +132,11 @@ inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
     return w;
 }
 
+// Host-side configuration helpers (defined in sbs_api.cu).
+int validate_config(const sbs_config* c);
+int validate_gait(const sbs_gait* g);
+void fill_params(const sbs_config* cfg, InstParams* out);
+
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);

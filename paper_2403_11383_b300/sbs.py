@@ -92,6 +92,8 @@ ABI = {
     "sbs_batch_destroy": (None, [C.c_void_p]),
     "sbs_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_status_str": (C.c_char_p, [C.c_int]),
+    "sbs_solve_mppi_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
+                                        C.c_void_p]),
     "sbs_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_batch_stage_ms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -348,6 +350,25 @@ class Batch:
         ps = (Problem * n)(*problems)
         check(lib().sbs_batch_solve(self._b, n, hs, ps, C.c_void_p(results.data_ptr()), _stream_ptr(stream)),
               "sbs_batch_solve")
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def solve_mppi_static(cfg: dict, x0, xref, gait, f_ext, shift, state_in, state_out, it, result, stream=None,
+                      tile: int = 0):
+    """sbs_solve_mppi_static: one MPPI iteration with the library's static scratch
+    (no device allocation).  All tensors are CUDA tensors; state_* hold
+    [mean | variance]; result is a uint8 tensor of RESULT_BYTES."""
+    c = make_config(cfg, tile)
+    p = Problem()
+    p.x0, p.xref = x0.data_ptr(), xref.data_ptr()
+    p.f_ext = None if f_ext is None else f_ext.data_ptr()
+    p.gait = make_gait(gait)
+    p.shift, p.host_memory = shift, 0
+    check(lib().sbs_solve_mppi_static(C.byref(c), C.byref(p), C.c_void_p(state_in.data_ptr()),
+                                      C.c_void_p(state_out.data_ptr()), it, C.c_void_p(result.data_ptr()),
+                                      _stream_ptr(stream)), "sbs_solve_mppi_static")
 
 
 def philox(ctr, key, stream=None):
