@@ -34,14 +34,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Box-Muller on two words: the top 24 bits give exact uniforms u1 in (0, 1]
 // and u2 in [0, 1).  The radius uses the accurate logarithm (its argument is
-// often within a few ulp of 1); the angle uses the hardware sine/cosine, whose
-// absolute error (about 4e-7 on [0, 2 pi)) moves a normal by at most 3e-6.
+// often within a few ulp of 1) and x * rsqrt(x) for the square root; the angle
+// uses the hardware sine/cosine, whose absolute error (about 4e-7 on
+// [0, 2 pi)) moves a normal by at most 3e-6.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {
     const float two_m24 = 5.9604644775390625e-8f;
     const float u1 = __uint2float_rn((a >> 8) + 1u) * two_m24;
     const float u2 = __uint2float_rn(b >> 8) * two_m24;
-    const float r = sqrtf(-2.0f * logf(u1));
+    const float r2 = -2.0f * logf(u1);
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     float s, c;
     __sincosf(6.28318530717958648f * u2, &s, &c);
     return make_float2(r * c, r * s);
@@ -130,7 +132,9 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
         r = fmaf(P.R[1] * gy, gy, r);
         r = fmaf(P.R[2] * gz, gz, r);
         // friction cone on stance legs; a swing leg's zero force adds nothing
-        const float slip = sqrtf(fmaf(gx, gx, gy * gy)) - P.mu * gz;
+        // (|G_xy| as x * rsqrt(x), exact zero for a zero force)
+        const float t2 = fmaf(gx, gx, gy * gy);
+        const float slip = (t2 > 0.0f ? t2 * rsqrtf(t2) : 0.0f) - P.mu * gz;
         float pen = slip > 0.0f ? slip * slip : 0.0f;
         pen += gz < 0.0f ? gz * gz : 0.0f;
         r = fmaf(P.w_fc, pen, r);
