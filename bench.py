@@ -219,9 +219,12 @@ def main():
     def tick(first=False):
         batch.solve(ctls, probs0 if first else probs1, results)
 
-    # warm-up (the first tick initialises every controller)
+    # warm-up (the first tick initialises every controller), then the launch-mode
+    # autotuner measures both modes on this mix and keeps the faster
     for w in range(max(args.warmup, 3)):
         tick(first=(w == 0))
+    tune_ms = batch.autotune(ctls, probs1, results, ticks=5)
+    mode = "grid" if batch.mode() == S.BATCH_GRID else "persistent"
     torch.cuda.synchronize()
 
     # ---- timed region: K ticks back to back on the stream
@@ -329,14 +332,16 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances": n, "sample_steps_per_tick": ss_tick,
-                       "tile": 128, "graph": True, "l2": "per-tick working set above L2 (sampled deviations "
+                       "tile": 128, "graph": True, "launch_mode": mode,
+                       "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
+                       "l2": "per-tick working set above L2 (sampled deviations "
                        f"{arena / 1e9:.2f} GB)", "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
             "latency_ms": {"p50": p50, "p99": p99, "kind": "device time of one 256-controller tick"},
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
                       "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
-            "roofline": {"kernel": "k_batch_rollout<0>", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": "k_grid_rollout<0>" if mode == "grid" else "k_batch_rollout<0>", "bound": "alu", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,

@@ -255,6 +255,22 @@ void sbs_batch_destroy(sbs_batch* b);
 int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                     sbs_result* results, void* stream);
 
+/* Launch mode of a batch.  SBS_BATCH_GRID (default): one block per item, the
+ * hardware block scheduler dispatching items in order, heaviest controllers
+ * first.  SBS_BATCH_PERSISTENT: as many blocks as fit on the GPU pull items from
+ * device queues (atomic heads).  Both give identical results. */
+#define SBS_BATCH_GRID 1
+#define SBS_BATCH_PERSISTENT 0
+int sbs_batch_set_mode(sbs_batch* b, int mode);
+int sbs_batch_get_mode(const sbs_batch* b);
+
+/* Autotuner: runs `ticks` profiled ticks in each launch mode on these
+ * controllers and problems (real solves: they advance the controllers), keeps
+ * the mode with the shorter mean tick and reports the mean tick times in
+ * ms_out[0] (grid) and ms_out[1] (persistent). */
+int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                       sbs_result* results, int ticks, float ms_out[2], void* stream);
+
 /* Tracing: with profiling on, a batch launches its three stages (rollout,
  * selection, refit) as separate kernels bracketed by CUDA events instead of
  * replaying its graph; sbs_batch_stage_ms waits for the last tick and gives the

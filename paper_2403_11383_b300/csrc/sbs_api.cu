@@ -564,9 +564,10 @@ struct sbs_batch_slot {
     bool used;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    cudaGraphNode_t copy_node;
+    cudaGraphNode_t copy_node, kernel_node[3];
+    cudaKernelNodeParams kparams[3];
     size_t key_smem, key_sel;
-    int key_T, key_P;
+    int key_T, key_P, key_mode;
     int grids[3];
 };
 
@@ -580,6 +581,7 @@ struct sbs_batch {
     sbs_batch_slot slot[2];
     int next;
     bool use_graph;
+    int mode;
     bool profiling;
     cudaEvent_t ev[4];
     bool ev_valid;
@@ -598,10 +600,12 @@ extern "C" int sbs_batch_create(int max_instances, size_t workspace_bytes, const
     b->has_alloc = alloc != nullptr;
     if (alloc) b->alloc = *alloc;
     b->bytes = 16 + (size_t)max_instances * sizeof(InstRec);
+    b->mode = SBS_BATCH_GRID;
     const char* ng = std::getenv("SBS_NO_GRAPH");
     b->use_graph = !(ng && ng[0] == '1');
     for (int i = 0; i < 2; ++i) {
         sbs_batch_slot& sl = b->slot[i];
+        sl.key_mode = -1;
         const size_t rec_bytes = align_up(b->bytes, 256);
         const size_t cnt_bytes = align_up((size_t)b->counter_words * 4, 256);
         const size_t total = rec_bytes + 256 + cnt_bytes + b->arena_bytes;
@@ -623,6 +627,15 @@ extern "C" int sbs_batch_create(int max_instances, size_t workspace_bytes, const
     *out = b;
     return SBS_OK;
 }
+
+extern "C" int sbs_batch_set_mode(sbs_batch* b, int mode)
+{
+    if (!b || (mode != SBS_BATCH_GRID && mode != SBS_BATCH_PERSISTENT)) return SBS_ERR_INVALID_ARG;
+    b->mode = mode;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_get_mode(const sbs_batch* b) { return b ? b->mode : SBS_ERR_INVALID_ARG; }
 
 extern "C" int sbs_batch_set_profiling(sbs_batch* b, int on)
 {
@@ -662,7 +675,8 @@ extern "C" void sbs_batch_destroy(sbs_batch* b)
     delete b;
 }
 
-static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, size_t sel_smem, int T)
+// The tick graph of a slot: records copy -> queue-head reset -> rollout -> select -> refit.
+static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t smem, size_t sel_smem, int T)
 {
     if (sl.exec) {
         cudaGraphExecDestroy(sl.exec);
@@ -672,11 +686,9 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, siz
         cudaGraphDestroy(sl.graph);
         sl.graph = nullptr;
     }
-    int st = batch_grid(P, smem, sel_smem, T, sl.grids);
-    if (st) return st;
     cudaGraph_t g;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return SBS_ERR_CUDA;
-    cudaGraphNode_t n_cp, n_ms, n_k1, n_k2, n_k3;
+    cudaGraphNode_t n_cp, n_ms;
     bool ok = cudaGraphAddMemcpyNode1D(&n_cp, g, nullptr, 0, sl.dev, sl.pin, b->bytes, cudaMemcpyHostToDevice) ==
               cudaSuccess;
     cudaMemsetParams mp;
@@ -691,26 +703,21 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, siz
     const int* counts = (const int*)sl.dev;
     int* heads = sl.heads;
     void* args[] = {(void*)&recs, (void*)&counts, (void*)&heads};
-    cudaKernelNodeParams k1;
-    std::memset(&k1, 0, sizeof(k1));
-    k1.func = (void*)batch_rollout_fn(P);
-    k1.gridDim = dim3(sl.grids[0]);
-    k1.blockDim = dim3(T);
-    k1.sharedMemBytes = (unsigned)smem;
-    k1.kernelParams = args;
-    ok = ok && cudaGraphAddKernelNode(&n_k1, g, &n_ms, 1, &k1) == cudaSuccess;
-    cudaKernelNodeParams k2 = k1;
-    k2.func = (void*)batch_select_fn();
-    k2.gridDim = dim3(sl.grids[1]);
-    k2.blockDim = dim3(kSelectThreads);
-    k2.sharedMemBytes = (unsigned)sel_smem;
-    ok = ok && cudaGraphAddKernelNode(&n_k2, g, &n_k1, 1, &k2) == cudaSuccess;
-    cudaKernelNodeParams k3 = k1;
-    k3.func = (void*)batch_refit_fn();
-    k3.gridDim = dim3(sl.grids[2]);
-    k3.blockDim = dim3(kRefitThreads);
-    k3.sharedMemBytes = 0;
-    ok = ok && cudaGraphAddKernelNode(&n_k3, g, &n_k2, 1, &k3) == cudaSuccess;
+    const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode)};
+    const int threads[3] = {T, kSelectThreads, kRefitThreads};
+    const size_t shm[3] = {smem, sel_smem, 0};
+    cudaGraphNode_t prev = n_ms;
+    for (int k = 0; k < 3 && ok; ++k) {
+        cudaKernelNodeParams& kp = sl.kparams[k];
+        std::memset(&kp, 0, sizeof(kp));
+        kp.func = (void*)fns[k];
+        kp.gridDim = dim3(sl.grids[k]);
+        kp.blockDim = dim3(threads[k]);
+        kp.sharedMemBytes = (unsigned)shm[k];
+        kp.kernelParams = args;
+        ok = cudaGraphAddKernelNode(&sl.kernel_node[k], g, &prev, 1, &kp) == cudaSuccess;
+        prev = sl.kernel_node[k];
+    }
     cudaGraphExec_t ex = nullptr;
     ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
     if (!ok) {
@@ -718,9 +725,28 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, size_t smem, siz
         cudaGraphDestroy(g);
         return SBS_ERR_CUDA;
     }
+    for (int k = 0; k < 3; ++k) sl.kparams[k].kernelParams = nullptr;  // args above go out of scope
     sl.graph = g;
     sl.exec = ex;
     sl.copy_node = n_cp;
+    return SBS_OK;
+}
+
+// Point a graph's kernel nodes at new grid sizes (grid mode).
+static int update_graph_grids(sbs_batch_slot& sl, const int grids[3])
+{
+    const InstRec* recs = (const InstRec*)(sl.dev + 16);
+    const int* counts = (const int*)sl.dev;
+    int* heads = sl.heads;
+    void* args[] = {(void*)&recs, (void*)&counts, (void*)&heads};
+    for (int k = 0; k < 3; ++k) {
+        if (sl.kparams[k].gridDim.x == (unsigned)grids[k]) continue;
+        cudaKernelNodeParams kp = sl.kparams[k];
+        kp.gridDim = dim3(grids[k]);
+        kp.kernelParams = args;
+        if (cudaGraphExecKernelNodeSetParams(sl.exec, sl.kernel_node[k], &kp) != cudaSuccess) return SBS_ERR_CUDA;
+        sl.kparams[k].gridDim = kp.gridDim;
+    }
     return SBS_OK;
 }
 
@@ -809,11 +835,19 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     counts[3] = refit_begin;
     if (sel_smem == 0) sel_smem = 256;
     const size_t used = 16 + (size_t)n * sizeof(InstRec);
-    int st = SBS_OK;
-    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_P != Pk;
+    const int mode = b->mode;
+    int grids[3];
+    int st = batch_grid(Pk, mode, smem, sel_smem, T, counts, grids);
+    if (st) return st;
+    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_P != Pk ||
+                       sl.key_mode != mode;
     if (b->use_graph && !b->profiling) {
         if (!sl.exec || rekey) {
-            st = build_graph(b, sl, Pk, smem, sel_smem, T);
+            std::memcpy(sl.grids, grids, sizeof(grids));
+            st = build_graph(b, sl, Pk, mode, smem, sel_smem, T);
+            if (st) return st;
+        } else if (mode == SBS_BATCH_GRID) {
+            st = update_graph_grids(sl, grids);
             if (st) return st;
         }
         if (cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.pin, used,
@@ -821,18 +855,14 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
             return SBS_ERR_CUDA;
         if (cudaGraphLaunch(sl.exec, s) != cudaSuccess) return SBS_ERR_CUDA;
     } else {
-        if (rekey || !sl.grids[0]) {
-            st = batch_grid(Pk, smem, sel_smem, T, sl.grids);
-            if (st) return st;
-            if (sl.exec) {  // the graph's launch shapes no longer match
-                cudaGraphExecDestroy(sl.exec);
-                sl.exec = nullptr;
-            }
+        if (sl.exec && rekey) {  // the graph's launch shapes no longer match
+            cudaGraphExecDestroy(sl.exec);
+            sl.exec = nullptr;
         }
         if (cudaMemcpyAsync(sl.dev, sl.pin, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return SBS_ERR_CUDA;
         if (cudaMemsetAsync(sl.heads, 0, 16, s) != cudaSuccess) return SBS_ERR_CUDA;
-        st = launch_batch(Pk, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, sel_smem, T,
-                          sl.grids, stream, b->profiling ? (void* const*)b->ev : nullptr);
+        st = launch_batch(Pk, mode, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, sel_smem, T,
+                          grids, stream, b->profiling ? (void* const*)b->ev : nullptr);
         if (st) return st;
         b->ev_valid = b->profiling;
     }
@@ -840,6 +870,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     sl.key_sel = sel_smem;
     sl.key_T = T;
     sl.key_P = Pk;
+    sl.key_mode = mode;
     if (cudaEventRecord(sl.done, s) != cudaSuccess) return SBS_ERR_CUDA;
     sl.used = true;
     for (int i = 0; i < n; ++i) {
@@ -848,6 +879,32 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         h->cur ^= 1;
         h->iter += 1;
     }
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                                  sbs_result* results, int ticks, float ms_out[2], void* stream)
+{
+    if (!b || ticks < 1 || !ms_out) return SBS_ERR_INVALID_ARG;
+    const bool prof = b->profiling;
+    int st = sbs_batch_set_profiling(b, 1);
+    if (st) return st;
+    const int modes[2] = {SBS_BATCH_GRID, SBS_BATCH_PERSISTENT};
+    for (int m = 0; m < 2; ++m) {
+        b->mode = modes[m];
+        double tot = 0.0;
+        for (int k = 0; k <= ticks && st == SBS_OK; ++k) {  // the first tick of a mode is a warm-up
+            st = sbs_batch_solve(b, n, handles, probs, results, stream);
+            float ms[3];
+            if (st == SBS_OK) st = sbs_batch_stage_ms(b, ms);
+            if (st == SBS_OK && k > 0) tot += (double)ms[0] + ms[1] + ms[2];
+        }
+        if (st) break;
+        ms_out[m] = (float)(tot / ticks);
+    }
+    sbs_batch_set_profiling(b, prof ? 1 : 0);
+    if (st) return st;
+    b->mode = ms_out[0] <= ms_out[1] ? SBS_BATCH_GRID : SBS_BATCH_PERSISTENT;
     return SBS_OK;
 }
 

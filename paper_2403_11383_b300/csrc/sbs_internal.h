@@ -142,12 +142,12 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
-int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem, size_t sel_smem,
-                 int T, const int grids[3], void* stream, void* const* events);
-int batch_grid(int P, size_t smem, size_t sel_smem, int T, int grids[3]);
-const void* batch_rollout_fn(int P);
-const void* batch_select_fn();
-const void* batch_refit_fn();
+int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem,
+                 size_t sel_smem, int T, const int grids[3], void* stream, void* const* events);
+int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int counts[4], int grids[3]);
+const void* batch_rollout_fn(int P, int mode);
+const void* batch_select_fn(int mode);
+const void* batch_refit_fn(int mode);
 int launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream);
 int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
 int launch_fma_peak(float* out, int iters, int blocks, int threads, void* stream);

@@ -877,6 +877,50 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* _
     }
 }
 
+// One block per item: the hardware block scheduler is the queue (items are
+// dispatched in index order, heavy controllers first).  Unused blocks exit.
+template <int NP>
+__global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __restrict__ recs,
+                                                               const int* __restrict__ counts)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    const int it = blockIdx.x;
+    if (it >= counts[1]) return;
+    const int i = find_rec(recs, counts[0], it, 0);
+    load_params(recs[i].dP, sh);
+    load_tick(&recs[i].t, sh);
+    __syncthreads();
+    rollout_tile<NP>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+}
+
+__global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* __restrict__ recs,
+                                                               const int* __restrict__ counts)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    const int it = blockIdx.x;
+    if (it >= counts[2]) return;
+    const int i = find_rec(recs, counts[0], it, 1);
+    load_params(recs[i].dP, sh);
+    load_tick(&recs[i].t, sh);
+    __syncthreads();
+    select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
+}
+
+__global__ void __launch_bounds__(kRefitThreads) k_grid_refit(const InstRec* __restrict__ recs,
+                                                             const int* __restrict__ counts)
+{
+    __shared__ BlockShared sh;
+    const int it = blockIdx.x;
+    if (it >= counts[3]) return;
+    const int i = find_rec(recs, counts[0], it, 2);
+    load_params(recs[i].dP, sh);
+    load_tick(&recs[i].t, sh);
+    __syncthreads();
+    refit_block(sh, it - recs[i].refit_begin);
+}
+
 __global__ void __launch_bounds__(kSelectThreads) k_batch_select(const InstRec* __restrict__ recs,
                                                                 const int* __restrict__ counts, int* heads)
 {
@@ -981,9 +1025,9 @@ static const void* rollout_fn()
 }
 
 template <int NP>
-static const void* batch_fn()
+static const void* batch_fn(int mode)
 {
-    return (const void*)k_batch_rollout<NP>;
+    return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout<NP> : (const void*)k_batch_rollout<NP>;
 }
 
 static const void* rollout_kernel(int P)
@@ -999,21 +1043,28 @@ static const void* rollout_kernel(int P)
     }
 }
 
-const void* batch_rollout_fn(int P)
+const void* batch_rollout_fn(int P, int mode)
 {
     switch (P) {
-        case 0: return batch_fn<0>();
-        case 2: return batch_fn<2>();
-        case 3: return batch_fn<3>();
-        case 4: return batch_fn<4>();
-        case 6: return batch_fn<6>();
-        case 8: return batch_fn<8>();
+        case 0: return batch_fn<0>(mode);
+        case 2: return batch_fn<2>(mode);
+        case 3: return batch_fn<3>(mode);
+        case 4: return batch_fn<4>(mode);
+        case 6: return batch_fn<6>(mode);
+        case 8: return batch_fn<8>(mode);
         default: return nullptr;
     }
 }
 
-const void* batch_select_fn() { return (const void*)k_batch_select; }
-const void* batch_refit_fn() { return (const void*)k_batch_refit; }
+const void* batch_select_fn(int mode)
+{
+    return mode == SBS_BATCH_GRID ? (const void*)k_grid_select : (const void*)k_batch_select;
+}
+
+const void* batch_refit_fn(int mode)
+{
+    return mode == SBS_BATCH_GRID ? (const void*)k_grid_refit : (const void*)k_batch_refit;
+}
 
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
@@ -1051,17 +1102,25 @@ int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, 
     return status_of(cudaGetLastError());
 }
 
-int batch_grid(int P, size_t smem, size_t sel_smem, int T, int grids[3])
+// Grid sizes of the three stages.  Persistent mode: as many blocks as fit on the
+// GPU at once.  Grid mode: one block per item (at least one).
+int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int counts[4], int grids[3])
 {
-    int dev, sms, b1 = 0, b2 = 0, b3 = 0;
-    const void* fn = batch_rollout_fn(P);
+    const void* fn = batch_rollout_fn(P, mode);
     if (!fn) return SBS_ERR_INVALID_ARG;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SBS_ERR_CUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SBS_ERR_CUDA;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;
-    st = ensure_smem_attr((const void*)k_batch_select, sel_smem);
+    st = ensure_smem_attr(batch_select_fn(mode), sel_smem);
     if (st) return st;
+    if (mode == SBS_BATCH_GRID) {
+        grids[0] = counts[1] > 0 ? counts[1] : 1;
+        grids[1] = counts[2] > 0 ? counts[2] : 1;
+        grids[2] = counts[3] > 0 ? counts[3] : 1;
+        return SBS_OK;
+    }
+    int dev, sms, b1 = 0, b2 = 0, b3 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SBS_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SBS_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, T, smem) != cudaSuccess) return SBS_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_batch_select, kSelectThreads, sel_smem) != cudaSuccess)
         return SBS_ERR_CUDA;
@@ -1075,25 +1134,24 @@ int batch_grid(int P, size_t smem, size_t sel_smem, int T, int grids[3])
 }
 
 // events: null, or four CUDA events recorded before and after each stage.
-int launch_batch(int P, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem, size_t sel_smem,
-                 int T, const int grids[3], void* stream, void* const* events)
+int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem,
+                 size_t sel_smem, int T, const int grids[3], void* stream, void* const* events)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    const void* fn = batch_rollout_fn(P);
-    if (!fn) return SBS_ERR_INVALID_ARG;
+    const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode)};
+    if (!fns[0]) return SBS_ERR_INVALID_ARG;
+    const dim3 blocks[3] = {dim3(T), dim3(kSelectThreads), dim3(kRefitThreads)};
+    const size_t shm[3] = {smem, sel_smem, 0};
     const InstRec* r = dRecs;
     const int* c = dCounts;
     int* hd = dHeads;
     void* args[] = {(void*)&r, (void*)&c, (void*)&hd};
-    if (events) cudaEventRecord((cudaEvent_t)events[0], s);
-    if (cudaLaunchKernel(fn, dim3(grids[0]), dim3(T), args, smem, s) != cudaSuccess) return SBS_ERR_CUDA;
-    if (events) cudaEventRecord((cudaEvent_t)events[1], s);
-    k_batch_select<<<grids[1], kSelectThreads, sel_smem, s>>>(dRecs, dCounts, dHeads);
-    if (cudaGetLastError() != cudaSuccess) return SBS_ERR_CUDA;
-    if (events) cudaEventRecord((cudaEvent_t)events[2], s);
-    k_batch_refit<<<grids[2], kRefitThreads, 0, s>>>(dRecs, dCounts, dHeads);
+    for (int k = 0; k < 3; ++k) {
+        if (events) cudaEventRecord((cudaEvent_t)events[k], s);
+        if (cudaLaunchKernel(fns[k], dim3(grids[k]), blocks[k], args, shm[k], s) != cudaSuccess) return SBS_ERR_CUDA;
+    }
     if (events) cudaEventRecord((cudaEvent_t)events[3], s);
-    return status_of(cudaGetLastError());
+    return SBS_OK;
 }
 
 int launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream)

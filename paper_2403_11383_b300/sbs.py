@@ -20,6 +20,7 @@ ERR_INVALID_ARG, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_DIVERGED = -1, 
 MPPI, ELITE, NAIVE = 0, 1, 2
 BUF_MEAN, BUF_VAR, BUF_COST, BUF_FREQ, BUF_ELITE, BUF_MPPI_MEAN = 0, 1, 2, 3, 4, 5
 MAX_H, MAX_K, MAX_TILE = 128, 1 << 24, 256
+BATCH_PERSISTENT, BATCH_GRID = 0, 1
 
 
 class Model(C.Structure):
@@ -95,6 +96,10 @@ ABI = {
     "sbs_solve_mppi_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                         C.c_void_p]),
     "sbs_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_batch_get_mode": (C.c_int, [C.c_void_p]),
+    "sbs_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                     C.c_void_p]),
     "sbs_batch_stage_ms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -332,6 +337,23 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_mode(self, mode: int):
+        check(lib().sbs_batch_set_mode(self._b, mode), "sbs_batch_set_mode")
+
+    def mode(self) -> int:
+        return lib().sbs_batch_get_mode(self._b)
+
+    def autotune(self, controllers, problems, results, ticks=5, stream=None):
+        """Measure both launch modes on these controllers (real solves) and keep
+        the faster; returns (grid_ms, persistent_ms) per tick."""
+        n = len(controllers)
+        hs = (C.c_void_p * n)(*[c.handle.value for c in controllers])
+        ps = (Problem * n)(*problems)
+        ms = (C.c_float * 2)()
+        check(lib().sbs_batch_autotune(self._b, n, hs, ps, C.c_void_p(results.data_ptr()), ticks, ms,
+                                       _stream_ptr(stream)), "sbs_batch_autotune")
+        return ms[0], ms[1]
 
     def set_profiling(self, on: bool):
         check(lib().sbs_batch_set_profiling(self._b, 1 if on else 0), "sbs_batch_set_profiling")

@@ -1,0 +1,168 @@
+"""Batched ticks: every controller's result in a mix of uneven controllers
+equals its own plain sbs_solve (same tile size), in both launch modes, over
+warm-started ticks; budget admission and the launch-mode autotuner."""
+import numpy as np
+import pytest
+
+from paper_2403_11383_b300 import sbs as S
+from paper_2403_11383_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    base = W.config("plain_mppi_k512_h12")
+    specs = [
+        dict(K=1000, H=7, gait="trot", method="mppi"),
+        dict(K=4096, H=25, gait="pace", method="elite", elite_count=205),
+        dict(K=300, H=12, gait="crawl", method="naive"),
+        dict(K=2048, H=10, gait="trot", method="mppi", adaptive=True),
+        dict(K=777, H=50, gait="pace", method="elite", elite_count=39, adaptive=True),
+        dict(K=16384, H=12, gait="trot", method="mppi"),
+        dict(K=129, H=3, gait="crawl", method="elite", elite_count=7),
+        dict(K=5000, H=33, gait="trot", method="mppi", adaptive=True, compare_mppi=True),
+    ]
+    out = []
+    for i, sp in enumerate(specs):
+        c = dict(base)
+        c.update(sp)
+        c.update(seed=100 + i, ctrl=i)
+        out.append((c, W.problem(c)))
+    return out
+
+
+def _tensors(prob):
+    import torch
+    d = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+    return d(prob["x0"]), d(prob["xref"]), d(prob["f_ext"])
+
+
+def _gait(prob, tick, cfg):
+    g = dict(prob["gait"])
+    g["phase0"] = (g["phase0"] + tick * cfg["q_init"] * cfg["dt_us"]) % W.PHASE_ONE
+    return g
+
+
+def _state(ctl):
+    return ctl.read(S.BUF_MEAN).cpu().numpy(), ctl.read(S.BUF_VAR).cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", [S.BATCH_GRID, S.BATCH_PERSISTENT])
+def test_batch_equals_plain(mode):
+    import torch
+    mix = _mix()
+    plain = [S.Controller(c) for c, _ in mix]
+    batched = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    n = len(mix)
+    b = S.Batch(n, sum(c.workspace_bytes() + 256 for c in batched))
+    b.set_mode(mode)
+    assert b.mode() == mode
+    res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(3):
+        shift = 0 if tick == 0 else 1
+        probs = []
+        plain_res = []
+        for i, (c, p) in enumerate(mix):
+            x0, xr, fe = tens[i]
+            g = _gait(p, tick, c)
+            plain_res.append(plain[i].solve(x0, xr, g, fe, shift).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, shift))
+        b.solve(batched, probs, res)
+        torch.cuda.synchronize()
+        for i in range(n):
+            rp = S.parse_result(plain_res[i].cpu().numpy())
+            rb = S.parse_result(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy())
+            assert rb["status"] == rp["status"]
+            np.testing.assert_array_equal(rb["u0"], rp["u0"])
+            assert rb["cost_min"] == rp["cost_min"] and rb["ess"] == rp["ess"]
+            assert rb["q_freq"] == rp["q_freq"] and rb["n_finite"] == rp["n_finite"] and rb["iter"] == rp["iter"]
+            mp, vp = _state(plain[i])
+            mb, vb = _state(batched[i])
+            np.testing.assert_array_equal(mb, mp)
+            np.testing.assert_array_equal(vb, vp)
+            if mix[i][0].get("compare_mppi"):
+                np.testing.assert_array_equal(batched[i].read(S.BUF_MPPI_MEAN).cpu().numpy(),
+                                              plain[i].read(S.BUF_MPPI_MEAN).cpu().numpy())
+    b.close()
+
+
+def test_same_alone_and_in_the_mix():
+    # one controller solved in a batch of one and inside a batch of eight
+    import torch
+    mix = _mix()
+    k = 4
+    alone = S.Controller(mix[k][0])
+    inmix = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    b1 = S.Batch(1, alone.workspace_bytes() + 256)
+    b8 = S.Batch(len(mix), sum(c.workspace_bytes() + 256 for c in inmix))
+    r1 = torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    r8 = torch.empty(len(mix) * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(2):
+        x0, xr, fe = tens[k]
+        g = _gait(mix[k][1], tick, mix[k][0])
+        b1.solve([alone], [alone.problem(x0, xr, g, fe, min(tick, 1))], r1)
+        probs = [inmix[i].problem(*tens[i][:2], _gait(mix[i][1], tick, mix[i][0]), tens[i][2], min(tick, 1))
+                 for i in range(len(mix))]
+        b8.solve(inmix, probs, r8)
+    torch.cuda.synchronize()
+    a, m = _state(alone), _state(inmix[k])
+    np.testing.assert_array_equal(a[0], m[0])
+    np.testing.assert_array_equal(a[1], m[1])
+    assert bytes(r1.cpu().numpy()) == bytes(r8[k * S.RESULT_BYTES:(k + 1) * S.RESULT_BYTES].cpu().numpy())
+
+
+def test_budget_admission_rejects_without_side_effects():
+    import torch
+    mix = _mix()[:3]
+    ctls = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    need = sum(c.workspace_bytes() + 256 for c in ctls)
+    b = S.Batch(3, need - 4096)
+    res = torch.empty(3 * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    probs = [ctls[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 0) for i in range(3)]
+    with pytest.raises(S.SBSError) as e:
+        b.solve(ctls, probs, res)
+    assert e.value.status == S.ERR_BUDGET
+    # the controllers were not touched: their first solve still initialises them
+    b2 = S.Batch(3, need)
+    b2.solve(ctls, probs, res)
+    torch.cuda.synchronize()
+    for i in range(3):
+        assert S.parse_result(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy())["iter"] == 0
+
+
+def test_batch_rejects_duplicates_and_mixed_tiles():
+    import torch
+    mix = _mix()[:2]
+    a = S.Controller(mix[0][0])
+    c128 = S.Controller(mix[1][0])
+    c64 = S.Controller(mix[1][0], tile=64)
+    tens = [_tensors(p) for _, p in mix]
+    b = S.Batch(4, 1 << 28)
+    res = torch.empty(4 * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    pa = a.problem(*tens[0][:2], mix[0][1]["gait"], tens[0][2], 0)
+    with pytest.raises(S.SBSError):
+        b.solve([a, a], [pa, pa], res)
+    with pytest.raises(S.SBSError):
+        b.solve([c128, c64], [c128.problem(*tens[1][:2], mix[1][1]["gait"], tens[1][2], 0),
+                              c64.problem(*tens[1][:2], mix[1][1]["gait"], tens[1][2], 0)], res)
+
+
+def test_autotune_picks_a_mode_and_results_stay_valid():
+    import torch
+    mix = _mix()
+    ctls = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    b = S.Batch(len(mix), sum(c.workspace_bytes() + 256 for c in ctls))
+    res = torch.empty(len(mix) * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    probs = [ctls[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 0) for i in range(len(mix))]
+    g_ms, p_ms = b.autotune(ctls, probs, res, ticks=2)
+    assert g_ms > 0 and p_ms > 0
+    assert b.mode() == (S.BATCH_GRID if g_ms <= p_ms else S.BATCH_PERSISTENT)
+    b.solve(ctls, probs, res)
+    torch.cuda.synchronize()
+    for i in range(len(mix)):
+        r = S.parse_result(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy())
+        assert r["status"] in (S.OK, S.ERR_DIVERGED) and r["iter"] == 6
