@@ -208,7 +208,7 @@ def main():
     ss_tick = sum(c["K"] * c["H"] for c, _ in mix)
     mppi_ss = sum(c["K"] * c["H"] for c, _ in mix if c["method"] == "mppi")
     arena = sum(c.workspace_bytes() + 256 for c in ctls)
-    batch = S.Batch(n, arena)
+    batch = S.Batch(n, 2 * arena, inflight=2)  # two ticks in flight: the next is prepared while one runs
     results = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device=dev)
 
     def problems(shift):
@@ -335,7 +335,7 @@ def main():
                        "tile": 128, "graph": True, "launch_mode": mode,
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
                        "l2": "per-tick working set above L2 (sampled deviations "
-                       f"{arena / 1e9:.2f} GB)", "parallelism": f"replicas x{world}"},
+                       f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
             "latency_ms": {"p50": p50, "p99": p99, "kind": "device time of one 256-controller tick"},
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),

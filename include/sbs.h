@@ -170,9 +170,16 @@ typedef struct sbs_batch sbs_batch;
 
 /* Create a controller.  Validates cfg (SBS_ERR_INVALID_ARG), allocates its device
  * state through alloc (NULL: cudaMalloc; SBS_ERR_OOM on failure) on the current
- * device.  The distribution is initialised on the first solve (or sbs_reset). */
+ * device.  The distribution is initialised on the first solve (or sbs_reset).
+ * The scratch of plain solves (sbs_workspace_bytes) is allocated through the
+ * same allocator on the first sbs_solve; controllers solved only through
+ * batches or a server never allocate it. */
 int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** out);
 void sbs_destroy(sbs_handle* h);
+
+/* Allocate the handle's plain-solve workspace now instead of on the first
+ * sbs_solve (for callers that must not allocate while they control). */
+int sbs_prepare(sbs_handle* h);
 
 /* Decision-vector length D = 12 (H or P) + adaptive. */
 int sbs_dim(const sbs_handle* h);
@@ -196,7 +203,8 @@ int sbs_reset(sbs_handle* h, const sbs_gait* gait, uint64_t iter, void* stream);
 int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* stream);
 
 /* Copy a device buffer of the handle (SBS_BUF_*) to dst (host_dst: host memory),
- * bytes must equal the buffer's size.  Enqueued on stream. */
+ * bytes must equal the buffer's size.  Enqueued on stream.  The cost, frequency
+ * and elite buffers are those of the last plain sbs_solve. */
 int sbs_read(const sbs_handle* h, int which, void* dst, size_t bytes, int host_dst, void* stream);
 
 /* Checkpoint: the distribution and iteration counter as an opaque byte blob.
@@ -239,11 +247,14 @@ int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* prob, const 
  * (controller, tile) items from a device work queue; the tick is captured in a
  * CUDA graph and replayed.  Every controller's result equals its own sbs_solve
  * (same tile size), bit for bit. */
-/* A batch context for up to max_instances controllers per tick with a device
- * workspace of workspace_bytes shared by the controllers of one tick (the
- * device-memory budget of in-flight solves).  Two ticks may be in flight per
- * batch object; use one object per stream. */
-int sbs_batch_create(int max_instances, size_t workspace_bytes, const sbs_allocator* alloc, sbs_batch** out);
+/* A batch context for up to max_instances controllers per tick and up to
+ * `inflight` (1..8) of its ticks in flight at once.  workspace_bytes is the
+ * device-memory budget of its solves' scratch, split evenly between the
+ * in-flight ticks: each tick's controllers must fit workspace_bytes / inflight.
+ * A tick reuses the slot of the tick `inflight` calls earlier and waits for
+ * that tick on the host first. */
+int sbs_batch_create(int max_instances, int inflight, size_t workspace_bytes, const sbs_allocator* alloc,
+                     sbs_batch** out);
 void sbs_batch_destroy(sbs_batch* b);
 
 /* Solve n controllers (one iteration each; controllers configured with
@@ -277,6 +288,50 @@ int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sb
  * three stage durations in milliseconds. */
 int sbs_batch_set_profiling(sbs_batch* b, int on);
 int sbs_batch_stage_ms(sbs_batch* b, float ms[3]);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop with continuous batching.  Callers submit solves of their
+ * controllers as they arrive (host-memory inputs, copied at submission).  A
+ * dispatcher thread admits waiting requests into the next free tick slot while
+ * earlier ticks are still running on the GPU: a request joins a tick when its
+ * controller has no solve in flight and its workspace fits the slot's share of
+ * the device-memory budget; the tick is one batched launch (sbs_batch_solve) on
+ * the slot's own stream, so the work of consecutive ticks overlaps on the
+ * device.  Controllers keep their warm-start distribution and RNG counter on
+ * the device between requests.  With plain = 1 the dispatcher instead solves
+ * one request at a time with sbs_solve (one launch set per solve), for
+ * comparison.  A controller must not be used by the caller while it has a
+ * request outstanding; requests of one controller are served in order. */
+typedef struct sbs_server sbs_server;
+
+typedef struct sbs_server_config {
+    int32_t slots;         /* ticks in flight (streams), 1..8 */
+    int32_t max_batch;     /* controllers per tick, >= 1 */
+    int32_t max_pending;   /* outstanding requests accepted, >= 1 */
+    int32_t plain;         /* 1: serve one request per sbs_solve instead of batching */
+    size_t budget_bytes;   /* device workspace budget shared by the slots */
+} sbs_server_config;
+
+typedef struct sbs_server_stats {
+    uint64_t completed;    /* requests finished */
+    uint64_t ticks;        /* batched launches (or plain solves) issued */
+    double p50_us, p99_us, max_us, mean_us;  /* submit-to-completion latency of finished requests */
+    double mean_batch;     /* mean controllers per tick */
+    uint64_t admission_waits;  /* times a ready request waited for budget or a slot */
+} sbs_server_stats;
+
+int sbs_server_create(const sbs_server_config* cfg, const sbs_allocator* alloc, sbs_server** out);
+void sbs_server_destroy(sbs_server* s);
+/* Submit n requests: probs[i] (host memory) for handles[i]; tickets[i] receives
+ * each request's ticket.  SBS_ERR_BUDGET: a request whose workspace can never fit
+ * a slot; SBS_PENDING: the queue is full (nothing submitted). */
+int sbs_server_submit(sbs_server* s, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                      uint64_t* tickets);
+/* Collect finished requests: status[i] = SBS_OK (result copied into results[i],
+ * the ticket retired), SBS_PENDING, or SBS_ERR_INVALID_ARG (unknown ticket). */
+int sbs_server_poll(sbs_server* s, int n, const uint64_t* tickets, sbs_result* results, int32_t* status);
+/* Latency and throughput statistics since creation (or the last reset). */
+int sbs_server_stats_get(sbs_server* s, sbs_server_stats* out, int reset);
 
 /* ---------------------------------------------------------------- utilities */
 const char* sbs_status_str(int status);

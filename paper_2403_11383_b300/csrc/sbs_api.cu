@@ -15,27 +15,6 @@
 
 using namespace sbs;
 
-struct sbs_handle {
-    sbs_config cfg;
-    InstParams hP;         // host copy (device pointers filled in)
-    InstParams* dP;        // device copy
-    char* dev_base;
-    size_t dev_bytes;
-    sbs_allocator alloc;
-    bool has_alloc;
-    int device;
-    int cur;               // current state buffer
-    uint64_t iter;         // Philox iteration counter of the next iteration
-    bool initialized;
-    WsLayout wsl;          // layout of one solve's workspace
-    Workspace ws;          // the handle's own workspace (plain solves)
-    float* dev_in;         // device staging of host inputs: x0 (12) | f_ext (3) | pad | xref (12 H)
-    sbs_result* res_dev;   // device result for host-memory solves
-    float* pin_in;         // pinned host staging of inputs
-    cudaEvent_t in_done;   // last copy out of pin_in has run
-    bool in_pending;
-};
-
 namespace {
 
 constexpr uint32_t kStateMagic = 0x53425331u;  // "SBS1"
@@ -295,8 +274,6 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     const size_t o_res = take(sizeof(sbs_result));
     const size_t in_floats = 16 + 12 * (size_t)P.H;
     const size_t o_in = take(in_floats * sizeof(float));
-    const size_t o_cnt = take((size_t)h->wsl.counters * sizeof(unsigned));
-    const size_t o_ws = take(h->wsl.bytes);
     h->dev_bytes = off;
     h->dev_base = (char*)dev_alloc(&h->alloc, h->has_alloc, off);
     if (!h->dev_base) {
@@ -312,7 +289,6 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     P.Ssp = P.P > 0 ? (const float*)(b + o_S) : nullptr;
     h->res_dev = (sbs_result*)(b + o_res);
     h->dev_in = (float*)(b + o_in);
-    h->ws = ws_at(h->wsl, b + o_ws, (unsigned*)(b + o_cnt));
 
     cudaError_t e = cudaMemset(b, 0, off);
     if (e == cudaSuccess && P.P > 0) {
@@ -330,7 +306,7 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     }
     if (e == cudaSuccess) e = cudaMemcpy(h->dP, &P, sizeof(P), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&h->pin_in, in_floats * sizeof(float), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->in_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags((cudaEvent_t*)&h->in_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (h->pin_in) cudaFreeHost(h->pin_in);
@@ -349,7 +325,8 @@ void sbs_destroy(sbs_handle* h)
 {
     if (!h) return;
     cudaDeviceSynchronize();
-    if (h->in_done) cudaEventDestroy(h->in_done);
+    if (h->in_done) cudaEventDestroy((cudaEvent_t)h->in_done);
+    dev_free(&h->alloc, h->has_alloc, h->ws_base);
     if (h->pin_in) cudaFreeHost(h->pin_in);
     dev_free(&h->alloc, h->has_alloc, h->dev_base);
     delete h;
@@ -374,6 +351,25 @@ int sbs_reset(sbs_handle* h, const sbs_gait* gait, uint64_t iter, void* stream)
     return SBS_OK;
 }
 
+// The handle's own workspace, allocated (zeroed) on its first plain solve.
+static int ensure_workspace(sbs_handle* h)
+{
+    if (h->ws_base) return SBS_OK;
+    const size_t cnt = align_up((size_t)h->wsl.counters * sizeof(unsigned), 256);
+    char* b = (char*)dev_alloc(&h->alloc, h->has_alloc, cnt + h->wsl.bytes);
+    if (!b) return SBS_ERR_OOM;
+    if (cudaMemset(b, 0, cnt) != cudaSuccess) {
+        dev_free(&h->alloc, h->has_alloc, b);
+        return SBS_ERR_CUDA;
+    }
+    h->ws_base = b;
+    h->ws = ws_at(h->wsl, b + cnt, (unsigned*)b);
+    h->dev_bytes += cnt + h->wsl.bytes;
+    return SBS_OK;
+}
+
+int sbs_prepare(sbs_handle* h) { return h ? ensure_workspace(h) : SBS_ERR_INVALID_ARG; }
+
 int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* stream)
 {
     if (!h || !prob || !result || !prob->x0 || !prob->xref) return SBS_ERR_INVALID_ARG;
@@ -382,13 +378,15 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
     const InstParams& P = h->hP;
     if (prob->shift < 0) return SBS_ERR_INVALID_ARG;
     if (P.P > 0 && prob->shift > 1) return SBS_ERR_INVALID_ARG;
+    st = ensure_workspace(h);
+    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const float *x0 = prob->x0, *xref = prob->xref, *fext = prob->f_ext;
     sbs_result* res = result;
     if (prob->host_memory) {
         if (!finite_all(x0, 12) || !finite_all(xref, 12 * P.H) || (fext && !finite_all(fext, 3)))
             return SBS_ERR_INVALID_ARG;
-        if (h->in_pending && cudaEventSynchronize(h->in_done) != cudaSuccess) return SBS_ERR_CUDA;
+        if (h->in_pending && cudaEventSynchronize((cudaEvent_t)h->in_done) != cudaSuccess) return SBS_ERR_CUDA;
         std::memcpy(h->pin_in, x0, 12 * sizeof(float));
         if (fext) std::memcpy(h->pin_in + 12, fext, 3 * sizeof(float));
         else std::memset(h->pin_in + 12, 0, 3 * sizeof(float));
@@ -397,7 +395,7 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         if (cudaMemcpyAsync(h->dev_in, h->pin_in, (16 + 12 * (size_t)P.H) * sizeof(float), cudaMemcpyHostToDevice,
                             s) != cudaSuccess)
             return SBS_ERR_CUDA;
-        if (cudaEventRecord(h->in_done, s) != cudaSuccess) return SBS_ERR_CUDA;
+        if (cudaEventRecord((cudaEvent_t)h->in_done, s) != cudaSuccess) return SBS_ERR_CUDA;
         h->in_pending = true;
         x0 = h->dev_in;
         fext = h->dev_in + 12;
@@ -456,6 +454,8 @@ int sbs_read(const sbs_handle* h, int which, void* dst, size_t bytes, int host_d
         default: return SBS_ERR_INVALID_ARG;
     }
     if (bytes != n) return SBS_ERR_INVALID_ARG;
+    if ((which == SBS_BUF_COST || which == SBS_BUF_FREQ || which == SBS_BUF_ELITE) && !h->ws_base)
+        return SBS_ERR_INVALID_ARG;  // no plain solve yet
     cudaError_t e = cudaMemcpyAsync(dst, src, n, host_dst ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                                     (cudaStream_t)stream);
     return e == cudaSuccess ? SBS_OK : SBS_ERR_CUDA;
@@ -578,7 +578,8 @@ struct sbs_batch {
     sbs_allocator alloc;
     bool has_alloc;
     size_t bytes;
-    sbs_batch_slot slot[2];
+    int nslots;
+    sbs_batch_slot slot[8];
     int next;
     bool use_graph;
     int mode;
@@ -587,15 +588,17 @@ struct sbs_batch {
     bool ev_valid;
 };
 
-extern "C" int sbs_batch_create(int max_instances, size_t workspace_bytes, const sbs_allocator* alloc,
+extern "C" int sbs_batch_create(int max_instances, int inflight, size_t workspace_bytes, const sbs_allocator* alloc,
                                 sbs_batch** out)
 {
-    if (!out || max_instances < 1 || workspace_bytes < 256) return SBS_ERR_INVALID_ARG;
+    if (!out || max_instances < 1 || inflight < 1 || inflight > 8 || workspace_bytes < 256 * (size_t)inflight)
+        return SBS_ERR_INVALID_ARG;
     *out = nullptr;
     sbs_batch* b = new (std::nothrow) sbs_batch();
     if (!b) return SBS_ERR_OOM;
     b->max_inst = max_instances;
-    b->arena_bytes = align_up(workspace_bytes, 256);
+    b->nslots = inflight;
+    b->arena_bytes = workspace_bytes / inflight / 256 * 256;
     b->counter_words = 4 * max_instances + (int)std::min<size_t>(b->arena_bytes / 8192, 1 << 24) + 1024;
     b->has_alloc = alloc != nullptr;
     if (alloc) b->alloc = *alloc;
@@ -603,7 +606,7 @@ extern "C" int sbs_batch_create(int max_instances, size_t workspace_bytes, const
     b->mode = SBS_BATCH_GRID;
     const char* ng = std::getenv("SBS_NO_GRAPH");
     b->use_graph = !(ng && ng[0] == '1');
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < b->nslots; ++i) {
         sbs_batch_slot& sl = b->slot[i];
         sl.key_mode = -1;
         const size_t rec_bytes = align_up(b->bytes, 256);
@@ -664,7 +667,7 @@ extern "C" void sbs_batch_destroy(sbs_batch* b)
     cudaDeviceSynchronize();
     for (int i = 0; i < 4; ++i)
         if (b->ev[i]) cudaEventDestroy(b->ev[i]);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 8; ++i) {
         sbs_batch_slot& sl = b->slot[i];
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
         if (sl.graph) cudaGraphDestroy(sl.graph);
@@ -786,7 +789,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         return A.ntiles > C.ntiles;
     });
     sbs_batch_slot& sl = b->slot[b->next];
-    b->next ^= 1;
+    b->next = (b->next + 1) % b->nslots;
     if (sl.used && cudaEventSynchronize(sl.done) != cudaSuccess) return SBS_ERR_CUDA;
     // controllers solved for the first time start from their initial distribution
     for (int i = 0; i < n; ++i) {

@@ -153,3 +153,28 @@ int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, 
 int launch_fma_peak(float* out, int iters, int blocks, int threads, void* stream);
 
 }  // namespace sbs
+
+// A controller (opaque in the C ABI).
+struct sbs_handle {
+    sbs_config cfg;
+    sbs::InstParams hP;    // host copy (device pointers filled in)
+    sbs::InstParams* dP;   // device copy
+    char* dev_base;
+    size_t dev_bytes;
+    sbs_allocator alloc;
+    bool has_alloc;
+    int device;
+    int cur;               // current state buffer
+    uint64_t iter;         // Philox iteration counter of the next iteration
+    bool initialized;
+    sbs::WsLayout wsl;     // layout of one solve's workspace
+    sbs::Workspace ws;     // the handle's own workspace (plain solves), allocated on first use
+    char* ws_base;         // its allocation (null until the first plain solve)
+    float* dev_in;         // device staging of host inputs: x0 (12) | f_ext (3) | pad | xref (12 H)
+    sbs_result* res_dev;   // device result for host-memory solves
+    float* pin_in;         // pinned host staging of inputs
+    void* in_done;         // cudaEvent_t: last copy out of pin_in has run
+    bool in_pending;
+};
+
+

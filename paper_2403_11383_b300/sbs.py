@@ -60,6 +60,25 @@ class Result(C.Structure):
 
 RESULT_BYTES = C.sizeof(Result)
 
+
+class ServerConfig(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("max_pending", C.c_int32), ("plain", C.c_int32),
+                ("budget_bytes", C.c_size_t)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("ticks", C.c_uint64), ("p50_us", C.c_double), ("p99_us", C.c_double),
+                ("max_us", C.c_double), ("mean_us", C.c_double), ("mean_batch", C.c_double),
+                ("admission_waits", C.c_uint64)]
+
+
+# numpy views of the ABI records, for vectorised marshalling of many requests
+PROBLEM_DTYPE = np.dtype([("x0", "<u8"), ("xref", "<u8"), ("f_ext", "<u8"), ("offset", "<u4", (4,)),
+                          ("duty", "<u4"), ("phase0", "<u4"), ("shift", "<i4"), ("host_memory", "<i4")])
+RESULT_DTYPE = np.dtype([("u0", "<f4", (12,)), ("cost_min", "<f4"), ("ess", "<f4"), ("f_mean", "<f4"),
+                         ("q_freq", "<i4"), ("status", "<i4"), ("n_finite", "<i4"), ("iter_lo", "<u4"),
+                         ("iter_hi", "<u4")])
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -81,6 +100,7 @@ ABI = {
     "sbs_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_destroy": (None, [C.c_void_p]),
     "sbs_dim": (C.c_int, [C.c_void_p]),
+    "sbs_prepare": (C.c_int, [C.c_void_p]),
     "sbs_device_bytes": (C.c_size_t, [C.c_void_p]),
     "sbs_workspace_bytes": (C.c_size_t, [C.c_void_p]),
     "sbs_reset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
@@ -89,7 +109,7 @@ ABI = {
     "sbs_state_size": (C.c_size_t, [C.c_void_p]),
     "sbs_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "sbs_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
-    "sbs_batch_create": (C.c_int, [C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "sbs_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
     "sbs_batch_destroy": (None, [C.c_void_p]),
     "sbs_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_status_str": (C.c_char_p, [C.c_int]),
@@ -97,6 +117,11 @@ ABI = {
                                         C.c_void_p]),
     "sbs_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_server_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_server_destroy": (None, [C.c_void_p]),
+    "sbs_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_server_poll": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_server_stats_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sbs_batch_get_mode": (C.c_int, [C.c_void_p]),
     "sbs_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                      C.c_void_p]),
@@ -246,6 +271,10 @@ class Controller:
     def device_bytes(self) -> int:
         return lib().sbs_device_bytes(self._h)
 
+    def prepare(self):
+        """Allocate the plain-solve workspace now."""
+        check(lib().sbs_prepare(self._h), "sbs_prepare")
+
     def workspace_bytes(self) -> int:
         return lib().sbs_workspace_bytes(self._h)
 
@@ -322,10 +351,12 @@ class Controller:
 class Batch:
     """Many controllers per persistent, graph-captured launch (sbs_batch_*)."""
 
-    def __init__(self, max_instances: int, workspace_bytes: int, use_torch_allocator: bool = True):
+    def __init__(self, max_instances: int, workspace_bytes: int, inflight: int = 1, use_torch_allocator: bool = True):
+        """workspace_bytes: total scratch budget, split between `inflight` ticks."""
         self._b = C.c_void_p()
         alloc = C.byref(torch_allocator().struct) if use_torch_allocator else None
-        check(lib().sbs_batch_create(max_instances, workspace_bytes, alloc, C.byref(self._b)), "sbs_batch_create")
+        check(lib().sbs_batch_create(max_instances, inflight, workspace_bytes, alloc, C.byref(self._b)),
+              "sbs_batch_create")
 
     def close(self):
         if self._b:
@@ -410,6 +441,59 @@ def normals(seed, ctrl, it, k0, nk, nn, stream=None):
     check(lib().sbs_normals(seed, ctrl, it, k0, nk, nn, C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
           "sbs_normals")
     return out
+
+
+class Server:
+    """The request loop with continuous batching (sbs_server_*)."""
+
+    def __init__(self, slots=2, max_batch=2048, max_pending=1 << 16, budget_bytes=8 << 30, plain=False,
+                 use_torch_allocator=False):
+        self._s = C.c_void_p()
+        cfg = ServerConfig(slots, max_batch, max_pending, 1 if plain else 0, budget_bytes)
+        alloc = C.byref(torch_allocator().struct) if use_torch_allocator else None
+        check(lib().sbs_server_create(C.byref(cfg), alloc, C.byref(self._s)), "sbs_server_create")
+
+    def close(self):
+        if self._s:
+            lib().sbs_server_destroy(self._s)
+            self._s = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, handles: np.ndarray, problems: np.ndarray) -> np.ndarray:
+        """handles: uint64 array of controller handles; problems: PROBLEM_DTYPE
+        records with host pointers.  Returns the tickets (uint64)."""
+        n = len(handles)
+        tickets = np.zeros(n, dtype=np.uint64)
+        if n == 0:
+            return tickets
+        h = np.ascontiguousarray(handles, dtype=np.uint64)
+        p = np.ascontiguousarray(problems, dtype=PROBLEM_DTYPE)
+        st = lib().sbs_server_submit(self._s, n, h.ctypes.data, p.ctypes.data, tickets.ctypes.data)
+        if st == PENDING:
+            raise SBSError(st, "sbs_server_submit: queue full")
+        check(st, "sbs_server_submit")
+        return tickets
+
+    def poll(self, tickets: np.ndarray):
+        """Returns (status int32 array, RESULT_DTYPE array)."""
+        n = len(tickets)
+        status = np.zeros(n, dtype=np.int32)
+        res = np.zeros(n, dtype=RESULT_DTYPE)
+        if n:
+            t = np.ascontiguousarray(tickets, dtype=np.uint64)
+            check(lib().sbs_server_poll(self._s, n, t.ctypes.data, res.ctypes.data, status.ctypes.data),
+                  "sbs_server_poll")
+        return status, res
+
+    def stats(self, reset=False) -> dict:
+        st = ServerStats()
+        check(lib().sbs_server_stats_get(self._s, C.byref(st), 1 if reset else 0), "sbs_server_stats_get")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
 
 
 def fp32_peak(stream=None) -> float:
