@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="sbs", choices=["sbs", "reference"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
+    ap.add_argument("--serving-seconds", type=float, default=3.0)
     return ap.parse_args()
 
 
@@ -118,6 +120,22 @@ class Clocks:
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def rollout_traffic():
+    """DRAM bytes per sample-step of the rollout kernel from the committed ncu
+    record, or None when the kernel sources changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "rollout_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as g:
+            h.update(g.read())
+    return rec["dram_bytes_per_sample_step"] if h.hexdigest() == rec["sources_sha256"] else None
 
 
 def measured_peaks():
@@ -225,6 +243,8 @@ def main():
         tick(first=(w == 0))
     tune_ms = batch.autotune(ctls, probs1, results, ticks=5)
     mode = "grid" if batch.mode() == S.BATCH_GRID else "persistent"
+    for _ in range(3):  # rebuild the tick graphs in the chosen mode before timing
+        tick()
     torch.cuda.synchronize()
 
     # ---- timed region: K ticks back to back on the stream
@@ -233,11 +253,13 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # profilers can select exactly the timed launches
     e0.record(stream)
     for _ in range(args.steps):
         tick()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -316,6 +338,15 @@ def main():
     e2e_value = world * ss_tick / e2e_s
     status = [S.parse_result(h_out[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].numpy())["status"] for i in range(n)]
 
+    # ---- served: 2048 closed-loop robots, continuous batching vs plain solves
+    served = None
+    if not args.no_serving:
+        from paper_2403_11383_b300 import serving
+        robots = serving.Robots(2048, seed=3)
+        served = {"batched": serving.run(plain=False, duration=args.serving_seconds, warmup=1.0, robots=robots),
+                  "plain": serving.run(plain=True, duration=args.serving_seconds, warmup=1.0, robots=robots)}
+        del robots
+
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0)
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -326,6 +357,7 @@ def main():
                          f"{t_:.1f} s)"}
 
     peaks = measured_peaks()
+    traffic_ss = rollout_traffic()
     if rank == 0:
         line = {
             "metric": "rollout sample-steps/s", "value": value, "unit": "sample-steps/s", "n_gpus": world,
@@ -345,7 +377,10 @@ def main():
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,
-                         "flops_per_launch": flops_launch, "traffic": None},
+                         "flops_per_launch": flops_launch,
+                         "traffic": None if traffic_ss is None else traffic_ss * ss_tick,
+                         "traffic_note": "ncu DRAM read+write per sample-step on the 48-controller mix, scaled "
+                                         "to this launch's sample-steps (profiles/rollout_traffic.json)"},
             "e2e": {"value": e2e_value, "unit": "sample-steps/s",
                     "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel())},
             "gpu_launches": 3 * args.steps,
@@ -354,6 +389,8 @@ def main():
                               "diverged": sum(s == S.ERR_DIVERGED for s in status)},
             "hbm_gbs_measured": peaks.get("hbm_gbs"),
         }
+        if served:
+            line["served"] = served
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

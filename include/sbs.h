@@ -318,6 +318,7 @@ typedef struct sbs_server_stats {
     double p50_us, p99_us, max_us, mean_us;  /* submit-to-completion latency of finished requests */
     double mean_batch;     /* mean controllers per tick */
     uint64_t admission_waits;  /* times a ready request waited for budget or a slot */
+    uint64_t max_inflight;     /* most ticks that were in flight at once */
 } sbs_server_stats;
 
 int sbs_server_create(const sbs_server_config* cfg, const sbs_allocator* alloc, sbs_server** out);

@@ -78,7 +78,7 @@ struct sbs_server {
     int error = SBS_OK;
     // statistics
     std::vector<double> lat_us;
-    uint64_t ticks = 0, completed = 0, admission_waits = 0;
+    uint64_t ticks = 0, completed = 0, admission_waits = 0, max_inflight = 0;
     double batch_sum = 0.0;
 };
 
@@ -194,9 +194,12 @@ int issue(sbs_server* s, Slot& sl)
         return SBS_ERR_CUDA;
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return SBS_ERR_CUDA;
     sl.busy = true;
+    uint64_t inflight = 0;
+    for (const Slot& o : s->slots) inflight += o.busy ? 1 : 0;
     std::lock_guard<std::mutex> lock(s->mu);
     s->ticks += 1;
     s->batch_sum += (double)n;
+    s->max_inflight = std::max(s->max_inflight, inflight);
     return SBS_OK;
 }
 
@@ -397,6 +400,7 @@ extern "C" int sbs_server_stats_get(sbs_server* s, sbs_server_stats* out, int re
     out->completed = s->completed;
     out->ticks = s->ticks;
     out->admission_waits = s->admission_waits;
+    out->max_inflight = s->max_inflight;
     out->mean_batch = s->ticks ? s->batch_sum / (double)s->ticks : 0.0;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
@@ -411,7 +415,7 @@ extern "C" int sbs_server_stats_get(sbs_server* s, sbs_server_stats* out, int re
     }
     if (reset) {
         s->lat_us.clear();
-        s->completed = s->ticks = s->admission_waits = 0;
+        s->completed = s->ticks = s->admission_waits = s->max_inflight = 0;
         s->batch_sum = 0.0;
     }
     return SBS_OK;

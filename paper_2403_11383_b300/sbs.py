@@ -69,7 +69,7 @@ class ServerConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("ticks", C.c_uint64), ("p50_us", C.c_double), ("p99_us", C.c_double),
                 ("max_us", C.c_double), ("mean_us", C.c_double), ("mean_batch", C.c_double),
-                ("admission_waits", C.c_uint64)]
+                ("admission_waits", C.c_uint64), ("max_inflight", C.c_uint64)]
 
 
 # numpy views of the ABI records, for vectorised marshalling of many requests

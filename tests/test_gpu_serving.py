@@ -119,12 +119,17 @@ def test_continuous_batching_admits_while_ticks_run():
     srv = S.Server(slots=2, max_batch=64, budget_bytes=8 << 30)
     bufs = []
     h = np.array([c.handle.value for c in ctls], dtype=np.uint64)
+    import time
     t1 = srv.submit(h[:4], _records(ctls[:4], probs[:4], 0, bufs))
-    t2 = srv.submit(h[4:], _records(ctls[4:], probs[4:], 0, bufs))
+    t0 = time.time()
+    while srv.stats()["ticks"] < 1:  # the first tick is on the GPU ...
+        assert time.time() - t0 < 10
+    t2 = srv.submit(h[4:], _records(ctls[4:], probs[4:], 0, bufs))  # ... when these arrive
     r = _wait(srv, np.concatenate([t1, t2]))
     assert (r["iter_lo"] == 0).all()
     st = srv.stats()
     assert st["completed"] == 8 and st["ticks"] >= 2
+    assert st["max_inflight"] >= 2  # the second tick was issued while the first still ran
     srv.close()
 
 
