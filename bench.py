@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
     ap.add_argument("--serving-seconds", type=float, default=3.0)
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100"],
+                    help="batched: the 256-controller tick (default); otherwise one controller's solves")
     return ap.parse_args()
 
 
@@ -198,6 +201,91 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- single controller
+
+def flops_per_sample_step(cfg):
+    """Algorithmic FP32 work per sample-step of one controller (FMA = 2).
+    Per-step policy: see FLOPS_ROLLOUT.  Spline policy: per step the basis
+    evaluation (2 P FLOP per force) replaces Box-Muller and sampling, and the
+    knot noise (Box-Muller 6 FLOP per pair, 12 P normals; sampling 2 FLOP per
+    knot value) is counted once per sample, i.e. divided by H."""
+    P, H = cfg.get("P", 0), cfg["H"]
+    base = 128 + 201  # stage cost + SRBD Euler step
+    if P > 0:
+        per = base + 12 * 2 * P + (6 * 6 * P + 2 * 12 * P) / H
+        part = (2 * 12 * P) / H  # MPPI partials from the knot deviations
+    else:
+        per = FLOPS_ROLLOUT
+        part = FLOPS_MPPI_PARTIAL
+    mppi = cfg["method"] == "mppi" or cfg.get("compare_mppi")
+    return per + (part if mppi else 0.0)
+
+
+def run_single(args, world, rank, local):
+    """Timed solves of one controller of a named workload (warm-started ticks)."""
+    import torch
+    from paper_2403_11383_b300 import sbs as S
+    from paper_2403_11383_b300 import workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    cfg = W.config(args.workload)
+    prob = W.problem(cfg)
+    ctl = S.Controller(cfg)
+    x0, xref, fe = (torch.tensor(np.float32(prob[k]), device=dev) for k in ("x0", "xref", "f_ext"))
+    res = torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    for w in range(max(args.warmup, 3)):
+        ctl.solve(x0, xref, prob["gait"], fe, 0 if w == 0 else 1, res)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctl.solve(x0, xref, prob["gait"], fe, 1, res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    ss = cfg["K"] * cfg["H"] * cfg["iterations"]
+    fl = flops_per_sample_step(cfg) * ss
+    # the solve is rollout + (select + refit) launches; the roofline uses the whole solve
+    achieved = fl / (ms * 1e-3) / 1e12
+    peak = S.fp32_peak() / 1e12
+    # host inputs and result, synchronised per solve
+    hx0, hxr, hfe = (np.ascontiguousarray(np.float32(prob[k])) for k in ("x0", "xref", "f_ext"))
+    r = S.Result()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctl.solve_host(hx0, hxr, prob["gait"], hfe, 1, r)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    if rank == 0:
+        line = {"metric": "rollout sample-steps/s", "value": world * ss / (ms * 1e-3), "unit": "sample-steps/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "K": cfg["K"], "H": cfg["H"], "P": cfg.get("P", 0),
+                           "iterations": cfg["iterations"], "method": cfg["method"],
+                           "parallelism": f"replicas x{world}"},
+                "solves_per_s": world / (ms * 1e-3),
+                "roofline": {"kernel": "whole solve", "bound": "alu", "achieved": achieved, "peak": peak,
+                             "unit": "TFLOP/s", "frac": achieved / peak,
+                             "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
+                             "flops_per_sample_step": flops_per_sample_step(cfg), "traffic": None},
+                "e2e": {"value": world * ss / e2e_s, "unit": "sample-steps/s",
+                        "h2d_bytes_per_step": int(4 * (12 + 3 + 12 * cfg["H"])),
+                        "d2h_bytes_per_step": S.RESULT_BYTES},
+                "gpu_launches": args.steps * cfg["iterations"] * (1 if cfg["method"] == "mppi" else 3),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -205,6 +293,12 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    if args.workload != "batched":
+        run_single(args, world, rank, local)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

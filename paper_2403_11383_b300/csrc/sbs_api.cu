@@ -261,7 +261,7 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     fill_params(cfg, &P);
 
     // device layout (256-byte aligned pieces)
-    h->wsl = ws_layout(P.K, P.H, P.P, P.T, P.Ke);
+    h->wsl = ws_layout(P.K, P.H, P.P, P.T, P.Ke, P.method != SBS_MPPI && P.K > kSelectSmemMaxK);
     const size_t D = P.D;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };

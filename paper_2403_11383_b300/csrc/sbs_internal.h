@@ -45,6 +45,7 @@ struct Workspace {
     float* gpart;      // [ngroups][part_stride] group partial sums
     int32_t* elite;    // [Ke] elite indices, ascending
     unsigned* counters;  // [ngroups + 1]
+    unsigned* hist;    // [65536] histogram of the top 16 cost-key bits (large elite selections), or null
 };
 
 // Per-solve, per-iteration arguments.
@@ -71,7 +72,7 @@ struct InstRec {
     int32_t tile_begin;
     int32_t select_begin;
     int32_t refit_begin;
-    int32_t pad;
+    int32_t pad[3];
 };
 
 static_assert(sizeof(InstRec) % 16 == 0, "InstRec must be a multiple of 16 bytes");
@@ -86,7 +87,8 @@ inline size_t rollout_smem_bytes(int H, int P, int T)
     int nwarps = T / 32;
     size_t floats = 3 * (size_t)nf   // mean, variance, standard deviation (shifted)
                   + 12 * (size_t)H   // reference
-                  + (P > 0 ? (size_t)H * P + 12 * (size_t)H : 0)  // spline basis, mean forces
+                  + (P > 0 ? (size_t)H * 4 * ((P + 3) / 4) + 12 * (size_t)H : 0)  // spline basis, mean forces
+                  + (P > 0 ? (size_t)48 * ((P + 3) / 4) * T : 0)  // per-thread knot deviations
                   + (size_t)nwarps * nf;  // per-warp partial sums / combined row
     return floats * sizeof(float);
 }
@@ -96,17 +98,23 @@ inline size_t select_smem_bytes(int K) { return 4 * (size_t)(K < kSelectSmemMaxK
 // Byte layout of a workspace inside one allocation (256-byte aligned pieces).
 struct WsLayout {
     size_t J, q, theta, part, gpart, elite, bytes;
-    int ntiles, ngroups, counters;
+    int ntiles, ngroups, counters;  // counters: zero-when-idle words (completion counters, histogram)
+    bool hist;
 };
 
-inline WsLayout ws_layout(int K, int H, int P, int T, int Ke)
+constexpr int kHistBins = 65536;
+
+// hist: the solve selects elites from more costs than fit in shared memory, so
+// the rollout tiles also build a histogram of the top 16 key bits.
+inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false)
 {
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     const int nt = P > 0 ? P : H, nf = 12 * nt;
     WsLayout L;
     L.ntiles = (K + T - 1) / T;
     L.ngroups = (L.ntiles + kGroup - 1) / kGroup;
-    L.counters = L.ngroups + 1;
+    L.hist = hist;
+    L.counters = L.ngroups + 1 + (hist ? kHistBins : 0);
     const size_t PS = kPartHeader + nf;
     size_t o = 0;
     L.J = o; o = up(o + 4 * (size_t)K);
@@ -129,6 +137,7 @@ inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
     w.gpart = (float*)(base + L.gpart);
     w.elite = (int32_t*)(base + L.elite);
     w.counters = counters;
+    w.hist = L.hist ? counters + L.ngroups + 1 : nullptr;
     return w;
 }
 

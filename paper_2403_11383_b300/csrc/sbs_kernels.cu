@@ -42,11 +42,22 @@ struct __align__(16) BlockShared {
     float wacc[32][12];
 };
 
+// A shared-memory vector load the compiler may not hoist out of the step loop
+// (keeping the knot deviations in shared memory instead of 48 registers).
+__device__ __forceinline__ float4 lds4(const float4* p)
+{
+    float4 r;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(a));
+    return r;
+}
+
 struct Views {
     float *mu, *vr, *sd, *xr, *Bs, *Mb, *acc;
+    float4* dsm;  // spline: per-thread knot deviations [12][nq][T] as float4 (knots padded to 4)
 };
 
-__device__ __forceinline__ Views carve(float* base, int H, int P, int nf)
+__device__ __forceinline__ Views carve(float* base, int H, int P, int nf, int T)
 {
     Views v;
     v.mu = base;
@@ -54,11 +65,15 @@ __device__ __forceinline__ Views carve(float* base, int H, int P, int nf)
     v.sd = v.vr + nf;
     v.xr = v.sd + nf;
     float* p = v.xr + 12 * H;
+    v.dsm = nullptr;
     if (P > 0) {
-        v.Bs = p;
-        p += H * P;
+        const int nq = (P + 3) / 4;
+        v.Bs = p;  // [H][4 nq], zero padded
+        p += H * 4 * nq;
         v.Mb = p;
         p += 12 * H;
+        v.dsm = reinterpret_cast<float4*>(p);
+        p += 48 * nq * T;
     } else {
         v.Bs = v.Mb = nullptr;
     }
@@ -141,8 +156,14 @@ __device__ void stage(BlockShared& sh, const Views& v, int P_knots)
         v.sd[i] = sqrtf(var);
     }
     for (int i = threadIdx.x; i < 12 * P.H; i += blockDim.x) v.xr[i] = t.xref[i];
-    if (P_knots > 0)
-        for (int i = threadIdx.x; i < P.H * P_knots; i += blockDim.x) v.Bs[i] = P.Bsp[i];
+    if (P_knots > 0) {
+        const int w4 = 4 * ((P_knots + 3) / 4);
+        for (int i = threadIdx.x; i < P.H * w4; i += blockDim.x) {
+            const int j = i / w4, p = i % w4;
+            v.Bs[i] = p < P_knots ? P.Bsp[j * P_knots + p] : 0.0f;
+        }
+    }
+
     if (threadIdx.x < 12) sh.x0[threadIdx.x] = t.x0[threadIdx.x];
     if (threadIdx.x < 3) sh.fe[threadIdx.x] = t.fext ? t.fext[threadIdx.x] : 0.0f;
     if (threadIdx.x == 0) {
@@ -160,7 +181,7 @@ __device__ void stage(BlockShared& sh, const Views& v, int P_knots)
         for (int i = threadIdx.x; i < 12 * P.H; i += blockDim.x) {
             const int j = i / 12, c = i % 12;
             float s = 0.0f;
-            for (int p = 0; p < P_knots; ++p) s = fmaf(v.Bs[j * P_knots + p], v.mu[12 * p + c], s);
+            for (int p = 0; p < P_knots; ++p) s = fmaf(v.Bs[j * 4 * ((P_knots + 3) / 4) + p], v.mu[12 * p + c], s);
             v.Mb[i] = s;
         }
         __syncthreads();
@@ -323,7 +344,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    const Views v = carve(dyn, P.H, NP, P.nf);
+    const Views v = carve(dyn, P.H, NP, P.nf, T);
     stage(sh, v, NP);
 
     const int K = P.K;
@@ -348,21 +369,28 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     const uint32_t step = q * P.dt_us;
     const uint32_t duty = t.duty;
 
-    constexpr int ND = NP > 0 ? 12 * NP : 1;
-    float dth[ND];
+    constexpr int NQ = NP > 0 ? (NP + 3) / 4 : 1;
     if constexpr (NP > 0) {
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
+        float* dsf = reinterpret_cast<float*>(v.dsm);
+#pragma unroll 1
+        for (int p = 0; p < 4 * NQ; ++p) {
             float e[12];
-            normals12(k, p, iter, seed, ctrl, e);
+            if (p < NP) {
+                normals12(k, p, iter, seed, ctrl, e);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) dth[12 * p + c] = v.sd[12 * p + c] * e[c];
-            if (valid) {
-                float4* o = reinterpret_cast<float4*>(theta + ((size_t)p * K + k) * 12);
-                o[0] = make_float4(dth[12 * p + 0], dth[12 * p + 1], dth[12 * p + 2], dth[12 * p + 3]);
-                o[1] = make_float4(dth[12 * p + 4], dth[12 * p + 5], dth[12 * p + 6], dth[12 * p + 7]);
-                o[2] = make_float4(dth[12 * p + 8], dth[12 * p + 9], dth[12 * p + 10], dth[12 * p + 11]);
+                for (int c = 0; c < 12; ++c) e[c] = v.sd[12 * p + c] * e[c];
+                if (valid) {
+                    float4* o = reinterpret_cast<float4*>(theta + ((size_t)p * K + k) * 12);
+                    o[0] = make_float4(e[0], e[1], e[2], e[3]);
+                    o[1] = make_float4(e[4], e[5], e[6], e[7]);
+                    o[2] = make_float4(e[8], e[9], e[10], e[11]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) e[c] = 0.0f;
             }
+#pragma unroll
+            for (int c = 0; c < 12; ++c) dsf[(((size_t)c * NQ + p / 4) * T + tid) * 4 + (p & 3)] = e[c];
         }
     }
 
@@ -384,11 +412,19 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
                 o[2] = make_float4(e[8], e[9], e[10], e[11]);
             }
         } else {
+            const float4* b4 = reinterpret_cast<const float4*>(v.Bs + j * 4 * NQ);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
                 float s = v.Mb[12 * j + c];
 #pragma unroll
-                for (int p = 0; p < NP; ++p) s = fmaf(v.Bs[j * NP + p], dth[12 * p + c], s);
+                for (int qq = 0; qq < NQ; ++qq) {
+                    const float4 b = b4[qq];
+                    const float4 d = lds4(v.dsm + (c * NQ + qq) * T + tid);
+                    s = fmaf(b.x, d.x, s);
+                    s = fmaf(b.y, d.y, s);
+                    s = fmaf(b.z, d.z, s);
+                    s = fmaf(b.w, d.w, s);
+                }
                 G[c] = s;
             }
         }
@@ -411,6 +447,14 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     if (valid) {
         t.ws.J[k] = J;
         t.ws.q[k] = (int32_t)q;
+    }
+    if (t.ws.hist) {  // top-16-bit key histogram for a large elite selection (one atomic per distinct bin)
+        const uint32_t bin = cost_key(J) >> 16;
+        const unsigned act = __ballot_sync(kFull, valid);
+        if (valid) {
+            const unsigned peers = __match_any_sync(act, bin);
+            if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
+        }
     }
     if (!t.partials) return;
 
@@ -455,11 +499,12 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             }
         }
     } else {
-#pragma unroll
+        const float* dsf = reinterpret_cast<const float*>(v.dsm);
+#pragma unroll 1
         for (int p = 0; p < NP; ++p) {
             float vv[12], o[3];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) vv[c] = w * dth[12 * p + c];
+            for (int c = 0; c < 12; ++c) vv[c] = w * dsf[(((size_t)c * NQ + p / 4) * T + tid) * 4 + (p & 3)];
             const int c0 = warp_sum12(vv, o);
             if ((lane & 7) == 0) {
                 float* a = v.acc + warp * P.nf + 12 * p + c0;
@@ -551,20 +596,64 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
     }
     uint32_t prefix = 0, mask = 0;
     int rank = Ke;  // 1-based rank of the threshold key among the keys matching prefix
-    for (int pass = 0; pass < 4; ++pass) {
+    int first_pass = 0;
+    if (!in_smem && t.ws.hist) {
+        // the rollout built the histogram of the top 16 bits: find the bin holding rank
+        // Ke (64 bins per thread, then a block scan), then clear the histogram
+        unsigned* hist = t.ws.hist;
+        constexpr int kPer = kHistBins / kSelectThreads;
+        int local = 0;
+        for (int b = 0; b < kPer; ++b) local += (int)__ldcg(hist + tid * kPer + b);
+        int tot;
+        const int excl = block_scan(sh, local, &tot);
+        if (excl < rank && rank <= excl + local) {
+            int c = excl;
+            for (int b = 0; b < kPer; ++b) {
+                const int hcount = (int)__ldcg(hist + tid * kPer + b);
+                if (c + hcount >= rank) {
+                    sh.digit = tid * kPer + b;
+                    sh.below = c;
+                    break;
+                }
+                c += hcount;
+            }
+        }
+        __syncthreads();
+        for (int b = 0; b < kPer; ++b) hist[tid * kPer + b] = 0u;
+        rank -= sh.below;
+        prefix = (uint32_t)sh.digit << 16;
+        mask = 0xffff0000u;
+        first_pass = 2;
+        __syncthreads();
+    }
+    for (int pass = first_pass; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         for (int i = tid; i < 256; i += T) sh.hist[i] = 0;
         __syncthreads();
-        for (int base = 0; base < K; base += 8 * T) {
-            uint32_t keys[8];
+        constexpr int KPT = 16;  // keys per thread per iteration
+        for (int base = 0; base < K; base += KPT * T) {
+            uint32_t keys[KPT];
+            if (!in_smem && base + KPT * T <= K) {
+                // 16-byte loads: thread tid covers keys base + 4 (tid + T u') + 0..3
+                const float4* J4 = reinterpret_cast<const float4*>(J + base);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = base + u * T + tid;
-                keys[u] = i < K ? (in_smem ? skeys[i] : cost_key(__ldcg(J + i))) : 0u;
+                for (int u = 0; u < KPT / 4; ++u) {
+                    const float4 v = __ldcg(J4 + tid + u * T);
+                    keys[4 * u] = cost_key(v.x);
+                    keys[4 * u + 1] = cost_key(v.y);
+                    keys[4 * u + 2] = cost_key(v.z);
+                    keys[4 * u + 3] = cost_key(v.w);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < KPT; ++u) {
+                    const int i = base + u * T + tid;
+                    keys[u] = i < K ? (in_smem ? skeys[i] : cost_key(__ldcg(J + i))) : 0u;
+                }
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = base + u * T + tid;
+            for (int u = 0; u < KPT; ++u) {
+                const int i = base + u * T + tid;  // index only decides validity (all valid on the full path)
                 const bool match = i < K && (keys[u] & mask) == prefix;
                 const uint32_t dig = (keys[u] >> shift) & 255u;
                 // warp-aggregated histogram update: one atomic per distinct digit
@@ -615,11 +704,21 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
         const int k0 = base + 8 * tid;
         uint32_t keys[8];
         int neq = 0;
+        float Jv[8];
+        if (k0 + 8 <= K) {  // 8 consecutive costs, 32-byte aligned: two 16-byte loads
+            const float4 a = __ldcg(reinterpret_cast<const float4*>(J + k0));
+            const float4 b = __ldcg(reinterpret_cast<const float4*>(J + k0) + 1);
+            Jv[0] = a.x; Jv[1] = a.y; Jv[2] = a.z; Jv[3] = a.w;
+            Jv[4] = b.x; Jv[5] = b.y; Jv[6] = b.z; Jv[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) Jv[i] = k0 + i < K ? __ldcg(J + k0 + i) : kInf;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k = k0 + i;
             if (k < K) {
-                const float Jk = __ldcg(J + k);
+                const float Jk = Jv[i];
                 keys[i] = in_smem ? skeys[k] : cost_key(Jk);
                 bmin = fminf(bmin, Jk);
                 nf += Jk < kInf ? 1 : 0;
