@@ -32,6 +32,61 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// Philox4x32-10 for one sample k and one tick: counters (k, d, iter lo, iter hi)
+// with only the draw index d varying along the rollout.  The first round's
+// products involve only k and iter, the second round's second product only
+// round-one words that do not depend on d, and the third round's first product
+// only such words again; those products (and the round keys folded into the
+// XORs) are formed once per sample, leaving one product in round two, one in
+// round three and two in each of rounds four to ten per draw.  Bit-identical to
+// philox4x32_10.
+struct PhiloxPre {
+    uint32_t B;    // round 1 word x XOR d (hi(M1 iter_lo) ^ k0)
+    uint32_t W1K;  // round 1 word w ^ round-2 key k1
+    uint32_t Y2K;  // round 2 word y ^ round-3 key k0
+    uint32_t FHK;  // hi(M0 x2) ^ round-3 key k1
+    uint32_t FLO;  // lo(M0 x2): round 3 word w
+    uint32_t k0, k1;
+};
+
+__device__ __forceinline__ PhiloxPre philox_pre(uint32_t k, uint64_t iter, uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    const uint32_t lo = (uint32_t)iter, hi = (uint32_t)(iter >> 32);
+    const uint64_t a = (uint64_t)M0 * k, b = (uint64_t)M1 * lo;
+    PhiloxPre p;
+    p.B = (uint32_t)(b >> 32) ^ k0;
+    const uint32_t y1 = (uint32_t)b, z1 = (uint32_t)(a >> 32) ^ hi ^ k1, w1 = (uint32_t)a;
+    const uint64_t e = (uint64_t)M1 * z1;
+    const uint32_t x2 = (uint32_t)(e >> 32) ^ y1 ^ (k0 + W0), y2 = (uint32_t)e;
+    const uint64_t f = (uint64_t)M0 * x2;
+    p.W1K = w1 ^ (k1 + W1);
+    p.Y2K = y2 ^ (k0 + 2u * W0);
+    p.FHK = (uint32_t)(f >> 32) ^ (k1 + 2u * W1);
+    p.FLO = (uint32_t)f;
+    p.k0 = k0;
+    p.k1 = k1;
+    return p;
+}
+
+__device__ __forceinline__ uint4 philox_draw(const PhiloxPre& p, uint32_t d)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    const uint64_t c = (uint64_t)M0 * (p.B ^ d);  // round 2, first product
+    const uint32_t z2 = (uint32_t)(c >> 32) ^ p.W1K;
+    const uint64_t g = (uint64_t)M1 * z2;  // round 3, second product
+    uint4 s = make_uint4((uint32_t)(g >> 32) ^ p.Y2K, (uint32_t)g, p.FHK ^ (uint32_t)c, p.FLO);
+    uint32_t k0 = p.k0 + 3u * W0, k1 = p.k1 + 3u * W1;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)M0 * s.x, p1 = (uint64_t)M1 * s.z;
+        s = make_uint4((uint32_t)(p1 >> 32) ^ s.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ s.w ^ k1, (uint32_t)p0);
+        k0 += W0;
+        k1 += W1;
+    }
+    return s;
+}
+
 // Box-Muller on two words: the top 24 bits give exact uniforms u1 in (0, 1]
 // and u2 in [0, 1).  The radius uses the accurate logarithm (its argument is
 // often within a few ulp of 1) and x * rsqrt(x) for the square root; the angle
@@ -70,6 +125,21 @@ __device__ __forceinline__ void normals12(uint32_t k, int j, uint64_t iter, uint
         e[4 * d + 1] = z.y;
         e[4 * d + 2] = z.z;
         e[4 * d + 3] = z.w;
+    }
+}
+
+// The same 12 normals from a sample's precomputed Philox state.
+__device__ __forceinline__ void normals12(const PhiloxPre& pp, int j, float e[12])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const uint4 w = philox_draw(pp, 1u + 3u * (uint32_t)j + (uint32_t)d);
+        const float2 a = box_muller(w.x, w.y);
+        const float2 b = box_muller(w.z, w.w);
+        e[4 * d + 0] = a.x;
+        e[4 * d + 1] = a.y;
+        e[4 * d + 2] = b.x;
+        e[4 * d + 3] = b.y;
     }
 }
 
@@ -115,9 +185,12 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 // One explicit-Euler step of Eq. (1) plus the stage cost of the pre-step state
 // (Alg. 2 charges r(u_i, x_i, x^r_i) before x_{i+1} = f(x_i, u_i)).
 // G: world-frame forces already zeroed on swing legs.  fe: f_ext / m.
+// live: bit i clear when leg i swings on every lane of the warp; its terms are
+// then skipped (a +0 force contributes +0 to every sum, so the result is
+// unchanged for finite states).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[12], const float* xr,
-                                            const float G[12])
+                                            const float G[12], unsigned live = 0xfu)
 {
     float r = 0.0f;
 #pragma unroll
@@ -127,6 +200,7 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        if (!(live & (1u << i))) continue;  // zero force on every lane: adds exactly nothing
         const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
         r = fmaf(P.R[0] * gx, gx, r);
         r = fmaf(P.R[1] * gy, gy, r);
@@ -152,7 +226,7 @@ __device__ __forceinline__ void angle_sincos(float a, float* s, float* c)
 }
 
 __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], const float G[12],
-                                          const float fe[3])
+                                          const float fe[3], unsigned live = 0xfu)
 {
     float sr, cr, sp, cp, sy, cy;
     angle_sincos(x[3], &sr, &cr);
@@ -165,6 +239,7 @@ __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], cons
     float F0 = 0.f, F1 = 0.f, F2 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        if (!(live & (1u << i))) continue;  // zero force on every lane: adds exactly nothing
         const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
         F0 += gx;
         F1 += gy;

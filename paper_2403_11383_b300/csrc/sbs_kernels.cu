@@ -395,11 +395,12 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     }
 
     float J = 0.0f, Jc = 0.0f;
+    const PhiloxPre pp = philox_pre(k, iter, seed, ctrl);
     for (int j = 0; j < P.H; ++j) {
         float G[12];
         if constexpr (NP == 0) {
             float e[12];
-            normals12(k, j, iter, seed, ctrl, e);
+            normals12(pp, j, e);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
                 e[c] = v.sd[12 * j + c] * e[c];  // deviation sigma * eps
@@ -428,11 +429,17 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
                 G[c] = s;
             }
         }
+        unsigned st = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
             if (ph[i] >= duty) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
-        kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G));
-        srbd_step(P, x, G, fe);
+            else st |= 1u << i;
+        }
+        // legs in swing on the whole warp skip their terms (per-step forces only:
+        // the spline kernel runs faster without the branches)
+        const unsigned live = NP == 0 ? __reduce_or_sync(kFull, st) : 0xfu;
+        kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live));
+        srbd_step(P, x, G, fe, live);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             ph[i] += step;
@@ -1079,9 +1086,12 @@ __global__ void k_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, i
     float* o = out + (size_t)i * (nn + 1);
     const uint4 w = philox4x32_10(make_uint4(k, 0u, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
     o[0] = box_muller(w.x, w.y).x;
+    // force draws through the per-sample precomputed Philox state the rollout uses
+    const PhiloxPre pp = philox_pre(k, iter, seed, ctrl);
     for (int d = 0; 4 * d < nn; ++d) {
-        const float4 z = normals4(k, 1u + (uint32_t)d, iter, seed, ctrl);
-        const float zz[4] = {z.x, z.y, z.z, z.w};
+        const uint4 u = philox_draw(pp, 1u + (uint32_t)d);
+        const float2 a = box_muller(u.x, u.y), b = box_muller(u.z, u.w);
+        const float zz[4] = {a.x, a.y, b.x, b.y};
         for (int s = 0; s < 4 && 4 * d + s < nn; ++s) o[1 + 4 * d + s] = zz[s];
     }
 }
