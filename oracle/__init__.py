@@ -17,6 +17,7 @@ from . import build as _build
 MPPI, ELITE, NAIVE = 0, 1, 2
 OK, DIVERGED = 0, -6
 PHASE_ONE = 1_000_000_000
+MAX_FREQ = 8
 
 
 class Params(C.Structure):
@@ -33,6 +34,7 @@ class Params(C.Structure):
         ("f_min", C.c_double), ("f_max", C.c_double),
         ("sigma_init", C.c_double), ("sigma_min", C.c_double),
         ("sigma_f_init", C.c_double), ("sigma_f_min", C.c_double),
+        ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ),
     ]
 
 
@@ -64,6 +66,9 @@ def lib():
             "orc_spline_basis": (None, [C.c_int, C.c_int, d, vp]),
             "orc_spline_at": (d, [C.c_int, C.c_int, d, vp, d]),
             "orc_dim": (C.c_int, [vp]),
+            "orc_sample_dim": (C.c_int, [vp]),
+            "orc_freq_bin": (C.c_int, [u32, u32, u32, u64, C.c_int]),
+            "orc_naive_sets": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "orc_init_dist": (None, [vp, vp, vp, vp]),
             "orc_warm_shift": (None, [vp, vp, C.c_int, vp, vp]),
             "orc_rollout": (None, [vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, vp, C.c_int]),
@@ -121,6 +126,10 @@ def make_params(cfg) -> Params:
     p.f_min, p.f_max = cfg["f_min"], cfg["f_max"]
     p.sigma_init, p.sigma_min = cfg["sigma_init"], cfg["sigma_min"]
     p.sigma_f_init, p.sigma_f_min = cfg["sigma_f_init"], cfg["sigma_f_min"]
+    fs = list(cfg.get("freq_set_mhz", []))
+    p.n_freq = len(fs)
+    for i, f in enumerate(fs):
+        p.freq_set[i] = f
     return p
 
 
@@ -219,7 +228,30 @@ def spline_at(H, P, dt, y, t):
 
 
 def dim(params):
+    """Length of the distribution's mean (one force block per set frequency)."""
     return lib().orc_dim(C.byref(params))
+
+
+def sample_dim(params):
+    """Length of one sample's decision vector."""
+    return lib().orc_sample_dim(C.byref(params))
+
+
+def freq_bin(seed, ctrl, k, it, n):
+    """Set entry drawn by sample k for a discrete frequency set of n values (Sec. V)."""
+    return lib().orc_freq_bin(seed, ctrl, k, it, n)
+
+
+def naive_sets(params, J, q, theta, mean):
+    """Naive update over a discrete frequency set (Alg. 3 per frequency's Gaussian).
+    Returns (entry of the best sample or -1, per-entry winners, new mean)."""
+    J = _f64(J, params.K)
+    q = np.ascontiguousarray(q, dtype=np.uint32)
+    theta = _f64(theta)
+    mean = _f64(mean, dim(params)).copy()
+    best = np.zeros(max(1, params.n_freq), dtype=np.int32)
+    bs = lib().orc_naive_sets(C.byref(params), _p(J), _p(q), _p(theta), _p(mean), _p(best))
+    return bs, best[:params.n_freq], mean
 
 
 def init_dist(params, gait):
@@ -246,7 +278,7 @@ def rollout(params, gait, x0, xref, f_ext, mean, var, it, want_theta=False, nthr
     J = np.zeros(K)
     q = np.zeros(K, dtype=np.uint32)
     margin = np.zeros(K)
-    theta = np.zeros((K, D)) if want_theta else None
+    theta = np.zeros((K, sample_dim(params))) if want_theta else None
     lib().orc_rollout(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(mean), _p(var),
                       it, _p(J), _p(q), _p(theta), _p(margin), nthreads)
     return J, q, theta, margin
@@ -258,7 +290,7 @@ def rollout_sample(params, gait, x0, xref, f_ext, mean, var, it, k, q_override=-
     xref = _f64(xref, 12 * params.H)
     fe = None if f_ext is None else _f64(f_ext, 3)
     mean, var = _f64(mean, D), _f64(var, D)
-    theta = np.zeros(D)
+    theta = np.zeros(sample_dim(params))
     J = lib().orc_rollout_sample(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe),
                                  _p(mean), _p(var), it, k, q_override, _p(theta))
     return J, theta
@@ -311,7 +343,7 @@ def solve(params, gait, x0, xref, f_ext, shift, iter0, mean, var, nthreads=1):
     info = np.zeros(4)
     J = np.zeros(K)
     q = np.zeros(K, dtype=np.uint32)
-    Ke = max(1, params.elite_count)
+    Ke = max(1, params.elite_count, params.n_freq)
     elite = np.full(Ke, -1, dtype=np.int32)
     mppi_mean = np.zeros(D)
     st = lib().orc_solve(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), shift, iter0,

@@ -24,6 +24,8 @@
  *   MPPI weights and weighted mean ..................... Sec. III-C, Alg. 5
  *   elite mean / covariance refit ...................... Alg. 1 (Update), Alg. 4
  *   Naive optimiser (best sample, covariance frozen) ... Sec. III-B, Alg. 3
+ *   step frequency uniform over a discrete set, one
+ *   Gaussian per frequency (Naive) ..................... Sec. V (gait optimisation), Sec. V-A
  *   one warm-started iteration per control tick ........ Sec. III-A
  *
  * Random numbers: Philox4x32-10 from Salmon, Moraes, Dror, Shaw, "Parallel
@@ -41,6 +43,7 @@
 #define NX 12
 #define NU 12
 #define PHASE_ONE 1000000000u /* one gait cycle in units of 1e-9 cycle */
+#define MAX_FREQ 8            /* largest discrete frequency set */
 
 enum { ORC_MPPI = 0, ORC_ELITE = 1, ORC_NAIVE = 2 };
 enum { ORC_OK = 0, ORC_DIVERGED = -6 };
@@ -59,6 +62,8 @@ typedef struct {
     double Q[NX], R[3], w_fc, mu, rho, f_nominal;
     double f_min, f_max;
     double sigma_init, sigma_min, sigma_f_init, sigma_f_min;
+    int32_t n_freq;          /* 0, or the size of a discrete step-frequency set (Naive only) */
+    uint32_t freq_set[MAX_FREQ]; /* its frequencies in mHz, distinct */
 } orc_params;
 
 typedef struct {
@@ -355,26 +360,45 @@ void orc_spline_basis(int H, int P, double dt, double* B)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Decision vector layout: theta = [force part (12 H per-step values, or 12 P  */
-/* knot values), step frequency (adaptive only)], so D = 12 H (+1) or 12 P (+1). */
+/* Decision vector layout: a sample is theta = [force part (nf = 12 H per-step */
+/* values, or 12 P knot values), step frequency (adaptive only)].  The        */
+/* distribution holds one force Gaussian per frequency of a discrete set       */
+/* (n_freq blocks of nf, Sec. V), else one, then the frequency entry           */
+/* (adaptive only): D = n_blocks nf (+1).                                      */
 /* ------------------------------------------------------------------------- */
-int orc_dim(const orc_params* P)
+static int nforce(const orc_params* P) { return 12 * (P->P > 0 ? P->P : P->H); }
+static int nblocks(const orc_params* P) { return P->n_freq > 0 ? P->n_freq : 1; }
+
+int orc_dim(const orc_params* P) { return nblocks(P) * nforce(P) + (P->adaptive ? 1 : 0); }
+
+int orc_sample_dim(const orc_params* P) { return nforce(P) + (P->adaptive ? 1 : 0); }
+
+/* Nominal step frequency (mHz) of force block b: its set value, else q_init. */
+static uint32_t block_q(const orc_params* P, int b) { return P->n_freq > 0 ? P->freq_set[b] : P->q_init; }
+
+/* Discrete step frequency (Sec. V: theta_1 takes one of a few values, drawn
+ * uniformly).  The frequency draw's first Philox word gives a 24-bit uniform
+ * integer u (its top bits, as in the Box-Muller uniforms); sample k takes set
+ * entry floor(n u / 2^24). */
+int orc_freq_bin(uint32_t seed, uint32_t ctrl, uint32_t k, uint64_t iter, int n)
 {
-    int nf = 12 * (P->P > 0 ? P->P : P->H);
-    return nf + (P->adaptive ? 1 : 0);
+    uint32_t ctr[4] = {k, 0u, (uint32_t)iter, (uint32_t)(iter >> 32)};
+    uint32_t key[2] = {seed, ctrl}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    return (int)(((uint64_t)(w[0] >> 8) * (uint64_t)n) >> 24);
 }
 
 static double weight_z(const orc_params* P) { return P->mass * (-P->gravity[2]); }
 
 /* Initial distribution (reset).  Per-step policy: at each step j every leg's mean
  * force is (0, 0, m|g| / n_j) with n_j the number of stance legs at step j of the
- * nominal schedule (q_init), 0 when no leg is in stance.  Spline policy: every
- * knot is (0, 0, m|g| / (4 D_f)).  Variances sigma_init^2; frequency mean
- * q_init / 1000 Hz with variance sigma_f_init^2. */
-static void init_step(const orc_params* P, const orc_gait* g, int j, double* mu, double* var)
+ * block's nominal schedule (its set frequency, else q_init), 0 when no leg is in
+ * stance.  Spline policy: every knot is (0, 0, m|g| / (4 D_f)).  Variances
+ * sigma_init^2; frequency mean q_init / 1000 Hz with variance sigma_f_init^2. */
+static void init_step(const orc_params* P, const orc_gait* g, uint32_t q, int j, double* mu, double* var)
 {
     int n = 0;
-    for (int i = 0; i < 4; ++i) n += orc_stance(g, i, P->q_init, P->dt_us, j);
+    for (int i = 0; i < 4; ++i) n += orc_stance(g, i, q, P->dt_us, j);
     double fz = n > 0 ? weight_z(P) / n : 0.0;
     for (int i = 0; i < 4; ++i) {
         mu[3 * i] = 0; mu[3 * i + 1] = 0; mu[3 * i + 2] = fz;
@@ -384,20 +408,24 @@ static void init_step(const orc_params* P, const orc_gait* g, int j, double* mu,
 
 void orc_init_dist(const orc_params* P, const orc_gait* g, double* mean, double* var)
 {
-    int nt = P->P > 0 ? P->P : P->H;
-    if (P->P > 0) {
-        double fz = weight_z(P) / (4.0 * (double)g->duty / (double)PHASE_ONE);
-        for (int p = 0; p < nt; ++p)
-            for (int i = 0; i < 4; ++i) {
-                mean[12 * p + 3 * i] = 0; mean[12 * p + 3 * i + 1] = 0; mean[12 * p + 3 * i + 2] = fz;
-                for (int a = 0; a < 3; ++a) var[12 * p + 3 * i + a] = P->sigma_init * P->sigma_init;
-            }
-    } else {
-        for (int j = 0; j < nt; ++j) init_step(P, g, j, mean + 12 * j, var + 12 * j);
+    int nt = P->P > 0 ? P->P : P->H, nf = nforce(P);
+    for (int b = 0; b < nblocks(P); ++b) {
+        double* mb = mean + (size_t)b * nf;
+        double* vb = var + (size_t)b * nf;
+        if (P->P > 0) {
+            double fz = weight_z(P) / (4.0 * (double)g->duty / (double)PHASE_ONE);
+            for (int p = 0; p < nt; ++p)
+                for (int i = 0; i < 4; ++i) {
+                    mb[12 * p + 3 * i] = 0; mb[12 * p + 3 * i + 1] = 0; mb[12 * p + 3 * i + 2] = fz;
+                    for (int a = 0; a < 3; ++a) vb[12 * p + 3 * i + a] = P->sigma_init * P->sigma_init;
+                }
+        } else {
+            for (int j = 0; j < nt; ++j) init_step(P, g, block_q(P, b), j, mb + 12 * j, vb + 12 * j);
+        }
     }
     if (P->adaptive) {
-        mean[12 * nt] = P->q_init / 1000.0;
-        var[12 * nt] = P->sigma_f_init * P->sigma_f_init;
+        mean[nf] = P->q_init / 1000.0;
+        var[nf] = P->sigma_f_init * P->sigma_f_init;
     }
 }
 
@@ -409,42 +437,50 @@ void orc_init_dist(const orc_params* P, const orc_gait* g, double* mean, double*
 void orc_warm_shift(const orc_params* P, const orc_gait* g, int shift, double* mean, double* var)
 {
     if (shift <= 0) return;
-    if (P->P > 0) {
-        double dt = P->dt_us * 1e-6, T = (P->H - 1) * dt, tk[64], y[64];
-        orc_knot_times(P->H, P->P, dt, tk);
-        for (int c = 0; c < 12; ++c) {
-            double nv[64];
-            for (int p = 0; p < P->P; ++p) y[p] = mean[12 * p + c];
-            for (int p = 0; p < P->P; ++p) {
-                double t = tk[p] + shift * dt;
-                if (t > T) t = T;
-                nv[p] = orc_spline_at(P->H, P->P, dt, y, t);
-            }
-            for (int p = 0; p < P->P; ++p) mean[12 * p + c] = nv[p];
-        }
-        return;
-    }
-    int H = P->H;
-    for (int j = 0; j < H; ++j) {
-        if (j + shift < H) {
+    int nf = nforce(P);
+    for (int b = 0; b < nblocks(P); ++b) {  /* each frequency's Gaussian moves on its own */
+        double* mb = mean + (size_t)b * nf;
+        double* vb = var + (size_t)b * nf;
+        if (P->P > 0) {
+            double dt = P->dt_us * 1e-6, T = (P->H - 1) * dt, tk[64], y[64];
+            orc_knot_times(P->H, P->P, dt, tk);
             for (int c = 0; c < 12; ++c) {
-                mean[12 * j + c] = mean[12 * (j + shift) + c];
-                var[12 * j + c] = var[12 * (j + shift) + c];
+                double nv[64];
+                for (int p = 0; p < P->P; ++p) y[p] = mb[12 * p + c];
+                for (int p = 0; p < P->P; ++p) {
+                    double t = tk[p] + shift * dt;
+                    if (t > T) t = T;
+                    nv[p] = orc_spline_at(P->H, P->P, dt, y, t);
+                }
+                for (int p = 0; p < P->P; ++p) mb[12 * p + c] = nv[p];
             }
-        } else {
-            init_step(P, g, j, mean + 12 * j, var + 12 * j);
+            continue;
+        }
+        int H = P->H;
+        for (int j = 0; j < H; ++j) {
+            if (j + shift < H) {
+                for (int c = 0; c < 12; ++c) {
+                    mb[12 * j + c] = mb[12 * (j + shift) + c];
+                    vb[12 * j + c] = vb[12 * (j + shift) + c];
+                }
+            } else {
+                init_step(P, g, block_q(P, b), j, mb + 12 * j, vb + 12 * j);
+            }
         }
     }
 }
 
 /* ------------------------------------------------------------------------- */
 /* Rollout(theta_k) (Alg. 2), for sample k of iteration `iter`:               */
-/*   theta_k = mean + sqrt(var) * eps_k (Alg. 1 Sampling, diagonal C);         */
+/*   theta_k = mean + sqrt(var) * eps_k (Alg. 1 Sampling, diagonal C); with a  */
+/*         discrete frequency set the sample first draws its frequency, and  */
+/*         mean, var are that frequency's Gaussian (Sec. V);                 */
 /*   u_j = pi(theta_k, t_j): contact flags from the sample's frequency and     */
 /*         forces from the per-step values or the spline, zeroed on swing legs */
 /*         (Alg. 4, function pi);                                              */
 /*   J  += r(u_j, x_j, x^r_j); x_{j+1} = f(x_j, u_j).                          */
-/* After the loop, adaptive gaits add rho (theta_1 - f_nominal)^2 (Sec. V).    */
+/* After the loop, adaptive gaits (Gaussian or discrete frequency) add         */
+/* rho (theta_1 - f_nominal)^2 (Sec. V).                                      */
 /* A non-finite cost is +inf.  q_override >= 0 replaces the sample's quantised */
 /* frequency (used to evaluate both candidates of an ambiguous rounding).      */
 /* ------------------------------------------------------------------------- */
@@ -486,20 +522,26 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
                            uint32_t* q_out, double* margin_out, double eps, uint64_t pkey)
 {
     const orc_params* P = c->P;
-    int H = P->H, nt = P->P > 0 ? P->P : H;
-    int D = orc_dim(P);
+    int H = P->H, nf = nforce(P);
     double dt = P->dt_us * 1e-6;
-    /* Sampling */
-    for (int n = 0; n < 12 * nt; ++n)
-        theta[n] = c->mean[n] + sqrt(c->var[n]) * orc_normal(P->seed, P->ctrl, k, (uint32_t)n, c->iter);
+    /* Sampling: the frequency first (it picks the force Gaussian of a discrete set) */
     uint32_t q = P->q_init;
     double margin = 1.0;
+    int blk = 0;
+    if (P->n_freq > 0) {
+        blk = orc_freq_bin(P->seed, P->ctrl, k, c->iter, P->n_freq);
+        q = P->freq_set[blk];
+    }
+    const double* mean = c->mean + (size_t)blk * nf;
+    const double* var = c->var + (size_t)blk * nf;
+    for (int n = 0; n < nf; ++n)
+        theta[n] = mean[n] + sqrt(var[n]) * orc_normal(P->seed, P->ctrl, k, (uint32_t)n, c->iter);
     if (P->adaptive) {
         double z = orc_freq_normal(P->seed, P->ctrl, k, c->iter);
-        q = orc_quantise_freq(c->mean[D - 1], sqrt(c->var[D - 1]), z, P->f_min, P->f_max, &margin);
+        q = orc_quantise_freq(c->mean[nf], sqrt(c->var[nf]), z, P->f_min, P->f_max, &margin);
     }
     if (q_override >= 0) q = (uint32_t)q_override;
-    if (P->adaptive) theta[D - 1] = q / 1000.0;
+    if (P->adaptive) theta[nf] = q / 1000.0;
     if (q_out) *q_out = q;
     if (margin_out) *margin_out = margin;
 
@@ -527,7 +569,7 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
         if (eps > 0)
             for (int n = 0; n < NX; ++n) x[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j + 1, (uint64_t)n);
     }
-    if (P->adaptive) {
+    if (P->adaptive || P->n_freq > 0) {
         double d = q / 1000.0 - P->f_nominal;
         J += P->rho * d * d;
     }
@@ -535,13 +577,13 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
     return J;
 }
 
-/* Evaluate all K samples.  theta (K x D) and margin (K) may be NULL.
+/* Evaluate all K samples.  theta (K x sample dim) and margin (K) may be NULL.
  * nthreads > 1 runs samples in parallel (each sample is computed identically). */
 void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
                  const double* f_ext, const double* mean, const double* var, uint64_t iter,
                  double* J, uint32_t* q, double* theta, double* margin, int nthreads)
 {
-    int D = orc_dim(P);
+    int D = orc_sample_dim(P);
     double* B = NULL;
     if (P->P > 0) {
         B = (double*)malloc(sizeof(double) * P->H * P->P);
@@ -706,6 +748,33 @@ void orc_elite_refit(const double* theta, int D, const int32_t* idx, int Ke, con
     }
 }
 
+/* Naive update over a discrete frequency set (Sec. III-B, Alg. 3, with one
+ * Gaussian per frequency, Sec. V-A): for each set entry b, the best sample among
+ * those that drew it (lowest cost, then lowest index) becomes b's force mean; an
+ * entry that no finite-cost sample drew keeps its mean.  Covariances unchanged.
+ * q[k] identifies sample k's entry.  best[b] gets b's winning sample or -1; the
+ * return value is the entry of the best sample overall, -1 when no cost is finite. */
+int orc_naive_sets(const orc_params* P, const double* J, const uint32_t* q, const double* theta,
+                   double* mean, int32_t* best)
+{
+    int nb = P->n_freq, nf = nforce(P), Ds = orc_sample_dim(P);
+    for (int b = 0; b < nb; ++b) best[b] = -1;
+    for (int k = 0; k < P->K; ++k) {
+        if (!isfinite(J[k])) continue;
+        int b = 0;
+        while (b < nb && P->freq_set[b] != q[k]) ++b;
+        if (b == nb) continue; /* not a set frequency: cannot happen for this method's samples */
+        if (best[b] < 0 || J[k] < J[best[b]]) best[b] = k; /* ascending k: ties keep the lower index */
+    }
+    int bs = -1;
+    for (int b = 0; b < nb; ++b) {
+        if (best[b] < 0) continue;
+        if (bs < 0 || J[best[b]] < J[best[bs]] || (J[best[b]] == J[best[bs]] && best[b] < best[bs])) bs = b;
+        for (int n = 0; n < nf; ++n) mean[(size_t)b * nf + n] = theta[(size_t)best[b] * Ds + n];
+    }
+    return bs;
+}
+
 /* First control of a distribution: the mean's forces at t_0, zeroed on legs not in
  * stance at t_0 (the contact flags at step 0 do not depend on the frequency). */
 void orc_first_control(const orc_params* P, const orc_gait* g, const double* mean, double u0[NU])
@@ -722,42 +791,51 @@ void orc_first_control(const orc_params* P, const orc_gait* g, const double* mea
 /* (mean, var) is updated in place; iter0 is the Philox iteration counter of   */
 /* the first iteration (iteration i uses iter0 + i).                           */
 /* Outputs (any may be NULL): u0[12]; info[4] = {beta, ess, mean frequency,    */
-/* status}; J_last, q_last (K) of the last iteration; elite_last (K_e) of the  */
-/* last elite iteration; mppi_mean (D): with the elite/naive method, the MPPI  */
-/* mean from the first iteration's samples.                                    */
+/* status}; J_last, q_last (K) of the last iteration; elite_last (K_e, or the  */
+/* n_freq per-frequency winners) of the last elite iteration; mppi_mean (D):   */
+/* with the elite/naive method, the MPPI mean from the first iteration's       */
+/* samples.  With a discrete frequency set, u0 and the mean frequency come     */
+/* from the Gaussian of the best sample's frequency (the first set entry when  */
+/* the last iteration has no finite cost).                                     */
 /* ------------------------------------------------------------------------- */
 int orc_solve(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
               const double* f_ext, int shift, uint64_t iter0, double* mean, double* var, double* u0,
               double* info, double* J_last, uint32_t* q_last, int32_t* elite_last,
               double* mppi_mean, int nthreads)
 {
-    int K = P->K, D = orc_dim(P);
+    int K = P->K, D = orc_dim(P), Ds = orc_sample_dim(P);
     orc_warm_shift(P, g, shift, mean, var);
-    double* theta = (double*)malloc(sizeof(double) * (size_t)K * D);
+    double* theta = (double*)malloc(sizeof(double) * (size_t)K * Ds);
     double* J = (double*)malloc(sizeof(double) * K);
     uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * K);
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (P->elite_count > 0 ? P->elite_count : 1));
     double* floor_ = (double*)malloc(sizeof(double) * D);
     for (int d = 0; d < D; ++d) floor_[d] = P->sigma_min * P->sigma_min;
     if (P->adaptive) floor_[D - 1] = P->sigma_f_min * P->sigma_f_min;
-    int status = ORC_OK;
+    int status = ORC_OK, bstar = 0;
     double beta = INFINITY, ess = 0;
     for (int it = 0; it < P->iterations; ++it) {
         orc_rollout(P, g, x0, xref, f_ext, mean, var, iter0 + (uint64_t)it, J, q, theta, NULL, nthreads);
         double b = INFINITY;
         for (int k = 0; k < K; ++k)
             if (J[k] < b) b = J[k];
-        if (!isfinite(b)) { status = ORC_DIVERGED; break; }
-        if (P->method == ORC_MPPI) {
-            orc_mppi(J, theta, K, D, P->lambda, mean, &ess, &beta);
+        if (!isfinite(b)) { status = ORC_DIVERGED; bstar = 0; break; }
+        if (P->n_freq > 0) { /* Naive over the frequency set's Gaussians */
+            int32_t best[MAX_FREQ];
+            bstar = orc_naive_sets(P, J, q, theta, mean, best);
+            if (elite_last) memcpy(elite_last, best, sizeof(int32_t) * P->n_freq);
+            beta = b;
+            ess = 1;
+        } else if (P->method == ORC_MPPI) {
+            orc_mppi(J, theta, K, Ds, P->lambda, mean, &ess, &beta);
         } else {
-            if (it == 0 && mppi_mean) orc_mppi(J, theta, K, D, P->lambda, mppi_mean, NULL, NULL);
+            if (it == 0 && mppi_mean) orc_mppi(J, theta, K, Ds, P->lambda, mppi_mean, NULL, NULL);
             int Ke = P->method == ORC_NAIVE ? 1 : P->elite_count;
             orc_elite_select(J, K, Ke, idx);
             if (P->method == ORC_NAIVE) {
-                for (int d = 0; d < D; ++d) mean[d] = theta[(size_t)idx[0] * D + d];
+                for (int d = 0; d < Ds; ++d) mean[d] = theta[(size_t)idx[0] * Ds + d];
             } else {
-                orc_elite_refit(theta, D, idx, Ke, floor_, mean, var);
+                orc_elite_refit(theta, Ds, idx, Ke, floor_, mean, var);
             }
             if (elite_last) memcpy(elite_last, idx, sizeof(int32_t) * Ke);
             beta = b;
@@ -766,11 +844,11 @@ int orc_solve(const orc_params* P, const orc_gait* g, const double* x0, const do
         if (J_last) memcpy(J_last, J, sizeof(double) * K);
         if (q_last) memcpy(q_last, q, sizeof(uint32_t) * K);
     }
-    if (u0) orc_first_control(P, g, mean, u0);
+    if (u0) orc_first_control(P, g, mean + (size_t)bstar * nforce(P), u0);
     if (info) {
         info[0] = beta;
         info[1] = ess;
-        info[2] = P->adaptive ? mean[D - 1] : P->q_init / 1000.0;
+        info[2] = P->adaptive ? mean[D - 1] : block_q(P, bstar) / 1000.0;
         info[3] = status;
     }
     free(theta); free(J); free(q); free(idx); free(floor_);

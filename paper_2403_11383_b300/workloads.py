@@ -92,10 +92,16 @@ def config(name: str) -> dict:
     if name == "spline_k262144_h100":
         return _cfg(K=262144, H=100, P=4, dt_us=10_000, seed=4, method="elite",
                     elite_count=elite_count(0.01, 262144), adaptive=True, compare_mppi=True)
+    if name == "naive_freqset_k10000_h12":
+        # the paper's gait-adaptation setting (Sec. V): 10 000 rollouts, N = 12,
+        # dt = 0.02 s, trot, step frequency uniform over {1.3, 2.0, 2.4} Hz with one
+        # force Gaussian per frequency, Naive optimiser, regulariser towards 1.3 Hz
+        return _cfg(K=10_000, H=12, seed=5, method="naive", q_init=1300,
+                    freq_set_mhz=(1300, 2000, 2400), v_ref=(0.5, 0.0))
     raise KeyError(name)
 
 
-SINGLE = ("plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100")
+SINGLE = ("plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100", "naive_freqset_k10000_h12")
 
 
 def initial_state(rng: np.random.Generator, z: float = 0.30) -> np.ndarray:
