@@ -10,7 +10,8 @@
  *   - per-step tracking, force and friction-cone cost (Sec. V, Sec. IV-B);
  *   - the distribution update: MPPI weighted mean (Sec. III-C, Alg. 5), elite
  *     mean and diagonal variance refit (Alg. 1, Alg. 4) and the Naive best-sample
- *     rule (Sec. III-B, Alg. 3);
+ *     rule (Sec. III-B, Alg. 3), also with the step frequency drawn uniformly
+ *     from a discrete set and one force Gaussian per frequency (Sec. V);
  *   - one warm-started iteration per control tick (Sec. III-A).
  * Every step runs in the library's own CUDA kernels (sm_103a).
  *
@@ -18,13 +19,18 @@
  *   State x = [p (3, world, m), roll/pitch/yaw (3, rad, ZYX), v (3, world, m/s),
  *              omega (3, body, rad/s)].
  *   Forces: 4 legs (FL, FR, RL, RR) x 3 world-frame components, N.
- *   Decision vector theta (length D): the force part first (12 values per step,
- *   step-major, for the per-step policy; 12 values per knot, knot-major, for the
- *   spline policy), then the step frequency in Hz when the gait is adaptive.
+ *   Decision vector theta of one sample: the force part first (nf = 12 values per
+ *   step, step-major, for the per-step policy; 12 values per knot, knot-major,
+ *   for the spline policy), then the step frequency in Hz when the gait is
+ *   adaptive.  The distribution (mean and variance, length D each) has the same
+ *   layout, except that a discrete frequency set of n values holds n force
+ *   blocks of nf values, block b for set entry b: D = n nf.
  *   Gait phases are integers in units of 1e-9 cycle (1e9 = one cycle).
  *   Random numbers: Philox4x32-10 keyed by (seed, controller_id), counter
  *   (sample, draw, iteration low, iteration high); draw 0 is the frequency,
  *   draw 1 + n/4 holds force normal n (Box-Muller on word pairs (0,1), (2,3)).
+ *   With a discrete frequency set of n values, sample k takes entry
+ *   floor(n u / 2^24), u the top 24 bits of draw 0's first word.
  *
  * Errors: every call returns an int status (SBS_OK = 0, negative on error).  No
  * C++ exception crosses the boundary.  A call that fails validation leaves the
@@ -67,13 +73,17 @@ extern "C" {
 #define SBS_MAX_H 128         /* horizon steps */
 #define SBS_MAX_K (1 << 24)   /* samples per controller */
 #define SBS_MAX_TILE 256      /* samples per tile (threads per block) */
+#define SBS_MAX_FREQ 8        /* values of a discrete step-frequency set */
 
 /* ---------------------------------------------------------------- buffers for sbs_read */
 #define SBS_BUF_MEAN 0      /* float[D]  current mean */
 #define SBS_BUF_VAR 1       /* float[D]  current diagonal variance */
 #define SBS_BUF_COST 2      /* float[K]  costs of the last iteration (+inf when not finite) */
 #define SBS_BUF_FREQ 3      /* int32[K]  quantised step frequency of each sample, mHz */
-#define SBS_BUF_ELITE 4     /* int32[K_e] elite sample indices of the last elite iteration, ascending */
+#define SBS_BUF_ELITE 4     /* int32[K_e] elite sample indices of the last elite iteration, ascending;
+                             Naive: int32[n + 1], the winning sample of each set entry (-1: none
+                             with a finite cost) then the entry of the best sample (n = 1 without
+                             a set) */
 #define SBS_BUF_MPPI_MEAN 5 /* float[D]  MPPI mean from the first iteration's samples (compare_mppi) */
 
 /* Single rigid body model of Eq. (1). */
@@ -88,7 +98,8 @@ typedef struct sbs_model {
  * step-frequency regulariser:
  *   r = sum_c Q_c (x_c - xref_c)^2 + sum_legs sum_a R_a Gamma_a^2
  *     + w_fc sum_stance [max(0, |Gamma_xy| - mu Gamma_z)^2 + max(0, -Gamma_z)^2]
- *   J = sum_{j<H} r(u_j, x_j, xref_j) (+ rho (f - f_nominal)^2 when adaptive). */
+ *   J = sum_{j<H} r(u_j, x_j, xref_j) (+ rho (f - f_nominal)^2 when the step
+ *   frequency is sampled, from a Gaussian or from a discrete set). */
 typedef struct sbs_cost {
     float Q[12];
     float R[3];
@@ -120,6 +131,12 @@ typedef struct sbs_config {
     int32_t tile;         /* samples per tile (64..SBS_MAX_TILE, multiple of 32); 0: default 128 */
     sbs_model model;
     sbs_cost cost;
+    /* Discrete step-frequency set (Sec. V): 0, or 1..SBS_MAX_FREQ values drawn
+     * uniformly per sample, each with its own force Gaussian.  Requires
+     * method SBS_NAIVE, adaptive 0 and compare_mppi 0; q_init, f_min and f_max
+     * are then unused (each block's nominal schedule uses its own frequency). */
+    int32_t n_freq;
+    uint32_t freq_set[SBS_MAX_FREQ]; /* mHz, distinct, 1..10000 */
 } sbs_config;
 
 /* Periodic gait (Sec. IV-C): leg i is in stance while its phase
@@ -181,7 +198,8 @@ void sbs_destroy(sbs_handle* h);
  * sbs_solve (for callers that must not allocate while they control). */
 int sbs_prepare(sbs_handle* h);
 
-/* Decision-vector length D = 12 (H or P) + adaptive. */
+/* Length D of the mean (and of the variance): n_blocks 12 (H or P) + adaptive,
+ * n_blocks = n_freq when a discrete frequency set is configured, else 1. */
 int sbs_dim(const sbs_handle* h);
 
 /* Bytes of device memory the handle holds (state, tables and its own workspace). */

@@ -64,6 +64,22 @@ int validate_config(const sbs_config* c)
     for (int i = 0; i < 3; ++i)
         if (k.R[i] < 0) return SBS_ERR_INVALID_ARG;
     if (!(k.w_fc >= 0) || !(k.mu >= 0) || !(k.rho >= 0) || !std::isfinite(k.f_nominal)) return SBS_ERR_INVALID_ARG;
+    // discrete step-frequency set (Naive only): distinct values, each advancing the
+    // phase by less than one cycle per step
+    if (c->n_freq < 0 || c->n_freq > SBS_MAX_FREQ) return SBS_ERR_INVALID_ARG;
+    if (c->n_freq > 0) {
+        if (c->method != SBS_NAIVE || c->adaptive || c->compare_mppi) return SBS_ERR_INVALID_ARG;
+        for (int i = 0; i < c->n_freq; ++i) {
+            const uint32_t f = c->freq_set[i];
+            if (f < 1 || f > 10000 || (double)f * c->dt_us >= 1e9) return SBS_ERR_INVALID_ARG;
+            for (int j = 0; j < i; ++j)
+                if (c->freq_set[j] == f) return SBS_ERR_INVALID_ARG;
+        }
+    }
+    // the rollout's shared memory (the distribution of every block, reference,
+    // spline tables, per-warp sums) must fit one block
+    const int T = c->tile ? c->tile : 128;
+    if (rollout_smem_bytes(c->H, c->P, T, c->n_freq > 0 ? c->n_freq : 1) > kMaxDynamicSmem) return SBS_ERR_INVALID_ARG;
     return SBS_OK;
 }
 
@@ -87,7 +103,10 @@ void fill_params(const sbs_config* cfg, InstParams* out)
     P.nt = cfg->P > 0 ? cfg->P : cfg->H;
     P.nf = 12 * P.nt;
     P.adaptive = cfg->adaptive ? 1 : 0;
-    P.D = P.nf + P.adaptive;
+    P.n_freq = cfg->n_freq;
+    P.nb = cfg->n_freq > 0 ? cfg->n_freq : 1;
+    for (int i = 0; i < cfg->n_freq; ++i) P.freq[i] = cfg->freq_set[i];
+    P.D = P.nb * P.nf + P.adaptive;
     P.method = cfg->method;
     P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
     P.T = cfg->tile ? cfg->tile : 128;
@@ -261,7 +280,8 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     fill_params(cfg, &P);
 
     // device layout (256-byte aligned pieces)
-    h->wsl = ws_layout(P.K, P.H, P.P, P.T, P.Ke, P.method != SBS_MPPI && P.K > kSelectSmemMaxK);
+    h->wsl = ws_layout(P.K, P.H, P.P, P.T, P.Ke, P.method == SBS_ELITE && P.K > kSelectSmemMaxK,
+                       P.method == SBS_NAIVE ? P.nb : 0);
     const size_t D = P.D;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -449,7 +469,10 @@ int sbs_read(const sbs_handle* h, int which, void* dst, size_t bytes, int host_d
         case SBS_BUF_VAR: src = P.state[h->cur] + P.D; n = P.D * sizeof(float); break;
         case SBS_BUF_COST: src = h->ws.J; n = (size_t)P.K * sizeof(float); break;
         case SBS_BUF_FREQ: src = h->ws.q; n = (size_t)P.K * sizeof(int32_t); break;
-        case SBS_BUF_ELITE: src = h->ws.elite; n = (size_t)P.Ke * sizeof(int32_t); break;
+        case SBS_BUF_ELITE:
+            src = h->ws.elite;
+            n = (size_t)(P.method == SBS_NAIVE ? P.nb + 1 : P.Ke) * sizeof(int32_t);
+            break;
         case SBS_BUF_MPPI_MEAN: src = P.mppi_mean; n = P.D * sizeof(float); break;
         default: return SBS_ERR_INVALID_ARG;
     }
@@ -567,7 +590,7 @@ struct sbs_batch_slot {
     cudaGraphNode_t copy_node, kernel_node[3];
     cudaKernelNodeParams kparams[3];
     size_t key_smem, key_sel;
-    int key_T, key_P, key_mode;
+    int key_T, key_var, key_mode;
     int grids[3];
 };
 
@@ -599,7 +622,9 @@ extern "C" int sbs_batch_create(int max_instances, int inflight, size_t workspac
     b->max_inst = max_instances;
     b->nslots = inflight;
     b->arena_bytes = workspace_bytes / inflight / 256 * 256;
-    b->counter_words = 4 * max_instances + (int)std::min<size_t>(b->arena_bytes / 8192, 1 << 24) + 1024;
+    // zero-when-idle words: per controller its completion counters and, for Naive,
+    // its best keys (at most 2 SBS_MAX_FREQ + 2 words); large selections add a histogram
+    b->counter_words = 24 * max_instances + (int)std::min<size_t>(b->arena_bytes / 8192, 1 << 24) + 1024;
     b->has_alloc = alloc != nullptr;
     if (alloc) b->alloc = *alloc;
     b->bytes = 16 + (size_t)max_instances * sizeof(InstRec);
@@ -761,6 +786,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     if (!handles[0]) return SBS_ERR_INVALID_ARG;
     const int T = handles[0]->hP.T;
     const int Pk = handles[0]->hP.P;
+    bool sets = false;  // some controller draws from a discrete frequency set
     size_t smem = 0, sel_smem = 0, arena = 0;
     long long counters = 0;
     std::vector<int> order(n);
@@ -770,7 +796,8 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         if (!h || !p->x0 || !p->xref || p->host_memory || h->hP.T != T || h->hP.P != Pk) return SBS_ERR_INVALID_ARG;
         if (h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
-        smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T));
+        smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb));
+        sets = sets || h->hP.n_freq > 0;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
         arena += align_up(h->wsl.bytes, 256);
         counters += h->wsl.counters;
@@ -840,14 +867,15 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     const size_t used = 16 + (size_t)n * sizeof(InstRec);
     const int mode = b->mode;
     int grids[3];
-    int st = batch_grid(Pk, mode, smem, sel_smem, T, counts, grids);
+    const int var = rollout_variant(Pk, sets);
+    int st = batch_grid(var, mode, smem, sel_smem, T, counts, grids);
     if (st) return st;
-    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_P != Pk ||
+    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_var != var ||
                        sl.key_mode != mode;
     if (b->use_graph && !b->profiling) {
         if (!sl.exec || rekey) {
             std::memcpy(sl.grids, grids, sizeof(grids));
-            st = build_graph(b, sl, Pk, mode, smem, sel_smem, T);
+            st = build_graph(b, sl, var, mode, smem, sel_smem, T);
             if (st) return st;
         } else if (mode == SBS_BATCH_GRID) {
             st = update_graph_grids(sl, grids);
@@ -864,7 +892,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         }
         if (cudaMemcpyAsync(sl.dev, sl.pin, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return SBS_ERR_CUDA;
         if (cudaMemsetAsync(sl.heads, 0, 16, s) != cudaSuccess) return SBS_ERR_CUDA;
-        st = launch_batch(Pk, mode, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, sel_smem, T,
+        st = launch_batch(var, mode, (const InstRec*)(sl.dev + 16), (const int*)sl.dev, sl.heads, smem, sel_smem, T,
                           grids, stream, b->profiling ? (void* const*)b->ev : nullptr);
         if (st) return st;
         b->ev_valid = b->profiling;
@@ -872,7 +900,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     sl.key_smem = smem;
     sl.key_sel = sel_smem;
     sl.key_T = T;
-    sl.key_P = Pk;
+    sl.key_var = var;
     sl.key_mode = mode;
     if (cudaEventRecord(sl.done, s) != cudaSuccess) return SBS_ERR_CUDA;
     sl.used = true;

@@ -158,6 +158,15 @@ __device__ __forceinline__ uint32_t sample_freq(uint32_t k, uint64_t iter, uint3
     return (uint32_t)floorf(__fadd_rn(t, 0.5f));
 }
 
+// Entry of a discrete step-frequency set of n values drawn by sample k (Sec. V:
+// uniform over the set): floor(n u / 2^24), u the top 24 bits of the frequency
+// draw's first Philox word.
+__device__ __forceinline__ int freq_block(uint32_t k, uint64_t iter, uint32_t seed, uint32_t ctrl, int n)
+{
+    const uint4 w = philox4x32_10(make_uint4(k, 0u, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
+    return (int)(((w.x >> 8) * (uint32_t)n) >> 24);
+}
+
 __device__ __forceinline__ uint32_t quantise_mhz(float f, float f_min, float f_max)
 {
     if (f < f_min) f = f_min;

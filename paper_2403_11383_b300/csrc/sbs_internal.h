@@ -15,6 +15,8 @@ constexpr int kGroup = 16;                   // tiles whose partial rows one blo
 constexpr int kRefitThreads = 256;
 constexpr int kSelectThreads = 1024;
 constexpr int kSelectSmemMaxK = 32768;       // costs staged in shared memory up to this K
+constexpr size_t kMaxDynamicSmem = 220 * 1024;  // dynamic shared memory one block may use (below the 227 KB
+                                                 // opt-in limit, which also covers the static part)
 
 // Per-controller constants and persistent device state.  Lives in device
 // memory; every kernel copies it into shared memory before use.
@@ -24,13 +26,16 @@ struct InstParams {
     int32_t nf;        // 12 * nt: length of the force part of theta
     int32_t method, adaptive, Ke, T, ntiles, ngroups, compare_mppi;
     int32_t part_stride;  // floats per partial row: kPartHeader + nf
-    int32_t pad0;
+    int32_t n_freq;       // discrete step-frequency set size (0: none)
+    int32_t nb;           // force blocks of the distribution: n_freq, else 1
+    uint32_t freq[SBS_MAX_FREQ];  // the set, mHz
+    int32_t pad1[3];
     uint32_t dt_us, q_init, seed, ctrl;
     float dt, lambda, inv_lambda, inv_mass, weight_z;
     float inertia[3], inv_inertia[3], foot[12], gravity[3];
     float Q[12], R[3], w_fc, mu, rho, f_nominal, f_min, f_max;
     float var_init, var_min, var_f_init, var_f_min;
-    float* state[2];   // ping-pong distribution: mean[D] then var[D]
+    float* state[2];   // ping-pong distribution: mean[D] then var[D] (nb force blocks of nf, then the frequency)
     float* mppi_mean;  // [D]
     const float* Bsp;  // [H][P] spline basis
     const float* Ssp;  // [P][P] spline shift-by-one-step map
@@ -43,9 +48,11 @@ struct Workspace {
     float* theta;      // [nt][K][12] sampled deviations sigma * eps of every sample
     float* part;       // [ntiles][part_stride] tile partial sums (MPPI)
     float* gpart;      // [ngroups][part_stride] group partial sums
-    int32_t* elite;    // [Ke] elite indices, ascending
-    unsigned* counters;  // [ngroups + 1]
+    int32_t* elite;    // [Ke] elite indices, ascending; Naive: [nb] per-block winners (-1: none), best block
+    unsigned* counters;  // [ngroups + 1] completion counters
     unsigned* hist;    // [65536] histogram of the top 16 cost-key bits (large elite selections), or null
+    unsigned long long* best;  // Naive: [nb] complemented (cost key, index) of each block's best sample, or null
+    unsigned* nfin;    // Naive: samples with a finite cost, or null
 };
 
 // Per-solve, per-iteration arguments.
@@ -79,15 +86,15 @@ static_assert(sizeof(InstRec) % 16 == 0, "InstRec must be a multiple of 16 bytes
 static_assert(sizeof(InstParams) % 16 == 0, "InstParams must be a multiple of 16 bytes");
 static_assert(sizeof(TickArgs) % 8 == 0, "TickArgs must be a multiple of 8 bytes");
 
-// Dynamic shared memory of one rollout item (bytes).
-inline size_t rollout_smem_bytes(int H, int P, int T)
+// Dynamic shared memory of one rollout item (bytes); nb force blocks.
+inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1)
 {
     int nt = P > 0 ? P : H;
     int nf = 12 * nt;
     int nwarps = T / 32;
-    size_t floats = 3 * (size_t)nf   // mean, variance, standard deviation (shifted)
+    size_t floats = 3 * (size_t)nb * nf   // mean, variance, standard deviation (shifted)
                   + 12 * (size_t)H   // reference
-                  + (P > 0 ? (size_t)H * 4 * ((P + 3) / 4) + 12 * (size_t)H : 0)  // spline basis, mean forces
+                  + (P > 0 ? (size_t)H * 4 * ((P + 3) / 4) + 12 * (size_t)nb * H : 0)  // spline basis, mean forces
                   + (P > 0 ? (size_t)48 * ((P + 3) / 4) * T : 0)  // per-thread knot deviations
                   + (size_t)nwarps * nf;  // per-warp partial sums / combined row
     return floats * sizeof(float);
@@ -95,18 +102,24 @@ inline size_t rollout_smem_bytes(int H, int P, int T)
 
 inline size_t select_smem_bytes(int K) { return 4 * (size_t)(K < kSelectSmemMaxK ? K : kSelectSmemMaxK); }
 
-// Byte layout of a workspace inside one allocation (256-byte aligned pieces).
+// Byte layout of a workspace inside one allocation (256-byte aligned pieces),
+// and the word layout of its zero-when-idle counter block (an even number of
+// words starting 8-byte aligned): Naive best keys (2 nb words) and finite count
+// (2 words), completion counters (ngroups + 1), histogram.
 struct WsLayout {
     size_t J, q, theta, part, gpart, elite, bytes;
-    int ntiles, ngroups, counters;  // counters: zero-when-idle words (completion counters, histogram)
+    int ntiles, ngroups, counters;  // counters: zero-when-idle words
+    int c_groups, c_hist;           // word offsets of the completion counters and the histogram
+    int naive_nb;                   // Naive force blocks (0: not Naive)
     bool hist;
 };
 
 constexpr int kHistBins = 65536;
 
 // hist: the solve selects elites from more costs than fit in shared memory, so
-// the rollout tiles also build a histogram of the top 16 key bits.
-inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false)
+// the rollout tiles also build a histogram of the top 16 key bits.  naive_nb:
+// the Naive method's force blocks (the rollout keeps each block's best sample).
+inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false, int naive_nb = 0)
 {
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     const int nt = P > 0 ? P : H, nf = 12 * nt;
@@ -114,7 +127,12 @@ inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false)
     L.ntiles = (K + T - 1) / T;
     L.ngroups = (L.ntiles + kGroup - 1) / kGroup;
     L.hist = hist;
-    L.counters = L.ngroups + 1 + (hist ? kHistBins : 0);
+    L.naive_nb = naive_nb;
+    L.c_groups = naive_nb > 0 ? 2 * naive_nb + 2 : 0;
+    L.c_hist = L.c_groups + L.ngroups + 1;
+    L.counters = L.c_hist + (hist ? kHistBins : 0);
+    L.counters += L.counters & 1;
+    if (naive_nb + 1 > Ke) Ke = naive_nb + 1;
     const size_t PS = kPartHeader + nf;
     size_t o = 0;
     L.J = o; o = up(o + 4 * (size_t)K);
@@ -136,8 +154,10 @@ inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
     w.part = (float*)(base + L.part);
     w.gpart = (float*)(base + L.gpart);
     w.elite = (int32_t*)(base + L.elite);
-    w.counters = counters;
-    w.hist = L.hist ? counters + L.ngroups + 1 : nullptr;
+    w.counters = counters + L.c_groups;
+    w.hist = L.hist ? counters + L.c_hist : nullptr;
+    w.best = L.naive_nb > 0 ? reinterpret_cast<unsigned long long*>(counters) : nullptr;
+    w.nfin = L.naive_nb > 0 ? counters + 2 * L.naive_nb : nullptr;
     return w;
 }
 
@@ -145,6 +165,13 @@ inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
 int validate_config(const sbs_config* c);
 int validate_gait(const sbs_gait* g);
 void fill_params(const sbs_config* cfg, InstParams* out);
+
+// Rollout kernel variant of a launch: the policy's knot count (0: per-step
+// forces), plus kSetsVariant when a controller of the launch draws its step
+// frequency from a discrete set.  The batched launchers take a variant where
+// they say P.
+constexpr int kSetsVariant = 256;
+inline int rollout_variant(int P, bool sets) { return P | (sets ? kSetsVariant : 0); }
 
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);

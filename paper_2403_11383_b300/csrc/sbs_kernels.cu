@@ -57,13 +57,14 @@ struct Views {
     float4* dsm;  // spline: per-thread knot deviations [12][nq][T] as float4 (knots padded to 4)
 };
 
-__device__ __forceinline__ Views carve(float* base, int H, int P, int nf, int T)
+// mu, vr, sd: nb force blocks of nf; Mb: nb blocks of 12 H.
+__device__ __forceinline__ Views carve(float* base, int H, int P, int nf, int T, int nb)
 {
     Views v;
     v.mu = base;
-    v.vr = v.mu + nf;
-    v.sd = v.vr + nf;
-    v.xr = v.sd + nf;
+    v.vr = v.mu + nb * nf;
+    v.sd = v.vr + nb * nf;
+    v.xr = v.sd + nb * nf;
     float* p = v.xr + 12 * H;
     v.dsm = nullptr;
     if (P > 0) {
@@ -71,7 +72,7 @@ __device__ __forceinline__ Views carve(float* base, int H, int P, int nf, int T)
         v.Bs = p;  // [H][4 nq], zero padded
         p += H * 4 * nq;
         v.Mb = p;
-        p += 12 * H;
+        p += 12 * H * nb;
         v.dsm = reinterpret_cast<float4*>(p);
         p += 48 * nq * T;
     } else {
@@ -97,25 +98,29 @@ __device__ __forceinline__ void load_tick(const TickArgs* src, BlockShared& sh)
 
 // Initial value of force entry idx (reset rule of the warm start, Sec. III-A):
 // every leg's mean force at step j is (0, 0, m|g| / n_j), n_j the stance legs of
-// the nominal schedule; spline knots carry m|g| / (4 D_f).
+// the nominal schedule (of the entry's block frequency for a discrete set);
+// spline knots carry m|g| / (4 D_f).
 __device__ __forceinline__ void init_entry(const InstParams& P, const TickArgs& t, int idx, float& m,
                                            float& v)
 {
-    const int axis = idx % 3;
+    const int blk = idx / P.nf, local = idx - blk * P.nf;
+    const int axis = local % 3;
     double fz;
     if (P.P > 0) {
         fz = (double)P.weight_z / (4.0 * (double)t.duty / (double)kPhaseOne);
     } else {
-        const int j = idx / 12;
+        const int j = local / 12;
+        const uint32_t q = P.n_freq > 0 ? P.freq[blk] : P.q_init;
         int n = 0;
-        for (int i = 0; i < 4; ++i) n += stance_at(t, i, P.q_init, P.dt_us, j);
+        for (int i = 0; i < 4; ++i) n += stance_at(t, i, q, P.dt_us, j);
         fz = n > 0 ? (double)P.weight_z / n : 0.0;
     }
     m = axis == 2 ? (float)fz : 0.0f;
     v = P.var_init;
 }
 
-// Force entry idx of the distribution after this tick's warm shift.
+// Force entry idx of the distribution after this tick's warm shift (each force
+// block moves on its own).
 __device__ __forceinline__ void shifted_entry(const InstParams& P, const TickArgs& t, const float* sm,
                                               const float* sv, int idx, float& m, float& v)
 {
@@ -124,15 +129,17 @@ __device__ __forceinline__ void shifted_entry(const InstParams& P, const TickArg
         v = sv[idx];
         return;
     }
+    const int blk = idx / P.nf, local = idx - blk * P.nf;
     if (P.P > 0) {  // spline: knots re-evaluated one step later (shift is 1)
-        const int p = idx / 12, c = idx % 12;
+        const int p = local / 12, c = local % 12;
+        const float* smb = sm + blk * P.nf;
         float s = 0.0f;
-        for (int r = 0; r < P.P; ++r) s = fmaf(P.Ssp[p * P.P + r], sm[12 * r + c], s);
+        for (int r = 0; r < P.P; ++r) s = fmaf(P.Ssp[p * P.P + r], smb[12 * r + c], s);
         m = s;
         v = sv[idx];
         return;
     }
-    const int j = idx / 12;
+    const int j = local / 12;
     if (j + t.shift < P.H) {
         m = sm[idx + 12 * t.shift];
         v = sv[idx + 12 * t.shift];
@@ -148,7 +155,7 @@ __device__ void stage(BlockShared& sh, const Views& v, int P_knots)
     const TickArgs& t = sh.t;
     const float* sm = P.state[t.src];
     const float* sv = sm + P.D;
-    for (int i = threadIdx.x; i < P.nf; i += blockDim.x) {
+    for (int i = threadIdx.x; i < P.nb * P.nf; i += blockDim.x) {
         float m, var;
         shifted_entry(P, t, sm, sv, i, m, var);
         v.mu[i] = m;
@@ -177,11 +184,13 @@ __device__ void stage(BlockShared& sh, const Views& v, int P_knots)
         sh.sig_f = sqrtf(sh.var_f);
     }
     __syncthreads();
-    if (P_knots > 0) {  // mean force trajectory of the spline mean
-        for (int i = threadIdx.x; i < 12 * P.H; i += blockDim.x) {
-            const int j = i / 12, c = i % 12;
+    if (P_knots > 0) {  // mean force trajectory of each block's spline mean
+        for (int i = threadIdx.x; i < 12 * P.H * P.nb; i += blockDim.x) {
+            const int blk = i / (12 * P.H), r = i - blk * 12 * P.H;
+            const int j = r / 12, c = r % 12;
+            const float* mub = v.mu + blk * P.nf;
             float s = 0.0f;
-            for (int p = 0; p < P_knots; ++p) s = fmaf(v.Bs[j * 4 * ((P_knots + 3) / 4) + p], v.mu[12 * p + c], s);
+            for (int p = 0; p < P_knots; ++p) s = fmaf(v.Bs[j * 4 * ((P_knots + 3) / 4) + p], mub[12 * p + c], s);
             v.Mb[i] = s;
         }
         __syncthreads();
@@ -337,14 +346,18 @@ __device__ void mppi_finish(BlockShared& sh, const Views& v, const float* row, b
 
 // ---------------------------------------------------------------------------
 // One tile of T samples.  NP = 0: per-step forces; NP > 0: NP spline knots.
+// SETS: the launch may hold controllers that draw their step frequency from a
+// discrete set; each of their samples reads the force Gaussian of its draw.
+// Without it every sample reads block 0 at addresses uniform across the warp
+// (a separate instantiation: per-thread addressing costs the common case ~3 %).
 // ---------------------------------------------------------------------------
-template <int NP>
+template <int NP, bool SETS>
 __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
 {
     const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    const Views v = carve(dyn, P.H, NP, P.nf, T);
+    const Views v = carve(dyn, P.H, NP, P.nf, T, P.nb);
     stage(sh, v, NP);
 
     const int K = P.K;
@@ -354,7 +367,17 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     const uint64_t iter = t.iter;
     float* theta = t.ws.theta;
     uint32_t q = P.q_init;
-    if (P.adaptive) q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
+    int blk = 0;  // force block: the sample's entry of a discrete frequency set
+    if (P.adaptive) {
+        q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
+    } else if constexpr (SETS) {
+        if (P.n_freq > 0) {
+            blk = freq_block(k, iter, seed, ctrl, P.n_freq);
+            q = P.freq[blk];
+        }
+    }
+    const float* mu = v.mu + blk * P.nf;  // this sample's Gaussian
+    const float* sd = v.sd + blk * P.nf;
 
     float x[12];
 #pragma unroll
@@ -378,7 +401,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             if (p < NP) {
                 normals12(k, p, iter, seed, ctrl, e);
 #pragma unroll
-                for (int c = 0; c < 12; ++c) e[c] = v.sd[12 * p + c] * e[c];
+                for (int c = 0; c < 12; ++c) e[c] = sd[12 * p + c] * e[c];
                 if (valid) {
                     float4* o = reinterpret_cast<float4*>(theta + ((size_t)p * K + k) * 12);
                     o[0] = make_float4(e[0], e[1], e[2], e[3]);
@@ -403,8 +426,8 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             normals12(pp, j, e);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                e[c] = v.sd[12 * j + c] * e[c];  // deviation sigma * eps
-                G[c] = v.mu[12 * j + c] + e[c];
+                e[c] = sd[12 * j + c] * e[c];  // deviation sigma * eps
+                G[c] = mu[12 * j + c] + e[c];
             }
             if (valid) {
                 float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
@@ -416,7 +439,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             const float4* b4 = reinterpret_cast<const float4*>(v.Bs + j * 4 * NQ);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                float s = v.Mb[12 * j + c];
+                float s = v.Mb[blk * 12 * P.H + 12 * j + c];
 #pragma unroll
                 for (int qq = 0; qq < NQ; ++qq) {
                     const float4 b = b4[qq];
@@ -446,7 +469,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
         }
     }
-    if (P.adaptive) {
+    if (P.adaptive || P.n_freq > 0) {
         const float d = (float)q / 1000.0f - P.f_nominal;
         kahan_add(J, Jc, P.rho * d * d);
     }
@@ -462,6 +485,26 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             const unsigned peers = __match_any_sync(act, bin);
             if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
         }
+    }
+    if (t.ws.best) {
+        // Naive: each force block's best finite (cost, index), kept as the maximum of
+        // the complemented 64-bit key; one atomic per warp and block present
+        const bool fin = valid && J < kInf;
+        const unsigned long long key = fin ? ~(((unsigned long long)cost_key(J) << 32) | k) : 0ull;
+        unsigned todo = __reduce_or_sync(kFull, fin ? 1u << blk : 0u);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            unsigned long long m = blk == b ? key : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long x = __shfl_xor_sync(kFull, m, o);
+                m = x > m ? x : m;
+            }
+            if (lane == 0) atomicMax(t.ws.best + b, m);
+        }
+        const unsigned nfw = __popc(__ballot_sync(kFull, fin));
+        if (lane == 0 && nfw) atomicAdd(t.ws.nfin, nfw);
     }
     if (!t.partials) return;
 
@@ -582,6 +625,57 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     mppi_finish(sh, v, comb, t.mppi_to_state != 0);
 }
 
+// Cost of an order-preserving key (inverse of cost_key).
+__device__ __forceinline__ float key_cost(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ---------------------------------------------------------------------------
+// Naive selection (Alg. 3 Sorting) per force block: the rollout left each
+// block's best (cost, index) as a complemented key.  Warp 0 reads and clears
+// them, lists each block's winner (-1: no finite cost) followed by the block of
+// the overall best, and writes the result record.
+// ---------------------------------------------------------------------------
+__device__ void naive_select(BlockShared& sh)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x;
+    if (tid >= 32) return;
+    unsigned long long key = ~0ull;  // no finite sample
+    if (tid < P.nb) {
+        const unsigned long long c = __ldcg(t.ws.best + tid);
+        t.ws.best[tid] = 0ull;
+        key = ~c;
+        t.ws.elite[tid] = c ? (int32_t)(uint32_t)key : -1;
+    }
+    unsigned long long m = key;
+    int b = tid;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long om = __shfl_xor_sync(kFull, m, o);
+        const int ob = __shfl_xor_sync(kFull, b, o);
+        if (om < m || (om == m && ob < b)) {
+            m = om;
+            b = ob;
+        }
+    }
+    if (tid == 0) {
+        const bool any = m != ~0ull;
+        t.ws.elite[P.nb] = any ? b : 0;
+        const unsigned nfin = __ldcg(t.ws.nfin);
+        *t.ws.nfin = 0u;
+        sbs_result* r = t.result;
+        r->cost_min = any ? key_cost((uint32_t)(m >> 32)) : kInf;
+        r->ess = 1.0f;
+        r->status = any ? SBS_OK : SBS_ERR_DIVERGED;
+        r->n_finite = (int32_t)nfin;
+        r->iter_lo = (uint32_t)t.iter;
+        r->iter_hi = (uint32_t)(t.iter >> 32);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Elite selection (Alg. 1 Sorting) by one block: the Ke smallest (cost, index)
 // pairs.  4-pass 8-bit radix select on the order-preserving cost key (costs
@@ -592,9 +686,13 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
 {
     const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
+    if (P.method == SBS_NAIVE) {
+        naive_select(sh);
+        return;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
     const int K = P.K;
-    const int Ke = P.method == SBS_NAIVE ? 1 : P.Ke;
+    const int Ke = P.Ke;
     const float* J = t.ws.J;
     const bool in_smem = K <= kSelectSmemMaxK;
     if (in_smem) {
@@ -774,6 +872,45 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
 }
 
 // ---------------------------------------------------------------------------
+// Naive refit (Alg. 3) of step (or knot) j in every force block: the block's
+// winner becomes its mean (shifted mean + the winner's stored deviation), the
+// variance is kept; a block without a finite-cost sample keeps its mean.  u0
+// and the reported frequency come from the block of the overall best (the first
+// block when no cost is finite).
+// ---------------------------------------------------------------------------
+__device__ void naive_refit(BlockShared& sh, int j)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const float* sm = P.state[t.src];
+    const float* sv = sm + P.D;
+    float* dm = P.state[1 - t.src];
+    float* dv = dm + P.D;
+    sbs_result* r = t.result;
+    const bool diverged = __ldcg(&r->status) != SBS_OK;
+    const int bstar = diverged ? 0 : __ldcg(t.ws.elite + P.nb);
+    for (int i = threadIdx.x; i < 12 * P.nb; i += blockDim.x) {
+        const int blk = i / 12, c = i - 12 * blk;
+        const int idx = blk * P.nf + 12 * j + c;
+        float m, var;
+        shifted_entry(P, t, sm, sv, idx, m, var);
+        const int kb = diverged ? -1 : __ldcg(t.ws.elite + blk);
+        if (kb >= 0) m += __ldcg(t.ws.theta + ((size_t)j * P.K + kb) * 12 + c);
+        dm[idx] = m;
+        dv[idx] = var;
+        if (j == 0 && blk == bstar) {
+            const uint32_t ph = (t.phase0 + t.offset[c / 3]) % kPhaseOne;
+            r->u0[c] = ph < t.duty ? m : 0.0f;
+        }
+    }
+    if (j == 0 && threadIdx.x == 0 && !P.adaptive) {
+        const uint32_t q = P.n_freq > 0 ? P.freq[bstar] : P.q_init;
+        r->f_mean = q * 0.001f;
+        r->q_freq = (int32_t)q;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Elite / Naive refit of one step (or knot) b, or of the frequency (b == nt).
 // With d = theta - mu the stored deviations of the elites: mean = mu + mean(d),
 // var = mean((d - mean(d))^2) floored (Alg. 1 Update, two passes); Naive
@@ -793,6 +930,10 @@ __device__ void refit_block(BlockShared& sh, int b)
     const int32_t* elite = t.ws.elite;
     sbs_result* r = t.result;
     const bool diverged = __ldcg(&r->status) != SBS_OK;
+    if (b < P.nt && P.method == SBS_NAIVE) {
+        naive_refit(sh, b);
+        return;
+    }
     if (b < P.nt) {
         if (tid < 12) {
             float m, var;
@@ -805,12 +946,6 @@ __device__ void refit_block(BlockShared& sh, int b)
         if (diverged) {
             if (tid < 12) {
                 mean_c = sh.mu12[tid];
-                var_c = sh.vr12[tid];
-            }
-        } else if (P.method == SBS_NAIVE) {
-            if (tid < 12) {
-                const int kb = __ldcg(elite);
-                mean_c = sh.mu12[tid] + __ldcg(t.ws.theta + ((size_t)b * K + kb) * 12 + tid);
                 var_c = sh.vr12[tid];
             }
         } else {
@@ -899,7 +1034,7 @@ __device__ void refit_block(BlockShared& sh, int b)
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-template <int NP>
+template <int NP, bool SETS>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __restrict__ dP, TickArgs t)
 {
     extern __shared__ float4 dyn4[];
@@ -907,7 +1042,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __re
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    rollout_tile<NP>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
+    rollout_tile<NP, SETS>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -938,7 +1073,7 @@ __global__ void k_init(const InstParams* __restrict__ dP, TickArgs t)
     const InstParams& P = sh.P;
     float* m = P.state[sh.t.src];
     float* v = m + P.D;
-    for (int i = threadIdx.x; i < P.nf; i += blockDim.x) init_entry(P, sh.t, i, m[i], v[i]);
+    for (int i = threadIdx.x; i < P.nb * P.nf; i += blockDim.x) init_entry(P, sh.t, i, m[i], v[i]);
     if (threadIdx.x == 0 && P.adaptive) {
         m[P.D - 1] = P.q_init * 0.001f;
         v[P.D - 1] = P.var_f_init;
@@ -962,7 +1097,7 @@ __device__ __forceinline__ int find_rec(const InstRec* recs, int n, int it, int 
 
 // counts = {controllers, tile items, selection items, refit items}; heads = queue heads.
 // Every controller of one launch uses the same policy (NP).
-template <int NP>
+template <int NP, bool SETS>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* __restrict__ recs,
                                                                 const int* __restrict__ counts, int* heads)
 {
@@ -978,14 +1113,14 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* _
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
-        rollout_tile<NP>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+        rollout_tile<NP, SETS>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
         __syncthreads();
     }
 }
 
 // One block per item: the hardware block scheduler is the queue (items are
 // dispatched in index order, heavy controllers first).  Unused blocks exit.
-template <int NP>
+template <int NP, bool SETS>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __restrict__ recs,
                                                                const int* __restrict__ counts)
 {
@@ -997,7 +1132,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
-    rollout_tile<NP>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+    rollout_tile<NP, SETS>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* __restrict__ recs,
@@ -1127,42 +1262,50 @@ static int ensure_smem_attr(const void* fn, size_t smem)
     return status_of(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 }
 
-template <int NP>
-static const void* rollout_fn()
-{
-    return (const void*)k_rollout<NP>;
-}
-
-template <int NP>
+template <int NP, bool S>
 static const void* batch_fn(int mode)
 {
-    return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout<NP> : (const void*)k_batch_rollout<NP>;
+    return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout<NP, S> : (const void*)k_batch_rollout<NP, S>;
 }
 
-static const void* rollout_kernel(int P)
+template <bool S>
+static const void* rollout_kernel_s(int P)
 {
     switch (P) {
-        case 0: return rollout_fn<0>();
-        case 2: return rollout_fn<2>();
-        case 3: return rollout_fn<3>();
-        case 4: return rollout_fn<4>();
-        case 6: return rollout_fn<6>();
-        case 8: return rollout_fn<8>();
+        case 0: return (const void*)k_rollout<0, S>;
+        case 2: return (const void*)k_rollout<2, S>;
+        case 3: return (const void*)k_rollout<3, S>;
+        case 4: return (const void*)k_rollout<4, S>;
+        case 6: return (const void*)k_rollout<6, S>;
+        case 8: return (const void*)k_rollout<8, S>;
         default: return nullptr;
     }
 }
 
-const void* batch_rollout_fn(int P, int mode)
+template <bool S>
+static const void* batch_rollout_fn_s(int P, int mode)
 {
     switch (P) {
-        case 0: return batch_fn<0>(mode);
-        case 2: return batch_fn<2>(mode);
-        case 3: return batch_fn<3>(mode);
-        case 4: return batch_fn<4>(mode);
-        case 6: return batch_fn<6>(mode);
-        case 8: return batch_fn<8>(mode);
+        case 0: return batch_fn<0, S>(mode);
+        case 2: return batch_fn<2, S>(mode);
+        case 3: return batch_fn<3, S>(mode);
+        case 4: return batch_fn<4, S>(mode);
+        case 6: return batch_fn<6, S>(mode);
+        case 8: return batch_fn<8, S>(mode);
         default: return nullptr;
     }
+}
+
+static const void* rollout_kernel(int variant)
+{
+    const int P = variant & ~kSetsVariant;
+    return (variant & kSetsVariant) ? rollout_kernel_s<true>(P) : rollout_kernel_s<false>(P);
+}
+
+const void* batch_rollout_fn(int variant, int mode)
+{
+    const int P = variant & ~kSetsVariant;
+    return (variant & kSetsVariant) ? batch_rollout_fn_s<true>(P, mode) : batch_rollout_fn_s<false>(P, mode);
 }
 
 const void* batch_select_fn(int mode)
@@ -1184,8 +1327,8 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
 
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
-    const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T);
-    const void* fn = rollout_kernel(hP.P);
+    const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb);
+    const void* fn = rollout_kernel(rollout_variant(hP.P, hP.n_freq > 0));
     if (!fn) return SBS_ERR_INVALID_ARG;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;

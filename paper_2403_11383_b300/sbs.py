@@ -19,7 +19,7 @@ OK, PENDING = 0, 1
 ERR_INVALID_ARG, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_DIVERGED = -1, -2, -3, -4, -5, -6
 MPPI, ELITE, NAIVE = 0, 1, 2
 BUF_MEAN, BUF_VAR, BUF_COST, BUF_FREQ, BUF_ELITE, BUF_MPPI_MEAN = 0, 1, 2, 3, 4, 5
-MAX_H, MAX_K, MAX_TILE = 128, 1 << 24, 256
+MAX_H, MAX_K, MAX_TILE, MAX_FREQ = 128, 1 << 24, 256, 8
 BATCH_PERSISTENT, BATCH_GRID = 0, 1
 
 
@@ -40,7 +40,8 @@ class Config(C.Structure):
                 ("seed", C.c_uint32), ("controller_id", C.c_uint32), ("lam", C.c_float),
                 ("f_min", C.c_float), ("f_max", C.c_float), ("sigma_init", C.c_float),
                 ("sigma_min", C.c_float), ("sigma_f_init", C.c_float), ("sigma_f_min", C.c_float),
-                ("tile", C.c_int32), ("model", Model), ("cost", Cost)]
+                ("tile", C.c_int32), ("model", Model), ("cost", Cost),
+                ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ)]
 
 
 class Gait(C.Structure):
@@ -191,6 +192,10 @@ def make_config(cfg: dict, tile: int = 0) -> Config:
     c.cost.Q[:] = list(k["Q"])
     c.cost.R[:] = list(k["R"])
     c.cost.w_fc, c.cost.mu, c.cost.rho, c.cost.f_nominal = k["w_fc"], k["mu"], k["rho"], k["f_nominal"]
+    fs = list(cfg.get("freq_set_mhz", ()))
+    c.n_freq = len(fs)
+    for i, f in enumerate(fs[:MAX_FREQ]):
+        c.freq_set[i] = f
     return c
 
 
@@ -328,8 +333,9 @@ class Controller:
 
     def read(self, which: int, stream=None):
         import torch
+        naive_n = max(1, len(self.cfg.get("freq_set_mhz", ()))) + 1  # per-block winners, best block
         n = {BUF_MEAN: self.D, BUF_VAR: self.D, BUF_COST: self.K, BUF_FREQ: self.K,
-             BUF_ELITE: self.cfg.get("elite_count", 1) if self.cfg["method"] == "elite" else 1,
+             BUF_ELITE: self.cfg.get("elite_count", 1) if self.cfg["method"] == "elite" else naive_n,
              BUF_MPPI_MEAN: self.D}[which]
         dt = torch.int32 if which in (BUF_FREQ, BUF_ELITE) else torch.float32
         out = torch.empty(n, dtype=dt, device="cuda")

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
         getattr(lib, n)
 
 
-def test_struct_sizes_match_header():
+def test_struct_sizes_match_header(tmp_path):
     # gcc computes the sizes of the ABI structs from the header itself
     code = r'''
 #include <stdio.h>
@@ -47,8 +47,7 @@ def test_struct_sizes_match_header():
 int main(void) { printf("%zu %zu %zu %zu %zu %zu\n", sizeof(sbs_config), sizeof(sbs_problem),
   sizeof(sbs_result), sizeof(sbs_gait), sizeof(sbs_model), sizeof(sbs_cost)); return 0; }
 '''
-    tmp = os.path.join(B.OUT_DIR, "abi_sizes")
-    os.makedirs(B.OUT_DIR, exist_ok=True)
+    tmp = os.path.join(tmp_path, "abi_sizes")
     with open(tmp + ".c", "w") as f:
         f.write(code)
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", tmp, tmp + ".c"], check=True)
@@ -87,6 +86,23 @@ def test_invalid_model_rejected_without_device(lib):
     cfg2 = dict(cfg, dt_us=300000, f_max=4.0)
     c = S.make_config(cfg2)
     assert lib.sbs_create(C.byref(c), None, C.byref(h)) == S.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("change", [
+    dict(method="mppi"), dict(method="elite", elite_count=10), dict(adaptive=True), dict(compare_mppi=True),
+    dict(freq_set_mhz=(1300, 2000, 1300)), dict(freq_set_mhz=(0, 2000)), dict(freq_set_mhz=(1300, 20000)),
+    dict(freq_set_mhz=tuple(range(1000, 1900, 100))),  # nine values
+    dict(dt_us=500_000, f_max=1.5),  # 2.4 Hz advances the phase by more than a cycle per step
+])
+def test_invalid_frequency_set_rejected_without_device(lib, change):
+    cfg = W.config("naive_freqset_k10000_h12")
+    cfg.update(change)
+    c = S.make_config(cfg)
+    if len(cfg["freq_set_mhz"]) > S.MAX_FREQ:
+        c.n_freq = len(cfg["freq_set_mhz"])
+    h = C.c_void_p()
+    assert lib.sbs_create(C.byref(c), None, C.byref(h)) == S.ERR_INVALID_ARG
+    assert not h.value
 
 
 def test_null_arguments(lib):

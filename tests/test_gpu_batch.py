@@ -21,6 +21,7 @@ def _mix():
         dict(K=16384, H=12, gait="trot", method="mppi"),
         dict(K=129, H=3, gait="crawl", method="elite", elite_count=7),
         dict(K=5000, H=33, gait="trot", method="mppi", adaptive=True, compare_mppi=True),
+        dict(K=2500, H=12, gait="trot", method="naive", freq_set_mhz=(1300, 2000, 2400)),
     ]
     out = []
     for i, sp in enumerate(specs):
