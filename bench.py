@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
     ap.add_argument("--serving-seconds", type=float, default=3.0)
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100"],
+                    choices=["batched", "plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100",
+                             "naive_freqset_k10000_h12"],
                     help="batched: the 256-controller tick (default); otherwise one controller's solves")
     return ap.parse_args()
 
@@ -467,7 +468,7 @@ def main():
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
                       "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
-            "roofline": {"kernel": "k_grid_rollout<0>" if mode == "grid" else "k_batch_rollout<0>", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": "k_grid_rollout<0, false>" if mode == "grid" else "k_batch_rollout<0, false>", "bound": "alu", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,
