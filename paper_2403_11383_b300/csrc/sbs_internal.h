@@ -50,7 +50,8 @@ struct Workspace {
     float* gpart;      // [ngroups][part_stride] group partial sums
     int32_t* elite;    // [Ke] elite indices, ascending; Naive: [nb] per-block winners (-1: none), best block
     unsigned* counters;  // [ngroups + 1] completion counters
-    unsigned* hist;    // [65536] histogram of the top 16 cost-key bits (large elite selections), or null
+    unsigned* hist;    // [65536 + 256] histograms of the top 16 and top 8 cost-key bits (large elite
+                       // selections), or null
     unsigned long long* best;  // Naive: [nb] complemented (cost key, index) of each block's best sample, or null
     unsigned* nfin;    // Naive: samples with a finite cost, or null
 };
@@ -130,7 +131,7 @@ inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false,
     L.naive_nb = naive_nb;
     L.c_groups = naive_nb > 0 ? 2 * naive_nb + 2 : 0;
     L.c_hist = L.c_groups + L.ngroups + 1;
-    L.counters = L.c_hist + (hist ? kHistBins : 0);
+    L.counters = L.c_hist + (hist ? kHistBins + 256 : 0);
     L.counters += L.counters & 1;
     if (naive_nb + 1 > Ke) Ke = naive_nb + 1;
     const size_t PS = kPartHeader + nf;

@@ -36,8 +36,8 @@ struct __align__(16) BlockShared {
     int item;
     int last;
     int hist[256];
-    int wtot[32];
-    int digit, below;
+    int wtot[32], wtot2[32];
+    int digit, below, count;
     float mu12[12], vr12[12], dbar[12];
     float wacc[32][12];
 };
@@ -478,12 +478,16 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         t.ws.J[k] = J;
         t.ws.q[k] = (int32_t)q;
     }
-    if (t.ws.hist) {  // top-16-bit key histogram for a large elite selection (one atomic per distinct bin)
+    if (t.ws.hist) {
+        // histograms of the top 16 and top 8 key bits for a large elite selection
+        // (one atomic per distinct bin and warp)
         const uint32_t bin = cost_key(J) >> 16;
         const unsigned act = __ballot_sync(kFull, valid);
         if (valid) {
             const unsigned peers = __match_any_sync(act, bin);
             if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
+            const unsigned peers8 = __match_any_sync(act, bin >> 8);
+            if (lane == __ffs(peers8) - 1) atomicAdd(t.ws.hist + kHistBins + (bin >> 8), (unsigned)__popc(peers8));
         }
     }
     if (t.ws.best) {
@@ -678,67 +682,80 @@ __device__ void naive_select(BlockShared& sh)
 
 // ---------------------------------------------------------------------------
 // Elite selection (Alg. 1 Sorting) by one block: the Ke smallest (cost, index)
-// pairs.  4-pass 8-bit radix select on the order-preserving cost key (costs
-// staged in shared memory when K <= kSelectSmemMaxK), then an ordered
-// compaction that takes ties at the threshold key by ascending index.
+// pairs, listed by ascending index.  A radix select on the order-preserving cost
+// key gives the threshold key thr (the Ke-th smallest) and need_eq, the number of
+// keys equal to thr that belong to the elite (ties go to the lowest indices); an
+// ordered compaction then lists the elite.
+//  * K <= kSelectSmemMaxK: the keys are staged in shared memory; four 8-bit passes.
+//  * larger K: the rollout built histograms of the top 8 and top 16 key bits.
+//    They give the 16-bit bin holding rank Ke; that bin's keys are gathered into
+//    shared memory and two 8-bit passes finish there (two passes over all keys
+//    in global memory if the bin holds more keys than fit).
 // ---------------------------------------------------------------------------
-__device__ void select_block(BlockShared& sh, uint32_t* skeys)
+
+// The four costs of keys i0 .. i0 + 3 (+inf at and past end); i0 a multiple of 4.
+__device__ __forceinline__ void load4(const float* J, int i0, int end, float c[4])
 {
-    const InstParams& P = sh.P;
-    const TickArgs& t = sh.t;
-    if (P.method == SBS_NAIVE) {
-        naive_select(sh);
-        return;
+    if (i0 + 4 <= end) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(J + i0));
+        c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = i0 + u < end ? __ldcg(J + i0 + u) : kInf;
     }
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
-    const int K = P.K;
-    const int Ke = P.Ke;
-    const float* J = t.ws.J;
-    const bool in_smem = K <= kSelectSmemMaxK;
-    if (in_smem) {
-        for (int i = tid; i < K; i += T) skeys[i] = cost_key(__ldcg(J + i));
-        __syncthreads();
+}
+
+// The digit of the 256-bin histogram in shared memory holding rank (1-based):
+// sets sh.digit and sh.below (keys in lower digits).  Warp 0, 8 bins per lane.
+__device__ __forceinline__ void find_digit(BlockShared& sh, const int* hist, int rank)
+{
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    int local = 0;
+    for (int b = 0; b < 8; ++b) local += hist[8 * lane + b];
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += u;
     }
-    uint32_t prefix = 0, mask = 0;
-    int rank = Ke;  // 1-based rank of the threshold key among the keys matching prefix
-    int first_pass = 0;
-    if (!in_smem && t.ws.hist) {
-        // the rollout built the histogram of the top 16 bits: find the bin holding rank
-        // Ke (64 bins per thread, then a block scan), then clear the histogram
-        unsigned* hist = t.ws.hist;
-        constexpr int kPer = kHistBins / kSelectThreads;
-        int local = 0;
-        for (int b = 0; b < kPer; ++b) local += (int)__ldcg(hist + tid * kPer + b);
-        int tot;
-        const int excl = block_scan(sh, local, &tot);
-        if (excl < rank && rank <= excl + local) {
-            int c = excl;
-            for (int b = 0; b < kPer; ++b) {
-                const int hcount = (int)__ldcg(hist + tid * kPer + b);
-                if (c + hcount >= rank) {
-                    sh.digit = tid * kPer + b;
-                    sh.below = c;
-                    break;
-                }
-                c += hcount;
+    const int excl = incl - local;
+    const unsigned hit = __ballot_sync(kFull, excl < rank && rank <= incl);
+    if (lane == __ffs(hit) - 1) {
+        int c = excl;
+        for (int b = 0; b < 8; ++b) {
+            const int h = hist[8 * lane + b];
+            if (c + h >= rank) {
+                sh.digit = 8 * lane + b;
+                sh.below = c;
+                break;
             }
+            c += h;
         }
-        __syncthreads();
-        for (int b = 0; b < kPer; ++b) hist[tid * kPer + b] = 0u;
-        rank -= sh.below;
-        prefix = (uint32_t)sh.digit << 16;
-        mask = 0xffff0000u;
-        first_pass = 2;
-        __syncthreads();
     }
-    for (int pass = first_pass; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        for (int i = tid; i < 256; i += T) sh.hist[i] = 0;
-        __syncthreads();
+}
+
+// One 8-bit radix pass over n keys: the histogram of digit (key >> shift) & 255
+// among keys matching prefix under mask, then the digit holding rank; narrows
+// prefix, mask and rank.  SMEM: keys in shared memory; else costs in global memory.
+template <bool SMEM>
+__device__ void radix_pass(BlockShared& sh, const uint32_t* skeys, const float* J, int n, int shift,
+                           uint32_t& prefix, uint32_t& mask, int& rank)
+{
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int i = tid; i < 256; i += T) sh.hist[i] = 0;
+    __syncthreads();
+    if constexpr (SMEM) {
+        for (int i = tid; i < n; i += T) {
+            const uint32_t key = skeys[i];
+            if ((key & mask) == prefix) atomicAdd(&sh.hist[(key >> shift) & 255u], 1);
+        }
+    } else {
         constexpr int KPT = 16;  // keys per thread per iteration
-        for (int base = 0; base < K; base += KPT * T) {
+        for (int base = 0; base < n; base += KPT * T) {
             uint32_t keys[KPT];
-            if (!in_smem && base + KPT * T <= K) {
+            bool ok[KPT];
+            if (base + KPT * T <= n) {
                 // 16-byte loads: thread tid covers keys base + 4 (tid + T u') + 0..3
                 const float4* J4 = reinterpret_cast<const float4*>(J + base);
 #pragma unroll
@@ -749,121 +766,260 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
                     keys[4 * u + 2] = cost_key(v.z);
                     keys[4 * u + 3] = cost_key(v.w);
                 }
+#pragma unroll
+                for (int u = 0; u < KPT; ++u) ok[u] = true;
             } else {
 #pragma unroll
                 for (int u = 0; u < KPT; ++u) {
                     const int i = base + u * T + tid;
-                    keys[u] = i < K ? (in_smem ? skeys[i] : cost_key(__ldcg(J + i))) : 0u;
+                    ok[u] = i < n;
+                    keys[u] = ok[u] ? cost_key(__ldcg(J + i)) : 0u;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < KPT; ++u) {
-                const int i = base + u * T + tid;  // index only decides validity (all valid on the full path)
-                const bool match = i < K && (keys[u] & mask) == prefix;
-                const uint32_t dig = (keys[u] >> shift) & 255u;
-                // warp-aggregated histogram update: one atomic per distinct digit
-                const unsigned act = __ballot_sync(kFull, match);
-                if (match) {
-                    const unsigned peers = __match_any_sync(act, dig);
-                    if (lane == __ffs(peers) - 1) atomicAdd(&sh.hist[dig], __popc(peers));
-                }
-            }
+            for (int u = 0; u < KPT; ++u)
+                if (ok[u] && (keys[u] & mask) == prefix) atomicAdd(&sh.hist[(keys[u] >> shift) & 255u], 1);
         }
-        __syncthreads();
-        if (warp == 0) {
-            int local = 0;
-            for (int b = 0; b < 8; ++b) local += sh.hist[8 * lane + b];
-            int incl = local;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += u;
-            }
-            const int excl = incl - local;
-            const unsigned hit = __ballot_sync(kFull, excl < rank && rank <= incl);
-            if (lane == __ffs(hit) - 1) {
-                int c = excl;
-                for (int b = 0; b < 8; ++b) {
-                    const int h = sh.hist[8 * lane + b];
-                    if (c + h >= rank) {
-                        sh.digit = 8 * lane + b;
-                        sh.below = c;
-                        break;
-                    }
-                    c += h;
-                }
-            }
-        }
-        __syncthreads();
-        rank -= sh.below;
-        prefix |= (uint32_t)sh.digit << shift;
-        mask |= 255u << shift;
-        __syncthreads();
     }
-    const uint32_t thr = prefix;
-    const int need_eq = rank;  // keys equal to thr taken in index order
+    __syncthreads();
+    find_digit(sh, sh.hist, rank);
+    __syncthreads();
+    rank -= sh.below;
+    prefix |= (uint32_t)sh.digit << shift;
+    mask |= 255u << shift;
+    __syncthreads();
+}
+
+// Threshold key and tie count for K > kSelectSmemMaxK from the rollout's
+// histograms (which it clears for the next solve); cand: shared-memory space for
+// kSelectSmemMaxK keys.
+__device__ void large_threshold(BlockShared& sh, uint32_t* cand, uint32_t& thr, int& need_eq)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
+    const int K = P.K;
+    const float* J = t.ws.J;
+    unsigned* hist16 = t.ws.hist;
+    unsigned* hist8 = hist16 + kHistBins;
+    int rank = P.Ke;
+    // the top-8-bit bin holding rank Ke, then its 16-bit sub-bin
+    for (int i = tid; i < 256; i += T) sh.hist[i] = (int)__ldcg(hist8 + i);
+    __syncthreads();
+    find_digit(sh, sh.hist, rank);
+    __syncthreads();
+    const int b8 = sh.digit;
+    rank -= sh.below;
+    __syncthreads();
+    const int v = tid < 256 ? (int)__ldcg(hist16 + b8 * 256 + tid) : 0;
+    int tot;
+    const int excl = block_scan(sh, v, &tot);
+    if (tid < 256 && excl < rank && rank <= excl + v) {
+        sh.digit = b8 * 256 + tid;
+        sh.below = excl;
+        sh.count = v;
+    }
+    __syncthreads();
+    const uint32_t b16 = (uint32_t)sh.digit;
+    rank -= sh.below;
+    const int ncand = sh.count;
+    __syncthreads();
+    for (int i = tid; i < 256; i += T) hist8[i] = 0u;
+    for (int i = tid; i < kHistBins; i += T) hist16[i] = 0u;
+    uint32_t prefix = b16 << 16, mask = 0xffff0000u;
+    if (ncand > kSelectSmemMaxK) {  // the bin does not fit: finish over all keys
+        radix_pass<false>(sh, nullptr, J, K, 8, prefix, mask, rank);
+        radix_pass<false>(sh, nullptr, J, K, 0, prefix, mask, rank);
+        thr = prefix;
+        need_eq = rank;
+        return;
+    }
+    // gather the low 16 bits of the bin's keys (order does not matter for the
+    // threshold; the compaction takes ties by index)
+    if (tid == 0) sh.count = 0;
+    __syncthreads();
+    constexpr int R = 4;  // 16-byte loads in flight per thread
+    for (int base = 0; base < K; base += 4 * R * T) {
+        float c[4 * R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) load4(J, base + 4 * (tid + r * T), K, c + 4 * r);
+#pragma unroll
+        for (int u = 0; u < 4 * R; ++u) {
+            const int i = base + 4 * (tid + (u / 4) * T) + (u & 3);
+            const uint32_t key = cost_key(c[u]);
+            const bool m = i < K && (key >> 16) == b16;
+            const unsigned bal = __ballot_sync(kFull, m);
+            if (bal) {
+                int at = 0;
+                if (lane == __ffs(bal) - 1) at = atomicAdd(&sh.count, __popc(bal));
+                at = __shfl_sync(kFull, at, __ffs(bal) - 1);
+                const int pos = at + __popc(bal & ((1u << lane) - 1u));
+                if (m && pos < kSelectSmemMaxK) cand[pos] = key & 0xffffu;
+            }
+        }
+    }
+    __syncthreads();
+    const int n = min(sh.count, kSelectSmemMaxK);
+    uint32_t p2 = 0, m2 = 0;
+    radix_pass<true>(sh, cand, nullptr, n, 8, p2, m2, rank);
+    radix_pass<true>(sh, cand, nullptr, n, 0, p2, m2, rank);
+    thr = (b16 << 16) | p2;
+    need_eq = rank;
+}
+
+__device__ __forceinline__ int warp_sum_int(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int* total)
+{
+    const int lane = threadIdx.x & 31;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += u;
+    }
+    *total = __shfl_sync(kFull, incl, 31);
+    return incl - v;
+}
+
+// List the keys below thr and the first need_eq keys equal to thr, by ascending
+// index, into out (Ke entries).  Warp w owns a contiguous range of indices (a
+// multiple of 128 long, read as 16-byte loads); a first pass counts, the warps'
+// offsets follow in warp order, a second pass writes.  Also the best cost and the
+// number of finite costs.  R: rounds of 128 keys per warp whose loads are in
+// flight together (more only pays when every warp has that many rounds).
+template <int R>
+__device__ void ordered_compaction(BlockShared& sh, uint32_t thr, int need_eq, float* best, int* nfinite)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int K = P.K, Ke = P.Ke;
+    const float* J = t.ws.J;
     int32_t* out = t.ws.elite;
-    int pos = 0, eq_seen = 0, nf = 0;
+    const int Cw = ((K + nw - 1) / nw + 127) / 128 * 128;
+    const int c0 = min(K, warp * Cw), c1 = min(K, c0 + Cw);
+    int lt = 0, eq = 0, nf = 0;
     float bmin = kInf;
-    for (int base = 0; base < K; base += 8 * T) {
-        const int k0 = base + 8 * tid;
-        uint32_t keys[8];
-        int neq = 0;
-        float Jv[8];
-        if (k0 + 8 <= K) {  // 8 consecutive costs, 32-byte aligned: two 16-byte loads
-            const float4 a = __ldcg(reinterpret_cast<const float4*>(J + k0));
-            const float4 b = __ldcg(reinterpret_cast<const float4*>(J + k0) + 1);
-            Jv[0] = a.x; Jv[1] = a.y; Jv[2] = a.z; Jv[3] = a.w;
-            Jv[4] = b.x; Jv[5] = b.y; Jv[6] = b.z; Jv[7] = b.w;
-        } else {
+    for (int base = c0; base < c1; base += 128 * R) {
+        float c[4 * R];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) Jv[i] = k0 + i < K ? __ldcg(J + k0 + i) : kInf;
-        }
+        for (int r = 0; r < R; ++r) load4(J, base + 128 * r + 4 * lane, c1, c + 4 * r);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = k0 + i;
-            if (k < K) {
-                const float Jk = Jv[i];
-                keys[i] = in_smem ? skeys[k] : cost_key(Jk);
-                bmin = fminf(bmin, Jk);
-                nf += Jk < kInf ? 1 : 0;
-            } else {
-                keys[i] = 0xffffffffu;
-            }
-            neq += (k < K && keys[i] == thr) ? 1 : 0;
-        }
-        int eq_tot;
-        int eq_rank = eq_seen + block_scan(sh, neq, &eq_tot);
-        int ntake = 0;
-        bool take[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const bool valid = k0 + i < K;
-            const bool lt = valid && keys[i] < thr;
-            const bool eq = valid && keys[i] == thr;
-            take[i] = lt || (eq && eq_rank < need_eq);
-            eq_rank += eq ? 1 : 0;
-            ntake += take[i] ? 1 : 0;
-        }
-        int take_tot;
-        int off = pos + block_scan(sh, ntake, &take_tot);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (take[i]) {
-                if (off < Ke) out[off] = k0 + i;  // never past the Ke-sized output
-                ++off;
+        for (int u = 0; u < 4 * R; ++u) {
+            if (base + 128 * (u / 4) + 4 * lane + (u & 3) < c1) {
+                const uint32_t key = cost_key(c[u]);
+                lt += key < thr ? 1 : 0;
+                eq += key == thr ? 1 : 0;
+                bmin = fminf(bmin, c[u]);
+                nf += c[u] < kInf ? 1 : 0;
             }
         }
-        pos += take_tot;
-        eq_seen += eq_tot;
     }
-    const float beta = block_min(sh, bmin);
+    lt = warp_sum_int(lt);
+    eq = warp_sum_int(eq);
+    if (lane == 0) {
+        sh.wtot[warp] = lt;
+        sh.wtot2[warp] = eq;
+    }
+    __syncthreads();
+    int off = 0, eqb = 0;
+    for (int w = 0; w < warp; ++w) {
+        const int e = sh.wtot2[w];
+        off += sh.wtot[w] + min(e, max(0, need_eq - eqb));
+        eqb += e;
+    }
+    const int take_eq = min(eq, max(0, need_eq - eqb));  // this warp's ties, in index order
+    int eq_seen = 0;
+    for (int base0 = c0; base0 < c1; base0 += 128 * R) {
+        float cr[4 * R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) load4(J, base0 + 128 * r + 4 * lane, c1, cr + 4 * r);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i0 = base0 + 128 * r + 4 * lane;
+            const float* c = cr + 4 * r;
+            bool is_lt[4], is_eq[4];
+            int ne = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t key = cost_key(c[u]);
+                is_lt[u] = i0 + u < c1 && key < thr;
+                is_eq[u] = i0 + u < c1 && key == thr;
+                ne += is_eq[u] ? 1 : 0;
+            }
+            int ne_tot;
+            int er = eq_seen + warp_excl_scan(ne, &ne_tot);  // ties before this lane's keys
+            bool take[4];
+            int nt = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                take[u] = is_lt[u] || (is_eq[u] && er < take_eq);
+                er += is_eq[u] ? 1 : 0;
+                nt += take[u] ? 1 : 0;
+            }
+            int nt_tot;
+            int pos = off + warp_excl_scan(nt, &nt_tot);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (take[u]) {
+                    if (pos < Ke) out[pos] = i0 + u;  // never past the Ke-sized output
+                    ++pos;
+                }
+            }
+            off += nt_tot;
+            eq_seen += ne_tot;
+        }
+    }
+    *best = block_min(sh, bmin);
+    int tot;
+    block_scan(sh, nf, &tot);
+    *nfinite = tot;
+}
+
+__device__ void select_block(BlockShared& sh, uint32_t* skeys)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    if (P.method == SBS_NAIVE) {
+        naive_select(sh);
+        return;
+    }
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int K = P.K;
+    const float* J = t.ws.J;
+    uint32_t thr;
+    int need_eq;
+    if (K <= kSelectSmemMaxK) {
+        for (int i = tid; i < K; i += T) skeys[i] = cost_key(__ldcg(J + i));
+        __syncthreads();
+        uint32_t prefix = 0, mask = 0;
+        int rank = P.Ke;
+        for (int pass = 0; pass < 4; ++pass) radix_pass<true>(sh, skeys, nullptr, K, 24 - 8 * pass, prefix, mask, rank);
+        thr = prefix;
+        need_eq = rank;
+    } else if (t.ws.hist) {
+        large_threshold(sh, skeys, thr, need_eq);
+    } else {  // larger K always comes with the histograms; kept for completeness
+        uint32_t prefix = 0, mask = 0;
+        int rank = P.Ke;
+        for (int pass = 0; pass < 4; ++pass) radix_pass<false>(sh, nullptr, J, K, 24 - 8 * pass, prefix, mask, rank);
+        thr = prefix;
+        need_eq = rank;
+    }
+    float beta;
     int nfin;
-    block_scan(sh, nf, &nfin);
+    if (K >= 16384) ordered_compaction<4>(sh, thr, need_eq, &beta, &nfin);
+    else ordered_compaction<1>(sh, thr, need_eq, &beta, &nfin);
     if (tid == 0) {
         sbs_result* r = t.result;
         r->cost_min = beta;
-        r->ess = (float)Ke;
+        r->ess = (float)P.Ke;
         r->status = nfin > 0 ? SBS_OK : SBS_ERR_DIVERGED;
         r->n_finite = nfin;
         r->iter_lo = (uint32_t)t.iter;
