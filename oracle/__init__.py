@@ -35,6 +35,7 @@ class Params(C.Structure):
         ("sigma_init", C.c_double), ("sigma_min", C.c_double),
         ("sigma_f_init", C.c_double), ("sigma_f_min", C.c_double),
         ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ),
+        ("feet_mode", C.c_int32),
     ]
 
 
@@ -62,6 +63,8 @@ def lib():
             "orc_euler_rates": (None, [vp, vp, vp]),
             "orc_srbd_deriv": (None, [vp, vp, vp, vp, vp]),
             "orc_srbd_step": (None, [vp, vp, vp, vp, d, vp]),
+            "orc_srbd_deriv_feet": (None, [vp, vp, vp, vp, vp, vp]),
+            "orc_foothold": (None, [vp, vp, vp, u32, u32, C.c_int, vp]),
             "orc_stage_cost": (d, [vp, vp, vp, vp, vp]),
             "orc_spline_basis": (None, [C.c_int, C.c_int, d, vp]),
             "orc_spline_at": (d, [C.c_int, C.c_int, d, vp, d]),
@@ -71,17 +74,17 @@ def lib():
             "orc_naive_sets": (C.c_int, [vp, vp, vp, vp, vp, vp]),
             "orc_init_dist": (None, [vp, vp, vp, vp]),
             "orc_warm_shift": (None, [vp, vp, C.c_int, vp, vp]),
-            "orc_rollout": (None, [vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, vp, C.c_int]),
-            "orc_rollout_sample": (d, [vp, vp, vp, vp, vp, vp, vp, u64, u32, i64, vp]),
+            "orc_rollout": (None, [vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, vp, C.c_int]),
+            "orc_rollout_sample": (d, [vp, vp, vp, vp, vp, vp, vp, vp, u64, u32, i64, vp]),
             "orc_mppi": (C.c_int, [vp, vp, C.c_int, C.c_int, d, vp, vp, vp]),
             "orc_elite_select": (None, [vp, C.c_int, C.c_int, vp]),
             "orc_elite_refit": (None, [vp, C.c_int, vp, C.c_int, vp, vp, vp]),
             "orc_first_control": (None, [vp, vp, vp, vp]),
-            "orc_solve": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, u64, vp, vp, vp, vp, vp, vp, vp,
+            "orc_solve": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int, u64, vp, vp, vp, vp, vp, vp, vp,
                                     vp, C.c_int]),
             "orc_max_threads": (C.c_int, []),
-            "orc_cost_condition": (d, [vp, vp, vp, vp, vp, vp, vp, u64, u32, d, vp]),
-            "orc_cost_condition_all": (None, [vp, vp, vp, vp, vp, vp, vp, u64, d, vp, C.c_int]),
+            "orc_cost_condition": (d, [vp, vp, vp, vp, vp, vp, vp, vp, u64, u32, d, vp]),
+            "orc_cost_condition_all": (None, [vp, vp, vp, vp, vp, vp, vp, vp, u64, d, vp, C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -130,6 +133,7 @@ def make_params(cfg) -> Params:
     p.n_freq = len(fs)
     for i, f in enumerate(fs):
         p.freq_set[i] = f
+    p.feet_mode = 1 if cfg.get("world_feet") else 0
     return p
 
 
@@ -201,6 +205,30 @@ def srbd_deriv(params, x, gamma, f_ext=None):
     return out
 
 
+def srbd_deriv_feet(params, x, gamma, feet, f_ext=None):
+    """Right-hand side of Eq. (1) with world-fixed contact points (x, y) on the ground."""
+    xx, gg, ff = _f64(x, 12), _f64(gamma, 12), _f64(feet, 8)
+    fe = None if f_ext is None else _f64(f_ext, 3)
+    out = np.zeros(12)
+    lib().orc_srbd_deriv_feet(C.byref(params), _p(xx), _p(gg), _p(fe), _p(ff), _p(out))
+    return out
+
+
+def foothold(params, x, vd, q_mhz, duty, leg):
+    """Touchdown foothold (x, y) of one leg (Sec. IV-D)."""
+    xx, v = _f64(x, 12), _f64(vd, 2)
+    out = np.zeros(2)
+    lib().orc_foothold(C.byref(params), _p(xx), _p(v), q_mhz, duty, leg, _p(out))
+    return out
+
+
+def _feet(params, feet):
+    if not params.feet_mode:
+        return None
+    assert feet is not None, "world-fixed feet need the feet's ground positions at t_0"
+    return _f64(feet, 8)
+
+
 def srbd_step(params, x, gamma, dt, f_ext=None):
     xx, gg = _f64(x, 12), _f64(gamma, 12)
     fe = None if f_ext is None else _f64(f_ext, 3)
@@ -268,9 +296,10 @@ def warm_shift(params, gait, shift, mean, var):
     return mean, var
 
 
-def rollout(params, gait, x0, xref, f_ext, mean, var, it, want_theta=False, nthreads=1):
+def rollout(params, gait, x0, xref, f_ext, mean, var, it, want_theta=False, nthreads=1, feet=None):
     """Costs of all K samples of iteration `it` (Alg. 2 for each sample)."""
     K, D = params.K, dim(params)
+    ft = _feet(params, feet)
     x0 = _f64(x0, 12)
     xref = _f64(xref, 12 * params.H)
     fe = None if f_ext is None else _f64(f_ext, 3)
@@ -279,19 +308,20 @@ def rollout(params, gait, x0, xref, f_ext, mean, var, it, want_theta=False, nthr
     q = np.zeros(K, dtype=np.uint32)
     margin = np.zeros(K)
     theta = np.zeros((K, sample_dim(params))) if want_theta else None
-    lib().orc_rollout(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(mean), _p(var),
+    lib().orc_rollout(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(ft), _p(mean), _p(var),
                       it, _p(J), _p(q), _p(theta), _p(margin), nthreads)
     return J, q, theta, margin
 
 
-def rollout_sample(params, gait, x0, xref, f_ext, mean, var, it, k, q_override=-1):
+def rollout_sample(params, gait, x0, xref, f_ext, mean, var, it, k, q_override=-1, feet=None):
     D = dim(params)
+    ft = _feet(params, feet)
     x0 = _f64(x0, 12)
     xref = _f64(xref, 12 * params.H)
     fe = None if f_ext is None else _f64(f_ext, 3)
     mean, var = _f64(mean, D), _f64(var, D)
     theta = np.zeros(sample_dim(params))
-    J = lib().orc_rollout_sample(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe),
+    J = lib().orc_rollout_sample(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(ft),
                                  _p(mean), _p(var), it, k, q_override, _p(theta))
     return J, theta
 
@@ -331,9 +361,10 @@ def first_control(params, gait, mean):
     return u0
 
 
-def solve(params, gait, x0, xref, f_ext, shift, iter0, mean, var, nthreads=1):
+def solve(params, gait, x0, xref, f_ext, shift, iter0, mean, var, nthreads=1, feet=None):
     """One controller solve (Alg. 4, Alg. 1 iterated). Returns a dict."""
     K, D = params.K, dim(params)
+    ft = _feet(params, feet)
     mean = _f64(mean, D).copy()
     var = _f64(var, D).copy()
     x0 = _f64(x0, 12)
@@ -346,7 +377,7 @@ def solve(params, gait, x0, xref, f_ext, shift, iter0, mean, var, nthreads=1):
     Ke = max(1, params.elite_count, params.n_freq)
     elite = np.full(Ke, -1, dtype=np.int32)
     mppi_mean = np.zeros(D)
-    st = lib().orc_solve(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), shift, iter0,
+    st = lib().orc_solve(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(ft), shift, iter0,
                          _p(mean), _p(var), _p(u0), _p(info), _p(J), _p(q), _p(elite),
                          _p(mppi_mean), nthreads)
     return {"status": st, "mean": mean, "var": var, "u0": u0, "beta": info[0], "ess": info[1],
@@ -356,27 +387,29 @@ def solve(params, gait, x0, xref, f_ext, shift, iter0, mean, var, nthreads=1):
 EPS_FP32 = 2.0 ** -23
 
 
-def cost_condition(params, gait, x0, xref, f_ext, mean, var, it, k, eps=EPS_FP32):
+def cost_condition(params, gait, x0, xref, f_ext, mean, var, it, k, eps=EPS_FP32, feet=None):
     """Relative change of sample k's cost under rounding-sized perturbations."""
     D = dim(params)
+    ft = _feet(params, feet)
     x0 = _f64(x0, 12)
     xref = _f64(xref, 12 * params.H)
     fe = None if f_ext is None else _f64(f_ext, 3)
     mean, var = _f64(mean, D), _f64(var, D)
     J = C.c_double()
-    kap = lib().orc_cost_condition(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(mean),
+    kap = lib().orc_cost_condition(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(ft), _p(mean),
                                    _p(var), it, k, eps, C.byref(J))
     return kap, J.value
 
 
-def cost_condition_all(params, gait, x0, xref, f_ext, mean, var, it, eps=EPS_FP32, nthreads=1):
+def cost_condition_all(params, gait, x0, xref, f_ext, mean, var, it, eps=EPS_FP32, nthreads=1, feet=None):
     D = dim(params)
+    ft = _feet(params, feet)
     x0 = _f64(x0, 12)
     xref = _f64(xref, 12 * params.H)
     fe = None if f_ext is None else _f64(f_ext, 3)
     mean, var = _f64(mean, D), _f64(var, D)
     kap = np.zeros(params.K)
-    lib().orc_cost_condition_all(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(mean),
+    lib().orc_cost_condition_all(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(ft), _p(mean),
                                  _p(var), it, eps, _p(kap), nthreads)
     return kap
 

@@ -26,6 +26,7 @@
  *   Naive optimiser (best sample, covariance frozen) ... Sec. III-B, Alg. 3
  *   step frequency uniform over a discrete set, one
  *   Gaussian per frequency (Naive) ..................... Sec. V (gait optimisation), Sec. V-A
+ *   world-fixed stance feet, footholds at touchdown .... Eq. (1) (p_cf,i = p_f,i - p_c), Sec. IV-D
  *   one warm-started iteration per control tick ........ Sec. III-A
  *
  * Random numbers: Philox4x32-10 from Salmon, Moraes, Dror, Shaw, "Parallel
@@ -64,6 +65,7 @@ typedef struct {
     double sigma_init, sigma_min, sigma_f_init, sigma_f_min;
     int32_t n_freq;          /* 0, or the size of a discrete step-frequency set (Naive only) */
     uint32_t freq_set[MAX_FREQ]; /* its frequencies in mHz, distinct */
+    int32_t feet_mode;       /* 0: lever arms fixed in the body frame; 1: stance feet fixed on the ground */
 } orc_params;
 
 typedef struct {
@@ -226,9 +228,12 @@ static void cross3(const double a[3], const double b[3], double c[3])
 }
 
 /* Right-hand side of Eq. (1).  gamma: 4 legs x 3 world-frame force components,
- * already multiplied by the contact flags. f_ext: external world force (may be NULL). */
-void orc_srbd_deriv(const orc_params* P, const double x[NX], const double gamma[NU],
-                    const double* f_ext, double xdot[NX])
+ * already multiplied by the contact flags. f_ext: external world force (may be NULL).
+ * feet: NULL for lever arms fixed in the body frame (p_cf,i = foot offset i); else
+ * the world contact points (x, y) of the 4 feet on the flat ground z = 0, and
+ * p_cf,i = p_f,i - p_c, so that tau_B = R^T sum_i (p_f,i - p_c) x Gamma_i. */
+static void srbd_deriv(const orc_params* P, const double x[NX], const double gamma[NU],
+                       const double* f_ext, const double* feet, double xdot[NX])
 {
     const double* rpy = x + 3;
     const double* v = x + 6;
@@ -247,12 +252,18 @@ void orc_srbd_deriv(const orc_params* P, const double x[NX], const double gamma[
     /* rotational: tau_B = sum p_cf,i x (R^T Gamma_i); omega_dot = I^{-1}(tau_B - omega x I omega) */
     double tau[3] = {0, 0, 0};
     for (int i = 0; i < 4; ++i) {
-        double gb[3];
-        for (int r = 0; r < 3; ++r)
-            gb[r] = Rm[0 * 3 + r] * gamma[3 * i + 0] + Rm[1 * 3 + r] * gamma[3 * i + 1] +
-                    Rm[2 * 3 + r] * gamma[3 * i + 2];
+        double gb[3], r[3];
+        for (int a = 0; a < 3; ++a)
+            gb[a] = Rm[0 * 3 + a] * gamma[3 * i + 0] + Rm[1 * 3 + a] * gamma[3 * i + 1] +
+                    Rm[2 * 3 + a] * gamma[3 * i + 2];
+        if (feet) { /* body-frame lever arm R^T (p_f,i - p_c) */
+            double d[3] = {feet[2 * i] - x[0], feet[2 * i + 1] - x[1], 0.0 - x[2]};
+            for (int a = 0; a < 3; ++a) r[a] = Rm[0 * 3 + a] * d[0] + Rm[1 * 3 + a] * d[1] + Rm[2 * 3 + a] * d[2];
+        } else {
+            for (int a = 0; a < 3; ++a) r[a] = P->foot[3 * i + a];
+        }
         double t[3];
-        cross3(P->foot + 3 * i, gb, t);
+        cross3(r, gb, t);
         for (int a = 0; a < 3; ++a) tau[a] += t[a];
     }
     double Iw[3] = {P->inertia[0] * w[0], P->inertia[1] * w[1], P->inertia[2] * w[2]};
@@ -264,13 +275,51 @@ void orc_srbd_deriv(const orc_params* P, const double x[NX], const double gamma[
     for (int a = 0; a < 3; ++a) xdot[3 + a] = rates[a];
 }
 
+void orc_srbd_deriv(const orc_params* P, const double x[NX], const double gamma[NU],
+                    const double* f_ext, double xdot[NX])
+{
+    srbd_deriv(P, x, gamma, f_ext, NULL, xdot);
+}
+
+void orc_srbd_deriv_feet(const orc_params* P, const double x[NX], const double gamma[NU],
+                         const double* f_ext, const double feet[8], double xdot[NX])
+{
+    srbd_deriv(P, x, gamma, f_ext, feet, xdot);
+}
+
 /* Discrete dynamics x_{j+1} = x_j + dt * f(x_j, u_j) (explicit Euler). */
+static void srbd_step(const orc_params* P, const double x[NX], const double gamma[NU],
+                      const double* f_ext, const double* feet, double dt, double xn[NX])
+{
+    double xd[NX];
+    srbd_deriv(P, x, gamma, f_ext, feet, xd);
+    for (int c = 0; c < NX; ++c) xn[c] = x[c] + dt * xd[c];
+}
+
 void orc_srbd_step(const orc_params* P, const double x[NX], const double gamma[NU],
                    const double* f_ext, double dt, double xn[NX])
 {
-    double xd[NX];
-    orc_srbd_deriv(P, x, gamma, f_ext, xd);
-    for (int c = 0; c < NX; ++c) xn[c] = x[c] + dt * xd[c];
+    srbd_step(P, x, gamma, f_ext, NULL, dt, xn);
+}
+
+/* Foothold of leg i touching down with the body in state x (Sec. IV-D, Eq.
+ * (foothold)): p_f = p_hip + (T_st / 2) v^d + sqrt(p_c,z / g) (v_c - v^d) in the
+ * ground plane, with T_st = D_f / f_s the stance time of the sample's step
+ * frequency (q mHz, duty in 1e-9 cycle), v^d the desired planar velocity and
+ * the hip at p_c + R (foot offset x, foot offset y, 0) (the hip above the
+ * nominal foot).  A CoM below the ground counts as height 0. */
+void orc_foothold(const orc_params* P, const double x[NX], const double vd[2], uint32_t q_mhz, uint32_t duty,
+                  int leg, double out[2])
+{
+    double Rm[9];
+    orc_rotation(x + 3, Rm);
+    double h[3] = {P->foot[3 * leg], P->foot[3 * leg + 1], 0.0};
+    double Tst = ((double)duty / (double)PHASE_ONE) / (q_mhz / 1000.0);
+    double s = sqrt(fmax(x[2], 0.0) / (-P->gravity[2]));
+    for (int a = 0; a < 2; ++a) {
+        double hw = Rm[3 * a] * h[0] + Rm[3 * a + 1] * h[1] + Rm[3 * a + 2] * h[2];
+        out[a] = x[a] + hw + 0.5 * Tst * vd[a] + s * (x[6 + a] - vd[a]);
+    }
 }
 
 /* Stage cost r(u_j, x_j, x^r_j) (Sec. V): diagonal quadratic state tracking,
@@ -494,6 +543,7 @@ typedef struct {
     const double* var;
     const double* B; /* H x P spline basis, or NULL */
     uint64_t iter;
+    const double* feet0; /* feet_mode 1: (x, y) of the 4 feet at t_0 */
 } rollout_ctx;
 
 /* Sign of a perturbation: a fixed integer hash of (key, a, b) mapped to +-1.
@@ -547,10 +597,18 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
 
     double x[NX], xn[NX];
     memcpy(x, c->x0, sizeof(x));
+    double feet[8];  /* world contact points (feet_mode 1) */
+    int prev[4] = {1, 1, 1, 1};
+    if (P->feet_mode) memcpy(feet, c->feet0, sizeof(feet));
     double J = 0;
     for (int j = 0; j < H; ++j) {
         int st[4];
         for (int i = 0; i < 4; ++i) st[i] = orc_stance(c->g, i, q, P->dt_us, j);
+        if (P->feet_mode) /* a leg touching down at step j takes its foothold from x_j */
+            for (int i = 0; i < 4; ++i) {
+                if (st[i] && !prev[i]) orc_foothold(P, x, c->xref + NX * j + 6, q, c->g->duty, i, feet + 2 * i);
+                prev[i] = st[i];
+            }
         double u[NU];
         for (int n = 0; n < NU; ++n) {
             double val;
@@ -564,7 +622,7 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
             if (eps > 0) u[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j, (uint64_t)n);
         }
         J += orc_stage_cost(P, x, c->xref + NX * j, u, st);
-        orc_srbd_step(P, x, u, c->f_ext, dt, xn);
+        srbd_step(P, x, u, c->f_ext, P->feet_mode ? feet : NULL, dt, xn);
         memcpy(x, xn, sizeof(x));
         if (eps > 0)
             for (int n = 0; n < NX; ++n) x[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j + 1, (uint64_t)n);
@@ -580,7 +638,7 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
 /* Evaluate all K samples.  theta (K x sample dim) and margin (K) may be NULL.
  * nthreads > 1 runs samples in parallel (each sample is computed identically). */
 void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
-                 const double* f_ext, const double* mean, const double* var, uint64_t iter,
+                 const double* f_ext, const double* feet, const double* mean, const double* var, uint64_t iter,
                  double* J, uint32_t* q, double* theta, double* margin, int nthreads)
 {
     int D = orc_sample_dim(P);
@@ -589,7 +647,7 @@ void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const
         B = (double*)malloc(sizeof(double) * P->H * P->P);
         orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
     }
-    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter};
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter, feet};
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
     for (int k = 0; k < P->K; ++k) {
@@ -606,7 +664,7 @@ void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const
 
 /* One sample with an optional forced frequency (q_override < 0: its own). */
 double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* x0,
-                          const double* xref, const double* f_ext, const double* mean,
+                          const double* xref, const double* f_ext, const double* feet, const double* mean,
                           const double* var, uint64_t iter, uint32_t k, int64_t q_override,
                           double* theta)
 {
@@ -615,7 +673,7 @@ double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* 
         B = (double*)malloc(sizeof(double) * P->H * P->P);
         orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
     }
-    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter};
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter, feet};
     double J = rollout_one(&c, k, q_override, theta, NULL, NULL);
     free(B);
     return J;
@@ -628,7 +686,7 @@ double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* 
  * perturbations cannot be reproduced to that tolerance by any single-precision
  * evaluation; such samples are ill-conditioned. */
 double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
-                          const double* f_ext, const double* mean, const double* var, uint64_t iter,
+                          const double* f_ext, const double* feet, const double* mean, const double* var, uint64_t iter,
                           uint32_t k, double eps, double* J_out)
 {
     double* B = NULL;
@@ -636,7 +694,7 @@ double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* 
         B = (double*)malloc(sizeof(double) * P->H * P->P);
         orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
     }
-    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter};
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter, feet};
     double* th = (double*)malloc(sizeof(double) * orc_dim(P));
     uint32_t q;
     double J = rollout_core(&c, k, -1, th, &q, NULL, 0.0, 0);
@@ -657,13 +715,13 @@ double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* 
 
 /* Conditioning of all K samples (parallel over samples). */
 void orc_cost_condition_all(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
-                            const double* f_ext, const double* mean, const double* var, uint64_t iter,
-                            double eps, double* kappa, int nthreads)
+                            const double* f_ext, const double* feet, const double* mean, const double* var,
+                            uint64_t iter, double eps, double* kappa, int nthreads)
 {
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
     for (int k = 0; k < P->K; ++k)
-        kappa[k] = orc_cost_condition(P, g, x0, xref, f_ext, mean, var, iter, (uint32_t)k, eps, NULL);
+        kappa[k] = orc_cost_condition(P, g, x0, xref, f_ext, feet, mean, var, iter, (uint32_t)k, eps, NULL);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -787,6 +845,7 @@ void orc_first_control(const orc_params* P, const orc_gait* g, const double* mea
 
 /* ------------------------------------------------------------------------- */
 /* One solve (Alg. 4 with Alg. 1 repeated `iterations` times): warm shift,    */
+/* (feet: the 4 feet's ground (x, y) at t_0 for feet_mode 1, else NULL)       */
 /* then per iteration sample / evaluate / sort / update.  The distribution     */
 /* (mean, var) is updated in place; iter0 is the Philox iteration counter of   */
 /* the first iteration (iteration i uses iter0 + i).                           */
@@ -799,7 +858,7 @@ void orc_first_control(const orc_params* P, const orc_gait* g, const double* mea
 /* the last iteration has no finite cost).                                     */
 /* ------------------------------------------------------------------------- */
 int orc_solve(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
-              const double* f_ext, int shift, uint64_t iter0, double* mean, double* var, double* u0,
+              const double* f_ext, const double* feet, int shift, uint64_t iter0, double* mean, double* var, double* u0,
               double* info, double* J_last, uint32_t* q_last, int32_t* elite_last,
               double* mppi_mean, int nthreads)
 {
@@ -815,7 +874,7 @@ int orc_solve(const orc_params* P, const orc_gait* g, const double* x0, const do
     int status = ORC_OK, bstar = 0;
     double beta = INFINITY, ess = 0;
     for (int it = 0; it < P->iterations; ++it) {
-        orc_rollout(P, g, x0, xref, f_ext, mean, var, iter0 + (uint64_t)it, J, q, theta, NULL, nthreads);
+        orc_rollout(P, g, x0, xref, f_ext, feet, mean, var, iter0 + (uint64_t)it, J, q, theta, NULL, nthreads);
         double b = INFINITY;
         for (int k = 0; k < K; ++k)
             if (J[k] < b) b = J[k];

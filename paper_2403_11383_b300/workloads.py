@@ -98,10 +98,15 @@ def config(name: str) -> dict:
         # force Gaussian per frequency, Naive optimiser, regulariser towards 1.3 Hz
         return _cfg(K=10_000, H=12, seed=5, method="naive", q_init=1300,
                     freq_set_mhz=(1300, 2000, 2400), v_ref=(0.5, 0.0))
+    if name == "worldfeet_mppi_k4096_h25":
+        # stance feet fixed on the ground with footholds placed at touchdown
+        # (Sec. IV-D) over a 0.5 s horizon: every leg touches down at least once
+        return _cfg(K=4096, H=25, seed=6, world_feet=True, v_ref=(0.5, 0.0))
     raise KeyError(name)
 
 
-SINGLE = ("plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100", "naive_freqset_k10000_h12")
+SINGLE = ("plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100", "naive_freqset_k10000_h12",
+          "worldfeet_mppi_k4096_h25")
 
 
 def initial_state(rng: np.random.Generator, z: float = 0.30) -> np.ndarray:
@@ -125,6 +130,13 @@ def reference(H: int, dt_us: int, x0: np.ndarray, v_ref, z_ref: float = 0.30) ->
     return xr
 
 
+def initial_feet(rng: np.random.Generator, x0: np.ndarray, model: dict = MODEL) -> np.ndarray:
+    """Ground (x, y) of the 4 feet at t_0: under the nominal foot offsets from the
+    CoM, plus U(-0.02, 0.02) m per coordinate (a robot mid-stride)."""
+    off = np.asarray(model["foot"], dtype=np.float64)[:, :2]
+    return (x0[None, :2] + off + rng.uniform(-0.02, 0.02, size=(4, 2))).ravel()
+
+
 def gait(name: str, phase0: int) -> dict:
     g = GAITS[name]
     return {"offset": tuple(g["offset"]), "duty": g["duty"], "phase0": int(phase0) % PHASE_ONE}
@@ -135,12 +147,15 @@ def problem(cfg: dict, seed: int | None = None) -> dict:
     rng = np.random.default_rng(cfg["seed"] if seed is None else seed)
     x0 = initial_state(rng, cfg["z_ref"])
     phase0 = int(rng.integers(0, PHASE_ONE))
-    return {
+    out = {
         "x0": x0,
         "xref": reference(cfg["H"], cfg["dt_us"], x0, cfg["v_ref"], cfg["z_ref"]),
         "gait": gait(cfg["gait"], phase0),
         "f_ext": np.asarray(cfg["f_ext"], dtype=np.float64),
     }
+    if cfg.get("world_feet"):
+        out["feet"] = initial_feet(rng, x0, cfg["model"])
+    return out
 
 
 def batch_mix(n: int = 256, seed: int = 2, Ks=(256, 1024, 4096, 16384), Hs=(10, 25, 50),
