@@ -137,6 +137,14 @@ typedef struct sbs_config {
      * are then unused (each block's nominal schedule uses its own frequency). */
     int32_t n_freq;
     uint32_t freq_set[SBS_MAX_FREQ]; /* mHz, distinct, 1..10000 */
+    /* 0: the foot lever arms are the body-frame offsets model.foot (fixed to the
+     * body).  1: stance feet stay fixed on the flat ground z = 0 and the lever arm
+     * of leg i is p_f,i - p_c (Eq. (1)); a leg touching down inside the horizon
+     * lands at the foothold of Sec. IV-D, p_hip + (T_st / 2) v^d + sqrt(p_c,z / g)
+     * (v_c - v^d), with the hip at R (foot x, foot y, 0) from the CoM, T_st the
+     * stance time of the sample's frequency and v^d the reference's planar
+     * velocity at that step.  sbs_problem.feet gives the feet at t_0. */
+    int32_t world_feet;
 } sbs_config;
 
 /* Periodic gait (Sec. IV-C): leg i is in stance while its phase
@@ -160,6 +168,8 @@ typedef struct sbs_problem {
     sbs_gait gait;
     int32_t shift;      /* warm start: steps elapsed since the previous solve (0 = none) */
     int32_t host_memory;
+    const float* feet;  /* world_feet: [4][2] ground (x, y) of the feet at t_0 (legs FL, FR, RL, RR; a
+                           leg in stance at t_0 stays there until it lifts off); else NULL */
 } sbs_problem;
 
 /* Result of a solve, written by the device. */

@@ -64,6 +64,8 @@ int validate_config(const sbs_config* c)
     for (int i = 0; i < 3; ++i)
         if (k.R[i] < 0) return SBS_ERR_INVALID_ARG;
     if (!(k.w_fc >= 0) || !(k.mu >= 0) || !(k.rho >= 0) || !std::isfinite(k.f_nominal)) return SBS_ERR_INVALID_ARG;
+    if (c->world_feet != 0 && c->world_feet != 1) return SBS_ERR_INVALID_ARG;
+    if (c->world_feet && !(m.gravity[2] < 0.0f)) return SBS_ERR_INVALID_ARG;  // the foothold rule needs g_z < 0
     // discrete step-frequency set (Naive only): distinct values, each advancing the
     // phase by less than one cycle per step
     if (c->n_freq < 0 || c->n_freq > SBS_MAX_FREQ) return SBS_ERR_INVALID_ARG;
@@ -107,6 +109,8 @@ void fill_params(const sbs_config* cfg, InstParams* out)
     P.nb = cfg->n_freq > 0 ? cfg->n_freq : 1;
     for (int i = 0; i < cfg->n_freq; ++i) P.freq[i] = cfg->freq_set[i];
     P.D = P.nb * P.nf + P.adaptive;
+    P.world_feet = cfg->world_feet;
+    P.inv_g = cfg->world_feet ? 1.0f / -cfg->model.gravity[2] : 0.0f;
     P.method = cfg->method;
     P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
     P.T = cfg->tile ? cfg->tile : 128;
@@ -292,7 +296,7 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     const size_t o_B = take(P.P > 0 ? (size_t)P.H * P.P * sizeof(float) : 0);
     const size_t o_S = take(P.P > 0 ? (size_t)P.P * P.P * sizeof(float) : 0);
     const size_t o_res = take(sizeof(sbs_result));
-    const size_t in_floats = 16 + 12 * (size_t)P.H;
+    const size_t in_floats = 24 + 12 * (size_t)P.H;  // x0 | f_ext | pad | feet | xref
     const size_t o_in = take(in_floats * sizeof(float));
     h->dev_bytes = off;
     h->dev_base = (char*)dev_alloc(&h->alloc, h->has_alloc, off);
@@ -393,6 +397,7 @@ int sbs_prepare(sbs_handle* h) { return h ? ensure_workspace(h) : SBS_ERR_INVALI
 int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* stream)
 {
     if (!h || !prob || !result || !prob->x0 || !prob->xref) return SBS_ERR_INVALID_ARG;
+    if (h->hP.world_feet && !prob->feet) return SBS_ERR_INVALID_ARG;
     int st = validate_gait(&prob->gait);
     if (st) return st;
     const InstParams& P = h->hP;
@@ -401,25 +406,29 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
     st = ensure_workspace(h);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const float *x0 = prob->x0, *xref = prob->xref, *fext = prob->f_ext;
+    const float *x0 = prob->x0, *xref = prob->xref, *fext = prob->f_ext, *feet = prob->feet;
     sbs_result* res = result;
     if (prob->host_memory) {
-        if (!finite_all(x0, 12) || !finite_all(xref, 12 * P.H) || (fext && !finite_all(fext, 3)))
+        if (!finite_all(x0, 12) || !finite_all(xref, 12 * P.H) || (fext && !finite_all(fext, 3)) ||
+            (P.world_feet && !finite_all(feet, 8)))
             return SBS_ERR_INVALID_ARG;
         if (h->in_pending && cudaEventSynchronize((cudaEvent_t)h->in_done) != cudaSuccess) return SBS_ERR_CUDA;
         std::memcpy(h->pin_in, x0, 12 * sizeof(float));
         if (fext) std::memcpy(h->pin_in + 12, fext, 3 * sizeof(float));
         else std::memset(h->pin_in + 12, 0, 3 * sizeof(float));
         h->pin_in[15] = 0.0f;
-        std::memcpy(h->pin_in + 16, xref, 12 * (size_t)P.H * sizeof(float));
-        if (cudaMemcpyAsync(h->dev_in, h->pin_in, (16 + 12 * (size_t)P.H) * sizeof(float), cudaMemcpyHostToDevice,
+        if (P.world_feet) std::memcpy(h->pin_in + 16, feet, 8 * sizeof(float));
+        else std::memset(h->pin_in + 16, 0, 8 * sizeof(float));
+        std::memcpy(h->pin_in + 24, xref, 12 * (size_t)P.H * sizeof(float));
+        if (cudaMemcpyAsync(h->dev_in, h->pin_in, (24 + 12 * (size_t)P.H) * sizeof(float), cudaMemcpyHostToDevice,
                             s) != cudaSuccess)
             return SBS_ERR_CUDA;
         if (cudaEventRecord((cudaEvent_t)h->in_done, s) != cudaSuccess) return SBS_ERR_CUDA;
         h->in_pending = true;
         x0 = h->dev_in;
         fext = h->dev_in + 12;
-        xref = h->dev_in + 16;
+        feet = P.world_feet ? h->dev_in + 16 : nullptr;
+        xref = h->dev_in + 24;
         res = h->res_dev;
     }
     int shift = prob->shift;
@@ -435,6 +444,7 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         t.x0 = x0;
         t.xref = xref;
         t.fext = fext;
+        t.feet = feet;
         t.shift = it == 0 ? shift : 0;
         t.partials = (P.method == SBS_MPPI || (P.compare_mppi && it == 0)) ? 1 : 0;
         t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
@@ -786,7 +796,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     if (!handles[0]) return SBS_ERR_INVALID_ARG;
     const int T = handles[0]->hP.T;
     const int Pk = handles[0]->hP.P;
-    bool sets = false;  // some controller draws from a discrete frequency set
+    bool ext = false;  // some controller uses an extended model feature
     size_t smem = 0, sel_smem = 0, arena = 0;
     long long counters = 0;
     std::vector<int> order(n);
@@ -794,10 +804,11 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         const sbs_handle* h = handles[i];
         const sbs_problem* p = &probs[i];
         if (!h || !p->x0 || !p->xref || p->host_memory || h->hP.T != T || h->hP.P != Pk) return SBS_ERR_INVALID_ARG;
+        if (h->hP.world_feet && !p->feet) return SBS_ERR_INVALID_ARG;
         if (h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
         smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb));
-        sets = sets || h->hP.n_freq > 0;
+        ext = ext || h->hP.n_freq > 0 || h->hP.world_feet;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
         arena += align_up(h->wsl.bytes, 256);
         counters += h->wsl.counters;
@@ -842,6 +853,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         R.t.x0 = probs[i].x0;
         R.t.xref = probs[i].xref;
         R.t.fext = probs[i].f_ext;
+        R.t.feet = probs[i].feet;
         R.t.shift = h->initialized ? probs[i].shift : 0;
         R.t.partials = (P.method == SBS_MPPI || P.compare_mppi) ? 1 : 0;
         R.t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
@@ -867,7 +879,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     const size_t used = 16 + (size_t)n * sizeof(InstRec);
     const int mode = b->mode;
     int grids[3];
-    const int var = rollout_variant(Pk, sets);
+    const int var = rollout_variant(Pk, ext);
     int st = batch_grid(var, mode, smem, sel_smem, T, counts, grids);
     if (st) return st;
     const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_var != var ||

@@ -234,6 +234,41 @@ __device__ __forceinline__ void angle_sincos(float a, float* s, float* c)
     else __sincosf(a, s, c);
 }
 
+// The rotational and translational rates of Eq. (1) from the net force F and
+// body-frame moment t, then the explicit Euler step of all 12 states.
+__device__ __forceinline__ void srbd_integrate(const InstParams& P, float x[12], float sr, float cr, float sp,
+                                               float cp, float F0, float F1, float F2, float t0, float t1,
+                                               float t2, const float fe[3])
+{
+    const float w0 = x[9], w1 = x[10], w2 = x[11];
+    const float L0 = P.inertia[0] * w0, L1 = P.inertia[1] * w1, L2 = P.inertia[2] * w2;
+    const float wd0 = (t0 - (w1 * L2 - w2 * L1)) * P.inv_inertia[0];
+    const float wd1 = (t1 - (w2 * L0 - w0 * L2)) * P.inv_inertia[1];
+    const float wd2 = (t2 - (w0 * L1 - w1 * L0)) * P.inv_inertia[2];
+    // E'^{-1}(Phi) omega for the ZYX angles
+    const float ic = __frcp_rn(cp);
+    const float a = sr * w1 + cr * w2;
+    const float rd = w0 + sp * ic * a;
+    const float pd = cr * w1 - sr * w2;
+    const float yd = a * ic;
+    const float dt = P.dt;
+    const float vd0 = fmaf(F0 + fe[0], P.inv_mass, P.gravity[0]);
+    const float vd1 = fmaf(F1 + fe[1], P.inv_mass, P.gravity[1]);
+    const float vd2 = fmaf(F2 + fe[2], P.inv_mass, P.gravity[2]);
+    x[0] = fmaf(dt, x[6], x[0]);
+    x[1] = fmaf(dt, x[7], x[1]);
+    x[2] = fmaf(dt, x[8], x[2]);
+    x[3] = fmaf(dt, rd, x[3]);
+    x[4] = fmaf(dt, pd, x[4]);
+    x[5] = fmaf(dt, yd, x[5]);
+    x[6] = fmaf(dt, vd0, x[6]);
+    x[7] = fmaf(dt, vd1, x[7]);
+    x[8] = fmaf(dt, vd2, x[8]);
+    x[9] = fmaf(dt, wd0, w0);
+    x[10] = fmaf(dt, wd1, w1);
+    x[11] = fmaf(dt, wd2, w2);
+}
+
 __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], const float G[12],
                                           const float fe[3], unsigned live = 0xfu)
 {
@@ -262,33 +297,55 @@ __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], cons
         t1 += rz * bx - rx * bz;
         t2 += rx * by - ry * bx;
     }
-    const float w0 = x[9], w1 = x[10], w2 = x[11];
-    const float L0 = P.inertia[0] * w0, L1 = P.inertia[1] * w1, L2 = P.inertia[2] * w2;
-    const float wd0 = (t0 - (w1 * L2 - w2 * L1)) * P.inv_inertia[0];
-    const float wd1 = (t1 - (w2 * L0 - w0 * L2)) * P.inv_inertia[1];
-    const float wd2 = (t2 - (w0 * L1 - w1 * L0)) * P.inv_inertia[2];
-    // E'^{-1}(Phi) omega for the ZYX angles
-    const float ic = __frcp_rn(cp);
-    const float a = sr * w1 + cr * w2;
-    const float rd = w0 + sp * ic * a;
-    const float pd = cr * w1 - sr * w2;
-    const float yd = a * ic;
-    const float dt = P.dt;
-    const float vd0 = fmaf(F0 + fe[0], P.inv_mass, P.gravity[0]);
-    const float vd1 = fmaf(F1 + fe[1], P.inv_mass, P.gravity[1]);
-    const float vd2 = fmaf(F2 + fe[2], P.inv_mass, P.gravity[2]);
-    x[0] = fmaf(dt, x[6], x[0]);
-    x[1] = fmaf(dt, x[7], x[1]);
-    x[2] = fmaf(dt, x[8], x[2]);
-    x[3] = fmaf(dt, rd, x[3]);
-    x[4] = fmaf(dt, pd, x[4]);
-    x[5] = fmaf(dt, yd, x[5]);
-    x[6] = fmaf(dt, vd0, x[6]);
-    x[7] = fmaf(dt, vd1, x[7]);
-    x[8] = fmaf(dt, vd2, x[8]);
-    x[9] = fmaf(dt, wd0, w0);
-    x[10] = fmaf(dt, wd1, w1);
-    x[11] = fmaf(dt, wd2, w2);
+    srbd_integrate(P, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
+}
+
+// The same step with stance feet fixed on the ground z = 0: the lever arm of leg
+// i is p_f,i - p_c, so the body moment is R^T sum_i (p_f,i - p_c) x Gamma_i
+// (fx, fy: the feet's ground positions).  Legs in touch land at this step: they
+// first take the foothold of the pre-step state (Sec. IV-D), the hip R (foot x,
+// foot y, 0) from the CoM plus tsh v^d + sqrt(p_c,z / g) (v_c - v^d), with
+// tsh = T_st / 2 and (vdx, vdy) the desired planar velocity.
+__device__ __forceinline__ void srbd_step_world(const InstParams& P, float x[12], const float G[12],
+                                                const float fe[3], unsigned live, float fx[4], float fy[4],
+                                                unsigned touch, float vdx, float vdy, float tsh)
+{
+    float sr, cr, sp, cp, sy, cy;
+    angle_sincos(x[3], &sr, &cr);
+    angle_sincos(x[4], &sp, &cp);
+    angle_sincos(x[5], &sy, &cy);
+    const float R00 = cy * cp, R01 = cy * sp * sr - sy * cr, R02 = cy * sp * cr + sy * sr;
+    const float R10 = sy * cp, R11 = sy * sp * sr + cy * cr, R12 = sy * sp * cr - cy * sr;
+    const float R20 = -sp, R21 = cp * sr, R22 = cp * cr;
+    if (touch) {
+        const float s = sqrtf(fmaxf(x[2], 0.0f) * P.inv_g);
+        const float ax = fmaf(s, x[6] - vdx, tsh * vdx), ay = fmaf(s, x[7] - vdy, tsh * vdy);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (touch & (1u << i)) {
+                const float hx = P.foot[3 * i], hy = P.foot[3 * i + 1];
+                fx[i] = x[0] + (R00 * hx + R01 * hy) + ax;
+                fy[i] = x[1] + (R10 * hx + R11 * hy) + ay;
+            }
+        }
+    }
+    float F0 = 0.f, F1 = 0.f, F2 = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;  // u: world moment
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!(live & (1u << i))) continue;
+        const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
+        F0 += gx;
+        F1 += gy;
+        F2 += gz;
+        const float dx = fx[i] - x[0], dy = fy[i] - x[1], dz = -x[2];
+        u0 += dy * gz - dz * gy;
+        u1 += dz * gx - dx * gz;
+        u2 += dx * gy - dy * gx;
+    }
+    const float t0 = R00 * u0 + R10 * u1 + R20 * u2;
+    const float t1 = R01 * u0 + R11 * u1 + R21 * u2;
+    const float t2 = R02 * u0 + R12 * u1 + R22 * u2;
+    srbd_integrate(P, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,7 +29,9 @@ struct InstParams {
     int32_t n_freq;       // discrete step-frequency set size (0: none)
     int32_t nb;           // force blocks of the distribution: n_freq, else 1
     uint32_t freq[SBS_MAX_FREQ];  // the set, mHz
-    int32_t pad1[3];
+    int32_t world_feet;   // 1: stance feet fixed on the ground, footholds at touchdown
+    float inv_g;          // 1 / |g_z| (foothold rule)
+    int32_t pad1;
     uint32_t dt_us, q_init, seed, ctrl;
     float dt, lambda, inv_lambda, inv_mass, weight_z;
     float inertia[3], inv_inertia[3], foot[12], gravity[3];
@@ -61,6 +63,7 @@ struct TickArgs {
     const float* x0;
     const float* xref;
     const float* fext;   // may be null
+    const float* feet;   // world_feet: [4][2] ground (x, y) of the feet at t_0
     uint32_t offset[4];
     uint32_t duty, phase0;
     int32_t shift;       // warm-start shift applied while staging (first iteration only)
@@ -80,7 +83,7 @@ struct InstRec {
     int32_t tile_begin;
     int32_t select_begin;
     int32_t refit_begin;
-    int32_t pad[3];
+    int32_t pad[1];
 };
 
 static_assert(sizeof(InstRec) % 16 == 0, "InstRec must be a multiple of 16 bytes");
@@ -168,11 +171,11 @@ int validate_gait(const sbs_gait* g);
 void fill_params(const sbs_config* cfg, InstParams* out);
 
 // Rollout kernel variant of a launch: the policy's knot count (0: per-step
-// forces), plus kSetsVariant when a controller of the launch draws its step
-// frequency from a discrete set.  The batched launchers take a variant where
-// they say P.
-constexpr int kSetsVariant = 256;
-inline int rollout_variant(int P, bool sets) { return P | (sets ? kSetsVariant : 0); }
+// forces), plus kExtVariant when a controller of the launch uses an extended
+// model feature (a discrete step-frequency set, stance feet fixed on the
+// ground).  The batched launchers take a variant where they say P.
+constexpr int kExtVariant = 256;
+inline int rollout_variant(int P, bool ext) { return P | (ext ? kExtVariant : 0); }
 
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
@@ -207,7 +210,7 @@ struct sbs_handle {
     sbs::WsLayout wsl;     // layout of one solve's workspace
     sbs::Workspace ws;     // the handle's own workspace (plain solves), allocated on first use
     char* ws_base;         // its allocation (null until the first plain solve)
-    float* dev_in;         // device staging of host inputs: x0 (12) | f_ext (3) | pad | xref (12 H)
+    float* dev_in;         // device staging of host inputs: x0 (12) | f_ext (3) | pad | feet (8) | xref (12 H)
     sbs_result* res_dev;   // device result for host-memory solves
     float* pin_in;         // pinned host staging of inputs
     void* in_done;         // cudaEvent_t: last copy out of pin_in has run

@@ -31,6 +31,7 @@ struct __align__(16) BlockShared {
     TickArgs t;
     float x0[12];
     float fe[3];
+    float feet[8];
     float mu_f, var_f, sig_f;
     float red[32][4];
     int item;
@@ -173,6 +174,7 @@ __device__ void stage(BlockShared& sh, const Views& v, int P_knots)
 
     if (threadIdx.x < 12) sh.x0[threadIdx.x] = t.x0[threadIdx.x];
     if (threadIdx.x < 3) sh.fe[threadIdx.x] = t.fext ? t.fext[threadIdx.x] : 0.0f;
+    if (threadIdx.x < 8) sh.feet[threadIdx.x] = P.world_feet ? t.feet[threadIdx.x] : 0.0f;
     if (threadIdx.x == 0) {
         if (P.adaptive) {
             sh.mu_f = sm[P.D - 1];
@@ -346,12 +348,14 @@ __device__ void mppi_finish(BlockShared& sh, const Views& v, const float* row, b
 
 // ---------------------------------------------------------------------------
 // One tile of T samples.  NP = 0: per-step forces; NP > 0: NP spline knots.
-// SETS: the launch may hold controllers that draw their step frequency from a
-// discrete set; each of their samples reads the force Gaussian of its draw.
-// Without it every sample reads block 0 at addresses uniform across the warp
-// (a separate instantiation: per-thread addressing costs the common case ~3 %).
+// EXT: the launch may hold controllers with the extended model features: a
+// discrete step-frequency set (each sample reads the force Gaussian of its
+// draw) or stance feet fixed on the ground (per-sample footholds).  Without it
+// every sample reads block 0 at addresses uniform across the warp and uses the
+// body-fixed lever arms (a separate instantiation: per-thread addressing alone
+// costs the common case ~3 %).
 // ---------------------------------------------------------------------------
-template <int NP, bool SETS>
+template <int NP, bool EXT>
 __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
 {
     const InstParams& P = sh.P;
@@ -370,7 +374,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     int blk = 0;  // force block: the sample's entry of a discrete frequency set
     if (P.adaptive) {
         q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
-    } else if constexpr (SETS) {
+    } else if constexpr (EXT) {
         if (P.n_freq > 0) {
             blk = freq_block(k, iter, seed, ctrl, P.n_freq);
             q = P.freq[blk];
@@ -391,6 +395,18 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
     }
     const uint32_t step = q * P.dt_us;
     const uint32_t duty = t.duty;
+    // world-fixed feet: ground positions, last step's stance flags, T_st / 2
+    float fx[4], fy[4];
+    unsigned prev = 0xfu;  // legs in stance at t_0 keep the given feet
+    float tsh = 0.0f;
+    if constexpr (EXT) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            fx[i] = sh.feet[2 * i];
+            fy[i] = sh.feet[2 * i + 1];
+        }
+        tsh = (0.5e-6f * (float)duty) / (float)q;
+    }
 
     constexpr int NQ = NP > 0 ? (NP + 3) / 4 : 1;
     if constexpr (NP > 0) {
@@ -462,7 +478,17 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         // the spline kernel runs faster without the branches)
         const unsigned live = NP == 0 ? __reduce_or_sync(kFull, st) : 0xfu;
         kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live));
-        srbd_step(P, x, G, fe, live);
+        if constexpr (EXT) {
+            if (P.world_feet) {
+                const unsigned touch = st & ~prev;  // legs landing at this step
+                prev = st;
+                srbd_step_world(P, x, G, fe, live, fx, fy, touch, v.xr[12 * j + 6], v.xr[12 * j + 7], tsh);
+            } else {
+                srbd_step(P, x, G, fe, live);
+            }
+        } else {
+            srbd_step(P, x, G, fe, live);
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             ph[i] += step;
@@ -1190,7 +1216,7 @@ __device__ void refit_block(BlockShared& sh, int b)
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-template <int NP, bool SETS>
+template <int NP, bool EXT>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __restrict__ dP, TickArgs t)
 {
     extern __shared__ float4 dyn4[];
@@ -1198,7 +1224,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __re
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    rollout_tile<NP, SETS>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
+    rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -1253,7 +1279,7 @@ __device__ __forceinline__ int find_rec(const InstRec* recs, int n, int it, int 
 
 // counts = {controllers, tile items, selection items, refit items}; heads = queue heads.
 // Every controller of one launch uses the same policy (NP).
-template <int NP, bool SETS>
+template <int NP, bool EXT>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* __restrict__ recs,
                                                                 const int* __restrict__ counts, int* heads)
 {
@@ -1269,14 +1295,14 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* _
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
-        rollout_tile<NP, SETS>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+        rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
         __syncthreads();
     }
 }
 
 // One block per item: the hardware block scheduler is the queue (items are
 // dispatched in index order, heavy controllers first).  Unused blocks exit.
-template <int NP, bool SETS>
+template <int NP, bool EXT>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __restrict__ recs,
                                                                const int* __restrict__ counts)
 {
@@ -1288,7 +1314,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
-    rollout_tile<NP, SETS>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+    rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* __restrict__ recs,
@@ -1454,14 +1480,14 @@ static const void* batch_rollout_fn_s(int P, int mode)
 
 static const void* rollout_kernel(int variant)
 {
-    const int P = variant & ~kSetsVariant;
-    return (variant & kSetsVariant) ? rollout_kernel_s<true>(P) : rollout_kernel_s<false>(P);
+    const int P = variant & ~kExtVariant;
+    return (variant & kExtVariant) ? rollout_kernel_s<true>(P) : rollout_kernel_s<false>(P);
 }
 
 const void* batch_rollout_fn(int variant, int mode)
 {
-    const int P = variant & ~kSetsVariant;
-    return (variant & kSetsVariant) ? batch_rollout_fn_s<true>(P, mode) : batch_rollout_fn_s<false>(P, mode);
+    const int P = variant & ~kExtVariant;
+    return (variant & kExtVariant) ? batch_rollout_fn_s<true>(P, mode) : batch_rollout_fn_s<false>(P, mode);
 }
 
 const void* batch_select_fn(int mode)
@@ -1484,7 +1510,7 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb);
-    const void* fn = rollout_kernel(rollout_variant(hP.P, hP.n_freq > 0));
+    const void* fn = rollout_kernel(rollout_variant(hP.P, hP.n_freq > 0 || hP.world_feet));
     if (!fn) return SBS_ERR_INVALID_ARG;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;

@@ -31,7 +31,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kInFloats = 16 + 12 * SBS_MAX_H;  // x0 | f_ext | pad | xref, per request
+constexpr int kInFloats = 24 + 12 * SBS_MAX_H;  // x0 | f_ext | pad | feet | xref, per request
 
 struct Request {
     uint64_t ticket;
@@ -39,10 +39,11 @@ struct Request {
     sbs_gait gait;
     int32_t shift;
     bool has_fext;
+    bool has_feet;
     int H;
     size_t ws;
     Clock::time_point t_submit;
-    std::vector<float> in;  // 16 + 12 H floats
+    std::vector<float> in;  // 24 + 12 H floats
 };
 
 struct Slot {
@@ -176,7 +177,8 @@ int issue(sbs_server* s, Slot& sl)
         std::memset(&p, 0, sizeof(p));
         p.x0 = base;
         p.f_ext = r.has_fext ? base + 12 : nullptr;
-        p.xref = base + 16;
+        p.feet = r.has_feet ? base + 16 : nullptr;
+        p.xref = base + 24;
         p.gait = r.gait;
         p.shift = r.shift;
         p.host_memory = 0;
@@ -346,18 +348,21 @@ extern "C" int sbs_server_submit(sbs_server* s, int n, sbs_handle* const* handle
         const int H = h->hP.H;
         if (!finite_n(p->x0, 12) || !finite_n(p->xref, 12 * H) || (p->f_ext && !finite_n(p->f_ext, 3)))
             return SBS_ERR_INVALID_ARG;
+        if (h->hP.world_feet && (!p->feet || !finite_n(p->feet, 8))) return SBS_ERR_INVALID_ARG;
         if (!s->cfg.plain && h->wsl.bytes + 256 > s->slot_budget) return SBS_ERR_BUDGET;
         Request& r = reqs[i];
         r.h = h;
         r.gait = p->gait;
         r.shift = p->shift;
         r.has_fext = p->f_ext != nullptr;
+        r.has_feet = h->hP.world_feet != 0;
         r.H = H;
         r.ws = h->wsl.bytes;
-        r.in.assign(16 + 12 * (size_t)H, 0.0f);
+        r.in.assign(24 + 12 * (size_t)H, 0.0f);
         std::memcpy(r.in.data(), p->x0, 12 * sizeof(float));
         if (p->f_ext) std::memcpy(r.in.data() + 12, p->f_ext, 3 * sizeof(float));
-        std::memcpy(r.in.data() + 16, p->xref, 12 * (size_t)H * sizeof(float));
+        if (r.has_feet) std::memcpy(r.in.data() + 16, p->feet, 8 * sizeof(float));
+        std::memcpy(r.in.data() + 24, p->xref, 12 * (size_t)H * sizeof(float));
     }
     {
         std::lock_guard<std::mutex> lock(s->mu);

@@ -61,6 +61,7 @@ extern "C" int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* p
     if (cfg->method != SBS_MPPI || cfg->P != 0 || cfg->iterations != 1) return SBS_ERR_INVALID_ARG;
     if (!prob || prob->host_memory || !prob->x0 || !prob->xref || !state_in || !state_out || !result)
         return SBS_ERR_INVALID_ARG;
+    if (cfg->world_feet && !prob->feet) return SBS_ERR_INVALID_ARG;
     if ((const void*)state_in == (const void*)state_out || prob->shift < 0) return SBS_ERR_INVALID_ARG;
     st = validate_gait(&prob->gait);
     if (st) return st;
@@ -98,6 +99,7 @@ extern "C" int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* p
     t.x0 = prob->x0;
     t.xref = prob->xref;
     t.fext = prob->f_ext;
+    t.feet = prob->feet;
     for (int i = 0; i < 4; ++i) t.offset[i] = prob->gait.offset[i];
     t.duty = prob->gait.duty;
     t.phase0 = prob->gait.phase0;

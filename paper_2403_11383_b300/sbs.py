@@ -41,7 +41,7 @@ class Config(C.Structure):
                 ("f_min", C.c_float), ("f_max", C.c_float), ("sigma_init", C.c_float),
                 ("sigma_min", C.c_float), ("sigma_f_init", C.c_float), ("sigma_f_min", C.c_float),
                 ("tile", C.c_int32), ("model", Model), ("cost", Cost),
-                ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ)]
+                ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ), ("world_feet", C.c_int32)]
 
 
 class Gait(C.Structure):
@@ -50,7 +50,7 @@ class Gait(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("x0", C.c_void_p), ("xref", C.c_void_p), ("f_ext", C.c_void_p), ("gait", Gait),
-                ("shift", C.c_int32), ("host_memory", C.c_int32)]
+                ("shift", C.c_int32), ("host_memory", C.c_int32), ("feet", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -75,7 +75,8 @@ class ServerStats(C.Structure):
 
 # numpy views of the ABI records, for vectorised marshalling of many requests
 PROBLEM_DTYPE = np.dtype([("x0", "<u8"), ("xref", "<u8"), ("f_ext", "<u8"), ("offset", "<u4", (4,)),
-                          ("duty", "<u4"), ("phase0", "<u4"), ("shift", "<i4"), ("host_memory", "<i4")])
+                          ("duty", "<u4"), ("phase0", "<u4"), ("shift", "<i4"), ("host_memory", "<i4"),
+                          ("feet", "<u8")])
 RESULT_DTYPE = np.dtype([("u0", "<f4", (12,)), ("cost_min", "<f4"), ("ess", "<f4"), ("f_mean", "<f4"),
                          ("q_freq", "<i4"), ("status", "<i4"), ("n_finite", "<i4"), ("iter_lo", "<u4"),
                          ("iter_hi", "<u4")])
@@ -196,6 +197,7 @@ def make_config(cfg: dict, tile: int = 0) -> Config:
     c.n_freq = len(fs)
     for i, f in enumerate(fs[:MAX_FREQ]):
         c.freq_set[i] = f
+    c.world_feet = 1 if cfg.get("world_feet") else 0
     return c
 
 
@@ -298,8 +300,10 @@ class Controller:
         g = make_gait(gait)
         check(lib().sbs_reset(self._h, C.byref(g), it, _stream_ptr(stream)), "sbs_reset")
 
-    def problem(self, x0, xref, gait, f_ext=None, shift=0, host=False) -> Problem:
+    def problem(self, x0, xref, gait, f_ext=None, shift=0, host=False, feet=None) -> Problem:
         p = Problem()
+        if feet is not None:
+            p.feet = feet.data_ptr() if hasattr(feet, "data_ptr") else feet.ctypes.data
         p.x0 = x0.data_ptr() if hasattr(x0, "data_ptr") else x0.ctypes.data
         p.xref = xref.data_ptr() if hasattr(xref, "data_ptr") else xref.ctypes.data
         if f_ext is None:
@@ -311,23 +315,25 @@ class Controller:
         p.host_memory = 1 if host else 0
         return p
 
-    def solve(self, x0, xref, gait, f_ext=None, shift=0, result=None, stream=None):
-        """Device solve: x0 [12], xref [H,12], f_ext [3] float32 CUDA tensors.
-        Returns the device result buffer (uint8 tensor of RESULT_BYTES)."""
+    def solve(self, x0, xref, gait, f_ext=None, shift=0, result=None, stream=None, feet=None):
+        """Device solve: x0 [12], xref [H,12], f_ext [3] (and feet [4,2] for world-fixed
+        feet) float32 CUDA tensors.  Returns the device result buffer (uint8 tensor of
+        RESULT_BYTES)."""
         import torch
         if result is None:
             result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device="cuda")
-        p = self.problem(x0, xref, gait, f_ext, shift, host=False)
+        p = self.problem(x0, xref, gait, f_ext, shift, host=False, feet=feet)
         check(lib().sbs_solve(self._h, C.byref(p), C.c_void_p(result.data_ptr()), _stream_ptr(stream)),
               "sbs_solve")
         return result
 
-    def solve_host(self, x0, xref, gait, f_ext=None, shift=0, result: Optional[Result] = None, stream=None):
+    def solve_host(self, x0, xref, gait, f_ext=None, shift=0, result: Optional[Result] = None, stream=None,
+                   feet=None):
         """Host-memory solve: numpy/pinned-CPU float32 inputs; the result struct is
         written on the stream (synchronize before reading)."""
         if result is None:
             result = Result()
-        p = self.problem(x0, xref, gait, f_ext, shift, host=True)
+        p = self.problem(x0, xref, gait, f_ext, shift, host=True, feet=feet)
         check(lib().sbs_solve(self._h, C.byref(p), C.byref(result), _stream_ptr(stream)), "sbs_solve")
         return result
 

@@ -48,10 +48,12 @@ class GpuRun:
         self.x0 = dev(prob["x0"])
         self.xref = dev(prob["xref"])
         self.fext = dev(prob["f_ext"])
+        self.feet = dev(prob["feet"]) if "feet" in prob else None
         self.torch = torch
 
-    def solve(self, shift=0, gait=None, x0=None):
-        res = self.ctl.solve(self.x0 if x0 is None else x0, self.xref, gait or self.prob["gait"], self.fext, shift)
+    def solve(self, shift=0, gait=None, x0=None, feet=None):
+        res = self.ctl.solve(self.x0 if x0 is None else x0, self.xref, gait or self.prob["gait"], self.fext, shift,
+                             feet=self.feet if feet is None else feet)
         self.torch.cuda.synchronize()
         return S.parse_result(res.cpu().numpy())
 
@@ -77,29 +79,30 @@ class OracleRun:
         self.x0 = np.float64(f32(prob["x0"]))
         self.xref = np.float64(f32(prob["xref"]))
         self.fext = np.float64(f32(prob["f_ext"]))
+        self.feet = np.float64(f32(prob["feet"])) if "feet" in prob else None
         self.mean, self.var = orc.init_dist(self.P, self.g)
         self.iter = 0
 
     def rollout(self, want_theta=True, kappa=True, nthreads=8):
         J, q, th, margin = orc.rollout(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
-                                       self.iter, want_theta=want_theta, nthreads=nthreads)
+                                       self.iter, want_theta=want_theta, nthreads=nthreads, feet=self.feet)
         kap = None
         if kappa:
             kap = orc.cost_condition_all(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
-                                         self.iter, nthreads=nthreads)
+                                         self.iter, nthreads=nthreads, feet=self.feet)
         return J, q, th, margin, kap
 
     def sample(self, k, q_override=-1):
         return orc.rollout_sample(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
-                                  self.iter, k, q_override)
+                                  self.iter, k, q_override, feet=self.feet)
 
     def kappa(self, k):
         return orc.cost_condition(self.P, self.g, self.x0, self.xref, self.fext, self.mean, self.var,
-                                  self.iter, k)[0]
+                                  self.iter, k, feet=self.feet)[0]
 
     def solve(self, shift=0, nthreads=8):
         r = orc.solve(self.P, self.g, self.x0, self.xref, self.fext, shift, self.iter, self.mean, self.var,
-                      nthreads=nthreads)
+                      nthreads=nthreads, feet=self.feet)
         self.mean, self.var = r["mean"], r["var"]
         self.iter += self.P.iterations
         return r
@@ -178,3 +181,26 @@ def elite_band_ok(gpu_set, orc_J, Ke, kap, alt_J=None):
             near = near or alt_J[i] <= hi + band
         assert near, f"sample {i} cost {key[i]} far from threshold {thr} (tol {tol[i]})"
     return len(diff)
+
+
+def mppi_parity(cfg, prob, name, tile=0):
+    """One MPPI solve against the oracle: frequencies, costs, mean, kept variance,
+    result record."""
+    g, o = GpuRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    r = g.solve()
+    Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
+    amb = check_frequencies(qg, q, margin)
+    rep = check_costs(Jg, J, kap, skip=amb)
+    st, mo, esso, beta = orc.mppi(J, th, cfg["lam"])
+    mg, vg = g.state()
+    tol = mppi_tolerance(J, th, kap, cfg["lam"], mo)
+    assert np.all(np.abs(mg - mo) <= tol), (name, np.max(np.abs(mg - mo) - tol))
+    np.testing.assert_array_equal(vg, f32(o.var))  # MPPI keeps the covariance
+    assert r["status"] == S.OK
+    assert r["cost_min"] == float(np.min(Jg))  # its value is covered by the cost parity above
+    assert r["n_finite"] == int(np.sum(np.isfinite(J) & (J < 3e38)))
+    u0 = orc.first_control(o.P, o.g, mo)
+    np.testing.assert_allclose(r["u0"], u0, atol=float(np.max(tol[:12])))
+    g.close()
+    return rep

@@ -22,6 +22,7 @@ def _mix():
         dict(K=129, H=3, gait="crawl", method="elite", elite_count=7),
         dict(K=5000, H=33, gait="trot", method="mppi", adaptive=True, compare_mppi=True),
         dict(K=2500, H=12, gait="trot", method="naive", freq_set_mhz=(1300, 2000, 2400)),
+        dict(K=1500, H=25, gait="pace", method="mppi", world_feet=True),
     ]
     out = []
     for i, sp in enumerate(specs):
@@ -35,7 +36,7 @@ def _mix():
 def _tensors(prob):
     import torch
     d = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
-    return d(prob["x0"]), d(prob["xref"]), d(prob["f_ext"])
+    return d(prob["x0"]), d(prob["xref"]), d(prob["f_ext"]), (d(prob["feet"]) if "feet" in prob else None)
 
 
 def _gait(prob, tick, cfg):
@@ -65,10 +66,10 @@ def test_batch_equals_plain(mode):
         probs = []
         plain_res = []
         for i, (c, p) in enumerate(mix):
-            x0, xr, fe = tens[i]
+            x0, xr, fe, ft = tens[i]
             g = _gait(p, tick, c)
-            plain_res.append(plain[i].solve(x0, xr, g, fe, shift).clone())
-            probs.append(batched[i].problem(x0, xr, g, fe, shift))
+            plain_res.append(plain[i].solve(x0, xr, g, fe, shift, feet=ft).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, shift, feet=ft))
         b.solve(batched, probs, res)
         torch.cuda.synchronize()
         for i in range(n):
@@ -101,10 +102,11 @@ def test_same_alone_and_in_the_mix():
     r1 = torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     r8 = torch.empty(len(mix) * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     for tick in range(2):
-        x0, xr, fe = tens[k]
+        x0, xr, fe, ft = tens[k]
         g = _gait(mix[k][1], tick, mix[k][0])
-        b1.solve([alone], [alone.problem(x0, xr, g, fe, min(tick, 1))], r1)
-        probs = [inmix[i].problem(*tens[i][:2], _gait(mix[i][1], tick, mix[i][0]), tens[i][2], min(tick, 1))
+        b1.solve([alone], [alone.problem(x0, xr, g, fe, min(tick, 1), feet=ft)], r1)
+        probs = [inmix[i].problem(*tens[i][:2], _gait(mix[i][1], tick, mix[i][0]), tens[i][2], min(tick, 1),
+                                  feet=tens[i][3])
                  for i in range(len(mix))]
         b8.solve(inmix, probs, r8)
     torch.cuda.synchronize()
@@ -158,7 +160,8 @@ def test_autotune_picks_a_mode_and_results_stay_valid():
     tens = [_tensors(p) for _, p in mix]
     b = S.Batch(len(mix), sum(c.workspace_bytes() + 256 for c in ctls))
     res = torch.empty(len(mix) * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    probs = [ctls[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 0) for i in range(len(mix))]
+    probs = [ctls[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 0, feet=tens[i][3])
+             for i in range(len(mix))]
     g_ms, p_ms = b.autotune(ctls, probs, res, ticks=2)
     assert g_ms > 0 and p_ms > 0
     assert b.mode() == (S.BATCH_GRID if g_ms <= p_ms else S.BATCH_PERSISTENT)

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as orc
 from gpu_helpers import (MEAN_ATOL, GpuRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
-                         elite_band_ok, f32, mppi_tolerance)
+                         elite_band_ok, f32, mppi_parity, mppi_tolerance)
 from paper_2403_11383_b300 import sbs as S
 from paper_2403_11383_b300 import workloads as W
 
@@ -63,30 +63,9 @@ def test_normals_gpu_vs_oracle(cuda):
 
 # ------------------------------------------------------------------ single solves
 
-def _mppi_parity(cfg, prob, name):
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
-    J, q, th, margin, kap = o.rollout()
-    r = g.solve()
-    Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
-    amb = check_frequencies(qg, q, margin)
-    rep = check_costs(Jg, J, kap, skip=amb)
-    st, mo, esso, beta = orc.mppi(J, th, cfg["lam"])
-    mg, vg = g.state()
-    tol = mppi_tolerance(J, th, kap, cfg["lam"], mo)
-    assert np.all(np.abs(mg - mo) <= tol), (name, np.max(np.abs(mg - mo) - tol))
-    np.testing.assert_array_equal(vg, f32(o.var))  # MPPI keeps the covariance
-    assert r["status"] == S.OK
-    assert r["cost_min"] == float(np.min(Jg))  # its value is covered by the cost parity above
-    assert r["n_finite"] == int(np.sum(np.isfinite(J) & (J < 3e38)))
-    u0 = orc.first_control(o.P, o.g, mo)
-    np.testing.assert_allclose(r["u0"], u0, atol=float(np.max(tol[:12])))
-    g.close()
-    return rep
-
-
 def test_plain_mppi_single_solve(cuda):
     cfg = W.config("plain_mppi_k512_h12")
-    rep = _mppi_parity(cfg, W.problem(cfg), "c1")
+    rep = mppi_parity(cfg, W.problem(cfg), "c1")
     assert rep["gated"] == cfg["K"]
 
 
@@ -95,7 +74,7 @@ def test_plain_mppi_single_solve(cuda):
 def test_mppi_ragged_and_small(cuda, K, H, gait, tile):
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(K=K, H=H, gait=gait, tile=tile, seed=K)
-    _mppi_parity(cfg, W.problem(cfg), f"K{K}")
+    mppi_parity(cfg, W.problem(cfg), f"K{K}")
 
 
 def test_mppi_k1_returns_its_sample(cuda):
@@ -114,7 +93,7 @@ def test_mppi_many_tiles_hierarchical_combine(cuda):
     # 40 000 samples = 313 tiles = 20 groups of 16: exercises the two-level combine
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(K=40000, seed=9)
-    _mppi_parity(cfg, W.problem(cfg), "K40000")
+    mppi_parity(cfg, W.problem(cfg), "K40000")
 
 
 def test_adaptive_elite_iteration0_full_size(cuda):
@@ -279,7 +258,7 @@ def test_spline_full_size_sampled(cuda):
 def test_spline_small_mppi_parity(cuda):
     cfg = W.config("spline_k262144_h100")
     cfg.update(K=3000, H=25, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=8)
-    _mppi_parity(cfg, W.problem(cfg), "spline-small")
+    mppi_parity(cfg, W.problem(cfg), "spline-small")
 
 
 def test_spline_warm_shift(cuda):
