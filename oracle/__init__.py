@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("sigma_init", C.c_double), ("sigma_min", C.c_double),
         ("sigma_f_init", C.c_double), ("sigma_f_min", C.c_double),
         ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ),
-        ("feet_mode", C.c_int32),
+        ("feet_mode", C.c_int32), ("friction_project", C.c_int32),
     ]
 
 
@@ -65,6 +65,7 @@ def lib():
             "orc_srbd_step": (None, [vp, vp, vp, vp, d, vp]),
             "orc_srbd_deriv_feet": (None, [vp, vp, vp, vp, vp, vp]),
             "orc_foothold": (None, [vp, vp, vp, u32, u32, C.c_int, vp]),
+            "orc_cone_project": (None, [d, vp, vp]),
             "orc_stage_cost": (d, [vp, vp, vp, vp, vp]),
             "orc_spline_basis": (None, [C.c_int, C.c_int, d, vp]),
             "orc_spline_at": (d, [C.c_int, C.c_int, d, vp, d]),
@@ -134,6 +135,7 @@ def make_params(cfg) -> Params:
     for i, f in enumerate(fs):
         p.freq_set[i] = f
     p.feet_mode = 1 if cfg.get("world_feet") else 0
+    p.friction_project = 1 if cfg.get("friction_project") else 0
     return p
 
 
@@ -219,6 +221,14 @@ def foothold(params, x, vd, q_mhz, duty, leg):
     xx, v = _f64(x, 12), _f64(vd, 2)
     out = np.zeros(2)
     lib().orc_foothold(C.byref(params), _p(xx), _p(v), q_mhz, duty, leg, _p(out))
+    return out
+
+
+def cone_project(mu, force):
+    """Orthogonal projection of a force onto the friction cone (Sec. IV-B)."""
+    f = _f64(force, 3)
+    out = np.zeros(3)
+    lib().orc_cone_project(mu, _p(f), _p(out))
     return out
 
 

@@ -27,6 +27,7 @@
  *   step frequency uniform over a discrete set, one
  *   Gaussian per frequency (Naive) ..................... Sec. V (gait optimisation), Sec. V-A
  *   world-fixed stance feet, footholds at touchdown .... Eq. (1) (p_cf,i = p_f,i - p_c), Sec. IV-D
+ *   policy output constrained to the friction cone ..... Sec. IV-B
  *   one warm-started iteration per control tick ........ Sec. III-A
  *
  * Random numbers: Philox4x32-10 from Salmon, Moraes, Dror, Shaw, "Parallel
@@ -66,6 +67,7 @@ typedef struct {
     int32_t n_freq;          /* 0, or the size of a discrete step-frequency set (Naive only) */
     uint32_t freq_set[MAX_FREQ]; /* its frequencies in mHz, distinct */
     int32_t feet_mode;       /* 0: lever arms fixed in the body frame; 1: stance feet fixed on the ground */
+    int32_t friction_project; /* 1: stance forces projected onto the friction cone (no penalty) */
 } orc_params;
 
 typedef struct {
@@ -322,6 +324,30 @@ void orc_foothold(const orc_params* P, const double x[NX], const double vd[2], u
     }
 }
 
+/* Orthogonal (Euclidean) projection of a force onto the friction cone
+ * {|Gamma_xy| <= mu Gamma_z} (Sec. IV-B constrains the policy output to the cone).
+ * With s = |Gamma_xy| and t = Gamma_z: inside the cone nothing changes; in the
+ * polar cone (mu s <= -t) the force becomes 0; otherwise it moves to the nearest
+ * point of the boundary ray (mu, 1) in the (s, t) half-plane of the force,
+ * lambda = (mu s + t) / (1 + mu^2), t' = lambda, s' = mu lambda. */
+void orc_cone_project(double mu, const double in[3], double out[3])
+{
+    double s = sqrt(in[0] * in[0] + in[1] * in[1]), t = in[2];
+    if (s <= mu * t) {
+        out[0] = in[0]; out[1] = in[1]; out[2] = in[2];
+        return;
+    }
+    if (mu * s <= -t) {
+        out[0] = out[1] = out[2] = 0.0;
+        return;
+    }
+    double lam = (mu * s + t) / (1.0 + mu * mu);
+    double k = mu * lam / s;
+    out[0] = k * in[0];
+    out[1] = k * in[1];
+    out[2] = lam;
+}
+
 /* Stage cost r(u_j, x_j, x^r_j) (Sec. V): diagonal quadratic state tracking,
  * diagonal quadratic force cost with u^r = 0, and a friction-cone penalty
  * (mu) on stance legs: max(0, |Gamma_xy| - mu Gamma_z)^2 + max(0, -Gamma_z)^2. */
@@ -336,7 +362,7 @@ double orc_stage_cost(const orc_params* P, const double x[NX], const double xr[N
     for (int i = 0; i < 4; ++i)
         for (int a = 0; a < 3; ++a) J += P->R[a] * gamma[3 * i + a] * gamma[3 * i + a];
     for (int i = 0; i < 4; ++i) {
-        if (!stance[i]) continue;
+        if (!stance[i] || P->friction_project) continue; /* projected forces need no penalty */
         double gx = gamma[3 * i], gy = gamma[3 * i + 1], gz = gamma[3 * i + 2];
         double slip = sqrt(gx * gx + gy * gy) - P->mu * gz;
         double pen = 0;
@@ -619,8 +645,15 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
                 val = theta[12 * j + n];
             }
             u[n] = st[n / 3] ? val : 0.0;
-            if (eps > 0) u[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j, (uint64_t)n);
         }
+        if (P->friction_project)
+            for (int i = 0; i < 4; ++i) {
+                double pr[3];
+                orc_cone_project(P->mu, u + 3 * i, pr);
+                memcpy(u + 3 * i, pr, sizeof(pr));
+            }
+        if (eps > 0)
+            for (int n = 0; n < NU; ++n) u[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j, (uint64_t)n);
         J += orc_stage_cost(P, x, c->xref + NX * j, u, st);
         srbd_step(P, x, u, c->f_ext, P->feet_mode ? feet : NULL, dt, xn);
         memcpy(x, xn, sizeof(x));
