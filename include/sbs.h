@@ -145,6 +145,11 @@ typedef struct sbs_config {
      * stance time of the sample's frequency and v^d the reference's planar
      * velocity at that step.  sbs_problem.feet gives the feet at t_0. */
     int32_t world_feet;
+    /* 0: the friction cone is a penalty in the stage cost (w_fc).  1: the policy's
+     * stance forces are projected orthogonally onto the cone |Gamma_xy| <= mu Gamma_z
+     * before they act (Sec. IV-B), and the penalty is dropped; the samples (and
+     * the distribution update) stay on the unprojected decision variables. */
+    int32_t friction_project;
 } sbs_config;
 
 /* Periodic gait (Sec. IV-C): leg i is in stance while its phase

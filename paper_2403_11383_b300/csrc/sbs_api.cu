@@ -65,6 +65,7 @@ int validate_config(const sbs_config* c)
         if (k.R[i] < 0) return SBS_ERR_INVALID_ARG;
     if (!(k.w_fc >= 0) || !(k.mu >= 0) || !(k.rho >= 0) || !std::isfinite(k.f_nominal)) return SBS_ERR_INVALID_ARG;
     if (c->world_feet != 0 && c->world_feet != 1) return SBS_ERR_INVALID_ARG;
+    if (c->friction_project != 0 && c->friction_project != 1) return SBS_ERR_INVALID_ARG;
     if (c->world_feet && !(m.gravity[2] < 0.0f)) return SBS_ERR_INVALID_ARG;  // the foothold rule needs g_z < 0
     // discrete step-frequency set (Naive only): distinct values, each advancing the
     // phase by less than one cycle per step
@@ -111,6 +112,8 @@ void fill_params(const sbs_config* cfg, InstParams* out)
     P.D = P.nb * P.nf + P.adaptive;
     P.world_feet = cfg->world_feet;
     P.inv_g = cfg->world_feet ? 1.0f / -cfg->model.gravity[2] : 0.0f;
+    P.friction_project = cfg->friction_project;
+    P.inv_1pmu2 = 1.0f / (1.0f + cfg->cost.mu * cfg->cost.mu);
     P.method = cfg->method;
     P.Ke = cfg->method == SBS_ELITE ? cfg->elite_count : 1;
     P.T = cfg->tile ? cfg->tile : 128;
@@ -808,7 +811,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         if (h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
         smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb));
-        ext = ext || h->hP.n_freq > 0 || h->hP.world_feet;
+        ext = ext || h->hP.n_freq > 0 || h->hP.world_feet || h->hP.friction_project;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
         arena += align_up(h->wsl.bytes, 256);
         counters += h->wsl.counters;

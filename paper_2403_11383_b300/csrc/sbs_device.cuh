@@ -199,7 +199,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 // unchanged for finite states).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[12], const float* xr,
-                                            const float G[12], unsigned live = 0xfu)
+                                            const float G[12], unsigned live = 0xfu, bool penalty = true)
 {
     float r = 0.0f;
 #pragma unroll
@@ -214,6 +214,7 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
         r = fmaf(P.R[0] * gx, gx, r);
         r = fmaf(P.R[1] * gy, gy, r);
         r = fmaf(P.R[2] * gz, gz, r);
+        if (!penalty) continue;  // forces already projected onto the cone
         // friction cone on stance legs; a swing leg's zero force adds nothing
         // (|G_xy| as x * rsqrt(x), exact zero for a zero force)
         const float t2 = fmaf(gx, gx, gy * gy);
@@ -223,6 +224,26 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
         r = fmaf(P.w_fc, pen, r);
     }
     return r;
+}
+
+// Orthogonal projection of one force onto the friction cone |G_xy| <= mu G_z
+// (Sec. IV-B): unchanged inside, zero in the polar cone (mu |G_xy| <= -G_z),
+// otherwise the nearest point of the boundary, G_z' = lambda = (mu |G_xy| + G_z)
+// / (1 + mu^2) and |G_xy'| = mu lambda.  A swing leg's zero force stays zero.
+__device__ __forceinline__ void cone_project(float mu, float inv_1pmu2, float& gx, float& gy, float& gz)
+{
+    const float s2 = fmaf(gx, gx, gy * gy);
+    const float s = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;
+    if (s <= mu * gz) return;
+    if (mu * s <= -gz) {
+        gx = gy = gz = 0.0f;
+        return;
+    }
+    const float lam = fmaf(mu, s, gz) * inv_1pmu2;
+    const float k = mu * lam / s;
+    gx *= k;
+    gy *= k;
+    gz = lam;
 }
 
 // sin and cos of an attitude angle.  Beyond 1e5 rad (a rollout that has long left

@@ -477,7 +477,15 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         // legs in swing on the whole warp skip their terms (per-step forces only:
         // the spline kernel runs faster without the branches)
         const unsigned live = NP == 0 ? __reduce_or_sync(kFull, st) : 0xfu;
-        kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live));
+        bool penalty = true;
+        if constexpr (EXT) {
+            if (P.friction_project) {  // the policy output constrained to the cone (Sec. IV-B)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) cone_project(P.mu, P.inv_1pmu2, G[3 * i], G[3 * i + 1], G[3 * i + 2]);
+                penalty = false;
+            }
+        }
+        kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live, penalty));
         if constexpr (EXT) {
             if (P.world_feet) {
                 const unsigned touch = st & ~prev;  // legs landing at this step
@@ -1510,7 +1518,7 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb);
-    const void* fn = rollout_kernel(rollout_variant(hP.P, hP.n_freq > 0 || hP.world_feet));
+    const void* fn = rollout_kernel(rollout_variant(hP.P, hP.n_freq > 0 || hP.world_feet || hP.friction_project));
     if (!fn) return SBS_ERR_INVALID_ARG;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;

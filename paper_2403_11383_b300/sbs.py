@@ -41,7 +41,8 @@ class Config(C.Structure):
                 ("f_min", C.c_float), ("f_max", C.c_float), ("sigma_init", C.c_float),
                 ("sigma_min", C.c_float), ("sigma_f_init", C.c_float), ("sigma_f_min", C.c_float),
                 ("tile", C.c_int32), ("model", Model), ("cost", Cost),
-                ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ), ("world_feet", C.c_int32)]
+                ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ), ("world_feet", C.c_int32),
+                ("friction_project", C.c_int32)]
 
 
 class Gait(C.Structure):
@@ -198,6 +199,7 @@ def make_config(cfg: dict, tile: int = 0) -> Config:
     for i, f in enumerate(fs[:MAX_FREQ]):
         c.freq_set[i] = f
     c.world_feet = 1 if cfg.get("world_feet") else 0
+    c.friction_project = 1 if cfg.get("friction_project") else 0
     return c
 
 

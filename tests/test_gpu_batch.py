@@ -23,6 +23,7 @@ def _mix():
         dict(K=5000, H=33, gait="trot", method="mppi", adaptive=True, compare_mppi=True),
         dict(K=2500, H=12, gait="trot", method="naive", freq_set_mhz=(1300, 2000, 2400)),
         dict(K=1500, H=25, gait="pace", method="mppi", world_feet=True),
+        dict(K=1024, H=12, gait="trot", method="elite", elite_count=52, friction_project=True),
     ]
     out = []
     for i, sp in enumerate(specs):
