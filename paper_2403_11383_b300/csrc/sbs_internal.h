@@ -58,6 +58,9 @@ struct Workspace {
                        // selections), or null
     unsigned long long* best;  // Naive: [nb] complemented (cost key, index) of each block's best sample, or null
     unsigned* nfin;    // Naive: samples with a finite cost, or null
+    uint32_t* cand;    // large elite selections: [K] keys of the threshold bin (low 16 bits), or null
+    int32_t* bcnt;     // large elite selections: [2 ceil(K / 2048)] keys below / equal to the threshold per block
+    uint32_t* sel;     // large elite selections: [8] selection scratch
 };
 
 // Per-solve, per-iteration arguments.
@@ -85,7 +88,7 @@ struct InstRec {
     int32_t tile_begin;
     int32_t select_begin;
     int32_t refit_begin;
-    int32_t pad[1];
+    int32_t pad[3];
 };
 
 static_assert(sizeof(InstRec) % 16 == 0, "InstRec must be a multiple of 16 bytes");
@@ -113,7 +116,7 @@ inline size_t select_smem_bytes(int K) { return 4 * (size_t)(K < kSelectSmemMaxK
 // words starting 8-byte aligned): Naive best keys (2 nb words) and finite count
 // (2 words), completion counters (ngroups + 1), histogram.
 struct WsLayout {
-    size_t J, q, theta, part, gpart, elite, bytes;
+    size_t J, q, theta, part, gpart, elite, cand, bcnt, sel, bytes;
     int ntiles, ngroups, counters;  // counters: zero-when-idle words
     int c_groups, c_hist;           // word offsets of the completion counters and the histogram
     int naive_nb;                   // Naive force blocks (0: not Naive)
@@ -147,6 +150,10 @@ inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false,
     L.part = o; o = up(o + 4 * (size_t)L.ntiles * PS);
     L.gpart = o; o = up(o + 4 * (size_t)L.ngroups * PS);
     L.elite = o; o = up(o + 4 * (size_t)(Ke > 0 ? Ke : 1));
+    const size_t nblk = ((size_t)K + 2047) / 2048;  // blocks of the multi-block selection
+    L.cand = o; o = up(o + (hist ? 4 * (size_t)K : 0));
+    L.bcnt = o; o = up(o + (hist ? 8 * nblk : 0));
+    L.sel = o; o = up(o + (hist ? 32 : 0));
     L.bytes = o;
     return L;
 }
@@ -164,6 +171,9 @@ inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
     w.hist = L.hist ? counters + L.c_hist : nullptr;
     w.best = L.naive_nb > 0 ? reinterpret_cast<unsigned long long*>(counters) : nullptr;
     w.nfin = L.naive_nb > 0 ? counters + 2 * L.naive_nb : nullptr;
+    w.cand = L.hist ? (uint32_t*)(base + L.cand) : nullptr;
+    w.bcnt = L.hist ? (int32_t*)(base + L.bcnt) : nullptr;
+    w.sel = L.hist ? (uint32_t*)(base + L.sel) : nullptr;
     return w;
 }
 

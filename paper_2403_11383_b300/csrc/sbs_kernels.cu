@@ -827,13 +827,14 @@ __device__ void radix_pass(BlockShared& sh, const uint32_t* skeys, const float* 
 // Threshold key and tie count for K > kSelectSmemMaxK from the rollout's
 // histograms (which it clears for the next solve); cand: shared-memory space for
 // kSelectSmemMaxK keys.
-__device__ void large_threshold(BlockShared& sh, uint32_t* cand, uint32_t& thr, int& need_eq)
+// The 16-bit key bin holding rank Ke, from the rollout's histograms: the bin, the
+// rank within it and its key count.  clear: also clear the histograms for the
+// next solve (else the caller's next kernel does).
+__device__ void find_bin16(BlockShared& sh, uint32_t& b16_out, int& rank_out, int& ncand_out, bool clear = true)
 {
     const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
-    const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
-    const int K = P.K;
-    const float* J = t.ws.J;
+    const int tid = threadIdx.x, T = blockDim.x;
     unsigned* hist16 = t.ws.hist;
     unsigned* hist8 = hist16 + kHistBins;
     int rank = P.Ke;
@@ -858,8 +859,25 @@ __device__ void large_threshold(BlockShared& sh, uint32_t* cand, uint32_t& thr, 
     rank -= sh.below;
     const int ncand = sh.count;
     __syncthreads();
-    for (int i = tid; i < 256; i += T) hist8[i] = 0u;
-    for (int i = tid; i < kHistBins; i += T) hist16[i] = 0u;
+    if (clear) {
+        for (int i = tid; i < 256; i += T) hist8[i] = 0u;
+        for (int i = tid; i < kHistBins; i += T) hist16[i] = 0u;
+    }
+    b16_out = b16;
+    rank_out = rank;
+    ncand_out = ncand;
+}
+
+__device__ void large_threshold(BlockShared& sh, uint32_t* cand, uint32_t& thr, int& need_eq)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
+    const int K = P.K;
+    const float* J = t.ws.J;
+    uint32_t b16;
+    int rank, ncand;
+    find_bin16(sh, b16, rank, ncand);
     uint32_t prefix = b16 << 16, mask = 0xffff0000u;
     if (ncand > kSelectSmemMaxK) {  // the bin does not fit: finish over all keys
         radix_pass<false>(sh, nullptr, J, K, 8, prefix, mask, rank);
@@ -921,23 +939,26 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total)
     return incl - v;
 }
 
-// List the keys below thr and the first need_eq keys equal to thr, by ascending
-// index, into out (Ke entries).  Warp w owns a contiguous range of indices (a
-// multiple of 128 long, read as 16-byte loads); a first pass counts, the warps'
-// offsets follow in warp order, a second pass writes.  Also the best cost and the
-// number of finite costs.  R: rounds of 128 keys per warp whose loads are in
-// flight together (more only pays when every warp has that many rounds).
+// List the keys of [begin, end) below thr and the first need_eq keys equal to
+// thr, by ascending index, into out from position out0 on (never past Ke).
+// begin is a multiple of 4.  Warp w owns a contiguous sub-range (a multiple of
+// 128 long, read as 16-byte loads); a first pass counts, the warps' offsets
+// follow in warp order, a second pass writes.  Each thread also returns its
+// part of the best cost and of the number of finite costs.  R: rounds of 128
+// keys per warp whose loads are in flight together (more only pays when every
+// warp has that many rounds).
 template <int R>
-__device__ void ordered_compaction(BlockShared& sh, uint32_t thr, int need_eq, float* best, int* nfinite)
+__device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int begin, int end, int out0,
+                              float* bmin_out, int* nf_out)
 {
-    const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int K = P.K, Ke = P.Ke;
+    const int Ke = sh.P.Ke;
     const float* J = t.ws.J;
     int32_t* out = t.ws.elite;
-    const int Cw = ((K + nw - 1) / nw + 127) / 128 * 128;
-    const int c0 = min(K, warp * Cw), c1 = min(K, c0 + Cw);
+    const int n = end - begin;
+    const int Cw = ((n + nw - 1) / nw + 127) / 128 * 128;
+    const int c0 = min(end, begin + warp * Cw), c1 = min(end, c0 + Cw);
     int lt = 0, eq = 0, nf = 0;
     float bmin = kInf;
     for (int base = c0; base < c1; base += 128 * R) {
@@ -962,7 +983,7 @@ __device__ void ordered_compaction(BlockShared& sh, uint32_t thr, int need_eq, f
         sh.wtot2[warp] = eq;
     }
     __syncthreads();
-    int off = 0, eqb = 0;
+    int off = out0, eqb = 0;
     for (int w = 0; w < warp; ++w) {
         const int e = sh.wtot2[w];
         off += sh.wtot[w] + min(e, max(0, need_eq - eqb));
@@ -1010,10 +1031,8 @@ __device__ void ordered_compaction(BlockShared& sh, uint32_t thr, int need_eq, f
             eq_seen += ne_tot;
         }
     }
-    *best = block_min(sh, bmin);
-    int tot;
-    block_scan(sh, nf, &tot);
-    *nfinite = tot;
+    *bmin_out = bmin;
+    *nf_out = nf;
 }
 
 __device__ void select_block(BlockShared& sh, uint32_t* skeys)
@@ -1046,10 +1065,13 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
         thr = prefix;
         need_eq = rank;
     }
-    float beta;
+    float bm;
+    int nf;
+    if (K >= 16384) compact_range<4>(sh, thr, need_eq, 0, K, 0, &bm, &nf);
+    else compact_range<1>(sh, thr, need_eq, 0, K, 0, &bm, &nf);
+    const float beta = block_min(sh, bm);
     int nfin;
-    if (K >= 16384) ordered_compaction<4>(sh, thr, need_eq, &beta, &nfin);
-    else ordered_compaction<1>(sh, thr, need_eq, &beta, &nfin);
+    block_scan(sh, nf, &nfin);
     if (tid == 0) {
         sbs_result* r = t.result;
         r->cost_min = beta;
@@ -1442,6 +1464,197 @@ __global__ void k_fma_peak(float* out, int iters)
 }
 
 // ---------------------------------------------------------------------------
+// Multi-block elite selection of one large controller (K > kSelectSmemMaxK, plain
+// solves): the same threshold key and ordered list as select_block, with the
+// passes over all K costs spread over blocks of kSelChunk keys.
+//   k_sel_find    1 block: the 16-bit bin holding rank Ke (rollout histograms)
+//   k_sel_gather  the bin's keys (low 16 bits) into ws.cand, any order
+//   k_sel_thr     1 block: two 8-bit passes over them: thr, need_eq
+//   k_sel_count   per block: keys below / equal to thr; best cost, finite count
+//   k_sel_write   per block: its offset from the blocks before it, then its
+//                 part of the list in index order; block 0 writes the record
+// ws.sel holds {b16, rank in bin, bin count, gather counter, thr, need_eq, best
+// cost key, finite count}.
+// ---------------------------------------------------------------------------
+constexpr int kSelChunk = 2048;
+constexpr int kSelBlock = 256;
+
+__device__ __forceinline__ void load_block_params(BlockShared& sh, const InstParams* dP, const TickArgs& t)
+{
+    load_params(dP, sh);
+    if (threadIdx.x == 0) sh.t = t;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSelectThreads) k_sel_find(const InstParams* __restrict__ dP, TickArgs t)
+{
+    __shared__ BlockShared sh;
+    load_block_params(sh, dP, t);
+    uint32_t b16;
+    int rank, ncand;
+    find_bin16(sh, b16, rank, ncand, false);  // k_sel_gather clears the histograms
+    if (threadIdx.x == 0) {
+        uint32_t* sc = t.ws.sel;
+        sc[0] = b16;
+        sc[1] = (uint32_t)rank;
+        sc[2] = (uint32_t)ncand;
+        sc[3] = 0u;
+        sc[6] = 0xffffffffu;
+        sc[7] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kSelBlock) k_sel_gather(const InstParams* __restrict__ dP, TickArgs t)
+{
+    const int K = dP->K;
+    const uint32_t b16 = __ldcg(t.ws.sel);
+    const int lane = threadIdx.x & 31;
+    // clear the rollout's histograms for the next solve (k_sel_find has read them)
+    for (int i = blockIdx.x * kSelBlock + threadIdx.x; i < kHistBins + 256; i += gridDim.x * kSelBlock)
+        t.ws.hist[i] = 0u;
+    const int i0 = blockIdx.x * kSelChunk + 4 * threadIdx.x;
+    for (int r = 0; r < kSelChunk / (4 * kSelBlock); ++r) {
+        const int i = i0 + r * 4 * kSelBlock;
+        float c[4];
+        load4(t.ws.J, i, K, c);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t key = cost_key(c[u]);
+            const bool m = i + u < K && (key >> 16) == b16;
+            const unsigned bal = __ballot_sync(kFull, m);
+            if (bal) {
+                unsigned at = 0;
+                if (lane == __ffs(bal) - 1) at = atomicAdd(t.ws.sel + 3, (unsigned)__popc(bal));
+                at = __shfl_sync(kFull, at, __ffs(bal) - 1);
+                if (m) t.ws.cand[at + __popc(bal & ((1u << lane) - 1u))] = key & 0xffffu;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSelectThreads) k_sel_thr(const InstParams* __restrict__ dP, TickArgs t)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    load_block_params(sh, dP, t);
+    uint32_t* sc = t.ws.sel;
+    const uint32_t b16 = __ldcg(sc);
+    int rank = (int)__ldcg(sc + 1);
+    const int n = (int)__ldcg(sc + 3);
+    uint32_t prefix, mask;
+    if (n <= kSelectSmemMaxK) {
+        uint32_t* keys = reinterpret_cast<uint32_t*>(dyn4);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = __ldcg(t.ws.cand + i);
+        __syncthreads();
+        prefix = 0;
+        mask = 0;
+        radix_pass<true>(sh, keys, nullptr, n, 8, prefix, mask, rank);
+        radix_pass<true>(sh, keys, nullptr, n, 0, prefix, mask, rank);
+        prefix |= b16 << 16;
+    } else {  // the bin does not fit: finish over all keys
+        prefix = b16 << 16;
+        mask = 0xffff0000u;
+        radix_pass<false>(sh, nullptr, t.ws.J, sh.P.K, 8, prefix, mask, rank);
+        radix_pass<false>(sh, nullptr, t.ws.J, sh.P.K, 0, prefix, mask, rank);
+    }
+    if (threadIdx.x == 0) {
+        sc[4] = prefix;
+        sc[5] = (uint32_t)rank;
+    }
+}
+
+__global__ void __launch_bounds__(kSelBlock) k_sel_count(const InstParams* __restrict__ dP, TickArgs t)
+{
+    __shared__ int s_cnt[2][kSelBlock / 32];
+    __shared__ float s_min[kSelBlock / 32];
+    const int K = dP->K;
+    const uint32_t thr = __ldcg(t.ws.sel + 4);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = blockIdx.x * kSelChunk + 4 * tid;
+    int lt = 0, eq = 0, nf = 0;
+    float bmin = kInf;
+    for (int r = 0; r < kSelChunk / (4 * kSelBlock); ++r) {
+        const int i = i0 + r * 4 * kSelBlock;
+        float c[4];
+        load4(t.ws.J, i, K, c);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i + u < K) {
+                const uint32_t key = cost_key(c[u]);
+                lt += key < thr ? 1 : 0;
+                eq += key == thr ? 1 : 0;
+                bmin = fminf(bmin, c[u]);
+                nf += c[u] < kInf ? 1 : 0;
+            }
+        }
+    }
+    lt = warp_sum_int(lt);
+    eq = warp_sum_int(eq);
+    nf = warp_sum_int(nf);
+    bmin = warp_min(bmin);
+    if (lane == 0) {
+        s_cnt[0][warp] = lt;
+        s_cnt[1][warp] = eq;
+        s_min[warp] = bmin;
+        if (nf) atomicAdd(t.ws.sel + 7, (unsigned)nf);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int a = 0, b = 0;
+        float m = kInf;
+        for (int w = 0; w < kSelBlock / 32; ++w) {
+            a += s_cnt[0][w];
+            b += s_cnt[1][w];
+            m = fminf(m, s_min[w]);
+        }
+        t.ws.bcnt[2 * blockIdx.x] = a;
+        t.ws.bcnt[2 * blockIdx.x + 1] = b;
+        atomicMin(t.ws.sel + 6, cost_key(m));
+    }
+}
+
+__global__ void __launch_bounds__(kSelBlock) k_sel_write(const InstParams* __restrict__ dP, TickArgs t)
+{
+    __shared__ BlockShared sh;
+    load_block_params(sh, dP, t);
+    const int K = sh.P.K;
+    const uint32_t* sc = t.ws.sel;
+    const uint32_t thr = __ldcg(sc + 4);
+    const int need_eq = (int)__ldcg(sc + 5);
+    if (threadIdx.x < 32) {
+        // this block's offset and share of the ties: the blocks before it hold lt keys
+        // below thr and eq equal to it, of which the first need_eq are taken
+        int lt = 0, eq = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) {
+            lt += __ldcg(t.ws.bcnt + 2 * b);
+            eq += __ldcg(t.ws.bcnt + 2 * b + 1);
+        }
+        lt = warp_sum_int(lt);
+        eq = warp_sum_int(eq);
+        if (threadIdx.x == 0) {
+            sh.digit = lt + min(eq, need_eq);
+            sh.below = max(0, need_eq - eq);
+        }
+    }
+    __syncthreads();
+    const int begin = blockIdx.x * kSelChunk, end = min(K, begin + kSelChunk);
+    float bm;
+    int nf;
+    compact_range<1>(sh, thr, sh.below, begin, end, sh.digit, &bm, &nf);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t mk = __ldcg(sc + 6);
+        const int nfin = (int)__ldcg(sc + 7);
+        sbs_result* r = t.result;
+        r->cost_min = mk == 0xffffffffu ? kInf : key_cost(mk);
+        r->ess = (float)sh.P.Ke;
+        r->status = nfin > 0 ? SBS_OK : SBS_ERR_DIVERGED;
+        r->n_finite = nfin;
+        r->iter_lo = (uint32_t)t.iter;
+        r->iter_hi = (uint32_t)(t.iter >> 32);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 static int status_of(cudaError_t e) { return e == cudaSuccess ? SBS_OK : SBS_ERR_CUDA; }
@@ -1530,6 +1743,19 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
 
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
+    if (hP.method == SBS_ELITE && hP.K > kSelectSmemMaxK && t.ws.hist && t.ws.sel) {
+        cudaStream_t s = (cudaStream_t)stream;
+        const int G = (hP.K + kSelChunk - 1) / kSelChunk;
+        const size_t thr_smem = 4 * (size_t)kSelectSmemMaxK;
+        int st = ensure_smem_attr((const void*)k_sel_thr, thr_smem);
+        if (st) return st;
+        k_sel_find<<<1, kSelectThreads, 0, s>>>(dP, t);
+        k_sel_gather<<<G, kSelBlock, 0, s>>>(dP, t);
+        k_sel_thr<<<1, kSelectThreads, thr_smem, s>>>(dP, t);
+        k_sel_count<<<G, kSelBlock, 0, s>>>(dP, t);
+        k_sel_write<<<G, kSelBlock, 0, s>>>(dP, t);
+        return status_of(cudaGetLastError());
+    }
     const size_t smem = select_smem_bytes(hP.K);
     int st = ensure_smem_attr((const void*)k_select, smem);
     if (st) return st;

@@ -248,10 +248,28 @@ def test_spline_full_size_sampled(cuda):
     amb = check_frequencies(qg[ks], qo[:, 0].astype(np.uint32), qo[:, 1])
     check_costs(Jg[ks], J, kap, skip=amb)
     assert eg.size == cfg["elite_count"] and np.all(np.diff(eg) > 0)
-    # every elite's cost is at most every non-elite's (on the GPU's own costs)
+    # every elite's cost is at most every non-elite's (on the GPU's own costs), and
+    # the list is exactly the first K_e of the (cost, index) order
     mask = np.zeros(cfg["K"], bool)
     mask[eg] = True
     assert Jg[mask].max() <= Jg[~mask].min()
+    np.testing.assert_array_equal(eg, np.sort(np.lexsort((np.arange(cfg["K"]), Jg))[:cfg["elite_count"]]))
+    g.close()
+
+
+@pytest.mark.parametrize("K,frac", [(32769, 0.05), (40000, 0.3), (70001, 0.01)])
+def test_large_k_selection_is_the_cost_index_order(cuda, K, frac):
+    # elite selections above the shared-memory size run as five multi-block passes
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(K=K, method="elite", elite_count=W.elite_count(frac, K), seed=K % 97)
+    prob = W.problem(cfg)
+    g = GpuRun(cfg, prob)
+    for shift in (0, 1):
+        r = g.solve(shift=shift)
+        Jg, eg = g.read(S.BUF_COST), g.read(S.BUF_ELITE)
+        want = np.sort(np.lexsort((np.arange(K), Jg))[:cfg["elite_count"]])
+        np.testing.assert_array_equal(eg, want)
+        assert r["cost_min"] == float(Jg.min()) and r["n_finite"] == int(np.isfinite(Jg).sum())
     g.close()
 
 
