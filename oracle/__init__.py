@@ -36,6 +36,7 @@ class Params(C.Structure):
         ("sigma_f_init", C.c_double), ("sigma_f_min", C.c_double),
         ("n_freq", C.c_int32), ("freq_set", C.c_uint32 * MAX_FREQ),
         ("feet_mode", C.c_int32), ("friction_project", C.c_int32),
+        ("w_terminal", C.c_double),
     ]
 
 
@@ -136,6 +137,7 @@ def make_params(cfg) -> Params:
         p.freq_set[i] = f
     p.feet_mode = 1 if cfg.get("world_feet") else 0
     p.friction_project = 1 if cfg.get("friction_project") else 0
+    p.w_terminal = cfg["cost"].get("w_terminal", 0.0)
     return p
 
 

@@ -68,6 +68,7 @@ typedef struct {
     uint32_t freq_set[MAX_FREQ]; /* its frequencies in mHz, distinct */
     int32_t feet_mode;       /* 0: lever arms fixed in the body frame; 1: stance feet fixed on the ground */
     int32_t friction_project; /* 1: stance forces projected onto the friction cone (no penalty) */
+    double w_terminal;       /* weight of the terminal state cost (0: none) */
 } orc_params;
 
 typedef struct {
@@ -554,8 +555,9 @@ void orc_warm_shift(const orc_params* P, const orc_gait* g, int shift, double* m
 /*         forces from the per-step values or the spline, zeroed on swing legs */
 /*         (Alg. 4, function pi);                                              */
 /*   J  += r(u_j, x_j, x^r_j); x_{j+1} = f(x_j, u_j).                          */
-/* After the loop, adaptive gaits (Gaussian or discrete frequency) add         */
-/* rho (theta_1 - f_nominal)^2 (Sec. V).                                      */
+/* After the loop, an optional terminal cost w_T sum_c Q_c (x_H - x^r_{H-1})^2 */
+/* (Alg. 2 leaves x_H uncosted) and, for adaptive gaits (Gaussian or discrete  */
+/* frequency), rho (theta_1 - f_nominal)^2 (Sec. V).                          */
 /* A non-finite cost is +inf.  q_override >= 0 replaces the sample's quantised */
 /* frequency (used to evaluate both candidates of an ambiguous rounding).      */
 /* ------------------------------------------------------------------------- */
@@ -659,6 +661,14 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
         memcpy(x, xn, sizeof(x));
         if (eps > 0)
             for (int n = 0; n < NX; ++n) x[n] *= 1.0 + eps * pert_sign(pkey, 2 * (uint64_t)j + 1, (uint64_t)n);
+    }
+    if (P->w_terminal > 0) { /* the state reached after the last step, against the last reference */
+        double Jt = 0;
+        for (int n = 0; n < NX; ++n) {
+            double e = x[n] - c->xref[NX * (H - 1) + n];
+            Jt += P->Q[n] * e * e;
+        }
+        J += P->w_terminal * Jt;
     }
     if (P->adaptive || P->n_freq > 0) {
         double d = q / 1000.0 - P->f_nominal;

@@ -197,6 +197,35 @@ def test_rollout_ballistic_cost_closed_form(orc):
     np.testing.assert_allclose(J, want, rtol=1e-12)
 
 
+@pytest.mark.parametrize("w_t", [0.0, 2.5])
+def test_terminal_cost_on_the_flight_closed_form(orc, w_t):
+    # the optional terminal cost charges x_H (the state after the last step)
+    # against the last reference, weighted by w_t, on top of Alg. 2's stage costs
+    c = copy.deepcopy(W.config("plain_mppi_k512_h12"))
+    c["K"] = 4
+    c["cost"] = dict(c["cost"], w_terminal=w_t)
+    P = orc.make_params(c)
+    g = orc.make_gait({"offset": (0, 0, 0, 0), "duty": 0, "phase0": 0})
+    pr = W.problem(c)
+    x0, xref = pr["x0"].copy(), pr["xref"]
+    x0[3:6] = 0
+    x0[9:12] = 0
+    mean, var = orc.init_dist(P, g)
+    J, _, _, _ = orc.rollout(P, g, x0, xref, None, mean, var, 0)
+    Q = np.array(W.COST["Q"])
+    dt, gz = 0.02, -9.81
+
+    def flight(j):
+        x = x0.copy()
+        x[0:3] = x0[0:3] + x0[6:9] * j * dt + np.array([0, 0, gz]) * dt * dt * j * (j - 1) / 2
+        x[6:9] = x0[6:9] + np.array([0, 0, gz]) * j * dt
+        return x
+
+    want = sum(np.sum(Q * (flight(j) - xref[j]) ** 2) for j in range(12))
+    want += w_t * np.sum(Q * (flight(12) - xref[11]) ** 2)
+    np.testing.assert_allclose(J, want, rtol=1e-12)
+
+
 def test_rollout_hover_cost_closed_form(orc):
     # duty 1: all legs in stance; zero noise, vertical m|g|/4 per leg, level body
     # at rest: the state never moves, J = H (state error + force cost)
