@@ -107,6 +107,8 @@ typedef struct sbs_cost {
     float mu;
     float rho;
     float f_nominal; /* Hz */
+    float w_terminal; /* >= 0: adds w_terminal sum_c Q_c (x_H - xref_{H-1})^2 for the state after the
+                         last step (Alg. 2 leaves it uncosted; 0 follows the paper) */
 } sbs_cost;
 
 typedef struct sbs_config {

@@ -64,6 +64,7 @@ int validate_config(const sbs_config* c)
     for (int i = 0; i < 3; ++i)
         if (k.R[i] < 0) return SBS_ERR_INVALID_ARG;
     if (!(k.w_fc >= 0) || !(k.mu >= 0) || !(k.rho >= 0) || !std::isfinite(k.f_nominal)) return SBS_ERR_INVALID_ARG;
+    if (!(k.w_terminal >= 0) || !std::isfinite(k.w_terminal)) return SBS_ERR_INVALID_ARG;
     if (c->world_feet != 0 && c->world_feet != 1) return SBS_ERR_INVALID_ARG;
     if (c->friction_project != 0 && c->friction_project != 1) return SBS_ERR_INVALID_ARG;
     if (c->world_feet && !(m.gravity[2] < 0.0f)) return SBS_ERR_INVALID_ARG;  // the foothold rule needs g_z < 0
@@ -142,6 +143,7 @@ void fill_params(const sbs_config* cfg, InstParams* out)
     P.mu = cfg->cost.mu;
     P.rho = cfg->cost.rho;
     P.f_nominal = cfg->cost.f_nominal;
+    P.w_terminal = cfg->cost.w_terminal;
     P.f_min = cfg->f_min;
     P.f_max = cfg->f_max;
     P.var_init = cfg->sigma_init * cfg->sigma_init;

@@ -33,7 +33,8 @@ struct InstParams {
     float inv_g;          // 1 / |g_z| (foothold rule)
     int32_t friction_project;  // 1: stance forces projected onto the friction cone, no penalty
     float inv_1pmu2;      // 1 / (1 + mu^2)
-    int32_t pad1[3];
+    float w_terminal;     // terminal state cost weight (0: none)
+    int32_t pad1[2];
     uint32_t dt_us, q_init, seed, ctrl;
     float dt, lambda, inv_lambda, inv_mass, weight_z;
     float inertia[3], inv_inertia[3], foot[12], gravity[3];

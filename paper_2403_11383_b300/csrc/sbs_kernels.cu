@@ -503,6 +503,16 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
         }
     }
+    if (P.w_terminal > 0.0f) {  // optional terminal cost of the state after the last step
+        const float* xr = v.xr + 12 * (P.H - 1);
+        float r = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const float e = x[c] - xr[c];
+            r = fmaf(P.Q[c] * e, e, r);
+        }
+        kahan_add(J, Jc, P.w_terminal * r);
+    }
     if (P.adaptive || P.n_freq > 0) {
         const float d = (float)q / 1000.0f - P.f_nominal;
         kahan_add(J, Jc, P.rho * d * d);

@@ -30,7 +30,7 @@ class Model(C.Structure):
 
 class Cost(C.Structure):
     _fields_ = [("Q", C.c_float * 12), ("R", C.c_float * 3), ("w_fc", C.c_float), ("mu", C.c_float),
-                ("rho", C.c_float), ("f_nominal", C.c_float)]
+                ("rho", C.c_float), ("f_nominal", C.c_float), ("w_terminal", C.c_float)]
 
 
 class Config(C.Structure):
@@ -194,6 +194,7 @@ def make_config(cfg: dict, tile: int = 0) -> Config:
     c.cost.Q[:] = list(k["Q"])
     c.cost.R[:] = list(k["R"])
     c.cost.w_fc, c.cost.mu, c.cost.rho, c.cost.f_nominal = k["w_fc"], k["mu"], k["rho"], k["f_nominal"]
+    c.cost.w_terminal = k.get("w_terminal", 0.0)
     fs = list(cfg.get("freq_set_mhz", ()))
     c.n_freq = len(fs)
     for i, f in enumerate(fs[:MAX_FREQ]):

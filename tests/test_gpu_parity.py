@@ -257,6 +257,18 @@ def test_spline_full_size_sampled(cuda):
     g.close()
 
 
+@pytest.mark.parametrize("name,extra", [
+    ("plain_mppi_k512_h12", dict(K=2048, seed=71)),
+    ("spline_k262144_h100", dict(K=3000, H=25, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0,
+                                 seed=73)),
+])
+def test_terminal_cost_parity(cuda, name, extra):
+    cfg = W.config(name)
+    cfg.update(extra)
+    cfg["cost"] = dict(cfg["cost"], w_terminal=4.0)
+    mppi_parity(cfg, W.problem(cfg), f"terminal {name}")
+
+
 @pytest.mark.parametrize("K,frac", [(32769, 0.05), (40000, 0.3), (70001, 0.01)])
 def test_large_k_selection_is_the_cost_index_order(cuda, K, frac):
     # elite selections above the shared-memory size run as five multi-block passes

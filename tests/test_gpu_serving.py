@@ -71,6 +71,37 @@ def test_served_results_equal_plain_solves():
     srv.close()
 
 
+def test_served_extended_features_equal_plain_solves():
+    # ground-fixed feet, the frequency set, the friction projection and the terminal
+    # cost go through the server's staging (feet included) and the extended kernels
+    import torch
+    base = W.config("worldfeet_mppi_k4096_h25")
+    cfgs = [dict(base, K=700, seed=61, ctrl=0),
+            dict(base, K=900, H=12, seed=61, ctrl=1, friction_project=True,
+                 cost=dict(base["cost"], w_terminal=3.0)),
+            dict(W.config("naive_freqset_k10000_h12"), K=1200, world_feet=True, seed=61, ctrl=2)]
+    probs = [W.problem(c) for c in cfgs]
+    served = [S.Controller(c) for c in cfgs]
+    plain = [S.Controller(c) for c in cfgs]
+    srv = S.Server(slots=2, max_batch=8, budget_bytes=1 << 30)
+    handles = np.array([c.handle.value for c in served], dtype=np.uint64)
+    for rnd in range(2):
+        bufs = []
+        recs = _records(served, probs, 0 if rnd == 0 else 1, bufs)
+        for i, p in enumerate(probs):
+            f = np.ascontiguousarray(p["feet"], dtype=np.float32)
+            bufs.append(f)
+            recs[i]["feet"] = f.ctypes.data
+        res = _wait(srv, srv.submit(handles, recs))
+        for i, c in enumerate(plain):
+            r = c.solve_host(np.float32(probs[i]["x0"]), np.float32(probs[i]["xref"]), probs[i]["gait"], None,
+                             0 if rnd == 0 else 1, feet=np.float32(probs[i]["feet"]))
+            torch.cuda.synchronize()
+            want = np.frombuffer(bytes(r), dtype=S.RESULT_DTYPE)[0]
+            assert res[i].tobytes() == want.tobytes()
+    srv.close()
+
+
 def test_requests_of_one_controller_are_served_in_order():
     cfgs, probs = _setup(2)
     c = S.Controller(cfgs[0])
