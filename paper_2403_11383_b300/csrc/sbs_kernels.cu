@@ -7,14 +7,22 @@
 //              MPPI the tile forms max-shifted partial sums of w and
 //              w (theta - mean); the last tile of each group of 16 combines the
 //              group, the last group the whole controller (Alg. 5).
+//              Naive keeps each force block's best (cost, index) with 64-bit
+//              atomics instead.  <NP, EXT>: spline knots (0: one force per step);
+//              the extended model features (frequency set, ground-fixed feet,
+//              friction projection).
 //  k_select    one 1024-thread block per elite/naive controller: radix select of
-//              the K_e lowest (cost, index) pairs (Alg. 1 Sorting).
+//              the K_e lowest (cost, index) pairs and their ordered list (Alg. 1
+//              Sorting); Naive reads the per-block best keys.
+//  k_sel_*     the same selection spread over many blocks, for one controller
+//              with more costs than fit in shared memory (plain solves).
 //  k_refit     one block per step (or knot): elite mean and diagonal variance
-//              (Alg. 1 Update) or the best sample (Alg. 3) from the stored
-//              deviations.
-//  k_batch_*   the same three stages for many controllers, pulled as items from
-//              device queues by persistent blocks.
+//              (Alg. 1 Update) or the best sample per force block (Alg. 3) from
+//              the stored deviations.
+//  k_grid_* / k_batch_*  the same three stages for many controllers: one block
+//              per item, or persistent blocks pulling items from device queues.
 //  k_init      the initial distribution.
+//  k_philox, k_normals  the random numbers the controller draws (tests).
 //  k_fma_peak  FP32 FMA-chain microbenchmark for the roofline denominator.
 #include <cuda_runtime.h>
 
