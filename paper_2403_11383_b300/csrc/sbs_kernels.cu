@@ -1179,36 +1179,33 @@ __device__ void refit_block(BlockShared& sh, int b)
                 var_c = sh.vr12[tid];
             }
         } else {
-            for (int pass = 0; pass < 2; ++pass) {
-                float s[12];
+            // one pass: sums of the deviations and of their squares, both taken
+            // about the first elite s deviation d0 (keeps the cancellation small)
+            if (tid < 12) sh.dbar[tid] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + tid);
+            __syncthreads();
+            float s[12], s2[12];
 #pragma unroll
-                for (int c = 0; c < 12; ++c) s[c] = 0.0f;
-                for (int e = tid; e < Ke; e += blockDim.x) {
-                    const int kb = __ldcg(elite + e);
-                    const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
-                    const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
-                    const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
+            for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
+            for (int e = tid; e < Ke; e += blockDim.x) {
+                const int kb = __ldcg(elite + e);
+                const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
+                const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
+                const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
-                    for (int c = 0; c < 12; ++c) {
-                        if (pass == 0) {
-                            s[c] += d[c];
-                        } else {
-                            const float q = d[c] - sh.dbar[c];
-                            s[c] = fmaf(q, q, s[c]);
-                        }
-                    }
+                for (int c = 0; c < 12; ++c) {
+                    const float q = d[c] - sh.dbar[c];
+                    s[c] += q;
+                    s2[c] = fmaf(q, q, s2[c]);
                 }
-                const float tot = block_sum12(sh, s);
-                if (tid < 12) {
-                    if (pass == 0) {
-                        sh.dbar[tid] = tot / (float)Ke;
-                    } else {
-                        var_c = fmaxf(tot / (float)Ke, P.var_min);
-                        mean_c = sh.mu12[tid] + sh.dbar[tid];
-                    }
-                }
-                __syncthreads();
             }
+            const float tot = block_sum12(sh, s);
+            const float tot2 = block_sum12(sh, s2);
+            if (tid < 12) {
+                const float m = tot / (float)Ke;
+                var_c = fmaxf(fmaf(-m, m, tot2 / (float)Ke), P.var_min);
+                mean_c = sh.mu12[tid] + (sh.dbar[tid] + m);
+            }
+            __syncthreads();
         }
         if (tid < 12) {
             dm[12 * b + tid] = mean_c;

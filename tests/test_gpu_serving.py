@@ -143,19 +143,23 @@ def test_admission_by_budget_and_full_queue():
 
 
 def test_continuous_batching_admits_while_ticks_run():
+    # the first tick is long (4 spline controllers of 2^21 samples over 128 steps,
+    # ~20 ms on the GPU), so the second batch arrives while it runs
     cfgs, _ = _setup(8)
-    cfgs = [dict(c, K=16384, H=50) for c in cfgs]
+    cfgs = [dict(c, K=1 << 21, H=128, P=4) if i < 4 else dict(c, K=4096, H=12) for i, c in enumerate(cfgs)]
     probs = [W.problem(c) for c in cfgs]
     ctls = [S.Controller(c) for c in cfgs]
     srv = S.Server(slots=2, max_batch=64, budget_bytes=8 << 30)
     bufs = []
     h = np.array([c.handle.value for c in ctls], dtype=np.uint64)
     import time
-    t1 = srv.submit(h[:4], _records(ctls[:4], probs[:4], 0, bufs))
+    rec1 = _records(ctls[:4], probs[:4], 0, bufs)
+    rec2 = _records(ctls[4:], probs[4:], 0, bufs)
+    t1 = srv.submit(h[:4], rec1)
     t0 = time.time()
     while srv.stats()["ticks"] < 1:  # the first tick is on the GPU ...
         assert time.time() - t0 < 10
-    t2 = srv.submit(h[4:], _records(ctls[4:], probs[4:], 0, bufs))  # ... when these arrive
+    t2 = srv.submit(h[4:], rec2)  # ... when these arrive
     r = _wait(srv, np.concatenate([t1, t2]))
     assert (r["iter_lo"] == 0).all()
     st = srv.stats()
