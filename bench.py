@@ -468,7 +468,7 @@ def main():
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
                       "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
-            "roofline": {"kernel": "k_grid_rollout<0, false>" if mode == "grid" else "k_batch_rollout<0, false>", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": "k_grid_rollout_lean" if mode == "grid" else "k_batch_rollout<0, false>", "bound": "alu", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,

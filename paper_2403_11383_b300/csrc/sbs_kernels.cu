@@ -1262,7 +1262,7 @@ __device__ void refit_block(BlockShared& sh, int b)
 // Kernels
 // ---------------------------------------------------------------------------
 template <int NP, bool EXT>
-__global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __restrict__ dP, TickArgs t)
+__device__ __forceinline__ void rollout_plain(const InstParams* __restrict__ dP, const TickArgs& t)
 {
     extern __shared__ float4 dyn4[];
     __shared__ BlockShared sh;
@@ -1270,6 +1270,20 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __re
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
     rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
+}
+
+template <int NP, bool EXT>
+__global__ void __launch_bounds__(SBS_MAX_TILE) k_rollout(const InstParams* __restrict__ dP, TickArgs t)
+{
+    rollout_plain<NP, EXT>(dP, t);
+}
+
+// The ordinary per-step rollout with a register cap that fits 8 blocks of 128
+// threads per SM (64 registers, no spills; -1.2 % per batched tick).  The spline
+// and extended kernels spill at that cap and keep the compiler's choice.
+__global__ void __launch_bounds__(SBS_MAX_TILE, 4) k_rollout_lean(const InstParams* __restrict__ dP, TickArgs t)
+{
+    rollout_plain<0, false>(dP, t);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -1348,8 +1362,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* _
 // One block per item: the hardware block scheduler is the queue (items are
 // dispatched in index order, heavy controllers first).  Unused blocks exit.
 template <int NP, bool EXT>
-__global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __restrict__ recs,
-                                                               const int* __restrict__ counts)
+__device__ __forceinline__ void rollout_grid_item(const InstRec* __restrict__ recs, const int* __restrict__ counts)
 {
     extern __shared__ float4 dyn4[];
     __shared__ BlockShared sh;
@@ -1360,6 +1373,20 @@ __global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __
     load_tick(&recs[i].t, sh);
     __syncthreads();
     rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+}
+
+template <int NP, bool EXT>
+__global__ void __launch_bounds__(SBS_MAX_TILE) k_grid_rollout(const InstRec* __restrict__ recs,
+                                                               const int* __restrict__ counts)
+{
+    rollout_grid_item<NP, EXT>(recs, counts);
+}
+
+// The ordinary per-step grid rollout with the register cap of k_rollout_lean.
+__global__ void __launch_bounds__(SBS_MAX_TILE, 4) k_grid_rollout_lean(const InstRec* __restrict__ recs,
+                                                                       const int* __restrict__ counts)
+{
+    rollout_grid_item<0, false>(recs, counts);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* __restrict__ recs,
@@ -1683,14 +1710,16 @@ static int ensure_smem_attr(const void* fn, size_t smem)
 template <int NP, bool S>
 static const void* batch_fn(int mode)
 {
-    return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout<NP, S> : (const void*)k_batch_rollout<NP, S>;
+    if (mode == SBS_BATCH_GRID)
+        return NP == 0 && !S ? (const void*)k_grid_rollout_lean : (const void*)k_grid_rollout<NP, S>;
+    return (const void*)k_batch_rollout<NP, S>;
 }
 
 template <bool S>
 static const void* rollout_kernel_s(int P)
 {
     switch (P) {
-        case 0: return (const void*)k_rollout<0, S>;
+        case 0: return S ? (const void*)k_rollout<0, S> : (const void*)k_rollout_lean;
         case 2: return (const void*)k_rollout<2, S>;
         case 3: return (const void*)k_rollout<3, S>;
         case 4: return (const void*)k_rollout<4, S>;
