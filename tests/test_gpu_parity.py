@@ -183,6 +183,28 @@ def test_naive_is_best_sample(cuda):
     g.close()
 
 
+def test_naive_with_sampled_frequency(cuda):
+    # Naive with the Gaussian step frequency: the best sample's forces and its
+    # quantised frequency become the mean, variances kept (Alg. 3)
+    cfg = W.config("adaptive_elite_k8192_h25")
+    cfg.update(method="naive", K=3000, H=12, iterations=1, compare_mppi=False, seed=83)
+    prob = W.problem(cfg)
+    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    r = g.solve()
+    Jg, qg, eg = g.read(S.BUF_COST), g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
+    amb = check_frequencies(qg, q, margin)
+    check_costs(Jg, J, kap, skip=amb)
+    kb = int(np.lexsort((np.arange(Jg.size), Jg))[0])
+    assert eg.tolist() == [kb, 0]  # the winner of the single force block, then that block
+    mg, vg = g.state()
+    np.testing.assert_allclose(mg[:-1], th[kb, :-1], atol=MEAN_ATOL)
+    assert mg[-1] == np.float32(qg[kb] / 1000.0)
+    np.testing.assert_array_equal(vg, f32(o.var))
+    assert r["q_freq"] == qg[kb] and r["cost_min"] == float(Jg[kb]) and r["ess"] == 1.0
+    g.close()
+
+
 def test_iterations_compose_on_gpu(cuda):
     # one solve with I iterations equals I single-iteration solves, bit for bit
     cfg = W.config("adaptive_elite_k8192_h25")
