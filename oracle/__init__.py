@@ -56,6 +56,8 @@ def lib():
         sig = {
             "orc_philox4x32_10": (None, [vp, vp, vp]),
             "orc_box_muller": (None, [u32, u32, vp, vp]),
+            "orc_box_muller21": (None, [u32, u32, vp, vp]),
+            "orc_uniforms21": (None, [vp, vp]),
             "orc_normal": (d, [u32, u32, u32, u32, u64]),
             "orc_freq_normal": (d, [u32, u32, u32, u64]),
             "orc_quantise_freq": (u32, [d, d, d, d, d, vp]),
@@ -164,6 +166,19 @@ def box_muller(x, y):
     z0, z1 = C.c_double(), C.c_double()
     lib().orc_box_muller(x, y, C.byref(z0), C.byref(z1))
     return z0.value, z1.value
+
+
+def box_muller21(a, b):
+    z0, z1 = C.c_double(), C.c_double()
+    lib().orc_box_muller21(a, b, C.byref(z0), C.byref(z1))
+    return z0.value, z1.value
+
+
+def uniforms21(words):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    u = np.zeros(6, dtype=np.uint32)
+    lib().orc_uniforms21(_p(w), _p(u))
+    return u
 
 
 def normal(seed, ctrl, k, n, it):

@@ -113,24 +113,48 @@ void orc_box_muller(uint32_t x, uint32_t y, double* z0, double* z1)
     *z1 = r * sin(2.0 * M_PI * u2);
 }
 
+/* Box-Muller on two 21-bit integers: u1 = (a + 1) 2^-21 in (0, 1] and
+ * u2 = b 2^-21 in [0, 1); z0 = r cos(2 pi u2), z1 = r sin(2 pi u2) with
+ * r = sqrt(-2 ln u1). */
+void orc_box_muller21(uint32_t a, uint32_t b, double* z0, double* z1)
+{
+    const double two_m21 = 1.0 / 2097152.0;
+    double u1 = (double)(a + 1u) * two_m21;
+    double u2 = (double)b * two_m21;
+    double r = sqrt(-2.0 * log(u1));
+    *z0 = r * cos(2.0 * M_PI * u2);
+    *z1 = r * sin(2.0 * M_PI * u2);
+}
+
+/* The six 21-bit integers of one 128-bit Philox block (words w0..w3): the top 21
+ * bits of each word, then (low 11 bits of w0, low 10 bits of w1) and (low 11 bits
+ * of w2, low 10 bits of w3), each pair joined high-to-low.  126 of the 128 bits. */
+void orc_uniforms21(const uint32_t w[4], uint32_t u[6])
+{
+    for (int i = 0; i < 4; ++i) u[i] = w[i] >> 11;
+    u[4] = ((w[0] & 0x7FFu) << 10) | (w[1] & 0x3FFu);
+    u[5] = ((w[2] & 0x7FFu) << 10) | (w[3] & 0x3FFu);
+}
+
 /* The counter layout of one sample's normals.
  *   key     = (seed, controller id)
  *   counter = (sample k, draw d, iteration low word, iteration high word)
- *   draw 0  : the step-frequency normal (first Box-Muller output of words 0,1)
- *   draw d>0: normals n = 4(d-1) .. 4(d-1)+3; words (0,1) give n%4 = 0 (cos), 1 (sin),
- *             words (2,3) give n%4 = 2 (cos), 3 (sin).
- * Force normal n of step j, leg i, axis a is n = 12 j + 3 i + a (knot p instead of j
- * for the spline policy). */
+ *   draw 0  : the step-frequency normal (first Box-Muller output of the top 24
+ *             bits of words 0, 1)
+ *   draw d>0: force normals n = 6(d-1) .. 6(d-1)+5 from the block's six 21-bit
+ *             integers: n%6 = 2p (cos) and 2p+1 (sin) from the pair (u_2p, u_2p+1).
+ * Force normal n of a sample is the n-th entry of its decision vector's force
+ * part (12 per step or knot), so each step uses two draws. */
 double orc_normal(uint32_t seed, uint32_t ctrl, uint32_t k, uint32_t n, uint64_t iter)
 {
-    uint32_t ctr[4] = {k, 1u + n / 4u, (uint32_t)iter, (uint32_t)(iter >> 32)};
+    uint32_t ctr[4] = {k, 1u + n / 6u, (uint32_t)iter, (uint32_t)(iter >> 32)};
     uint32_t key[2] = {seed, ctrl};
-    uint32_t w[4];
+    uint32_t w[4], u[6];
     orc_philox4x32_10(ctr, key, w);
+    orc_uniforms21(w, u);
+    unsigned slot = n % 6u, pair = slot / 2u;
     double z0, z1;
-    unsigned slot = n % 4u;
-    if (slot < 2) orc_box_muller(w[0], w[1], &z0, &z1);
-    else orc_box_muller(w[2], w[3], &z0, &z1);
+    orc_box_muller21(u[2 * pair], u[2 * pair + 1], &z0, &z1);
     return (slot % 2u == 0) ? z0 : z1;
 }
 

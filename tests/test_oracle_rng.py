@@ -70,6 +70,39 @@ def test_box_muller_closed_forms(orc):
     assert orc.box_muller(0x00000100, 0x100) == orc.box_muller(0x000001FF, 0x1FF)
 
 
+def test_box_muller21_closed_forms(orc):
+    # a = 2^21 - 1: u1 = 1 -> radius 0; a = 0: u1 = 2^-21 -> radius sqrt(42 ln 2)
+    z0, z1 = orc.box_muller21((1 << 21) - 1, 12345)
+    assert z0 == 0.0 and abs(z1) == 0.0
+    r = math.sqrt(42.0 * math.log(2.0))
+    z0, z1 = orc.box_muller21(0, 0)
+    assert z0 == pytest.approx(r, rel=1e-15) and z1 == 0.0
+    z0, z1 = orc.box_muller21(0, 1 << 19)  # u2 = 1/4: angle pi/2
+    assert abs(z0) < 1e-15 and z1 == pytest.approx(r, rel=1e-15)
+    z0, z1 = orc.box_muller21(0, 1 << 20)  # u2 = 1/2: angle pi
+    assert z0 == pytest.approx(-r, rel=1e-15) and abs(z1) < 1e-14
+
+
+def test_uniforms21_partition_the_block(orc):
+    # the six 21-bit integers take 126 distinct bits of the block: each used input
+    # bit sets exactly one output bit, no two input bits the same one (so the map
+    # is a bijection onto the integers); bits 10 of words 1 and 3 are unused
+    images = set()
+    for word in range(4):
+        for bit in range(32):
+            w = np.zeros(4, dtype=np.uint32)
+            w[word] = np.uint32(1) << np.uint32(bit)
+            u = orc.uniforms21(w)
+            nz = np.nonzero(u)[0]
+            if (word, bit) in ((1, 10), (3, 10)):
+                assert nz.size == 0
+                continue
+            v = int(u[nz[0]])
+            assert nz.size == 1 and v & (v - 1) == 0 and v < (1 << 21)
+            images.add((int(nz[0]), v.bit_length() - 1))
+    assert len(images) == 126
+
+
 def test_normal_moments(orc):
     # 200 000 normals of the force layout: mean 0, variance 1, kurtosis 3
     z = np.array([orc.normal(3, 1, k, n, 5) for k in range(5000) for n in range(40)])
@@ -86,13 +119,15 @@ def test_normal_moments(orc):
 
 
 def test_normal_counter_layout(orc):
-    # normal n uses draw 1 + n // 4; slots 0,1 are words (0,1), slots 2,3 words (2,3)
+    # force normal n uses draw 1 + n // 6; slots 2p, 2p+1 are the pair (u_2p, u_2p+1)
     seed, ctrl, k, it = 9, 4, 17, (1 << 33) + 5
     w = orc.philox4x32_10([k, 1 + 2, it & 0xFFFFFFFF, it >> 32], [seed, ctrl])
-    a0, a1 = orc.box_muller(int(w[0]), int(w[1]))
-    b0, b1 = orc.box_muller(int(w[2]), int(w[3]))
-    got = [orc.normal(seed, ctrl, k, n, it) for n in (8, 9, 10, 11)]
-    assert got == [a0, a1, b0, b1]
+    u = orc.uniforms21(w)
+    want = []
+    for p in range(3):
+        want += list(orc.box_muller21(int(u[2 * p]), int(u[2 * p + 1])))
+    got = [orc.normal(seed, ctrl, k, n, it) for n in range(12, 18)]
+    assert got == want
     w0 = orc.philox4x32_10([k, 0, it & 0xFFFFFFFF, it >> 32], [seed, ctrl])
     assert orc.freq_normal(seed, ctrl, k, it) == orc.box_muller(int(w0[0]), int(w0[1]))[0]
 
