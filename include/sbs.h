@@ -27,8 +27,11 @@
  *   blocks of nf values, block b for set entry b: D = n nf.
  *   Gait phases are integers in units of 1e-9 cycle (1e9 = one cycle).
  *   Random numbers: Philox4x32-10 keyed by (seed, controller_id), counter
- *   (sample, draw, iteration low, iteration high); draw 0 is the frequency,
- *   draw 1 + n/4 holds force normal n (Box-Muller on word pairs (0,1), (2,3)).
+ *   (sample, draw, iteration low, iteration high); draw 0 is the frequency
+ *   (Box-Muller on the top 24 bits of words 0, 1); draw 1 + n/6 holds force
+ *   normal n: six 21-bit integers per 128-bit block (the top 21 bits of each word,
+ *   then the low 11 bits of words 0 and 2 joined to the low 10 bits of words 1
+ *   and 3), Box-Muller on the pairs (u0, u1), (u2, u3), (u4, u5).
  *   With a discrete frequency set of n values, sample k takes entry
  *   floor(n u / 2^24), u the top 24 bits of draw 0's first word.
  *
@@ -379,7 +382,7 @@ int sbs_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, i
 /* The standard normals the controller with key (seed, ctrl) draws in iteration
  * iter (Alg. 1 Sampling): for samples k0 .. k0 + nk - 1, out[i (nn + 1)] is the
  * frequency normal (draw 0) and out[i (nn + 1) + 1 + n] force normal n < nn
- * (draw 1 + n/4).  Device output of nk (nn + 1) floats; enqueued on stream. */
+ * (draw 1 + n/6).  Device output of nk (nn + 1) floats; enqueued on stream. */
 int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
 
 /* Measure the FP32 FMA throughput of the current device with a register-resident

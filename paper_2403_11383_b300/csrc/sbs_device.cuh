@@ -104,27 +104,48 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
     return make_float2(r * c, r * s);
 }
 
-// The four normals of one draw: counter (k, draw, iter lo, iter hi), key (seed, ctrl).
-__device__ __forceinline__ float4 normals4(uint32_t k, uint32_t draw, uint64_t iter, uint32_t seed,
-                                           uint32_t ctrl)
+// Box-Muller on two 21-bit integers: u1 = (a + 1) 2^-21 in (0, 1] and
+// u2 = b 2^-21 in [0, 1) (exact), with the radius and angle evaluated as above.
+__device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
 {
-    const uint4 w = philox4x32_10(make_uint4(k, draw, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
-    const float2 a = box_muller(w.x, w.y);
-    const float2 b = box_muller(w.z, w.w);
-    return make_float4(a.x, a.y, b.x, b.y);
+    const float two_m21 = 4.76837158203125e-7f;
+    const float u1 = __uint2float_rn(a + 1u) * two_m21;
+    const float u2 = __uint2float_rn(b) * two_m21;
+    const float r2 = -2.0f * logf(u1);
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    float s, c;
+    __sincosf(6.28318530717958648f * u2, &s, &c);
+    return make_float2(r * c, r * s);
 }
 
-// The 12 normals of step (or knot) j: draws 1 + 3j .. 3 + 3j.
+// The six force normals of one 128-bit draw: six 21-bit integers (the top 21
+// bits of each word, then the low 11 bits of words 0 and 2 joined to the low 10
+// bits of words 1 and 3), Box-Muller on the pairs (u0, u1), (u2, u3), (u4, u5).
+__device__ __forceinline__ void normals6(uint4 w, float* e)
+{
+    const uint32_t u4 = ((w.x & 0x7ffu) << 10) | (w.y & 0x3ffu);
+    const uint32_t u5 = ((w.z & 0x7ffu) << 10) | (w.w & 0x3ffu);
+    const float2 a = box_muller21(w.x >> 11, w.y >> 11);
+    const float2 b = box_muller21(w.z >> 11, w.w >> 11);
+    const float2 c = box_muller21(u4, u5);
+    e[0] = a.x;
+    e[1] = a.y;
+    e[2] = b.x;
+    e[3] = b.y;
+    e[4] = c.x;
+    e[5] = c.y;
+}
+
+// The 12 force normals of step (or knot) j: draws 1 + 2j and 2 + 2j, counter
+// (k, draw, iter lo, iter hi), key (seed, ctrl).
 __device__ __forceinline__ void normals12(uint32_t k, int j, uint64_t iter, uint32_t seed, uint32_t ctrl,
                                           float e[12])
 {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const float4 z = normals4(k, 1u + 3u * (uint32_t)j + (uint32_t)d, iter, seed, ctrl);
-        e[4 * d + 0] = z.x;
-        e[4 * d + 1] = z.y;
-        e[4 * d + 2] = z.z;
-        e[4 * d + 3] = z.w;
+    for (int d = 0; d < 2; ++d) {
+        const uint4 w = philox4x32_10(
+            make_uint4(k, 1u + 2u * (uint32_t)j + (uint32_t)d, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
+        normals6(w, e + 6 * d);
     }
 }
 
@@ -132,15 +153,7 @@ __device__ __forceinline__ void normals12(uint32_t k, int j, uint64_t iter, uint
 __device__ __forceinline__ void normals12(const PhiloxPre& pp, int j, float e[12])
 {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const uint4 w = philox_draw(pp, 1u + 3u * (uint32_t)j + (uint32_t)d);
-        const float2 a = box_muller(w.x, w.y);
-        const float2 b = box_muller(w.z, w.w);
-        e[4 * d + 0] = a.x;
-        e[4 * d + 1] = a.y;
-        e[4 * d + 2] = b.x;
-        e[4 * d + 3] = b.y;
-    }
+    for (int d = 0; d < 2; ++d) normals6(philox_draw(pp, 1u + 2u * (uint32_t)j + (uint32_t)d), e + 6 * d);
 }
 
 // Step frequency of sample k (Sec. IV-C): clip(mu_f + sigma_f z, f_min, f_max)

@@ -1477,11 +1477,10 @@ __global__ void k_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, i
     o[0] = box_muller(w.x, w.y).x;
     // force draws through the per-sample precomputed Philox state the rollout uses
     const PhiloxPre pp = philox_pre(k, iter, seed, ctrl);
-    for (int d = 0; 4 * d < nn; ++d) {
-        const uint4 u = philox_draw(pp, 1u + (uint32_t)d);
-        const float2 a = box_muller(u.x, u.y), b = box_muller(u.z, u.w);
-        const float zz[4] = {a.x, a.y, b.x, b.y};
-        for (int s = 0; s < 4 && 4 * d + s < nn; ++s) o[1 + 4 * d + s] = zz[s];
+    for (int d = 0; 6 * d < nn; ++d) {
+        float zz[6];
+        normals6(philox_draw(pp, 1u + (uint32_t)d), zz);
+        for (int s = 0; s < 6 && 6 * d + s < nn; ++s) o[1 + 6 * d + s] = zz[s];
     }
 }
 
