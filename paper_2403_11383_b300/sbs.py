@@ -4,6 +4,20 @@ Every step of the controller runs in the library's CUDA kernels.  PyTorch
 provides device memory (through the allocator callbacks below) and streams.
 The binding fails loudly when the compiled library is missing; there is no
 fallback implementation.
+
+One controller, one warm-started solve per control tick (device inputs)::
+
+    from paper_2403_11383_b300 import sbs, workloads
+    cfg = workloads.config("naive_freqset_k10000_h12")   # or a dict of the same keys
+    ctl = sbs.Controller(cfg)
+    res = ctl.solve(x0, xref, gait, f_ext, shift=1)     # x0 [12], xref [H, 12], f_ext [3] CUDA tensors
+    r = sbs.parse_result(res.cpu().numpy())              # u0 (first forces), q_freq, cost_min, status ...
+
+Host inputs: ``ctl.solve_host(...)`` with float32 numpy arrays.  Many
+controllers per launch: ``sbs.Batch(n, workspace_bytes).solve(controllers,
+[c.problem(...) for c in controllers], results)``.  A request loop with
+continuous batching: ``sbs.Server(...).submit(handles, records)`` /
+``poll(tickets)``.  Ground-fixed feet pass ``feet=`` ([4, 2] ground positions).
 """
 from __future__ import annotations
 
