@@ -747,7 +747,7 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     int* heads = sl.heads;
     void* args[] = {(void*)&recs, (void*)&counts, (void*)&heads};
     const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode)};
-    const int threads[3] = {T, kSelectThreads, kRefitThreads};
+    const int threads[3] = {T, kSelectThreads, kBatchRefitThreads};
     const size_t shm[3] = {smem, sel_smem, 0};
     cudaGraphNode_t prev = n_ms;
     for (int k = 0; k < 3 && ok; ++k) {

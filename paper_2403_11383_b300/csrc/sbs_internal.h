@@ -12,7 +12,8 @@ constexpr uint32_t kPhaseOne = 1000000000u;  // one gait cycle in 1e-9 cycle
 constexpr int kMaxKnots = 8;
 constexpr int kPartHeader = 8;               // floats ahead of the per-dimension sums in a partial row
 constexpr int kGroup = 16;                   // tiles whose partial rows one block combines
-constexpr int kRefitThreads = 256;
+constexpr int kRefitThreads = 256;       // plain solves: few controllers, possibly many elites per step
+constexpr int kBatchRefitThreads = 128;  // batched ticks: thousands of small refit items (8 blocks per SM)
 constexpr int kSelectThreads = 1024;
 constexpr int kSelectSmemMaxK = 32768;       // costs staged in shared memory up to this K
 constexpr size_t kMaxDynamicSmem = 220 * 1024;  // dynamic shared memory one block may use (below the 227 KB

@@ -49,6 +49,7 @@ struct __align__(16) BlockShared {
     int digit, below, count;
     float mu12[12], vr12[12], dbar[12];
     float wacc[32][12];
+    float wacc2[kRefitThreads / 32][12];
 };
 
 // A shared-memory vector load the compiler may not hoist out of the step loop
@@ -1150,7 +1151,7 @@ __device__ void refit_block(BlockShared& sh, int b)
 {
     const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const float* sm = P.state[t.src];
     const float* sv = sm + P.D;
     float* dm = P.state[1 - t.src];
@@ -1180,26 +1181,44 @@ __device__ void refit_block(BlockShared& sh, int b)
             }
         } else {
             // one pass: sums of the deviations and of their squares, both taken
-            // about the first elite s deviation d0 (keeps the cancellation small)
+            // about the first elite's deviation d0 (keeps the cancellation small).
+            // The order of the sums is that of kRefitThreads virtual lanes (lane v
+            // takes elites v, v + kRefitThreads, ...; warp totals in warp order), so
+            // a block of any size that divides kRefitThreads gives the same bits.
             if (tid < 12) sh.dbar[tid] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + tid);
             __syncthreads();
-            float s[12], s2[12];
+            for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
+                const int vl = v0 + tid, vw = vl >> 5;  // virtual lane and warp
+                float s[12], s2[12];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
-            for (int e = tid; e < Ke; e += blockDim.x) {
-                const int kb = __ldcg(elite + e);
-                const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
-                const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
-                const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
+                for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
+                for (int e = vl; e < Ke; e += kRefitThreads) {
+                    const int kb = __ldcg(elite + e);
+                    const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
+                    const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
+                    const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
-                for (int c = 0; c < 12; ++c) {
-                    const float q = d[c] - sh.dbar[c];
-                    s[c] += q;
-                    s2[c] = fmaf(q, q, s2[c]);
+                    for (int c = 0; c < 12; ++c) {
+                        const float q = d[c] - sh.dbar[c];
+                        s[c] += q;
+                        s2[c] = fmaf(q, q, s2[c]);
+                    }
                 }
+                float o[3];
+                int c0 = warp_sum12(s, o);
+                if ((lane & 7) == 0)
+                    for (int i = 0; i < 3; ++i) sh.wacc[vw][c0 + i] = o[i];
+                c0 = warp_sum12(s2, o);
+                if ((lane & 7) == 0)
+                    for (int i = 0; i < 3; ++i) sh.wacc2[vw][c0 + i] = o[i];
             }
-            const float tot = block_sum12(sh, s);
-            const float tot2 = block_sum12(sh, s2);
+            __syncthreads();
+            float tot = 0.0f, tot2 = 0.0f;
+            if (tid < 12)
+                for (int w = 0; w < kRefitThreads / 32; ++w) {
+                    tot += sh.wacc[w][tid];
+                    tot2 += sh.wacc2[w][tid];
+                }
             if (tid < 12) {
                 const float m = tot / (float)Ke;
                 var_c = fmaxf(fmaf(-m, m, tot2 / (float)Ke), P.var_min);
@@ -1227,25 +1246,33 @@ __device__ void refit_block(BlockShared& sh, int b)
             if (P.method == SBS_NAIVE) {
                 mean_f = (float)__ldcg(t.ws.q + __ldcg(elite)) / 1000.0f;
             } else {
-                float s = 0.0f;
-                for (int e = tid; e < Ke; e += blockDim.x) s += (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f;
-                s = warp_sum(s);
+                // two passes over kRefitThreads virtual lanes (the order is
+                // independent of the block size, as above)
                 __syncthreads();
-                if (lane == 0) sh.red[warp][0] = s;
+                for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
+                    const int vl = v0 + tid;
+                    float s = 0.0f;
+                    for (int e = vl; e < Ke; e += kRefitThreads) s += (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f;
+                    s = warp_sum(s);
+                    if (lane == 0) sh.red[vl >> 5][0] = s;
+                }
                 __syncthreads();
                 float tot = 0.0f;
-                for (int w = 0; w < nw; ++w) tot += sh.red[w][0];
+                for (int w = 0; w < kRefitThreads / 32; ++w) tot += sh.red[w][0];
                 mean_f = tot / (float)Ke;
-                float s2 = 0.0f;
-                for (int e = tid; e < Ke; e += blockDim.x) {
-                    const float d = (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f - mean_f;
-                    s2 = fmaf(d, d, s2);
+                for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
+                    const int vl = v0 + tid;
+                    float s2 = 0.0f;
+                    for (int e = vl; e < Ke; e += kRefitThreads) {
+                        const float d = (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f - mean_f;
+                        s2 = fmaf(d, d, s2);
+                    }
+                    s2 = warp_sum(s2);
+                    if (lane == 0) sh.red[vl >> 5][1] = s2;
                 }
-                s2 = warp_sum(s2);
-                if (lane == 0) sh.red[warp][1] = s2;
                 __syncthreads();
                 float tot2 = 0.0f;
-                for (int w = 0; w < nw; ++w) tot2 += sh.red[w][1];
+                for (int w = 0; w < kRefitThreads / 32; ++w) tot2 += sh.red[w][1];
                 vf = fmaxf(tot2 / (float)Ke, P.var_f_min);
             }
         }
@@ -1403,7 +1430,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* _
     select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
 }
 
-__global__ void __launch_bounds__(kRefitThreads) k_grid_refit(const InstRec* __restrict__ recs,
+__global__ void __launch_bounds__(kBatchRefitThreads) k_grid_refit(const InstRec* __restrict__ recs,
                                                              const int* __restrict__ counts)
 {
     __shared__ BlockShared sh;
@@ -1436,7 +1463,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_batch_select(const InstRec* 
     }
 }
 
-__global__ void __launch_bounds__(kRefitThreads) k_batch_refit(const InstRec* __restrict__ recs,
+__global__ void __launch_bounds__(kBatchRefitThreads) k_batch_refit(const InstRec* __restrict__ recs,
                                                               const int* __restrict__ counts, int* heads)
 {
     __shared__ BlockShared sh;
@@ -1835,7 +1862,7 @@ int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int c
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, T, smem) != cudaSuccess) return SBS_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_batch_select, kSelectThreads, sel_smem) != cudaSuccess)
         return SBS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_batch_refit, kRefitThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_batch_refit, kBatchRefitThreads, 0) != cudaSuccess)
         return SBS_ERR_CUDA;
     if (b1 < 1 || b2 < 1 || b3 < 1) return SBS_ERR_INVALID_ARG;
     grids[0] = sms * b1;
@@ -1851,7 +1878,7 @@ int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int*
     cudaStream_t s = (cudaStream_t)stream;
     const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode)};
     if (!fns[0]) return SBS_ERR_INVALID_ARG;
-    const dim3 blocks[3] = {dim3(T), dim3(kSelectThreads), dim3(kRefitThreads)};
+    const dim3 blocks[3] = {dim3(T), dim3(kSelectThreads), dim3(kBatchRefitThreads)};
     const size_t shm[3] = {smem, sel_smem, 0};
     const InstRec* r = dRecs;
     const int* c = dCounts;
