@@ -106,15 +106,19 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 
 // Box-Muller on two 21-bit integers: u1 = (a + 1) 2^-21 in (0, 1] and
 // u2 = b 2^-21 in [0, 1) (exact), with the radius and angle evaluated as above.
+// The integers (at most 2^21) are turned into floats without a conversion
+// instruction: 0x4B000000 | n is the float 2^23 + n, and fma(2^23 + n, c, -2^23 c)
+// is n c rounded once, the same bits as float(n) * c.
 __device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
 {
     const float two_m21 = 4.76837158203125e-7f;
-    const float u1 = __uint2float_rn(a + 1u) * two_m21;
-    const float u2 = __uint2float_rn(b) * two_m21;
+    const float c_ang = 6.28318530717958648f * two_m21;
+    const float u1 = fmaf(__int_as_float(0x4b000000 | (int)(a + 1u)), two_m21, -4.0f);
+    const float ang = fmaf(__int_as_float(0x4b000000 | (int)b), c_ang, -8388608.0f * c_ang);
     const float r2 = -2.0f * logf(u1);
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     float s, c;
-    __sincosf(6.28318530717958648f * u2, &s, &c);
+    __sincosf(ang, &s, &c);
     return make_float2(r * c, r * s);
 }
 
