@@ -219,10 +219,17 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
                                             const float G[12], unsigned live = 0xfu, bool penalty = true)
 {
     float r = 0.0f;
+    const float4* xr4 = reinterpret_cast<const float4*>(xr);  // 16-byte aligned rows of 12
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
-        const float e = x[c] - xr[c];
-        r = fmaf(P.Q[c] * e, e, r);
+    for (int q = 0; q < 3; ++q) {
+        const float4 a = xr4[q];
+        const float xa[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = 4 * q + i;
+            const float e = x[c] - xa[i];
+            r = fmaf(P.Q[c] * e, e, r);
+        }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {

@@ -30,21 +30,27 @@ struct InstParams {
     int32_t n_freq;       // discrete step-frequency set size (0: none)
     int32_t nb;           // force blocks of the distribution: n_freq, else 1
     uint32_t freq[SBS_MAX_FREQ];  // the set, mHz
+    // model and cost constants read at every step, in 16-byte groups
+    float Q[12];
+    float R[3], w_fc;
+    float foot[12];
+    float inertia[3], inv_mass;
+    float inv_inertia[3], dt;
+    float gravity[3], mu;
     int32_t world_feet;   // 1: stance feet fixed on the ground, footholds at touchdown
     float inv_g;          // 1 / |g_z| (foothold rule)
     int32_t friction_project;  // 1: stance forces projected onto the friction cone, no penalty
     float inv_1pmu2;      // 1 / (1 + mu^2)
     float w_terminal;     // terminal state cost weight (0: none)
-    int32_t pad1[2];
     uint32_t dt_us, q_init, seed, ctrl;
-    float dt, lambda, inv_lambda, inv_mass, weight_z;
-    float inertia[3], inv_inertia[3], foot[12], gravity[3];
-    float Q[12], R[3], w_fc, mu, rho, f_nominal, f_min, f_max;
+    float lambda, inv_lambda, weight_z;
+    float rho, f_nominal, f_min, f_max;
     float var_init, var_min, var_f_init, var_f_min;
     float* state[2];   // ping-pong distribution: mean[D] then var[D] (nb force blocks of nf, then the frequency)
     float* mppi_mean;  // [D]
     const float* Bsp;  // [H][P] spline basis
     const float* Ssp;  // [P][P] spline shift-by-one-step map
+    int32_t pad1[2];
 };
 
 // Scratch of one in-flight solve.  Counters are zero whenever no launch uses them.

@@ -449,10 +449,18 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         if constexpr (NP == 0) {
             float e[12];
             normals12(pp, j, e);
+            const float4* m4 = reinterpret_cast<const float4*>(mu + 12 * j);  // 16-byte aligned rows
+            const float4* s4 = reinterpret_cast<const float4*>(sd + 12 * j);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                e[c] = sd[12 * j + c] * e[c];  // deviation sigma * eps
-                G[c] = mu[12 * j + c] + e[c];
+            for (int q = 0; q < 3; ++q) {
+                const float4 ma = m4[q], sa = s4[q];
+                const float mv[4] = {ma.x, ma.y, ma.z, ma.w}, sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = 4 * q + i;
+                    e[c] = sv[i] * e[c];  // deviation sigma * eps
+                    G[c] = mv[i] + e[c];
+                }
             }
             if (valid) {
                 float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
