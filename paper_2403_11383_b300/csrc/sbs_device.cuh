@@ -243,8 +243,8 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
         // (|G_xy| as x * rsqrt(x), exact zero for a zero force)
         const float t2 = fmaf(gx, gx, gy * gy);
         const float slip = (t2 > 0.0f ? t2 * rsqrtf(t2) : 0.0f) - P.mu * gz;
-        float pen = slip > 0.0f ? slip * slip : 0.0f;
-        pen += gz < 0.0f ? gz * gz : 0.0f;
+        const float sp = fmaxf(slip, 0.0f), gn = fminf(gz, 0.0f);
+        const float pen = fmaf(gn, gn, sp * sp);
         r = fmaf(P.w_fc, pen, r);
     }
     return r;
@@ -291,7 +291,7 @@ __device__ __forceinline__ void srbd_integrate(const InstParams& P, float x[12],
     const float wd1 = (t1 - (w2 * L0 - w0 * L2)) * P.inv_inertia[1];
     const float wd2 = (t2 - (w0 * L1 - w1 * L0)) * P.inv_inertia[2];
     // E'^{-1}(Phi) omega for the ZYX angles
-    const float ic = __frcp_rn(cp);
+    const float ic = __fdividef(1.0f, cp);
     const float a = sr * w1 + cr * w2;
     const float rd = w0 + sp * ic * a;
     const float pd = cr * w1 - sr * w2;
@@ -338,9 +338,9 @@ __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], cons
         const float by = R01 * gx + R11 * gy + R21 * gz;
         const float bz = R02 * gx + R12 * gy + R22 * gz;
         const float rx = P.foot[3 * i], ry = P.foot[3 * i + 1], rz = P.foot[3 * i + 2];
-        t0 += ry * bz - rz * by;
-        t1 += rz * bx - rx * bz;
-        t2 += rx * by - ry * bx;
+        t0 = fmaf(-rz, by, fmaf(ry, bz, t0));
+        t1 = fmaf(-rx, bz, fmaf(rz, bx, t1));
+        t2 = fmaf(-ry, bx, fmaf(rx, by, t2));
     }
     srbd_integrate(P, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
 }
