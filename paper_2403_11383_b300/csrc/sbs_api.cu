@@ -132,7 +132,9 @@ void fill_params(const sbs_config* cfg, InstParams* out)
     P.inv_mass = 1.0f / cfg->model.mass;
     P.weight_z = cfg->model.mass * -cfg->model.gravity[2];
     for (int a = 0; a < 3; ++a) {
-        P.inertia[a] = cfg->model.inertia[a];
+        const double I0 = cfg->model.inertia[a], I1 = cfg->model.inertia[(a + 1) % 3],
+                     I2 = cfg->model.inertia[(a + 2) % 3];
+        P.gyro[a] = (float)((I1 - I2) / I0);
         P.inv_inertia[a] = 1.0f / cfg->model.inertia[a];
         P.gravity[a] = cfg->model.gravity[a];
         P.R[a] = cfg->cost.R[a];

@@ -286,10 +286,11 @@ __device__ __forceinline__ void srbd_integrate(const InstParams& P, float x[12],
                                                float t2, const float fe[3])
 {
     const float w0 = x[9], w1 = x[10], w2 = x[11];
-    const float L0 = P.inertia[0] * w0, L1 = P.inertia[1] * w1, L2 = P.inertia[2] * w2;
-    const float wd0 = (t0 - (w1 * L2 - w2 * L1)) * P.inv_inertia[0];
-    const float wd1 = (t1 - (w2 * L0 - w0 * L2)) * P.inv_inertia[1];
-    const float wd2 = (t2 - (w0 * L1 - w1 * L0)) * P.inv_inertia[2];
+    // I^{-1} (t - omega x I omega) with a diagonal I: component a is
+    // t_a / I_a + omega_{a+1} omega_{a+2} (I_{a+1} - I_{a+2}) / I_a
+    const float wd0 = fmaf(w1 * w2, P.gyro[0], t0 * P.inv_inertia[0]);
+    const float wd1 = fmaf(w2 * w0, P.gyro[1], t1 * P.inv_inertia[1]);
+    const float wd2 = fmaf(w0 * w1, P.gyro[2], t2 * P.inv_inertia[2]);
     // E'^{-1}(Phi) omega for the ZYX angles
     const float ic = __fdividef(1.0f, cp);
     const float a = sr * w1 + cr * w2;

@@ -34,7 +34,7 @@ struct InstParams {
     float Q[12];
     float R[3], w_fc;
     float foot[12];
-    float inertia[3], inv_mass;
+    float gyro[3], inv_mass;  // gyro[a] = (I_{a+1} - I_{a+2}) / I_a (indices mod 3)
     float inv_inertia[3], dt;
     float gravity[3], mu;
     int32_t world_feet;   // 1: stance feet fixed on the ground, footholds at touchdown

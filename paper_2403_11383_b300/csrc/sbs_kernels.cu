@@ -487,13 +487,17 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         }
         unsigned st = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (ph[i] >= duty) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
-            else st |= 1u << i;
-        }
+        for (int i = 0; i < 4; ++i) st |= (ph[i] < duty ? 1u : 0u) << i;
         // legs in swing on the whole warp skip their terms (per-step forces only:
-        // the spline kernel runs faster without the branches)
+        // the spline kernel runs faster without the branches); swing forces are
+        // zeroed only where a leg is live on the warp but swings on some lanes
         const unsigned live = NP == 0 ? __reduce_or_sync(kFull, st) : 0xfu;
+        const unsigned all = NP == 0 ? __reduce_and_sync(kFull, st) : st;
+        if (live != all) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (!(st & (1u << i))) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
+        }
         bool penalty = true;
         if constexpr (EXT) {
             if (P.friction_project) {  // the policy output constrained to the cone (Sec. IV-B)
