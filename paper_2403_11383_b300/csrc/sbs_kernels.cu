@@ -47,6 +47,7 @@ struct __align__(16) BlockShared {
     int hist[256];
     int wtot[32], wtot2[32];
     int digit, below, count;
+    unsigned char sched[SBS_MAX_H];  // stance legs of every step when all samples share the frequency
     float mu12[12], vr12[12], dbar[12];
     float wacc[32][12];
     float wacc2[kRefitThreads / 32][12];
@@ -193,6 +194,18 @@ __device__ void stage(BlockShared& sh, const Views& v, int P_knots)
             sh.var_f = 0.0f;
         }
         sh.sig_f = sqrtf(sh.var_f);
+    }
+    if (P_knots == 0 && !P.adaptive && P.n_freq == 0) {  // one contact schedule for every sample
+        const uint64_t step = (uint64_t)P.q_init * P.dt_us;
+        for (int j = threadIdx.x; j < P.H; j += blockDim.x) {
+            unsigned st = 0;
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t p0 = t.phase0 + t.offset[i];
+                const uint64_t ph = ((uint64_t)(p0 >= kPhaseOne ? p0 - kPhaseOne : p0) + (uint64_t)j * step) % kPhaseOne;
+                st |= (ph < t.duty ? 1u : 0u) << i;
+            }
+            sh.sched[j] = (unsigned char)st;
+        }
     }
     __syncthreads();
     if (P_knots > 0) {  // mean force trajectory of each block's spline mean
@@ -403,6 +416,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         ph[i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
     }
     const uint32_t step = q * P.dt_us;
+    const bool uniform_q = NP == 0 && !P.adaptive && P.n_freq == 0;
     const uint32_t duty = t.duty;
     // world-fixed feet: ground positions, last step's stance flags, T_st / 2
     float fx[4], fy[4];
@@ -485,14 +499,26 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
                 G[c] = s;
             }
         }
-        unsigned st = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) st |= (ph[i] < duty ? 1u : 0u) << i;
         // legs in swing on the whole warp skip their terms (per-step forces only:
         // the spline kernel runs faster without the branches); swing forces are
         // zeroed only where a leg is live on the warp but swings on some lanes
-        const unsigned live = NP == 0 ? __reduce_or_sync(kFull, st) : 0xfu;
-        const unsigned all = NP == 0 ? __reduce_and_sync(kFull, st) : st;
+        unsigned st, live, all;
+        if (uniform_q) {  // the block-wide schedule
+            st = sh.sched[j];
+            live = NP == 0 ? st : 0xfu;
+            all = st;
+        } else {
+            st = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) st |= (ph[i] < duty ? 1u : 0u) << i;
+            live = NP == 0 ? __reduce_or_sync(kFull, st) : 0xfu;
+            all = NP == 0 ? __reduce_and_sync(kFull, st) : st;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ph[i] += step;
+                if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
+            }
+        }
         if (live != all) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -517,11 +543,6 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             }
         } else {
             srbd_step(P, x, G, fe, live);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ph[i] += step;
-            if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
         }
     }
     if (P.w_terminal > 0.0f) {  // optional terminal cost of the state after the last step
