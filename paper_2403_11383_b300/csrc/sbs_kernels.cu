@@ -1204,6 +1204,8 @@ __device__ void refit_block(BlockShared& sh, int b)
             shifted_entry(P, t, sm, sv, 12 * b + tid, m, var);
             sh.mu12[tid] = m;
             sh.vr12[tid] = var;
+        } else if (tid >= 32 && tid < 44 && !diverged) {  // the first elite's deviation, alongside
+            sh.dbar[tid - 32] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + (tid - 32));
         }
         __syncthreads();
         float mean_c = 0.0f, var_c = 0.0f;  // valid in threads < 12
@@ -1218,15 +1220,15 @@ __device__ void refit_block(BlockShared& sh, int b)
             // The order of the sums is that of kRefitThreads virtual lanes (lane v
             // takes elites v, v + kRefitThreads, ...; warp totals in warp order), so
             // a block of any size that divides kRefitThreads gives the same bits.
-            if (tid < 12) sh.dbar[tid] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + tid);
-            __syncthreads();
             for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
                 const int vl = v0 + tid, vw = vl >> 5;  // virtual lane and warp
                 float s[12], s2[12];
 #pragma unroll
                 for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
+                int kb = vl < Ke ? __ldcg(elite + vl) : 0;
                 for (int e = vl; e < Ke; e += kRefitThreads) {
-                    const int kb = __ldcg(elite + e);
+                    // the next elite's index is loaded before this one's row is used
+                    const int kn = e + kRefitThreads < Ke ? __ldcg(elite + e + kRefitThreads) : 0;
                     const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
                     const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
                     const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
@@ -1236,6 +1238,7 @@ __device__ void refit_block(BlockShared& sh, int b)
                         s[c] += q;
                         s2[c] = fmaf(q, q, s2[c]);
                     }
+                    kb = kn;
                 }
                 float o[3];
                 int c0 = warp_sum12(s, o);
@@ -1396,6 +1399,25 @@ __device__ __forceinline__ int find_rec(const InstRec* recs, int n, int it, int 
     return lo;
 }
 
+// The same record found by the whole block at once: record i holds item it when
+// begin(i) <= it < begin(i + 1), so every thread tests its records with two
+// independent loads instead of the search's chain of dependent ones.
+__device__ __forceinline__ int find_rec_block(BlockShared& sh, const InstRec* recs, int n, int it, int which)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const InstRec& a = recs[i];
+        const int b0 = which == 0 ? a.tile_begin : (which == 1 ? a.select_begin : a.refit_begin);
+        int b1 = 0x7fffffff;
+        if (i + 1 < n) {
+            const InstRec& c = recs[i + 1];
+            b1 = which == 0 ? c.tile_begin : (which == 1 ? c.select_begin : c.refit_begin);
+        }
+        if (b0 <= it && it < b1) sh.item = i;
+    }
+    __syncthreads();
+    return sh.item;
+}
+
 // counts = {controllers, tile items, selection items, refit items}; heads = queue heads.
 // Every controller of one launch uses the same policy (NP).
 template <int NP, bool EXT>
@@ -1428,7 +1450,7 @@ __device__ __forceinline__ void rollout_grid_item(const InstRec* __restrict__ re
     __shared__ BlockShared sh;
     const int it = blockIdx.x;
     if (it >= counts[1]) return;
-    const int i = find_rec(recs, counts[0], it, 0);
+    const int i = find_rec_block(sh, recs, counts[0], it, 0);
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
@@ -1456,7 +1478,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* _
     __shared__ BlockShared sh;
     const int it = blockIdx.x;
     if (it >= counts[2]) return;
-    const int i = find_rec(recs, counts[0], it, 1);
+    const int i = find_rec_block(sh, recs, counts[0], it, 1);
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
@@ -1469,7 +1491,7 @@ __global__ void __launch_bounds__(kBatchRefitThreads) k_grid_refit(const InstRec
     __shared__ BlockShared sh;
     const int it = blockIdx.x;
     if (it >= counts[3]) return;
-    const int i = find_rec(recs, counts[0], it, 2);
+    const int i = find_rec_block(sh, recs, counts[0], it, 2);
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
