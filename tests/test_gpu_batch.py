@@ -117,6 +117,38 @@ def test_same_alone_and_in_the_mix():
     assert bytes(r1.cpu().numpy()) == bytes(r8[k * S.RESULT_BYTES:(k + 1) * S.RESULT_BYTES].cpu().numpy())
 
 
+def test_packed_closed_loop_equals_solve():
+    # one Packed object edited in place (gait phase, shift) tick after tick gives
+    # the same bits as packing fresh problems on every call
+    import torch
+    mix = _mix()
+    a = [S.Controller(c) for c, _ in mix]
+    p = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(pr) for _, pr in mix]
+    n = len(mix)
+    ba = S.Batch(n, sum(c.workspace_bytes() + 256 for c in a))
+    bp = S.Batch(n, 2 * sum(c.workspace_bytes() + 256 for c in p), inflight=2)  # split between two ticks
+    ra = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rp = torch.empty_like(ra)
+    packed = S.Packed(p, [p[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 0, feet=tens[i][3])
+                          for i in range(n)])
+    for tick in range(3):
+        probs = [a[i].problem(*tens[i][:2], _gait(mix[i][1], tick, mix[i][0]), tens[i][2], min(tick, 1),
+                              feet=tens[i][3]) for i in range(n)]
+        ba.solve(a, probs, ra)
+        for i in range(n):
+            packed.problems[i].gait.phase0 = _gait(mix[i][1], tick, mix[i][0])["phase0"]
+            packed.problems[i].shift = min(tick, 1)
+        bp.solve_packed(packed, rp)
+        torch.cuda.synchronize()
+        assert bytes(ra.cpu().numpy()) == bytes(rp.cpu().numpy())
+    for i in range(n):
+        np.testing.assert_array_equal(_state(a[i])[0], _state(p[i])[0])
+        np.testing.assert_array_equal(_state(a[i])[1], _state(p[i])[1])
+    ba.close()
+    bp.close()
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
