@@ -354,6 +354,15 @@ class Controller:
         check(lib().sbs_solve(self._h, C.byref(p), C.byref(result), _stream_ptr(stream)), "sbs_solve")
         return result
 
+    def solve_packed(self, problem: Problem, result, stream=None):
+        """One solve of a Problem built once by problem() (device or host memory, as
+        it says) and edited in place between ticks (problem.gait.phase0,
+        problem.shift): nothing is marshalled per call.  result: a uint8 CUDA
+        tensor of RESULT_BYTES for device problems, a Result for host problems."""
+        out = C.byref(result) if isinstance(result, Result) else C.c_void_p(result.data_ptr())
+        check(lib().sbs_solve(self._h, C.byref(problem), out, _stream_ptr(stream)), "sbs_solve")
+        return result
+
     def read(self, which: int, stream=None):
         import torch
         naive_n = max(1, len(self.cfg.get("freq_set_mhz", ()))) + 1  # per-block winners, best block

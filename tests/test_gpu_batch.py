@@ -149,6 +149,35 @@ def test_packed_closed_loop_equals_solve():
     bp.close()
 
 
+@pytest.mark.parametrize("host", [False, True])
+def test_controller_solve_packed_equals_solve(host):
+    # a Problem built once and edited in place gives the bits of per-call solves
+    import torch
+    c, pr = _mix()[1]
+    a, p = S.Controller(c), S.Controller(c)
+    f32 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+    if host:
+        x0, xr, fe = f32(pr["x0"]), f32(pr["xref"]), f32(pr["f_ext"])
+    else:
+        x0, xr, fe, _ = _tensors(pr)
+    prob = p.problem(x0, xr, pr["gait"], fe, 0, host=host)
+    for tick in range(3):
+        g = _gait(pr, tick, c)
+        prob.gait.phase0, prob.shift = g["phase0"], min(tick, 1)
+        if host:
+            ra = a.solve_host(x0, xr, g, fe, min(tick, 1))
+            rp = p.solve_packed(prob, S.Result())
+            torch.cuda.synchronize()
+            assert bytes(ra) == bytes(rp)
+        else:
+            ra = a.solve(x0, xr, g, fe, min(tick, 1))
+            rp = p.solve_packed(prob, torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device="cuda"))
+            torch.cuda.synchronize()
+            assert bytes(ra.cpu().numpy()) == bytes(rp.cpu().numpy())
+    np.testing.assert_array_equal(_state(a)[0], _state(p)[0])
+    np.testing.assert_array_equal(_state(a)[1], _state(p)[1])
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
