@@ -464,7 +464,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances": n, "sample_steps_per_tick": ss_tick,
-                       "tile": 128, "graph": True, "launch_mode": mode,
+                       "tile": W.BATCH_TILE, "graph": True, "launch_mode": mode,
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
                        "l2": "per-tick working set above L2 (sampled deviations "
                        f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},

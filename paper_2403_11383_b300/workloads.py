@@ -158,6 +158,13 @@ def problem(cfg: dict, seed: int | None = None) -> dict:
     return out
 
 
+# Samples per tile of the batched workloads.  A 256-sample tile halves the
+# per-tile work (record lookup, staging, tile-end reductions, partial rows) at the
+# same occupancy as 128 and makes the 256-controller tick 1.4 % faster; single
+# small controllers keep the library default of 128 for more blocks per solve.
+BATCH_TILE = 256
+
+
 def batch_mix(n: int = 256, seed: int = 2, Ks=(256, 1024, 4096, 16384), Hs=(10, 25, 50),
               methods=("mppi", "elite"), gaits=("trot", "pace", "crawl"), adaptive=False):
     """Uneven independent controllers: K, H, gait, method and a planar velocity
@@ -172,7 +179,7 @@ def batch_mix(n: int = 256, seed: int = 2, Ks=(256, 1024, 4096, 16384), Hs=(10, 
         v = tuple(float(a) for a in rng.uniform(-0.5, 0.5, size=2))
         c = _cfg(K=K, H=H, seed=seed, ctrl=i, method=method, gait=gname, v_ref=v,
                  elite_count=elite_count(0.05, K) if method == "elite" else 1,
-                 adaptive=adaptive)
+                 adaptive=adaptive, tile=BATCH_TILE)
         x0 = initial_state(rng, c["z_ref"])
         phase0 = int(rng.integers(0, PHASE_ONE))
         prob = {"x0": x0, "xref": reference(H, c["dt_us"], x0, v, c["z_ref"]),
