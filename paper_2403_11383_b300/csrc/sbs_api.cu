@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <numeric>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -280,8 +282,10 @@ int sbs_create(const sbs_config* cfg, const sbs_allocator* alloc, sbs_handle** o
     int st = validate_config(cfg);
     if (st) return st;
     if (alloc && (!alloc->alloc || !alloc->free)) return SBS_ERR_INVALID_ARG;
+    static std::atomic<uint64_t> next_uid{1};
     sbs_handle* h = new (std::nothrow) sbs_handle();
     if (!h) return SBS_ERR_OOM;
+    h->uid = next_uid.fetch_add(1);
     h->cfg = *cfg;
     h->has_alloc = alloc != nullptr;
     if (alloc) h->alloc = *alloc;
@@ -609,6 +613,19 @@ struct sbs_batch_slot {
     size_t key_smem, key_sel;
     int key_T, key_var, key_mode;
     int grids[3];
+    size_t copy_bytes;    // bytes the graph's record copy moves
+};
+
+// What a batched tick needs that depends on its controllers alone (not on their
+// problems or state): checked and computed when the list of controllers differs
+// from the last call's, reused otherwise.
+struct sbs_batch_plan {
+    std::vector<const sbs_handle*> h;
+    std::vector<uint64_t> uid;
+    std::vector<int> order;  // heavier tiles first
+    size_t smem = 0, sel_smem = 0, arena = 0;
+    long long counters = 0;
+    bool ext = false;
 };
 
 struct sbs_batch {
@@ -626,6 +643,7 @@ struct sbs_batch {
     bool profiling;
     cudaEvent_t ev[4];
     bool ev_valid;
+    sbs_batch_plan plan;
 };
 
 extern "C" int sbs_batch_create(int max_instances, int inflight, size_t workspace_bytes, const sbs_allocator* alloc,
@@ -736,6 +754,7 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     cudaGraphNode_t n_cp, n_ms;
     bool ok = cudaGraphAddMemcpyNode1D(&n_cp, g, nullptr, 0, sl.dev, sl.pin, b->bytes, cudaMemcpyHostToDevice) ==
               cudaSuccess;
+    sl.copy_bytes = b->bytes;
     cudaMemsetParams mp;
     std::memset(&mp, 0, sizeof(mp));
     mp.dst = sl.heads;
@@ -795,44 +814,77 @@ static int update_graph_grids(sbs_batch_slot& sl, const int grids[3])
     return SBS_OK;
 }
 
-extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
-                               sbs_result* results, void* stream)
+// The controllers' own checks (same tile and policy, one iteration, distinct
+// handles) and the launch sizes and tile order that follow from them.
+static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
 {
-    if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!handles[0]) return SBS_ERR_INVALID_ARG;
-    const int T = handles[0]->hP.T;
-    const int Pk = handles[0]->hP.P;
-    bool ext = false;  // some controller uses an extended model feature
+    pl.h.clear();
+    pl.uid.clear();
+    const int T = handles[0]->hP.T, Pk = handles[0]->hP.P;
     size_t smem = 0, sel_smem = 0, arena = 0;
     long long counters = 0;
-    std::vector<int> order(n);
+    bool ext = false;  // some controller uses an extended model feature
     for (int i = 0; i < n; ++i) {
         const sbs_handle* h = handles[i];
-        const sbs_problem* p = &probs[i];
-        if (!h || !p->x0 || !p->xref || p->host_memory || h->hP.T != T || h->hP.P != Pk) return SBS_ERR_INVALID_ARG;
-        if (h->hP.world_feet && !p->feet) return SBS_ERR_INVALID_ARG;
-        if (h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
-        if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
+        if (h->hP.T != T || h->hP.P != Pk || h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb));
         ext = ext || h->hP.n_freq > 0 || h->hP.world_feet || h->hP.friction_project;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
         arena += align_up(h->wsl.bytes, 256);
         counters += h->wsl.counters;
-        order[i] = i;
     }
-    if (arena > b->arena_bytes || counters > b->counter_words) return SBS_ERR_BUDGET;
     {
         std::vector<const sbs_handle*> u(handles, handles + n);
         std::sort(u.begin(), u.end());
         if (std::adjacent_find(u.begin(), u.end()) != u.end()) return SBS_ERR_INVALID_ARG;
     }
     // heavier tiles first (longer horizon, then more tiles) so the tail is short
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         const InstParams &A = handles[a]->hP, &C = handles[c]->hP;
         if (A.H != C.H) return A.H > C.H;
         return A.ntiles > C.ntiles;
     });
+    pl.order = std::move(order);
+    pl.smem = smem;
+    pl.sel_smem = sel_smem;
+    pl.arena = arena;
+    pl.counters = counters;
+    pl.ext = ext;
+    pl.h.assign(handles, handles + n);
+    for (int i = 0; i < n; ++i) pl.uid.push_back(handles[i]->uid);
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                               sbs_result* results, void* stream)
+{
+    if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i)
+        if (!handles[i]) return SBS_ERR_INVALID_ARG;
+    sbs_batch_plan& pl = b->plan;
+    bool same = (int)pl.h.size() == n;
+    for (int i = 0; same && i < n; ++i) same = pl.h[i] == handles[i] && pl.uid[i] == handles[i]->uid;
+    if (!same) {
+        const int st = plan_batch(pl, n, handles);
+        if (st) return st;
+    }
+    for (int i = 0; i < n; ++i) {
+        const sbs_handle* h = handles[i];
+        const sbs_problem* p = &probs[i];
+        if (!p->x0 || !p->xref || p->host_memory) return SBS_ERR_INVALID_ARG;
+        if (h->hP.world_feet && !p->feet) return SBS_ERR_INVALID_ARG;
+        if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
+    }
+    if (pl.arena > b->arena_bytes || pl.counters > b->counter_words) return SBS_ERR_BUDGET;
+    const int T = handles[0]->hP.T;
+    const int Pk = handles[0]->hP.P;
+    const std::vector<int>& order = pl.order;
+    const bool ext = pl.ext;
+    const size_t smem = pl.smem;
+    size_t sel_smem = pl.sel_smem;
     sbs_batch_slot& sl = b->slot[b->next];
     b->next = (b->next + 1) % b->nslots;
     if (sl.used && cudaEventSynchronize(sl.done) != cudaSuccess) return SBS_ERR_CUDA;
@@ -855,8 +907,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         sbs_handle* h = handles[i];
         const InstParams& P = h->hP;
         InstRec& R = recs[r];
-        std::memset(&R, 0, sizeof(R));
-        R.t = make_tick(h, probs[i].gait);
+        R.t = make_tick(h, probs[i].gait);  // zeroed there; every other field is written below
         R.t.x0 = probs[i].x0;
         R.t.xref = probs[i].xref;
         R.t.fext = probs[i].f_ext;
@@ -872,6 +923,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         R.tile_begin = tile_begin;
         R.select_begin = select_begin;
         R.refit_begin = refit_begin;
+        R.pad[0] = R.pad[1] = R.pad[2] = 0;
         tile_begin += P.ntiles;
         if (P.method != SBS_MPPI) {
             select_begin += 1;
@@ -900,9 +952,12 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
             st = update_graph_grids(sl, grids);
             if (st) return st;
         }
-        if (cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.pin, used,
-                                               cudaMemcpyHostToDevice) != cudaSuccess)
-            return SBS_ERR_CUDA;
+        if (used != sl.copy_bytes) {  // the record copy keeps its size while the batch does
+            if (cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.pin, used,
+                                                   cudaMemcpyHostToDevice) != cudaSuccess)
+                return SBS_ERR_CUDA;
+            sl.copy_bytes = used;
+        }
         if (cudaGraphLaunch(sl.exec, s) != cudaSuccess) return SBS_ERR_CUDA;
     } else {
         if (sl.exec && rekey) {  // the graph's launch shapes no longer match

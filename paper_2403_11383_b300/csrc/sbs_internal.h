@@ -235,6 +235,7 @@ struct sbs_handle {
     float* pin_in;         // pinned host staging of inputs
     void* in_done;         // cudaEvent_t: last copy out of pin_in has run
     bool in_pending;
+    uint64_t uid;          // creation number, unique over the process (a reused address gets a new one)
 };
 
 

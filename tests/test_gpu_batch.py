@@ -178,6 +178,40 @@ def test_controller_solve_packed_equals_solve(host):
     np.testing.assert_array_equal(_state(a)[1], _state(p)[1])
 
 
+def test_batch_replans_when_the_controllers_change():
+    # one batch object alternates between two lists of controllers (the launch
+    # plan is cached per list of handles); every tick equals the plain solves, and
+    # a list with a duplicate is still rejected after a plan was cached
+    import torch
+    mix = _mix()
+    lists = [[0, 1, 2, 3, 4, 5], [6, 7, 8, 9, 10, 1]]
+    batched = {i: S.Controller(c) for i, (c, _) in enumerate(mix)}
+    plain = {i: S.Controller(c) for i, (c, _) in enumerate(mix)}
+    tens = [_tensors(p) for _, p in mix]
+    b = S.Batch(len(mix), sum(c.workspace_bytes() + 256 for c in batched.values()))
+    ticks = {i: 0 for i in batched}
+    for rnd in range(4):
+        idx = lists[rnd % 2]
+        res = torch.empty(len(idx) * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        probs, want = [], []
+        for i in idx:
+            x0, xr, fe, ft = tens[i]
+            g = _gait(mix[i][1], ticks[i], mix[i][0])
+            sh = min(ticks[i], 1)
+            want.append(plain[i].solve(x0, xr, g, fe, sh, feet=ft).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, sh, feet=ft))
+            ticks[i] += 1
+        b.solve([batched[i] for i in idx], probs, res)
+        torch.cuda.synchronize()
+        for k in range(len(idx)):
+            assert bytes(res[k * S.RESULT_BYTES:(k + 1) * S.RESULT_BYTES].cpu().numpy()) == \
+                bytes(want[k].cpu().numpy())
+    with pytest.raises(S.SBSError) as e:
+        b.solve([batched[0], batched[1], batched[0]], probs[:3], res)
+    assert e.value.status == S.ERR_INVALID_ARG
+    b.close()
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
