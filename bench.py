@@ -102,7 +102,14 @@ class Clocks:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
+        # time nothing until nvidia-smi has written its first sample: its start-up
+        # contends for the driver, its steady 200 ms polling barely does
+        deadline = time.time() + 5.0
+        while self.proc is not None and self.proc.poll() is None and time.time() < deadline:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.02)
+        time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
