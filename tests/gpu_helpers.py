@@ -38,7 +38,7 @@ def f32(a):
     return np.asarray(a, dtype=np.float32)
 
 
-class GpuRun:
+class CudaRun:
     """One controller on the GPU with device-resident inputs."""
 
     def __init__(self, cfg, prob, tile=0):
@@ -192,7 +192,7 @@ def elite_band_ok(gpu_set, orc_J, Ke, kap, alt_J=None):
 def mppi_parity(cfg, prob, name, tile=0):
     """One MPPI solve against the oracle: frequencies, costs, mean, kept variance,
     result record."""
-    g, o = GpuRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     r = g.solve()
     Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
@@ -221,7 +221,7 @@ def elite_parity(cfg, prob, name, tile=0):
     """One elite solve (one iteration) against the oracle: frequencies, costs,
     the elite set up to the threshold band, and the refit as the elite mean and
     floored biased variance of the selected samples."""
-    g, o = GpuRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     r = g.solve()
     Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_helpers import (MEAN_ATOL, GpuRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
+from gpu_helpers import (MEAN_ATOL, CudaRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
                          elite_band_ok, f32, mppi_parity)
 from paper_2403_11383_b300 import sbs as S
 from paper_2403_11383_b300 import workloads as W
@@ -41,7 +41,7 @@ def test_elite_with_sampled_frequencies(cuda):
     cfg = W.config("adaptive_elite_k8192_h25")
     cfg.update(K=2048, H=25, iterations=1, world_feet=True, seed=17, compare_mppi=False)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     r = g.solve()
     Jg, qg, eg = g.read(S.BUF_COST), g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
@@ -66,7 +66,7 @@ def test_frequency_set_with_world_feet(cuda):
     cfg = W.config("naive_freqset_k10000_h12")
     cfg.update(K=3000, H=25, world_feet=True, seed=23)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     _check_iteration(cfg, g, o, g.solve())
     g.close()
 
@@ -75,7 +75,7 @@ def test_warm_tick_with_new_feet(cuda):
     cfg = W.config("worldfeet_mppi_k4096_h25")
     cfg.update(K=2048, seed=29)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     g.solve()
     mg, vg = g.state()
     gait = dict(prob["gait"])
@@ -96,7 +96,7 @@ def test_host_inputs_equal_device_inputs(cuda):
     cfg = W.config("worldfeet_mppi_k4096_h25")
     cfg.update(K=1024, seed=31)
     prob = W.problem(cfg)
-    a, b = GpuRun(cfg, prob), GpuRun(cfg, prob)
+    a, b = CudaRun(cfg, prob), CudaRun(cfg, prob)
     ra = a.solve()
     hb = b.ctl.solve_host(f32(prob["x0"]), f32(prob["xref"]), prob["gait"], f32(prob["f_ext"]), 0,
                           feet=f32(prob["feet"]))
@@ -113,7 +113,7 @@ def test_missing_feet_is_rejected(cuda):
     cfg = W.config("worldfeet_mppi_k4096_h25")
     cfg.update(K=256)
     prob = W.problem(cfg)
-    g = GpuRun(cfg, prob)
+    g = CudaRun(cfg, prob)
     with pytest.raises(S.SBSError) as e:
         g.ctl.solve(g.x0, g.xref, prob["gait"], g.fext, 0)
     assert e.value.status == S.ERR_INVALID_ARG

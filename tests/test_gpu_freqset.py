@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_helpers import MEAN_ATOL, GpuRun, OracleRun, check_costs, cost_tolerance, f32
+from gpu_helpers import MEAN_ATOL, CudaRun, OracleRun, check_costs, cost_tolerance, f32
 from paper_2403_11383_b300 import sbs as S
 from paper_2403_11383_b300 import workloads as W
 
@@ -79,7 +79,7 @@ def _check_iteration(cfg, g, o, r):
 def test_paper_gait_adaptation_setting_full_size(cuda):
     cfg = W.config("naive_freqset_k10000_h12")
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     r = g.solve()
     _, _, rep = _check_iteration(cfg, g, o, r)
     assert rep["strict"] > 0.5 * cfg["K"]
@@ -96,7 +96,7 @@ def test_ragged_sizes_and_set_lengths(cuda, K, H, fs, tile):
     cfg = W.config("naive_freqset_k10000_h12")
     cfg.update(K=K, H=H, freq_set_mhz=fs, seed=K + H)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
     _check_iteration(cfg, g, o, g.solve())
     g.close()
 
@@ -105,7 +105,7 @@ def test_spline_policy_with_a_frequency_set(cuda):
     cfg = W.config("naive_freqset_k10000_h12")
     cfg.update(K=2000, H=25, P=4, seed=21, sigma_init=5.0)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     _check_iteration(cfg, g, o, g.solve())
     g.close()
 
@@ -117,7 +117,7 @@ def test_warm_started_ticks_and_iterations(cuda):
     cfg = W.config("naive_freqset_k10000_h12")
     cfg.update(K=3000, seed=31)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     mg, vg, _ = _check_iteration(cfg, g, o, g.solve())
     for tick in (1, 2):
         gait = dict(prob["gait"])
@@ -128,7 +128,7 @@ def test_warm_started_ticks_and_iterations(cuda):
         mg, vg, _ = _check_iteration(cfg, g, o, g.solve(shift=1, gait=gait))
     g.close()
     c2 = dict(cfg, iterations=2)
-    g2, g1 = GpuRun(c2, prob), GpuRun(dict(cfg, iterations=1), prob)
+    g2, g1 = CudaRun(c2, prob), CudaRun(dict(cfg, iterations=1), prob)
     r2 = g2.solve()
     g1.solve()
     r1 = g1.solve()
@@ -142,10 +142,10 @@ def test_checkpoint_round_trip_with_blocks(cuda):
     cfg = W.config("naive_freqset_k10000_h12")
     cfg.update(K=1024, seed=41)
     prob = W.problem(cfg)
-    a = GpuRun(cfg, prob)
+    a = CudaRun(cfg, prob)
     a.solve()
     blob = a.ctl.get_state()
-    b = GpuRun(cfg, prob)
+    b = CudaRun(cfg, prob)
     b.ctl.set_state(blob)
     ra, rb = a.solve(shift=1), b.solve(shift=1)
     np.testing.assert_array_equal(a.state()[0], b.state()[0])

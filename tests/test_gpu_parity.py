@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_helpers import (MEAN_ATOL, GpuRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
+from gpu_helpers import (MEAN_ATOL, CudaRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
                          elite_band_ok, f32, mppi_parity, mppi_tolerance)
 from paper_2403_11383_b300 import sbs as S
 from paper_2403_11383_b300 import workloads as W
@@ -81,7 +81,7 @@ def test_mppi_k1_returns_its_sample(cuda):
     cfg = W.config("plain_mppi_k512_h12")
     cfg["K"] = 1
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     g.solve()
     mg, _ = g.state()
@@ -101,7 +101,7 @@ def test_adaptive_elite_iteration0_full_size(cuda):
     cfg = W.config("adaptive_elite_k8192_h25")
     cfg["iterations"] = 1
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     r = g.solve()
     Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
@@ -143,7 +143,7 @@ def test_elite_iterations_track_oracle(cuda):
     # elite sets agree (a swap at a near tie ends the comparison)
     cfg = _well_conditioned_elite()
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     compared = 0
     for it in range(5):
         J, q, th, margin, kap = o.rollout()
@@ -169,7 +169,7 @@ def test_naive_is_best_sample(cuda):
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(method="naive", K=1500, seed=5)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     r = g.solve()
     Jg = g.read(S.BUF_COST)
@@ -189,7 +189,7 @@ def test_naive_with_sampled_frequency(cuda):
     cfg = W.config("adaptive_elite_k8192_h25")
     cfg.update(method="naive", K=3000, H=12, iterations=1, compare_mppi=False, seed=83)
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     J, q, th, margin, kap = o.rollout()
     r = g.solve()
     Jg, qg, eg = g.read(S.BUF_COST), g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
@@ -210,11 +210,11 @@ def test_iterations_compose_on_gpu(cuda):
     cfg = W.config("adaptive_elite_k8192_h25")
     cfg.update(K=2048, seed=7)
     prob = W.problem(cfg)
-    g5 = GpuRun(cfg, prob)
+    g5 = CudaRun(cfg, prob)
     r5 = g5.solve()
     m5, v5 = g5.state()
     c1 = dict(cfg, iterations=1)
-    g1 = GpuRun(c1, prob)
+    g1 = CudaRun(c1, prob)
     for _ in range(5):
         r1 = g1.solve()
     m1, v1 = g1.state()
@@ -231,7 +231,7 @@ def test_warm_start_two_ticks(cuda):
     cfg = W.config("plain_mppi_k512_h12")
     cfg["seed"] = 3
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     g.solve()
     o.solve()
     gait2 = dict(prob["gait"])
@@ -258,7 +258,7 @@ def test_spline_full_size_sampled(cuda):
     # the spline workload at full size (K=262144, H=100, 4 knots): sampled costs
     cfg = W.config("spline_k262144_h100")
     prob = W.problem(cfg)
-    g, o = GpuRun(cfg, prob), OracleRun(cfg, prob)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
     r = g.solve()
     Jg, qg, eg = g.read(S.BUF_COST), g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
     rng = np.random.default_rng(1)
@@ -297,7 +297,7 @@ def test_large_k_selection_is_the_cost_index_order(cuda, K, frac):
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(K=K, method="elite", elite_count=W.elite_count(frac, K), seed=K % 97)
     prob = W.problem(cfg)
-    g = GpuRun(cfg, prob)
+    g = CudaRun(cfg, prob)
     for shift in (0, 1):
         r = g.solve(shift=shift)
         Jg, eg = g.read(S.BUF_COST), g.read(S.BUF_ELITE)
@@ -317,7 +317,7 @@ def test_spline_warm_shift(cuda):
     cfg = W.config("spline_k262144_h100")
     cfg.update(K=512, H=25, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=12)
     prob = W.problem(cfg)
-    g = GpuRun(cfg, prob)
+    g = CudaRun(cfg, prob)
     g.solve()
     mg1, vg1 = g.state()
     r = g.solve(shift=1)
@@ -334,7 +334,7 @@ def test_host_memory_path_equals_device_path(cuda):
     cfg = W.config("adaptive_elite_k8192_h25")
     cfg.update(K=1024, iterations=2, seed=4)
     prob = W.problem(cfg)
-    g = GpuRun(cfg, prob)
+    g = CudaRun(cfg, prob)
     rd = g.solve()
     md, vd = g.state()
     c2 = S.Controller(cfg)
@@ -352,7 +352,7 @@ def test_host_memory_path_equals_device_path(cuda):
 def test_checkpoint_resume_bit_exact(cuda):
     cfg = W.config("plain_mppi_k512_h12")
     prob = W.problem(cfg)
-    g = GpuRun(cfg, prob)
+    g = CudaRun(cfg, prob)
     g.solve()
     blob = g.ctl.get_state()
     r1 = g.solve(shift=1)
@@ -374,7 +374,7 @@ def test_checkpoint_resume_bit_exact(cuda):
 def test_all_costs_nonfinite_reports_divergence(cuda):
     cfg = W.config("plain_mppi_k512_h12")
     prob = W.problem(cfg)
-    g = GpuRun(cfg, prob)
+    g = CudaRun(cfg, prob)
     g.solve()
     m0, v0 = g.state()
     x0 = g.x0.clone()
@@ -385,7 +385,7 @@ def test_all_costs_nonfinite_reports_divergence(cuda):
     np.testing.assert_array_equal(m0, m1)
     np.testing.assert_array_equal(v0, v1)
     cfg2 = dict(cfg, method="elite", elite_count=10)
-    g2 = GpuRun(cfg2, prob)
+    g2 = CudaRun(cfg2, prob)
     g2.solve()
     m0, v0 = g2.state()
     r = g2.solve(shift=0, x0=x0)
