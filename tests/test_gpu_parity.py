@@ -7,7 +7,7 @@ import pytest
 
 import oracle as orc
 from gpu_helpers import (MEAN_ATOL, CudaRun, OracleRun, alt_frequency, check_costs, check_frequencies, dev,
-                         elite_band_ok, f32, mppi_parity, mppi_tolerance)
+                         elite_band_ok, elite_parity, f32, mppi_parity, mppi_tolerance)
 from paper_2403_11383_b300 import sbs as S
 from paper_2403_11383_b300 import workloads as W
 
@@ -75,6 +75,18 @@ def test_mppi_ragged_and_small(cuda, K, H, gait, tile):
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(K=K, H=H, gait=gait, tile=tile, seed=K)
     mppi_parity(cfg, W.problem(cfg), f"K{K}")
+
+
+@pytest.mark.parametrize("method", ["mppi", "elite"])
+def test_longest_horizon(cuda, method):
+    # H at its maximum (128 steps) with 256-sample tiles; dt = 1 ms keeps the
+    # 0.128 s open-loop horizon well conditioned
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(K=777, H=128, dt_us=1000, tile=256, seed=128, method=method,
+               elite_count=W.elite_count(0.05, 777) if method == "elite" else 1)
+    prob = W.problem(cfg)
+    rep = (mppi_parity if method == "mppi" else elite_parity)(cfg, prob, f"H128 {method}", tile=256)
+    assert rep["gated"] >= 0.9 * cfg["K"], rep
 
 
 def test_mppi_k1_returns_its_sample(cuda):
