@@ -2,8 +2,9 @@
 
 Workload: 256 independent controllers of uneven size solved together each
 control tick (K in {256, 1024, 4096, 16384}, H in {10, 25, 50}, trot/pace/crawl,
-MPPI or elite 5 %), one persistent graph-captured batched launch per tick,
-inputs resident in HBM, synthetic seeded data.  A step is one tick: rollout,
+MPPI or elite 5 %), one graph-replayed batched launch set per tick (grid or
+persistent mode, picked by the autotuner), inputs resident in HBM, synthetic
+seeded data.  A step is one tick: rollout,
 cost, update of all 256 controllers (warm-started from the previous tick).
 
 Metric: rollout sample-steps per second (sum of K*H over the controllers
@@ -395,6 +396,17 @@ def main():
     sel_ms, ref_ms = float(st[:, 1].mean()), float(st[:, 2].mean())
     flops_launch = ss_tick * FLOPS_ROLLOUT + mppi_ss * FLOPS_MPPI_PARTIAL
     achieved = flops_launch / (roll_ms * 1e-3) / 1e12
+    # algorithmic bytes of the elite update: the selection reads each cost once and
+    # writes the elite indices; the refit reads each elite's deviation row (48 B)
+    # and index per step, and reads and writes the distribution (mean, variance)
+    sel_bytes = ref_bytes = 0
+    for c, _ in mix:
+        if c["method"] == "mppi":
+            continue
+        ke = c["elite_count"] if c["method"] == "elite" else 1
+        d = 12 * c["H"] + (1 if c.get("adaptive") else 0)
+        sel_bytes += 4 * c["K"] + 4 * ke
+        ref_bytes += (48 + 4) * ke * c["H"] + 16 * d
     fp32_peak = S.fp32_peak() / 1e12
     nominal = 148 * 128 * 2 * 2032e6 / 1e12
 
@@ -488,6 +500,14 @@ def main():
                          "traffic": None if traffic_ss is None else traffic_ss * ss_tick,
                          "traffic_note": "ncu DRAM read+write per sample-step on the 48-controller mix, scaled "
                                          "to this launch's sample-steps (profiles/rollout_traffic.json)"},
+            "update_roofline": {
+                "bound": "hbm", "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
+                "select": {"bytes": sel_bytes, "achieved": sel_bytes / (sel_ms * 1e-3) / 1e9,
+                           "frac": sel_bytes / (sel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
+                "refit": {"bytes": ref_bytes, "achieved": ref_bytes / (ref_ms * 1e-3) / 1e9,
+                          "frac": ref_bytes / (ref_ms * 1e-3) / 1e9 / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
+                "note": "algorithmic bytes of the elite controllers' selection and refit; both stages are "
+                        "latency-bound chains of dependent loads, far from the HBM roof"},
             "e2e": {"value": e2e_value, "unit": "sample-steps/s",
                     "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel())},
             "gpu_launches": 3 * args.steps,
