@@ -281,10 +281,11 @@ int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* prob, const 
                           float* state_out, uint64_t iter, sbs_result* result, void* stream);
 
 /* ---------------------------------------------------------------- batching
- * Many controllers of uneven K and H solved in one persistent launch that pulls
- * (controller, tile) items from a device work queue; the tick is captured in a
- * CUDA graph and replayed.  Every controller's result equals its own sbs_solve
- * (same tile size), bit for bit. */
+ * Many controllers of uneven K and H solved in one set of launches per tick
+ * (one block per (controller, tile) item, or a persistent launch pulling items
+ * from a device work queue); the tick is captured in a CUDA graph and replayed.
+ * Every controller's result equals its own sbs_solve (same tile size), bit for
+ * bit. */
 /* A batch context for up to max_instances controllers per tick and up to
  * `inflight` (1..8) of its ticks in flight at once.  workspace_bytes is the
  * device-memory budget of its solves' scratch, split evenly between the
@@ -298,9 +299,13 @@ void sbs_batch_destroy(sbs_batch* b);
 /* Solve n controllers (one iteration each; controllers configured with
  * iterations > 1 are rejected) on stream.  probs[i] must use device memory
  * (host_memory = 0) and results is a device array of n sbs_result.  All
- * controllers must share the tile size and the policy (P).  Returns
- * SBS_ERR_BUDGET, with nothing enqueued, when their workspaces together exceed
- * the batch workspace. */
+ * controllers must share the tile size and the policy (P), and appear once.
+ * Returns SBS_ERR_BUDGET, with nothing enqueued, when their workspaces together
+ * exceed the batch workspace.  What follows from the list of controllers alone
+ * (their checks, tile order and launch sizes) is kept from the previous call
+ * when the same handles come in the same order (a handle destroyed and another
+ * created at its address does not match); the problems are checked every call.
+ * One thread at a time per batch. */
 int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                     sbs_result* results, void* stream);
 
