@@ -87,11 +87,12 @@ __device__ __forceinline__ uint4 philox_draw(const PhiloxPre& p, uint32_t d)
     return s;
 }
 
-// Box-Muller on two words: the top 24 bits give exact uniforms u1 in (0, 1]
-// and u2 in [0, 1).  The radius uses the accurate logarithm (its argument is
-// often within a few ulp of 1) and x * rsqrt(x) for the square root; the angle
-// uses the hardware sine/cosine, whose absolute error (about 4e-7 on
-// [0, 2 pi)) moves a normal by at most 3e-6.
+// Box-Muller on two words (the step-frequency draw): the top 24 bits give exact
+// uniforms u1 in (0, 1] and u2 in [0, 1).  The radius uses the accurate
+// logarithm, since the frequency's rounding to integer mHz must match the exact
+// transform (its argument is often within a few ulp of 1), and x * rsqrt(x) for
+// the square root; the angle uses the hardware sine/cosine, whose absolute error
+// (about 4e-7 on [0, 2 pi)) moves a normal by at most 3e-6.
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {
     const float two_m24 = 5.9604644775390625e-8f;
@@ -104,18 +105,23 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
     return make_float2(r * c, r * s);
 }
 
-// Box-Muller on two 21-bit integers: u1 = (a + 1) 2^-21 in (0, 1] and
-// u2 = b 2^-21 in [0, 1) (exact), with the radius and angle evaluated as above.
-// The integers (at most 2^21) are turned into floats without a conversion
-// instruction: 0x4B000000 | n is the float 2^23 + n, and fma(2^23 + n, c, -2^23 c)
-// is n c rounded once, the same bits as float(n) * c.
+// Box-Muller on two 21-bit integers (the force normals): u1 = (a + 1) 2^-21 in
+// (0, 1] and u2 = b 2^-21 in [0, 1) (exact).  The radius uses the hardware
+// logarithm (absolute error at most 2^-21.41 on [0.5, 2], 3 ulp below): with
+// r = sqrt(-2 ln u1) the radius moves by at most min(2 e / r, sqrt(2 e)) for a
+// logarithm error e, about 1e-6 at typical radii and up to 5e-4 at the smallest
+// (u1 within a few 2^-21 of 1).  These are the sampler's draws, not model
+// arithmetic: the accurate routine cost 12 % of the rollout.  The angle is as
+// above.  The integers (at most 2^21) are turned into floats without a
+// conversion instruction: 0x4B000000 | n is the float 2^23 + n, and
+// fma(2^23 + n, c, -2^23 c) is n c rounded once, the same bits as float(n) * c.
 __device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
 {
     const float two_m21 = 4.76837158203125e-7f;
     const float c_ang = 6.28318530717958648f * two_m21;
     const float u1 = fmaf(__int_as_float(0x4b000000 | (int)(a + 1u)), two_m21, -4.0f);
     const float ang = fmaf(__int_as_float(0x4b000000 | (int)b), c_ang, -8388608.0f * c_ang);
-    const float r2 = -2.0f * logf(u1);
+    const float r2 = -2.0f * __logf(u1);
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     float s, c;
     __sincosf(ang, &s, &c);
