@@ -109,8 +109,8 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 // (0, 1] and u2 = b 2^-21 in [0, 1) (exact).  The radius uses the hardware
 // logarithm (absolute error at most 2^-21.41 on [0.5, 2], 3 ulp below): with
 // r = sqrt(-2 ln u1) the radius moves by at most min(2 e / r, sqrt(2 e)) for a
-// logarithm error e, about 1e-6 at typical radii and up to 5e-4 at the smallest
-// (u1 within a few 2^-21 of 1).  These are the sampler's draws, not model
+// logarithm error e, about 1e-6 at typical radii and at most sqrt(2 e) = 8.5e-4
+// at the smallest (u1 within a few 2^-21 of 1).  These are the sampler's draws, not model
 // arithmetic: the accurate routine cost 12 % of the rollout.  The angle is as
 // above.  The integers (at most 2^21) are turned into floats without a
 // conversion instruction: 0x4B000000 | n is the float 2^23 + n, and
