@@ -51,22 +51,38 @@ class Plant:
             return self._deriv_raw(x, u, stance)
 
     def _deriv_raw(self, x, u, stance):
-        rpy, v, w = x[:, 3:6], x[:, 6:9], x[:, 9:12]
-        sr, cr = np.sin(rpy[:, 0]), np.cos(rpy[:, 0])
-        sp, cp = np.sin(rpy[:, 1]), np.cos(rpy[:, 1])
-        sy, cy = np.sin(rpy[:, 2]), np.cos(rpy[:, 2])
-        R = np.stack([np.stack([cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr], -1),
-                      np.stack([sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr], -1),
-                      np.stack([-sp, cp * sr, cp * cr], -1)], -2)  # [n, 3, 3] body to world
+        # Eq. (1) with body-fixed lever arms, component by component (vectorised over robots)
+        sr, cr = np.sin(x[:, 3]), np.cos(x[:, 3])
+        sp, cp = np.sin(x[:, 4]), np.cos(x[:, 4])
+        sy, cy = np.sin(x[:, 5]), np.cos(x[:, 5])
+        # body-to-world R = Rz(yaw) Ry(pitch) Rx(roll)
+        r00, r01, r02 = cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr
+        r10, r11, r12 = sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr
+        r20, r21, r22 = -sp, cp * sr, cp * cr
         G = u.reshape(-1, 4, 3) * stance[:, :, None]
-        F = G.sum(axis=1)
-        Gb = np.einsum("nji,nkj->nki", R, G)  # R^T G per leg
-        tau = np.cross(self.foot[None, :, :], Gb).sum(axis=1)
-        Iw = self.I[None, :] * w
-        wd = (tau - np.cross(w, Iw)) / self.I[None, :]
-        rates = np.stack([w[:, 0] + sr * sp / cp * w[:, 1] + cr * sp / cp * w[:, 2],
-                          cr * w[:, 1] - sr * w[:, 2], (sr * w[:, 1] + cr * w[:, 2]) / cp], -1)
-        return np.concatenate([v, rates, (F + self.push_sel) / self.m + self.g[None, :], wd], axis=1)
+        gx, gy, gz = G[:, :, 0], G[:, :, 1], G[:, :, 2]  # [n, 4] world forces per leg
+        bx = r00[:, None] * gx + r10[:, None] * gy + r20[:, None] * gz  # R^T G per leg
+        by = r01[:, None] * gx + r11[:, None] * gy + r21[:, None] * gz
+        bz = r02[:, None] * gx + r12[:, None] * gy + r22[:, None] * gz
+        fx, fy, fz = self.foot[:, 0], self.foot[:, 1], self.foot[:, 2]
+        t0 = (fy * bz - fz * by).sum(axis=1)
+        t1 = (fz * bx - fx * bz).sum(axis=1)
+        t2 = (fx * by - fy * bx).sum(axis=1)
+        w0, w1, w2 = x[:, 9], x[:, 10], x[:, 11]
+        I0, I1, I2 = self.I
+        out = np.empty_like(x)
+        out[:, 0:3] = x[:, 6:9]
+        tp = sp / cp
+        out[:, 3] = w0 + sr * tp * w1 + cr * tp * w2
+        out[:, 4] = cr * w1 - sr * w2
+        out[:, 5] = (sr * w1 + cr * w2) / cp
+        out[:, 6] = (gx.sum(axis=1) + self.push_sel[:, 0]) / self.m + self.g[0]
+        out[:, 7] = (gy.sum(axis=1) + self.push_sel[:, 1]) / self.m + self.g[1]
+        out[:, 8] = (gz.sum(axis=1) + self.push_sel[:, 2]) / self.m + self.g[2]
+        out[:, 9] = (t0 - (w1 * I2 * w2 - w2 * I1 * w1)) / I0
+        out[:, 10] = (t1 - (w2 * I0 * w0 - w0 * I2 * w2)) / I1
+        out[:, 11] = (t2 - (w0 * I1 * w1 - w1 * I0 * w0)) / I2
+        return out
 
     def advance(self, idx, dt, u, phase, q, offset, duty, now):
         """Advance robots idx by dt seconds; phase (uint32 1e-9 cycle) advances too."""
@@ -129,6 +145,7 @@ class Robots:
         self.probs["xref"] = self.xref.ctypes.data + np.arange(n, dtype=np.uint64) * (50 * 12 * 4)
         self.probs["offset"] = self.offset.astype(np.uint32)
         self.probs["duty"] = self.duty.astype(np.uint32)
+        self._steps = np.arange(50, dtype=np.float64)
 
     def prepare(self, idx, now, last_update, anchor, first):
         """Advance robots idx to `now` and fill their request records."""
@@ -140,14 +157,14 @@ class Robots:
         self.x0[idx] = x.astype(np.float32)
         # constant-velocity reference from the current state (planar velocity, height 0.30 m, level)
         H = 50
-        j = np.arange(H)[None, :]
-        ref = np.zeros((len(idx), H, 12), dtype=np.float64)
-        ref[:, :, 0] = x[:, 0:1] + self.v_ref[idx, 0:1] * j * self.dt[idx, None]
-        ref[:, :, 1] = x[:, 1:2] + self.v_ref[idx, 1:2] * j * self.dt[idx, None]
+        t = self._steps[None, :] * self.dt[idx, None]  # [n, H] step times
+        ref = np.zeros((len(idx), H, 12), dtype=np.float32)
+        ref[:, :, 0] = x[:, 0:1] + self.v_ref[idx, 0:1] * t
+        ref[:, :, 1] = x[:, 1:2] + self.v_ref[idx, 1:2] * t
         ref[:, :, 2] = 0.30
         ref[:, :, 6] = self.v_ref[idx, 0:1]
         ref[:, :, 7] = self.v_ref[idx, 1:2]
-        self.xref[idx] = ref.reshape(len(idx), -1).astype(np.float32)
+        self.xref[idx] = ref.reshape(len(idx), -1)
         shift = np.floor((now - anchor[idx]) / self.dt[idx]).astype(np.int64)
         shift = np.minimum(shift, self.H[idx])
         anchor[idx] += shift * self.dt[idx]
