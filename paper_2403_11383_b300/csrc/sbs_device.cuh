@@ -107,10 +107,10 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 
 // Box-Muller on two 21-bit integers (the force normals): u1 = (a + 1) 2^-21 in
 // (0, 1] and u2 = b 2^-21 in [0, 1) (exact).  The radius uses the hardware
-// logarithm (absolute error at most 2^-21.41 on [0.5, 2], 3 ulp below): with
-// r = sqrt(-2 ln u1) the radius moves by at most min(2 e / r, sqrt(2 e)) for a
-// logarithm error e, about 1e-6 at typical radii and at most sqrt(2 e) = 8.5e-4
-// at the smallest (u1 within a few 2^-21 of 1).  These are the sampler's draws, not model
+// base-2 logarithm (absolute error at most 2^-22 on [0.5, 2], 2 ulp below), so
+// ln u1 is off by at most e = 2^-22 ln 2 = 1.65e-7 there: with r = sqrt(-2 ln u1)
+// the radius moves by at most min(2 e / r, sqrt(2 e)), about 1e-6 at typical radii
+// and at most sqrt(2 e) = 5.7e-4 at the smallest (u1 within a few 2^-21 of 1).  These are the sampler's draws, not model
 // arithmetic: the accurate routine cost 12 % of the rollout.  The angle is as
 // above.  The integers (at most 2^21) are turned into floats without a
 // conversion instruction: 0x4B000000 | n is the float 2^23 + n, and
@@ -121,7 +121,7 @@ __device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
     const float c_ang = 6.28318530717958648f * two_m21;
     const float u1 = fmaf(__int_as_float(0x4b000000 | (int)(a + 1u)), two_m21, -4.0f);
     const float ang = fmaf(__int_as_float(0x4b000000 | (int)b), c_ang, -8388608.0f * c_ang);
-    const float r2 = -2.0f * __logf(u1);
+    const float r2 = -1.38629436111989061f * __log2f(u1);  // -2 ln 2 log2(u1)
     const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
     float s, c;
     __sincosf(ang, &s, &c);

@@ -6,8 +6,8 @@ Tolerances (derived from the arithmetic):
     frequency whose FP64 value lies within 2e-3 mHz of a rounding boundary may
     round either way in single precision and is checked against both candidates.
   * normals: 3e-6 + 2e-6 |z| (hardware sine/cosine of the angle); force normals
-    also the radius bound min(2 e / r, sqrt(2 e)) of the hardware logarithm
-    (error e at most 2^-21.41 on [0.5, 1], 3 ulp below).
+    also the radius bound min(2 e / r, sqrt(2 e)) of the hardware base-2
+    logarithm (ln error e at most 2^-22 ln 2 on [0.5, 1], 3 ulp below).
   * costs: relative error <= 1e-4 for samples whose conditioning estimate
     kappa (the oracle's relative cost change under per-step rounding-sized
     perturbations) is <= 1e-6, and <= max(1e-4, 100 kappa) up to kappa = 1e-5;

@@ -54,15 +54,16 @@ def test_philox_gpu_known_answers_and_oracle(cuda):
 
 
 def _radius_bound(seed, ctrl, k, n, it):
-    """Bound on the force normal's radius error from the hardware logarithm: the
-    log of u1 = (a + 1) 2^-21 is off by at most e = 2^-21.41 on [0.5, 1] and 3 ulp
-    below, so r = sqrt(-2 ln u1) moves by at most min(2 e / r, sqrt(2 e))."""
+    """Bound on the force normal's radius error from the hardware base-2
+    logarithm: log2 of u1 = (a + 1) 2^-21 is off by at most 2^-22 on [0.5, 1] and
+    2 ulp below (3 with the scaling), so ln u1 is off by e = 2^-22 ln 2 there and
+    r = sqrt(-2 ln u1) moves by at most min(2 e / r, sqrt(2 e))."""
     w = orc.philox4x32_10(np.array([k, 1 + n // 6, it & 0xFFFFFFFF, it >> 32], dtype=np.uint32),
                           np.array([seed, ctrl], dtype=np.uint32))
     a = int(orc.uniforms21(w)[2 * ((n % 6) // 2)])
     u1 = (a + 1) / 2.0 ** 21
     ln = math.log(u1)
-    e = 2.0 ** -21.41 if u1 >= 0.5 else 3.0 * 2.0 ** -23 * abs(ln)
+    e = 2.0 ** -22 * math.log(2.0) if u1 >= 0.5 else 3.0 * 2.0 ** -23 * abs(ln)
     r = math.sqrt(-2.0 * ln)
     return math.sqrt(2.0 * e) if r == 0.0 else min(2.0 * e / r, math.sqrt(2.0 * e))
 
