@@ -484,9 +484,12 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             }
         } else {
             const float4* b4 = reinterpret_cast<const float4*>(v.Bs + j * 4 * NQ);
+            const float4* m4 = reinterpret_cast<const float4*>(v.Mb + blk * 12 * P.H + 12 * j);  // 16-byte aligned
+            const float4 ma = m4[0], mb = m4[1], mc = m4[2];
+            const float mrow[12] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w, mc.x, mc.y, mc.z, mc.w};
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                float s = v.Mb[blk * 12 * P.H + 12 * j + c];
+                float s = mrow[c];
 #pragma unroll
                 for (int qq = 0; qq < NQ; ++qq) {
                     const float4 b = b4[qq];
