@@ -18,6 +18,17 @@ controllers per launch: ``sbs.Batch(n, workspace_bytes).solve(controllers,
 [c.problem(...) for c in controllers], results)``.  A request loop with
 continuous batching: ``sbs.Server(...).submit(handles, records)`` /
 ``poll(tickets)``.  Ground-fixed feet pass ``feet=`` ([4, 2] ground positions).
+
+A control loop that solves the same controllers tick after tick packs its
+arguments once and edits them in place, so a tick marshals nothing::
+
+    p = ctl.problem(x0, xref, gait, f_ext, shift=1)     # buffers updated in place
+    p.gait.phase0 = phase                                # per tick
+    ctl.solve_packed(p, res)
+
+    packed = sbs.Packed(controllers, problems)
+    packed.problems[i].gait.phase0 = phase_i             # per tick
+    batch.solve_packed(packed, results)
 """
 from __future__ import annotations
 
