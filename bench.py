@@ -316,17 +316,22 @@ def main():
         return
     import torch
     from paper_2403_11383_b300 import sbs as S
+    from paper_2403_11383_b300 import tuning
     from paper_2403_11383_b300 import workloads as W
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     mix = W.batch_config(args.instances)
-    ctls = [S.Controller(c) for c, _ in mix]
     x0 = [torch.tensor(np.float32(p["x0"]), device=dev) for _, p in mix]
     xref = [torch.tensor(np.float32(p["xref"]), device=dev) for _, p in mix]
     fext = [torch.tensor(np.float32(p["f_ext"]), device=dev) for _, p in mix]
     gaits = [dict(p["gait"]) for _, p in mix]
+    # samples per block: timed on this mix at each candidate before the controllers are built
+    tile, tile_ms = tuning.tile_for_batch([c for c, _ in mix], list(zip(x0, xref, gaits, fext)))
+    for c, _ in mix:
+        c["tile"] = tile
+    ctls = [S.Controller(c) for c, _ in mix]
     n = len(ctls)
     ss_tick = sum(c["K"] * c["H"] for c, _ in mix)
     mppi_ss = sum(c["K"] * c["H"] for c, _ in mix if c["method"] == "mppi")
@@ -483,7 +488,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances": n, "sample_steps_per_tick": ss_tick,
-                       "tile": W.BATCH_TILE, "graph": True, "launch_mode": mode,
+                       "tile": tile, "tile_autotune_ms_per_tick": tile_ms, "graph": True, "launch_mode": mode,
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
                        "l2": "per-tick working set above L2 (sampled deviations "
                        f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},

@@ -140,3 +140,11 @@ def test_packed_batch_arguments():
         S.Packed(ctls, probs[:4])
     with pytest.raises(ValueError):
         S.Packed([], [])
+
+
+def test_tile_tuner_checks_its_arguments():
+    from paper_2403_11383_b300 import tuning
+    with pytest.raises(ValueError):
+        tuning.tile_for_batch([], [])
+    with pytest.raises(ValueError):
+        tuning.tile_for_batch([W.config("plain_mppi_k512_h12")] * 2, [None])

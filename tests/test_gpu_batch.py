@@ -212,6 +212,16 @@ def test_batch_replans_when_the_controllers_change():
     b.close()
 
 
+def test_tile_tuner_times_every_candidate():
+    from paper_2403_11383_b300 import tuning
+    mix = _mix()
+    tens = [_tensors(p) for _, p in mix]
+    best, ms = tuning.tile_for_batch([c for c, _ in mix], [(t[0], t[1], p["gait"], t[2], t[3]) for t, (_, p) in
+                                                           zip(tens, mix)], tiles=(64, 128, 256), ticks=2)
+    assert set(ms) == {64, 128, 256} and all(v > 0 for v in ms.values())
+    assert best == min(ms, key=ms.get)
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
