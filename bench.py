@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="sbs", choices=["sbs", "reference"])
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="samples per block of the batched controllers; 0: timed at 128 and 256, fastest kept")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
     ap.add_argument("--serving-seconds", type=float, default=3.0)
@@ -328,7 +330,10 @@ def main():
     fext = [torch.tensor(np.float32(p["f_ext"]), device=dev) for _, p in mix]
     gaits = [dict(p["gait"]) for _, p in mix]
     # samples per block: timed on this mix at each candidate before the controllers are built
-    tile, tile_ms = tuning.tile_for_batch([c for c, _ in mix], list(zip(x0, xref, gaits, fext)))
+    if args.tile:
+        tile, tile_ms = args.tile, None
+    else:
+        tile, tile_ms = tuning.tile_for_batch([c for c, _ in mix], list(zip(x0, xref, gaits, fext)))
     for c, _ in mix:
         c["tile"] = tile
     ctls = [S.Controller(c) for c, _ in mix]
