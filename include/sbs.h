@@ -387,7 +387,12 @@ int sbs_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, i
 /* The standard normals the controller with key (seed, ctrl) draws in iteration
  * iter (Alg. 1 Sampling): for samples k0 .. k0 + nk - 1, out[i (nn + 1)] is the
  * frequency normal (draw 0) and out[i (nn + 1) + 1 + n] force normal n < nn
- * (draw 1 + n/6).  Device output of nk (nn + 1) floats; enqueued on stream. */
+ * (draw 1 + n/6).  Device output of nk (nn + 1) floats; enqueued on stream.
+ * Precision: the angle uses the hardware sine/cosine (a normal moves by at most
+ * 3e-6); the frequency normal's radius uses the accurate logarithm, the force
+ * normals' radius the hardware base-2 logarithm (error at most 2^-22 on
+ * [0.5, 2]), which moves the radius r by at most min(2e/r, sqrt(2e)) with
+ * e = 2^-22 ln 2: about 1e-6 at typical radii, at most 5.7e-4 at the smallest. */
 int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
 
 /* Measure the FP32 FMA throughput of the current device with a register-resident
