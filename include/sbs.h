@@ -392,8 +392,14 @@ int sbs_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, i
  * 3e-6); the frequency normal's radius uses the accurate logarithm, the force
  * normals' radius the hardware base-2 logarithm (error at most 2^-22 on
  * [0.5, 2]), which moves the radius r by at most min(2e/r, sqrt(2e)) with
- * e = 2^-22 ln 2: about 1e-6 at typical radii, at most 5.7e-4 at the smallest. */
+ * e = 2^-22 ln 2: about 1e-6 at typical radii, at most 5.7e-4 at the smallest;
+ * their square root is sbs_sqrt_hw's (relative error below 1.1e-7, under one ulp). */
 int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
+
+/* The square root the rollout takes of the normals' radius and of the friction
+ * cone's |Gamma_xy|: y[i] = the hardware approximation of sqrt(x[i]) for i < n
+ * (device arrays, enqueued on stream); for tests of its error bound. */
+int sbs_sqrt_hw(const float* x, float* y, int n, void* stream);
 
 /* Measure the FP32 FMA throughput of the current device with a register-resident
  * FMA chain kernel; returns FLOP/s (2 per FMA) in *flops, or an error. */

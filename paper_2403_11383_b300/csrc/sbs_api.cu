@@ -563,6 +563,12 @@ int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int
     return launch_normals(seed, ctrl, iter, k0, nk, nn, out, stream);
 }
 
+int sbs_sqrt_hw(const float* x, float* y, int n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return SBS_ERR_INVALID_ARG;
+    return launch_sqrt_hw(x, y, n, stream);
+}
+
 int sbs_fp32_peak(double* flops, void* stream)
 {
     if (!flops) return SBS_ERR_INVALID_ARG;

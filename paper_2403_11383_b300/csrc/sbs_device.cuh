@@ -87,6 +87,16 @@ __device__ __forceinline__ uint4 philox_draw(const PhiloxPre& p, uint32_t d)
     return s;
 }
 
+// Square root by the hardware approximation: relative error below 1.1e-7 (under
+// one ulp; measured against double precision over every single-precision
+// mantissa of both exponent parities), sqrt(0) = 0.
+__device__ __forceinline__ float sqrt_hw(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Box-Muller on two words (the step-frequency draw): the top 24 bits give exact
 // uniforms u1 in (0, 1] and u2 in [0, 1).  The radius uses the accurate
 // logarithm, since the frequency's rounding to integer mHz must match the exact
@@ -110,11 +120,13 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 // base-2 logarithm (absolute error at most 2^-22 on [0.5, 2], 2 ulp below), so
 // ln u1 is off by at most e = 2^-22 ln 2 = 1.65e-7 there: with r = sqrt(-2 ln u1)
 // the radius moves by at most min(2 e / r, sqrt(2 e)), about 1e-6 at typical radii
-// and at most sqrt(2 e) = 5.7e-4 at the smallest (u1 within a few 2^-21 of 1).  These are the sampler's draws, not model
-// arithmetic: the accurate routine cost 12 % of the rollout.  The angle is as
-// above.  The integers (at most 2^21) are turned into floats without a
-// conversion instruction: 0x4B000000 | n is the float 2^23 + n, and
-// fma(2^23 + n, c, -2^23 c) is n c rounded once, the same bits as float(n) * c.
+// and at most sqrt(2 e) = 5.7e-4 at the smallest (u1 within a few 2^-21 of 1).
+// These are the sampler's draws, not model arithmetic: the accurate routine cost
+// 12 % of the rollout.  The square root is sqrt_hw (a logarithm slightly above 0
+// gives r = 0); the angle is as above.  The integers (at most 2^21) are turned
+// into floats without a conversion instruction: 0x4B000000 | n is the float
+// 2^23 + n, and fma(2^23 + n, c, -2^23 c) is n c rounded once, the same bits as
+// float(n) * c.
 __device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
 {
     const float two_m21 = 4.76837158203125e-7f;
@@ -122,7 +134,7 @@ __device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
     const float u1 = fmaf(__int_as_float(0x4b000000 | (int)(a + 1u)), two_m21, -4.0f);
     const float ang = fmaf(__int_as_float(0x4b000000 | (int)b), c_ang, -8388608.0f * c_ang);
     const float r2 = -1.38629436111989061f * __log2f(u1);  // -2 ln 2 log2(u1)
-    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float r = sqrt_hw(fmaxf(r2, 0.0f));
     float s, c;
     __sincosf(ang, &s, &c);
     return make_float2(r * c, r * s);
@@ -246,9 +258,9 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
         r = fmaf(P.R[2] * gz, gz, r);
         if (!penalty) continue;  // forces already projected onto the cone
         // friction cone on stance legs; a swing leg's zero force adds nothing
-        // (|G_xy| as x * rsqrt(x), exact zero for a zero force)
+        // (|G_xy| by sqrt_hw, exact zero for a zero force)
         const float t2 = fmaf(gx, gx, gy * gy);
-        const float slip = (t2 > 0.0f ? t2 * rsqrtf(t2) : 0.0f) - P.mu * gz;
+        const float slip = sqrt_hw(t2) - P.mu * gz;
         const float sp = fmaxf(slip, 0.0f), gn = fminf(gz, 0.0f);
         const float pen = fmaf(gn, gn, sp * sp);
         r = fmaf(P.w_fc, pen, r);
@@ -263,7 +275,7 @@ __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[1
 __device__ __forceinline__ void cone_project(float mu, float inv_1pmu2, float& gx, float& gy, float& gz)
 {
     const float s2 = fmaf(gx, gx, gy * gy);
-    const float s = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;
+    const float s = sqrt_hw(s2);
     if (s <= mu * gz) return;
     if (mu * s <= -gz) {
         gx = gy = gz = 0.0f;

@@ -23,6 +23,7 @@
 //              per item, or persistent blocks pulling items from device queues.
 //  k_init      the initial distribution.
 //  k_philox, k_normals  the random numbers the controller draws (tests).
+//  k_sqrt_hw  the hardware square root the rollout uses (tests).
 //  k_fma_peak  FP32 FMA-chain microbenchmark for the roofline denominator.
 #include <cuda_runtime.h>
 
@@ -1573,6 +1574,12 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __res
     out[4 * i + 3] = w.w;
 }
 
+__global__ void k_sqrt_hw(const float* __restrict__ x, float* __restrict__ y, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = sqrt_hw(x[i]);
+}
+
 __global__ void k_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1982,6 +1989,13 @@ int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, 
 {
     if (nk <= 0) return SBS_OK;
     k_normals<<<(nk + 127) / 128, 128, 0, (cudaStream_t)stream>>>(seed, ctrl, iter, k0, nk, nn, out);
+    return status_of(cudaGetLastError());
+}
+
+int launch_sqrt_hw(const float* x, float* y, int n, void* stream)
+{
+    if (n <= 0) return SBS_OK;
+    k_sqrt_hw<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, y, n);
     return status_of(cudaGetLastError());
 }
 

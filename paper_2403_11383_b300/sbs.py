@@ -156,6 +156,7 @@ ABI = {
     "sbs_batch_stage_ms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sbs_sqrt_hw": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_normals": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_void_p,
                               C.c_void_p]),
 }
@@ -498,6 +499,15 @@ def philox(ctr, key, stream=None):
     out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
     check(lib().sbs_philox4x32_10(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()),
                                   C.c_void_p(out.data_ptr()), n, _stream_ptr(stream)), "sbs_philox4x32_10")
+    return out
+
+
+def sqrt_hw(x, stream=None):
+    """The rollout's hardware square root of a float32 CUDA tensor."""
+    import torch
+    out = torch.empty_like(x)
+    check(lib().sbs_sqrt_hw(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel(), _stream_ptr(stream)),
+          "sbs_sqrt_hw")
     return out
 
 

@@ -68,6 +68,25 @@ def _radius_bound(seed, ctrl, k, n, it):
     return math.sqrt(2.0 * e) if r == 0.0 else min(2.0 * e / r, math.sqrt(2.0 * e))
 
 
+def test_hardware_square_root_bound(cuda):
+    # every single-precision mantissa of both exponent parities ([1, 4)), then
+    # scaled arguments: relative error below 1.1e-7 (under one ulp) against double
+    # precision, and an exact zero (the bound the normals' radius and the cone
+    # norm rely on)
+    torch = cuda
+    bits = np.arange(0x3F800000, 0x3F800000 + (1 << 24), dtype=np.uint32)
+    x = bits.view(np.float32)
+    y = S.sqrt_hw(torch.from_numpy(x).cuda()).cpu().numpy()
+    rel = np.abs(y.astype(np.float64) - np.sqrt(x.astype(np.float64))) / np.sqrt(x.astype(np.float64))
+    assert rel.max() <= 1.1e-7, rel.max()
+    ulp = np.abs(y.astype(np.float64) - np.sqrt(x.astype(np.float64))) / np.spacing(y)
+    assert ulp.max() < 1.0, ulp.max()
+    xs = np.float32([0.0, 1e-30, 3.7e-9, 4.2, 1.5e12, 3e38])
+    ys = S.sqrt_hw(torch.from_numpy(xs).cuda()).cpu().numpy()
+    assert ys[0] == 0.0
+    np.testing.assert_allclose(ys, np.sqrt(xs.astype(np.float64)), rtol=1.1e-7)
+
+
 def test_normals_gpu_vs_oracle(cuda):
     seed, ctrl, it = 11, 3, (1 << 32) + 7
     nk, nn = 1024, 50
