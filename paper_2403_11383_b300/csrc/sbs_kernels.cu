@@ -1105,11 +1105,22 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
     uint32_t thr;
     int need_eq;
     if (K <= kSelectSmemMaxK) {
-        for (int i = tid; i < K; i += T) skeys[i] = cost_key(__ldcg(J + i));
+        // staging fused with the first pass's histogram (top 8 key bits)
+        for (int i = tid; i < 256; i += T) sh.hist[i] = 0;
         __syncthreads();
-        uint32_t prefix = 0, mask = 0;
+        for (int i = tid; i < K; i += T) {
+            const uint32_t key = cost_key(__ldcg(J + i));
+            skeys[i] = key;
+            atomicAdd(&sh.hist[key >> 24], 1);
+        }
+        __syncthreads();
         int rank = P.Ke;
-        for (int pass = 0; pass < 4; ++pass) radix_pass<true>(sh, skeys, nullptr, K, 24 - 8 * pass, prefix, mask, rank);
+        find_digit(sh, sh.hist, rank);
+        __syncthreads();
+        rank -= sh.below;
+        uint32_t prefix = (uint32_t)sh.digit << 24, mask = 255u << 24;
+        __syncthreads();
+        for (int pass = 1; pass < 4; ++pass) radix_pass<true>(sh, skeys, nullptr, K, 24 - 8 * pass, prefix, mask, rank);
         thr = prefix;
         need_eq = rank;
     } else if (t.ws.hist) {
