@@ -222,6 +222,82 @@ def test_tile_tuner_times_every_candidate():
     assert best == min(ms, key=ms.get)
 
 
+def test_two_batches_on_two_streams_at_once():
+    # two batches of independent controllers ticking concurrently on two streams
+    # give the bits of the same ticks run one after the other: no state is shared
+    # between batches
+    import torch
+    mix = _mix()
+    half = len(mix) // 2
+    groups = [list(range(half)), list(range(half, len(mix)))]
+    tens = [_tensors(p) for _, p in mix]
+
+    def run(concurrent):
+        ctls = [S.Controller(c) for c, _ in mix]
+        batches, packs, outs = [], [], []
+        for g in groups:
+            cs = [ctls[i] for i in g]
+            batches.append(S.Batch(len(g), 2 * sum(c.workspace_bytes() + 256 for c in cs), inflight=2))
+            packs.append([S.Packed(cs, [ctls[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], sh,
+                                                        feet=tens[i][3]) for i in g]) for sh in (0, 1)])
+            outs.append(torch.empty(len(g) * S.RESULT_BYTES, dtype=torch.uint8, device="cuda"))
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for tick in range(3):
+            for k in range(2):
+                if concurrent:
+                    with torch.cuda.stream(streams[k]):
+                        batches[k].solve_packed(packs[k][min(tick, 1)], outs[k], stream=streams[k])
+                else:
+                    batches[k].solve_packed(packs[k][min(tick, 1)], outs[k])
+                    torch.cuda.synchronize()
+            torch.cuda.synchronize()
+        res = [bytes(o.cpu().numpy()) for o in outs]
+        states = [_state(c) for c in ctls]
+        for b in batches:
+            b.close()
+        return res, states
+
+    ra, sa = run(False)
+    rb, sb = run(True)
+    assert ra == rb
+    for (ma, va), (mb, vb) in zip(sa, sb):
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+
+
+def test_checkpoint_resume_in_the_batch():
+    # controllers saved after a batched tick and restored into fresh handles
+    # continue in a batch with the same bits as the uninterrupted ones
+    import torch
+    mix = _mix()
+    n = len(mix)
+    tens = [_tensors(p) for _, p in mix]
+    a = [S.Controller(c) for c, _ in mix]
+    ba = S.Batch(n, sum(c.workspace_bytes() + 256 for c in a))
+    res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    probs = lambda cs, tick: [cs[i].problem(*tens[i][:2], _gait(mix[i][1], tick, mix[i][0]), tens[i][2],
+                                            min(tick, 1), feet=tens[i][3]) for i in range(n)]
+    ba.solve(a, probs(a, 0), res)
+    torch.cuda.synchronize()
+    blobs = [c.get_state() for c in a]
+    ba.solve(a, probs(a, 1), res)
+    torch.cuda.synchronize()
+    want = bytes(res.cpu().numpy())
+    fresh = [S.Controller(c) for c, _ in mix]
+    for c, blob in zip(fresh, blobs):
+        c.set_state(blob)
+    bf = S.Batch(n, sum(c.workspace_bytes() + 256 for c in fresh))
+    rf = torch.empty_like(res)
+    bf.solve(fresh, probs(fresh, 1), rf)
+    torch.cuda.synchronize()
+    assert bytes(rf.cpu().numpy()) == want
+    for i in range(n):
+        np.testing.assert_array_equal(_state(a[i])[0], _state(fresh[i])[0])
+        np.testing.assert_array_equal(_state(a[i])[1], _state(fresh[i])[1])
+    ba.close()
+    bf.close()
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
