@@ -403,6 +403,38 @@ def test_host_memory_path_equals_device_path(cuda):
     c2.close()
 
 
+def test_maximum_sample_count(cuda):
+    # K at its maximum (2^24), elite 1 %: sampled costs (first, middle, last and
+    # scattered samples, including the last tile) match the oracle's one-sample
+    # rollouts, and the multi-block selection returns exactly the K_e smallest
+    # (cost, index) keys of the GPU's own costs in index order
+    cfg = W.config("plain_mppi_k512_h12")
+    K = S.MAX_K
+    cfg.update(K=K, H=4, seed=24, method="elite", elite_count=W.elite_count(0.01, K), tile=256)
+    prob = W.problem(cfg)
+    g, o = CudaRun(cfg, prob, tile=256), OracleRun(cfg, prob)
+    r = g.solve()
+    Jg = g.read(S.BUF_COST)
+    ks = [0, 1, 255, 256, K // 2, K // 2 + 77, K - 257, K - 256, K - 2, K - 1] + \
+         np.random.default_rng(24).integers(0, K, size=30).tolist()
+    gated = 0
+    for k in ks:
+        Jo = o.sample(int(k))[0]
+        kap = o.kappa(int(k))
+        if np.isfinite(Jo) and Jo < 3e38 and kap <= 1e-5:
+            assert abs(float(Jg[k]) - Jo) <= max(1e-4, 100 * kap) * abs(Jo), (k, float(Jg[k]), Jo)
+            gated += 1
+    assert gated >= 0.75 * len(ks)  # a 4-step horizon keeps the rollouts well conditioned
+    key = np.where(np.isfinite(Jg), Jg, np.inf).astype(np.float64)
+    Ke = cfg["elite_count"]
+    order = np.lexsort((np.arange(K), key))
+    want = np.sort(order[:Ke])
+    eg = g.read(S.BUF_ELITE)
+    np.testing.assert_array_equal(eg, want)
+    assert r["cost_min"] == float(key.min())
+    g.close()
+
+
 def test_checkpoint_resume_bit_exact(cuda):
     cfg = W.config("plain_mppi_k512_h12")
     prob = W.problem(cfg)
