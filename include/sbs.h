@@ -290,6 +290,10 @@ int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* prob, const 
  * `inflight` (1..8) of its ticks in flight at once.  workspace_bytes is the
  * device-memory budget of its solves' scratch, split evenly between the
  * in-flight ticks: each tick's controllers must fit workspace_bytes / inflight.
+ * Each tick also has 24 max_instances + min(w / 8192, 2^24) + 1024 zero-when-idle
+ * counter words, w = workspace_bytes / inflight: a controller takes a few, an
+ * elite controller selecting from more than 32 768 costs 65 792 (histograms); a
+ * tick over either budget is refused with SBS_ERR_BUDGET.
  * A tick reuses the slot of the tick `inflight` calls earlier and waits for
  * that tick on the host first. */
 int sbs_batch_create(int max_instances, int inflight, size_t workspace_bytes, const sbs_allocator* alloc,

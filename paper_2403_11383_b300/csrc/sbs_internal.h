@@ -13,6 +13,11 @@ constexpr int kMaxKnots = 8;
 constexpr int kPartHeader = 8;               // floats ahead of the per-dimension sums in a partial row
 constexpr int kGroup = 16;                   // tiles whose partial rows one block combines
 constexpr int kRefitThreads = 256;       // plain solves: few controllers, possibly many elites per step
+constexpr int kRefitLanesMax = 1024;     // virtual lanes of a refit with a large elite set
+
+// Virtual lanes of a refit (the order of its sums, the same for every block
+// size): more lanes for a large elite set shorten each lane's chain of loads.
+__host__ __device__ inline int refit_lanes(int Ke) { return Ke > 2048 ? kRefitLanesMax : kRefitThreads; }
 constexpr int kBatchRefitThreads = 128;  // batched ticks: thousands of small refit items (8 blocks per SM)
 constexpr int kSelectThreads = 1024;
 constexpr int kSelectSmemMaxK = 32768;       // costs staged in shared memory up to this K

@@ -51,7 +51,7 @@ struct __align__(16) BlockShared {
     unsigned char sched[SBS_MAX_H];  // stance legs of every step when all samples share the frequency
     float mu12[12], vr12[12], dbar[12];
     float wacc[32][12];
-    float wacc2[kRefitThreads / 32][12];
+    float wacc2[kRefitLanesMax / 32][12];
 };
 
 // A shared-memory vector load the compiler may not hoist out of the step loop
@@ -1206,6 +1206,7 @@ __device__ void refit_block(BlockShared& sh, int b)
     float* dv = dm + P.D;
     const int K = P.K;
     const int Ke = P.method == SBS_NAIVE ? 1 : P.Ke;
+    const int V = refit_lanes(Ke);  // virtual lanes: the order of the sums
     const int32_t* elite = t.ws.elite;
     sbs_result* r = t.result;
     const bool diverged = __ldcg(&r->status) != SBS_OK;
@@ -1232,18 +1233,18 @@ __device__ void refit_block(BlockShared& sh, int b)
         } else {
             // one pass: sums of the deviations and of their squares, both taken
             // about the first elite's deviation d0 (keeps the cancellation small).
-            // The order of the sums is that of kRefitThreads virtual lanes (lane v
-            // takes elites v, v + kRefitThreads, ...; warp totals in warp order), so
-            // a block of any size that divides kRefitThreads gives the same bits.
-            for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
+            // The order of the sums is that of V virtual lanes (lane v takes elites
+            // v, v + V, ...; warp totals in warp order), so a block of any size that
+            // divides V gives the same bits.
+            for (int v0 = 0; v0 < V; v0 += blockDim.x) {
                 const int vl = v0 + tid, vw = vl >> 5;  // virtual lane and warp
                 float s[12], s2[12];
 #pragma unroll
                 for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
                 int kb = vl < Ke ? __ldcg(elite + vl) : 0;
-                for (int e = vl; e < Ke; e += kRefitThreads) {
+                for (int e = vl; e < Ke; e += V) {
                     // the next elite's index is loaded before this one's row is used
-                    const int kn = e + kRefitThreads < Ke ? __ldcg(elite + e + kRefitThreads) : 0;
+                    const int kn = e + V < Ke ? __ldcg(elite + e + V) : 0;
                     const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
                     const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
                     const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
@@ -1266,7 +1267,7 @@ __device__ void refit_block(BlockShared& sh, int b)
             __syncthreads();
             float tot = 0.0f, tot2 = 0.0f;
             if (tid < 12)
-                for (int w = 0; w < kRefitThreads / 32; ++w) {
+                for (int w = 0; w < V / 32; ++w) {
                     tot += sh.wacc[w][tid];
                     tot2 += sh.wacc2[w][tid];
                 }
@@ -1297,24 +1298,24 @@ __device__ void refit_block(BlockShared& sh, int b)
             if (P.method == SBS_NAIVE) {
                 mean_f = (float)__ldcg(t.ws.q + __ldcg(elite)) / 1000.0f;
             } else {
-                // two passes over kRefitThreads virtual lanes (the order is
+                // two passes over V virtual lanes (the order is
                 // independent of the block size, as above)
                 __syncthreads();
-                for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
+                for (int v0 = 0; v0 < V; v0 += blockDim.x) {
                     const int vl = v0 + tid;
                     float s = 0.0f;
-                    for (int e = vl; e < Ke; e += kRefitThreads) s += (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f;
+                    for (int e = vl; e < Ke; e += V) s += (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f;
                     s = warp_sum(s);
                     if (lane == 0) sh.red[vl >> 5][0] = s;
                 }
                 __syncthreads();
                 float tot = 0.0f;
-                for (int w = 0; w < kRefitThreads / 32; ++w) tot += sh.red[w][0];
+                for (int w = 0; w < V / 32; ++w) tot += sh.red[w][0];
                 mean_f = tot / (float)Ke;
-                for (int v0 = 0; v0 < kRefitThreads; v0 += blockDim.x) {
+                for (int v0 = 0; v0 < V; v0 += blockDim.x) {
                     const int vl = v0 + tid;
                     float s2 = 0.0f;
-                    for (int e = vl; e < Ke; e += kRefitThreads) {
+                    for (int e = vl; e < Ke; e += V) {
                         const float d = (float)__ldcg(t.ws.q + __ldcg(elite + e)) / 1000.0f - mean_f;
                         s2 = fmaf(d, d, s2);
                     }
@@ -1323,7 +1324,7 @@ __device__ void refit_block(BlockShared& sh, int b)
                 }
                 __syncthreads();
                 float tot2 = 0.0f;
-                for (int w = 0; w < kRefitThreads / 32; ++w) tot2 += sh.red[w][1];
+                for (int w = 0; w < V / 32; ++w) tot2 += sh.red[w][1];
                 vf = fmaxf(tot2 / (float)Ke, P.var_f_min);
             }
         }
@@ -1374,7 +1375,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __r
     select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
 }
 
-__global__ void __launch_bounds__(kRefitThreads) k_refit(const InstParams* __restrict__ dP, TickArgs t)
+__global__ void __launch_bounds__(kRefitLanesMax) k_refit(const InstParams* __restrict__ dP, TickArgs t)
 {
     __shared__ BlockShared sh;
     load_params(dP, sh);
@@ -1933,7 +1934,8 @@ int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t,
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
 {
     const int grid = hP.nt + (hP.adaptive ? 1 : 0);
-    k_refit<<<grid, kRefitThreads, 0, (cudaStream_t)stream>>>(dP, t);
+    const int threads = hP.method == SBS_ELITE ? refit_lanes(hP.Ke) : kRefitThreads;
+    k_refit<<<grid, threads, 0, (cudaStream_t)stream>>>(dP, t);
     return status_of(cudaGetLastError());
 }
 

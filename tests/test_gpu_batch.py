@@ -298,6 +298,45 @@ def test_checkpoint_resume_in_the_batch():
     bf.close()
 
 
+def test_large_elite_set_batch_equals_plain():
+    # more than 2048 elites: 1024 virtual lanes, refit by 1024-thread blocks in a
+    # plain solve and by 128-thread blocks in eight passes in a batch, same bits
+    import torch
+    base = W.config("plain_mppi_k512_h12")
+    specs = [dict(K=65536, H=5, method="elite", elite_count=3277),
+             dict(K=40000, H=6, method="elite", elite_count=2500, adaptive=True),
+             dict(K=4096, H=8, method="elite", elite_count=205)]
+    mix = []
+    for i, sp in enumerate(specs):
+        c = dict(base)
+        c.update(sp)
+        c.update(seed=300 + i, ctrl=i)
+        mix.append((c, W.problem(c)))
+    plain = [S.Controller(c) for c, _ in mix]
+    batched = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    n = len(mix)
+    # two selections over more than 32 768 costs need 2 x 65 792 counter words,
+    # workspace / 8192 of which the batch holds
+    b = S.Batch(n, max(sum(c.workspace_bytes() + 256 for c in batched), 2 << 30))
+    res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(2):
+        probs, want = [], []
+        for i, (c, p) in enumerate(mix):
+            x0, xr, fe, _ = tens[i]
+            g = _gait(p, tick, c)
+            want.append(plain[i].solve(x0, xr, g, fe, min(tick, 1)).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, min(tick, 1)))
+        b.solve(batched, probs, res)
+        torch.cuda.synchronize()
+        for i in range(n):
+            assert bytes(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy()) == \
+                bytes(want[i].cpu().numpy())
+            np.testing.assert_array_equal(_state(batched[i])[0], _state(plain[i])[0])
+            np.testing.assert_array_equal(_state(batched[i])[1], _state(plain[i])[1])
+    b.close()
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
