@@ -118,7 +118,8 @@ inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1)
                   + 12 * (size_t)H   // reference
                   + (P > 0 ? (size_t)H * 4 * ((P + 3) / 4) + 12 * (size_t)nb * H : 0)  // spline basis, mean forces
                   + (P > 0 ? (size_t)48 * ((P + 3) / 4) * T : 0)  // per-thread knot deviations
-                  + (size_t)nwarps * nf;  // per-warp partial sums / combined row
+                  + (P > 0 ? (size_t)nwarps * nf  // per-warp partial sums, then the combined row
+                           : (size_t)(6 * T > nf + kPartHeader ? 6 * T : nf + kPartHeader));  // weight list and slice sums, then the combined row
     return floats * sizeof(float);
 }
 

@@ -616,55 +616,90 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             sh.red[warp][3] = s3;
         }
     }
-    // A warp whose weights all underflowed to zero contributes exact zeros.
-    const bool warp_live = __any_sync(kFull, w != 0.0f);
-    if (!warp_live) {
-        for (int d = lane; d < P.nf; d += 32) v.acc[warp * P.nf + d] = 0.0f;
-    } else if constexpr (NP == 0) {
+    const int PS = P.part_stride;
+    float* row = t.ws.part + (size_t)tile * PS;
+    if constexpr (NP == 0) {
+        // Weighted deviation sums over the tile's samples of nonzero weight (the rest
+        // underflowed, are non-finite or lie past K).  Those samples are listed in
+        // shared memory in sample order; thread i then owns float4 column c = i mod 3H
+        // of the tile's row (step c / 3, forces 4 (c mod 3) .. +3) and slice
+        // s = i / 3H of the list (every nsl-th entry), so each deviation row is read
+        // once, by three threads, with no cross-lane reduction; the slices' sums
+        // are added in slice order.
+        float2* lst = reinterpret_cast<float2*>(v.acc);  // (weight, sample) per listed sample
+        const unsigned nzb = __ballot_sync(kFull, w != 0.0f);
+        if (lane == 0) sh.wtot[warp] = __popc(nzb);
+        __syncthreads();
+        int pos = 0, nnz = 0;
+        for (int g = 0; g < nw; ++g) {
+            const int c = sh.wtot[g];
+            pos += g < warp ? c : 0;
+            nnz += c;
+        }
+        if (w != 0.0f) lst[pos + __popc(nzb & ((1u << lane) - 1u))] = make_float2(w, __int_as_float(tid));
+        __syncthreads();
+        const int ncol = 3 * P.H;
+        const int nsl = ncol < T ? T / ncol : 1;
+        float4* slice_sum = reinterpret_cast<float4*>(v.acc + 2 * T);  // [nsl][ncol] when nsl > 1
+        const float4* th4 = reinterpret_cast<const float4*>(theta) + (size_t)tile * T * 3;
+        float4* row4 = reinterpret_cast<float4*>(row + kPartHeader);
+        for (int it = tid; it < nsl * ncol; it += T) {
+            const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
+            const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 4
-        for (int j = 0; j < P.H; ++j) {
-            float vv[12], o[3];
-            if (valid) {
-                const float4* src = reinterpret_cast<const float4*>(theta + ((size_t)j * K + k) * 12);
-                const float4 a = src[0], b = src[1], c = src[2];
-                vv[0] = w * a.x; vv[1] = w * a.y; vv[2] = w * a.z; vv[3] = w * a.w;
-                vv[4] = w * b.x; vv[5] = w * b.y; vv[6] = w * b.z; vv[7] = w * b.w;
-                vv[8] = w * c.x; vv[9] = w * c.y; vv[10] = w * c.z; vv[11] = w * c.w;
-            } else {
-#pragma unroll
-                for (int c = 0; c < 12; ++c) vv[c] = 0.0f;
+            for (int e = sl; e < nnz; e += nsl) {
+                const float2 we = lst[e];
+                const float4 d = src[3 * __float_as_int(we.y)];
+                a.x = fmaf(we.x, d.x, a.x);
+                a.y = fmaf(we.x, d.y, a.y);
+                a.z = fmaf(we.x, d.z, a.z);
+                a.w = fmaf(we.x, d.w, a.w);
             }
-            const int c0 = warp_sum12(vv, o);
-            if ((lane & 7) == 0) {
-                float* a = v.acc + warp * P.nf + 12 * j + c0;
-                a[0] = o[0];
-                a[1] = o[1];
-                a[2] = o[2];
+            if (nsl == 1) row4[c] = a;
+            else slice_sum[it] = a;
+        }
+        if (nsl > 1) {
+            __syncthreads();
+            for (int c = tid; c < ncol; c += T) {
+                float4 a = slice_sum[c];
+                for (int sl = 1; sl < nsl; ++sl) {
+                    const float4 b = slice_sum[sl * ncol + c];
+                    a.x += b.x;
+                    a.y += b.y;
+                    a.z += b.z;
+                    a.w += b.w;
+                }
+                row4[c] = a;
             }
         }
     } else {
+        // A warp whose weights all underflowed to zero contributes exact zeros.
+        const bool warp_live = __any_sync(kFull, w != 0.0f);
         const float* dsf = reinterpret_cast<const float*>(v.dsm);
+        if (!warp_live) {
+            for (int d = lane; d < P.nf; d += 32) v.acc[warp * P.nf + d] = 0.0f;
+        } else {
 #pragma unroll 1
-        for (int p = 0; p < NP; ++p) {
-            float vv[12], o[3];
+            for (int p = 0; p < NP; ++p) {
+                float vv[12], o[3];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) vv[c] = w * dsf[(((size_t)c * NQ + p / 4) * T + tid) * 4 + (p & 3)];
-            const int c0 = warp_sum12(vv, o);
-            if ((lane & 7) == 0) {
-                float* a = v.acc + warp * P.nf + 12 * p + c0;
-                a[0] = o[0];
-                a[1] = o[1];
-                a[2] = o[2];
+                for (int c = 0; c < 12; ++c) vv[c] = w * dsf[(((size_t)c * NQ + p / 4) * T + tid) * 4 + (p & 3)];
+                const int c0 = warp_sum12(vv, o);
+                if ((lane & 7) == 0) {
+                    float* a = v.acc + warp * P.nf + 12 * p + c0;
+                    a[0] = o[0];
+                    a[1] = o[1];
+                    a[2] = o[2];
+                }
             }
         }
-    }
-    __syncthreads();
-    const int PS = P.part_stride;
-    float* row = t.ws.part + (size_t)tile * PS;
-    for (int d = tid; d < P.nf; d += T) {
-        float s = 0.0f;
-        for (int ww = 0; ww < nw; ++ww) s += v.acc[ww * P.nf + d];
-        row[kPartHeader + d] = s;
+        __syncthreads();
+        for (int d = tid; d < P.nf; d += T) {
+            float s = 0.0f;
+            for (int ww = 0; ww < nw; ++ww) s += v.acc[ww * P.nf + d];
+            row[kPartHeader + d] = s;
+        }
     }
     if (tid == 0) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
