@@ -174,7 +174,7 @@ class Robots:
         return self.probs[idx]
 
 
-def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=3, budget=8 << 30, seed=3, robots=None):
+def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, seed=3, robots=None):
     """Serve n robots for warmup + duration seconds; statistics of the measured window."""
     import torch
     R = robots if robots is not None else Robots(n, seed)

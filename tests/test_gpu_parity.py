@@ -143,6 +143,33 @@ def test_mppi_k1_returns_its_sample(cuda):
     g.close()
 
 
+@pytest.mark.parametrize("lam,tile", [(1e-7, 128), (1e6, 256), (1e6, 64)])
+def test_mppi_weight_extremes(cuda, lam, tile):
+    # lambda -> 0: a tile keeps nonzero weights only within a few ulps of its best
+    # cost, and the update is the best sample (Alg. 5 with beta = min J); lambda
+    # -> inf: every finite sample has weight ~1 and the update is the plain
+    # sample mean.  The FP64 update is taken from the GPU's own costs (the staged
+    # parity of the update), on the oracle's samples.
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(K=3001, lam=lam, seed=97, tile=tile)
+    prob = W.problem(cfg)
+    g, o = CudaRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
+    J, q, th, margin, kap = o.rollout()
+    g.solve()
+    Jg = g.read(S.BUF_COST).astype(np.float64)
+    mg, _ = g.state()
+    _, mo, _, _ = orc.mppi(Jg, th, lam)
+    assert np.all(np.abs(mg - mo) <= MEAN_ATOL), np.max(np.abs(mg - mo))
+    fin = np.isfinite(Jg)
+    if lam < 1.0:
+        gap = np.sort(Jg[fin])[1] - Jg[fin].min()
+        if gap * 1.0 / lam > 120.0:  # the second-best weight underflows: the best sample alone
+            np.testing.assert_allclose(mg, th[int(np.argmin(Jg))], atol=MEAN_ATOL, rtol=0)
+    else:
+        np.testing.assert_allclose(mg, th[fin].mean(axis=0), atol=MEAN_ATOL, rtol=0)
+    g.close()
+
+
 def test_mppi_many_tiles_hierarchical_combine(cuda):
     # 40 000 samples = 313 tiles = 20 groups of 16: exercises the two-level combine
     cfg = W.config("plain_mppi_k512_h12")
