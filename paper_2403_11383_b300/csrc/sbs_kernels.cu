@@ -1862,7 +1862,8 @@ static int status_of(cudaError_t e) { return e == cudaSuccess ? SBS_OK : SBS_ERR
 
 static int ensure_smem_attr(const void* fn, size_t smem)
 {
-    if (smem <= 48 * 1024) return SBS_OK;
+    // the 48 KB a block may take without opting in include its static BlockShared
+    if (smem + sizeof(BlockShared) <= 48 * 1024) return SBS_OK;
     return status_of(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 }
 

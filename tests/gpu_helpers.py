@@ -166,8 +166,12 @@ def mppi_tolerance(J, th, kap, lam, mean_ref):
     # from it: an unbounded tolerance (infinite conditioning) times a zero
     # distance adds nothing
     diff = np.abs(th - mean_ref[None, :])
+    # the mean's derivative with respect to J_k is -(w_k / lam)(theta_k - mean): a
+    # sample of zero weight moves it by nothing to first order, whatever its
+    # cost tolerance (an unbounded one included)
     with np.errstate(invalid="ignore"):
-        prop = np.where(diff == 0.0, 0.0, (w * tolJ)[:, None] * diff) / lam
+        wt = np.where(w == 0.0, 0.0, w * tolJ)
+        prop = np.where(diff == 0.0, 0.0, wt[:, None] * diff) / lam
     return MEAN_ATOL + prop.sum(axis=0)
 
 

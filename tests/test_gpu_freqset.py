@@ -92,10 +92,15 @@ def test_paper_gait_adaptation_setting_full_size(cuda):
 @pytest.mark.parametrize("K,H,fs,tile", [(5, 7, (1300, 2000, 2400), 0), (300, 12, (1300, 2400), 64),
                                          (1000, 25, (1100, 1500, 1900, 2300, 2700), 128),
                                          (777, 12, (2000,), 256),
-                                         (4000, 12, (1000, 1300, 1600, 2000, 2400, 2800, 3200, 3600), 256)])
+                                         (4000, 12, (1000, 1300, 1600, 2000, 2400, 2800, 3200, 3600), 256),
+                                         # 44.5 KB of dynamic shared memory: with the static block state
+                                         # above 48 KB, so the launch must opt in
+                                         (600, 80, (1300, 2000, 2400), 256)])
 def test_ragged_sizes_and_set_lengths(cuda, K, H, fs, tile):
     cfg = W.config("naive_freqset_k10000_h12")
     cfg.update(K=K, H=H, freq_set_mhz=fs, seed=K + H)
+    if H > 50:
+        cfg["dt_us"] = 5000  # a 0.4 s horizon
     prob = W.problem(cfg)
     g, o = CudaRun(cfg, prob, tile=tile), OracleRun(cfg, prob)
     _check_iteration(cfg, g, o, g.solve())

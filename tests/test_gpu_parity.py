@@ -394,6 +394,16 @@ def test_spline_small_mppi_parity(cuda):
     mppi_parity(cfg, W.problem(cfg), "spline-small")
 
 
+@pytest.mark.parametrize("tile", [96, 160])
+def test_spline_full_horizon_odd_tiles(cuda, tile):
+    # 100 steps, 4 knots: 160-sample tiles take 43.5 KB of dynamic shared memory,
+    # above 48 KB with the static block state (the launch opts in); 96 leaves
+    # three warps per block.  dt = 1 ms keeps the 0.1 s horizon well conditioned.
+    cfg = W.config("spline_k262144_h100")
+    cfg.update(K=3001, method="mppi", compare_mppi=False, sigma_init=5.0, seed=tile, dt_us=1000)
+    mppi_parity(cfg, W.problem(cfg), f"spline-T{tile}", tile=tile)
+
+
 def test_spline_warm_shift(cuda):
     cfg = W.config("spline_k262144_h100")
     cfg.update(K=512, H=25, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=12)
