@@ -284,7 +284,7 @@ def run_single(args, world, rank, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "K": cfg["K"], "H": cfg["H"], "P": cfg.get("P", 0),
-                           "iterations": cfg["iterations"], "method": cfg["method"],
+                           "iterations": cfg["iterations"], "method": cfg["method"], "tile": ctl.tile,
                            "parallelism": f"replicas x{world}"},
                 "solves_per_s": world / (ms * 1e-3),
                 "roofline": {"kernel": "whole solve", "bound": "alu", "achieved": achieved, "peak": peak,

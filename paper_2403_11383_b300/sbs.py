@@ -304,6 +304,11 @@ class Controller:
     def handle(self):
         return self._h
 
+    @property
+    def tile(self) -> int:
+        """Samples per tile (sbs_config.tile; 0 there selects 128)."""
+        return self._c.tile or 128
+
     def device_bytes(self) -> int:
         return lib().sbs_device_bytes(self._h)
 

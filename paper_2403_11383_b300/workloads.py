@@ -90,8 +90,10 @@ def config(name: str) -> dict:
                     elite_count=elite_count(0.05, 8192), adaptive=True, compare_mppi=True,
                     f_ext=(0.0, 60.0, 0.0))
     if name == "spline_k262144_h100":
+        # 256-sample tiles: 473 us per solve on a B300 against 494 (128), 509 (192),
+        # 521 (160), 532 (96) and 557 (64)
         return _cfg(K=262144, H=100, P=4, dt_us=10_000, seed=4, method="elite",
-                    elite_count=elite_count(0.01, 262144), adaptive=True, compare_mppi=True)
+                    elite_count=elite_count(0.01, 262144), adaptive=True, compare_mppi=True, tile=256)
     if name == "naive_freqset_k10000_h12":
         # the paper's gait-adaptation setting (Sec. V): 10 000 rollouts, N = 12,
         # dt = 0.02 s, trot, step frequency uniform over {1.3, 2.0, 2.4} Hz with one
