@@ -208,8 +208,14 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
 int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
+// A batched tick's device header: two count blocks of 8 ints (the first rollout
+// launch, select and refit read the first; a second rollout launch over the MPPI
+// controllers' tiles reads the second), then the records.
+constexpr int kBatchCountsB = 8;
+constexpr size_t kBatchHeader = 64;
+// grids: rollout, select, refit, and the second rollout launch (0: none).
 int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem,
-                 size_t sel_smem, int T, const int grids[3], void* stream, void* const* events);
+                 size_t sel_smem, int T, const int grids[4], void* stream, void* const* events);
 int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int counts[4], int grids[3]);
 const void* batch_rollout_fn(int P, int mode);
 const void* batch_select_fn(int mode);

@@ -1490,7 +1490,8 @@ __device__ __forceinline__ int find_rec_block(BlockShared& sh, const InstRec* re
     return sh.item;
 }
 
-// counts = {controllers, tile items, selection items, refit items}; heads = queue heads.
+// counts = {controllers, end of the tile items, selection items, refit items, first
+// tile item of a grid launch}; heads = queue heads.
 // Every controller of one launch uses the same policy (NP).
 template <int NP, bool EXT>
 __global__ void __launch_bounds__(SBS_MAX_TILE) k_batch_rollout(const InstRec* __restrict__ recs,
@@ -1520,7 +1521,7 @@ __device__ __forceinline__ void rollout_grid_item(const InstRec* __restrict__ re
 {
     extern __shared__ float4 dyn4[];
     __shared__ BlockShared sh;
-    const int it = blockIdx.x;
+    const int it = blockIdx.x + counts[4];  // a launch may start past the first tiles
     if (it >= counts[1]) return;
     const int i = find_rec_block(sh, recs, counts[0], it, 0);
     load_params(recs[i].dP, sh);
@@ -2008,7 +2009,7 @@ int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int c
 
 // events: null, or four CUDA events recorded before and after each stage.
 int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int* dHeads, size_t smem,
-                 size_t sel_smem, int T, const int grids[3], void* stream, void* const* events)
+                 size_t sel_smem, int T, const int grids[4], void* stream, void* const* events)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode)};
@@ -2017,11 +2018,16 @@ int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int*
     const size_t shm[3] = {smem, sel_smem, 0};
     const InstRec* r = dRecs;
     const int* c = dCounts;
+    const int* c2 = dCounts + kBatchCountsB;
     int* hd = dHeads;
     void* args[] = {(void*)&r, (void*)&c, (void*)&hd};
+    void* args2[] = {(void*)&r, (void*)&c2, (void*)&hd};
     for (int k = 0; k < 3; ++k) {
         if (events) cudaEventRecord((cudaEvent_t)events[k], s);
         if (cudaLaunchKernel(fns[k], dim3(grids[k]), blocks[k], args, shm[k], s) != cudaSuccess) return SBS_ERR_CUDA;
+        if (k == 0 && grids[3] > 0 &&  // the MPPI controllers' tiles (grid mode, split tick)
+            cudaLaunchKernel(fns[0], dim3(grids[3]), blocks[0], args2, shm[0], s) != cudaSuccess)
+            return SBS_ERR_CUDA;
     }
     if (events) cudaEventRecord((cudaEvent_t)events[3], s);
     return SBS_OK;
