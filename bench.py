@@ -136,6 +136,16 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def solve_launches(cfg):
+    """Kernel launches of one plain solve: per iteration the rollout, and for elite
+    and Naive the selection (five kernels for an elite set chosen from more than
+    32 768 costs) and the refit."""
+    if cfg["method"] == "mppi":
+        return cfg["iterations"]
+    select = 5 if cfg["method"] == "elite" and cfg["K"] > 32768 else 1
+    return cfg["iterations"] * (2 + select)
+
+
 def rollout_traffic():
     """DRAM bytes per sample-step of the rollout kernel from the committed ncu
     record, or None when the kernel sources changed since that capture."""
@@ -294,7 +304,7 @@ def run_single(args, world, rank, local):
                 "e2e": {"value": world * ss / e2e_s, "unit": "sample-steps/s",
                         "h2d_bytes_per_step": int(4 * (12 + 3 + 12 * cfg["H"])),
                         "d2h_bytes_per_step": S.RESULT_BYTES},
-                "gpu_launches": args.steps * cfg["iterations"] * (1 if cfg["method"] == "mppi" else 3),
+                "gpu_launches": args.steps * solve_launches(cfg),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
 
@@ -340,6 +350,7 @@ def main():
     n = len(ctls)
     ss_tick = sum(c["K"] * c["H"] for c, _ in mix)
     mppi_ss = sum(c["K"] * c["H"] for c, _ in mix if c["method"] == "mppi")
+    mppi_n = sum(1 for c, _ in mix if c["method"] == "mppi")
     arena = sum(c.workspace_bytes() + 256 for c in ctls)
     batch = S.Batch(n, 2 * arena, inflight=2)  # two ticks in flight: the next is prepared while one runs
     results = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device=dev)
@@ -520,7 +531,9 @@ def main():
                         "latency-bound chains of dependent loads, far from the HBM roof"},
             "e2e": {"value": e2e_value, "unit": "sample-steps/s",
                     "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel())},
-            "gpu_launches": 3 * args.steps,
+            # rollout, selection and refit; a split tick (grid mode, MPPI and elite or
+            # Naive controllers together) launches the rollout twice
+            "gpu_launches": (4 if mode == "grid" and 0 < mppi_n < len(mix) else 3) * args.steps,
             "clocks": clk,
             "status_counts": {"ok": sum(s == S.OK for s in status),
                               "diverged": sum(s == S.ERR_DIVERGED for s in status)},
