@@ -519,8 +519,9 @@ def main():
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,
                          "flops_per_launch": flops_launch,
                          "traffic": None if traffic_ss is None else traffic_ss * ss_tick,
-                         "traffic_note": "ncu DRAM read+write per sample-step on the 48-controller mix, scaled "
-                                         "to this launch's sample-steps (profiles/rollout_traffic.json)"},
+                         "traffic_note": "ncu DRAM read+write of the two rollout launches of this workload's tick "
+                                         "(one-pass capture, profiles/rollout_traffic.json), per sample-step "
+                                         "times this tick's sample-steps"},
             "update_roofline": {
                 "bound": "hbm", "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
                 "select": {"bytes": sel_bytes, "achieved": sel_bytes / (sel_ms * 1e-3) / 1e9,
