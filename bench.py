@@ -509,7 +509,7 @@ def main():
                        "l2": "per-tick working set above L2 (sampled deviations "
                        f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
-            "latency_ms": {"p50": p50, "p99": p99, "kind": "device time of one 256-controller tick"},
+            "latency_ms": {"p50": p50, "p99": p99, "kind": f"device time of one {len(mix)}-controller tick"},
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
                       "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
