@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=3.0)
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100",
-                             "naive_freqset_k10000_h12"],
+                             "naive_freqset_k10000_h12", "worldfeet_mppi_k4096_h25"],
                     help="batched: the 256-controller tick (default); otherwise one controller's solves")
     return ap.parse_args()
 
@@ -254,10 +254,12 @@ def run_single(args, world, rank, local):
     prob = W.problem(cfg)
     ctl = S.Controller(cfg)
     x0, xref, fe = (torch.tensor(np.float32(prob[k]), device=dev) for k in ("x0", "xref", "f_ext"))
+    # ground-fixed stance feet ([4, 2] positions) for the controllers that use them
+    feet = torch.tensor(np.float32(prob["feet"]), device=dev) if "feet" in prob else None
     res = torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device=dev)
     for w in range(max(args.warmup, 3)):
-        ctl.solve(x0, xref, prob["gait"], fe, 0 if w == 0 else 1, res)
-    p1 = ctl.problem(x0, xref, prob["gait"], fe, 1)  # built once, as a control loop would
+        ctl.solve(x0, xref, prob["gait"], fe, 0 if w == 0 else 1, res, feet=feet)
+    p1 = ctl.problem(x0, xref, prob["gait"], fe, 1, feet=feet)  # built once, as a control loop would
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
@@ -280,8 +282,9 @@ def run_single(args, world, rank, local):
     peak = S.fp32_peak() / 1e12
     # host inputs and result, synchronised per solve
     hx0, hxr, hfe = (np.ascontiguousarray(np.float32(prob[k])) for k in ("x0", "xref", "f_ext"))
+    hfeet = np.ascontiguousarray(np.float32(prob["feet"])) if "feet" in prob else None
     r = S.Result()
-    hp = ctl.problem(hx0, hxr, prob["gait"], hfe, 1, host=True)
+    hp = ctl.problem(hx0, hxr, prob["gait"], hfe, 1, host=True, feet=hfeet)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -302,7 +305,7 @@ def run_single(args, world, rank, local):
                              "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
                              "flops_per_sample_step": flops_per_sample_step(cfg), "traffic": None},
                 "e2e": {"value": world * ss / e2e_s, "unit": "sample-steps/s",
-                        "h2d_bytes_per_step": int(4 * (12 + 3 + 12 * cfg["H"])),
+                        "h2d_bytes_per_step": int(4 * (12 + 3 + 12 * cfg["H"] + (8 if "feet" in prob else 0))),
                         "d2h_bytes_per_step": S.RESULT_BYTES},
                 "gpu_launches": args.steps * solve_launches(cfg),
                 "clocks": clk}
