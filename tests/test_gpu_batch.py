@@ -90,6 +90,51 @@ def test_batch_equals_plain(mode):
     b.close()
 
 
+@pytest.mark.parametrize("inflight", [1, 2])
+def test_changing_controller_sets(inflight):
+    # ticks over changing subsets of the mix, as a request loop makes them: the
+    # tick's graph splits its rollout when elite or Naive and MPPI controllers meet,
+    # and keeps one launch otherwise, so consecutive ticks of a slot rebuild or
+    # update it; every result and state equals the controller's own plain solve
+    import torch
+    mix = _mix()
+    n = len(mix)
+    plain = [S.Controller(c) for c, _ in mix]
+    batched = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    mppi = [i for i, (c, _) in enumerate(mix) if c["method"] == "mppi"]
+    upd = [i for i, (c, _) in enumerate(mix) if c["method"] != "mppi"]
+    subsets = [list(range(n)), mppi, upd, list(range(n)), list(range(6)), upd[:2] + mppi[:1], list(range(n))]
+    b = S.Batch(n, inflight * sum(c.workspace_bytes() + 256 for c in batched), inflight=inflight)
+    b.set_mode(S.BATCH_GRID)
+    res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ticks = [0] * n
+    for sub in subsets:
+        probs, plain_res = [], []
+        for i in sub:
+            c, p = mix[i]
+            x0, xr, fe, ft = tens[i]
+            shift = 0 if ticks[i] == 0 else 1
+            g = _gait(p, ticks[i], c)
+            plain_res.append(plain[i].solve(x0, xr, g, fe, shift, feet=ft).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, shift, feet=ft))
+            ticks[i] += 1
+        out = res[:len(sub) * S.RESULT_BYTES]
+        b.solve([batched[i] for i in sub], probs, out)
+        torch.cuda.synchronize()
+        for r, i in enumerate(sub):
+            rp = S.parse_result(plain_res[r].cpu().numpy())
+            rb = S.parse_result(out[r * S.RESULT_BYTES:(r + 1) * S.RESULT_BYTES].cpu().numpy())
+            assert rb["status"] == rp["status"], (sub, i)
+            np.testing.assert_array_equal(rb["u0"], rp["u0"])
+            assert rb["cost_min"] == rp["cost_min"] and rb["q_freq"] == rp["q_freq"] and rb["iter"] == rp["iter"]
+            mp, vp = _state(plain[i])
+            mb, vb = _state(batched[i])
+            np.testing.assert_array_equal(mb, mp)
+            np.testing.assert_array_equal(vb, vp)
+    b.close()
+
+
 def test_same_alone_and_in_the_mix():
     # one controller solved in a batch of one and inside a batch of eight
     import torch
