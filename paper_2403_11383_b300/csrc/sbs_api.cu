@@ -611,16 +611,16 @@ struct sbs_batch_slot {
     char* arena;          // workspace arena of this slot's ticks
     unsigned* counters;   // counter arena (zero while idle)
     cudaEvent_t done;
+    cudaEvent_t copied;   // the records are on the device (replayed ticks copy them on the batch's copy stream)
     bool used;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    cudaGraphNode_t copy_node, kernel_node[4];  // rollout, select, refit, MPPI rollout
+    cudaGraphNode_t kernel_node[4];  // rollout, select, refit, MPPI rollout
     cudaKernelNodeParams kparams[4];
     size_t key_smem, key_sel;
     int key_T, key_var, key_mode;
     bool key_split;
     int grids[4];
-    size_t copy_bytes;    // bytes the graph's record copy moves
 };
 
 // What a batched tick needs that depends on its controllers alone (not on their
@@ -650,6 +650,7 @@ struct sbs_batch {
     bool profiling;
     cudaEvent_t ev[4];
     bool ev_valid;
+    cudaStream_t cstream;  // records copies of replayed ticks, ahead of the tick before
     sbs_batch_plan plan;
 };
 
@@ -673,6 +674,11 @@ extern "C" int sbs_batch_create(int max_instances, int inflight, size_t workspac
     b->mode = SBS_BATCH_GRID;
     const char* ng = std::getenv("SBS_NO_GRAPH");
     b->use_graph = !(ng && ng[0] == '1');
+    if (cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return SBS_ERR_CUDA;
+    }
     for (int i = 0; i < b->nslots; ++i) {
         sbs_batch_slot& sl = b->slot[i];
         sl.key_mode = -1;
@@ -681,7 +687,8 @@ extern "C" int sbs_batch_create(int max_instances, int inflight, size_t workspac
         const size_t total = rec_bytes + 256 + cnt_bytes + b->arena_bytes;
         sl.dev = (char*)dev_alloc(&b->alloc, b->has_alloc, total);
         if (!sl.dev || cudaHostAlloc((void**)&sl.pin, b->bytes, cudaHostAllocDefault) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             sbs_batch_destroy(b);
             return SBS_ERR_OOM;
@@ -739,14 +746,16 @@ extern "C" void sbs_batch_destroy(sbs_batch* b)
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
         if (sl.graph) cudaGraphDestroy(sl.graph);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.copied) cudaEventDestroy(sl.copied);
         if (sl.pin) cudaFreeHost(sl.pin);
         dev_free(&b->alloc, b->has_alloc, sl.dev);
     }
+    if (b->cstream) cudaStreamDestroy(b->cstream);
     delete b;
 }
 
-// The tick graph of a slot: records copy -> queue-head reset -> rollout -> select ->
-// refit.  A split tick (grid mode, elite or Naive controllers and MPPI controllers in
+// The tick graph of a slot: queue-head reset -> rollout -> select -> refit (the records
+// reach the device before the launch, on the batch's copy stream).  A split tick (grid mode, elite or Naive controllers and MPPI controllers in
 // one batch) rolls out the former first, so their selection and refit run beside a
 // second rollout launch over the MPPI controllers' tiles; the update chain takes
 // the device's highest stream priority so that its blocks are dispatched first
@@ -765,10 +774,8 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     }
     cudaGraph_t g;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return SBS_ERR_CUDA;
-    cudaGraphNode_t n_cp, n_ms;
-    bool ok = cudaGraphAddMemcpyNode1D(&n_cp, g, nullptr, 0, sl.dev, sl.pin, b->bytes, cudaMemcpyHostToDevice) ==
-              cudaSuccess;
-    sl.copy_bytes = b->bytes;
+    cudaGraphNode_t n_ms;
+    bool ok = true;
     cudaMemsetParams mp;
     std::memset(&mp, 0, sizeof(mp));
     mp.dst = sl.heads;
@@ -776,7 +783,7 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     mp.elementSize = 4;
     mp.width = 4;
     mp.height = 1;
-    ok = ok && cudaGraphAddMemsetNode(&n_ms, g, &n_cp, 1, &mp) == cudaSuccess;
+    ok = ok && cudaGraphAddMemsetNode(&n_ms, g, nullptr, 0, &mp) == cudaSuccess;
     const InstRec* recs = (const InstRec*)(sl.dev + kBatchHeader);
     const int* counts = (const int*)sl.dev;
     const int* counts_b = counts + kBatchCountsB;
@@ -819,7 +826,6 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     for (int k = 0; k < 4; ++k) sl.kparams[k].kernelParams = nullptr;  // args above go out of scope
     sl.graph = g;
     sl.exec = ex;
-    sl.copy_node = n_cp;
     return SBS_OK;
 }
 
@@ -1000,12 +1006,11 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
             st = update_graph_grids(sl, grids, split);
             if (st) return st;
         }
-        if (used != sl.copy_bytes) {  // the record copy keeps its size while the batch does
-            if (cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.pin, used,
-                                                   cudaMemcpyHostToDevice) != cudaSuccess)
-                return SBS_ERR_CUDA;
-            sl.copy_bytes = used;
-        }
+        // the slot's last tick has finished (synchronised above), so its records may be
+        // replaced while the tick before this one still runs
+        if (cudaMemcpyAsync(sl.dev, sl.pin, used, cudaMemcpyHostToDevice, b->cstream) != cudaSuccess ||
+            cudaEventRecord(sl.copied, b->cstream) != cudaSuccess || cudaStreamWaitEvent(s, sl.copied, 0) != cudaSuccess)
+            return SBS_ERR_CUDA;
         if (cudaGraphLaunch(sl.exec, s) != cudaSuccess) return SBS_ERR_CUDA;
     } else {
         if (sl.exec && rekey) {  // the graph's launch shapes no longer match
