@@ -295,7 +295,11 @@ int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* prob, const 
  * elite controller selecting from more than 32 768 costs 65 792 (histograms); a
  * tick over either budget is refused with SBS_ERR_BUDGET.
  * A tick reuses the slot of the tick `inflight` calls earlier and waits for
- * that tick on the host first. */
+ * that tick on the host first.  The batch owns one non-blocking CUDA stream on
+ * which a replayed tick copies its records to the device while the tick before
+ * still runs; the caller's stream waits for that copy through an event, so a
+ * batched tick cannot be recorded by the caller's own stream capture.
+ * sbs_batch_destroy synchronises the device first. */
 int sbs_batch_create(int max_instances, int inflight, size_t workspace_bytes, const sbs_allocator* alloc,
                      sbs_batch** out);
 void sbs_batch_destroy(sbs_batch* b);
