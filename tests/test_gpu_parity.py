@@ -394,6 +394,56 @@ def test_spline_small_mppi_parity(cuda):
     mppi_parity(cfg, W.problem(cfg), "spline-small")
 
 
+@pytest.mark.parametrize("P,tile", [(2, 128), (3, 64), (6, 128), (8, 128), (8, 256)])
+def test_spline_knot_counts_mppi(cuda, P, tile):
+    # every compiled knot count: 2-4 knots keep one float4 of deviations per
+    # force axis and thread, 6 and 8 two
+    cfg = W.config("spline_k262144_h100")
+    cfg.update(K=3001, H=25, P=P, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=40 + P,
+               tile=tile)
+    mppi_parity(cfg, W.problem(cfg), f"spline-P{P}-T{tile}", tile=tile)
+
+
+@pytest.mark.parametrize("P", [3, 8])
+def test_spline_knot_counts_elite(cuda, P):
+    # the elite refit of every knot and the frequency (one refit block per knot)
+    cfg = W.config("spline_k262144_h100")
+    cfg.update(K=3001, H=25, P=P, dt_us=20000, compare_mppi=False, sigma_init=5.0, seed=50 + P, tile=128,
+               elite_count=W.elite_count(0.02, 3001))
+    elite_parity(cfg, W.problem(cfg), f"spline-elite-P{P}", tile=128)
+
+
+@pytest.mark.parametrize("P", [4, 6, 8])
+def test_spline_warm_start_two_ticks(cuda, P):
+    # the second tick samples about the first tick's knots moved one step along the
+    # spline (the knot shift map), on both sides
+    cfg = W.config("spline_k262144_h100")
+    cfg.update(K=2001, H=25, P=P, dt_us=20000, method="mppi", compare_mppi=False, sigma_init=5.0, seed=60 + P,
+               tile=128)
+    prob = W.problem(cfg)
+    g, o = CudaRun(cfg, prob, tile=128), OracleRun(cfg, prob)
+    g.solve()
+    o.solve()
+    gait2 = dict(prob["gait"])
+    gait2["phase0"] = (gait2["phase0"] + cfg["q_init"] * cfg["dt_us"]) % W.PHASE_ONE
+    o.g = orc.make_gait(gait2)
+    m_shift, v_shift = orc.warm_shift(o.P, o.g, 1, o.mean, o.var)
+    o.mean, o.var = m_shift, v_shift
+    J, q, th, margin, kap = o.rollout()
+    g.solve(shift=1, gait=gait2)
+    Jg, qg = g.read(S.BUF_COST), g.read(S.BUF_FREQ)
+    amb = check_frequencies(qg, q, margin)
+    check_costs(Jg, J, kap, skip=amb)
+    st, mo, _, _ = orc.mppi(J, th, cfg["lam"])
+    mg, vg = g.state()
+    tol = mppi_tolerance(J, th, kap, cfg["lam"], mo)
+    # the first tick's GPU/oracle means differ within their tolerance, and that
+    # difference enters the second tick's sampling mean linearly
+    assert np.all(np.abs(mg - mo) <= tol + 2 * MEAN_ATOL), np.max(np.abs(mg - mo) - tol)
+    np.testing.assert_allclose(vg, v_shift, rtol=1e-6)
+    g.close()
+
+
 @pytest.mark.parametrize("tile", [96, 160])
 def test_spline_full_horizon_odd_tiles(cuda, tile):
     # 100 steps, 4 knots: 160-sample tiles take 43.5 KB of dynamic shared memory,
