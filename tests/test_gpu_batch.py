@@ -135,6 +135,51 @@ def test_changing_controller_sets(inflight):
     b.close()
 
 
+@pytest.mark.parametrize("P", [3, 8])
+def test_spline_batch_equals_plain(P):
+    # a batch of spline controllers (one knot count per batch): uneven K and H, MPPI,
+    # elite and Naive, so the tick splits its rollout; two warm-started ticks
+    import torch
+    base = W.config("spline_k262144_h100")
+    specs = [dict(K=3000, H=25, method="mppi", compare_mppi=False), dict(K=1500, H=12, method="elite"),
+             dict(K=700, H=40, method="naive", compare_mppi=False), dict(K=4097, H=20, method="mppi"),
+             dict(K=257, H=8, method="elite", adaptive=False)]
+    mix = []
+    for i, sp in enumerate(specs):
+        c = dict(base)
+        c.update(P=P, dt_us=20000, sigma_init=5.0, tile=128, seed=200 + i, ctrl=i, **sp)
+        if c["method"] == "elite":
+            c["elite_count"] = W.elite_count(0.03, c["K"])
+        mix.append((c, W.problem(c)))
+    n = len(mix)
+    plain = [S.Controller(c) for c, _ in mix]
+    batched = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    b = S.Batch(n, sum(c.workspace_bytes() + 256 for c in batched))
+    b.set_mode(S.BATCH_GRID)
+    res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(2):
+        probs, plain_res = [], []
+        for i, (c, p) in enumerate(mix):
+            x0, xr, fe, ft = tens[i]
+            g = _gait(p, tick, c)
+            plain_res.append(plain[i].solve(x0, xr, g, fe, min(tick, 1)).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, min(tick, 1)))
+        b.solve(batched, probs, res)
+        torch.cuda.synchronize()
+        for i in range(n):
+            rp = S.parse_result(plain_res[i].cpu().numpy())
+            rb = S.parse_result(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy())
+            assert rb["status"] == rp["status"], i
+            np.testing.assert_array_equal(rb["u0"], rp["u0"])
+            assert rb["cost_min"] == rp["cost_min"] and rb["q_freq"] == rp["q_freq"]
+            mp, vp = _state(plain[i])
+            mb, vb = _state(batched[i])
+            np.testing.assert_array_equal(mb, mp)
+            np.testing.assert_array_equal(vb, vp)
+    b.close()
+
+
 def test_same_alone_and_in_the_mix():
     # one controller solved in a batch of one and inside a batch of eight
     import torch
