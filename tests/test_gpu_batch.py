@@ -135,8 +135,9 @@ def test_changing_controller_sets(inflight):
     b.close()
 
 
+@pytest.mark.parametrize("mode", [S.BATCH_GRID, S.BATCH_PERSISTENT])
 @pytest.mark.parametrize("P", [3, 8])
-def test_spline_batch_equals_plain(P):
+def test_spline_batch_equals_plain(P, mode):
     # a batch of spline controllers (one knot count per batch): uneven K and H, MPPI,
     # elite and Naive, so the tick splits its rollout; two warm-started ticks
     import torch
@@ -156,7 +157,7 @@ def test_spline_batch_equals_plain(P):
     batched = [S.Controller(c) for c, _ in mix]
     tens = [_tensors(p) for _, p in mix]
     b = S.Batch(n, sum(c.workspace_bytes() + 256 for c in batched))
-    b.set_mode(S.BATCH_GRID)
+    b.set_mode(mode)
     res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     for tick in range(2):
         probs, plain_res = [], []
