@@ -9,9 +9,9 @@
  * header, table or constant generator with the CUDA library; the two meet only
  * through seeded inputs made by the workload module.
  *
- * Everything is double precision except the one place where floating point
- * decides an integer (the quantised step frequency, Sec. IV-C), which is taken
- * in single precision, the precision of the GPU path.
+ * Everything is double precision, the quantised step frequency (Sec. IV-C)
+ * included; where its FP64 value lies within rounding distance of a boundary
+ * the oracle reports the margin, and the tests accept either neighbour there.
  *
  * Paper passages followed (section / equation / algorithm of the paper):
  *   sampling theta_k ~ N(theta, C), C diagonal ........ Alg. 1 (Sampling)
@@ -170,28 +170,20 @@ double orc_freq_normal(uint32_t seed, uint32_t ctrl, uint32_t k, uint64_t iter)
 }
 
 /* Step frequency of one sample (Sec. IV-C, frequency as decision variable theta_1):
- * f = clip(mu_f + sigma_f z, f_min, f_max), quantised to integer mHz.  This is the
- * one float-to-integer decision of the path, so it is taken in single precision
- * (the precision of the GPU path).  *margin receives |1000 f - nearest half-integer|
- * evaluated in double; a small margin marks a sample whose rounding is ambiguous
- * between the two precisions. */
+ * f = clip(mu_f + sigma_f z, f_min, f_max), quantised to the nearest integer mHz,
+ * q = floor(1000 f + 1/2), all in double precision.  *margin receives
+ * |1000 f - (floor(1000 f) + 1/2)|, the distance to the nearest rounding
+ * boundary: a small margin marks a sample whose rounding a lower-precision
+ * evaluation of the same formula may take the other way. */
 uint32_t orc_quantise_freq(double mu_f, double sigma_f, double z, double f_min, double f_max,
                            double* margin)
 {
-    float zf = (float)z;
-    float ff = fmaf((float)sigma_f, zf, (float)mu_f);
-    if (ff < (float)f_min) ff = (float)f_min;
-    if (ff > (float)f_max) ff = (float)f_max;
-    float t = 1000.0f * ff;
-    uint32_t q = (uint32_t)floorf(t + 0.5f);
-    if (margin) {
-        double fd = mu_f + sigma_f * z;
-        if (fd < f_min) fd = f_min;
-        if (fd > f_max) fd = f_max;
-        double td = 1000.0 * fd;
-        double frac = td - floor(td);
-        *margin = fabs(frac - 0.5);
-    }
+    double f = mu_f + sigma_f * z;
+    if (f < f_min) f = f_min;
+    if (f > f_max) f = f_max;
+    double t = 1000.0 * f;
+    uint32_t q = (uint32_t)floor(t + 0.5);
+    if (margin) *margin = fabs((t - floor(t)) - 0.5);
     return q;
 }
 

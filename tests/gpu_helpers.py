@@ -3,8 +3,13 @@ on the same seeded inputs and compare with the tolerances below.
 
 Tolerances (derived from the arithmetic):
   * integers (Philox words, quantised frequencies, contact flags): exact; a
-    frequency whose FP64 value lies within 2e-3 mHz of a rounding boundary may
-    round either way in single precision and is checked against both candidates.
+    frequency whose FP64 value lies within Q_MARGIN of a rounding boundary may
+    round either way on the GPU and is checked against both candidates.  The GPU
+    forms f = mu_f + sigma_f z in single precision from its own normal, which is
+    within 3e-6 + 2e-6 |z| of the FP64 one (|z| <= 5.77 for 24-bit uniforms): at
+    sigma_f <= 0.3 Hz that moves 1000 f by at most 4.4e-3 mHz, and the
+    single-precision roundings of the fused multiply-add, the product by 1000 and
+    the added half by at most 6e-4 mHz more; Q_MARGIN = 6e-3 mHz covers both.
   * normals: 3e-6 + 2e-6 |z| (hardware sine/cosine of the angle); force normals
     also the radius bound min(2 e / r, sqrt(2 e)) of the hardware base-2
     logarithm (ln error e at most 2^-22 ln 2 on [0.5, 1], 3 ulp below).
@@ -27,7 +32,7 @@ from paper_2403_11383_b300 import workloads as W
 
 MG = 21.0 * 9.81
 MEAN_ATOL = 1e-4 * MG
-Q_MARGIN = 2e-3
+Q_MARGIN = 6e-3
 KAPPA_STRICT = 1e-6
 KAPPA_GATED = 1e-5
 

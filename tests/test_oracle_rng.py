@@ -1,6 +1,7 @@
 """Pins of the oracle's random numbers: Philox4x32-10 against published known
 answers and statistical properties, Box-Muller against closed forms."""
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -133,18 +134,27 @@ def test_normal_counter_layout(orc):
 
 
 def test_quantise_freq(orc):
-    # q = round(1000 clip(mu + sigma z)) in mHz; clipping at both ends
+    # q = round(1000 clip(mu + sigma z)) in mHz (Sec. IV-C, FP64); clipping at both ends
     q, m = orc.quantise_freq(2.0, 0.3, 0.0, 1.0, 4.0)
     assert q == 2000 and m == pytest.approx(0.5)
     q, _ = orc.quantise_freq(2.0, 0.3, -100.0, 1.0, 4.0)
     assert q == 1000
     q, _ = orc.quantise_freq(2.0, 0.3, 100.0, 1.0, 4.0)
     assert q == 4000
+    # against exact rational arithmetic on the same double inputs: the FP64 value
+    # rounds the same way except within ~1e-9 mHz of a half-integer, and the
+    # margin is the distance to that boundary
     rng = np.random.default_rng(0)
-    for z in rng.normal(size=2000):
-        q, margin = orc.quantise_freq(2.0, 0.3, float(z), 1.0, 4.0)
-        exact = 1000.0 * min(4.0, max(1.0, 2.0 + 0.3 * z))
-        if margin > 1e-3:
-            assert q == math.floor(exact + 0.5)
-        else:
-            assert q in (math.floor(exact), math.floor(exact) + 1)
+    for mu, sig in ((2.0, 0.3), (1.7351, 0.0731), (3.9, 0.5)):
+        for z in rng.normal(size=700):
+            q, margin = orc.quantise_freq(mu, sig, float(z), 1.0, 4.0)
+            f = Fraction(mu) + Fraction(sig) * Fraction(float(z))
+            f = min(Fraction(4), max(Fraction(1), f))
+            t = 1000 * f
+            exact_q = math.floor(t + Fraction(1, 2))
+            exact_m = abs((t - math.floor(t)) - Fraction(1, 2))
+            assert margin == pytest.approx(float(exact_m), abs=1e-9)
+            if exact_m > 1e-9:
+                assert q == exact_q
+            else:
+                assert q in (exact_q - 1, exact_q)
