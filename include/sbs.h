@@ -264,15 +264,21 @@ int sbs_set_state(sbs_handle* h, const void* buf, size_t bytes, void* stream);
  *   prob       device pointers only (host_memory = 0); shift is the warm-start
  *              shift applied to state_in.
  *   state_in   device [mean (D) | variance (D)] of the distribution to sample;
- *              D = 12 H (+1 when adaptive).  Use sbs_reset / sbs_read of a
- *              handle, or your own initial values, for the first call.
+ *              D = 12 H (+1 when adaptive), as sbs_dim reports for a handle of
+ *              the same cfg (a discrete frequency set, which would multiply the
+ *              12 H, needs the Naive method and is refused here).  Use
+ *              sbs_reset / sbs_read of a handle, or your own initial values, for
+ *              the first call.
  *   state_out  device [mean | variance] written with the updated distribution;
  *              must not alias state_in.
  *   iter       the Philox iteration counter of this solve.
  *   result     device sbs_result.
- * Returns SBS_ERR_BUDGET when the solve's scratch exceeds the array.  The first
- * call on a device looks the array's device address up (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one
+ * Returns SBS_ERR_BUDGET when the solve's scratch exceeds the array, and
+ * SBS_ERR_INVALID_ARG when `stream` is capturing (the parameter block is copied
+ * from memory that does not outlive the call).  The first call on a device, and
+ * the first after a device reset, looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ * calls share the one
  * array and it keeps the previous call's contents (the completion counters are
  * cleared by every call): calls whose work overlaps on the GPU - on different
  * streams, or from different threads - race and corrupt each other. */

@@ -27,25 +27,61 @@ namespace {
 
 constexpr int kMaxDevices = 128;
 std::mutex g_mutex;
-void* g_scratch[kMaxDevices] = {};  // device address of the array, per device
+struct Cached {
+    unsigned long long ctx_id;  // unique id of the context the address belongs to
+    void* addr;                 // device address of the array in that context
+};
+Cached g_scratch[kMaxDevices] = {};
+
+// Unique id of the current context (the driver's cuCtxGetCurrent and cuCtxGetId,
+// found once through the runtime, so the library needs no link to the driver
+// library); 0 when there is none.  A device reset ends the context that held the
+// array, and ids are never reused, so the next call sees a new id and looks the
+// address up again instead of using a stale one.
+unsigned long long current_context_id()
+{
+    typedef int (*CtxGetCurrent)(void**);
+    typedef int (*CtxGetId)(void*, unsigned long long*);
+    static void* fns[2] = {nullptr, nullptr};
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char* names[2] = {"cuCtxGetCurrent", "cuCtxGetId"};
+        for (int i = 0; i < 2; ++i) {
+            void* f = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion(names[i], &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                fns[i] = f;
+            cudaGetLastError();
+        }
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!fns[0] || !fns[1] || ((CtxGetCurrent)fns[0])(&ctx) != 0 || !ctx) return 0;
+    if (((CtxGetId)fns[1])(ctx, &id) != 0) return 0;
+    return id;
+}
 
 // Device address of the scratch array on the current device (looked up once per
-// device, with that device current).
+// device and context, with that device current).
 int scratch_address(void** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SBS_ERR_CUDA;
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
+    Cached& c = g_scratch[dev];
+    if (!c.addr || !id || c.ctx_id != id) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return SBS_ERR_CUDA;
         }
-        g_scratch[dev] = p;
+        c.addr = p;
+        c.ctx_id = current_context_id();  // the lookup made the device's context current
     }
-    *out = g_scratch[dev];
+    *out = c.addr;
     return SBS_OK;
 }
 
@@ -88,6 +124,14 @@ extern "C" int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* p
     P.Ssp = nullptr;
 
     cudaStream_t s = (cudaStream_t)stream;
+    // The parameter block is copied from this call's stack: a captured copy would
+    // read a dead frame when replayed, so the call refuses a capturing stream.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return SBS_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return SBS_ERR_INVALID_ARG;
     // the parameter block (from host memory) and zeroed counters, ahead of the kernel
     if (cudaMemcpyAsync(base + o_params, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return SBS_ERR_CUDA;

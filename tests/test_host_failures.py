@@ -89,7 +89,7 @@ def test_bench_reference_arm_two_ranks_gloo():
     assert rec["cpu_baseline"]["kind"] == "oracle"
 
 
-def test_bench_rank_helpers_gloo():
+def test_bench_rank_helpers_gloo(tmp_path):
     # the max-over-ranks reduction bench.py uses for its timing, on two gloo ranks
     code = r'''
 import os, sys
@@ -104,15 +104,10 @@ assert v == 2.0, v
 print("ok", r)
 dist.destroy_process_group()
 '''
-    path = os.path.join(ROOT, "tests", "_rank_probe_tmp.py")
-    try:
-        with open(path, "w") as f:
-            f.write(code)
-        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
-               "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), path, ROOT]
-        out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
-        assert out.returncode == 0, out.stderr[-2000:]
-        assert out.stdout.count("ok") == 2
-    finally:
-        if os.path.exists(path):
-            os.remove(path)
+    path = tmp_path / "rank_probe.py"
+    path.write_text(code)
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(path), ROOT]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.count("ok") == 2
