@@ -335,6 +335,53 @@ def test_warm_start_two_ticks(cuda):
     g.close()
 
 
+def test_spline_full_size_update(cuda):
+    # the spline workload at full size (K = 262 144, H = 100, 4 knots, adaptive
+    # frequency): the staged update against FP64 on the oracle's samples of all
+    # K draws, from the GPU's own costs and frequencies.  Elite (Alg. 1 Update):
+    # the 2 622 elites are the first K_e of the GPU's (cost, index) order, and the
+    # refit is their FP64 mean and floored biased variance.  MPPI on the same
+    # samples (Alg. 5): the FP64 weighted mean of the GPU's costs, and twice at a
+    # temperature where the effective sample size is intermediate.
+    cfg = W.config("spline_k262144_h100")
+    prob = W.problem(cfg)
+    g, o = CudaRun(cfg, prob), OracleRun(cfg, prob)
+    g.solve()
+    Jg = g.read(S.BUF_COST).astype(np.float64)
+    qg, eg = g.read(S.BUF_FREQ), g.read(S.BUF_ELITE)
+    _, _, th, _, _ = o.rollout(kappa=False, nthreads=orc.max_threads())
+    th[:, -1] = qg / 1000.0
+    Ke = cfg["elite_count"]
+    np.testing.assert_array_equal(eg, np.sort(np.lexsort((np.arange(cfg["K"]), Jg))[:Ke]))
+    sel = th[eg]
+    mg, vg = g.state()
+    np.testing.assert_allclose(mg, sel.mean(axis=0), atol=MEAN_ATOL, rtol=1e-5)
+    floor = np.r_[np.full(th.shape[1] - 1, cfg["sigma_min"] ** 2), cfg["sigma_f_min"] ** 2]
+    np.testing.assert_allclose(vg, np.maximum(sel.var(axis=0), floor), rtol=2e-4, atol=1e-6)
+    mm = g.read(S.BUF_MPPI_MEAN)
+    _, mo, _, _ = orc.mppi(Jg, th, cfg["lam"])
+    assert np.all(np.abs(mm - mo) <= MEAN_ATOL), float(np.max(np.abs(mm - mo)))
+    g.close()
+    # intermediate weights at full size: lambda from the GPU's costs of this solve
+    # (the rollout does not depend on lambda, so the costs repeat bit for bit)
+    fin = np.isfinite(Jg)
+    spread = np.sort(Jg[fin])
+    for lam in (spread[100] - spread[0], spread[3000] - spread[0]):
+        c2 = dict(cfg, lam=float(lam), method="mppi", compare_mppi=False)
+        g2 = CudaRun(c2, prob)
+        r2 = g2.solve()
+        J2 = g2.read(S.BUF_COST).astype(np.float64)
+        np.testing.assert_array_equal(J2, Jg)
+        m2, _ = g2.state()
+        _, mo2, ess2, _ = orc.mppi(J2, th, float(lam))
+        print(f"lambda {lam:.4g}: ESS oracle {ess2:.1f} gpu {r2['ess']:.1f}")
+        assert 10.0 <= ess2 <= cfg["K"] / 10.0
+        assert np.all(np.abs(m2 - mo2) <= MEAN_ATOL), float(np.max(np.abs(m2 - mo2)))
+        assert r2["ess"] == pytest.approx(ess2, rel=1e-4)
+        assert r2["n_finite"] == int(fin.sum())
+        g2.close()
+
+
 def test_spline_full_size_sampled(cuda):
     # the spline workload at full size (K=262144, H=100, 4 knots): sampled costs
     cfg = W.config("spline_k262144_h100")
