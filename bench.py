@@ -9,9 +9,12 @@ cost, update of all 256 controllers (warm-started from the previous tick).
 
 Metric: rollout sample-steps per second (sum of K*H over the controllers
 solved, per second of tick time); also reported: solves/s, tick latency
-p50/p99, the same tick as plain one-launch-set-per-controller solves, the
-end-to-end number with host inputs/outputs, the dominant kernel's roofline and
-the FP64 oracle's throughput on the host cores.
+p50/p99 (over at least 400 ticks), the same tick as plain
+one-launch-set-per-controller solves, the end-to-end number through the C ABI
+from host memory (sbs_batch_solve_host), the dominant kernel's roofline (its
+algorithmic FLOPs from the FP64 oracle's counting build), the FP64 oracle's
+throughput on the host cores, and each workload's per-output errors against
+the oracle (`parity`, computed after the timed regions).
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Multi-GPU: one process per GPU (torchrun); each rank runs its own 256
@@ -33,12 +36,50 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "batched_256_uneven_K256-16384_H10-50"
 
-# Algorithmic FP32 work per sample-step of the per-step policy (counted from the
-# kernel's formulation, FMA = 2): Box-Muller arithmetic 36, sampling 24, stage
-# cost 128, SRBD Euler step 201; MPPI partial sums add 24.  Transcendentals
-# (26 per sample-step) and the integer Philox rounds are not counted.
-FLOPS_ROLLOUT = 36 + 24 + 128 + 201
-FLOPS_MPPI_PARTIAL = 24
+# Algorithmic work of a rollout: the FP64 oracle's operation counts (its counting
+# build, oracle/count_flops.py) per sample as a function of the horizon H, the
+# stance (leg, step) pairs S, the knots P and a sampled frequency, and of the MPPI
+# update; FLOP = add + mul + div + sqrt, transcendentals and the integer Philox
+# rounds apart.  Read from profiles/oracle_flop_model.json (data, not code).
+PHASE_ONE = 1_000_000_000
+
+
+def flop_model():
+    with open(os.path.join(ROOT, "profiles", "oracle_flop_model.json")) as f:
+        return json.load(f)
+
+
+def stance_pairs(gait, q_mhz, dt_us, H):
+    """Stance (leg, step) pairs of each sample's horizon for step frequencies q
+    (mHz, array): the integer contact schedule of Sec. IV-C."""
+    q = np.atleast_1d(np.asarray(q_mhz, dtype=np.int64))
+    j = np.arange(H, dtype=np.int64)
+    S = np.zeros(q.size, dtype=np.int64)
+    for off in gait["offset"]:
+        ph = (int(gait["phase0"]) + int(off) + j[None, :] * q[:, None] * int(dt_us)) % PHASE_ONE
+        S += (ph < int(gait["duty"])).sum(axis=1)
+    return S
+
+
+def controller_flops(model, cfg, gait, q=None, n_finite=None):
+    """Algorithmic FLOPs of one iteration of a controller: (every sample's
+    rollout, the MPPI weighted mean over its samples).  q: the samples' step
+    frequencies (mHz) when sampled, else the nominal one; n_finite: samples of
+    finite cost (default all).  The friction-penalty terms the model leaves out
+    (2 FLOP each when active) make this a lower bound."""
+    P, H, K = cfg.get("P", 0), cfg["H"], cfg["K"]
+    ad = 1 if cfg.get("adaptive") else 0
+    fam = model["spline" if P > 0 else "per_step"]["coef"]["flop"]
+    S = stance_pairs(gait, cfg["q_init"] if q is None else q, cfg["dt_us"], H)
+    S_tot = int(S.sum()) * (K if q is None else 1)
+    roll = K * (fam[0] + fam[1] * H + fam[3] * ad) + fam[2] * S_tot
+    if P > 0:
+        roll += K * (fam[4] * P + fam[5] * H * P)
+    m = model["mppi_flop"]["coef"]
+    D = 12 * (P if P > 0 else H) + ad
+    kf = K if n_finite is None else int(n_finite)
+    mppi = m[0] + m[1] * K + m[2] * kf + m[3] * K * D + m[4] * D
+    return int(roll), int(mppi)
 
 
 def parse():
@@ -50,7 +91,8 @@ def parse():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--tile", type=int, default=0,
                     help="samples per block of the batched controllers; 0: timed at 128 and 256, fastest kept")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and the parity record")
+    ap.add_argument("--no-parity", action="store_true", help="skip the per-output FP64 error record")
     ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
     ap.add_argument("--serving-seconds", type=float, default=3.0)
     ap.add_argument("--workload", default="batched",
@@ -222,25 +264,113 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-# ----------------------------------------------------------------------------- single controller
+# ----------------------------------------------------------------------------- parity record
 
-def flops_per_sample_step(cfg):
-    """Algorithmic FP32 work per sample-step of one controller (FMA = 2).
-    Per-step policy: see FLOPS_ROLLOUT.  Spline policy: per step the basis
-    evaluation (2 P FLOP per force) replaces Box-Muller and sampling, and the
-    knot noise (Box-Muller 6 FLOP per pair, 12 P normals; sampling 2 FLOP per
-    knot value) is counted once per sample, i.e. divided by H."""
-    P, H = cfg.get("P", 0), cfg["H"]
-    base = 128 + 201  # stage cost + SRBD Euler step
-    if P > 0:
-        per = base + 12 * 2 * P + (6 * 6 * P + 2 * 12 * P) / H
-        part = (2 * 12 * P) / H  # MPPI partials from the knot deviations
+MEAN_ATOL = 1e-4 * 21.0 * 9.81  # 1e-4 m|g|: the updated controls' tolerance
+Q_MARGIN = 6e-3  # mHz: a frequency this close to a rounding boundary may round either way
+
+
+def parity_one(cfg, prob, nthreads, n_cost=4096, seed=0):
+    """Errors of one GPU solve (iteration 0, from the initial distribution,
+    through sbs_solve) against the FP64 oracle on the same seeded inputs.
+    Costs: relative error on the samples whose conditioning estimate kappa is at
+    most 1e-5 (the gate of the parity tests; a random subset of n_cost samples
+    when K is larger).  Update: staged, i.e. the FP64 update formed from the
+    GPU's own costs and frequencies on the oracle's samples; also end to end (the
+    oracle's own costs), reported only."""
+    import torch
+
+    import oracle as orc
+    from paper_2403_11383_b300 import sbs as S
+    cfg = dict(cfg, iterations=1)
+    ctl = S.Controller(cfg)
+    dv = lambda a: torch.tensor(np.float32(a), device="cuda")
+    feet = dv(prob["feet"]) if "feet" in prob else None
+    res = ctl.solve(dv(prob["x0"]), dv(prob["xref"]), prob["gait"], dv(prob["f_ext"]), 0, feet=feet)
+    torch.cuda.synchronize()
+    r = S.parse_result(res.cpu().numpy())
+    Jg = ctl.read(S.BUF_COST).cpu().numpy().astype(np.float64)
+    qg = ctl.read(S.BUF_FREQ).cpu().numpy()
+    mg, vg = ctl.read(S.BUF_MEAN).cpu().numpy(), ctl.read(S.BUF_VAR).cpu().numpy()
+    eg = ctl.read(S.BUF_ELITE).cpu().numpy() if cfg["method"] == "elite" else None
+    mm = ctl.read(S.BUF_MPPI_MEAN).cpu().numpy() if cfg.get("compare_mppi") else None
+    ctl.close()
+    P, g = orc.make_params(cfg), orc.make_gait(prob["gait"])
+    f64 = lambda a: np.float64(np.float32(a))
+    ft = f64(prob["feet"]) if "feet" in prob else None
+    x0, xr, fe = f64(prob["x0"]), f64(prob["xref"]), f64(prob["f_ext"])
+    m0, v0 = orc.init_dist(P, g)
+    J, q, th, margin = orc.rollout(P, g, x0, xr, fe, m0, v0, 0, want_theta=True, nthreads=nthreads, feet=ft)
+    K = cfg["K"]
+    idx = np.arange(K) if K <= n_cost else np.sort(np.random.default_rng(seed).choice(K, n_cost, replace=False))
+    if idx.size == K:
+        kap = orc.cost_condition_all(P, g, x0, xr, fe, m0, v0, 0, nthreads=nthreads, feet=ft)
     else:
-        per = FLOPS_ROLLOUT
-        part = FLOPS_MPPI_PARTIAL
-    mppi = cfg["method"] == "mppi" or cfg.get("compare_mppi")
-    return per + (part if mppi else 0.0)
+        kap = np.array([orc.cost_condition(P, g, x0, xr, fe, m0, v0, 0, int(k), feet=ft)[0] for k in idx])
+    Jo, Jgi = J[idx], Jg[idx]
+    fin_o = np.isfinite(Jo) & (Jo < 3e38)
+    amb = margin[idx] < Q_MARGIN
+    gated = fin_o & ~amb & (kap <= 1e-5)
+    rel = np.abs(Jgi - Jo) / np.maximum(np.abs(Jo), 1e-30)
+    out = {"K": K, "H": cfg["H"], "P": cfg.get("P", 0), "method": cfg["method"], "adaptive": bool(cfg.get("adaptive")),
+           "samples_checked": int(idx.size), "finite_frac_oracle": float(fin_o.mean()),
+           "finite_frac_gpu": float(np.isfinite(Jg).mean()), "gated": int(gated.sum()),
+           "gated_frac": float(gated.mean()),
+           "cost_rel_err_gated": {"max": float(rel[gated].max()) if gated.any() else None,
+                                  "p99": float(np.quantile(rel[gated], 0.99)) if gated.any() else None},
+           "freq_exact_frac": float(np.mean(qg[idx] == q[idx])) if cfg.get("adaptive") else None}
+    thg = th.copy()
+    if cfg.get("adaptive"):
+        thg[:, -1] = qg / 1000.0
+    fin_g = np.isfinite(Jg)
+    if cfg["method"] == "mppi" and fin_g.any():
+        _, mo, ess_o, _ = orc.mppi(Jg, thg, cfg["lam"])
+        out["staged"] = {"mean_abs_err": float(np.abs(mg - mo).max()),
+                         "u0_abs_err": float(np.abs(np.asarray(r["u0"]) - orc.first_control(P, g, mo)).max()),
+                         "ess_rel_err": float(abs(r["ess"] - ess_o) / ess_o), "ess": float(ess_o)}
+        _, me, _, _ = orc.mppi(J, th, cfg["lam"])
+        out["end_to_end"] = {"mean_abs_err": float(np.abs(mg - me).max()),
+                             "u0_abs_err": float(np.abs(np.asarray(r["u0"]) - orc.first_control(P, g, me)).max())}
+    elif cfg["method"] == "elite" and fin_g.any():
+        Ke = cfg["elite_count"]
+        order = np.lexsort((np.arange(K), np.where(fin_g, Jg, np.inf)))
+        sel = thg[eg]
+        floor = np.full(thg.shape[1], cfg["sigma_min"] ** 2)
+        if cfg.get("adaptive"):
+            floor[-1] = cfg["sigma_f_min"] ** 2
+        vref = np.maximum(sel.var(axis=0), floor)
+        out["staged"] = {"elite_set_is_first_Ke_of_gpu_costs": bool(np.array_equal(eg, np.sort(order[:Ke]))),
+                         "mean_abs_err": float(np.abs(mg - sel.mean(axis=0)).max()),
+                         "var_rel_err": float(np.max(np.abs(vg - vref) / vref))}
+        eo = orc.elite_select(J, Ke)
+        out["end_to_end"] = {"elite_overlap_frac": len(set(eo.tolist()) & set(eg.tolist())) / Ke,
+                             "mean_abs_err": float(np.abs(mg - th[eo].mean(axis=0)).max())}
+        if mm is not None:
+            _, mo, _, _ = orc.mppi(Jg, thg, cfg["lam"])
+            out["staged"]["compare_mppi_mean_abs_err"] = float(np.abs(mm - mo).max())
+    return out
 
+
+def parity_record(mix, tile, nthreads):
+    """Per-output FP64 errors of the workloads (outside any timed region)."""
+    from paper_2403_11383_b300 import workloads as W
+    t0 = time.perf_counter()
+    rec = {"tolerances": {"cost_rel": "1e-4 for kappa <= 1e-6, max(1e-4, 100 kappa) up to kappa = 1e-5, "
+                                      "samples above reported only",
+                          "mean_abs": MEAN_ATOL, "ess_rel": 1e-4},
+           "kind": "GPU iteration-0 solves (sbs_solve; a batched tick gives the same bits) against the FP64 "
+                   "oracle on the same seeded inputs"}
+    rec["batched_mix_first8"] = [parity_one(dict(c, tile=tile), p, nthreads) for c, p in mix[:8]]
+    for name in ("plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100"):
+        cfg = W.config(name)
+        rec[name] = parity_one(cfg, W.problem(cfg), nthreads, n_cost=512 if cfg["K"] > 100000 else 8192)
+    smix, _ = W.serving_mix(2048, seed=3)
+    rec["serving_mix_first4"] = [parity_one(c, p, nthreads) for c, p in smix[:4]]
+    rec["seconds"] = time.perf_counter() - t0
+    return rec
+
+
+# ----------------------------------------------------------------------------- single controller
 
 def run_single(args, world, rank, local):
     """Timed solves of one controller of a named workload (warm-started ticks)."""
@@ -276,7 +406,14 @@ def run_single(args, world, rank, local):
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     ss = cfg["K"] * cfg["H"] * cfg["iterations"]
-    fl = flops_per_sample_step(cfg) * ss
+    # algorithmic FLOPs of a solve from the oracle's counts: every iteration's
+    # rollouts (sampled frequencies: the last solve's), and the MPPI mean of an
+    # MPPI solve, or of the first iteration when the elite solve compares MPPI
+    rr = S.parse_result(res.cpu().numpy())
+    qs = ctl.read(S.BUF_FREQ).cpu().numpy() if cfg.get("adaptive") else None
+    roll_fl, mppi_fl = controller_flops(flop_model(), cfg, prob["gait"], qs, rr["n_finite"])
+    n_mppi = cfg["iterations"] if cfg["method"] == "mppi" else (1 if cfg.get("compare_mppi") else 0)
+    fl = cfg["iterations"] * roll_fl + n_mppi * mppi_fl
     # the solve is rollout + (select + refit) launches; the roofline uses the whole solve
     achieved = fl / (ms * 1e-3) / 1e12
     peak = S.fp32_peak() / 1e12
@@ -303,7 +440,9 @@ def run_single(args, world, rank, local):
                 "roofline": {"kernel": "whole solve", "bound": "alu", "achieved": achieved, "peak": peak,
                              "unit": "TFLOP/s", "frac": achieved / peak,
                              "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
-                             "flops_per_sample_step": flops_per_sample_step(cfg), "traffic": None},
+                             "flops_per_solve": fl, "flops_per_sample_step": fl / ss,
+                             "flops_source": "FP64 oracle counting build (profiles/oracle_flop_model.json)",
+                             "traffic": None},
                 "e2e": {"value": world * ss / e2e_s, "unit": "sample-steps/s",
                         "h2d_bytes_per_step": int(4 * (12 + 3 + 12 * cfg["H"] + (8 if "feet" in prob else 0))),
                         "d2h_bytes_per_step": S.RESULT_BYTES},
@@ -399,7 +538,8 @@ def main():
 
     # ---- tick latency distribution (device time of each tick)
     lat = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_lat = max(args.steps, 400)  # enough ticks for a 99th percentile
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
     for a, b in ev:
         a.record(stream)
         tick()
@@ -418,7 +558,15 @@ def main():
     st = np.array(st)
     roll_ms = float(st[:, 0].mean())
     sel_ms, ref_ms = float(st[:, 1].mean()), float(st[:, 2].mean())
-    flops_launch = ss_tick * FLOPS_ROLLOUT + mppi_ss * FLOPS_MPPI_PARTIAL
+    # algorithmic FLOPs of the rollout launch (every controller's samples, and the
+    # MPPI controllers' weighted means formed in the same launch), from the FP64
+    # oracle's operation counts; finite counts from the last profiled tick
+    model = flop_model()
+    last = [S.parse_result(results[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy()) for i in range(n)]
+    flops_launch = 0
+    for i, ((c, _), r) in enumerate(zip(mix, last)):
+        roll_fl, mppi_fl = controller_flops(model, c, gaits[i], None, r["n_finite"])
+        flops_launch += roll_fl + (mppi_fl if c["method"] == "mppi" else 0)
     achieved = flops_launch / (roll_ms * 1e-3) / 1e12
     # algorithmic bytes of the elite update: the selection reads each cost once and
     # writes the elite indices; the refit reads each elite's deviation row (48 B)
@@ -448,38 +596,27 @@ def main():
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / plain_ticks
 
-    # ---- end to end: inputs from pinned host memory, results back to the host
-    h_in = torch.empty(sum(12 + x.numel() + 3 for x in xref), dtype=torch.float32).pin_memory()
-    off = 0
-    views = []
-    for i in range(n):
-        nn_ = 12 + xref[i].numel() + 3
-        h_in[off:off + 12] = x0[i].cpu()
-        h_in[off + 12:off + 12 + xref[i].numel()] = xref[i].cpu().ravel()
-        h_in[off + 12 + xref[i].numel():off + nn_] = fext[i].cpu()
-        views.append((off, nn_))
-        off += nn_
-    d_in = torch.empty_like(h_in, device=dev)
-    eprobs = []
-    for i, (o, nn_) in enumerate(views):
-        xi = d_in[o:o + 12]
-        ri = d_in[o + 12:o + 12 + xref[i].numel()]
-        fi = d_in[o + 12 + xref[i].numel():o + nn_]
-        eprobs.append(ctls[i].problem(xi, ri, gaits[i], fi, 1))
-    epacked = S.Packed(ctls, eprobs)
-    h_out = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    # ---- end to end through the C ABI from host memory: sbs_batch_solve_host
+    # gathers every controller's inputs into its pinned staging buffer, copies
+    # them in one transfer, runs the tick and returns with the results on the host
+    h_x0 = [np.ascontiguousarray(np.float32(p["x0"])) for _, p in mix]
+    h_xr = [np.ascontiguousarray(np.float32(p["xref"])) for _, p in mix]
+    h_fe = [np.ascontiguousarray(np.float32(p["f_ext"])) for _, p in mix]
+    hpacked = S.Packed(ctls, [ctls[i].problem(h_x0[i], h_xr[i], gaits[i], h_fe[i], 1, host=True)
+                              for i in range(n)])
+    h_out = np.zeros(n * S.RESULT_BYTES, dtype=np.uint8)
+    for _ in range(3):
+        batch.solve_host(hpacked, h_out)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        d_in.copy_(h_in, non_blocking=True)
-        batch.solve_packed(epacked, results)
-        h_out.copy_(results, non_blocking=True)
-        torch.cuda.synchronize()
+        batch.solve_host(hpacked, h_out)
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_s = max_over_ranks(e2e_s, world, dev)
     e2e_value = world * ss_tick / e2e_s
-    status = [S.parse_result(h_out[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].numpy())["status"] for i in range(n)]
+    h2d_bytes = sum(4 * (a.size + b.size + c.size) for a, b, c in zip(h_x0, h_xr, h_fe))
+    status = [S.parse_result(h_out[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES])["status"] for i in range(n)]
 
     # ---- served: 2048 closed-loop robots, continuous batching vs plain solves
     served = None
@@ -490,14 +627,17 @@ def main():
                   "plain": serving.run(plain=True, duration=args.serving_seconds, warmup=1.0, robots=robots)}
         del robots
 
-    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0)
-    cpu = None
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0), and the
+    # per-output errors of the GPU path against it
+    cpu = parity = None
     if rank == 0 and not args.no_cpu:
         nthreads = os.cpu_count() or 1
         rate, ninst, ss, t_ = oracle_rate(W.batch_config(args.instances), 15.0, nthreads)
         cpu = {"value": rate, "unit": "sample-steps/s", "cores": nthreads, "kind": "oracle",
                "sample": f"first {ninst} controllers of the mix, one FP64 solve each ({ss} sample-steps, "
                          f"{t_:.1f} s)"}
+        if not args.no_parity:
+            parity = parity_record(W.batch_config(args.instances), tile, nthreads)
 
     peaks = measured_peaks()
     traffic_ss = rollout_traffic()
@@ -512,7 +652,8 @@ def main():
                        "l2": "per-tick working set above L2 (sampled deviations "
                        f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
-            "latency_ms": {"p50": p50, "p99": p99, "kind": f"device time of one {len(mix)}-controller tick"},
+            "latency_ms": {"p50": p50, "p99": p99, "ticks": len(lat),
+                           "kind": f"device time of one {len(mix)}-controller tick"},
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
                       "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
@@ -534,7 +675,8 @@ def main():
                 "note": "algorithmic bytes of the elite controllers' selection and refit; both stages are "
                         "latency-bound chains of dependent loads, far from the HBM roof"},
             "e2e": {"value": e2e_value, "unit": "sample-steps/s",
-                    "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel())},
+                    "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(h_out.size),
+                    "call": "sbs_batch_solve_host (host inputs, one staged copy each way, synchronous)"},
             # rollout, selection and refit; a split tick (grid mode, MPPI and elite or
             # Naive controllers together) launches the rollout twice
             "gpu_launches": (4 if mode == "grid" and 0 < mppi_n < len(mix) else 3) * args.steps,
@@ -547,6 +689,8 @@ def main():
             line["served"] = served
         if cpu:
             line["cpu_baseline"] = cpu
+        if parity:
+            line["parity"] = parity
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -323,6 +323,19 @@ void sbs_batch_destroy(sbs_batch* b);
 int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                     sbs_result* results, void* stream);
 
+/* The same tick from host memory, end to end: probs[i] in host memory
+ * (host_memory = 1 for every controller) and `results` a host array of n
+ * sbs_result.  The library gathers every controller's x0, reference, f_ext and
+ * feet into one pinned staging buffer it owns, copies it to the device in one
+ * transfer on `stream`, runs the tick of sbs_batch_solve on those copies, copies
+ * the n results back in one transfer and waits for it: on return the results are
+ * in `results`.  It first waits for the batch's earlier ticks.  The staging
+ * buffers (pinned host and device, through the batch's allocator) grow on demand
+ * and are freed by sbs_batch_destroy; SBS_ERR_OOM if they cannot grow.  Errors
+ * as sbs_batch_solve. */
+int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                         sbs_result* results, void* stream);
+
 /* Launch mode of a batch.  SBS_BATCH_GRID (default): one block per item, the
  * hardware block scheduler dispatching items in order, heaviest controllers
  * first.  SBS_BATCH_PERSISTENT: as many blocks as fit on the GPU pull items from

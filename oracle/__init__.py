@@ -45,57 +45,75 @@ class Gait(C.Structure):
 
 
 _lib = None
+_lib_flops = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        d, u32, i32, u64, i64, vp = C.c_double, C.c_uint32, C.c_int32, C.c_uint64, C.c_int64, C.c_void_p
-        sig = {
-            "orc_philox4x32_10": (None, [vp, vp, vp]),
-            "orc_box_muller": (None, [u32, u32, vp, vp]),
-            "orc_box_muller21": (None, [u32, u32, vp, vp]),
-            "orc_uniforms21": (None, [vp, vp]),
-            "orc_normal": (d, [u32, u32, u32, u32, u64]),
-            "orc_freq_normal": (d, [u32, u32, u32, u64]),
-            "orc_quantise_freq": (u32, [d, d, d, d, d, vp]),
-            "orc_stance": (C.c_int, [vp, C.c_int, u32, u32, C.c_int]),
-            "orc_rotation": (None, [vp, vp]),
-            "orc_euler_rates": (None, [vp, vp, vp]),
-            "orc_srbd_deriv": (None, [vp, vp, vp, vp, vp]),
-            "orc_srbd_step": (None, [vp, vp, vp, vp, d, vp]),
-            "orc_srbd_deriv_feet": (None, [vp, vp, vp, vp, vp, vp]),
-            "orc_foothold": (None, [vp, vp, vp, u32, u32, C.c_int, vp]),
-            "orc_cone_project": (None, [d, vp, vp]),
-            "orc_stage_cost": (d, [vp, vp, vp, vp, vp]),
-            "orc_spline_basis": (None, [C.c_int, C.c_int, d, vp]),
-            "orc_spline_at": (d, [C.c_int, C.c_int, d, vp, d]),
-            "orc_dim": (C.c_int, [vp]),
-            "orc_sample_dim": (C.c_int, [vp]),
-            "orc_freq_bin": (C.c_int, [u32, u32, u32, u64, C.c_int]),
-            "orc_naive_sets": (C.c_int, [vp, vp, vp, vp, vp, vp]),
-            "orc_init_dist": (None, [vp, vp, vp, vp]),
-            "orc_warm_shift": (None, [vp, vp, C.c_int, vp, vp]),
-            "orc_rollout": (None, [vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, vp, C.c_int]),
-            "orc_rollout_sample": (d, [vp, vp, vp, vp, vp, vp, vp, vp, u64, u32, i64, vp]),
-            "orc_mppi": (C.c_int, [vp, vp, C.c_int, C.c_int, d, vp, vp, vp]),
-            "orc_elite_select": (None, [vp, C.c_int, C.c_int, vp]),
-            "orc_elite_refit": (None, [vp, C.c_int, vp, C.c_int, vp, vp, vp]),
-            "orc_first_control": (None, [vp, vp, vp, vp]),
-            "orc_solve": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int, u64, vp, vp, vp, vp, vp, vp, vp,
-                                    vp, C.c_int]),
-            "orc_max_threads": (C.c_int, []),
-            "orc_cost_condition": (d, [vp, vp, vp, vp, vp, vp, vp, vp, u64, u32, d, vp]),
-            "orc_cost_condition_all": (None, [vp, vp, vp, vp, vp, vp, vp, vp, u64, d, vp, C.c_int]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = _load(_build.build())
     return _lib
+
+
+def lib_flops():
+    """The FLOP-counting build of the same source (single-threaded)."""
+    global _lib_flops
+    if _lib_flops is None:
+        L = _load(_build.build_flops())
+        L.orc_flops_reset.restype = None
+        L.orc_flops_reset.argtypes = []
+        L.orc_flops_read.restype = None
+        L.orc_flops_read.argtypes = [C.c_void_p]
+        _lib_flops = L
+    return _lib_flops
+
+
+def _load(path):
+    L = C.CDLL(path)
+    d, u32, i32, u64, i64, vp = C.c_double, C.c_uint32, C.c_int32, C.c_uint64, C.c_int64, C.c_void_p
+    sig = {
+        "orc_philox4x32_10": (None, [vp, vp, vp]),
+        "orc_box_muller": (None, [u32, u32, vp, vp]),
+        "orc_box_muller21": (None, [u32, u32, vp, vp]),
+        "orc_uniforms21": (None, [vp, vp]),
+        "orc_normal": (d, [u32, u32, u32, u32, u64]),
+        "orc_freq_normal": (d, [u32, u32, u32, u64]),
+        "orc_normals6": (None, [u32, u32, u32, u32, u64, vp]),
+        "orc_quantise_freq": (u32, [d, d, d, d, d, vp]),
+        "orc_stance": (C.c_int, [vp, C.c_int, u32, u32, C.c_int]),
+        "orc_rotation": (None, [vp, vp]),
+        "orc_euler_rates": (None, [vp, vp, vp]),
+        "orc_srbd_deriv": (None, [vp, vp, vp, vp, vp]),
+        "orc_srbd_step": (None, [vp, vp, vp, vp, d, vp]),
+        "orc_srbd_deriv_feet": (None, [vp, vp, vp, vp, vp, vp]),
+        "orc_foothold": (None, [vp, vp, vp, u32, u32, C.c_int, vp]),
+        "orc_cone_project": (None, [d, vp, vp]),
+        "orc_stage_cost": (d, [vp, vp, vp, vp, vp]),
+        "orc_spline_basis": (None, [C.c_int, C.c_int, d, vp]),
+        "orc_spline_at": (d, [C.c_int, C.c_int, d, vp, d]),
+        "orc_dim": (C.c_int, [vp]),
+        "orc_sample_dim": (C.c_int, [vp]),
+        "orc_freq_bin": (C.c_int, [u32, u32, u32, u64, C.c_int]),
+        "orc_naive_sets": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "orc_init_dist": (None, [vp, vp, vp, vp]),
+        "orc_warm_shift": (None, [vp, vp, C.c_int, vp, vp]),
+        "orc_rollout": (None, [vp, vp, vp, vp, vp, vp, vp, vp, u64, vp, vp, vp, vp, C.c_int]),
+        "orc_rollout_sample": (d, [vp, vp, vp, vp, vp, vp, vp, vp, u64, u32, i64, vp]),
+        "orc_mppi": (C.c_int, [vp, vp, C.c_int, C.c_int, d, vp, vp, vp]),
+        "orc_elite_select": (None, [vp, C.c_int, C.c_int, vp]),
+        "orc_elite_refit": (None, [vp, C.c_int, vp, C.c_int, vp, vp, vp]),
+        "orc_first_control": (None, [vp, vp, vp, vp]),
+        "orc_solve": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int, u64, vp, vp, vp, vp, vp, vp, vp,
+                                vp, C.c_int]),
+        "orc_max_threads": (C.c_int, []),
+        "orc_cost_condition": (d, [vp, vp, vp, vp, vp, vp, vp, vp, u64, u32, d, vp]),
+        "orc_cost_condition_all": (None, [vp, vp, vp, vp, vp, vp, vp, vp, u64, d, vp, C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def _p(a):
@@ -183,6 +201,13 @@ def uniforms21(words):
 
 def normal(seed, ctrl, k, n, it):
     return lib().orc_normal(seed, ctrl, k, n, it)
+
+
+def normals6(seed, ctrl, k, d, it):
+    """The six force normals of draw d >= 1 (one Philox block, three Box-Muller pairs)."""
+    out = np.zeros(6)
+    lib().orc_normals6(seed, ctrl, k, d, it, _p(out))
+    return out
 
 
 def freq_normal(seed, ctrl, k, it):
@@ -443,3 +468,55 @@ def cost_condition_all(params, gait, x0, xref, f_ext, mean, var, it, eps=EPS_FP3
 
 def max_threads():
     return lib().orc_max_threads()
+
+
+# ----------------------------------------------------------------------------- FLOP counts
+
+FLOP_KEYS = ("add", "mul", "div", "sqrt", "fn")
+
+
+def _flops_read():
+    out = np.zeros(5, dtype=np.uint64)
+    lib_flops().orc_flops_read(_p(out))
+    d = dict(zip(FLOP_KEYS, (int(v) for v in out)))
+    d["flop"] = d["add"] + d["mul"] + d["div"] + d["sqrt"]
+    return d
+
+
+def count_rollout(params, gait, x0, xref, f_ext, mean, var, it, k=0, feet=None):
+    """Floating-point operations of sample k's rollout in the counting build:
+    sampling, policy, stage cost and dynamics (Alg. 1 Sampling, Alg. 2), with the
+    sample's cost.  The per-solve set-up that orc_rollout_sample also performs
+    (the spline basis, and one square root per distribution entry for its
+    standard deviation) is counted on its own and subtracted."""
+    L = lib_flops()
+    D = dim(params)
+    ft = _feet(params, feet)
+    x0, xref = _f64(x0, 12), _f64(xref, 12 * params.H)
+    fe = None if f_ext is None else _f64(f_ext, 3)
+    mean, var = _f64(mean, D), _f64(var, D)
+    theta = np.zeros(sample_dim(params))
+    L.orc_flops_reset()
+    J = L.orc_rollout_sample(C.byref(params), C.byref(gait), _p(x0), _p(xref), _p(fe), _p(ft), _p(mean), _p(var),
+                             it, k, -1, _p(theta))
+    total = _flops_read()
+    L.orc_flops_reset()
+    if params.P > 0:
+        L.orc_spline_basis(params.H, params.P, params.dt_us * 1e-6, _p(np.zeros(params.H * params.P)))
+    setup = _flops_read()
+    setup["sqrt"] += D
+    out = {key: total[key] - setup[key] for key in FLOP_KEYS}
+    out["flop"] = out["add"] + out["mul"] + out["div"] + out["sqrt"]
+    return out, float(J)
+
+
+def count_mppi(J, theta, lam):
+    """Floating-point operations of the MPPI update (Alg. 5) over K samples."""
+    L = lib_flops()
+    J, theta = _f64(J), _f64(theta)
+    K, D = theta.shape
+    mean = np.zeros(D)
+    ess, beta = C.c_double(), C.c_double()
+    L.orc_flops_reset()
+    L.orc_mppi(_p(J), _p(theta), K, D, lam, _p(mean), C.byref(ess), C.byref(beta))
+    return _flops_read()

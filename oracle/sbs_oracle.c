@@ -158,6 +158,19 @@ double orc_normal(uint32_t seed, uint32_t ctrl, uint32_t k, uint32_t n, uint64_t
     return (slot % 2u == 0) ? z0 : z1;
 }
 
+/* The six force normals of draw d >= 1 (normals 6(d-1) .. 6(d-1)+5): one Philox
+ * block, its six 21-bit integers and their three Box-Muller pairs, each pair
+ * giving two normals.  Entry s equals orc_normal(seed, ctrl, k, 6(d-1)+s, iter). */
+void orc_normals6(uint32_t seed, uint32_t ctrl, uint32_t k, uint32_t d, uint64_t iter, double out[6])
+{
+    uint32_t ctr[4] = {k, d, (uint32_t)iter, (uint32_t)(iter >> 32)};
+    uint32_t key[2] = {seed, ctrl};
+    uint32_t w[4], u[6];
+    orc_philox4x32_10(ctr, key, w);
+    orc_uniforms21(w, u);
+    for (int p = 0; p < 3; ++p) orc_box_muller21(u[2 * p], u[2 * p + 1], &out[2 * p], &out[2 * p + 1]);
+}
+
 double orc_freq_normal(uint32_t seed, uint32_t ctrl, uint32_t k, uint64_t iter)
 {
     uint32_t ctr[4] = {k, 0u, (uint32_t)iter, (uint32_t)(iter >> 32)};
@@ -564,8 +577,9 @@ void orc_warm_shift(const orc_params* P, const orc_gait* g, int shift, double* m
 
 /* ------------------------------------------------------------------------- */
 /* Rollout(theta_k) (Alg. 2), for sample k of iteration `iter`:               */
-/*   theta_k = mean + sqrt(var) * eps_k (Alg. 1 Sampling, diagonal C); with a  */
-/*         discrete frequency set the sample first draws its frequency, and  */
+/*   theta_k = mean + sd * eps_k, sd = sqrt(var) (Alg. 1 Sampling, diagonal C); */
+/*         with a discrete frequency set the sample first draws its          */
+/*         frequency, and                                                    */
 /*         mean, var are that frequency's Gaussian (Sec. V);                 */
 /*   u_j = pi(theta_k, t_j): contact flags from the sample's frequency and     */
 /*         forces from the per-step values or the spline, zeroed on swing legs */
@@ -585,7 +599,8 @@ typedef struct {
     const double* f_ext;
     const double* mean;
     const double* var;
-    const double* B; /* H x P spline basis, or NULL */
+    const double* sd; /* sqrt(var), taken once per solve: C^(1/2) of the diagonal C */
+    const double* B;  /* H x P spline basis, or NULL */
     uint64_t iter;
     const double* feet0; /* feet_mode 1: (x, y) of the 4 feet at t_0 */
 } rollout_ctx;
@@ -597,6 +612,30 @@ static double pert_sign(uint64_t key, uint64_t a, uint64_t b)
     uint64_t z = key * 0x9E3779B97F4A7C15ull + a * 0xBF58476D1CE4E5B9ull + b * 0x94D049BB133111EBull;
     z ^= z >> 31; z *= 0xD6E8D07A4F2C6F35ull; z ^= z >> 29;
     return (z & 1ull) ? 1.0 : -1.0;
+}
+
+/* The per-solve context: the spline basis and the standard deviations are
+ * formed once, not per sample. */
+static rollout_ctx make_ctx(const orc_params* P, const orc_gait* g, const double* x0, const double* xref,
+                            const double* f_ext, const double* feet, const double* mean, const double* var,
+                            uint64_t iter)
+{
+    double* B = NULL;
+    if (P->P > 0) {
+        B = (double*)malloc(sizeof(double) * P->H * P->P);
+        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
+    }
+    int D = orc_dim(P);
+    double* sd = (double*)malloc(sizeof(double) * D);
+    for (int d = 0; d < D; ++d) sd[d] = sqrt(var[d]);
+    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, sd, B, iter, feet};
+    return c;
+}
+
+static void free_ctx(rollout_ctx* c)
+{
+    free((void*)c->B);
+    free((void*)c->sd);
 }
 
 static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override, double* theta,
@@ -627,12 +666,15 @@ static double rollout_core(const rollout_ctx* c, uint32_t k, int64_t q_override,
         q = P->freq_set[blk];
     }
     const double* mean = c->mean + (size_t)blk * nf;
-    const double* var = c->var + (size_t)blk * nf;
-    for (int n = 0; n < nf; ++n)
-        theta[n] = mean[n] + sqrt(var[n]) * orc_normal(P->seed, P->ctrl, k, (uint32_t)n, c->iter);
+    const double* sd = c->sd + (size_t)blk * nf;
+    for (int d = 0; d < nf / 6; ++d) { /* nf is a multiple of 12: whole draws */
+        double eps[6];
+        orc_normals6(P->seed, P->ctrl, k, 1u + (uint32_t)d, c->iter, eps);
+        for (int s = 0; s < 6; ++s) theta[6 * d + s] = mean[6 * d + s] + sd[6 * d + s] * eps[s];
+    }
     if (P->adaptive) {
         double z = orc_freq_normal(P->seed, P->ctrl, k, c->iter);
-        q = orc_quantise_freq(c->mean[nf], sqrt(c->var[nf]), z, P->f_min, P->f_max, &margin);
+        q = orc_quantise_freq(c->mean[nf], c->sd[nf], z, P->f_min, P->f_max, &margin);
     }
     if (q_override >= 0) q = (uint32_t)q_override;
     if (P->adaptive) theta[nf] = q / 1000.0;
@@ -701,12 +743,7 @@ void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const
                  double* J, uint32_t* q, double* theta, double* margin, int nthreads)
 {
     int D = orc_sample_dim(P);
-    double* B = NULL;
-    if (P->P > 0) {
-        B = (double*)malloc(sizeof(double) * P->H * P->P);
-        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
-    }
-    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter, feet};
+    rollout_ctx c = make_ctx(P, g, x0, xref, f_ext, feet, mean, var, iter);
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
     for (int k = 0; k < P->K; ++k) {
@@ -718,7 +755,7 @@ void orc_rollout(const orc_params* P, const orc_gait* g, const double* x0, const
         if (margin) margin[k] = mk;
         if (!theta) free(th);
     }
-    free(B);
+    free_ctx(&c);
 }
 
 /* One sample with an optional forced frequency (q_override < 0: its own). */
@@ -727,14 +764,9 @@ double orc_rollout_sample(const orc_params* P, const orc_gait* g, const double* 
                           const double* var, uint64_t iter, uint32_t k, int64_t q_override,
                           double* theta)
 {
-    double* B = NULL;
-    if (P->P > 0) {
-        B = (double*)malloc(sizeof(double) * P->H * P->P);
-        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
-    }
-    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter, feet};
+    rollout_ctx c = make_ctx(P, g, x0, xref, f_ext, feet, mean, var, iter);
     double J = rollout_one(&c, k, q_override, theta, NULL, NULL);
-    free(B);
+    free_ctx(&c);
     return J;
 }
 
@@ -748,12 +780,7 @@ double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* 
                           const double* f_ext, const double* feet, const double* mean, const double* var, uint64_t iter,
                           uint32_t k, double eps, double* J_out)
 {
-    double* B = NULL;
-    if (P->P > 0) {
-        B = (double*)malloc(sizeof(double) * P->H * P->P);
-        orc_spline_basis(P->H, P->P, P->dt_us * 1e-6, B);
-    }
-    rollout_ctx c = {P, g, x0, xref, f_ext, mean, var, B, iter, feet};
+    rollout_ctx c = make_ctx(P, g, x0, xref, f_ext, feet, mean, var, iter);
     double* th = (double*)malloc(sizeof(double) * orc_dim(P));
     uint32_t q;
     double J = rollout_core(&c, k, -1, th, &q, NULL, 0.0, 0);
@@ -768,7 +795,7 @@ double orc_cost_condition(const orc_params* P, const orc_gait* g, const double* 
     }
     if (J_out) *J_out = J;
     free(th);
-    free(B);
+    free_ctx(&c);
     return worst;
 }
 

@@ -652,6 +652,15 @@ struct sbs_batch {
     bool ev_valid;
     cudaStream_t cstream;  // records copies of replayed ticks, ahead of the tick before
     sbs_batch_plan plan;
+    // host-memory ticks (sbs_batch_solve_host): pinned staging of every
+    // controller's inputs and results, and their device copies
+    char* h_in = nullptr;
+    char* d_in = nullptr;
+    size_t in_cap = 0;
+    sbs_result* h_res = nullptr;
+    sbs_result* d_res = nullptr;
+    int res_cap = 0;
+    std::vector<sbs_problem> dprobs;
 };
 
 extern "C" int sbs_batch_create(int max_instances, int inflight, size_t workspace_bytes, const sbs_allocator* alloc,
@@ -750,6 +759,10 @@ extern "C" void sbs_batch_destroy(sbs_batch* b)
         if (sl.pin) cudaFreeHost(sl.pin);
         dev_free(&b->alloc, b->has_alloc, sl.dev);
     }
+    if (b->h_in) cudaFreeHost(b->h_in);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    dev_free(&b->alloc, b->has_alloc, b->d_in);
+    dev_free(&b->alloc, b->has_alloc, b->d_res);
     if (b->cstream) cudaStreamDestroy(b->cstream);
     delete b;
 }
@@ -1038,6 +1051,92 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         h->cur ^= 1;
         h->iter += 1;
     }
+    return SBS_OK;
+}
+
+// One tick from host memory: every controller's inputs are gathered into one
+// pinned buffer and copied to the device in one transfer on the caller's stream,
+// the tick runs on the device copies, and the n results come back in one
+// transfer; the call returns when they are in `results`.
+extern "C" int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                                    sbs_result* results, void* stream)
+{
+    if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        const sbs_handle* h = handles[i];
+        const sbs_problem& p = probs[i];
+        if (!h || !p.x0 || !p.xref || p.host_memory != 1) return SBS_ERR_INVALID_ARG;
+        if (h->hP.world_feet && !p.feet) return SBS_ERR_INVALID_ARG;
+        need += align_up(12 * 4, 16) + align_up((size_t)12 * h->hP.H * 4, 16) + (p.f_ext ? 16 : 0) +
+                (h->hP.world_feet ? 32 : 0);
+    }
+    // wait for any earlier tick of this batch before its staging is rewritten
+    for (int k = 0; k < b->nslots; ++k)
+        if (b->slot[k].used && cudaEventSynchronize(b->slot[k].done) != cudaSuccess) return SBS_ERR_CUDA;
+    if (need > b->in_cap) {
+        if (b->h_in) cudaFreeHost(b->h_in);
+        dev_free(&b->alloc, b->has_alloc, b->d_in);
+        b->h_in = nullptr;
+        b->in_cap = 0;
+        const size_t cap = align_up(need + need / 4, 4096);
+        b->d_in = (char*)dev_alloc(&b->alloc, b->has_alloc, cap);
+        if (!b->d_in || cudaHostAlloc((void**)&b->h_in, cap, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            dev_free(&b->alloc, b->has_alloc, b->d_in);
+            b->d_in = nullptr;
+            b->h_in = nullptr;
+            return SBS_ERR_OOM;
+        }
+        b->in_cap = cap;
+    }
+    if (n > b->res_cap) {
+        if (b->h_res) cudaFreeHost(b->h_res);
+        dev_free(&b->alloc, b->has_alloc, b->d_res);
+        b->h_res = nullptr;
+        b->res_cap = 0;
+        b->d_res = (sbs_result*)dev_alloc(&b->alloc, b->has_alloc, (size_t)b->max_inst * sizeof(sbs_result));
+        if (!b->d_res ||
+            cudaHostAlloc((void**)&b->h_res, (size_t)b->max_inst * sizeof(sbs_result), cudaHostAllocDefault) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            dev_free(&b->alloc, b->has_alloc, b->d_res);
+            b->d_res = nullptr;
+            b->h_res = nullptr;
+            return SBS_ERR_OOM;
+        }
+        b->res_cap = b->max_inst;
+    }
+    b->dprobs.resize(n);
+    size_t off = 0;
+    auto stage = [&](const float* src, size_t count) -> const float* {
+        std::memcpy(b->h_in + off, src, count * 4);
+        const float* d = (const float*)(b->d_in + off);
+        off += align_up(count * 4, 16);
+        return d;
+    };
+    for (int i = 0; i < n; ++i) {
+        const sbs_problem& p = probs[i];
+        sbs_problem& q = b->dprobs[i];
+        q = p;
+        q.host_memory = 0;
+        q.x0 = stage(p.x0, 12);
+        q.xref = stage(p.xref, (size_t)12 * handles[i]->hP.H);
+        q.f_ext = p.f_ext ? stage(p.f_ext, 3) : nullptr;
+        q.feet = handles[i]->hP.world_feet ? stage(p.feet, 8) : nullptr;
+    }
+    if (cudaMemcpyAsync(b->d_in, b->h_in, off, cudaMemcpyHostToDevice, s) != cudaSuccess) return SBS_ERR_CUDA;
+    int st = sbs_batch_solve(b, n, handles, b->dprobs.data(), b->d_res, stream);
+    if (st) {
+        cudaStreamSynchronize(s);
+        return st;
+    }
+    if (cudaMemcpyAsync(b->h_res, b->d_res, (size_t)n * sizeof(sbs_result), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SBS_ERR_CUDA;
+    std::memcpy(results, b->h_res, (size_t)n * sizeof(sbs_result));
     return SBS_OK;
 }
 

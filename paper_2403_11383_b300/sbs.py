@@ -140,6 +140,7 @@ ABI = {
     "sbs_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p]),
     "sbs_batch_destroy": (None, [C.c_void_p]),
     "sbs_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_batch_solve_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_status_str": (C.c_char_p, [C.c_int]),
     "sbs_solve_mppi_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                         C.c_void_p]),
@@ -461,6 +462,17 @@ class Batch:
         """One tick of the packed controllers (no per-call marshalling)."""
         check(lib().sbs_batch_solve(self._b, packed.n, packed.handles, packed.problems,
                                     C.c_void_p(results.data_ptr()), _stream_ptr(stream)), "sbs_batch_solve")
+
+
+    def solve_host(self, packed: "Packed", results, stream=None):
+        """One tick from host memory, end to end (sbs_batch_solve_host): the packed
+        problems point at host arrays (host=True), results is a host buffer of
+        n * RESULT_BYTES (a ctypes array of Result, or a uint8 numpy array or CPU
+        tensor); on return the results are in it."""
+        ptr = results.data_ptr() if hasattr(results, "data_ptr") else (
+            results.ctypes.data if hasattr(results, "ctypes") else C.addressof(results))
+        check(lib().sbs_batch_solve_host(self._b, packed.n, packed.handles, packed.problems, C.c_void_p(ptr),
+                                         _stream_ptr(stream)), "sbs_batch_solve_host")
 
 
 class Packed:

@@ -482,3 +482,46 @@ def test_autotune_picks_a_mode_and_results_stay_valid():
     for i in range(len(mix)):
         r = S.parse_result(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy())
         assert r["status"] in (S.OK, S.ERR_DIVERGED) and r["iter"] == 6
+
+
+def test_batch_host_memory_equals_device():
+    # sbs_batch_solve_host: the same ticks from host arrays (one staged copy in, one
+    # out) give the bits of device-memory ticks, over warm-started ticks, with
+    # ground-fixed feet and external forces among the inputs
+    import torch
+    mix = _mix()
+    dev_c = [S.Controller(c) for c, _ in mix]
+    host_c = [S.Controller(c) for c, _ in mix]
+    tens = [_tensors(p) for _, p in mix]
+    host = []
+    for _, p in mix:
+        a = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+        host.append((a(p["x0"]), a(p["xref"]), a(p["f_ext"]), a(p["feet"]) if "feet" in p else None))
+    n = len(mix)
+    bd = S.Batch(n, sum(c.workspace_bytes() + 256 for c in dev_c))
+    bh = S.Batch(n, 2 * sum(c.workspace_bytes() + 256 for c in host_c), inflight=2)
+    res_d = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    res_h = np.zeros(n * S.RESULT_BYTES, dtype=np.uint8)
+    for tick in range(3):
+        shift = 0 if tick == 0 else 1
+        pd, ph = [], []
+        for i, (c, p) in enumerate(mix):
+            g = _gait(p, tick, c)
+            x0, xr, fe, ft = tens[i]
+            pd.append(dev_c[i].problem(x0, xr, g, fe, shift, feet=ft))
+            hx, hr, hf, hft = host[i]
+            ph.append(host_c[i].problem(hx, hr, g, hf, shift, host=True, feet=hft))
+        bd.solve(dev_c, pd, res_d)
+        bh.solve_host(S.Packed(host_c, ph), res_h)  # returns with the results on the host
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(res_h, res_d.cpu().numpy())
+        for i in range(n):
+            md, vd = _state(dev_c[i])
+            mh, vh = _state(host_c[i])
+            np.testing.assert_array_equal(mh, md)
+            np.testing.assert_array_equal(vh, vd)
+    # device pointers are refused by the host entry point
+    with pytest.raises(S.SBSError):
+        bh.solve_host(S.Packed(host_c, pd), res_h)
+    bd.close()
+    bh.close()

@@ -13,6 +13,8 @@ from paper_2403_11383_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 STEPS, WARMUP = 5, 3
 
 
@@ -59,3 +61,25 @@ def test_small_batched_line():
     split = d["config"]["launch_mode"] == "grid" and 0 < mppi < len(mix)
     assert d["gpu_launches"] == (4 if split else 3) * STEPS
     assert set(d["stages_ms"]) == {"rollout", "select", "refit"}
+    # the end-to-end leg copies x0, the reference and f_ext of every controller in
+    # and one result record per controller out
+    assert d["e2e"]["h2d_bytes_per_step"] == sum(4 * (12 + 12 * c["H"] + 3) for c, _ in mix)
+    assert d["e2e"]["d2h_bytes_per_step"] == 8 * 80
+    assert d["latency_ms"]["ticks"] >= 400
+
+
+@pytest.mark.parametrize("name", ["plain_mppi_k512_h12", "adaptive_elite_k8192_h25"])
+def test_parity_record_within_tolerances(name):
+    # the bench's per-output error record on two workloads: the staged update
+    # errors meet the parity tests' tolerances
+    import bench
+    cfg = W.config(name)
+    rec = bench.parity_one(cfg, W.problem(cfg), os.cpu_count() or 1)
+    assert rec["gated"] > 0 and rec["cost_rel_err_gated"]["max"] <= 1e-3
+    assert rec["staged"]["mean_abs_err"] <= bench.MEAN_ATOL
+    if cfg["method"] == "mppi":
+        assert rec["staged"]["ess_rel_err"] <= 1e-4
+    else:
+        assert rec["staged"]["elite_set_is_first_Ke_of_gpu_costs"]
+        assert rec["staged"]["var_rel_err"] <= 2e-4
+        assert rec["staged"]["compare_mppi_mean_abs_err"] <= bench.MEAN_ATOL

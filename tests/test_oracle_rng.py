@@ -158,3 +158,10 @@ def test_quantise_freq(orc):
                 assert q == exact_q
             else:
                 assert q in (exact_q - 1, exact_q)
+
+def test_normals6_equals_per_entry_normals(orc):
+    # one Philox block and its three Box-Muller pairs give the six normals of a draw
+    for seed, ctrl, k, d, it in ((0, 0, 0, 1, 0), (7, 3, 12345, 9, 2 ** 33 + 5), (1, 255, 99, 50, 17)):
+        got = orc.normals6(seed, ctrl, k, d, it)
+        want = [orc.normal(seed, ctrl, k, 6 * (d - 1) + s, it) for s in range(6)]
+        assert list(got) == want
