@@ -513,6 +513,7 @@ def main():
         tick(first=(w == 0))
     tune_ms = batch.autotune(ctls, probs1, results, ticks=5)
     mode = "grid" if batch.mode() == S.BATCH_GRID else "persistent"
+    spt = batch.samples_per_thread() or 1
     for _ in range(3):  # rebuild the tick graphs in the chosen mode before timing
         tick()
     torch.cuda.synchronize()
@@ -649,6 +650,7 @@ def main():
             "config": {"workload": WORKLOAD, "instances": n, "sample_steps_per_tick": ss_tick,
                        "tile": tile, "tile_autotune_ms_per_tick": tile_ms, "graph": True, "launch_mode": mode,
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
+                       "samples_per_thread": spt,
                        "l2": "per-tick working set above L2 (sampled deviations "
                        f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
@@ -657,7 +659,10 @@ def main():
             "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
                       "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
-            "roofline": {"kernel": "k_grid_rollout_lean" if mode == "grid" else "k_batch_rollout<0, false>", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": {("grid", 1): "k_grid_rollout_lean", ("grid", 2): "k_grid_rollout_pair",
+                                    ("persistent", 1): "k_batch_rollout<0, false>",
+                                    ("persistent", 2): "k_batch_rollout_pair"}[(mode, spt)],
+                         "bound": "alu", "achieved": achieved,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "peak_kind": "FP32 FMA-chain microbenchmark on this GPU (live)",
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,

@@ -345,9 +345,25 @@ int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* handles, const 
 int sbs_batch_set_mode(sbs_batch* b, int mode);
 int sbs_batch_get_mode(const sbs_batch* b);
 
-/* Autotuner: runs `ticks` profiled ticks in each launch mode on these
- * controllers and problems (real solves: they advance the controllers), keeps
- * the mode with the shorter mean tick and reports the mean tick times in
+/* Samples per thread of a batch's rollout launches: 1, 2, or 0 (the default,
+ * one; sbs_batch_autotune measures both and keeps the faster).  Two samples per
+ * thread apply to the per-step policy on the ordinary model (no spline, no
+ * frequency set, no ground-fixed feet, no friction projection) with tiles of a
+ * multiple of 64 samples; each thread then carries two samples whose FP32
+ * arithmetic issues as packed FP32x2 instructions, with half the threads and
+ * twice the registers per thread.  Other launches keep one.  Results are bit for
+ * bit the same either way: this is a launch shape, not a change of method. */
+int sbs_batch_set_samples_per_thread(sbs_batch* b, int spt);
+int sbs_batch_get_samples_per_thread(const sbs_batch* b);
+
+/* The same choice for a handle's plain solves (sbs_solve); 0 (the default) is
+ * one sample per thread. */
+int sbs_set_samples_per_thread(sbs_handle* h, int spt);
+
+/* Autotuner: runs `ticks` profiled ticks in each launch mode, with one and (where
+ * the launch can take them) two samples per thread, on these controllers and
+ * problems (real solves: they advance the controllers), keeps the setting with
+ * the shortest mean tick and reports each mode's best mean tick time in
  * ms_out[0] (grid) and ms_out[1] (persistent). */
 int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                        sbs_result* results, int ticks, float ms_out[2], void* stream);

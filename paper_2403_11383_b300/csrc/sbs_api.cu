@@ -461,7 +461,7 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
         t.result = res;
         t.ws = h->ws;
-        st = launch_rollout(h->dP, P, t, stream);
+        st = launch_rollout(h->dP, P, t, stream, h->spt == 2 ? 2 : 1);
         if (st) return st;
         if (P.method != SBS_MPPI) {
             st = launch_select(h->dP, P, t, stream);
@@ -630,7 +630,7 @@ struct sbs_batch_plan {
     std::vector<const sbs_handle*> h;
     std::vector<uint64_t> uid;
     std::vector<int> order;  // heavier tiles first
-    size_t smem = 0, sel_smem = 0, arena = 0;
+    size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0;
     long long counters = 0;
     bool ext = false;
 };
@@ -652,6 +652,7 @@ struct sbs_batch {
     bool ev_valid;
     cudaStream_t cstream;  // records copies of replayed ticks, ahead of the tick before
     sbs_batch_plan plan;
+    int spt;               // samples per thread of the rollout: 0 (default: one) , 1 or 2
     // host-memory ticks (sbs_batch_solve_host): pinned staging of every
     // controller's inputs and results, and their device copies
     char* h_in = nullptr;
@@ -869,13 +870,14 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
     pl.h.clear();
     pl.uid.clear();
     const int T = handles[0]->hP.T, Pk = handles[0]->hP.P;
-    size_t smem = 0, sel_smem = 0, arena = 0;
+    size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0;
     long long counters = 0;
     bool ext = false;  // some controller uses an extended model feature
     for (int i = 0; i < n; ++i) {
         const sbs_handle* h = handles[i];
         if (h->hP.T != T || h->hP.P != Pk || h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb));
+        smem_pair = std::max(smem_pair, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb, true));
         ext = ext || h->hP.n_freq > 0 || h->hP.world_feet || h->hP.friction_project;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
         arena += align_up(h->wsl.bytes, 256);
@@ -900,6 +902,7 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
     });
     pl.order = std::move(order);
     pl.smem = smem;
+    pl.smem_pair = smem_pair;
     pl.sel_smem = sel_smem;
     pl.arena = arena;
     pl.counters = counters;
@@ -935,7 +938,9 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     const int Pk = handles[0]->hP.P;
     const std::vector<int>& order = pl.order;
     const bool ext = pl.ext;
-    const size_t smem = pl.smem;
+    const bool pair = b->spt == 2 && pair_capable(Pk, ext, T);
+    const size_t smem = pair ? pl.smem_pair : pl.smem;
+    const int RT = pair ? T / 2 : T;  // threads of a rollout block
     size_t sel_smem = pl.sel_smem;
     sbs_batch_slot& sl = b->slot[b->next];
     b->next = (b->next + 1) % b->nslots;
@@ -1004,16 +1009,16 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     if (sel_smem == 0) sel_smem = 256;
     const size_t used = kBatchHeader + (size_t)n * sizeof(InstRec);
     int grids[4];
-    const int var = rollout_variant(Pk, ext);
-    int st = batch_grid(var, mode, smem, sel_smem, T, counts, grids);
+    const int var = rollout_variant(Pk, ext, pair);
+    int st = batch_grid(var, mode, smem, sel_smem, RT, counts, grids);
     if (st) return st;
     grids[3] = split ? tile_begin - tiles_upd : 0;
-    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != T || sl.key_var != var ||
+    const bool rekey = sl.key_smem != smem || sl.key_sel != sel_smem || sl.key_T != RT || sl.key_var != var ||
                        sl.key_mode != mode || sl.key_split != split;
     if (b->use_graph && !b->profiling) {
         if (!sl.exec || rekey) {
             std::memcpy(sl.grids, grids, sizeof(grids));
-            st = build_graph(b, sl, var, mode, smem, sel_smem, T, split);
+            st = build_graph(b, sl, var, mode, smem, sel_smem, RT, split);
             if (st) return st;
         } else if (mode == SBS_BATCH_GRID) {
             st = update_graph_grids(sl, grids, split);
@@ -1033,13 +1038,13 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         if (cudaMemcpyAsync(sl.dev, sl.pin, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return SBS_ERR_CUDA;
         if (cudaMemsetAsync(sl.heads, 0, 16, s) != cudaSuccess) return SBS_ERR_CUDA;
         st = launch_batch(var, mode, (const InstRec*)(sl.dev + kBatchHeader), (const int*)sl.dev, sl.heads, smem,
-                          sel_smem, T, grids, stream, b->profiling ? (void* const*)b->ev : nullptr);
+                          sel_smem, RT, grids, stream, b->profiling ? (void* const*)b->ev : nullptr);
         if (st) return st;
         b->ev_valid = b->profiling;
     }
     sl.key_smem = smem;
     sl.key_sel = sel_smem;
-    sl.key_T = T;
+    sl.key_T = RT;
     sl.key_var = var;
     sl.key_mode = mode;
     sl.key_split = split;
@@ -1143,26 +1148,61 @@ extern "C" int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* hand
 extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                                   sbs_result* results, int ticks, float ms_out[2], void* stream)
 {
-    if (!b || ticks < 1 || !ms_out) return SBS_ERR_INVALID_ARG;
+    if (!b || ticks < 1 || !ms_out || n < 1 || !handles || !handles[0]) return SBS_ERR_INVALID_ARG;
     const bool prof = b->profiling;
     int st = sbs_batch_set_profiling(b, 1);
     if (st) return st;
+    // launch modes, and one or two samples per thread where the launch can take two
+    bool ext = false;
+    for (int i = 0; i < n; ++i) {
+        if (!handles[i]) return SBS_ERR_INVALID_ARG;
+        ext = ext || handles[i]->hP.n_freq > 0 || handles[i]->hP.world_feet || handles[i]->hP.friction_project;
+    }
+    const int nspt = pair_capable(handles[0]->hP.P, ext, handles[0]->hP.T) ? 2 : 1;
     const int modes[2] = {SBS_BATCH_GRID, SBS_BATCH_PERSISTENT};
-    for (int m = 0; m < 2; ++m) {
+    float best = 1e30f;
+    int best_mode = SBS_BATCH_GRID, best_spt = 1;
+    for (int m = 0; m < 2 && st == SBS_OK; ++m) {
         b->mode = modes[m];
-        double tot = 0.0;
-        for (int k = 0; k <= ticks && st == SBS_OK; ++k) {  // the first tick of a mode is a warm-up
-            st = sbs_batch_solve(b, n, handles, probs, results, stream);
-            float ms[3];
-            if (st == SBS_OK) st = sbs_batch_stage_ms(b, ms);
-            if (st == SBS_OK && k > 0) tot += (double)ms[0] + ms[1] + ms[2];
+        ms_out[m] = 1e30f;
+        for (int sp = 1; sp <= nspt && st == SBS_OK; ++sp) {
+            b->spt = sp;
+            double tot = 0.0;
+            for (int k = 0; k <= ticks && st == SBS_OK; ++k) {  // the first tick of a setting is a warm-up
+                st = sbs_batch_solve(b, n, handles, probs, results, stream);
+                float ms[3];
+                if (st == SBS_OK) st = sbs_batch_stage_ms(b, ms);
+                if (st == SBS_OK && k > 0) tot += (double)ms[0] + ms[1] + ms[2];
+            }
+            const float avg = (float)(tot / ticks);
+            if (st == SBS_OK && avg < ms_out[m]) ms_out[m] = avg;
+            if (st == SBS_OK && avg < best) {
+                best = avg;
+                best_mode = modes[m];
+                best_spt = sp;
+            }
         }
-        if (st) break;
-        ms_out[m] = (float)(tot / ticks);
     }
     sbs_batch_set_profiling(b, prof ? 1 : 0);
     if (st) return st;
-    b->mode = ms_out[0] <= ms_out[1] ? SBS_BATCH_GRID : SBS_BATCH_PERSISTENT;
+    b->mode = best_mode;
+    b->spt = best_spt;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_set_samples_per_thread(sbs_batch* b, int spt)
+{
+    if (!b || spt < 0 || spt > 2) return SBS_ERR_INVALID_ARG;
+    b->spt = spt;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_get_samples_per_thread(const sbs_batch* b) { return b ? b->spt : SBS_ERR_INVALID_ARG; }
+
+extern "C" int sbs_set_samples_per_thread(sbs_handle* h, int spt)
+{
+    if (!h || spt < 0 || spt > 2) return SBS_ERR_INVALID_ARG;
+    h->spt = spt;
     return SBS_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -11,6 +12,161 @@
 namespace sbs {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Lane values.  The rollout's arithmetic is written once over a lane type V:
+// float carries one sample per thread; float2 carries two samples per thread,
+// and its additions, multiplications and fused multiply-adds issue as single
+// packed FP32x2 instructions (sm_100 and later), so two samples' arithmetic
+// takes one issue slot.  Every operation is explicit and rounded once
+// (round-to-nearest, no contraction left to the compiler), so a sample's result
+// has the same bits whichever lane type carries it.
+// ---------------------------------------------------------------------------
+template <class V>
+struct Lane;
+
+template <>
+struct Lane<float> {
+    static constexpr int N = 1;
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+    static __device__ __forceinline__ float bc(float s) { return s; }
+    static __device__ __forceinline__ float get(float v, int) { return v; }
+    static __device__ __forceinline__ void set(float& v, int, float s) { v = s; }
+};
+
+// The packed forms are written as PTX with an explicit round-to-nearest
+// modifier.  A packed difference whose operand is a packed product was still
+// measured to round as if fused (a - b c in one rounding) on sm_103a, so the
+// model never subtracts a product: a b - c d is written fma(a, b, (-c) d), with
+// the negation exact, in both lane widths.
+__device__ __forceinline__ unsigned long long f2_bits(float2 v)
+{
+    unsigned long long r;
+    memcpy(&r, &v, 8);
+    return r;
+}
+
+__device__ __forceinline__ float2 f2_from(unsigned long long r)
+{
+    float2 v;
+    memcpy(&v, &r, 8);
+    return v;
+}
+
+template <>
+struct Lane<float2> {
+    static constexpr int N = 2;
+    static __device__ __forceinline__ float2 add(float2 a, float2 b)
+    {
+        unsigned long long d;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+        return f2_from(d);
+    }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b)
+    {
+        unsigned long long d;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+        return f2_from(d);
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b)
+    {
+        unsigned long long d;
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+        return f2_from(d);
+    }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c)
+    {
+        unsigned long long d;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+        return f2_from(d);
+    }
+    static __device__ __forceinline__ float2 neg(float2 a) { return mul(a, make_float2(-1.0f, -1.0f)); }
+    static __device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+    static __device__ __forceinline__ float get(float2 v, int i) { return i ? v.y : v.x; }
+    static __device__ __forceinline__ void set(float2& v, int i, float s)
+    {
+        if (i) v.y = s;
+        else v.x = s;
+    }
+};
+
+// Model and cost constants duplicated into lane pairs (staged once per block in
+// shared memory for the two-sample rollout).
+struct __align__(16) PairConsts {
+    float2 Q[12];
+    float2 R[3], w_fc;
+    float2 foot[12], nfoot[12];  // lever arms and their negatives
+    float2 gyro[3], inv_mass;
+    float2 inv_inertia[3], dt;
+    float2 gravity[3], nmu;      // -mu
+    float2 fe[3], zero;          // f_ext
+};
+
+// The constants a lane type reads: the parameter block itself for one sample
+// per thread, the duplicated pairs for two.
+template <class V>
+struct Consts;
+
+template <>
+struct Consts<float> {
+    const InstParams& P;
+    __device__ __forceinline__ float Q(int c) const { return P.Q[c]; }
+    __device__ __forceinline__ float R(int a) const { return P.R[a]; }
+    __device__ __forceinline__ float w_fc() const { return P.w_fc; }
+    __device__ __forceinline__ float nmu() const { return -P.mu; }
+    __device__ __forceinline__ float foot(int i) const { return P.foot[i]; }
+    __device__ __forceinline__ float nfoot(int i) const { return -P.foot[i]; }
+    __device__ __forceinline__ float gyro(int a) const { return P.gyro[a]; }
+    __device__ __forceinline__ float inv_inertia(int a) const { return P.inv_inertia[a]; }
+    __device__ __forceinline__ float inv_mass() const { return P.inv_mass; }
+    __device__ __forceinline__ float dt() const { return P.dt; }
+    __device__ __forceinline__ float gravity(int a) const { return P.gravity[a]; }
+};
+
+template <>
+struct Consts<float2> {
+    const PairConsts& C;
+    __device__ __forceinline__ float2 Q(int c) const { return C.Q[c]; }
+    __device__ __forceinline__ float2 R(int a) const { return C.R[a]; }
+    __device__ __forceinline__ float2 w_fc() const { return C.w_fc; }
+    __device__ __forceinline__ float2 nmu() const { return C.nmu; }
+    __device__ __forceinline__ float2 foot(int i) const { return C.foot[i]; }
+    __device__ __forceinline__ float2 nfoot(int i) const { return C.nfoot[i]; }
+    __device__ __forceinline__ float2 gyro(int a) const { return C.gyro[a]; }
+    __device__ __forceinline__ float2 inv_inertia(int a) const { return C.inv_inertia[a]; }
+    __device__ __forceinline__ float2 inv_mass() const { return C.inv_mass; }
+    __device__ __forceinline__ float2 dt() const { return C.dt; }
+    __device__ __forceinline__ float2 gravity(int a) const { return C.gravity[a]; }
+};
+
+// Fill the pair constants (threads 0..63 of a block; f_ext given).
+__device__ __forceinline__ void fill_pair_consts(PairConsts& C, const InstParams& P, const float fe[3])
+{
+    const int t = threadIdx.x;
+    auto dup = [](float v) { return make_float2(v, v); };
+    if (t < 12) {
+        C.Q[t] = dup(P.Q[t]);
+        C.foot[t] = dup(P.foot[t]);
+        C.nfoot[t] = dup(-P.foot[t]);
+    } else if (t < 15) {
+        const int a = t - 12;
+        C.R[a] = dup(P.R[a]);
+        C.gyro[a] = dup(P.gyro[a]);
+        C.inv_inertia[a] = dup(P.inv_inertia[a]);
+        C.gravity[a] = dup(P.gravity[a]);
+        C.fe[a] = dup(fe[a]);
+    } else if (t == 15) {
+        C.w_fc = dup(P.w_fc);
+        C.inv_mass = dup(P.inv_mass);
+        C.dt = dup(P.dt);
+        C.nmu = dup(-P.mu);
+        C.zero = dup(0.0f);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
@@ -127,36 +283,65 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 // into floats without a conversion instruction: 0x4B000000 | n is the float
 // 2^23 + n, and fma(2^23 + n, c, -2^23 c) is n c rounded once, the same bits as
 // float(n) * c.
-__device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
+template <class V>
+__device__ __forceinline__ void box_muller21_v(const uint32_t* a, const uint32_t* b, V& z0, V& z1)
 {
+    using L = Lane<V>;
     const float two_m21 = 4.76837158203125e-7f;
     const float c_ang = 6.28318530717958648f * two_m21;
-    const float u1 = fmaf(__int_as_float(0x4b000000 | (int)(a + 1u)), two_m21, -4.0f);
-    const float ang = fmaf(__int_as_float(0x4b000000 | (int)b), c_ang, -8388608.0f * c_ang);
-    const float r2 = -1.38629436111989061f * __log2f(u1);  // -2 ln 2 log2(u1)
-    const float r = sqrt_hw(fmaxf(r2, 0.0f));
-    float s, c;
-    __sincosf(ang, &s, &c);
-    return make_float2(r * c, r * s);
+    V ia, ib;
+#pragma unroll
+    for (int i = 0; i < L::N; ++i) {
+        L::set(ia, i, __int_as_float(0x4b000000 | (int)(a[i] + 1u)));
+        L::set(ib, i, __int_as_float(0x4b000000 | (int)b[i]));
+    }
+    const V u1 = L::fma(ia, L::bc(two_m21), L::bc(-4.0f));
+    const V ang = L::fma(ib, L::bc(c_ang), L::bc(-8388608.0f * c_ang));
+    V lg, r, sn, cs;
+#pragma unroll
+    for (int i = 0; i < L::N; ++i) L::set(lg, i, __log2f(L::get(u1, i)));
+    const V r2 = L::mul(L::bc(-1.38629436111989061f), lg);  // -2 ln 2 log2(u1)
+#pragma unroll
+    for (int i = 0; i < L::N; ++i) {
+        L::set(r, i, sqrt_hw(fmaxf(L::get(r2, i), 0.0f)));
+        float si, ci;
+        __sincosf(L::get(ang, i), &si, &ci);
+        L::set(sn, i, si);
+        L::set(cs, i, ci);
+    }
+    z0 = L::mul(r, cs);
+    z1 = L::mul(r, sn);
+}
+
+__device__ __forceinline__ float2 box_muller21(uint32_t a, uint32_t b)
+{
+    float z0, z1;
+    box_muller21_v<float>(&a, &b, z0, z1);
+    return make_float2(z0, z1);
 }
 
 // The six force normals of one 128-bit draw: six 21-bit integers (the top 21
 // bits of each word, then the low 11 bits of words 0 and 2 joined to the low 10
 // bits of words 1 and 3), Box-Muller on the pairs (u0, u1), (u2, u3), (u4, u5).
-__device__ __forceinline__ void normals6(uint4 w, float* e)
+template <class V>
+__device__ __forceinline__ void normals6_v(const uint4* w, V* e)
 {
-    const uint32_t u4 = ((w.x & 0x7ffu) << 10) | (w.y & 0x3ffu);
-    const uint32_t u5 = ((w.z & 0x7ffu) << 10) | (w.w & 0x3ffu);
-    const float2 a = box_muller21(w.x >> 11, w.y >> 11);
-    const float2 b = box_muller21(w.z >> 11, w.w >> 11);
-    const float2 c = box_muller21(u4, u5);
-    e[0] = a.x;
-    e[1] = a.y;
-    e[2] = b.x;
-    e[3] = b.y;
-    e[4] = c.x;
-    e[5] = c.y;
+    constexpr int N = Lane<V>::N;
+    uint32_t a[3][N], b[3][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        a[0][i] = w[i].x >> 11;
+        b[0][i] = w[i].y >> 11;
+        a[1][i] = w[i].z >> 11;
+        b[1][i] = w[i].w >> 11;
+        a[2][i] = ((w[i].x & 0x7ffu) << 10) | (w[i].y & 0x3ffu);
+        b[2][i] = ((w[i].z & 0x7ffu) << 10) | (w[i].w & 0x3ffu);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) box_muller21_v<V>(a[p], b[p], e[2 * p], e[2 * p + 1]);
 }
+
+__device__ __forceinline__ void normals6(uint4 w, float* e) { normals6_v<float>(&w, e); }
 
 // The 12 force normals of step (or knot) j: draws 1 + 2j and 2 + 2j, counter
 // (k, draw, iter lo, iter hi), key (seed, ctrl).
@@ -217,13 +402,17 @@ __device__ __forceinline__ int stance_at(const TickArgs& t, int leg, uint32_t q,
 }
 
 // Kahan-compensated accumulation.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v)
+template <class V>
+__device__ __forceinline__ void kahan_add_v(V& s, V& c, V v)
 {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
+    using L = Lane<V>;
+    const V y = L::sub(v, c);
+    const V t = L::add(s, y);
+    c = L::sub(L::sub(t, s), y);
     s = t;
 }
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) { kahan_add_v<float>(s, c, v); }
 
 // ---------------------------------------------------------------------------
 // One explicit-Euler step of Eq. (1) plus the stage cost of the pre-step state
@@ -233,39 +422,74 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 // then skipped (a +0 force contributes +0 to every sum, so the result is
 // unchanged for finite states).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float stage_cost(const InstParams& P, const float x[12], const float* xr,
-                                            const float G[12], unsigned live = 0xfu, bool penalty = true)
+// Rows of 12 lane values from 16-byte aligned shared memory (one sample per
+// thread: 3 vector loads; two: 6, each holding two duplicated pairs).
+template <class V>
+__device__ __forceinline__ void load_row12(const V* p, V out[12])
 {
-    float r = 0.0f;
-    const float4* xr4 = reinterpret_cast<const float4*>(xr);  // 16-byte aligned rows of 12
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    if constexpr (Lane<V>::N == 1) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const float4 a = xr4[q];
-        const float xa[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c = 4 * q + i;
-            const float e = x[c] - xa[i];
-            r = fmaf(P.Q[c] * e, e, r);
+        for (int q = 0; q < 3; ++q) {
+            const float4 a = p4[q];
+            out[4 * q] = a.x;
+            out[4 * q + 1] = a.y;
+            out[4 * q + 2] = a.z;
+            out[4 * q + 3] = a.w;
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float4 a = p4[q];
+            out[2 * q] = make_float2(a.x, a.y);
+            out[2 * q + 1] = make_float2(a.z, a.w);
+        }
+    }
+}
+
+template <class V>
+__device__ __forceinline__ V stage_cost_v(const Consts<V>& K, const V x[12], const V* xr, const V G[12],
+                                          unsigned live, bool penalty)
+{
+    using L = Lane<V>;
+    V xrr[12];
+    load_row12<V>(xr, xrr);
+    V r = L::bc(0.0f);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const V e = L::sub(x[c], xrr[c]);
+        r = L::fma(L::mul(K.Q(c), e), e, r);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if (!(live & (1u << i))) continue;  // zero force on every lane: adds exactly nothing
-        const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
-        r = fmaf(P.R[0] * gx, gx, r);
-        r = fmaf(P.R[1] * gy, gy, r);
-        r = fmaf(P.R[2] * gz, gz, r);
+        const V gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
+        r = L::fma(L::mul(K.R(0), gx), gx, r);
+        r = L::fma(L::mul(K.R(1), gy), gy, r);
+        r = L::fma(L::mul(K.R(2), gz), gz, r);
         if (!penalty) continue;  // forces already projected onto the cone
         // friction cone on stance legs; a swing leg's zero force adds nothing
         // (|G_xy| by sqrt_hw, exact zero for a zero force)
-        const float t2 = fmaf(gx, gx, gy * gy);
-        const float slip = sqrt_hw(t2) - P.mu * gz;
-        const float sp = fmaxf(slip, 0.0f), gn = fminf(gz, 0.0f);
-        const float pen = fmaf(gn, gn, sp * sp);
-        r = fmaf(P.w_fc, pen, r);
+        const V t2 = L::fma(gx, gx, L::mul(gy, gy));
+        V sq, sp, gn;
+#pragma unroll
+        for (int l = 0; l < L::N; ++l) L::set(sq, l, sqrt_hw(L::get(t2, l)));
+        const V slip = L::fma(K.nmu(), gz, sq);
+#pragma unroll
+        for (int l = 0; l < L::N; ++l) {
+            L::set(sp, l, fmaxf(L::get(slip, l), 0.0f));
+            L::set(gn, l, fminf(L::get(gz, l), 0.0f));
+        }
+        const V pen = L::fma(gn, gn, L::mul(sp, sp));
+        r = L::fma(K.w_fc(), pen, r);
     }
     return r;
+}
+
+__device__ __forceinline__ float stage_cost(const InstParams& P, const float x[12], const float* xr,
+                                            const float G[12], unsigned live = 0xfu, bool penalty = true)
+{
+    return stage_cost_v<float>(Consts<float>{P}, x, xr, G, live, penalty);
 }
 
 // Orthogonal projection of one force onto the friction cone |G_xy| <= mu G_z
@@ -297,71 +521,124 @@ __device__ __forceinline__ void angle_sincos(float a, float* s, float* c)
     else __sincosf(a, s, c);
 }
 
+// sin and cos of lane angles (per lane: the accurate routine has no packed form).
+template <class V>
+__device__ __forceinline__ void angle_sincos_v(V a, V& s, V& c)
+{
+    using L = Lane<V>;
+#pragma unroll
+    for (int l = 0; l < L::N; ++l) {
+        float sl, cl;
+        angle_sincos(L::get(a, l), &sl, &cl);
+        L::set(s, l, sl);
+        L::set(c, l, cl);
+    }
+}
+
 // The rotational and translational rates of Eq. (1) from the net force F and
 // body-frame moment t, then the explicit Euler step of all 12 states.
+template <class V>
+__device__ __forceinline__ void srbd_integrate_v(const Consts<V>& K, V x[12], V sr, V cr, V sp, V cp, V F0, V F1,
+                                                 V F2, V t0, V t1, V t2, const V fe[3])
+{
+    using L = Lane<V>;
+    const V w0 = x[9], w1 = x[10], w2 = x[11];
+    // I^{-1} (t - omega x I omega) with a diagonal I: component a is
+    // t_a / I_a + omega_{a+1} omega_{a+2} (I_{a+1} - I_{a+2}) / I_a
+    const V wd0 = L::fma(L::mul(w1, w2), K.gyro(0), L::mul(t0, K.inv_inertia(0)));
+    const V wd1 = L::fma(L::mul(w2, w0), K.gyro(1), L::mul(t1, K.inv_inertia(1)));
+    const V wd2 = L::fma(L::mul(w0, w1), K.gyro(2), L::mul(t2, K.inv_inertia(2)));
+    // E'^{-1}(Phi) omega for the ZYX angles
+    V ic;
+#pragma unroll
+    for (int l = 0; l < L::N; ++l) L::set(ic, l, __fdividef(1.0f, L::get(cp, l)));
+    const V a = L::fma(sr, w1, L::mul(cr, w2));
+    const V rd = L::fma(L::mul(sp, ic), a, w0);
+    const V pd = L::fma(cr, w1, L::mul(L::neg(sr), w2));
+    const V yd = L::mul(a, ic);
+    const V dt = K.dt();
+    const V vd0 = L::fma(L::add(F0, fe[0]), K.inv_mass(), K.gravity(0));
+    const V vd1 = L::fma(L::add(F1, fe[1]), K.inv_mass(), K.gravity(1));
+    const V vd2 = L::fma(L::add(F2, fe[2]), K.inv_mass(), K.gravity(2));
+    x[0] = L::fma(dt, x[6], x[0]);
+    x[1] = L::fma(dt, x[7], x[1]);
+    x[2] = L::fma(dt, x[8], x[2]);
+    x[3] = L::fma(dt, rd, x[3]);
+    x[4] = L::fma(dt, pd, x[4]);
+    x[5] = L::fma(dt, yd, x[5]);
+    x[6] = L::fma(dt, vd0, x[6]);
+    x[7] = L::fma(dt, vd1, x[7]);
+    x[8] = L::fma(dt, vd2, x[8]);
+    x[9] = L::fma(dt, wd0, w0);
+    x[10] = L::fma(dt, wd1, w1);
+    x[11] = L::fma(dt, wd2, w2);
+}
+
 __device__ __forceinline__ void srbd_integrate(const InstParams& P, float x[12], float sr, float cr, float sp,
                                                float cp, float F0, float F1, float F2, float t0, float t1,
                                                float t2, const float fe[3])
 {
-    const float w0 = x[9], w1 = x[10], w2 = x[11];
-    // I^{-1} (t - omega x I omega) with a diagonal I: component a is
-    // t_a / I_a + omega_{a+1} omega_{a+2} (I_{a+1} - I_{a+2}) / I_a
-    const float wd0 = fmaf(w1 * w2, P.gyro[0], t0 * P.inv_inertia[0]);
-    const float wd1 = fmaf(w2 * w0, P.gyro[1], t1 * P.inv_inertia[1]);
-    const float wd2 = fmaf(w0 * w1, P.gyro[2], t2 * P.inv_inertia[2]);
-    // E'^{-1}(Phi) omega for the ZYX angles
-    const float ic = __fdividef(1.0f, cp);
-    const float a = sr * w1 + cr * w2;
-    const float rd = w0 + sp * ic * a;
-    const float pd = cr * w1 - sr * w2;
-    const float yd = a * ic;
-    const float dt = P.dt;
-    const float vd0 = fmaf(F0 + fe[0], P.inv_mass, P.gravity[0]);
-    const float vd1 = fmaf(F1 + fe[1], P.inv_mass, P.gravity[1]);
-    const float vd2 = fmaf(F2 + fe[2], P.inv_mass, P.gravity[2]);
-    x[0] = fmaf(dt, x[6], x[0]);
-    x[1] = fmaf(dt, x[7], x[1]);
-    x[2] = fmaf(dt, x[8], x[2]);
-    x[3] = fmaf(dt, rd, x[3]);
-    x[4] = fmaf(dt, pd, x[4]);
-    x[5] = fmaf(dt, yd, x[5]);
-    x[6] = fmaf(dt, vd0, x[6]);
-    x[7] = fmaf(dt, vd1, x[7]);
-    x[8] = fmaf(dt, vd2, x[8]);
-    x[9] = fmaf(dt, wd0, w0);
-    x[10] = fmaf(dt, wd1, w1);
-    x[11] = fmaf(dt, wd2, w2);
+    srbd_integrate_v<float>(Consts<float>{P}, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
+}
+
+// Body-to-world rotation R = Rz(yaw) Ry(pitch) Rx(roll) from the attitude's
+// sines and cosines; R20 = -sin(pitch) is left to the caller.
+template <class V>
+struct Rot {
+    V R00, R01, R02, R10, R11, R12, R21, R22;
+};
+
+template <class V>
+__device__ __forceinline__ Rot<V> rotation_v(V sr, V cr, V sp, V cp, V sy, V cy)
+{
+    using L = Lane<V>;
+    Rot<V> R;
+    const V t = L::mul(cy, sp), u = L::mul(sy, sp);
+    R.R00 = L::mul(cy, cp);
+    R.R01 = L::fma(t, sr, L::mul(L::neg(sy), cr));
+    R.R02 = L::fma(t, cr, L::mul(sy, sr));
+    R.R10 = L::mul(sy, cp);
+    R.R11 = L::fma(u, sr, L::mul(cy, cr));
+    R.R12 = L::fma(u, cr, L::mul(L::neg(cy), sr));
+    R.R21 = L::mul(cp, sr);
+    R.R22 = L::mul(cp, cr);
+    return R;
+}
+
+template <class V>
+__device__ __forceinline__ void srbd_step_v(const Consts<V>& K, V x[12], const V G[12], const V fe[3],
+                                            unsigned live = 0xfu)
+{
+    using L = Lane<V>;
+    V sr, cr, sp, cp, sy, cy;
+    angle_sincos_v<V>(x[3], sr, cr);
+    angle_sincos_v<V>(x[4], sp, cp);
+    angle_sincos_v<V>(x[5], sy, cy);
+    const Rot<V> R = rotation_v<V>(sr, cr, sp, cp, sy, cy);
+    const V nsp = L::neg(sp);  // R20
+    V F0 = L::bc(0.0f), F1 = F0, F2 = F0, t0 = F0, t1 = F0, t2 = F0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!(live & (1u << i))) continue;  // zero force on every lane: adds exactly nothing
+        const V gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
+        F0 = L::add(F0, gx);
+        F1 = L::add(F1, gy);
+        F2 = L::add(F2, gz);
+        // body-frame force R^T Gamma_i, then the lever arm cross product
+        const V bx = L::fma(R.R00, gx, L::fma(R.R10, gy, L::mul(nsp, gz)));
+        const V by = L::fma(R.R01, gx, L::fma(R.R11, gy, L::mul(R.R21, gz)));
+        const V bz = L::fma(R.R02, gx, L::fma(R.R12, gy, L::mul(R.R22, gz)));
+        t0 = L::fma(K.nfoot(3 * i + 2), by, L::fma(K.foot(3 * i + 1), bz, t0));
+        t1 = L::fma(K.nfoot(3 * i), bz, L::fma(K.foot(3 * i + 2), bx, t1));
+        t2 = L::fma(K.nfoot(3 * i + 1), bx, L::fma(K.foot(3 * i), by, t2));
+    }
+    srbd_integrate_v<V>(K, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
 }
 
 __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], const float G[12],
                                           const float fe[3], unsigned live = 0xfu)
 {
-    float sr, cr, sp, cp, sy, cy;
-    angle_sincos(x[3], &sr, &cr);
-    angle_sincos(x[4], &sp, &cp);
-    angle_sincos(x[5], &sy, &cy);
-    // body-to-world R = Rz(yaw) Ry(pitch) Rx(roll)
-    const float R00 = cy * cp, R01 = cy * sp * sr - sy * cr, R02 = cy * sp * cr + sy * sr;
-    const float R10 = sy * cp, R11 = sy * sp * sr + cy * cr, R12 = sy * sp * cr - cy * sr;
-    const float R20 = -sp, R21 = cp * sr, R22 = cp * cr;
-    float F0 = 0.f, F1 = 0.f, F2 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (!(live & (1u << i))) continue;  // zero force on every lane: adds exactly nothing
-        const float gx = G[3 * i], gy = G[3 * i + 1], gz = G[3 * i + 2];
-        F0 += gx;
-        F1 += gy;
-        F2 += gz;
-        // body-frame force R^T Gamma_i, then the lever arm cross product
-        const float bx = R00 * gx + R10 * gy + R20 * gz;
-        const float by = R01 * gx + R11 * gy + R21 * gz;
-        const float bz = R02 * gx + R12 * gy + R22 * gz;
-        const float rx = P.foot[3 * i], ry = P.foot[3 * i + 1], rz = P.foot[3 * i + 2];
-        t0 = fmaf(-rz, by, fmaf(ry, bz, t0));
-        t1 = fmaf(-rx, bz, fmaf(rz, bx, t1));
-        t2 = fmaf(-ry, bx, fmaf(rx, by, t2));
-    }
-    srbd_integrate(P, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
+    srbd_step_v<float>(Consts<float>{P}, x, G, fe, live);
 }
 
 // The same step with stance feet fixed on the ground z = 0: the lever arm of leg
@@ -378,9 +655,9 @@ __device__ __forceinline__ void srbd_step_world(const InstParams& P, float x[12]
     angle_sincos(x[3], &sr, &cr);
     angle_sincos(x[4], &sp, &cp);
     angle_sincos(x[5], &sy, &cy);
-    const float R00 = cy * cp, R01 = cy * sp * sr - sy * cr, R02 = cy * sp * cr + sy * sr;
-    const float R10 = sy * cp, R11 = sy * sp * sr + cy * cr, R12 = sy * sp * cr - cy * sr;
-    const float R20 = -sp, R21 = cp * sr, R22 = cp * cr;
+    const Rot<float> Rm = rotation_v<float>(sr, cr, sp, cp, sy, cy);
+    const float R00 = Rm.R00, R01 = Rm.R01, R02 = Rm.R02, R10 = Rm.R10, R11 = Rm.R11, R12 = Rm.R12;
+    const float R20 = -sp, R21 = Rm.R21, R22 = Rm.R22;
     if (touch) {
         const float s = sqrtf(fmaxf(x[2], 0.0f) * P.inv_g);
         const float ax = fmaf(s, x[6] - vdx, tsh * vdx), ay = fmaf(s, x[7] - vdy, tsh * vdy);

@@ -109,7 +109,7 @@ static_assert(sizeof(InstParams) % 16 == 0, "InstParams must be a multiple of 16
 static_assert(sizeof(TickArgs) % 8 == 0, "TickArgs must be a multiple of 8 bytes");
 
 // Dynamic shared memory of one rollout item (bytes); nb force blocks.
-inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1)
+inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1, bool pair = false)
 {
     int nt = P > 0 ? P : H;
     int nf = 12 * nt;
@@ -120,6 +120,7 @@ inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1)
                   + (P > 0 ? (size_t)48 * ((P + 3) / 4) * T : 0)  // per-thread knot deviations
                   + (P > 0 ? (size_t)nwarps * nf  // per-warp partial sums, then the combined row
                            : (size_t)(6 * T > nf + kPartHeader ? 6 * T : nf + kPartHeader));  // weight list and slice sums, then the combined row
+    if (pair) floats = ((floats + 3) & ~(size_t)3) + 24 * (size_t)H;  // the reference as duplicated pairs
     return floats * sizeof(float);
 }
 
@@ -201,11 +202,18 @@ void fill_params(const sbs_config* cfg, InstParams* out);
 // model feature (a discrete step-frequency set, stance feet fixed on the
 // ground).  The batched launchers take a variant where they say P.
 constexpr int kExtVariant = 256;
-inline int rollout_variant(int P, bool ext) { return P | (ext ? kExtVariant : 0); }
+constexpr int kPairVariant = 512;  // two samples per thread
+inline int rollout_variant(int P, bool ext, bool pair = false)
+{
+    return P | (ext ? kExtVariant : 0) | (pair ? kPairVariant : 0);
+}
+// Launches that can carry two samples per thread: the per-step policy on the
+// ordinary model, with tiles of a multiple of 64 samples (whole warps of pairs).
+inline bool pair_capable(int P, bool ext, int T) { return P == 0 && !ext && T % 64 == 0; }
 
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
-int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
+int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream, int spt = 1);
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 // A batched tick's device header: two count blocks of 8 ints (the first rollout
@@ -249,6 +257,7 @@ struct sbs_handle {
     void* in_done;         // cudaEvent_t: last copy out of pin_in has run
     bool in_pending;
     uint64_t uid;          // creation number, unique over the process (a reused address gets a new one)
+    int spt;               // samples per thread of plain solves: 0 (default: one), 1 or 2
 };
 
 

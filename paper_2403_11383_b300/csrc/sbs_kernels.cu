@@ -52,6 +52,7 @@ struct __align__(16) BlockShared {
     float mu12[12], vr12[12], dbar[12];
     float wacc[32][12];
     float wacc2[kRefitLanesMax / 32][12];
+    PairConsts pc;  // model and cost constants as duplicated pairs (two samples per thread)
 };
 
 // A shared-memory vector load the compiler may not hoist out of the step loop
@@ -369,6 +370,79 @@ __device__ void mppi_finish(BlockShared& sh, const Views& v, const float* row, b
     __syncthreads();
 }
 
+// ---- hierarchical combine: the last tile of a group of kGroup tiles combines
+// the group's rows in tile order; the last group combines the group rows, and the
+// last block of all finishes the MPPI update.
+__device__ void tile_combine(BlockShared& sh, const Views& v, int tile)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int PS = P.part_stride;
+    const int g = tile / kGroup;
+    const int gsize = min(kGroup, P.ntiles - g * kGroup);
+    unsigned* counters = t.ws.counters;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(&counters[g], 1u);
+        sh.last = prev == (unsigned)gsize - 1u;
+    }
+    __syncthreads();
+    if (!sh.last) return;
+    __threadfence();
+    float* comb = v.acc;  // nf + kPartHeader floats (blockDim >= 64 leaves room)
+    const float* src_rows = t.ws.part + (size_t)g * kGroup * PS;
+    combine_rows(sh, src_rows, gsize, PS, P.nf, P.inv_lambda, comb);
+    if (P.ngroups > 1) {
+        float* grow = t.ws.gpart + (size_t)g * PS;
+        for (int i = tid; i < PS; i += T) grow[i] = comb[i];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            counters[g] = 0u;
+            const unsigned prev = atomicAdd(&counters[P.ngroups], 1u);
+            sh.last = prev == (unsigned)P.ngroups - 1u;
+        }
+        __syncthreads();
+        if (!sh.last) return;
+        __threadfence();
+        combine_rows(sh, t.ws.gpart, P.ngroups, PS, P.nf, P.inv_lambda, comb);
+        if (tid == 0) counters[P.ngroups] = 0u;
+    } else if (tid == 0) {
+        counters[g] = 0u;
+    }
+    mppi_finish(sh, v, comb, t.mppi_to_state != 0);
+}
+
+// Reference rows as duplicated pairs for the two-sample rollout, after the
+// per-step layout (16-byte aligned).
+__device__ __forceinline__ float2* pair_ref(const Views& v, const InstParams& P, int T)
+{
+    const int acc = 6 * T > P.nf + kPartHeader ? 6 * T : P.nf + kPartHeader;
+    return reinterpret_cast<float2*>(v.acc + ((acc + 3) & ~3));
+}
+
+// Optional terminal cost of the state after the last step: w_T sum_c Q_c
+// (x_H - x^r_{H-1})^2.
+__device__ __forceinline__ float terminal_cost(const InstParams& P, const float x[12], const float* xr)
+{
+    float r = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const float e = __fsub_rn(x[c], xr[c]);
+        r = __fmaf_rn(__fmul_rn(P.Q[c], e), e, r);
+    }
+    return __fmul_rn(P.w_terminal, r);
+}
+
+// Step-frequency regulariser rho (q / 1000 - f_n)^2 (Sec. V).
+__device__ __forceinline__ float freq_regulariser(const InstParams& P, uint32_t q)
+{
+    const float d = __fsub_rn(__fdiv_rn((float)q, 1000.0f), P.f_nominal);
+    return __fmul_rn(__fmul_rn(P.rho, d), d);
+}
+
 // ---------------------------------------------------------------------------
 // One tile of T samples.  NP = 0: per-step forces; NP > 0: NP spline knots.
 // EXT: the launch may hold controllers with the extended model features: a
@@ -473,8 +547,8 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int c = 4 * q + i;
-                    e[c] = sv[i] * e[c];  // deviation sigma * eps
-                    G[c] = mv[i] + e[c];
+                    e[c] = __fmul_rn(sv[i], e[c]);  // deviation sigma * eps
+                    G[c] = __fadd_rn(mv[i], e[c]);
                 }
             }
             if (valid) {
@@ -549,20 +623,8 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             srbd_step(P, x, G, fe, live);
         }
     }
-    if (P.w_terminal > 0.0f) {  // optional terminal cost of the state after the last step
-        const float* xr = v.xr + 12 * (P.H - 1);
-        float r = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            const float e = x[c] - xr[c];
-            r = fmaf(P.Q[c] * e, e, r);
-        }
-        kahan_add(J, Jc, P.w_terminal * r);
-    }
-    if (P.adaptive || P.n_freq > 0) {
-        const float d = (float)q / 1000.0f - P.f_nominal;
-        kahan_add(J, Jc, P.rho * d * d);
-    }
+    if (P.w_terminal > 0.0f) kahan_add(J, Jc, terminal_cost(P, x, v.xr + 12 * (P.H - 1)));
+    if (P.adaptive || P.n_freq > 0) kahan_add(J, Jc, freq_regulariser(P, q));
     if (!isfinite(J)) J = kInf;
     if (valid) {
         t.ws.J[k] = J;
@@ -716,42 +778,284 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         row[4] = a3;
     }
 
-    // ---- hierarchical combine: the last tile of a group of kGroup tiles combines
-    // the group's rows in tile order; the last group combines the group rows.
-    const int g = tile / kGroup;
-    const int gsize = min(kGroup, P.ntiles - g * kGroup);
-    unsigned* counters = t.ws.counters;
-    __threadfence();
+    tile_combine(sh, v, tile);
+}
+
+// ---------------------------------------------------------------------------
+// One tile of T samples with two samples per thread: the per-step policy on the
+// ordinary model (no spline, no extended feature).  Thread i of the T / 2
+// threads carries samples i and i + T / 2 of the tile as the two lanes of float2
+// values, so the FP32 arithmetic of the model step, the stage cost, Box-Muller
+// and the Kahan sum issues as packed FP32x2 instructions; the Philox rounds, the
+// transcendentals and the stores stay per sample.  Every sample sees the same
+// operations in the same order as in rollout_tile<0, false>, and the tile's
+// reductions run over the same samples in the same order (virtual warp
+// s (T / 64) + w holds samples 32 (s (T / 64) + w) ..), so the results are
+// bit-identical to the one-sample-per-thread launch on the same tile.
+// ---------------------------------------------------------------------------
+__device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
+{
+    using L = Lane<float2>;
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int T2 = blockDim.x, T = 2 * T2, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw2 = T2 >> 5;
+    const Views v = carve(dyn, P.H, 0, P.nf, T, P.nb);
+    float2* xr2 = pair_ref(v, P, T);  // the reference rows as duplicated pairs
+    stage(sh, v, 0);
+    for (int i = tid; i < 12 * P.H; i += T2) xr2[i] = make_float2(v.xr[i], v.xr[i]);
+    fill_pair_consts(sh.pc, P, sh.fe);
     __syncthreads();
-    if (tid == 0) {
-        const unsigned prev = atomicAdd(&counters[g], 1u);
-        sh.last = prev == (unsigned)gsize - 1u;
+    const Consts<float2> Kc{sh.pc};
+
+    const int K = P.K;
+    const uint32_t seed = P.seed, ctrl = P.ctrl;
+    const uint64_t iter = t.iter;
+    float* theta = t.ws.theta;
+    uint32_t k[2], q[2];
+    bool valid[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        k[l] = (uint32_t)tile * (uint32_t)T + (uint32_t)(l * T2 + tid);
+        valid[l] = k[l] < (uint32_t)K;
+        q[l] = P.adaptive ? sample_freq(k[l], iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max) : P.q_init;
     }
-    __syncthreads();
-    if (!sh.last) return;
-    __threadfence();
-    float* comb = v.acc;  // nf + kPartHeader floats (blockDim >= 64 leaves room)
-    const float* src_rows = t.ws.part + (size_t)g * kGroup * PS;
-    combine_rows(sh, src_rows, gsize, PS, P.nf, P.inv_lambda, comb);
-    if (P.ngroups > 1) {
-        float* grow = t.ws.gpart + (size_t)g * PS;
-        for (int i = tid; i < PS; i += T) grow[i] = comb[i];
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            counters[g] = 0u;
-            const unsigned prev = atomicAdd(&counters[P.ngroups], 1u);
-            sh.last = prev == (unsigned)P.ngroups - 1u;
+    const float* mu = v.mu;
+    const float* sd = v.sd;
+
+    float2 x[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) x[c] = L::bc(sh.x0[c]);
+    const float2 fe[3] = {sh.pc.fe[0], sh.pc.fe[1], sh.pc.fe[2]};
+    const bool uniform_q = !P.adaptive;
+    uint32_t ph[2][4], step[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        step[l] = q[l] * P.dt_us;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t p0 = t.phase0 + t.offset[i];
+            ph[l][i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
+        }
+    }
+    const uint32_t duty = t.duty;
+
+    float2 J = L::bc(0.0f), Jc = L::bc(0.0f);
+    const PhiloxPre pp0 = philox_pre(k[0], iter, seed, ctrl), pp1 = philox_pre(k[1], iter, seed, ctrl);
+    for (int j = 0; j < P.H; ++j) {
+        float2 z[12];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const uint4 w[2] = {philox_draw(pp0, 1u + 2u * (uint32_t)j + (uint32_t)d),
+                                philox_draw(pp1, 1u + 2u * (uint32_t)j + (uint32_t)d)};
+            normals6_v<float2>(w, z + 6 * d);
+        }
+        // deviations sigma * eps per sample (stored whole, 48 B per sample), forces
+        // mean + deviation as lane pairs
+        float eA[12], eB[12];
+        float2 G[12];
+        const float4* m4 = reinterpret_cast<const float4*>(mu + 12 * j);  // 16-byte aligned rows
+        const float4* s4 = reinterpret_cast<const float4*>(sd + 12 * j);
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) {
+            const float4 ma = m4[qq], sa = s4[qq];
+            const float mv[4] = {ma.x, ma.y, ma.z, ma.w}, sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = 4 * qq + i;
+                eA[c] = __fmul_rn(sv[i], z[c].x);
+                eB[c] = __fmul_rn(sv[i], z[c].y);
+                G[c] = make_float2(__fadd_rn(mv[i], eA[c]), __fadd_rn(mv[i], eB[c]));
+            }
+        }
+        if (valid[0]) {
+            float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[0]) * 12);
+            o[0] = make_float4(eA[0], eA[1], eA[2], eA[3]);
+            o[1] = make_float4(eA[4], eA[5], eA[6], eA[7]);
+            o[2] = make_float4(eA[8], eA[9], eA[10], eA[11]);
+        }
+        if (valid[1]) {
+            float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[1]) * 12);
+            o[0] = make_float4(eB[0], eB[1], eB[2], eB[3]);
+            o[1] = make_float4(eB[4], eB[5], eB[6], eB[7]);
+            o[2] = make_float4(eB[8], eB[9], eB[10], eB[11]);
+        }
+        // stance: legs in swing on every sample of the warp skip their terms; swing
+        // forces are zeroed where a leg is live on the warp but swings on a sample
+        unsigned st[2], live, all;
+        if (uniform_q) {
+            st[0] = st[1] = live = all = sh.sched[j];
+        } else {
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                st[l] = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    st[l] |= (ph[l][i] < duty ? 1u : 0u) << i;
+                    ph[l][i] += step[l];
+                    if (ph[l][i] >= kPhaseOne) ph[l][i] -= kPhaseOne;
+                }
+            }
+            live = __reduce_or_sync(kFull, st[0] | st[1]);
+            all = __reduce_and_sync(kFull, st[0] & st[1]);
+        }
+        if (live != all) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!(st[0] & (1u << i))) G[3 * i].x = G[3 * i + 1].x = G[3 * i + 2].x = 0.0f;
+                if (!(st[1] & (1u << i))) G[3 * i].y = G[3 * i + 1].y = G[3 * i + 2].y = 0.0f;
+            }
+        }
+        kahan_add_v<float2>(J, Jc, stage_cost_v<float2>(Kc, x, xr2 + 12 * j, G, live, true));
+        srbd_step_v<float2>(Kc, x, G, fe, live);
+    }
+    float Jv[2] = {J.x, J.y}, Jcv[2] = {Jc.x, Jc.y};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        if (P.w_terminal > 0.0f) {
+            float xl[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) xl[c] = L::get(x[c], l);
+            kahan_add(Jv[l], Jcv[l], terminal_cost(P, xl, v.xr + 12 * (P.H - 1)));
+        }
+        if (P.adaptive) kahan_add(Jv[l], Jcv[l], freq_regulariser(P, q[l]));
+        if (!isfinite(Jv[l])) Jv[l] = kInf;
+        if (valid[l]) {
+            t.ws.J[k[l]] = Jv[l];
+            t.ws.q[k[l]] = (int32_t)q[l];
+        }
+    }
+    if (t.ws.hist) {
+        // histograms of the top 16 and top 8 key bits for a large elite selection
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const uint32_t bin = cost_key(Jv[l]) >> 16;
+            const unsigned act = __ballot_sync(kFull, valid[l]);
+            if (valid[l]) {
+                const unsigned peers = __match_any_sync(act, bin);
+                if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
+                const unsigned peers8 = __match_any_sync(act, bin >> 8);
+                if (lane == __ffs(peers8) - 1) atomicAdd(t.ws.hist + kHistBins + (bin >> 8), (unsigned)__popc(peers8));
+            }
+        }
+    }
+    if (t.ws.best) {
+        // Naive: the best finite (cost, index) of the one force block
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const bool fin = valid[l] && Jv[l] < kInf;
+            unsigned long long m = fin ? ~(((unsigned long long)cost_key(Jv[l]) << 32) | k[l]) : 0ull;
+            if (__any_sync(kFull, fin)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long xo = __shfl_xor_sync(kFull, m, o);
+                    m = xo > m ? xo : m;
+                }
+                if (lane == 0) atomicMax(t.ws.best, m);
+            }
+            const unsigned nfw = __popc(__ballot_sync(kFull, fin));
+            if (lane == 0 && nfw) atomicAdd(t.ws.nfin, nfw);
+        }
+    }
+    if (!t.partials) return;
+
+    // ---- MPPI partial sums of this tile, shifted by the tile's best cost
+    bool fin[2];
+    fin[0] = valid[0] && Jv[0] < kInf;
+    fin[1] = valid[1] && Jv[1] < kInf;
+    const float mt = block_min(sh, fminf(fin[0] ? Jv[0] : kInf, fin[1] ? Jv[1] : kInf));
+    float w[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        w[l] = (fin[l] && mt < kInf) ? expf(-(Jv[l] - mt) * P.inv_lambda) : 0.0f;
+        const float f = (float)q[l] / 1000.0f;
+        const float s0 = warp_sum(w[l]), s1 = warp_sum(w[l] * w[l]), s2 = warp_sum(w[l] * f),
+                    s3 = warp_sum(fin[l] ? 1.0f : 0.0f);
+        if (lane == 0) {
+            float* r = sh.red[l * nw2 + warp];
+            r[0] = s0;
+            r[1] = s1;
+            r[2] = s2;
+            r[3] = s3;
+        }
+    }
+    const int PS = P.part_stride;
+    float* row = t.ws.part + (size_t)tile * PS;
+    {
+        // the tile's samples of nonzero weight listed in sample order, then one
+        // float4 column of the row per thread over a slice of the list (as in
+        // rollout_tile)
+        float2* lst = reinterpret_cast<float2*>(v.acc);
+        unsigned nzb[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            nzb[l] = __ballot_sync(kFull, w[l] != 0.0f);
+            if (lane == 0) sh.wtot[l * nw2 + warp] = __popc(nzb[l]);
         }
         __syncthreads();
-        if (!sh.last) return;
-        __threadfence();
-        combine_rows(sh, t.ws.gpart, P.ngroups, PS, P.nf, P.inv_lambda, comb);
-        if (tid == 0) counters[P.ngroups] = 0u;
-    } else if (tid == 0) {
-        counters[g] = 0u;
+        const int nw = 2 * nw2;
+        int pos[2] = {0, 0}, nnz = 0;
+        for (int g = 0; g < nw; ++g) {
+            const int c = sh.wtot[g];
+            pos[0] += g < warp ? c : 0;
+            pos[1] += g < nw2 + warp ? c : 0;
+            nnz += c;
+        }
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+            if (w[l] != 0.0f)
+                lst[pos[l] + __popc(nzb[l] & ((1u << lane) - 1u))] = make_float2(w[l], __int_as_float(l * T2 + tid));
+        __syncthreads();
+        const int ncol = 3 * P.H;
+        const int nsl = ncol < T ? T / ncol : 1;
+        float4* slice_sum = reinterpret_cast<float4*>(v.acc + 2 * T);
+        const float4* th4 = reinterpret_cast<const float4*>(theta) + (size_t)tile * T * 3;
+        float4* row4 = reinterpret_cast<float4*>(row + kPartHeader);
+        for (int it = tid; it < nsl * ncol; it += T2) {
+            const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
+            const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 4
+            for (int e = sl; e < nnz; e += nsl) {
+                const float2 we = lst[e];
+                const float4 d = src[3 * __float_as_int(we.y)];
+                a.x = fmaf(we.x, d.x, a.x);
+                a.y = fmaf(we.x, d.y, a.y);
+                a.z = fmaf(we.x, d.z, a.z);
+                a.w = fmaf(we.x, d.w, a.w);
+            }
+            if (nsl == 1) row4[c] = a;
+            else slice_sum[it] = a;
+        }
+        if (nsl > 1) {
+            __syncthreads();
+            for (int c = tid; c < ncol; c += T2) {
+                float4 a = slice_sum[c];
+                for (int sl = 1; sl < nsl; ++sl) {
+                    const float4 b = slice_sum[sl * ncol + c];
+                    a.x += b.x;
+                    a.y += b.y;
+                    a.z += b.z;
+                    a.w += b.w;
+                }
+                row4[c] = a;
+            }
+        }
     }
-    mppi_finish(sh, v, comb, t.mppi_to_state != 0);
+    if (tid == 0) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int ww = 0; ww < 2 * nw2; ++ww) {
+            a0 += sh.red[ww][0];
+            a1 += sh.red[ww][1];
+            a2 += sh.red[ww][2];
+            a3 += sh.red[ww][3];
+        }
+        row[0] = mt;
+        row[1] = a0;
+        row[2] = a1;
+        row[3] = a2;
+        row[4] = a3;
+    }
+    tile_combine(sh, v, tile);
 }
 
 // Cost of an order-preserving key (inverse of cost_key).
@@ -1400,6 +1704,18 @@ __global__ void __launch_bounds__(SBS_MAX_TILE, 4) k_rollout_lean(const InstPara
     rollout_plain<0, false>(dP, t);
 }
 
+// Two samples per thread (per-step policy, ordinary model): T / 2 threads per
+// tile of T samples, at most 128 registers.
+__global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_rollout_pair(const InstParams* __restrict__ dP, TickArgs t)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    load_params(dP, sh);
+    if (threadIdx.x == 0) sh.t = t;
+    __syncthreads();
+    rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
+}
+
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
 {
     extern __shared__ float4 dyn4[];
@@ -1542,6 +1858,42 @@ __global__ void __launch_bounds__(SBS_MAX_TILE, 4) k_grid_rollout_lean(const Ins
                                                                        const int* __restrict__ counts)
 {
     rollout_grid_item<0, false>(recs, counts);
+}
+
+// The same with two samples per thread (T / 2 threads per tile item).
+__global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_grid_rollout_pair(const InstRec* __restrict__ recs,
+                                                                           const int* __restrict__ counts)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    const int it = blockIdx.x + counts[4];
+    if (it >= counts[1]) return;
+    const int i = find_rec_block(sh, recs, counts[0], it, 0);
+    load_params(recs[i].dP, sh);
+    load_tick(&recs[i].t, sh);
+    __syncthreads();
+    rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+}
+
+// Persistent blocks pulling tile items, two samples per thread.
+__global__ void __launch_bounds__(SBS_MAX_TILE / 2) k_batch_rollout_pair(const InstRec* __restrict__ recs,
+                                                                         const int* __restrict__ counts, int* heads)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    const int n = counts[0], nitems = counts[1];
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&heads[0], 1);
+        __syncthreads();
+        const int it = sh.item;
+        if (it >= nitems) break;
+        const int i = find_rec(recs, n, it, 0);
+        load_params(recs[i].dP, sh);
+        load_tick(&recs[i].t, sh);
+        __syncthreads();
+        rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* __restrict__ recs,
@@ -1906,12 +2258,17 @@ static const void* batch_rollout_fn_s(int P, int mode)
 
 static const void* rollout_kernel(int variant)
 {
+    if (variant & kPairVariant) return (variant == kPairVariant) ? (const void*)k_rollout_pair : nullptr;
     const int P = variant & ~kExtVariant;
     return (variant & kExtVariant) ? rollout_kernel_s<true>(P) : rollout_kernel_s<false>(P);
 }
 
 const void* batch_rollout_fn(int variant, int mode)
 {
+    if (variant & kPairVariant) {
+        if (variant != kPairVariant) return nullptr;
+        return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair : (const void*)k_batch_rollout_pair;
+    }
     const int P = variant & ~kExtVariant;
     return (variant & kExtVariant) ? batch_rollout_fn_s<true>(P, mode) : batch_rollout_fn_s<false>(P, mode);
 }
@@ -1933,17 +2290,20 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
     return status_of(cudaGetLastError());
 }
 
-int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
+int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream, int spt)
 {
-    const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb);
-    const void* fn = rollout_kernel(rollout_variant(hP.P, hP.n_freq > 0 || hP.world_feet || hP.friction_project));
+    const bool ext = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
+    const bool pair = spt == 2 && pair_capable(hP.P, ext, hP.T);
+    const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb, pair);
+    const void* fn = rollout_kernel(rollout_variant(hP.P, ext, pair));
     if (!fn) return SBS_ERR_INVALID_ARG;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;
     TickArgs targ = t;
     const InstParams* parg = dP;
     void* args[] = {(void*)&parg, (void*)&targ};
-    return status_of(cudaLaunchKernel(fn, dim3(hP.ntiles), dim3(hP.T), args, smem, (cudaStream_t)stream));
+    return status_of(
+        cudaLaunchKernel(fn, dim3(hP.ntiles), dim3(pair ? hP.T / 2 : hP.T), args, smem, (cudaStream_t)stream));
 }
 
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)

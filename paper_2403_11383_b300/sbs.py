@@ -155,6 +155,9 @@ ABI = {
     "sbs_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                      C.c_void_p]),
     "sbs_batch_stage_ms": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sbs_batch_set_samples_per_thread": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_batch_get_samples_per_thread": (C.c_int, [C.c_void_p]),
+    "sbs_set_samples_per_thread": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_sqrt_hw": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -313,6 +316,11 @@ class Controller:
     def device_bytes(self) -> int:
         return lib().sbs_device_bytes(self._h)
 
+    def set_samples_per_thread(self, spt: int):
+        """1, 2, or 0 (default, one): samples each rollout thread of a plain solve
+        carries (same results)."""
+        check(lib().sbs_set_samples_per_thread(self._h, spt), "sbs_set_samples_per_thread")
+
     def prepare(self):
         """Allocate the plain-solve workspace now."""
         check(lib().sbs_prepare(self._h), "sbs_prepare")
@@ -444,6 +452,13 @@ class Batch:
 
     def set_profiling(self, on: bool):
         check(lib().sbs_batch_set_profiling(self._b, 1 if on else 0), "sbs_batch_set_profiling")
+
+    def set_samples_per_thread(self, spt: int):
+        """1, 2, or 0 (default, one): samples each rollout thread carries (same results)."""
+        check(lib().sbs_batch_set_samples_per_thread(self._b, spt), "sbs_batch_set_samples_per_thread")
+
+    def samples_per_thread(self) -> int:
+        return lib().sbs_batch_get_samples_per_thread(self._b)
 
     def stage_ms(self):
         """(rollout, selection, refit) milliseconds of the last profiled tick."""

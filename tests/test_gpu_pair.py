@@ -1,0 +1,135 @@
+"""Two samples per thread (packed FP32x2 arithmetic) against one: every result,
+cost, frequency, elite list and distribution is bit-identical, in plain solves
+over warm-started ticks and in batched ticks of both launch modes."""
+import numpy as np
+import pytest
+
+from paper_2403_11383_b300 import sbs as S
+from paper_2403_11383_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    S.lib()
+    return torch
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+
+
+def _outputs(ctl, cfg):
+    out = {"mean": ctl.read(S.BUF_MEAN).cpu().numpy(), "var": ctl.read(S.BUF_VAR).cpu().numpy(),
+           "J": ctl.read(S.BUF_COST).cpu().numpy(), "q": ctl.read(S.BUF_FREQ).cpu().numpy()}
+    if cfg["method"] != "mppi":
+        out["elite"] = ctl.read(S.BUF_ELITE).cpu().numpy()
+    if cfg.get("compare_mppi"):
+        out["mppi"] = ctl.read(S.BUF_MPPI_MEAN).cpu().numpy()
+    return out
+
+
+CASES = {
+    "mppi_k3001_t64": dict(K=3001, H=12, tile=64),
+    "mppi_k40000_t128_groups": dict(K=40000, H=10, tile=128),
+    "mppi_adaptive_k5000_t256": dict(K=5000, H=25, tile=256, adaptive=True, gait="crawl"),
+    "elite_k4096_t128_adaptive_cmp": dict(K=4096, H=25, tile=128, method="elite", elite_count=205, adaptive=True,
+                                          compare_mppi=True),
+    "elite_k70000_hist_t256": dict(K=70000, H=8, tile=256, method="elite", elite_count=700),
+    "naive_k777_t64": dict(K=777, H=12, tile=64, method="naive"),
+    "mppi_terminal_fext_t128": dict(K=2000, H=20, tile=128, gait="pace", f_ext=(5.0, -8.0, 0.0)),
+    "mppi_h128_t256": dict(K=1500, H=128, dt_us=1000, tile=256),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_plain_solves_pair_equals_single(name):
+    import torch
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(CASES[name], seed=321)
+    if name == "mppi_terminal_fext_t128":
+        cfg["cost"] = dict(cfg["cost"], w_terminal=2.0)
+    prob = W.problem(cfg)
+    x0, xr, fe = _dev(prob["x0"]), _dev(prob["xref"]), _dev(prob["f_ext"])
+    a, b = S.Controller(cfg), S.Controller(cfg)
+    a.set_samples_per_thread(1)
+    b.set_samples_per_thread(2)
+    for tick in range(3):
+        g = dict(prob["gait"])
+        g["phase0"] = (g["phase0"] + tick * cfg["q_init"] * cfg["dt_us"]) % W.PHASE_ONE
+        ra = a.solve(x0, xr, g, fe, 0 if tick == 0 else 1).clone()
+        rb = b.solve(x0, xr, g, fe, 0 if tick == 0 else 1).clone()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
+        oa, ob = _outputs(a, cfg), _outputs(b, cfg)
+        for key in oa:
+            np.testing.assert_array_equal(oa[key], ob[key], err_msg=f"{name} tick {tick} {key}")
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("mode", [S.BATCH_GRID, S.BATCH_PERSISTENT])
+def test_batched_pair_equals_single(mode):
+    import torch
+    mix = W.batch_mix(12, seed=77)
+    for c, _ in mix:
+        c["tile"] = 128
+    sets = {1: [S.Controller(c) for c, _ in mix], 2: [S.Controller(c) for c, _ in mix]}
+    tens = [(_dev(p["x0"]), _dev(p["xref"]), _dev(p["f_ext"])) for _, p in mix]
+    n = len(mix)
+    res = {}
+    batches = {}
+    for spt in (1, 2):
+        b = S.Batch(n, sum(c.workspace_bytes() + 256 for c in sets[spt]))
+        b.set_mode(mode)
+        b.set_samples_per_thread(spt)
+        assert b.samples_per_thread() == spt
+        batches[spt] = b
+        res[spt] = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(3):
+        for spt in (1, 2):
+            probs = [sets[spt][i].problem(tens[i][0], tens[i][1], mix[i][1]["gait"], tens[i][2],
+                                          0 if tick == 0 else 1) for i in range(n)]
+            batches[spt].solve(sets[spt], probs, res[spt])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(res[1].cpu().numpy(), res[2].cpu().numpy())
+        for i in range(n):  # a batched controller's costs stay in the batch's arena: compare its distribution
+            for which in (S.BUF_MEAN, S.BUF_VAR):
+                np.testing.assert_array_equal(sets[1][i].read(which).cpu().numpy(),
+                                              sets[2][i].read(which).cpu().numpy())
+    for b in batches.values():
+        b.close()
+
+
+def test_autotune_keeps_results():
+    # the autotuner may pick either sample count: the next tick equals a
+    # one-sample-per-thread batch's
+    import torch
+    mix = W.batch_mix(6, seed=78)
+    for c, _ in mix:
+        c["tile"] = 256
+    ta = [S.Controller(c) for c, _ in mix]
+    tb = [S.Controller(c) for c, _ in mix]
+    tens = [(_dev(p["x0"]), _dev(p["xref"]), _dev(p["f_ext"])) for _, p in mix]
+    n = len(mix)
+    ba = S.Batch(n, sum(c.workspace_bytes() + 256 for c in ta))
+    bb = S.Batch(n, sum(c.workspace_bytes() + 256 for c in tb))
+    bb.set_samples_per_thread(1)
+    ra = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rb = torch.empty_like(ra)
+    pa = [ta[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 1) for i in range(n)]
+    pb = [tb[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 1) for i in range(n)]
+    ba.autotune(ta, pa, ra, ticks=2)  # 2 modes x 2 sample counts x (1 + 2) ticks, real solves
+    assert ba.samples_per_thread() in (1, 2)
+    for _ in range(2 * 2 * 3):
+        bb.solve(tb, pb, rb)
+    ba.solve(ta, pa, ra)
+    bb.solve(tb, pb, rb)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
+    ba.close()
+    bb.close()
