@@ -514,6 +514,7 @@ def main():
     tune_ms = batch.autotune(ctls, probs1, results, ticks=5)
     mode = "grid" if batch.mode() == S.BATCH_GRID else "persistent"
     spt = batch.samples_per_thread() or 1
+    theta = "regenerate" if batch.theta_mode() == S.THETA_REGENERATE else "store"
     for _ in range(3):  # rebuild the tick graphs in the chosen mode before timing
         tick()
     torch.cuda.synchronize()
@@ -650,9 +651,11 @@ def main():
             "config": {"workload": WORKLOAD, "instances": n, "sample_steps_per_tick": ss_tick,
                        "tile": tile, "tile_autotune_ms_per_tick": tile_ms, "graph": True, "launch_mode": mode,
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
-                       "samples_per_thread": spt,
-                       "l2": "per-tick working set above L2 (sampled deviations "
-                       f"{arena / 1e9:.2f} GB)", "workspace_bytes": 2 * arena, "parallelism": f"replicas x{world}"},
+                       "samples_per_thread": spt, "sampled_deviations": theta,
+                       "l2": "per-tick working set above L2 (workspace of the 256 controllers "
+                       f"{arena / 1e9:.2f} GB; with stored deviations every tick writes "
+                       f"{48 * ss_tick / 1e9:.2f} GB of them)", "workspace_bytes": 2 * arena,
+                       "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
             "latency_ms": {"p50": p50, "p99": p99, "ticks": len(lat),
                            "kind": f"device time of one {len(mix)}-controller tick"},

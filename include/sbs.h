@@ -360,11 +360,27 @@ int sbs_batch_get_samples_per_thread(const sbs_batch* b);
  * one sample per thread. */
 int sbs_set_samples_per_thread(sbs_handle* h, int spt);
 
+/* Sampled deviations (Alg. 1 Sampling): the update needs sigma * eps of the
+ * samples it weights or selects.  SBS_THETA_STORE (the default): the rollout
+ * writes every sample's deviations (48 bytes per sample-step, step-major) to
+ * the workspace and the update reads them.  SBS_THETA_REGENERATE: nothing is
+ * written; the MPPI tile sums and the elite / Naive refit regenerate the
+ * deviations of the samples they use from the same Philox counters, with the
+ * same operations.  Results are bit for bit the same either way; regeneration
+ * trades the stores for Philox and Box-Muller work proportional to the samples
+ * of nonzero MPPI weight and the elites.  sbs_batch_autotune measures both. */
+#define SBS_THETA_STORE 0
+#define SBS_THETA_REGENERATE 1
+int sbs_set_theta_mode(sbs_handle* h, int mode);
+int sbs_batch_set_theta_mode(sbs_batch* b, int mode);
+int sbs_batch_get_theta_mode(const sbs_batch* b);
+
 /* Autotuner: runs `ticks` profiled ticks in each launch mode, with one and (where
- * the launch can take them) two samples per thread, on these controllers and
- * problems (real solves: they advance the controllers), keeps the setting with
- * the shortest mean tick and reports each mode's best mean tick time in
- * ms_out[0] (grid) and ms_out[1] (persistent). */
+ * the launch can take them) two samples per thread, storing and regenerating the
+ * sampled deviations, on these controllers and problems (real solves: they
+ * advance the controllers), keeps the setting with the shortest mean tick and
+ * reports each mode's best mean tick time in ms_out[0] (grid) and ms_out[1]
+ * (persistent). */
 int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                        sbs_result* results, int ticks, float ms_out[2], void* stream);
 

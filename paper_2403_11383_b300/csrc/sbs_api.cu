@@ -459,6 +459,7 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         t.shift = it == 0 ? shift : 0;
         t.partials = (P.method == SBS_MPPI || (P.compare_mppi && it == 0)) ? 1 : 0;
         t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
+        t.regen = h->regen;
         t.result = res;
         t.ws = h->ws;
         st = launch_rollout(h->dP, P, t, stream, h->spt == 2 ? 2 : 1);
@@ -653,6 +654,7 @@ struct sbs_batch {
     cudaStream_t cstream;  // records copies of replayed ticks, ahead of the tick before
     sbs_batch_plan plan;
     int spt;               // samples per thread of the rollout: 0 (default: one) , 1 or 2
+    int regen;             // 1: the sampled deviations are regenerated by their readers, not stored
     // host-memory ticks (sbs_batch_solve_host): pinned staging of every
     // controller's inputs and results, and their device copies
     char* h_in = nullptr;
@@ -804,8 +806,8 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     int* heads = sl.heads;
     void* args[] = {(void*)&recs, (void*)&counts, (void*)&heads};
     void* args_b[] = {(void*)&recs, (void*)&counts_b, (void*)&heads};
-    const void* fns[4] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode),
-                          batch_rollout_fn(P, mode)};
+    const void* fns[4] = {batch_rollout_fn(P, mode), batch_select_fn(mode),
+                          batch_refit_fn(mode, (P & kRegenVariant) != 0), batch_rollout_fn(P, mode)};
     const int threads[4] = {T, kSelectThreads, kBatchRefitThreads, T};
     const size_t shm[4] = {smem, sel_smem, 0, smem};
     int least = 0, greatest = 0;
@@ -972,6 +974,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         R.t.shift = h->initialized ? probs[i].shift : 0;
         R.t.partials = (P.method == SBS_MPPI || P.compare_mppi) ? 1 : 0;
         R.t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
+        R.t.regen = b->regen;
         R.t.result = results + i;
         R.t.ws = ws_at(h->wsl, sl.arena + aoff, cnt);
         aoff += align_up(h->wsl.bytes, 256);
@@ -1009,7 +1012,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     if (sel_smem == 0) sel_smem = 256;
     const size_t used = kBatchHeader + (size_t)n * sizeof(InstRec);
     int grids[4];
-    const int var = rollout_variant(Pk, ext, pair);
+    const int var = rollout_variant(Pk, ext, pair, b->regen != 0);
     int st = batch_grid(var, mode, smem, sel_smem, RT, counts, grids);
     if (st) return st;
     grids[3] = split ? tile_begin - tiles_upd : 0;
@@ -1161,25 +1164,29 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
     const int nspt = pair_capable(handles[0]->hP.P, ext, handles[0]->hP.T) ? 2 : 1;
     const int modes[2] = {SBS_BATCH_GRID, SBS_BATCH_PERSISTENT};
     float best = 1e30f;
-    int best_mode = SBS_BATCH_GRID, best_spt = 1;
+    int best_mode = SBS_BATCH_GRID, best_spt = 1, best_regen = 0;
     for (int m = 0; m < 2 && st == SBS_OK; ++m) {
         b->mode = modes[m];
         ms_out[m] = 1e30f;
         for (int sp = 1; sp <= nspt && st == SBS_OK; ++sp) {
-            b->spt = sp;
-            double tot = 0.0;
-            for (int k = 0; k <= ticks && st == SBS_OK; ++k) {  // the first tick of a setting is a warm-up
-                st = sbs_batch_solve(b, n, handles, probs, results, stream);
-                float ms[3];
-                if (st == SBS_OK) st = sbs_batch_stage_ms(b, ms);
-                if (st == SBS_OK && k > 0) tot += (double)ms[0] + ms[1] + ms[2];
-            }
-            const float avg = (float)(tot / ticks);
-            if (st == SBS_OK && avg < ms_out[m]) ms_out[m] = avg;
-            if (st == SBS_OK && avg < best) {
-                best = avg;
-                best_mode = modes[m];
-                best_spt = sp;
+            for (int rg = 0; rg < 2 && st == SBS_OK; ++rg) {
+                b->spt = sp;
+                b->regen = rg;
+                double tot = 0.0;
+                for (int k = 0; k <= ticks && st == SBS_OK; ++k) {  // the first tick of a setting is a warm-up
+                    st = sbs_batch_solve(b, n, handles, probs, results, stream);
+                    float ms[3];
+                    if (st == SBS_OK) st = sbs_batch_stage_ms(b, ms);
+                    if (st == SBS_OK && k > 0) tot += (double)ms[0] + ms[1] + ms[2];
+                }
+                const float avg = (float)(tot / ticks);
+                if (st == SBS_OK && avg < ms_out[m]) ms_out[m] = avg;
+                if (st == SBS_OK && avg < best) {
+                    best = avg;
+                    best_mode = modes[m];
+                    best_spt = sp;
+                    best_regen = rg;
+                }
             }
         }
     }
@@ -1187,6 +1194,26 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
     if (st) return st;
     b->mode = best_mode;
     b->spt = best_spt;
+    b->regen = best_regen;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_set_theta_mode(sbs_batch* b, int mode)
+{
+    if (!b || (mode != SBS_THETA_STORE && mode != SBS_THETA_REGENERATE)) return SBS_ERR_INVALID_ARG;
+    b->regen = mode == SBS_THETA_REGENERATE ? 1 : 0;
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_get_theta_mode(const sbs_batch* b)
+{
+    return b ? (b->regen ? SBS_THETA_REGENERATE : SBS_THETA_STORE) : SBS_ERR_INVALID_ARG;
+}
+
+extern "C" int sbs_set_theta_mode(sbs_handle* h, int mode)
+{
+    if (!h || (mode != SBS_THETA_STORE && mode != SBS_THETA_REGENERATE)) return SBS_ERR_INVALID_ARG;
+    h->regen = mode == SBS_THETA_REGENERATE ? 1 : 0;
     return SBS_OK;
 }
 

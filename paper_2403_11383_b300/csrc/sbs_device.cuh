@@ -363,6 +363,61 @@ __device__ __forceinline__ void normals12(const PhiloxPre& pp, int j, float e[12
     for (int d = 0; d < 2; ++d) normals6(philox_draw(pp, 1u + 2u * (uint32_t)j + (uint32_t)d), e + 6 * d);
 }
 
+// Regeneration of the sampled deviations sigma * eps (for readers of a solve that
+// did not store them): the same draws and the same operations as the rollout,
+// so the same bits.  Force normal c of step (or knot) j comes from draw
+// 1 + 2 j + (c >= 6), slot s = c mod 6: Box-Muller pair s / 2 of that draw's six
+// 21-bit integers, its cosine output for even s and sine output for odd s.
+__device__ __forceinline__ float2 draw_pair(uint4 w, int p)
+{
+    uint32_t a, b;
+    if (p == 0) {
+        a = w.x >> 11;
+        b = w.y >> 11;
+    } else if (p == 1) {
+        a = w.z >> 11;
+        b = w.w >> 11;
+    } else {
+        a = ((w.x & 0x7ffu) << 10) | (w.y & 0x3ffu);
+        b = ((w.z & 0x7ffu) << 10) | (w.w & 0x3ffu);
+    }
+    return box_muller21(a, b);
+}
+
+// Deviations 4 qd .. 4 qd + 3 of sample k at step j (sd4: their standard
+// deviations).  Quads 0 and 2 lie in one draw each, quad 1 spans both.
+__device__ __forceinline__ float4 regen_quad(uint32_t k, int j, int qd, uint64_t iter, uint32_t seed, uint32_t ctrl,
+                                             float4 sd4)
+{
+    const uint32_t dA = 1u + 2u * (uint32_t)j;
+    const uint4 ctr = make_uint4(k, qd == 2 ? dA + 1u : dA, (uint32_t)iter, (uint32_t)(iter >> 32));
+    const uint4 w0 = philox4x32_10(ctr, seed, ctrl);
+    float2 p0, p1;
+    if (qd == 0) {
+        p0 = draw_pair(w0, 0);
+        p1 = draw_pair(w0, 1);
+    } else if (qd == 2) {
+        p0 = draw_pair(w0, 1);
+        p1 = draw_pair(w0, 2);
+    } else {
+        const uint4 w1 = philox4x32_10(make_uint4(k, dA + 1u, (uint32_t)iter, (uint32_t)(iter >> 32)), seed, ctrl);
+        p0 = draw_pair(w0, 2);
+        p1 = draw_pair(w1, 0);
+    }
+    return make_float4(__fmul_rn(sd4.x, p0.x), __fmul_rn(sd4.y, p0.y), __fmul_rn(sd4.z, p1.x),
+                       __fmul_rn(sd4.w, p1.y));
+}
+
+// All 12 deviations of sample k at step (or knot) j (sd12: their standard deviations).
+__device__ __forceinline__ void regen_row(uint32_t k, int j, uint64_t iter, uint32_t seed, uint32_t ctrl,
+                                          const float* sd12, float d[12])
+{
+    float e[12];
+    normals12(k, j, iter, seed, ctrl, e);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) d[c] = __fmul_rn(sd12[c], e[c]);
+}
+
 // Step frequency of sample k (Sec. IV-C): clip(mu_f + sigma_f z, f_min, f_max)
 // quantised to integer mHz.  The exact single-precision sequence (one fused
 // multiply-add, one multiply, one add, floor) defines the rounding.

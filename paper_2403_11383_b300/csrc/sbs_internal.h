@@ -89,6 +89,8 @@ struct TickArgs {
     uint64_t iter;       // Philox iteration counter
     int32_t partials;    // 1: this iteration forms MPPI partial sums
     int32_t mppi_to_state;  // 1: the MPPI combine is the update; 0: it goes to mppi_mean
+    int32_t regen;       // 1: the sampled deviations are not stored; their readers regenerate them
+    int32_t pad0;
     sbs_result* result;
     Workspace ws;
 };
@@ -101,7 +103,7 @@ struct InstRec {
     int32_t tile_begin;
     int32_t select_begin;
     int32_t refit_begin;
-    int32_t pad[3];
+    int32_t pad[1];
 };
 
 static_assert(sizeof(InstRec) % 16 == 0, "InstRec must be a multiple of 16 bytes");
@@ -202,10 +204,11 @@ void fill_params(const sbs_config* cfg, InstParams* out);
 // model feature (a discrete step-frequency set, stance feet fixed on the
 // ground).  The batched launchers take a variant where they say P.
 constexpr int kExtVariant = 256;
-constexpr int kPairVariant = 512;  // two samples per thread
-inline int rollout_variant(int P, bool ext, bool pair = false)
+constexpr int kPairVariant = 512;    // two samples per thread
+constexpr int kRegenVariant = 1024;  // deviations regenerated by the refit (not stored)
+inline int rollout_variant(int P, bool ext, bool pair = false, bool regen = false)
 {
-    return P | (ext ? kExtVariant : 0) | (pair ? kPairVariant : 0);
+    return P | (ext ? kExtVariant : 0) | (pair ? kPairVariant : 0) | (regen ? kRegenVariant : 0);
 }
 // Launches that can carry two samples per thread: the per-step policy on the
 // ordinary model, with tiles of a multiple of 64 samples (whole warps of pairs).
@@ -227,7 +230,7 @@ int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int*
 int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int counts[4], int grids[3]);
 const void* batch_rollout_fn(int P, int mode);
 const void* batch_select_fn(int mode);
-const void* batch_refit_fn(int mode);
+const void* batch_refit_fn(int mode, bool regen);
 int launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream);
 int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
 int launch_sqrt_hw(const float* x, float* y, int n, void* stream);
@@ -258,6 +261,7 @@ struct sbs_handle {
     bool in_pending;
     uint64_t uid;          // creation number, unique over the process (a reused address gets a new one)
     int spt;               // samples per thread of plain solves: 0 (default: one), 1 or 2
+    int regen;             // 1: plain solves do not store the sampled deviations (readers regenerate them)
 };
 
 

@@ -49,7 +49,7 @@ struct __align__(16) BlockShared {
     int wtot[32], wtot2[32];
     int digit, below, count;
     unsigned char sched[SBS_MAX_H];  // stance legs of every step when all samples share the frequency
-    float mu12[12], vr12[12], dbar[12];
+    float mu12[12], vr12[12], dbar[12], sd12[12];
     float wacc[32][12];
     float wacc2[kRefitLanesMax / 32][12];
     PairConsts pc;  // model and cost constants as duplicated pairs (two samples per thread)
@@ -515,8 +515,8 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             if (p < NP) {
                 normals12(k, p, iter, seed, ctrl, e);
 #pragma unroll
-                for (int c = 0; c < 12; ++c) e[c] = sd[12 * p + c] * e[c];
-                if (valid) {
+                for (int c = 0; c < 12; ++c) e[c] = __fmul_rn(sd[12 * p + c], e[c]);
+                if (valid && !t.regen) {
                     float4* o = reinterpret_cast<float4*>(theta + ((size_t)p * K + k) * 12);
                     o[0] = make_float4(e[0], e[1], e[2], e[3]);
                     o[1] = make_float4(e[4], e[5], e[6], e[7]);
@@ -551,7 +551,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
                     G[c] = __fadd_rn(mv[i], e[c]);
                 }
             }
-            if (valid) {
+            if (valid && !t.regen) {
                 float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
                 o[0] = make_float4(e[0], e[1], e[2], e[3]);
                 o[1] = make_float4(e[4], e[5], e[6], e[7]);
@@ -708,11 +708,14 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         for (int it = tid; it < nsl * ncol; it += T) {
             const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
             const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
+            const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
             float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 4
             for (int e = sl; e < nnz; e += nsl) {
                 const float2 we = lst[e];
-                const float4 d = src[3 * __float_as_int(we.y)];
+                const int ke = __float_as_int(we.y);
+                const float4 d = t.regen ? regen_quad((uint32_t)(tile * T + ke), j, c - 3 * j, t.iter, P.seed, P.ctrl, sd4)
+                                         : src[3 * ke];
                 a.x = fmaf(we.x, d.x, a.x);
                 a.y = fmaf(we.x, d.y, a.y);
                 a.z = fmaf(we.x, d.z, a.z);
@@ -867,13 +870,13 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
                 G[c] = make_float2(__fadd_rn(mv[i], eA[c]), __fadd_rn(mv[i], eB[c]));
             }
         }
-        if (valid[0]) {
+        if (valid[0] && !t.regen) {
             float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[0]) * 12);
             o[0] = make_float4(eA[0], eA[1], eA[2], eA[3]);
             o[1] = make_float4(eA[4], eA[5], eA[6], eA[7]);
             o[2] = make_float4(eA[8], eA[9], eA[10], eA[11]);
         }
-        if (valid[1]) {
+        if (valid[1] && !t.regen) {
             float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[1]) * 12);
             o[0] = make_float4(eB[0], eB[1], eB[2], eB[3]);
             o[1] = make_float4(eB[4], eB[5], eB[6], eB[7]);
@@ -1013,11 +1016,14 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
         for (int it = tid; it < nsl * ncol; it += T2) {
             const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
             const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
+            const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
             float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 4
             for (int e = sl; e < nnz; e += nsl) {
                 const float2 we = lst[e];
-                const float4 d = src[3 * __float_as_int(we.y)];
+                const int ke = __float_as_int(we.y);
+                const float4 d = t.regen ? regen_quad((uint32_t)(tile * T + ke), j, c - 3 * j, t.iter, P.seed, P.ctrl, sd4)
+                                         : src[3 * ke];
                 a.x = fmaf(we.x, d.x, a.x);
                 a.y = fmaf(we.x, d.y, a.y);
                 a.z = fmaf(we.x, d.z, a.z);
@@ -1496,6 +1502,7 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
 // and the reported frequency come from the block of the overall best (the first
 // block when no cost is finite).
 // ---------------------------------------------------------------------------
+template <bool REGEN>
 __device__ void naive_refit(BlockShared& sh, int j)
 {
     const InstParams& P = sh.P;
@@ -1513,7 +1520,20 @@ __device__ void naive_refit(BlockShared& sh, int j)
         float m, var;
         shifted_entry(P, t, sm, sv, idx, m, var);
         const int kb = diverged ? -1 : __ldcg(t.ws.elite + blk);
-        if (kb >= 0) m += __ldcg(t.ws.theta + ((size_t)j * P.K + kb) * 12 + c);
+        if (kb >= 0) {
+            float d;
+            if (REGEN) {  // the winner's deviation, regenerated (its block's standard deviation)
+                float e[12];
+                normals12((uint32_t)kb, j, t.iter, P.seed, P.ctrl, e);
+                float ec = e[0];
+#pragma unroll
+                for (int i = 1; i < 12; ++i) ec = i == c ? e[i] : ec;  // no local-memory indexing
+                d = __fmul_rn(sqrtf(var), ec);
+            } else {
+                d = __ldcg(t.ws.theta + ((size_t)j * P.K + kb) * 12 + c);
+            }
+            m += d;
+        }
         dm[idx] = m;
         dv[idx] = var;
         if (j == 0 && blk == bstar) {
@@ -1534,6 +1554,7 @@ __device__ void naive_refit(BlockShared& sh, int j)
 // var = mean((d - mean(d))^2) floored (Alg. 1 Update, two passes); Naive
 // (Alg. 3): the best sample, variance kept.
 // ---------------------------------------------------------------------------
+template <bool REGEN>
 __device__ void refit_block(BlockShared& sh, int b)
 {
     const InstParams& P = sh.P;
@@ -1550,7 +1571,7 @@ __device__ void refit_block(BlockShared& sh, int b)
     sbs_result* r = t.result;
     const bool diverged = __ldcg(&r->status) != SBS_OK;
     if (b < P.nt && P.method == SBS_NAIVE) {
-        naive_refit(sh, b);
+        naive_refit<REGEN>(sh, b);
         return;
     }
     if (b < P.nt) {
@@ -1559,10 +1580,21 @@ __device__ void refit_block(BlockShared& sh, int b)
             shifted_entry(P, t, sm, sv, 12 * b + tid, m, var);
             sh.mu12[tid] = m;
             sh.vr12[tid] = var;
-        } else if (tid >= 32 && tid < 44 && !diverged) {  // the first elite's deviation, alongside
+        } else if (tid >= 32 && tid < 44 && !diverged && !REGEN) {  // the first elite's deviation, alongside
             sh.dbar[tid - 32] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + (tid - 32));
         }
         __syncthreads();
+        if (REGEN && !diverged) {  // deviations not stored: regenerated from their draws
+            if (tid < 12) sh.sd12[tid] = sqrtf(sh.vr12[tid]);
+            __syncthreads();
+            if (tid == 0) {
+                float d[12];
+                regen_row((uint32_t)__ldcg(elite), b, t.iter, P.seed, P.ctrl, sh.sd12, d);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) sh.dbar[c] = d[c];
+            }
+            __syncthreads();
+        }
         float mean_c = 0.0f, var_c = 0.0f;  // valid in threads < 12
         if (diverged) {
             if (tid < 12) {
@@ -1581,19 +1613,33 @@ __device__ void refit_block(BlockShared& sh, int b)
 #pragma unroll
                 for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
                 int kb = vl < Ke ? __ldcg(elite + vl) : 0;
-                for (int e = vl; e < Ke; e += V) {
-                    // the next elite's index is loaded before this one's row is used
-                    const int kn = e + V < Ke ? __ldcg(elite + e + V) : 0;
-                    const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
-                    const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
-                    const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
+                if (REGEN) {  // deviations regenerated from their draws
+                    for (int e = vl; e < Ke; e += V) {
+                        float d[12];
+                        regen_row((uint32_t)kb, b, t.iter, P.seed, P.ctrl, sh.sd12, d);
+                        kb = e + V < Ke ? __ldcg(elite + e + V) : 0;
 #pragma unroll
-                    for (int c = 0; c < 12; ++c) {
-                        const float q = d[c] - sh.dbar[c];
-                        s[c] += q;
-                        s2[c] = fmaf(q, q, s2[c]);
+                        for (int c = 0; c < 12; ++c) {
+                            const float q = d[c] - sh.dbar[c];
+                            s[c] += q;
+                            s2[c] = fmaf(q, q, s2[c]);
+                        }
                     }
-                    kb = kn;
+                } else {
+                    for (int e = vl; e < Ke; e += V) {
+                        // the next elite's index is loaded before this one's row is used
+                        const int kn = e + V < Ke ? __ldcg(elite + e + V) : 0;
+                        const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)b * K + kb) * 12);
+                        const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
+                        const float d[12] = {a.x, a.y, a.z, a.w, bb.x, bb.y, bb.z, bb.w, cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                        for (int c = 0; c < 12; ++c) {
+                            const float q = d[c] - sh.dbar[c];
+                            s[c] += q;
+                            s2[c] = fmaf(q, q, s2[c]);
+                        }
+                        kb = kn;
+                    }
                 }
                 float o[3];
                 int c0 = warp_sum12(s, o);
@@ -1726,13 +1772,14 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __r
     select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
 }
 
+template <bool REGEN>
 __global__ void __launch_bounds__(kRefitLanesMax) k_refit(const InstParams* __restrict__ dP, TickArgs t)
 {
     __shared__ BlockShared sh;
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    refit_block(sh, blockIdx.x);
+    refit_block<REGEN>(sh, blockIdx.x);
 }
 
 __global__ void k_init(const InstParams* __restrict__ dP, TickArgs t)
@@ -1910,6 +1957,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_grid_select(const InstRec* _
     select_block(sh, reinterpret_cast<uint32_t*>(dyn4));
 }
 
+template <bool REGEN>
 __global__ void __launch_bounds__(kBatchRefitThreads) k_grid_refit(const InstRec* __restrict__ recs,
                                                              const int* __restrict__ counts)
 {
@@ -1920,7 +1968,7 @@ __global__ void __launch_bounds__(kBatchRefitThreads) k_grid_refit(const InstRec
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
-    refit_block(sh, it - recs[i].refit_begin);
+    refit_block<REGEN>(sh, it - recs[i].refit_begin);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_batch_select(const InstRec* __restrict__ recs,
@@ -1943,6 +1991,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_batch_select(const InstRec* 
     }
 }
 
+template <bool REGEN>
 __global__ void __launch_bounds__(kBatchRefitThreads) k_batch_refit(const InstRec* __restrict__ recs,
                                                               const int* __restrict__ counts, int* heads)
 {
@@ -1957,7 +2006,7 @@ __global__ void __launch_bounds__(kBatchRefitThreads) k_batch_refit(const InstRe
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
-        refit_block(sh, it - recs[i].refit_begin);
+        refit_block<REGEN>(sh, it - recs[i].refit_begin);
         __syncthreads();
     }
 }
@@ -2265,6 +2314,7 @@ static const void* rollout_kernel(int variant)
 
 const void* batch_rollout_fn(int variant, int mode)
 {
+    variant &= ~kRegenVariant;  // the rollouts read the tick's flag
     if (variant & kPairVariant) {
         if (variant != kPairVariant) return nullptr;
         return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair : (const void*)k_batch_rollout_pair;
@@ -2278,9 +2328,10 @@ const void* batch_select_fn(int mode)
     return mode == SBS_BATCH_GRID ? (const void*)k_grid_select : (const void*)k_batch_select;
 }
 
-const void* batch_refit_fn(int mode)
+const void* batch_refit_fn(int mode, bool regen)
 {
-    return mode == SBS_BATCH_GRID ? (const void*)k_grid_refit : (const void*)k_batch_refit;
+    if (regen) return mode == SBS_BATCH_GRID ? (const void*)k_grid_refit<true> : (const void*)k_batch_refit<true>;
+    return mode == SBS_BATCH_GRID ? (const void*)k_grid_refit<false> : (const void*)k_batch_refit<false>;
 }
 
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
@@ -2332,7 +2383,8 @@ int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, 
 {
     const int grid = hP.nt + (hP.adaptive ? 1 : 0);
     const int threads = hP.method == SBS_ELITE ? refit_lanes(hP.Ke) : kRefitThreads;
-    k_refit<<<grid, threads, 0, (cudaStream_t)stream>>>(dP, t);
+    if (t.regen) k_refit<true><<<grid, threads, 0, (cudaStream_t)stream>>>(dP, t);
+    else k_refit<false><<<grid, threads, 0, (cudaStream_t)stream>>>(dP, t);
     return status_of(cudaGetLastError());
 }
 
@@ -2358,7 +2410,8 @@ int batch_grid(int P, int mode, size_t smem, size_t sel_smem, int T, const int c
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, T, smem) != cudaSuccess) return SBS_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_batch_select, kSelectThreads, sel_smem) != cudaSuccess)
         return SBS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_batch_refit, kBatchRefitThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, batch_refit_fn(mode, (P & kRegenVariant) != 0),
+                                                      kBatchRefitThreads, 0) != cudaSuccess)
         return SBS_ERR_CUDA;
     if (b1 < 1 || b2 < 1 || b3 < 1) return SBS_ERR_INVALID_ARG;
     grids[0] = sms * b1;
@@ -2372,7 +2425,8 @@ int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int*
                  size_t sel_smem, int T, const int grids[4], void* stream, void* const* events)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode), batch_refit_fn(mode)};
+    const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode),
+                          batch_refit_fn(mode, (P & kRegenVariant) != 0)};
     if (!fns[0]) return SBS_ERR_INVALID_ARG;
     const dim3 blocks[3] = {dim3(T), dim3(kSelectThreads), dim3(kBatchRefitThreads)};
     const size_t shm[3] = {smem, sel_smem, 0};

@@ -44,6 +44,7 @@ OK, PENDING = 0, 1
 ERR_INVALID_ARG, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_DIVERGED = -1, -2, -3, -4, -5, -6
 MPPI, ELITE, NAIVE = 0, 1, 2
 BUF_MEAN, BUF_VAR, BUF_COST, BUF_FREQ, BUF_ELITE, BUF_MPPI_MEAN = 0, 1, 2, 3, 4, 5
+THETA_STORE, THETA_REGENERATE = 0, 1
 MAX_H, MAX_K, MAX_TILE, MAX_FREQ = 128, 1 << 24, 256, 8
 BATCH_PERSISTENT, BATCH_GRID = 0, 1
 
@@ -158,6 +159,9 @@ ABI = {
     "sbs_batch_set_samples_per_thread": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_batch_get_samples_per_thread": (C.c_int, [C.c_void_p]),
     "sbs_set_samples_per_thread": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_set_theta_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_batch_set_theta_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_batch_get_theta_mode": (C.c_int, [C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_sqrt_hw": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -321,6 +325,10 @@ class Controller:
         carries (same results)."""
         check(lib().sbs_set_samples_per_thread(self._h, spt), "sbs_set_samples_per_thread")
 
+    def set_theta_mode(self, mode: int):
+        """THETA_STORE or THETA_REGENERATE for plain solves (same results)."""
+        check(lib().sbs_set_theta_mode(self._h, mode), "sbs_set_theta_mode")
+
     def prepare(self):
         """Allocate the plain-solve workspace now."""
         check(lib().sbs_prepare(self._h), "sbs_prepare")
@@ -459,6 +467,13 @@ class Batch:
 
     def samples_per_thread(self) -> int:
         return lib().sbs_batch_get_samples_per_thread(self._b)
+
+    def set_theta_mode(self, mode: int):
+        """THETA_STORE or THETA_REGENERATE for the sampled deviations (same results)."""
+        check(lib().sbs_batch_set_theta_mode(self._b, mode), "sbs_batch_set_theta_mode")
+
+    def theta_mode(self) -> int:
+        return lib().sbs_batch_get_theta_mode(self._b)
 
     def stage_ms(self):
         """(rollout, selection, refit) milliseconds of the last profiled tick."""

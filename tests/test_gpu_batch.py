@@ -481,7 +481,9 @@ def test_autotune_picks_a_mode_and_results_stay_valid():
     torch.cuda.synchronize()
     for i in range(len(mix)):
         r = S.parse_result(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy())
-        assert r["status"] in (S.OK, S.ERR_DIVERGED) and r["iter"] == 6
+        # autotune ticks: 2 launch modes x 2 deviation modes (stored, regenerated) x
+        # (1 + 2); this mix has extended features, so one sample per thread only
+        assert r["status"] in (S.OK, S.ERR_DIVERGED) and r["iter"] == 12
 
 
 def test_batch_host_memory_equals_device():

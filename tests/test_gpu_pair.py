@@ -123,9 +123,10 @@ def test_autotune_keeps_results():
     rb = torch.empty_like(ra)
     pa = [ta[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 1) for i in range(n)]
     pb = [tb[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 1) for i in range(n)]
-    ba.autotune(ta, pa, ra, ticks=2)  # 2 modes x 2 sample counts x (1 + 2) ticks, real solves
-    assert ba.samples_per_thread() in (1, 2)
-    for _ in range(2 * 2 * 3):
+    # 2 launch modes x 2 sample counts x 2 deviation modes x (1 + 2) ticks, real solves
+    ba.autotune(ta, pa, ra, ticks=2)
+    assert ba.samples_per_thread() in (1, 2) and ba.theta_mode() in (S.THETA_STORE, S.THETA_REGENERATE)
+    for _ in range(2 * 2 * 2 * 3):
         bb.solve(tb, pb, rb)
     ba.solve(ta, pa, ra)
     bb.solve(tb, pb, rb)
