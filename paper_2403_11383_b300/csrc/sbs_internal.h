@@ -122,7 +122,7 @@ inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1, bool pair = fa
                   + (P > 0 ? (size_t)48 * ((P + 3) / 4) * T : 0)  // per-thread knot deviations
                   + (P > 0 ? (size_t)nwarps * nf  // per-warp partial sums, then the combined row
                            : (size_t)(6 * T > nf + kPartHeader ? 6 * T : nf + kPartHeader));  // weight list and slice sums, then the combined row
-    if (pair) floats = ((floats + 3) & ~(size_t)3) + 24 * (size_t)H;  // the reference as duplicated pairs
+    if (pair) floats = ((floats + 3) & ~(size_t)3) + 72 * (size_t)H;  // reference, mean, deviation as duplicated pairs
     return floats * sizeof(float);
 }
 

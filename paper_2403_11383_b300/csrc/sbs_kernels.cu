@@ -415,8 +415,8 @@ __device__ void tile_combine(BlockShared& sh, const Views& v, int tile)
     mppi_finish(sh, v, comb, t.mppi_to_state != 0);
 }
 
-// Reference rows as duplicated pairs for the two-sample rollout, after the
-// per-step layout (16-byte aligned).
+// Reference, mean and deviation rows as duplicated pairs for the two-sample
+// rollout ([12 H] float2 each), after the per-step layout (16-byte aligned).
 __device__ __forceinline__ float2* pair_ref(const Views& v, const InstParams& P, int T)
 {
     const int acc = 6 * T > P.nf + kPartHeader ? 6 * T : P.nf + kPartHeader;
@@ -540,22 +540,29 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             normals12(pp, j, e);
             const float4* m4 = reinterpret_cast<const float4*>(mu + 12 * j);  // 16-byte aligned rows
             const float4* s4 = reinterpret_cast<const float4*>(sd + 12 * j);
+            // force mu + sigma eps (one rounding); the deviation sigma eps itself only
+            // where it is stored
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const float4 ma = m4[q], sa = s4[q];
                 const float mv[4] = {ma.x, ma.y, ma.z, ma.w}, sv[4] = {sa.x, sa.y, sa.z, sa.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int c = 4 * q + i;
-                    e[c] = __fmul_rn(sv[i], e[c]);  // deviation sigma * eps
-                    G[c] = __fadd_rn(mv[i], e[c]);
-                }
+                for (int i = 0; i < 4; ++i) G[4 * q + i] = __fmaf_rn(sv[i], e[4 * q + i], mv[i]);
             }
-            if (valid && !t.regen) {
-                float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
-                o[0] = make_float4(e[0], e[1], e[2], e[3]);
-                o[1] = make_float4(e[4], e[5], e[6], e[7]);
-                o[2] = make_float4(e[8], e[9], e[10], e[11]);
+            if (!t.regen) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float4 sa = s4[q];
+                    const float sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) e[4 * q + i] = __fmul_rn(sv[i], e[4 * q + i]);
+                }
+                if (valid) {
+                    float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
+                    o[0] = make_float4(e[0], e[1], e[2], e[3]);
+                    o[1] = make_float4(e[4], e[5], e[6], e[7]);
+                    o[2] = make_float4(e[8], e[9], e[10], e[11]);
+                }
             }
         } else {
             const float4* b4 = reinterpret_cast<const float4*>(v.Bs + j * 4 * NQ);
@@ -710,16 +717,27 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
             const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
             float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (t.regen) {  // the listed samples' deviations regenerated from their draws
+#pragma unroll 1
+                for (int e = sl; e < nnz; e += nsl) {
+                    const float2 we = lst[e];
+                    const float4 d = regen_quad((uint32_t)(tile * T + __float_as_int(we.y)), j, c - 3 * j, t.iter,
+                                                P.seed, P.ctrl, sd4);
+                    a.x = fmaf(we.x, d.x, a.x);
+                    a.y = fmaf(we.x, d.y, a.y);
+                    a.z = fmaf(we.x, d.z, a.z);
+                    a.w = fmaf(we.x, d.w, a.w);
+                }
+            } else {
 #pragma unroll 4
-            for (int e = sl; e < nnz; e += nsl) {
-                const float2 we = lst[e];
-                const int ke = __float_as_int(we.y);
-                const float4 d = t.regen ? regen_quad((uint32_t)(tile * T + ke), j, c - 3 * j, t.iter, P.seed, P.ctrl, sd4)
-                                         : src[3 * ke];
-                a.x = fmaf(we.x, d.x, a.x);
-                a.y = fmaf(we.x, d.y, a.y);
-                a.z = fmaf(we.x, d.z, a.z);
-                a.w = fmaf(we.x, d.w, a.w);
+                for (int e = sl; e < nnz; e += nsl) {
+                    const float2 we = lst[e];
+                    const float4 d = src[3 * __float_as_int(we.y)];
+                    a.x = fmaf(we.x, d.x, a.x);
+                    a.y = fmaf(we.x, d.y, a.y);
+                    a.z = fmaf(we.x, d.z, a.z);
+                    a.w = fmaf(we.x, d.w, a.w);
+                }
             }
             if (nsl == 1) row4[c] = a;
             else slice_sum[it] = a;
@@ -803,9 +821,15 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
     const TickArgs& t = sh.t;
     const int T2 = blockDim.x, T = 2 * T2, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw2 = T2 >> 5;
     const Views v = carve(dyn, P.H, 0, P.nf, T, P.nb);
-    float2* xr2 = pair_ref(v, P, T);  // the reference rows as duplicated pairs
+    float2* xr2 = pair_ref(v, P, T);  // reference, mean and deviation rows as duplicated pairs
+    float2* mu2 = xr2 + 12 * P.H;
+    float2* sd2 = mu2 + 12 * P.H;
     stage(sh, v, 0);
-    for (int i = tid; i < 12 * P.H; i += T2) xr2[i] = make_float2(v.xr[i], v.xr[i]);
+    for (int i = tid; i < 12 * P.H; i += T2) {
+        xr2[i] = make_float2(v.xr[i], v.xr[i]);
+        mu2[i] = make_float2(v.mu[i], v.mu[i]);
+        sd2[i] = make_float2(v.sd[i], v.sd[i]);
+    }
     fill_pair_consts(sh.pc, P, sh.fe);
     __syncthreads();
     const Consts<float2> Kc{sh.pc};
@@ -852,35 +876,44 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
                                 philox_draw(pp1, 1u + 2u * (uint32_t)j + (uint32_t)d)};
             normals6_v<float2>(w, z + 6 * d);
         }
-        // deviations sigma * eps per sample (stored whole, 48 B per sample), forces
-        // mean + deviation as lane pairs
-        float eA[12], eB[12];
+        // forces mu + sigma eps as lane pairs (one rounding, packed); the deviations
+        // sigma eps per sample only where they are stored (48 B per sample)
         float2 G[12];
-        const float4* m4 = reinterpret_cast<const float4*>(mu + 12 * j);  // 16-byte aligned rows
-        const float4* s4 = reinterpret_cast<const float4*>(sd + 12 * j);
+        {
+            const float4* m2 = reinterpret_cast<const float4*>(mu2 + 12 * j);  // duplicated pairs
+            const float4* s2 = reinterpret_cast<const float4*>(sd2 + 12 * j);
 #pragma unroll
-        for (int qq = 0; qq < 3; ++qq) {
-            const float4 ma = m4[qq], sa = s4[qq];
-            const float mv[4] = {ma.x, ma.y, ma.z, ma.w}, sv[4] = {sa.x, sa.y, sa.z, sa.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int c = 4 * qq + i;
-                eA[c] = __fmul_rn(sv[i], z[c].x);
-                eB[c] = __fmul_rn(sv[i], z[c].y);
-                G[c] = make_float2(__fadd_rn(mv[i], eA[c]), __fadd_rn(mv[i], eB[c]));
+            for (int qq = 0; qq < 6; ++qq) {
+                const float4 ma = m2[qq], sa = s2[qq];
+                G[2 * qq] = L::fma(make_float2(sa.x, sa.y), z[2 * qq], make_float2(ma.x, ma.y));
+                G[2 * qq + 1] = L::fma(make_float2(sa.z, sa.w), z[2 * qq + 1], make_float2(ma.z, ma.w));
             }
         }
-        if (valid[0] && !t.regen) {
-            float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[0]) * 12);
-            o[0] = make_float4(eA[0], eA[1], eA[2], eA[3]);
-            o[1] = make_float4(eA[4], eA[5], eA[6], eA[7]);
-            o[2] = make_float4(eA[8], eA[9], eA[10], eA[11]);
-        }
-        if (valid[1] && !t.regen) {
-            float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[1]) * 12);
-            o[0] = make_float4(eB[0], eB[1], eB[2], eB[3]);
-            o[1] = make_float4(eB[4], eB[5], eB[6], eB[7]);
-            o[2] = make_float4(eB[8], eB[9], eB[10], eB[11]);
+        if (!t.regen) {
+            const float4* s4 = reinterpret_cast<const float4*>(sd + 12 * j);  // 16-byte aligned rows
+            float eA[12], eB[12];
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq) {
+                const float4 sa = s4[qq];
+                const float sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    eA[4 * qq + i] = __fmul_rn(sv[i], z[4 * qq + i].x);
+                    eB[4 * qq + i] = __fmul_rn(sv[i], z[4 * qq + i].y);
+                }
+            }
+            if (valid[0]) {
+                float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[0]) * 12);
+                o[0] = make_float4(eA[0], eA[1], eA[2], eA[3]);
+                o[1] = make_float4(eA[4], eA[5], eA[6], eA[7]);
+                o[2] = make_float4(eA[8], eA[9], eA[10], eA[11]);
+            }
+            if (valid[1]) {
+                float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k[1]) * 12);
+                o[0] = make_float4(eB[0], eB[1], eB[2], eB[3]);
+                o[1] = make_float4(eB[4], eB[5], eB[6], eB[7]);
+                o[2] = make_float4(eB[8], eB[9], eB[10], eB[11]);
+            }
         }
         // stance: legs in swing on every sample of the warp skip their terms; swing
         // forces are zeroed where a leg is live on the warp but swings on a sample
@@ -1018,16 +1051,27 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
             const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
             const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
             float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (t.regen) {  // the listed samples' deviations regenerated from their draws
+#pragma unroll 1
+                for (int e = sl; e < nnz; e += nsl) {
+                    const float2 we = lst[e];
+                    const float4 d = regen_quad((uint32_t)(tile * T + __float_as_int(we.y)), j, c - 3 * j, t.iter,
+                                                P.seed, P.ctrl, sd4);
+                    a.x = fmaf(we.x, d.x, a.x);
+                    a.y = fmaf(we.x, d.y, a.y);
+                    a.z = fmaf(we.x, d.z, a.z);
+                    a.w = fmaf(we.x, d.w, a.w);
+                }
+            } else {
 #pragma unroll 4
-            for (int e = sl; e < nnz; e += nsl) {
-                const float2 we = lst[e];
-                const int ke = __float_as_int(we.y);
-                const float4 d = t.regen ? regen_quad((uint32_t)(tile * T + ke), j, c - 3 * j, t.iter, P.seed, P.ctrl, sd4)
-                                         : src[3 * ke];
-                a.x = fmaf(we.x, d.x, a.x);
-                a.y = fmaf(we.x, d.y, a.y);
-                a.z = fmaf(we.x, d.z, a.z);
-                a.w = fmaf(we.x, d.w, a.w);
+                for (int e = sl; e < nnz; e += nsl) {
+                    const float2 we = lst[e];
+                    const float4 d = src[3 * __float_as_int(we.y)];
+                    a.x = fmaf(we.x, d.x, a.x);
+                    a.y = fmaf(we.x, d.y, a.y);
+                    a.z = fmaf(we.x, d.z, a.z);
+                    a.w = fmaf(we.x, d.w, a.w);
+                }
             }
             if (nsl == 1) row4[c] = a;
             else slice_sum[it] = a;
