@@ -390,6 +390,7 @@ def run_single(args, world, rank, local):
     for w in range(max(args.warmup, 3)):
         ctl.solve(x0, xref, prob["gait"], fe, 0 if w == 0 else 1, res, feet=feet)
     p1 = ctl.problem(x0, xref, prob["gait"], fe, 1, feet=feet)  # built once, as a control loop would
+    tune = ctl.autotune(p1, res, ticks=5)  # samples per thread x stored or regenerated deviations
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
@@ -435,6 +436,10 @@ def run_single(args, world, rank, local):
                 "data": "synthetic",
                 "config": {"workload": args.workload, "K": cfg["K"], "H": cfg["H"], "P": cfg.get("P", 0),
                            "iterations": cfg["iterations"], "method": cfg["method"], "tile": ctl.tile,
+                           "samples_per_thread": ctl.samples_per_thread(),
+                           "sampled_deviations": "regenerate" if ctl.theta_mode() == S.THETA_REGENERATE else "store",
+                           "autotune_ms_per_solve": {f"spt{k[0]}_{'regen' if k[1] else 'store'}": v
+                                                     for k, v in tune.items()},
                            "parallelism": f"replicas x{world}"},
                 "solves_per_s": world / (ms * 1e-3),
                 "roofline": {"kernel": "whole solve", "bound": "alu", "achieved": achieved, "peak": peak,

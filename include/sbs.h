@@ -372,8 +372,19 @@ int sbs_set_samples_per_thread(sbs_handle* h, int spt);
 #define SBS_THETA_STORE 0
 #define SBS_THETA_REGENERATE 1
 int sbs_set_theta_mode(sbs_handle* h, int mode);
+int sbs_get_theta_mode(const sbs_handle* h);
+int sbs_get_samples_per_thread(const sbs_handle* h);
 int sbs_batch_set_theta_mode(sbs_batch* b, int mode);
 int sbs_batch_get_theta_mode(const sbs_batch* b);
+
+/* Autotuner of a handle's plain solves: times `ticks` solves of prob (after one
+ * warm-up solve per setting; real solves, they advance the controller) at one
+ * and, where the controller can take them, two samples per thread, storing and
+ * regenerating the sampled deviations, and keeps the fastest setting.
+ * ms_out[2 (spt - 1) + mode] gets the mean solve time in ms of each setting
+ * (-1 where not measured).  Synchronises the stream. */
+int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int ticks, float ms_out[4],
+                 void* stream);
 
 /* Autotuner: runs `ticks` profiled ticks in each launch mode, with one and (where
  * the launch can take them) two samples per thread, storing and regenerating the
@@ -459,6 +470,16 @@ int sbs_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int
  * cone's |Gamma_xy|: y[i] = the hardware approximation of sqrt(x[i]) for i < n
  * (device arrays, enqueued on stream); for tests of its error bound. */
 int sbs_sqrt_hw(const float* x, float* y, int n, void* stream);
+
+/* The sine and cosine the model step takes of the attitude angles (Eq. (1):
+ * rotation and Euler-rate map): a Cody-Waite reduction by pi/2 and fitted
+ * polynomials on [-pi/4, pi/4]; beyond |x| = 65536 and for non-finite x (a
+ * diverged rollout) the hardware approximation.  out: 8 n floats = [sin | cos]
+ * of the one-sample form, [sin | cos] of the two-sample (packed) form on lane
+ * pairs (2m, 2m + 1), [sin | cos] of the library's accurate sincosf and [sin |
+ * cos] of the hardware approximation, for tests of the error bound and of the
+ * two forms' equality.  Device arrays, enqueued on stream. */
+int sbs_sincos(const float* x, float* out, int n, void* stream);
 
 /* Measure the FP32 FMA throughput of the current device with a register-resident
  * FMA chain kernel; returns FLOP/s (2 per FMA) in *flops, or an error. */

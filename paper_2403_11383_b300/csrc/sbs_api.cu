@@ -570,6 +570,12 @@ int sbs_sqrt_hw(const float* x, float* y, int n, void* stream)
     return launch_sqrt_hw(x, y, n, stream);
 }
 
+int sbs_sincos(const float* x, float* out, int n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) return SBS_ERR_INVALID_ARG;
+    return launch_sincos(x, out, n, stream);
+}
+
 int sbs_fp32_peak(double* flops, void* stream)
 {
     if (!flops) return SBS_ERR_INVALID_ARG;
@@ -1196,6 +1202,63 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
     b->spt = best_spt;
     b->regen = best_regen;
     return SBS_OK;
+}
+
+extern "C" int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int ticks, float ms_out[4],
+                            void* stream)
+{
+    if (!h || !prob || !result || ticks < 1 || !ms_out) return SBS_ERR_INVALID_ARG;
+    const InstParams& P = h->hP;
+    const bool ext = P.n_freq > 0 || P.world_feet || P.friction_project;
+    const int nspt = pair_capable(P.P, ext, P.T) ? 2 : 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return SBS_ERR_CUDA;
+    }
+    int st = SBS_OK, best_spt = 1, best_regen = 0;
+    float best = 1e30f;
+    for (int i = 0; i < 4; ++i) ms_out[i] = -1.0f;
+    for (int sp = 1; sp <= nspt && st == SBS_OK; ++sp) {
+        for (int rg = 0; rg < 2 && st == SBS_OK; ++rg) {
+            h->spt = sp;
+            h->regen = rg;
+            st = sbs_solve(h, prob, result, stream);  // warm-up of this setting
+            if (st) break;
+            if (cudaEventRecord(a, s) != cudaSuccess) st = SBS_ERR_CUDA;
+            for (int k = 0; k < ticks && st == SBS_OK; ++k) st = sbs_solve(h, prob, result, stream);
+            if (st == SBS_OK && (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess))
+                st = SBS_ERR_CUDA;
+            float ms = 0.0f;
+            if (st == SBS_OK && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) st = SBS_ERR_CUDA;
+            if (st) break;
+            ms /= (float)ticks;
+            ms_out[2 * (sp - 1) + rg] = ms;
+            if (ms < best) {
+                best = ms;
+                best_spt = sp;
+                best_regen = rg;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) {
+        cudaGetLastError();
+        return st;
+    }
+    h->spt = best_spt;
+    h->regen = best_regen;
+    return SBS_OK;
+}
+
+extern "C" int sbs_get_samples_per_thread(const sbs_handle* h) { return h ? (h->spt == 2 ? 2 : 1) : SBS_ERR_INVALID_ARG; }
+
+extern "C" int sbs_get_theta_mode(const sbs_handle* h)
+{
+    return h ? (h->regen ? SBS_THETA_REGENERATE : SBS_THETA_STORE) : SBS_ERR_INVALID_ARG;
 }
 
 extern "C" int sbs_batch_set_theta_mode(sbs_batch* b, int mode)

@@ -567,27 +567,63 @@ __device__ __forceinline__ void cone_project(float mu, float inv_1pmu2, float& g
     gz = lam;
 }
 
-// sin and cos of an attitude angle.  Beyond 1e5 rad (a rollout that has long left
-// any meaningful attitude) the argument reduction of the accurate routine would
-// take its slow path; the hardware approximation is used there instead.
-__device__ __forceinline__ void angle_sincos(float a, float* s, float* c)
-{
-    if (fabsf(a) <= 1.0e5f) sincosf(a, s, c);
-    else __sincosf(a, s, c);
-}
+// sin and cos of attitude angles, written here rather than taken from the math
+// library so that two samples' reduction and polynomials issue as packed
+// instructions.  Cody-Waite reduction (Cody & Waite, 1980): j = rint(2 x / pi)
+// from the low bits of fma(x, 2/pi, 1.5 2^23), r = x - j pi/2 with pi/2 in three
+// single-precision parts subtracted one fused multiply-add at a time (the first
+// step is exact: j P1 and x lie within a factor of two); on |r| <= pi/4,
+// sin r = r + r^3 (s1 + s2 r^2 + s3 r^4) and cos r = 1 + r^2 (c1 + .. + c4 r^6)
+// by Horner; the quadrant j mod 4 swaps and negates.  Constants from
+// paper_2403_11383_b300/sincos_coefficients.py (least-squares fits on Chebyshev
+// nodes; fit error 1.3e-8 relative for sin, 7.5e-10 for cos).  Beyond
+// |x| = kSinCosMax (a rollout that has long left any meaningful attitude: its
+// cost is infinite or ungated) and for non-finite x the lane takes the hardware
+// approximation, which costs a few instructions where the accurate library
+// routine would take its slow reduction path.
+constexpr float kSinCosMax = 65536.0f;
 
-// sin and cos of lane angles (per lane: the accurate routine has no packed form).
 template <class V>
-__device__ __forceinline__ void angle_sincos_v(V a, V& s, V& c)
+__device__ __forceinline__ void sincos_v(V x, V& s, V& c)
 {
     using L = Lane<V>;
+    const float magic = 12582912.0f;  // 1.5 2^23
+    const V jm = L::fma(x, L::bc(0x1.45f306p-1f), L::bc(magic));
+    const V j = L::sub(jm, L::bc(magic));
+    V r = L::fma(j, L::bc(-0x1.921fb6p+0f), x);
+    r = L::fma(j, L::bc(0x1.777a5cp-25f), r);
+    r = L::fma(j, L::bc(0x1.ee59dap-50f), r);
+    const V u = L::mul(r, r);
+    V ps = L::fma(u, L::bc(-0x1.9aca02p-13f), L::bc(0x1.110c2ap-7f));
+    ps = L::fma(u, ps, L::bc(-0x1.555552p-3f));
+    const V sn = L::fma(L::mul(u, r), ps, r);
+    V pc = L::fma(u, L::bc(0x1.9a6f60p-16f), L::bc(-0x1.6c0e0ap-10f));
+    pc = L::fma(u, pc, L::bc(0x1.55554cp-5f));
+    pc = L::fma(u, pc, L::bc(-0.5f));
+    const V cs = L::fma(u, pc, L::bc(1.0f));
 #pragma unroll
     for (int l = 0; l < L::N; ++l) {
+        const float xl = L::get(x, l);
         float sl, cl;
-        angle_sincos(L::get(a, l), &sl, &cl);
+        if (fabsf(xl) <= kSinCosMax) {
+            const int q = __float_as_int(L::get(jm, l));
+            const float a = L::get(sn, l), b = L::get(cs, l);
+            sl = (q & 1) ? b : a;
+            cl = (q & 1) ? a : b;
+            sl = __int_as_float(__float_as_int(sl) ^ ((q & 2) << 30));
+            cl = __int_as_float(__float_as_int(cl) ^ (((q + 1) & 2) << 30));
+        } else {
+            __sincosf(xl, &sl, &cl);
+        }
         L::set(s, l, sl);
         L::set(c, l, cl);
     }
+}
+
+template <class V>
+__device__ __forceinline__ void angle_sincos_v(V a, V& s, V& c)
+{
+    sincos_v<V>(a, s, c);
 }
 
 // The rotational and translational rates of Eq. (1) from the net force F and
@@ -707,9 +743,9 @@ __device__ __forceinline__ void srbd_step_world(const InstParams& P, float x[12]
                                                 unsigned touch, float vdx, float vdy, float tsh)
 {
     float sr, cr, sp, cp, sy, cy;
-    angle_sincos(x[3], &sr, &cr);
-    angle_sincos(x[4], &sp, &cp);
-    angle_sincos(x[5], &sy, &cy);
+    sincos_v<float>(x[3], sr, cr);
+    sincos_v<float>(x[4], sp, cp);
+    sincos_v<float>(x[5], sy, cy);
     const Rot<float> Rm = rotation_v<float>(sr, cr, sp, cp, sy, cy);
     const float R00 = Rm.R00, R01 = Rm.R01, R02 = Rm.R02, R10 = Rm.R10, R11 = Rm.R11, R12 = Rm.R12;
     const float R20 = -sp, R21 = Rm.R21, R22 = Rm.R22;

@@ -234,6 +234,7 @@ const void* batch_refit_fn(int mode, bool regen);
 int launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* stream);
 int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out, void* stream);
 int launch_sqrt_hw(const float* x, float* y, int n, void* stream);
+int launch_sincos(const float* x, float* out, int n, void* stream);
 int launch_fma_peak(float* out, int iters, int blocks, int threads, void* stream);
 
 }  // namespace sbs

@@ -24,6 +24,7 @@
 //  k_init      the initial distribution.
 //  k_philox, k_normals  the random numbers the controller draws (tests).
 //  k_sqrt_hw  the hardware square root the rollout uses (tests).
+//  k_sincos   the attitude sine and cosine of the model step (tests).
 //  k_fma_peak  FP32 FMA-chain microbenchmark for the roofline denominator.
 #include <cuda_runtime.h>
 
@@ -2073,6 +2074,30 @@ __global__ void k_sqrt_hw(const float* __restrict__ x, float* __restrict__ y, in
     if (i < n) y[i] = sqrt_hw(x[i]);
 }
 
+// The attitude sine and cosine: out = [sin, cos (one lane) | sin, cos (lane pairs
+// (2m, 2m + 1); the last lane of an odd n paired with itself) | the library's
+// sincosf | the hardware approximation], n floats each.
+__global__ void k_sincos(const float* __restrict__ x, float* __restrict__ out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s, c;
+    sincos_v<float>(x[i], s, c);
+    out[i] = s;
+    out[n + i] = c;
+    const int i0 = i & ~1, i1 = min(i0 + 1, n - 1);
+    float2 s2, c2;
+    sincos_v<float2>(make_float2(x[i0], x[i1]), s2, c2);
+    out[2 * n + i] = (i & 1) ? s2.y : s2.x;
+    out[3 * n + i] = (i & 1) ? c2.y : c2.x;
+    sincosf(x[i], &s, &c);
+    out[4 * n + i] = s;
+    out[5 * n + i] = c;
+    __sincosf(x[i], &s, &c);
+    out[6 * n + i] = s;
+    out[7 * n + i] = c;
+}
+
 __global__ void k_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, int nn, float* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2502,6 +2527,13 @@ int launch_normals(uint32_t seed, uint32_t ctrl, uint64_t iter, int k0, int nk, 
 {
     if (nk <= 0) return SBS_OK;
     k_normals<<<(nk + 127) / 128, 128, 0, (cudaStream_t)stream>>>(seed, ctrl, iter, k0, nk, nn, out);
+    return status_of(cudaGetLastError());
+}
+
+int launch_sincos(const float* x, float* out, int n, void* stream)
+{
+    if (n <= 0) return SBS_OK;
+    k_sincos<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, out, n);
     return status_of(cudaGetLastError());
 }
 

@@ -160,9 +160,13 @@ ABI = {
     "sbs_batch_get_samples_per_thread": (C.c_int, [C.c_void_p]),
     "sbs_set_samples_per_thread": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_set_theta_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "sbs_get_theta_mode": (C.c_int, [C.c_void_p]),
+    "sbs_get_samples_per_thread": (C.c_int, [C.c_void_p]),
+    "sbs_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "sbs_batch_set_theta_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_batch_get_theta_mode": (C.c_int, [C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sbs_sincos": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_sqrt_hw": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_normals": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_void_p,
@@ -328,6 +332,21 @@ class Controller:
     def set_theta_mode(self, mode: int):
         """THETA_STORE or THETA_REGENERATE for plain solves (same results)."""
         check(lib().sbs_set_theta_mode(self._h, mode), "sbs_set_theta_mode")
+
+    def theta_mode(self) -> int:
+        return lib().sbs_get_theta_mode(self._h)
+
+    def samples_per_thread(self) -> int:
+        return lib().sbs_get_samples_per_thread(self._h)
+
+    def autotune(self, problem: "Problem", result, ticks: int = 5, stream=None):
+        """sbs_autotune: time the plain-solve settings on this problem (real
+        solves), keep the fastest; returns {(spt, theta_mode): ms}."""
+        ms = (C.c_float * 4)()
+        ptr = result.data_ptr() if hasattr(result, "data_ptr") else C.addressof(result)
+        check(lib().sbs_autotune(self._h, C.byref(problem), C.c_void_p(ptr), ticks, ms, _stream_ptr(stream)),
+              "sbs_autotune")
+        return {(1 + i // 2, i % 2): ms[i] for i in range(4) if ms[i] >= 0}
 
     def prepare(self):
         """Allocate the plain-solve workspace now."""
@@ -547,6 +566,18 @@ def philox(ctr, key, stream=None):
     check(lib().sbs_philox4x32_10(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()),
                                   C.c_void_p(out.data_ptr()), n, _stream_ptr(stream)), "sbs_philox4x32_10")
     return out
+
+
+def sincos(x, stream=None):
+    """The model step's attitude sine and cosine of a float32 CUDA tensor:
+    returns (sin, cos, sin_packed, cos_packed, sin_library, cos_library,
+    sin_hardware, cos_hardware)."""
+    import torch
+    n = x.numel()
+    out = torch.empty(8 * n, dtype=torch.float32, device=x.device)
+    check(lib().sbs_sincos(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), n, _stream_ptr(stream)),
+          "sbs_sincos")
+    return tuple(out[i * n:(i + 1) * n] for i in range(8))
 
 
 def sqrt_hw(x, stream=None):

@@ -181,24 +181,38 @@ def mppi_tolerance(J, th, kap, lam, mean_ref):
 
 
 def elite_band_ok(gpu_set, orc_J, Ke, kap, alt_J=None):
-    """The GPU elite set equals the oracle's except for samples within their
-    tolerance band of the threshold cost (or with an ambiguous frequency whose
-    alternative cost crosses the threshold)."""
+    """The GPU elite set against the oracle's costs (Alg. 1 Sorting).
+
+    Samples whose cost no single-precision evaluation can reproduce (conditioning
+    estimate above KAPPA_GATED, or a non-finite oracle cost) may enter or leave the
+    set, and each one that does moves the K_e-th place.  So the set is compared on
+    the reproducible samples: among them, the GPU's elite set must be a prefix of
+    the oracle's cost order up to each sample's tolerance band, i.e. no
+    reproducible sample outside the set is clearly cheaper than one inside it.  A
+    sample with an ambiguous frequency counts with either of its two costs (alt_J).
+    Returns the size of the symmetric difference with the oracle's own set."""
     key = np.where(np.isnan(orc_J), np.inf, orc_J)
     order = np.lexsort((np.arange(key.size), key))
     orc_set = set(order[:Ke].tolist())
-    thr = key[order[Ke - 1]]
-    nxt = key[order[Ke]] if Ke < key.size else np.inf
-    diff = orc_set ^ set(int(i) for i in gpu_set)
+    gset = set(int(i) for i in gpu_set)
     tol = cost_tolerance(kap)
-    for i in diff:
-        lo, hi = min(thr, nxt), max(thr, nxt)
-        band = tol[i] * max(abs(key[i]), abs(lo)) * 2
-        near = (key[i] >= lo - band) and (key[i] <= hi + band)
-        if alt_J is not None and i in alt_J:
-            near = near or alt_J[i] <= hi + band
-        assert near, f"sample {i} cost {key[i]} far from threshold {thr} (tol {tol[i]})"
-    return len(diff)
+    with np.errstate(invalid="ignore"):
+        ok = np.isfinite(key) & (kap <= KAPPA_GATED)
+    band = np.where(ok, tol * np.abs(np.where(ok, key, 0.0)) * 2, np.inf)
+    lo_cost, hi_cost = key.copy(), key.copy()  # the range of a sample's admissible costs
+    if alt_J is not None:
+        for i, a in alt_J.items():
+            lo_cost[i], hi_cost[i] = min(key[i], a), max(key[i], a)
+    inside = np.array(sorted(i for i in gset if ok[i]), dtype=np.int64)
+    outside = np.nonzero(ok & ~np.isin(np.arange(key.size), np.fromiter(gset, np.int64)))[0]
+    if inside.size and outside.size:
+        worst_in = np.max(lo_cost[inside] - band[inside])
+        best_out = np.min(hi_cost[outside] + band[outside])
+        i_in = inside[np.argmax(lo_cost[inside] - band[inside])]
+        i_out = outside[np.argmin(hi_cost[outside] + band[outside])]
+        assert worst_in <= best_out, (f"sample {i_out} (cost {key[i_out]}) is outside the GPU's elite set but "
+                                      f"clearly cheaper than sample {i_in} (cost {key[i_in]}) inside it")
+    return len(orc_set ^ gset)
 
 
 def mppi_parity(cfg, prob, name, tile=0):

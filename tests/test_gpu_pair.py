@@ -134,3 +134,31 @@ def test_autotune_keeps_results():
     np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
     ba.close()
     bb.close()
+
+
+def test_plain_autotune_keeps_results():
+    # sbs_autotune times 2 sample counts x 2 deviation modes (1 + 3 solves each)
+    # and keeps the fastest; the controller then continues with the same bits as
+    # one solved the same number of times with the defaults
+    import torch
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(K=20000, H=20, tile=256, seed=5)
+    prob = W.problem(cfg)
+    x0, xr, fe = _dev(prob["x0"]), _dev(prob["xref"]), _dev(prob["f_ext"])
+    a, b = S.Controller(cfg), S.Controller(cfg)
+    ra = torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rb = torch.empty_like(ra)
+    pa = a.problem(x0, xr, prob["gait"], fe, 1)
+    ms = a.autotune(pa, ra, ticks=3)
+    assert set(ms) == {(1, 0), (1, 1), (2, 0), (2, 1)} and all(v > 0 for v in ms.values())
+    best = min(ms, key=ms.get)
+    assert (a.samples_per_thread(), a.theta_mode()) == best
+    for _ in range(4 * 4):
+        b.solve(x0, xr, prob["gait"], fe, 1, rb)
+    a.solve(x0, xr, prob["gait"], fe, 1, ra)
+    b.solve(x0, xr, prob["gait"], fe, 1, rb)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
+    np.testing.assert_array_equal(a.read(S.BUF_MEAN).cpu().numpy(), b.read(S.BUF_MEAN).cpu().numpy())
+    a.close()
+    b.close()
