@@ -91,6 +91,12 @@ def parse():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--tile", type=int, default=0,
                     help="samples per block of the batched controllers; 0: timed at 128 and 256, fastest kept")
+    ap.add_argument("--launch", default="auto", choices=["auto", "grid", "persistent"],
+                    help="batched launch mode; auto: measured by the autotuner (with --spt and --theta)")
+    ap.add_argument("--spt", type=int, default=0, choices=[0, 1, 2],
+                    help="samples per thread of the batched rollout; 0: autotuned")
+    ap.add_argument("--theta", default="auto", choices=["auto", "store", "regenerate"],
+                    help="sampled deviations stored or regenerated; auto: autotuned")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and the parity record")
     ap.add_argument("--no-parity", action="store_true", help="skip the per-output FP64 error record")
     ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
@@ -188,9 +194,10 @@ def solve_launches(cfg):
     return cfg["iterations"] * (2 + select)
 
 
-def rollout_traffic():
+def rollout_traffic(mode, spt, theta):
     """DRAM bytes per sample-step of the rollout kernel from the committed ncu
-    record, or None when the kernel sources changed since that capture."""
+    record, or None when the kernel sources changed since that capture or the
+    record was taken in another launch setting."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "rollout_traffic.json")
     if not os.path.exists(p):
@@ -201,7 +208,8 @@ def rollout_traffic():
     for src in rec["sources"]:
         with open(os.path.join(ROOT, src), "rb") as g:
             h.update(g.read())
-    return rec["dram_bytes_per_sample_step"] if h.hexdigest() == rec["sources_sha256"] else None
+    same = (rec.get("launch_mode"), rec.get("samples_per_thread"), rec.get("sampled_deviations")) == (mode, spt, theta)
+    return rec["dram_bytes_per_sample_step"] if h.hexdigest() == rec["sources_sha256"] and same else None
 
 
 def measured_peaks():
@@ -517,9 +525,18 @@ def main():
     for w in range(max(args.warmup, 3)):
         tick(first=(w == 0))
     tune_ms = batch.autotune(ctls, probs1, results, ticks=5)
+    # fixed choices (profiling captures) replace the autotuner's
+    if args.launch != "auto":
+        batch.set_mode(S.BATCH_GRID if args.launch == "grid" else S.BATCH_PERSISTENT)
+    if args.spt:
+        batch.set_samples_per_thread(args.spt)
+    if args.theta != "auto":
+        batch.set_theta_mode(S.THETA_REGENERATE if args.theta == "regenerate" else S.THETA_STORE)
     mode = "grid" if batch.mode() == S.BATCH_GRID else "persistent"
     spt = batch.samples_per_thread() or 1
     theta = "regenerate" if batch.theta_mode() == S.THETA_REGENERATE else "store"
+    fixed = {k: v for k, v in (("launch", args.launch), ("spt", args.spt), ("theta", args.theta))
+             if v not in ("auto", 0)}
     for _ in range(3):  # rebuild the tick graphs in the chosen mode before timing
         tick()
     torch.cuda.synchronize()
@@ -647,7 +664,7 @@ def main():
             parity = parity_record(W.batch_config(args.instances), tile, nthreads)
 
     peaks = measured_peaks()
-    traffic_ss = rollout_traffic()
+    traffic_ss = rollout_traffic(mode, spt, theta)
     if rank == 0:
         line = {
             "metric": "rollout sample-steps/s", "value": value, "unit": "sample-steps/s", "n_gpus": world,
@@ -657,6 +674,7 @@ def main():
                        "tile": tile, "tile_autotune_ms_per_tick": tile_ms, "graph": True, "launch_mode": mode,
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
                        "samples_per_thread": spt, "sampled_deviations": theta,
+                       "fixed_by_flags": fixed or None,
                        "l2": "per-tick working set above L2 (workspace of the 256 controllers "
                        f"{arena / 1e9:.2f} GB; with stored deviations every tick writes "
                        f"{48 * ss_tick / 1e9:.2f} GB of them)", "workspace_bytes": 2 * arena,
@@ -676,9 +694,10 @@ def main():
                          "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,
                          "flops_per_launch": flops_launch,
                          "traffic": None if traffic_ss is None else traffic_ss * ss_tick,
-                         "traffic_note": "ncu DRAM read+write of the two rollout launches of this workload's tick "
-                                         "(one-pass capture, profiles/rollout_traffic.json), per sample-step "
-                                         "times this tick's sample-steps"},
+                         "traffic_note": "ncu DRAM read+write of the rollout launches of this workload's tick "
+                                         "in the same launch setting (one-pass capture, "
+                                         "profiles/rollout_traffic.json), per sample-step times this tick's "
+                                         "sample-steps"},
             "update_roofline": {
                 "bound": "hbm", "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
                 "select": {"bytes": sel_bytes, "achieved": sel_bytes / (sel_ms * 1e-3) / 1e9,
