@@ -602,7 +602,9 @@ def main():
         ke = c["elite_count"] if c["method"] == "elite" else 1
         d = 12 * c["H"] + (1 if c.get("adaptive") else 0)
         sel_bytes += 4 * c["K"] + 4 * ke
-        ref_bytes += (48 + 4) * ke * c["H"] + 16 * d
+        # stored deviations: each elite's row (48 B) and index per step; regenerated:
+        # the indices only
+        ref_bytes += ((48 if theta == "store" else 0) + 4) * ke * c["H"] + 16 * d
     fp32_peak = S.fp32_peak() / 1e12
     nominal = 148 * 128 * 2 * 2032e6 / 1e12
 
@@ -675,7 +677,7 @@ def main():
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
                        "samples_per_thread": spt, "sampled_deviations": theta,
                        "fixed_by_flags": fixed or None,
-                       "l2": "per-tick working set above L2 (workspace of the 256 controllers "
+                       "l2": f"per-tick working set above L2 (workspace of the {n} controllers "
                        f"{arena / 1e9:.2f} GB; with stored deviations every tick writes "
                        f"{48 * ss_tick / 1e9:.2f} GB of them)", "workspace_bytes": 2 * arena,
                        "parallelism": f"replicas x{world}"},
