@@ -229,6 +229,11 @@ size_t sbs_device_bytes(const sbs_handle* h);
  * (costs, sampled deviations, partial sums, elite indices). */
 size_t sbs_workspace_bytes(const sbs_handle* h);
 
+/* The same for a batch in the given deviation mode (SBS_THETA_STORE or
+ * SBS_THETA_REGENERATE): a tick that regenerates the sampled deviations needs no
+ * room for them (K x nt x 48 bytes less). */
+size_t sbs_workspace_bytes_mode(const sbs_handle* h, int theta_mode);
+
 /* Reset the distribution to its initial value for the given gait (hover forces
  * m|g| / n_stance per step, sigma_init; frequency q_init, sigma_f_init) and the
  * iteration counter to iter. Enqueued on stream (a cudaStream_t; NULL = default). */
@@ -423,6 +428,9 @@ typedef struct sbs_server_config {
     int32_t max_pending;   /* outstanding requests accepted, >= 1 */
     int32_t plain;         /* 1: serve one request per sbs_solve instead of batching */
     size_t budget_bytes;   /* device workspace budget shared by the slots */
+    int32_t samples_per_thread;  /* the slots' batches: 0 (default) or 1, or 2 (sbs_batch_set_samples_per_thread) */
+    int32_t theta_mode;    /* the slots' batches: SBS_THETA_STORE (default) or SBS_THETA_REGENERATE; admission
+                              counts each request's workspace in this mode (sbs_workspace_bytes_mode) */
 } sbs_server_config;
 
 typedef struct sbs_server_stats {

@@ -373,6 +373,11 @@ size_t sbs_device_bytes(const sbs_handle* h) { return h ? h->dev_bytes : 0; }
 
 size_t sbs_workspace_bytes(const sbs_handle* h) { return h ? h->wsl.bytes : 0; }
 
+size_t sbs_workspace_bytes_mode(const sbs_handle* h, int theta_mode)
+{
+    return h ? ws_bytes(h->wsl, theta_mode == SBS_THETA_REGENERATE) : 0;
+}
+
 int sbs_reset(sbs_handle* h, const sbs_gait* gait, uint64_t iter, void* stream)
 {
     if (!h) return SBS_ERR_INVALID_ARG;
@@ -637,7 +642,7 @@ struct sbs_batch_plan {
     std::vector<const sbs_handle*> h;
     std::vector<uint64_t> uid;
     std::vector<int> order;  // heavier tiles first
-    size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0;
+    size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0, arena_regen = 0;
     long long counters = 0;
     bool ext = false;
 };
@@ -878,7 +883,7 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
     pl.h.clear();
     pl.uid.clear();
     const int T = handles[0]->hP.T, Pk = handles[0]->hP.P;
-    size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0;
+    size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0, arena_regen = 0;
     long long counters = 0;
     bool ext = false;  // some controller uses an extended model feature
     for (int i = 0; i < n; ++i) {
@@ -888,7 +893,8 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
         smem_pair = std::max(smem_pair, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb, true));
         ext = ext || h->hP.n_freq > 0 || h->hP.world_feet || h->hP.friction_project;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
-        arena += align_up(h->wsl.bytes, 256);
+        arena += align_up(ws_bytes(h->wsl), 256);
+        arena_regen += align_up(ws_bytes(h->wsl, true), 256);
         counters += h->wsl.counters;
     }
     {
@@ -913,6 +919,7 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
     pl.smem_pair = smem_pair;
     pl.sel_smem = sel_smem;
     pl.arena = arena;
+    pl.arena_regen = arena_regen;
     pl.counters = counters;
     pl.ext = ext;
     pl.h.assign(handles, handles + n);
@@ -941,7 +948,8 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         if (h->hP.world_feet && !p->feet) return SBS_ERR_INVALID_ARG;
         if (validate_gait(&p->gait) || p->shift < 0 || (h->hP.P > 0 && p->shift > 1)) return SBS_ERR_INVALID_ARG;
     }
-    if (pl.arena > b->arena_bytes || pl.counters > b->counter_words) return SBS_ERR_BUDGET;
+    const bool regen = b->regen != 0;
+    if ((regen ? pl.arena_regen : pl.arena) > b->arena_bytes || pl.counters > b->counter_words) return SBS_ERR_BUDGET;
     const int T = handles[0]->hP.T;
     const int Pk = handles[0]->hP.P;
     const std::vector<int>& order = pl.order;
@@ -982,8 +990,8 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         R.t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
         R.t.regen = b->regen;
         R.t.result = results + i;
-        R.t.ws = ws_at(h->wsl, sl.arena + aoff, cnt);
-        aoff += align_up(h->wsl.bytes, 256);
+        R.t.ws = ws_at(h->wsl, sl.arena + aoff, cnt, regen);
+        aoff += align_up(ws_bytes(h->wsl, regen), 256);
         cnt += h->wsl.counters;
         R.dP = h->dP;
         R.tile_begin = tile_begin;

@@ -134,6 +134,7 @@ inline size_t select_smem_bytes(int K) { return 4 * (size_t)(K < kSelectSmemMaxK
 // (2 words), completion counters (ngroups + 1), histogram.
 struct WsLayout {
     size_t J, q, theta, part, gpart, elite, cand, bcnt, sel, bytes;
+    size_t theta_bytes;  // the sampled deviations' region; absent when a tick regenerates them
     int ntiles, ngroups, counters;  // counters: zero-when-idle words
     int c_groups, c_hist;           // word offsets of the completion counters and the histogram
     int naive_nb;                   // Naive force blocks (0: not Naive)
@@ -164,6 +165,7 @@ inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false,
     L.J = o; o = up(o + 4 * (size_t)K);
     L.q = o; o = up(o + 4 * (size_t)K);
     L.theta = o; o = up(o + 4 * (size_t)K * nf);
+    L.theta_bytes = o - L.theta;
     L.part = o; o = up(o + 4 * (size_t)L.ntiles * PS);
     L.gpart = o; o = up(o + 4 * (size_t)L.ngroups * PS);
     L.elite = o; o = up(o + 4 * (size_t)(Ke > 0 ? Ke : 1));
@@ -175,12 +177,19 @@ inline WsLayout ws_layout(int K, int H, int P, int T, int Ke, bool hist = false,
     return L;
 }
 
-inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters)
+// Bytes of a workspace: without the deviations' region when they are regenerated.
+inline size_t ws_bytes(const WsLayout& L, bool regen = false) { return L.bytes - (regen ? L.theta_bytes : 0); }
+
+// A workspace at base.  With regen the deviations' region is left out: the
+// regions after it move down by its size and theta is null (never read or written).
+inline Workspace ws_at(const WsLayout& L, char* base, unsigned* counters, bool regen = false)
 {
     Workspace w;
+    const size_t sh = regen ? L.theta_bytes : 0;
     w.J = (float*)(base + L.J);
     w.q = (int32_t*)(base + L.q);
-    w.theta = (float*)(base + L.theta);
+    w.theta = regen ? nullptr : (float*)(base + L.theta);
+    base -= sh;  // the regions below follow theta
     w.part = (float*)(base + L.part);
     w.gpart = (float*)(base + L.gpart);
     w.elite = (int32_t*)(base + L.elite);

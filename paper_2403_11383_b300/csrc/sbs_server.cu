@@ -261,6 +261,9 @@ extern "C" int sbs_server_create(const sbs_server_config* cfg, const sbs_allocat
     *out = nullptr;
     if (cfg->slots < 1 || cfg->slots > 8 || cfg->max_batch < 1 || cfg->max_pending < 1) return SBS_ERR_INVALID_ARG;
     if (!cfg->plain && cfg->budget_bytes < 4096) return SBS_ERR_INVALID_ARG;
+    if (cfg->samples_per_thread < 0 || cfg->samples_per_thread > 2 ||
+        (cfg->theta_mode != SBS_THETA_STORE && cfg->theta_mode != SBS_THETA_REGENERATE))
+        return SBS_ERR_INVALID_ARG;
     if (alloc && (!alloc->alloc || !alloc->free)) return SBS_ERR_INVALID_ARG;
     sbs_server* s = new (std::nothrow) sbs_server();
     if (!s) return SBS_ERR_OOM;
@@ -291,6 +294,9 @@ extern "C" int sbs_server_create(const sbs_server_config* cfg, const sbs_allocat
         }
         if (!cfg->plain) {
             st = sbs_batch_create(mb, 1, s->slot_budget, alloc, &sl.batch);
+            if (st) break;
+            st = sbs_batch_set_samples_per_thread(sl.batch, cfg->samples_per_thread);
+            if (!st) st = sbs_batch_set_theta_mode(sl.batch, cfg->theta_mode);
             if (st) break;
         }
     }
@@ -349,7 +355,8 @@ extern "C" int sbs_server_submit(sbs_server* s, int n, sbs_handle* const* handle
         if (!finite_n(p->x0, 12) || !finite_n(p->xref, 12 * H) || (p->f_ext && !finite_n(p->f_ext, 3)))
             return SBS_ERR_INVALID_ARG;
         if (h->hP.world_feet && (!p->feet || !finite_n(p->feet, 8))) return SBS_ERR_INVALID_ARG;
-        if (!s->cfg.plain && h->wsl.bytes + 256 > s->slot_budget) return SBS_ERR_BUDGET;
+        const size_t ws = ws_bytes(h->wsl, !s->cfg.plain && s->cfg.theta_mode == SBS_THETA_REGENERATE);
+        if (!s->cfg.plain && ws + 256 > s->slot_budget) return SBS_ERR_BUDGET;
         Request& r = reqs[i];
         r.h = h;
         r.gait = p->gait;
@@ -357,7 +364,7 @@ extern "C" int sbs_server_submit(sbs_server* s, int n, sbs_handle* const* handle
         r.has_fext = p->f_ext != nullptr;
         r.has_feet = h->hP.world_feet != 0;
         r.H = H;
-        r.ws = h->wsl.bytes;
+        r.ws = ws;
         r.in.assign(24 + 12 * (size_t)H, 0.0f);
         std::memcpy(r.in.data(), p->x0, 12 * sizeof(float));
         if (p->f_ext) std::memcpy(r.in.data() + 12, p->f_ext, 3 * sizeof(float));

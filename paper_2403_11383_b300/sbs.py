@@ -91,7 +91,7 @@ RESULT_BYTES = C.sizeof(Result)
 
 class ServerConfig(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("max_pending", C.c_int32), ("plain", C.c_int32),
-                ("budget_bytes", C.c_size_t)]
+                ("budget_bytes", C.c_size_t), ("samples_per_thread", C.c_int32), ("theta_mode", C.c_int32)]
 
 
 class ServerStats(C.Structure):
@@ -132,6 +132,7 @@ ABI = {
     "sbs_prepare": (C.c_int, [C.c_void_p]),
     "sbs_device_bytes": (C.c_size_t, [C.c_void_p]),
     "sbs_workspace_bytes": (C.c_size_t, [C.c_void_p]),
+    "sbs_workspace_bytes_mode": (C.c_size_t, [C.c_void_p, C.c_int]),
     "sbs_reset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "sbs_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
@@ -354,6 +355,10 @@ class Controller:
 
     def workspace_bytes(self) -> int:
         return lib().sbs_workspace_bytes(self._h)
+
+    def workspace_bytes_mode(self, theta_mode: int) -> int:
+        """Batch workspace of one solve in the given deviation mode."""
+        return lib().sbs_workspace_bytes_mode(self._h, theta_mode)
 
     def close(self):
         if self._h:
@@ -602,9 +607,10 @@ class Server:
     """The request loop with continuous batching (sbs_server_*)."""
 
     def __init__(self, slots=2, max_batch=2048, max_pending=1 << 16, budget_bytes=8 << 30, plain=False,
-                 use_torch_allocator=False):
+                 use_torch_allocator=False, samples_per_thread=0, theta_mode=THETA_STORE):
         self._s = C.c_void_p()
-        cfg = ServerConfig(slots, max_batch, max_pending, 1 if plain else 0, budget_bytes)
+        cfg = ServerConfig(slots, max_batch, max_pending, 1 if plain else 0, budget_bytes, samples_per_thread,
+                           theta_mode)
         alloc = C.byref(torch_allocator().struct) if use_torch_allocator else None
         check(lib().sbs_server_create(C.byref(cfg), alloc, C.byref(self._s)), "sbs_server_create")
 

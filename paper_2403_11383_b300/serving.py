@@ -174,16 +174,26 @@ class Robots:
         return self.probs[idx]
 
 
-def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, seed=3, robots=None):
-    """Serve n robots for warmup + duration seconds; statistics of the measured window."""
+def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, seed=3, robots=None,
+        samples_per_thread=2, theta_mode=S.THETA_REGENERATE, max_batch=192):
+    """Serve n robots for warmup + duration seconds; statistics of the measured window.
+    samples_per_thread, theta_mode, max_batch: the batched server's launch settings
+    and requests per tick (None: all robots); plain solves take the same deviation
+    mode with one sample per thread.  The defaults are the fastest of a sweep on
+    B300 for this mix (2 s windows): regenerated deviations with 160-192 requests
+    per tick served 199 k solves/s, stored deviations (ticks capped by the budget,
+    about 185 requests) 182-186 k, regenerated without a cap (about 300 per tick,
+    the slots no longer overlapping) 129-147 k."""
     import torch
     R = robots if robots is not None else Robots(n, seed)
     n = R.n
     if plain:  # plain solves use each controller's own workspace: allocate it before serving
         for c in R.ctls:
             c.prepare()
-    server = S.Server(slots=1 if plain else slots, max_batch=n, max_pending=4 * n, budget_bytes=budget,
-                      plain=plain)
+            c.set_theta_mode(theta_mode)
+            c.set_samples_per_thread(1)
+    server = S.Server(slots=1 if plain else slots, max_batch=max_batch or n, max_pending=4 * n, budget_bytes=budget,
+                      plain=plain, samples_per_thread=samples_per_thread, theta_mode=theta_mode)
     rng = np.random.default_rng(seed + 11)
     outstanding = np.zeros(n, dtype=bool)
     tickets = np.zeros(n, dtype=np.uint64)
@@ -195,6 +205,8 @@ def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, 
     anchor = np.full(n, t0)
     measuring, m_start = False, None
     done_n, done_ss, missed = 0, 0, 0
+    rates = np.rint(1.0 / R.period).astype(np.int64)
+    by_rate = {int(r): [0, 0] for r in np.unique(rates)}  # solves done, deadlines missed
     lat_host = []
     while True:
         now = time.perf_counter()
@@ -202,6 +214,7 @@ def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, 
             measuring, m_start = True, now
             server.stats(reset=True)
             done_n, done_ss, missed = 0, 0, 0
+            by_rate = {r: [0, 0] for r in by_rate}
             lat_host = []
         if measuring and now - m_start >= duration:
             break
@@ -220,7 +233,12 @@ def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, 
                 if measuring:
                     done_n += len(fin)
                     done_ss += int((R.K[fin] * R.H[fin]).sum())
-                    missed += int((lat > R.period[fin]).sum())
+                    late = lat > R.period[fin]
+                    missed += int(late.sum())
+                    for r in by_rate:
+                        sel = rates[fin] == r
+                        by_rate[r][0] += int(sel.sum())
+                        by_rate[r][1] += int((late & sel).sum())
                     lat_host.extend(lat.tolist())
             bad = st == S.ERR_INVALID_ARG
             if bad.any():
@@ -253,6 +271,12 @@ def run(plain=False, n=2048, duration=4.0, warmup=1.0, slots=4, budget=8 << 30, 
                            "kind": "server: submit to result on the host"},
             "host_latency_ms": {"p50": 1e3 * lat_host[len(lat_host) // 2],
                                 "p99": 1e3 * lat_host[min(len(lat_host) - 1, int(0.99 * len(lat_host)))]},
-            "deadline_miss_frac": missed / max(done_n, 1), "mean_batch": stats["mean_batch"],
+            "deadline_miss_frac": missed / max(done_n, 1),
+            "by_rate_hz": {str(r): {"robots": int((rates == r).sum()), "solves_per_s": d / elapsed,
+                                    "offered_solves_per_s": float(r * (rates == r).sum()),
+                                    "deadline_miss_frac": m / max(d, 1)} for r, (d, m) in by_rate.items()},
+            "launch": {"samples_per_thread": 1 if plain else samples_per_thread,
+                       "sampled_deviations": "regenerate" if theta_mode == S.THETA_REGENERATE else "store"},
+            "mean_batch": stats["mean_batch"],
             "ticks": stats["ticks"], "admission_waits": stats["admission_waits"], "budget_bytes": budget,
             "offered_solves_per_s": float((1.0 / R.period).sum())}

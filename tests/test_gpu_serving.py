@@ -48,12 +48,15 @@ def _wait(server, tickets, timeout=30.0):
     return out
 
 
-def test_served_results_equal_plain_solves():
+@pytest.mark.parametrize("spt,theta", [(0, S.THETA_STORE), (2, S.THETA_REGENERATE)])
+def test_served_results_equal_plain_solves(spt, theta):
+    # in the library's default launch settings and in those the serving run uses
+    # (two samples per thread, regenerated deviations): the same bits
     import torch
     cfgs, probs = _setup()
     served = [S.Controller(c) for c in cfgs]
     plain = [S.Controller(c) for c in cfgs]
-    srv = S.Server(slots=2, max_batch=16, budget_bytes=1 << 30)
+    srv = S.Server(slots=2, max_batch=16, budget_bytes=1 << 30, samples_per_thread=spt, theta_mode=theta)
     handles = np.array([c.handle.value for c in served], dtype=np.uint64)
     for rnd in range(3):
         bufs = []
@@ -135,6 +138,15 @@ def test_admission_by_budget_and_full_queue():
         tiny.submit(np.array([ctls[0].handle.value], dtype=np.uint64), _records(ctls[:1], probs[:1], 0, bufs))
     assert e.value.status == S.ERR_BUDGET
     tiny.close()
+    # a server that regenerates the deviations admits by the smaller workspace: the
+    # same budget holds every request in one tick
+    need_r = sum(c.workspace_bytes_mode(S.THETA_REGENERATE) + 256 for c in ctls)
+    assert need_r < need
+    srv = S.Server(slots=1, max_batch=8, budget_bytes=need_r + 4096, theta_mode=S.THETA_REGENERATE)
+    t = srv.submit(np.array([c.handle.value for c in ctls], dtype=np.uint64), _records(ctls, probs, 1, bufs))
+    res = _wait(srv, t)
+    assert (res["status"] == S.OK).all() and srv.stats()["ticks"] == 1
+    srv.close()
     small = S.Server(slots=1, max_batch=8, max_pending=2, budget_bytes=1 << 30)
     with pytest.raises(S.SBSError) as e:
         small.submit(np.array([c.handle.value for c in ctls[:3]], dtype=np.uint64), _records(ctls[:3], probs[:3], 0, bufs))
