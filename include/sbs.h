@@ -291,6 +291,51 @@ int sbs_set_state(sbs_handle* h, const void* buf, size_t bytes, void* stream);
 int sbs_solve_mppi_static(const sbs_config* cfg, const sbs_problem* prob, const float* state_in,
                           float* state_out, uint64_t iter, sbs_result* result, void* stream);
 
+/* ---------------------------------------------------------------- sample sharding
+ * One controller's K samples split over `world` ranks (a process and a GPU
+ * each), by tiles: rank r rolls out tiles [r ntiles / world, (r + 1) ntiles /
+ * world).  The samples are independent (Alg. 1 Sampling and Rollout, Alg. 4);
+ * the updates (Alg. 1 Update, Alg. 3, Alg. 5) need every sample's cost, so one
+ * iteration is
+ *   sbs_shard_rollout on every rank (same problem, own rank),
+ *   an element-wise SUM over ranks of the exchange buffer taken as int32 words
+ *     (an all-reduce; each word is written by at most one rank and is zero on
+ *     all others, so the sum is the written bits exactly),
+ *   sbs_shard_update on every rank with the summed buffer.
+ * Every rank then holds the distribution, result, costs, frequencies and elite
+ * list an unsharded sbs_solve of the same controller gives, bit for bit: the
+ * MPPI combine runs over the same tile rows in tile order, the selection over
+ * the same costs, and the refit regenerates the elite deviations from their
+ * Philox counters.  A solve of `iterations` rounds is `iterations` such rounds
+ * (the warm-start shift applies to the first).  The library calls no
+ * collective: the caller brings its own (NCCL, or gloo through host memory). */
+
+/* Bytes of the exchange buffer: 32-bit words, costs [K] at word 0, quantised
+ * frequencies [K] at word Kp, MPPI tile rows [ntiles][12 nt + 8] at word 2 Kp,
+ * where Kp = K rounded up to a multiple of 64. */
+size_t sbs_shard_exchange_bytes(const sbs_handle* h);
+
+/* Tiles of the controller (ceil(K / tile)), the units sbs_shard_range splits. */
+int sbs_shard_tiles(const sbs_handle* h);
+
+/* Host only: the tiles [*begin, *end) of rank `rank` of `world` (contiguous,
+ * sizes differing by at most one, empty when world > ntiles).
+ * SBS_ERR_INVALID_ARG unless 0 <= rank < world and ntiles >= 0. */
+int sbs_shard_range(int ntiles, int rank, int world, int* begin, int* end);
+
+/* This rank's part of one iteration, enqueued on stream: zeroes the exchange
+ * buffer xbuf (device, 16-byte aligned, sbs_shard_exchange_bytes) and writes
+ * this rank's samples' costs and frequencies and its tiles' MPPI rows into it.
+ * prob: device pointers only (host_memory = 0).  The first call after creation
+ * resets the distribution with the problem's gait, as sbs_solve does.
+ * SBS_ERR_INVALID_ARG while a rollout of this handle waits for its
+ * sbs_shard_update (and sbs_solve refuses the handle meanwhile). */
+int sbs_shard_rollout(sbs_handle* h, const sbs_problem* prob, int rank, int world, void* xbuf, void* stream);
+
+/* The update of the iteration from the summed exchange buffer (device,
+ * unchanged), enqueued on stream; result is a device sbs_result. */
+int sbs_shard_update(sbs_handle* h, const void* xbuf, sbs_result* result, void* stream);
+
 /* ---------------------------------------------------------------- batching
  * Many controllers of uneven K and H solved in one set of launches per tick
  * (one block per (controller, tile) item, or a persistent launch pulling items

@@ -412,7 +412,7 @@ int sbs_prepare(sbs_handle* h) { return h ? ensure_workspace(h) : SBS_ERR_INVALI
 
 int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* stream)
 {
-    if (!h || !prob || !result || !prob->x0 || !prob->xref) return SBS_ERR_INVALID_ARG;
+    if (!h || !prob || !result || !prob->x0 || !prob->xref || h->shard_pending) return SBS_ERR_INVALID_ARG;
     if (h->hP.world_feet && !prob->feet) return SBS_ERR_INVALID_ARG;
     int st = validate_gait(&prob->gait);
     if (st) return st;
@@ -482,6 +482,114 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         if (cudaMemcpyAsync(result, h->res_dev, sizeof(sbs_result), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return SBS_ERR_CUDA;
     }
+    return SBS_OK;
+}
+
+// ---- sample sharding of one controller over ranks (one GPU each) -----------------
+// Exchange buffer, 32-bit words: costs [K] at 0, quantised frequencies [K] at Kp,
+// MPPI tile rows [ntiles][part_stride] at 2 Kp (Kp = K rounded up to 64 words).
+static size_t shard_costs_stride(const sbs_handle* h) { return align_up((size_t)h->hP.K, 64); }
+
+size_t sbs_shard_exchange_bytes(const sbs_handle* h)
+{
+    if (!h) return 0;
+    return 4 * (2 * shard_costs_stride(h) + (size_t)h->hP.ntiles * h->hP.part_stride);
+}
+
+int sbs_shard_range(int ntiles, int rank, int world, int* begin, int* end)
+{
+    if (ntiles < 0 || world < 1 || rank < 0 || rank >= world || !begin || !end) return SBS_ERR_INVALID_ARG;
+    *begin = (int)((int64_t)ntiles * rank / world);
+    *end = (int)((int64_t)ntiles * (rank + 1) / world);
+    return SBS_OK;
+}
+
+int sbs_shard_tiles(const sbs_handle* h) { return h ? h->hP.ntiles : SBS_ERR_INVALID_ARG; }
+
+int sbs_shard_rollout(sbs_handle* h, const sbs_problem* prob, int rank, int world, void* xbuf, void* stream)
+{
+    if (!h || !prob || !prob->x0 || !prob->xref || !xbuf || prob->host_memory) return SBS_ERR_INVALID_ARG;
+    if (((uintptr_t)xbuf & 15) != 0 || h->shard_pending) return SBS_ERR_INVALID_ARG;
+    if (h->hP.world_feet && !prob->feet) return SBS_ERR_INVALID_ARG;
+    const InstParams& P = h->hP;
+    int begin = 0, end = 0;
+    int st = sbs_shard_range(P.ntiles, rank, world, &begin, &end);
+    if (st) return st;
+    st = validate_gait(&prob->gait);
+    if (st) return st;
+    if (prob->shift < 0 || (P.P > 0 && prob->shift > 1)) return SBS_ERR_INVALID_ARG;
+    st = ensure_workspace(h);
+    if (st) return st;
+    int shift = prob->shift;
+    if (!h->initialized) {
+        TickArgs t0 = make_tick(h, prob->gait);
+        st = launch_init(h->dP, P, t0, stream);
+        if (st) return st;
+        h->initialized = true;
+        shift = 0;
+    }
+    TickArgs t = make_tick(h, prob->gait);
+    t.x0 = prob->x0;
+    t.xref = prob->xref;
+    t.fext = prob->f_ext;
+    t.feet = prob->feet;
+    const bool first = h->shard_it == 0;
+    t.shift = first ? shift : 0;
+    t.partials = (P.method == SBS_MPPI || (P.compare_mppi && first)) ? 2 : 0;
+    t.mppi_to_state = P.method == SBS_MPPI ? 1 : 0;
+    t.regen = 1;  // no rank holds another rank's deviations: the refit regenerates them
+    t.tile_base = begin;
+    t.result = nullptr;
+    t.ws = h->ws;
+    const size_t Kp = shard_costs_stride(h);
+    t.ws.J = (float*)xbuf;
+    t.ws.q = (int32_t*)xbuf + Kp;
+    t.ws.part = (float*)xbuf + 2 * Kp;
+    t.ws.hist = nullptr;  // built from the assembled costs by the update
+    t.ws.best = nullptr;
+    t.ws.nfin = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(xbuf, 0, sbs_shard_exchange_bytes(h), s) != cudaSuccess) return SBS_ERR_CUDA;
+    st = launch_rollout(h->dP, P, t, stream, h->spt == 2 ? 2 : 1, end - begin);
+    if (st) return st;
+    h->shard_t = t;
+    h->shard_pending = true;
+    return SBS_OK;
+}
+
+int sbs_shard_update(sbs_handle* h, const void* xbuf, sbs_result* result, void* stream)
+{
+    if (!h || !xbuf || !result || !h->shard_pending) return SBS_ERR_INVALID_ARG;
+    const InstParams& P = h->hP;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t Kp = shard_costs_stride(h);
+    const float* x = (const float*)xbuf;
+    TickArgs t = h->shard_t;
+    t.ws = h->ws;
+    t.result = result;
+    if (cudaMemcpyAsync(t.ws.J, x, (size_t)P.K * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(t.ws.q, x + Kp, (size_t)P.K * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return SBS_ERR_CUDA;
+    int st;
+    if (t.partials) {
+        if (cudaMemcpyAsync(t.ws.part, x + 2 * Kp, (size_t)P.ntiles * P.part_stride * 4, cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess)
+            return SBS_ERR_CUDA;
+        st = launch_shard_finish(h->dP, P, t, stream);
+        if (st) return st;
+    }
+    if (P.method != SBS_MPPI) {
+        st = launch_cost_keys(h->dP, P, t, stream);
+        if (st) return st;
+        st = launch_select(h->dP, P, t, stream);
+        if (st) return st;
+        st = launch_refit(h->dP, P, t, stream);
+        if (st) return st;
+    }
+    h->shard_pending = false;
+    h->shard_it = (h->shard_it + 1) % h->cfg.iterations;
+    h->cur ^= 1;
+    h->iter += 1;
     return SBS_OK;
 }
 

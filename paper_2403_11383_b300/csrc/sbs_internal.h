@@ -87,10 +87,11 @@ struct TickArgs {
     int32_t shift;       // warm-start shift applied while staging (first iteration only)
     int32_t src;         // current state buffer; the update writes state[1 - src]
     uint64_t iter;       // Philox iteration counter
-    int32_t partials;    // 1: this iteration forms MPPI partial sums
+    int32_t partials;    // 1: this iteration forms MPPI partial sums and combines them; 2: the tile
+                         // rows only (a sharded solve combines all ranks' rows afterwards)
     int32_t mppi_to_state;  // 1: the MPPI combine is the update; 0: it goes to mppi_mean
     int32_t regen;       // 1: the sampled deviations are not stored; their readers regenerate them
-    int32_t pad0;
+    int32_t tile_base;   // first tile of a plain rollout launch (a shard of the controller's tiles)
     sbs_result* result;
     Workspace ws;
 };
@@ -225,7 +226,10 @@ inline bool pair_capable(int P, bool ext, int T) { return P == 0 && !ext && T % 
 
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
-int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream, int spt = 1);
+int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream, int spt = 1,
+                   int tiles = -1);
+int launch_shard_finish(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
+int launch_cost_keys(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 int launch_refit(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);
 // A batched tick's device header: two count blocks of 8 ints (the first rollout
@@ -272,6 +276,9 @@ struct sbs_handle {
     uint64_t uid;          // creation number, unique over the process (a reused address gets a new one)
     int spt;               // samples per thread of plain solves: 0 (default: one), 1 or 2
     int regen;             // 1: plain solves do not store the sampled deviations (readers regenerate them)
+    bool shard_pending;    // a sample-sharded rollout waits for its update
+    int shard_it;          // iteration of the sharded solve in progress (0: its first)
+    sbs::TickArgs shard_t; // that rollout's tick arguments
 };
 
 

@@ -371,27 +371,50 @@ __device__ void mppi_finish(BlockShared& sh, const Views& v, const float* row, b
     __syncthreads();
 }
 
+// One listed sample's contribution w d to a float4 column of a tile's row, with
+// Kahan compensation (the weighted mean of Alg. 5 summed over the tile).
+__device__ __forceinline__ void kahan_wsum4(float4& s, float4& c, float w, float4 d)
+{
+    kahan_add(s.x, c.x, __fmul_rn(w, d.x));
+    kahan_add(s.y, c.y, __fmul_rn(w, d.y));
+    kahan_add(s.z, c.z, __fmul_rn(w, d.z));
+    kahan_add(s.w, c.w, __fmul_rn(w, d.w));
+}
+
 // ---- hierarchical combine: the last tile of a group of kGroup tiles combines
 // the group's rows in tile order; the last group combines the group rows, and the
 // last block of all finishes the MPPI update.
+__device__ void group_combine(BlockShared& sh, const Views& v, int g);
+
 __device__ void tile_combine(BlockShared& sh, const Views& v, int tile)
 {
     const InstParams& P = sh.P;
     const TickArgs& t = sh.t;
-    const int tid = threadIdx.x, T = blockDim.x;
-    const int PS = P.part_stride;
     const int g = tile / kGroup;
     const int gsize = min(kGroup, P.ntiles - g * kGroup);
     unsigned* counters = t.ws.counters;
     __threadfence();
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&counters[g], 1u);
         sh.last = prev == (unsigned)gsize - 1u;
     }
     __syncthreads();
     if (!sh.last) return;
     __threadfence();
+    group_combine(sh, v, g);
+}
+
+// Group g's rows combined in tile order (every row of the group written); the
+// last group to finish combines the group rows and finishes the update.
+__device__ void group_combine(BlockShared& sh, const Views& v, int g)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int PS = P.part_stride;
+    const int gsize = min(kGroup, P.ntiles - g * kGroup);
+    unsigned* counters = t.ws.counters;
     float* comb = v.acc;  // nf + kPartHeader floats (blockDim >= 64 leaves room)
     const float* src_rows = t.ws.part + (size_t)g * kGroup * PS;
     combine_rows(sh, src_rows, gsize, PS, P.nf, P.inv_lambda, comb);
@@ -717,27 +740,21 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
             const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
             const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
-            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ac = a;
             if (t.regen) {  // the listed samples' deviations regenerated from their draws
 #pragma unroll 1
                 for (int e = sl; e < nnz; e += nsl) {
                     const float2 we = lst[e];
                     const float4 d = regen_quad((uint32_t)(tile * T + __float_as_int(we.y)), j, c - 3 * j, t.iter,
                                                 P.seed, P.ctrl, sd4);
-                    a.x = fmaf(we.x, d.x, a.x);
-                    a.y = fmaf(we.x, d.y, a.y);
-                    a.z = fmaf(we.x, d.z, a.z);
-                    a.w = fmaf(we.x, d.w, a.w);
+                    kahan_wsum4(a, ac, we.x, d);
                 }
             } else {
 #pragma unroll 4
                 for (int e = sl; e < nnz; e += nsl) {
                     const float2 we = lst[e];
                     const float4 d = src[3 * __float_as_int(we.y)];
-                    a.x = fmaf(we.x, d.x, a.x);
-                    a.y = fmaf(we.x, d.y, a.y);
-                    a.z = fmaf(we.x, d.z, a.z);
-                    a.w = fmaf(we.x, d.w, a.w);
+                    kahan_wsum4(a, ac, we.x, d);
                 }
             }
             if (nsl == 1) row4[c] = a;
@@ -800,7 +817,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
         row[4] = a3;
     }
 
-    tile_combine(sh, v, tile);
+    if (t.partials == 1) tile_combine(sh, v, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -1051,27 +1068,21 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
             const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
             const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
             const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
-            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ac = a;
             if (t.regen) {  // the listed samples' deviations regenerated from their draws
 #pragma unroll 1
                 for (int e = sl; e < nnz; e += nsl) {
                     const float2 we = lst[e];
                     const float4 d = regen_quad((uint32_t)(tile * T + __float_as_int(we.y)), j, c - 3 * j, t.iter,
                                                 P.seed, P.ctrl, sd4);
-                    a.x = fmaf(we.x, d.x, a.x);
-                    a.y = fmaf(we.x, d.y, a.y);
-                    a.z = fmaf(we.x, d.z, a.z);
-                    a.w = fmaf(we.x, d.w, a.w);
+                    kahan_wsum4(a, ac, we.x, d);
                 }
             } else {
 #pragma unroll 4
                 for (int e = sl; e < nnz; e += nsl) {
                     const float2 we = lst[e];
                     const float4 d = src[3 * __float_as_int(we.y)];
-                    a.x = fmaf(we.x, d.x, a.x);
-                    a.y = fmaf(we.x, d.y, a.y);
-                    a.z = fmaf(we.x, d.z, a.z);
-                    a.w = fmaf(we.x, d.w, a.w);
+                    kahan_wsum4(a, ac, we.x, d);
                 }
             }
             if (nsl == 1) row4[c] = a;
@@ -1106,7 +1117,7 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
         row[3] = a2;
         row[4] = a3;
     }
-    tile_combine(sh, v, tile);
+    if (t.partials == 1) tile_combine(sh, v, tile);
 }
 
 // Cost of an order-preserving key (inverse of cost_key).
@@ -1778,7 +1789,7 @@ __device__ __forceinline__ void rollout_plain(const InstParams* __restrict__ dP,
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
+    rollout_tile<NP, EXT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
 }
 
 template <int NP, bool EXT>
@@ -1804,7 +1815,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_rollout_pair(const Inst
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), blockIdx.x);
+    rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -1825,6 +1836,88 @@ __global__ void __launch_bounds__(kRefitLanesMax) k_refit(const InstParams* __re
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
     refit_block<REGEN>(sh, blockIdx.x);
+}
+
+// ---- sample sharding: one controller's tiles split over ranks.  Each rank's
+// rollout writes its tiles' costs, frequencies and MPPI rows (t.partials = 2: no
+// combine); once every rank holds all of them, each runs the update below and
+// the selection / refit of the unsharded solve, on the same bits.
+
+// The MPPI combine over every tile's row (Alg. 5 with the per-tile max shift):
+// block g combines group g, the last group finishes, as the last tile of each
+// group does in an unsharded rollout.  Only the shifted mean and variance are
+// staged (the update reads nothing else of the rollout's staging).
+__global__ void __launch_bounds__(256) k_shard_combine(const InstParams* __restrict__ dP, TickArgs t)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    load_params(dP, sh);
+    if (threadIdx.x == 0) sh.t = t;
+    __syncthreads();
+    const InstParams& P = sh.P;
+    const float* sm = P.state[t.src];
+    const float* sv = sm + P.D;
+    Views v;
+    v.mu = reinterpret_cast<float*>(dyn4);
+    v.vr = v.mu + P.nb * P.nf;
+    v.acc = v.vr + P.nb * P.nf;
+    v.sd = v.xr = v.Bs = v.Mb = nullptr;
+    v.dsm = nullptr;
+    for (int i = threadIdx.x; i < P.nb * P.nf; i += blockDim.x) {
+        float m, var;
+        shifted_entry(P, sh.t, sm, sv, i, m, var);
+        v.mu[i] = m;
+        v.vr[i] = var;
+    }
+    if (threadIdx.x == 0) {
+        sh.mu_f = P.adaptive ? sm[P.D - 1] : P.q_init * 0.001f;
+        sh.var_f = P.adaptive ? sv[P.D - 1] : 0.0f;
+    }
+    __syncthreads();
+    group_combine(sh, v, blockIdx.x);
+}
+
+// The selection's side data from the full cost array: the key histograms of a
+// large elite selection, and Naive's best complemented (cost key, index) per
+// force block with its finite count.  Integer sums and maxima: the same words
+// as the rollout tiles' atomics leave, whatever the order.
+__global__ void __launch_bounds__(256) k_cost_keys(const InstParams* __restrict__ dP, TickArgs t)
+{
+    const int K = dP->K, n_freq = dP->n_freq, adaptive = dP->adaptive;
+    const uint32_t seed = dP->seed, ctrl = dP->ctrl;
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < (uint32_t)K;
+    const float J = valid ? __ldcg(t.ws.J + k) : kInf;
+    if (t.ws.hist) {
+        const uint32_t bin = cost_key(J) >> 16;
+        const unsigned act = __ballot_sync(kFull, valid);
+        if (valid) {
+            const unsigned peers = __match_any_sync(act, bin);
+            if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
+            const unsigned peers8 = __match_any_sync(act, bin >> 8);
+            if (lane == __ffs(peers8) - 1) atomicAdd(t.ws.hist + kHistBins + (bin >> 8), (unsigned)__popc(peers8));
+        }
+    }
+    if (t.ws.best) {
+        const int blk = (valid && !adaptive && n_freq > 0) ? freq_block(k, t.iter, seed, ctrl, n_freq) : 0;
+        const bool fin = valid && J < kInf;
+        const unsigned long long key = fin ? ~(((unsigned long long)cost_key(J) << 32) | k) : 0ull;
+        unsigned todo = __reduce_or_sync(kFull, fin ? 1u << blk : 0u);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            unsigned long long m = blk == b ? key : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long x = __shfl_xor_sync(kFull, m, o);
+                m = x > m ? x : m;
+            }
+            if (lane == 0) atomicMax(t.ws.best + b, m);
+        }
+        const unsigned nfw = __popc(__ballot_sync(kFull, fin));
+        if (lane == 0 && nfw) atomicAdd(t.ws.nfin, nfw);
+    }
 }
 
 __global__ void k_init(const InstParams* __restrict__ dP, TickArgs t)
@@ -2410,8 +2503,10 @@ int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, v
     return status_of(cudaGetLastError());
 }
 
-int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream, int spt)
+int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream, int spt, int tiles)
 {
+    if (tiles < 0) tiles = hP.ntiles;
+    if (tiles == 0) return SBS_OK;
     const bool ext = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
     const bool pair = spt == 2 && pair_capable(hP.P, ext, hP.T);
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb, pair);
@@ -2423,7 +2518,23 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
     const InstParams* parg = dP;
     void* args[] = {(void*)&parg, (void*)&targ};
     return status_of(
-        cudaLaunchKernel(fn, dim3(hP.ntiles), dim3(pair ? hP.T / 2 : hP.T), args, smem, (cudaStream_t)stream));
+        cudaLaunchKernel(fn, dim3(tiles), dim3(pair ? hP.T / 2 : hP.T), args, smem, (cudaStream_t)stream));
+}
+
+int launch_shard_finish(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
+{
+    const size_t smem = (2 * (size_t)hP.nb * hP.nf + hP.nf + kPartHeader) * sizeof(float);
+    int st = ensure_smem_attr((const void*)k_shard_combine, smem);
+    if (st) return st;
+    k_shard_combine<<<hP.ngroups, 256, smem, (cudaStream_t)stream>>>(dP, t);
+    return status_of(cudaGetLastError());
+}
+
+int launch_cost_keys(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)
+{
+    if (!t.ws.hist && !t.ws.best) return SBS_OK;
+    k_cost_keys<<<(hP.K + 255) / 256, 256, 0, (cudaStream_t)stream>>>(dP, t);
+    return status_of(cudaGetLastError());
 }
 
 int launch_select(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream)

@@ -166,6 +166,11 @@ ABI = {
     "sbs_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "sbs_batch_set_theta_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "sbs_batch_get_theta_mode": (C.c_int, [C.c_void_p]),
+    "sbs_shard_exchange_bytes": (C.c_size_t, [C.c_void_p]),
+    "sbs_shard_tiles": (C.c_int, [C.c_void_p]),
+    "sbs_shard_range": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sbs_shard_rollout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sbs_shard_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_fp32_peak": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sbs_sincos": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -421,6 +426,26 @@ class Controller:
         check(lib().sbs_solve(self._h, C.byref(problem), out, _stream_ptr(stream)), "sbs_solve")
         return result
 
+    # ---- sample sharding (the exchange between ranks is the caller's; see sharding.py)
+    def shard_exchange_bytes(self) -> int:
+        return lib().sbs_shard_exchange_bytes(self._h)
+
+    def shard_tiles(self) -> int:
+        return lib().sbs_shard_tiles(self._h)
+
+    def shard_rollout(self, problem: Problem, rank: int, world: int, xbuf, stream=None):
+        """This rank's tiles of one iteration into xbuf (a CUDA tensor of
+        shard_exchange_bytes() bytes), for a device Problem from problem()."""
+        check(lib().sbs_shard_rollout(self._h, C.byref(problem), rank, world, C.c_void_p(xbuf.data_ptr()),
+                                      _stream_ptr(stream)), "sbs_shard_rollout")
+
+    def shard_update(self, xbuf, result, stream=None):
+        """The iteration's update from the exchange buffer summed over ranks;
+        result: a uint8 CUDA tensor of RESULT_BYTES."""
+        check(lib().sbs_shard_update(self._h, C.c_void_p(xbuf.data_ptr()), C.c_void_p(result.data_ptr()),
+                                     _stream_ptr(stream)), "sbs_shard_update")
+        return result
+
     def read(self, which: int, stream=None):
         import torch
         naive_n = max(1, len(self.cfg.get("freq_set_mhz", ()))) + 1  # per-block winners, best block
@@ -561,6 +586,13 @@ def solve_mppi_static(cfg: dict, x0, xref, gait, f_ext, shift, state_in, state_o
     check(lib().sbs_solve_mppi_static(C.byref(c), C.byref(p), C.c_void_p(state_in.data_ptr()),
                                       C.c_void_p(state_out.data_ptr()), it, C.c_void_p(result.data_ptr()),
                                       _stream_ptr(stream)), "sbs_solve_mppi_static")
+
+
+def shard_range(ntiles: int, rank: int, world: int):
+    """Tiles [begin, end) of rank `rank` of `world` (host arithmetic, no GPU)."""
+    b, e = C.c_int(), C.c_int()
+    check(lib().sbs_shard_range(ntiles, rank, world, C.byref(b), C.byref(e)), "sbs_shard_range")
+    return b.value, e.value
 
 
 def philox(ctr, key, stream=None):
