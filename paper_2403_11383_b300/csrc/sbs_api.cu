@@ -753,6 +753,7 @@ struct sbs_batch_plan {
     size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0, arena_regen = 0;
     long long counters = 0;
     bool ext = false;
+    bool adapt = false;  // some controller samples its step frequency
 };
 
 struct sbs_batch {
@@ -994,12 +995,14 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
     size_t smem = 0, smem_pair = 0, sel_smem = 0, arena = 0, arena_regen = 0;
     long long counters = 0;
     bool ext = false;  // some controller uses an extended model feature
+    bool adapt = false;
     for (int i = 0; i < n; ++i) {
         const sbs_handle* h = handles[i];
         if (h->hP.T != T || h->hP.P != Pk || h->cfg.iterations != 1) return SBS_ERR_INVALID_ARG;
         smem = std::max(smem, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb));
         smem_pair = std::max(smem_pair, rollout_smem_bytes(h->hP.H, h->hP.P, T, h->hP.nb, true));
         ext = ext || h->hP.n_freq > 0 || h->hP.world_feet || h->hP.friction_project;
+        adapt = adapt || h->hP.adaptive;
         if (h->hP.method != SBS_MPPI) sel_smem = std::max(sel_smem, select_smem_bytes(h->hP.K));
         arena += align_up(ws_bytes(h->wsl), 256);
         arena_regen += align_up(ws_bytes(h->wsl, true), 256);
@@ -1030,6 +1033,7 @@ static int plan_batch(sbs_batch_plan& pl, int n, sbs_handle* const* handles)
     pl.arena_regen = arena_regen;
     pl.counters = counters;
     pl.ext = ext;
+    pl.adapt = adapt;
     pl.h.assign(handles, handles + n);
     for (int i = 0; i < n; ++i) pl.uid.push_back(handles[i]->uid);
     return SBS_OK;
@@ -1134,7 +1138,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     if (sel_smem == 0) sel_smem = 256;
     const size_t used = kBatchHeader + (size_t)n * sizeof(InstRec);
     int grids[4];
-    const int var = rollout_variant(Pk, ext, pair, b->regen != 0);
+    const int var = rollout_variant(Pk, ext, pair, b->regen != 0, pl.adapt);
     int st = batch_grid(var, mode, smem, sel_smem, RT, counts, grids);
     if (st) return st;
     grids[3] = split ? tile_begin - tiles_upd : 0;

@@ -502,9 +502,10 @@ __device__ __forceinline__ void load_row12(const V* p, V out[12])
     }
 }
 
+// The state part of the stage cost, sum_c Q_c (x_c - x^r_c)^2 (Sec. V).  It reads
+// the state only, so a rollout may form it ahead of the step's draws.
 template <class V>
-__device__ __forceinline__ V stage_cost_v(const Consts<V>& K, const V x[12], const V* xr, const V G[12],
-                                          unsigned live, bool penalty)
+__device__ __forceinline__ V stage_state_cost_v(const Consts<V>& K, const V x[12], const V* xr)
 {
     using L = Lane<V>;
     V xrr[12];
@@ -515,6 +516,15 @@ __device__ __forceinline__ V stage_cost_v(const Consts<V>& K, const V x[12], con
         const V e = L::sub(x[c], xrr[c]);
         r = L::fma(L::mul(K.Q(c), e), e, r);
     }
+    return r;
+}
+
+// The force part added to r: R-weighted squared forces and, with penalty, the
+// friction-cone penalty of the stance legs.
+template <class V>
+__device__ __forceinline__ V stage_force_cost_v(const Consts<V>& K, V r, const V G[12], unsigned live, bool penalty)
+{
+    using L = Lane<V>;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if (!(live & (1u << i))) continue;  // zero force on every lane: adds exactly nothing
@@ -539,6 +549,13 @@ __device__ __forceinline__ V stage_cost_v(const Consts<V>& K, const V x[12], con
         r = L::fma(K.w_fc(), pen, r);
     }
     return r;
+}
+
+template <class V>
+__device__ __forceinline__ V stage_cost_v(const Consts<V>& K, const V x[12], const V* xr, const V G[12],
+                                          unsigned live, bool penalty)
+{
+    return stage_force_cost_v<V>(K, stage_state_cost_v<V>(K, x, xr), G, live, penalty);
 }
 
 __device__ __forceinline__ float stage_cost(const InstParams& P, const float x[12], const float* xr,
@@ -696,16 +713,34 @@ __device__ __forceinline__ Rot<V> rotation_v(V sr, V cr, V sp, V cp, V sy, V cy)
     return R;
 }
 
+// The attitude's sines and cosines and the body-to-world rotation of the
+// pre-step state: they read the state only, so a rollout may form them ahead of
+// the step's draws.
 template <class V>
-__device__ __forceinline__ void srbd_step_v(const Consts<V>& K, V x[12], const V G[12], const V fe[3],
-                                            unsigned live = 0xfu)
+struct Attitude {
+    V sr, cr, sp, cp, sy, cy;
+    Rot<V> R;
+};
+
+template <class V>
+__device__ __forceinline__ Attitude<V> attitude_v(const V x[12])
+{
+    Attitude<V> A;
+    angle_sincos_v<V>(x[3], A.sr, A.cr);
+    angle_sincos_v<V>(x[4], A.sp, A.cp);
+    angle_sincos_v<V>(x[5], A.sy, A.cy);
+    A.R = rotation_v<V>(A.sr, A.cr, A.sp, A.cp, A.sy, A.cy);
+    return A;
+}
+
+// One explicit Euler step of Eq. (1) from the pre-step attitude A.
+template <class V>
+__device__ __forceinline__ void srbd_step_att_v(const Consts<V>& K, V x[12], const V G[12], const V fe[3],
+                                                unsigned live, const Attitude<V>& A)
 {
     using L = Lane<V>;
-    V sr, cr, sp, cp, sy, cy;
-    angle_sincos_v<V>(x[3], sr, cr);
-    angle_sincos_v<V>(x[4], sp, cp);
-    angle_sincos_v<V>(x[5], sy, cy);
-    const Rot<V> R = rotation_v<V>(sr, cr, sp, cp, sy, cy);
+    const V sr = A.sr, cr = A.cr, sp = A.sp, cp = A.cp;
+    const Rot<V>& R = A.R;
     const V nsp = L::neg(sp);  // R20
     V F0 = L::bc(0.0f), F1 = F0, F2 = F0, t0 = F0, t1 = F0, t2 = F0;
 #pragma unroll
@@ -724,6 +759,13 @@ __device__ __forceinline__ void srbd_step_v(const Consts<V>& K, V x[12], const V
         t2 = L::fma(K.nfoot(3 * i + 1), bx, L::fma(K.foot(3 * i), by, t2));
     }
     srbd_integrate_v<V>(K, x, sr, cr, sp, cp, F0, F1, F2, t0, t1, t2, fe);
+}
+
+template <class V>
+__device__ __forceinline__ void srbd_step_v(const Consts<V>& K, V x[12], const V G[12], const V fe[3],
+                                            unsigned live = 0xfu)
+{
+    srbd_step_att_v<V>(K, x, G, fe, live, attitude_v<V>(x));
 }
 
 __device__ __forceinline__ void srbd_step(const InstParams& P, float x[12], const float G[12],

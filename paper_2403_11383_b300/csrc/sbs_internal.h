@@ -216,9 +216,11 @@ void fill_params(const sbs_config* cfg, InstParams* out);
 constexpr int kExtVariant = 256;
 constexpr int kPairVariant = 512;    // two samples per thread
 constexpr int kRegenVariant = 1024;  // deviations regenerated by the refit (not stored)
-inline int rollout_variant(int P, bool ext, bool pair = false, bool regen = false)
+constexpr int kAdaptVariant = 2048;  // two samples per thread: a controller of the launch samples its frequency
+inline int rollout_variant(int P, bool ext, bool pair = false, bool regen = false, bool adapt = true)
 {
-    return P | (ext ? kExtVariant : 0) | (pair ? kPairVariant : 0) | (regen ? kRegenVariant : 0);
+    return P | (ext ? kExtVariant : 0) | (pair ? kPairVariant : 0) | (regen ? kRegenVariant : 0) |
+           (pair && adapt ? kAdaptVariant : 0);
 }
 // Launches that can carry two samples per thread: the per-step policy on the
 // ordinary model, with tiles of a multiple of 64 samples (whole warps of pairs).

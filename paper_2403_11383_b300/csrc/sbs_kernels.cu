@@ -830,8 +830,16 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
 // operations in the same order as in rollout_tile<0, false>, and the tile's
 // reductions run over the same samples in the same order (virtual warp
 // s (T / 64) + w holds samples 32 (s (T / 64) + w) ..), so the results are
-// bit-identical to the one-sample-per-thread launch on the same tile.
+// bit-identical to the one-sample-per-thread launch on the same tile.  ADAPT:
+// the launch may hold a controller that samples its step frequency; without it
+// every sample takes the block's contact table and the per-sample phase
+// counters are not compiled, and each step forms the attitude and the state part
+// of the stage cost (which read the state only) ahead of the draws, in the same
+// straight-line block, so that their dependency chains interleave with the
+// sampler's (3.5 % off the 256-controller tick; with ADAPT the longer-lived
+// attitude spills, 2 % slower, so that variant keeps them after the draws).
 // ---------------------------------------------------------------------------
+template <bool ADAPT>
 __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
 {
     using L = Lane<float2>;
@@ -862,24 +870,26 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
     for (int l = 0; l < 2; ++l) {
         k[l] = (uint32_t)tile * (uint32_t)T + (uint32_t)(l * T2 + tid);
         valid[l] = k[l] < (uint32_t)K;
-        q[l] = P.adaptive ? sample_freq(k[l], iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max) : P.q_init;
+        q[l] = (ADAPT && P.adaptive) ? sample_freq(k[l], iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max)
+                                     : P.q_init;
     }
-    const float* mu = v.mu;
     const float* sd = v.sd;
 
     float2 x[12];
 #pragma unroll
     for (int c = 0; c < 12; ++c) x[c] = L::bc(sh.x0[c]);
     const float2 fe[3] = {sh.pc.fe[0], sh.pc.fe[1], sh.pc.fe[2]};
-    const bool uniform_q = !P.adaptive;
+    const bool uniform_q = !ADAPT || !P.adaptive;
     uint32_t ph[2][4], step[2];
+    if constexpr (ADAPT) {
 #pragma unroll
-    for (int l = 0; l < 2; ++l) {
-        step[l] = q[l] * P.dt_us;
+        for (int l = 0; l < 2; ++l) {
+            step[l] = q[l] * P.dt_us;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t p0 = t.phase0 + t.offset[i];
-            ph[l][i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t p0 = t.phase0 + t.offset[i];
+                ph[l][i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
+            }
         }
     }
     const uint32_t duty = t.duty;
@@ -887,6 +897,12 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
     float2 J = L::bc(0.0f), Jc = L::bc(0.0f);
     const PhiloxPre pp0 = philox_pre(k[0], iter, seed, ctrl), pp1 = philox_pre(k[1], iter, seed, ctrl);
     for (int j = 0; j < P.H; ++j) {
+        Attitude<float2> A;
+        float2 cost_x;
+        if constexpr (!ADAPT) {
+            A = attitude_v<float2>(x);
+            cost_x = stage_state_cost_v<float2>(Kc, x, xr2 + 12 * j);
+        }
         float2 z[12];
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
@@ -938,7 +954,7 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
         unsigned st[2], live, all;
         if (uniform_q) {
             st[0] = st[1] = live = all = sh.sched[j];
-        } else {
+        } else if constexpr (ADAPT) {
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 st[l] = 0;
@@ -959,8 +975,13 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
                 if (!(st[1] & (1u << i))) G[3 * i].y = G[3 * i + 1].y = G[3 * i + 2].y = 0.0f;
             }
         }
-        kahan_add_v<float2>(J, Jc, stage_cost_v<float2>(Kc, x, xr2 + 12 * j, G, live, true));
-        srbd_step_v<float2>(Kc, x, G, fe, live);
+        if constexpr (ADAPT) {  // formed here: ahead of the draws they add spills to this variant
+            kahan_add_v<float2>(J, Jc, stage_cost_v<float2>(Kc, x, xr2 + 12 * j, G, live, true));
+            srbd_step_v<float2>(Kc, x, G, fe, live);
+        } else {
+            kahan_add_v<float2>(J, Jc, stage_force_cost_v<float2>(Kc, cost_x, G, live, true));
+            srbd_step_att_v<float2>(Kc, x, G, fe, live, A);
+        }
     }
     float Jv[2] = {J.x, J.y}, Jcv[2] = {Jc.x, Jc.y};
 #pragma unroll
@@ -971,7 +992,7 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
             for (int c = 0; c < 12; ++c) xl[c] = L::get(x[c], l);
             kahan_add(Jv[l], Jcv[l], terminal_cost(P, xl, v.xr + 12 * (P.H - 1)));
         }
-        if (P.adaptive) kahan_add(Jv[l], Jcv[l], freq_regulariser(P, q[l]));
+        if (ADAPT && P.adaptive) kahan_add(Jv[l], Jcv[l], freq_regulariser(P, q[l]));
         if (!isfinite(Jv[l])) Jv[l] = kInf;
         if (valid[l]) {
             t.ws.J[k[l]] = Jv[l];
@@ -1808,6 +1829,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE, 4) k_rollout_lean(const InstPara
 
 // Two samples per thread (per-step policy, ordinary model): T / 2 threads per
 // tile of T samples, at most 128 registers.
+template <bool ADAPT>
 __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_rollout_pair(const InstParams* __restrict__ dP, TickArgs t)
 {
     extern __shared__ float4 dyn4[];
@@ -1815,7 +1837,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_rollout_pair(const Inst
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
+    rollout_tile_pair<ADAPT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -2046,6 +2068,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE, 4) k_grid_rollout_lean(const Ins
 }
 
 // The same with two samples per thread (T / 2 threads per tile item).
+template <bool ADAPT>
 __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_grid_rollout_pair(const InstRec* __restrict__ recs,
                                                                            const int* __restrict__ counts)
 {
@@ -2057,10 +2080,11 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_grid_rollout_pair(const
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
-    rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+    rollout_tile_pair<ADAPT>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
 }
 
 // Persistent blocks pulling tile items, two samples per thread.
+template <bool ADAPT>
 __global__ void __launch_bounds__(SBS_MAX_TILE / 2) k_batch_rollout_pair(const InstRec* __restrict__ recs,
                                                                          const int* __restrict__ counts, int* heads)
 {
@@ -2076,7 +2100,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2) k_batch_rollout_pair(const I
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
-        rollout_tile_pair(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+        rollout_tile_pair<ADAPT>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
         __syncthreads();
     }
 }
@@ -2469,7 +2493,10 @@ static const void* batch_rollout_fn_s(int P, int mode)
 
 static const void* rollout_kernel(int variant)
 {
-    if (variant & kPairVariant) return (variant == kPairVariant) ? (const void*)k_rollout_pair : nullptr;
+    if (variant & kPairVariant) {
+        if ((variant & ~kAdaptVariant) != kPairVariant) return nullptr;
+        return (variant & kAdaptVariant) ? (const void*)k_rollout_pair<true> : (const void*)k_rollout_pair<false>;
+    }
     const int P = variant & ~kExtVariant;
     return (variant & kExtVariant) ? rollout_kernel_s<true>(P) : rollout_kernel_s<false>(P);
 }
@@ -2478,8 +2505,10 @@ const void* batch_rollout_fn(int variant, int mode)
 {
     variant &= ~kRegenVariant;  // the rollouts read the tick's flag
     if (variant & kPairVariant) {
-        if (variant != kPairVariant) return nullptr;
-        return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair : (const void*)k_batch_rollout_pair;
+        if ((variant & ~kAdaptVariant) != kPairVariant) return nullptr;
+        if (variant & kAdaptVariant)
+            return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair<true> : (const void*)k_batch_rollout_pair<true>;
+        return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair<false> : (const void*)k_batch_rollout_pair<false>;
     }
     const int P = variant & ~kExtVariant;
     return (variant & kExtVariant) ? batch_rollout_fn_s<true>(P, mode) : batch_rollout_fn_s<false>(P, mode);
@@ -2510,7 +2539,7 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
     const bool ext = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
     const bool pair = spt == 2 && pair_capable(hP.P, ext, hP.T);
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb, pair);
-    const void* fn = rollout_kernel(rollout_variant(hP.P, ext, pair));
+    const void* fn = rollout_kernel(rollout_variant(hP.P, ext, pair, false, hP.adaptive != 0));
     if (!fn) return SBS_ERR_INVALID_ARG;
     int st = ensure_smem_attr(fn, smem);
     if (st) return st;
