@@ -597,7 +597,8 @@ __device__ __forceinline__ void cone_project(float mu, float inv_1pmu2, float& g
 // |x| = kSinCosMax (a rollout that has long left any meaningful attitude: its
 // cost is infinite or ungated) and for non-finite x the lane takes the hardware
 // approximation, which costs a few instructions where the accurate library
-// routine would take its slow reduction path.
+// routine would take its slow reduction path.  Both are formed on every lane and
+// the lane selects (2.4 % off the batched tick against a per-lane branch).
 constexpr float kSinCosMax = 65536.0f;
 
 template <class V>
@@ -621,17 +622,16 @@ __device__ __forceinline__ void sincos_v(V x, V& s, V& c)
 #pragma unroll
     for (int l = 0; l < L::N; ++l) {
         const float xl = L::get(x, l);
-        float sl, cl;
-        if (fabsf(xl) <= kSinCosMax) {
-            const int q = __float_as_int(L::get(jm, l));
-            const float a = L::get(sn, l), b = L::get(cs, l);
-            sl = (q & 1) ? b : a;
-            cl = (q & 1) ? a : b;
-            sl = __int_as_float(__float_as_int(sl) ^ ((q & 2) << 30));
-            cl = __int_as_float(__float_as_int(cl) ^ (((q + 1) & 2) << 30));
-        } else {
-            __sincosf(xl, &sl, &cl);
-        }
+        const int q = __float_as_int(L::get(jm, l));
+        const float a = L::get(sn, l), b = L::get(cs, l);
+        float sl = (q & 1) ? b : a, cl = (q & 1) ? a : b;
+        sl = __int_as_float(__float_as_int(sl) ^ ((q & 2) << 30));
+        cl = __int_as_float(__float_as_int(cl) ^ (((q + 1) & 2) << 30));
+        float hs, hc;  // formed on every lane and selected: a per-lane branch splits the step's code
+        __sincosf(xl, &hs, &hc);
+        const bool big = !(fabsf(xl) <= kSinCosMax);
+        sl = big ? hs : sl;
+        cl = big ? hc : cl;
         L::set(s, l, sl);
         L::set(c, l, cl);
     }
