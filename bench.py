@@ -6,6 +6,9 @@ MPPI or elite 5 %), one graph-replayed batched launch set per tick (grid or
 persistent mode, picked by the autotuner), inputs resident in HBM, synthetic
 seeded data.  A step is one tick: rollout,
 cost, update of all 256 controllers (warm-started from the previous tick).
+Every timed tick (or single-controller solve) has its own CUDA events, and a
+buffer of twice the L2 size is written before it, outside the events, so no
+tick starts with the previous one's data in L2.
 
 Metric: rollout sample-steps per second (sum of K*H over the controllers
 solved, per second of tick time); also reported: solves/s, tick latency
@@ -100,6 +103,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and the parity record")
     ap.add_argument("--no-parity", action="store_true", help="skip the per-output FP64 error record")
     ap.add_argument("--no-serving", action="store_true", help="skip the closed-loop serving comparison")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the serialised plain-solve comparison (its controllers' own workspaces)")
     ap.add_argument("--serving-seconds", type=float, default=3.0)
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain_mppi_k512_h12", "adaptive_elite_k8192_h25", "spline_k262144_h100",
@@ -182,6 +187,55 @@ class Clocks:
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+class L2Flush:
+    """Writes a device buffer of twice the L2 size between timed iterations, so
+    each tick or solve starts with nothing of the previous one cached; the write
+    runs outside the iteration's CUDA events."""
+
+    def __init__(self, dev):
+        import torch
+        l2 = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (126 << 20)
+        self.bytes = 2 * int(l2)
+        self.buf = torch.empty(self.bytes, dtype=torch.uint8, device=dev)
+        self.n = 0
+
+    def __call__(self):
+        self.n += 1
+        self.buf.fill_(self.n & 0xFF)
+
+    def describe(self):
+        return (f"L2 flushed between timed iterations: {self.bytes / 2**20:.0f} MiB (2 x L2) written "
+                f"before each tick or solve, outside its CUDA events")
+
+
+def timed_iterations(fn, steps, flush, stream):
+    """Device time (ms) of each of `steps` calls of fn on the stream, with the L2
+    flushed before each call, outside the call's events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def timed_host_iterations(fn, steps, flush):
+    """Wall time (s) of each of `steps` synchronous calls of fn, with the L2
+    flushed (and the device idle) before each call."""
+    import torch
+    out = []
+    for _ in range(steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        out.append(time.perf_counter() - t0)
+    return out
 
 
 def solve_launches(cfg):
@@ -399,21 +453,17 @@ def run_single(args, world, rank, local):
         ctl.solve(x0, xref, prob["gait"], fe, 0 if w == 0 else 1, res, feet=feet)
     p1 = ctl.problem(x0, xref, prob["gait"], fe, 1, feet=feet)  # built once, as a control loop would
     tune = ctl.autotune(p1, res, ticks=5)  # samples per thread x stored or regenerated deviations
+    flush = L2Flush(dev)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
     barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctl.solve_packed(p1, res)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    solve_ms = timed_iterations(lambda: ctl.solve_packed(p1, res), args.steps, flush, stream)
     torch.cuda.nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    ms = max_over_ranks(sum(solve_ms) / args.steps, world, dev)
     ss = cfg["K"] * cfg["H"] * cfg["iterations"]
     # algorithmic FLOPs of a solve from the oracle's counts: every iteration's
     # rollouts (sampled frequencies: the last solve's), and the MPPI mean of an
@@ -432,11 +482,11 @@ def run_single(args, world, rank, local):
     r = S.Result()
     hp = ctl.problem(hx0, hxr, prob["gait"], hfe, 1, host=True, feet=hfeet)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+
+    def host_solve():
         ctl.solve_packed(hp, r)
         torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    e2e_s = max_over_ranks(sum(timed_host_iterations(host_solve, args.steps, flush)) / args.steps, world, dev)
     if rank == 0:
         line = {"metric": "rollout sample-steps/s", "value": world * ss / (ms * 1e-3), "unit": "sample-steps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -448,7 +498,7 @@ def run_single(args, world, rank, local):
                            "sampled_deviations": "regenerate" if ctl.theta_mode() == S.THETA_REGENERATE else "store",
                            "autotune_ms_per_solve": {f"spt{k[0]}_{'regen' if k[1] else 'store'}": v
                                                      for k, v in tune.items()},
-                           "parallelism": f"replicas x{world}"},
+                           "l2": flush.describe(), "parallelism": f"replicas x{world}"},
                 "solves_per_s": world / (ms * 1e-3),
                 "roofline": {"kernel": "whole solve", "bound": "alu", "achieved": achieved, "peak": peak,
                              "unit": "TFLOP/s", "frac": achieved / peak,
@@ -506,8 +556,12 @@ def main():
     ss_tick = sum(c["K"] * c["H"] for c, _ in mix)
     mppi_ss = sum(c["K"] * c["H"] for c, _ in mix if c["method"] == "mppi")
     mppi_n = sum(1 for c, _ in mix if c["method"] == "mppi")
-    arena = sum(c.workspace_bytes() + 256 for c in ctls)
+    # workspaces for stored deviations, unless the deviations are fixed to be regenerated
+    ws_mode = S.THETA_REGENERATE if args.theta == "regenerate" else S.THETA_STORE
+    arena = sum(c.workspace_bytes_mode(ws_mode) + 256 for c in ctls)
     batch = S.Batch(n, 2 * arena, inflight=2)  # two ticks in flight: the next is prepared while one runs
+    if args.theta != "auto":  # from the first tick: the arena may fit only this mode
+        batch.set_theta_mode(ws_mode)
     results = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device=dev)
 
     def problems(shift):
@@ -539,43 +593,34 @@ def main():
              if v not in ("auto", 0)}
     for _ in range(3):  # rebuild the tick graphs in the chosen mode before timing
         tick()
+    flush = L2Flush(dev)
     torch.cuda.synchronize()
 
-    # ---- timed region: K ticks back to back on the stream
+    # ---- timed region: K ticks on the stream, each timed by its own events with
+    # the L2 flushed before it
     clocks = Clocks(local)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")  # profilers can select exactly the timed launches
-    e0.record(stream)
-    for _ in range(args.steps):
-        tick()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    tick_ms = timed_iterations(tick, args.steps, flush, stream)
     torch.cuda.nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = sum(tick_ms) / args.steps
     ms = max_over_ranks(ms, world, dev)
     value = world * ss_tick / (ms * 1e-3)
 
     # ---- tick latency distribution (device time of each tick)
-    lat = []
     n_lat = max(args.steps, 400)  # enough ticks for a 99th percentile
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
-    for a, b in ev:
-        a.record(stream)
-        tick()
-        b.record(stream)
-    torch.cuda.synchronize()
-    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    lat = sorted(timed_iterations(tick, n_lat, flush, stream))
     p50, p99 = lat[len(lat) // 2], lat[min(len(lat) - 1, int(0.99 * len(lat)))]
 
     # ---- stage durations with per-stage events (dominant kernel for the roofline)
     batch.set_profiling(True)
     st = []
     for _ in range(args.steps):
+        flush()
         tick()
         st.append(batch.stage_ms())
     batch.set_profiling(False)
@@ -609,18 +654,17 @@ def main():
     nominal = 148 * 128 * 2 * 2032e6 / 1e12
 
     # ---- plain form: one sbs_solve (its own launches) per controller, serialised
-    plain_ticks = max(3, min(args.steps, 40))
-    pres = [torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device=dev) for _ in range(n)]
-    for i in range(n):
-        ctls[i].solve(x0[i], xref[i], gaits[i], fext[i], 1, pres[i])
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(plain_ticks):
-        for i in range(n):
-            ctls[i].solve(x0[i], xref[i], gaits[i], fext[i], 1, pres[i])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1) / plain_ticks
+    plain_ms = None
+    if not args.no_plain:
+        plain_ticks = max(3, min(args.steps, 40))
+        pres = [torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device=dev) for _ in range(n)]
+
+        def plain_tick():
+            for i in range(n):
+                ctls[i].solve(x0[i], xref[i], gaits[i], fext[i], 1, pres[i])
+        plain_tick()
+        torch.cuda.synchronize()
+        plain_ms = sum(timed_iterations(plain_tick, plain_ticks, flush, stream)) / plain_ticks
 
     # ---- end to end through the C ABI from host memory: sbs_batch_solve_host
     # gathers every controller's inputs into its pinned staging buffer, copies
@@ -635,10 +679,7 @@ def main():
         batch.solve_host(hpacked, h_out)
     torch.cuda.synchronize()
     barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        batch.solve_host(hpacked, h_out)
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = sum(timed_host_iterations(lambda: batch.solve_host(hpacked, h_out), args.steps, flush)) / args.steps
     e2e_s = max_over_ranks(e2e_s, world, dev)
     e2e_value = world * ss_tick / e2e_s
     h2d_bytes = sum(4 * (a.size + b.size + c.size) for a, b, c in zip(h_x0, h_xr, h_fe))
@@ -677,15 +718,14 @@ def main():
                        "autotune_ms_per_tick": {"grid": tune_ms[0], "persistent": tune_ms[1]},
                        "samples_per_thread": spt, "sampled_deviations": theta,
                        "fixed_by_flags": fixed or None,
-                       "l2": f"per-tick working set above L2 (workspace of the {n} controllers "
-                       f"{arena / 1e9:.2f} GB; with stored deviations every tick writes "
-                       f"{48 * ss_tick / 1e9:.2f} GB of them)", "workspace_bytes": 2 * arena,
+                       "l2": flush.describe(), "workspace_bytes": 2 * arena,
                        "parallelism": f"replicas x{world}"},
             "solves_per_s": world * n / (ms * 1e-3),
             "latency_ms": {"p50": p50, "p99": p99, "ticks": len(lat),
                            "kind": f"device time of one {len(mix)}-controller tick"},
-            "plain": {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
-                      "solves_per_s": n / (plain_ms * 1e-3), "kind": "256 serialised sbs_solve calls"},
+            "plain": None if plain_ms is None else
+                     {"ms_per_tick": plain_ms, "sample_steps_per_s": ss_tick / (plain_ms * 1e-3),
+                      "solves_per_s": n / (plain_ms * 1e-3), "kind": f"{n} serialised sbs_solve calls"},
             "stages_ms": {"rollout": roll_ms, "select": sel_ms, "refit": ref_ms},
             "roofline": {"kernel": {("grid", 1): "k_grid_rollout_lean", ("grid", 2): "k_grid_rollout_pair",
                                     ("persistent", 1): "k_batch_rollout<0, false>",

@@ -441,7 +441,10 @@ int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int
  * sampled deviations, on these controllers and problems (real solves: they
  * advance the controllers), keeps the setting with the shortest mean tick and
  * reports each mode's best mean tick time in ms_out[0] (grid) and ms_out[1]
- * (persistent). */
+ * (persistent; 1e30 where nothing was measured).  A setting whose workspace does
+ * not fit the batch's arena (stored deviations in an arena sized by
+ * sbs_workspace_bytes_mode(h, SBS_THETA_REGENERATE)) is skipped; SBS_ERR_BUDGET
+ * when none fits. */
 int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                        sbs_result* results, int ticks, float ms_out[2], void* stream);
 

@@ -1299,12 +1299,19 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
                 b->spt = sp;
                 b->regen = rg;
                 double tot = 0.0;
+                bool fits = true;
                 for (int k = 0; k <= ticks && st == SBS_OK; ++k) {  // the first tick of a setting is a warm-up
                     st = sbs_batch_solve(b, n, handles, probs, results, stream);
+                    if (k == 0 && st == SBS_ERR_BUDGET) {  // refused before any launch: the setting's
+                        st = SBS_OK;                       // workspace does not fit the arena
+                        fits = false;
+                        break;
+                    }
                     float ms[3];
                     if (st == SBS_OK) st = sbs_batch_stage_ms(b, ms);
                     if (st == SBS_OK && k > 0) tot += (double)ms[0] + ms[1] + ms[2];
                 }
+                if (!fits) continue;
                 const float avg = (float)(tot / ticks);
                 if (st == SBS_OK && avg < ms_out[m]) ms_out[m] = avg;
                 if (st == SBS_OK && avg < best) {
@@ -1318,6 +1325,7 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
     }
     sbs_batch_set_profiling(b, prof ? 1 : 0);
     if (st) return st;
+    if (best >= 1e30f) return SBS_ERR_BUDGET;  // no setting fits the arena
     b->mode = best_mode;
     b->spt = best_spt;
     b->regen = best_regen;

@@ -102,3 +102,46 @@ def test_batched_regenerate_equals_store(mode):
                                               sets[S.THETA_REGENERATE][i].read(which).cpu().numpy())
     for b in batches.values():
         b.close()
+
+
+def test_autotune_in_an_arena_for_regenerated_deviations():
+    # an arena sized for regenerated deviations: the autotuner skips the stored
+    # settings (refused before any launch) and keeps one that fits; the next tick
+    # equals a batch's that ran the same ticks with the kept setting; an arena that
+    # fits nothing is refused
+    import torch
+    mix = W.batch_mix(6, seed=93)
+    for c, _ in mix:
+        c.update(tile=128, lam=20.0)
+    ta = [S.Controller(c) for c, _ in mix]
+    tb = [S.Controller(c) for c, _ in mix]
+    tens = [(_dev(p["x0"]), _dev(p["xref"]), _dev(p["f_ext"])) for _, p in mix]
+    n = len(mix)
+    small = sum(c.workspace_bytes_mode(S.THETA_REGENERATE) + 256 for c in ta)
+    assert small < sum(c.workspace_bytes_mode(S.THETA_STORE) + 256 for c in ta)
+    ba = S.Batch(n, small)
+    ra = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rb = torch.empty_like(ra)
+    pa = [ta[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 1) for i in range(n)]
+    pb = [tb[i].problem(*tens[i][:2], mix[i][1]["gait"], tens[i][2], 1) for i in range(n)]
+    grid_ms, pers_ms = ba.autotune(ta, pa, ra, ticks=1)
+    assert 0 < grid_ms < 1e29 and 0 < pers_ms < 1e29
+    assert ba.theta_mode() == S.THETA_REGENERATE
+    bb = S.Batch(n, small)
+    bb.set_theta_mode(S.THETA_REGENERATE)
+    bb.set_mode(ba.mode())
+    bb.set_samples_per_thread(ba.samples_per_thread())
+    for _ in range(2 * 2 * 2):  # 2 launch modes x 2 sample counts x (1 + 1) ticks, regenerated only
+        bb.solve(tb, pb, rb)
+    ba.solve(ta, pa, ra)
+    bb.solve(tb, pb, rb)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
+    for i in range(n):
+        np.testing.assert_array_equal(ta[i].read(S.BUF_MEAN).cpu().numpy(), tb[i].read(S.BUF_MEAN).cpu().numpy())
+    tiny = S.Batch(n, 4096)
+    with pytest.raises(S.SBSError) as e:
+        tiny.autotune(ta, pa, ra, ticks=1)
+    assert e.value.status == S.ERR_BUDGET
+    for b in (ba, bb, tiny):
+        b.close()
