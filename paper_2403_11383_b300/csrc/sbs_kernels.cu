@@ -832,12 +832,13 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
 // s (T / 64) + w holds samples 32 (s (T / 64) + w) ..), so the results are
 // bit-identical to the one-sample-per-thread launch on the same tile.  ADAPT:
 // the launch may hold a controller that samples its step frequency; without it
-// every sample takes the block's contact table and the per-sample phase
-// counters are not compiled, and each step forms the attitude and the state part
-// of the stage cost (which read the state only) ahead of the draws, in the same
-// straight-line block, so that their dependency chains interleave with the
-// sampler's (3.5 % off the 256-controller tick; with ADAPT the longer-lived
-// attitude spills, 2 % slower, so that variant keeps them after the draws).
+// every sample takes the block's contact table and the per-sample phase counter
+// is not compiled (fewer registers, no spills).  With it, each sample carries
+// one gait phase and forms its legs' phases from the block's offsets at every
+// step (one register instead of four).  Each step forms the attitude and the
+// state part of the stage cost (which read the state only) ahead of the draws,
+// in the same straight-line block, so that their dependency chains interleave
+// with the sampler's (3.5 % off the 256-controller tick).
 // ---------------------------------------------------------------------------
 template <bool ADAPT>
 __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
@@ -880,16 +881,12 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
     for (int c = 0; c < 12; ++c) x[c] = L::bc(sh.x0[c]);
     const float2 fe[3] = {sh.pc.fe[0], sh.pc.fe[1], sh.pc.fe[2]};
     const bool uniform_q = !ADAPT || !P.adaptive;
-    uint32_t ph[2][4], step[2];
+    uint32_t ph[2], step[2];
     if constexpr (ADAPT) {
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
             step[l] = q[l] * P.dt_us;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t p0 = t.phase0 + t.offset[i];
-                ph[l][i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
-            }
+            ph[l] = t.phase0;
         }
     }
     const uint32_t duty = t.duty;
@@ -897,12 +894,8 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
     float2 J = L::bc(0.0f), Jc = L::bc(0.0f);
     const PhiloxPre pp0 = philox_pre(k[0], iter, seed, ctrl), pp1 = philox_pre(k[1], iter, seed, ctrl);
     for (int j = 0; j < P.H; ++j) {
-        Attitude<float2> A;
-        float2 cost_x;
-        if constexpr (!ADAPT) {
-            A = attitude_v<float2>(x);
-            cost_x = stage_state_cost_v<float2>(Kc, x, xr2 + 12 * j);
-        }
+        const Attitude<float2> A = attitude_v<float2>(x);
+        const float2 cost_x = stage_state_cost_v<float2>(Kc, x, xr2 + 12 * j);
         float2 z[12];
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
@@ -960,10 +953,12 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
                 st[l] = 0;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    st[l] |= (ph[l][i] < duty ? 1u : 0u) << i;
-                    ph[l][i] += step[l];
-                    if (ph[l][i] >= kPhaseOne) ph[l][i] -= kPhaseOne;
+                    uint32_t pi = ph[l] + sh.t.offset[i];
+                    if (pi >= kPhaseOne) pi -= kPhaseOne;
+                    st[l] |= (pi < duty ? 1u : 0u) << i;
                 }
+                ph[l] += step[l];
+                if (ph[l] >= kPhaseOne) ph[l] -= kPhaseOne;
             }
             live = __reduce_or_sync(kFull, st[0] | st[1]);
             all = __reduce_and_sync(kFull, st[0] & st[1]);
@@ -975,13 +970,8 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
                 if (!(st[1] & (1u << i))) G[3 * i].y = G[3 * i + 1].y = G[3 * i + 2].y = 0.0f;
             }
         }
-        if constexpr (ADAPT) {  // formed here: ahead of the draws they add spills to this variant
-            kahan_add_v<float2>(J, Jc, stage_cost_v<float2>(Kc, x, xr2 + 12 * j, G, live, true));
-            srbd_step_v<float2>(Kc, x, G, fe, live);
-        } else {
-            kahan_add_v<float2>(J, Jc, stage_force_cost_v<float2>(Kc, cost_x, G, live, true));
-            srbd_step_att_v<float2>(Kc, x, G, fe, live, A);
-        }
+        kahan_add_v<float2>(J, Jc, stage_force_cost_v<float2>(Kc, cost_x, G, live, true));
+        srbd_step_att_v<float2>(Kc, x, G, fe, live, A);
     }
     float Jv[2] = {J.x, J.y}, Jcv[2] = {Jc.x, Jc.y};
 #pragma unroll
