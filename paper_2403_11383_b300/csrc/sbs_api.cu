@@ -1066,7 +1066,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
     const int Pk = handles[0]->hP.P;
     const std::vector<int>& order = pl.order;
     const bool ext = pl.ext;
-    const bool pair = b->spt == 2 && pair_capable(Pk, ext, T);
+    const bool pair = b->spt == 2 && pair_capable(Pk, ext, T) && pl.smem_pair <= kMaxDynamicSmem;
     const size_t smem = pair ? pl.smem_pair : pl.smem;
     const int RT = pair ? T / 2 : T;  // threads of a rollout block
     size_t sel_smem = pl.sel_smem;
@@ -1282,12 +1282,14 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
     int st = sbs_batch_set_profiling(b, 1);
     if (st) return st;
     // launch modes, and one or two samples per thread where the launch can take two
-    bool ext = false;
+    bool ext = false, fits = true;
     for (int i = 0; i < n; ++i) {
         if (!handles[i]) return SBS_ERR_INVALID_ARG;
-        ext = ext || handles[i]->hP.n_freq > 0 || handles[i]->hP.world_feet || handles[i]->hP.friction_project;
+        const InstParams& Pi = handles[i]->hP;
+        ext = ext || Pi.n_freq > 0 || Pi.world_feet || Pi.friction_project;
+        fits = fits && pair_fits(Pi.H, Pi.P, Pi.T, Pi.nb);
     }
-    const int nspt = pair_capable(handles[0]->hP.P, ext, handles[0]->hP.T) ? 2 : 1;
+    const int nspt = pair_capable(handles[0]->hP.P, ext, handles[0]->hP.T) && fits ? 2 : 1;
     const int modes[2] = {SBS_BATCH_GRID, SBS_BATCH_PERSISTENT};
     float best = 1e30f;
     int best_mode = SBS_BATCH_GRID, best_spt = 1, best_regen = 0;
@@ -1338,7 +1340,7 @@ extern "C" int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* 
     if (!h || !prob || !result || ticks < 1 || !ms_out) return SBS_ERR_INVALID_ARG;
     const InstParams& P = h->hP;
     const bool ext = P.n_freq > 0 || P.world_feet || P.friction_project;
-    const int nspt = pair_capable(P.P, ext, P.T) ? 2 : 1;
+    const int nspt = pair_capable(P.P, ext, P.T) && pair_fits(P.H, P.P, P.T, P.nb) ? 2 : 1;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {

@@ -521,6 +521,29 @@ __device__ __forceinline__ V stage_state_cost_v(const Consts<V>& K, const V x[12
 
 // The force part added to r: R-weighted squared forces and, with penalty, the
 // friction-cone penalty of the stance legs.
+// The same from a reference row of single floats, broadcast to both lanes.
+__device__ __forceinline__ float2 stage_state_cost_bc(const Consts<float2>& K, const float2 x[12], const float* xr)
+{
+    using L = Lane<float2>;
+    const float4* r4 = reinterpret_cast<const float4*>(xr);
+    float xs[12];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float4 a = r4[q];
+        xs[4 * q] = a.x;
+        xs[4 * q + 1] = a.y;
+        xs[4 * q + 2] = a.z;
+        xs[4 * q + 3] = a.w;
+    }
+    float2 r = L::bc(0.0f);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const float2 e = L::sub(x[c], L::bc(xs[c]));
+        r = L::fma(L::mul(K.Q(c), e), e, r);
+    }
+    return r;
+}
+
 template <class V>
 __device__ __forceinline__ V stage_force_cost_v(const Consts<V>& K, V r, const V G[12], unsigned live, bool penalty)
 {

@@ -123,7 +123,8 @@ inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1, bool pair = fa
                   + (P > 0 ? (size_t)48 * ((P + 3) / 4) * T : 0)  // per-thread knot deviations
                   + (P > 0 ? (size_t)nwarps * nf  // per-warp partial sums, then the combined row
                            : (size_t)(6 * T > nf + kPartHeader ? 6 * T : nf + kPartHeader));  // weight list and slice sums, then the combined row
-    if (pair) floats = ((floats + 3) & ~(size_t)3) + 72 * (size_t)H;  // reference, mean, deviation as duplicated pairs
+    if (pair)  // duplicated pairs: reference, mean and deviation rows (per-step policy); basis rows (spline)
+        floats = ((floats + 3) & ~(size_t)3) + (P > 0 ? 8 * (size_t)((P + 3) / 4) * H : 72 * (size_t)H);
     return floats * sizeof(float);
 }
 
@@ -220,11 +221,13 @@ constexpr int kAdaptVariant = 2048;  // two samples per thread: a controller of 
 inline int rollout_variant(int P, bool ext, bool pair = false, bool regen = false, bool adapt = true)
 {
     return P | (ext ? kExtVariant : 0) | (pair ? kPairVariant : 0) | (regen ? kRegenVariant : 0) |
-           (pair && adapt ? kAdaptVariant : 0);
+           (pair && adapt && P == 0 ? kAdaptVariant : 0);
 }
-// Launches that can carry two samples per thread: the per-step policy on the
-// ordinary model, with tiles of a multiple of 64 samples (whole warps of pairs).
-inline bool pair_capable(int P, bool ext, int T) { return P == 0 && !ext && T % 64 == 0; }
+// Launches that can carry two samples per thread: the ordinary model (per-step or
+// spline policy), with tiles of a multiple of 64 samples (whole warps of pairs).
+inline bool pair_capable(int P, bool ext, int T) { (void)P; return !ext && T % 64 == 0; }
+// ... and whose duplicated rows fit the shared memory of a block.
+inline bool pair_fits(int H, int P, int T, int nb) { return rollout_smem_bytes(H, P, T, nb, true) <= kMaxDynamicSmem; }
 
 // Host-side launchers (defined in sbs_kernels.cu).
 int launch_init(const InstParams* dP, const InstParams& hP, const TickArgs& t, void* stream);

@@ -785,7 +785,7 @@ __device__ void rollout_tile(BlockShared& sh, float* dyn, int tile)
             for (int p = 0; p < NP; ++p) {
                 float vv[12], o[3];
 #pragma unroll
-                for (int c = 0; c < 12; ++c) vv[c] = w * dsf[(((size_t)c * NQ + p / 4) * T + tid) * 4 + (p & 3)];
+                for (int c = 0; c < 12; ++c) vv[c] = __fmul_rn(w, dsf[(((size_t)c * NQ + p / 4) * T + tid) * 4 + (p & 3)]);
                 const int c0 = warp_sum12(vv, o);
                 if ((lane & 7) == 0) {
                     float* a = v.acc + warp * P.nf + 12 * p + c0;
@@ -1113,6 +1113,284 @@ __device__ void rollout_tile_pair(BlockShared& sh, float* dyn, int tile)
                 row4[c] = a;
             }
         }
+    }
+    if (tid == 0) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int ww = 0; ww < 2 * nw2; ++ww) {
+            a0 += sh.red[ww][0];
+            a1 += sh.red[ww][1];
+            a2 += sh.red[ww][2];
+            a3 += sh.red[ww][3];
+        }
+        row[0] = mt;
+        row[1] = a0;
+        row[2] = a1;
+        row[3] = a2;
+        row[4] = a3;
+    }
+    if (t.partials == 1) tile_combine(sh, v, tile);
+}
+
+// The spline basis as duplicated pairs for the two-sample spline rollout, after
+// the spline layout's per-warp sums (16-byte aligned): bs2 [H][4 ceil(P / 4)].
+// The reference and the mean force trajectory stay single floats, broadcast to
+// both lanes when read: duplicated, they would take the shared memory of a third
+// block per SM (8 warps instead of 12; 0.436 against 0.421 ms per solve of the
+// 262 144-sample spline workload).
+__device__ __forceinline__ float2* pair_spline_rows(const Views& v, const InstParams& P, int T)
+{
+    return reinterpret_cast<float2*>(v.acc + (size_t)(T / 32) * P.nf);
+}
+
+// Float index of knot p, force component c of lane l (0: sample i, 1: sample
+// i + T / 2) of thread i in the two-sample knot-deviation planes: plane
+// (c ceil(NP / 4) + p / 4) 2 + (p mod 4) / 2 holds, per thread, the float4
+// (A_p', B_p', A_p'+1, B_p'+1) with p' = p - p mod 2 (A, B: the thread's two
+// samples), so that a 16-byte load gives two knots as lane pairs and a warp's
+// loads are contiguous.
+template <int NP>
+__device__ __forceinline__ size_t pair_knot_index(int c, int p, int l, int T2, int tid)
+{
+    constexpr int NQ = (NP + 3) / 4;
+    return ((((size_t)c * NQ + p / 4) * 2 + ((p & 3) >> 1)) * T2 + tid) * 4 + 2 * (p & 1) + l;
+}
+
+// ---------------------------------------------------------------------------
+// One tile of T samples with two samples per thread and the spline policy of NP
+// knots (ordinary model): the knot deviations of both samples are drawn once,
+// as in rollout_tile<NP, false>, and kept in shared memory as lane pairs; each
+// step evaluates both samples' forces from the basis with packed FMAs, and the
+// stage cost and model step run on float2 lanes.  Every sample sees the
+// operations of rollout_tile<NP, false> in the same order, and the tile's
+// reductions run over virtual warps in the same order, so the results are
+// bit-identical to the one-sample launch on the same tile.  Each step forms the
+// attitude and the state part of the stage cost ahead of the force evaluation
+// (1 % here; in the one-sample kernel the same change was 8 % slower).
+// ---------------------------------------------------------------------------
+template <int NP>
+__device__ void rollout_tile_pair_spline(BlockShared& sh, float* dyn, int tile)
+{
+    using L = Lane<float2>;
+    constexpr int NQ = (NP + 3) / 4;
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int T2 = blockDim.x, T = 2 * T2, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw2 = T2 >> 5;
+    const Views v = carve(dyn, P.H, NP, P.nf, T, P.nb);
+    float2* bs2 = pair_spline_rows(v, P, T);
+    stage(sh, v, NP);
+    for (int i = tid; i < 4 * NQ * P.H; i += T2) bs2[i] = make_float2(v.Bs[i], v.Bs[i]);
+    fill_pair_consts(sh.pc, P, sh.fe);
+
+    const int K = P.K;
+    const uint32_t seed = P.seed, ctrl = P.ctrl;
+    const uint64_t iter = t.iter;
+    float* theta = t.ws.theta;
+    uint32_t k[2], q[2];
+    bool valid[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        k[l] = (uint32_t)tile * (uint32_t)T + (uint32_t)(l * T2 + tid);
+        valid[l] = k[l] < (uint32_t)K;
+        q[l] = P.adaptive ? sample_freq(k[l], iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max) : P.q_init;
+    }
+    const float* sd = v.sd;
+    // the knots' deviations sigma eps (stored for the update in store mode)
+    float* dsf = reinterpret_cast<float*>(v.dsm);
+#pragma unroll 1
+    for (int p = 0; p < 4 * NQ; ++p) {
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            float e[12];
+            if (p < NP) {
+                normals12(k[l], p, iter, seed, ctrl, e);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) e[c] = __fmul_rn(sd[12 * p + c], e[c]);
+                if (valid[l] && !t.regen) {
+                    float4* o = reinterpret_cast<float4*>(theta + ((size_t)p * K + k[l]) * 12);
+                    o[0] = make_float4(e[0], e[1], e[2], e[3]);
+                    o[1] = make_float4(e[4], e[5], e[6], e[7]);
+                    o[2] = make_float4(e[8], e[9], e[10], e[11]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) e[c] = 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < 12; ++c) dsf[pair_knot_index<NP>(c, p, l, T2, tid)] = e[c];
+        }
+    }
+    __syncthreads();
+    const Consts<float2> Kc{sh.pc};
+
+    float2 x[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) x[c] = L::bc(sh.x0[c]);
+    const float2 fe[3] = {sh.pc.fe[0], sh.pc.fe[1], sh.pc.fe[2]};
+    uint32_t ph[2], step[2];  // each sample's gait phase; the legs' phases add the block's offsets
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        ph[l] = t.phase0;
+        step[l] = q[l] * P.dt_us;
+    }
+    const uint32_t duty = t.duty;
+    const float4* dsm = v.dsm;
+
+    float2 J = L::bc(0.0f), Jc = L::bc(0.0f);
+    for (int j = 0; j < P.H; ++j) {
+        const Attitude<float2> A = attitude_v<float2>(x);
+        const float2 cost_x = stage_state_cost_bc(Kc, x, v.xr + 12 * j);
+        // forces: the mean trajectory plus the basis-weighted knot deviations, in
+        // knot order (packed FMAs over both samples)
+        float2 G[12];
+        {
+            const float4* m4 = reinterpret_cast<const float4*>(v.Mb + 12 * j);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const float4 m = m4[cc];
+                G[4 * cc] = L::bc(m.x);
+                G[4 * cc + 1] = L::bc(m.y);
+                G[4 * cc + 2] = L::bc(m.z);
+                G[4 * cc + 3] = L::bc(m.w);
+            }
+            const float4* b4 = reinterpret_cast<const float4*>(bs2 + j * 4 * NQ);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                float2 g = G[c];
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) {
+                    const float4 ba = b4[2 * qq], bb = b4[2 * qq + 1];
+                    const float4 da = lds4(dsm + ((size_t)(c * NQ + qq) * 2) * T2 + tid);
+                    const float4 db = lds4(dsm + ((size_t)(c * NQ + qq) * 2 + 1) * T2 + tid);
+                    g = L::fma(make_float2(ba.x, ba.y), make_float2(da.x, da.y), g);
+                    g = L::fma(make_float2(ba.z, ba.w), make_float2(da.z, da.w), g);
+                    g = L::fma(make_float2(bb.x, bb.y), make_float2(db.x, db.y), g);
+                    g = L::fma(make_float2(bb.z, bb.w), make_float2(db.z, db.w), g);
+                }
+                G[c] = g;
+            }
+        }
+        // each sample's stance legs; a swing leg's force is zeroed on its lane (every
+        // leg's terms are then summed, as in the one-sample spline kernel)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            unsigned st = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t pi = ph[l] + sh.t.offset[i];
+                if (pi >= kPhaseOne) pi -= kPhaseOne;
+                st |= (pi < duty ? 1u : 0u) << i;
+            }
+            ph[l] += step[l];
+            if (ph[l] >= kPhaseOne) ph[l] -= kPhaseOne;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (!(st & (1u << i))) {
+                    L::set(G[3 * i], l, 0.0f);
+                    L::set(G[3 * i + 1], l, 0.0f);
+                    L::set(G[3 * i + 2], l, 0.0f);
+                }
+        }
+        kahan_add_v<float2>(J, Jc, stage_force_cost_v<float2>(Kc, cost_x, G, 0xfu, true));
+        srbd_step_att_v<float2>(Kc, x, G, fe, 0xfu, A);
+    }
+    float Jv[2] = {J.x, J.y}, Jcv[2] = {Jc.x, Jc.y};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        if (P.w_terminal > 0.0f) {
+            float xl[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) xl[c] = L::get(x[c], l);
+            kahan_add(Jv[l], Jcv[l], terminal_cost(P, xl, v.xr + 12 * (P.H - 1)));
+        }
+        if (P.adaptive) kahan_add(Jv[l], Jcv[l], freq_regulariser(P, q[l]));
+        if (!isfinite(Jv[l])) Jv[l] = kInf;
+        if (valid[l]) {
+            t.ws.J[k[l]] = Jv[l];
+            t.ws.q[k[l]] = (int32_t)q[l];
+        }
+    }
+    if (t.ws.hist) {
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const uint32_t bin = cost_key(Jv[l]) >> 16;
+            const unsigned act = __ballot_sync(kFull, valid[l]);
+            if (valid[l]) {
+                const unsigned peers = __match_any_sync(act, bin);
+                if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
+                const unsigned peers8 = __match_any_sync(act, bin >> 8);
+                if (lane == __ffs(peers8) - 1) atomicAdd(t.ws.hist + kHistBins + (bin >> 8), (unsigned)__popc(peers8));
+            }
+        }
+    }
+    if (t.ws.best) {
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const bool fin = valid[l] && Jv[l] < kInf;
+            unsigned long long m = fin ? ~(((unsigned long long)cost_key(Jv[l]) << 32) | k[l]) : 0ull;
+            if (__any_sync(kFull, fin)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long xo = __shfl_xor_sync(kFull, m, o);
+                    m = xo > m ? xo : m;
+                }
+                if (lane == 0) atomicMax(t.ws.best, m);
+            }
+            const unsigned nfw = __popc(__ballot_sync(kFull, fin));
+            if (lane == 0 && nfw) atomicAdd(t.ws.nfin, nfw);
+        }
+    }
+    if (!t.partials) return;
+
+    // ---- MPPI partial sums of this tile, shifted by the tile's best cost, over
+    // virtual warps (lane 0 of warp w: virtual warp w; lane 1: nw2 + w)
+    bool fin[2];
+    fin[0] = valid[0] && Jv[0] < kInf;
+    fin[1] = valid[1] && Jv[1] < kInf;
+    const float mt = block_min(sh, fminf(fin[0] ? Jv[0] : kInf, fin[1] ? Jv[1] : kInf));
+    float w[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        w[l] = (fin[l] && mt < kInf) ? expf(-(Jv[l] - mt) * P.inv_lambda) : 0.0f;
+        const float f = (float)q[l] / 1000.0f;
+        const float s0 = warp_sum(w[l]), s1 = warp_sum(w[l] * w[l]), s2 = warp_sum(w[l] * f),
+                    s3 = warp_sum(fin[l] ? 1.0f : 0.0f);
+        if (lane == 0) {
+            float* r = sh.red[l * nw2 + warp];
+            r[0] = s0;
+            r[1] = s1;
+            r[2] = s2;
+            r[3] = s3;
+        }
+    }
+    const int PS = P.part_stride;
+    float* row = t.ws.part + (size_t)tile * PS;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        // a virtual warp whose weights all underflowed to zero contributes exact zeros
+        float* acc = v.acc + (size_t)(l * nw2 + warp) * P.nf;
+        if (!__any_sync(kFull, w[l] != 0.0f)) {
+            for (int d = lane; d < P.nf; d += 32) acc[d] = 0.0f;
+        } else {
+#pragma unroll 1
+            for (int p = 0; p < NP; ++p) {
+                float vv[12], o[3];
+#pragma unroll
+                for (int c = 0; c < 12; ++c) vv[c] = __fmul_rn(w[l], dsf[pair_knot_index<NP>(c, p, l, T2, tid)]);
+                const int c0 = warp_sum12(vv, o);
+                if ((lane & 7) == 0) {
+                    float* a = acc + 12 * p + c0;
+                    a[0] = o[0];
+                    a[1] = o[1];
+                    a[2] = o[2];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < P.nf; d += T2) {
+        float s = 0.0f;
+        for (int ww = 0; ww < 2 * nw2; ++ww) s += v.acc[ww * P.nf + d];
+        row[kPartHeader + d] = s;
     }
     if (tid == 0) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -1830,6 +2108,20 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 4) k_rollout_pair(const Inst
     rollout_tile_pair<ADAPT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
 }
 
+// Two samples per thread with the spline policy: at most 168 registers (the
+// knot deviations' shared memory allows three blocks per SM).
+template <int NP>
+__global__ void __launch_bounds__(SBS_MAX_TILE / 2, 3) k_rollout_pair_spline(const InstParams* __restrict__ dP,
+                                                                             TickArgs t)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    load_params(dP, sh);
+    if (threadIdx.x == 0) sh.t = t;
+    __syncthreads();
+    rollout_tile_pair_spline<NP>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
+}
+
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
 {
     extern __shared__ float4 dyn4[];
@@ -2091,6 +2383,44 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2) k_batch_rollout_pair(const I
         load_tick(&recs[i].t, sh);
         __syncthreads();
         rollout_tile_pair<ADAPT>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+        __syncthreads();
+    }
+}
+
+// The spline policy with two samples per thread (T / 2 threads per tile item).
+template <int NP>
+__global__ void __launch_bounds__(SBS_MAX_TILE / 2, 3) k_grid_rollout_pair_spline(const InstRec* __restrict__ recs,
+                                                                                  const int* __restrict__ counts)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    const int it = blockIdx.x + counts[4];
+    if (it >= counts[1]) return;
+    const int i = find_rec_block(sh, recs, counts[0], it, 0);
+    load_params(recs[i].dP, sh);
+    load_tick(&recs[i].t, sh);
+    __syncthreads();
+    rollout_tile_pair_spline<NP>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(SBS_MAX_TILE / 2) k_batch_rollout_pair_spline(const InstRec* __restrict__ recs,
+                                                                                const int* __restrict__ counts,
+                                                                                int* heads)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    const int n = counts[0], nitems = counts[1];
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(&heads[0], 1);
+        __syncthreads();
+        const int it = sh.item;
+        if (it >= nitems) break;
+        const int i = find_rec(recs, n, it, 0);
+        load_params(recs[i].dP, sh);
+        load_tick(&recs[i].t, sh);
+        __syncthreads();
+        rollout_tile_pair_spline<NP>(sh, reinterpret_cast<float*>(dyn4), it - recs[i].tile_begin);
         __syncthreads();
     }
 }
@@ -2481,9 +2811,29 @@ static const void* batch_rollout_fn_s(int P, int mode)
     }
 }
 
+static const void* pair_spline_fn(int P, int mode)  // mode: -1 plain launch
+{
+    switch (P) {
+#define SBS_PAIR_SPLINE(N)                                                                        \
+    case N:                                                                                       \
+        return mode < 0 ? (const void*)k_rollout_pair_spline<N>                                   \
+                        : mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair_spline<N>     \
+                                                 : (const void*)k_batch_rollout_pair_spline<N>;
+        SBS_PAIR_SPLINE(2)
+        SBS_PAIR_SPLINE(3)
+        SBS_PAIR_SPLINE(4)
+        SBS_PAIR_SPLINE(6)
+        SBS_PAIR_SPLINE(8)
+#undef SBS_PAIR_SPLINE
+        default: return nullptr;
+    }
+}
+
 static const void* rollout_kernel(int variant)
 {
     if (variant & kPairVariant) {
+        const int P = variant & 0xff;
+        if (P > 0) return (variant & ~0xff) == kPairVariant ? pair_spline_fn(P, -1) : nullptr;
         if ((variant & ~kAdaptVariant) != kPairVariant) return nullptr;
         return (variant & kAdaptVariant) ? (const void*)k_rollout_pair<true> : (const void*)k_rollout_pair<false>;
     }
@@ -2495,6 +2845,8 @@ const void* batch_rollout_fn(int variant, int mode)
 {
     variant &= ~kRegenVariant;  // the rollouts read the tick's flag
     if (variant & kPairVariant) {
+        const int P = variant & 0xff;
+        if (P > 0) return (variant & ~0xff) == kPairVariant ? pair_spline_fn(P, mode) : nullptr;
         if ((variant & ~kAdaptVariant) != kPairVariant) return nullptr;
         if (variant & kAdaptVariant)
             return mode == SBS_BATCH_GRID ? (const void*)k_grid_rollout_pair<true> : (const void*)k_batch_rollout_pair<true>;
@@ -2527,7 +2879,7 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
     if (tiles < 0) tiles = hP.ntiles;
     if (tiles == 0) return SBS_OK;
     const bool ext = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
-    const bool pair = spt == 2 && pair_capable(hP.P, ext, hP.T);
+    const bool pair = spt == 2 && pair_capable(hP.P, ext, hP.T) && pair_fits(hP.H, hP.P, hP.T, hP.nb);
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb, pair);
     const void* fn = rollout_kernel(rollout_variant(hP.P, ext, pair, false, hP.adaptive != 0));
     if (!fn) return SBS_ERR_INVALID_ARG;

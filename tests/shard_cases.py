@@ -19,6 +19,8 @@ CASES = {
     "mppi_k40000_groups": _cfg(K=40000, H=10, tile=128, lam=30.0),
     "mppi_adaptive_pair": _cfg(K=5000, H=25, tile=256, adaptive=True, lam=50.0, spt=2),
     "mppi_spline_p4": _cfg(K=3000, H=30, P=4, dt_us=10000, lam=30.0),
+    "elite_spline_p4_pair": _cfg(K=6000, H=30, P=4, dt_us=10000, tile=256, method="elite", elite_count=60,
+                                 adaptive=True, spt=2),
     "mppi_worldfeet_friction": _cfg(K=2048, H=25, world_feet=True, friction_project=True, lam=30.0),
     "elite_cmp_adaptive_it2": _cfg(K=8192, H=25, method="elite", elite_count=410, adaptive=True,
                                    compare_mppi=True, iterations=2),

@@ -1,6 +1,7 @@
 """Two samples per thread (packed FP32x2 arithmetic) against one: every result,
 cost, frequency, elite list and distribution is bit-identical, in plain solves
-over warm-started ticks and in batched ticks of both launch modes."""
+over warm-started ticks and in batched ticks of both launch modes, for the
+per-step and the spline policy."""
 import numpy as np
 import pytest
 
@@ -43,6 +44,14 @@ CASES = {
     "naive_k777_t64": dict(K=777, H=12, tile=64, method="naive"),
     "mppi_terminal_fext_t128": dict(K=2000, H=20, tile=128, gait="pace", f_ext=(5.0, -8.0, 0.0)),
     "mppi_h128_t256": dict(K=1500, H=128, dt_us=1000, tile=256),
+    # spline policy (every compiled knot count)
+    "spline_mppi_p4_adaptive_t256": dict(K=3000, H=30, P=4, dt_us=10000, tile=256, lam=30.0, adaptive=True),
+    "spline_elite_p3_t128": dict(K=4096, H=25, P=3, dt_us=10000, tile=128, method="elite", elite_count=100),
+    "spline_naive_p8_t64": dict(K=1000, H=20, P=8, dt_us=10000, tile=64, method="naive"),
+    "spline_mppi_p2_terminal_t128": dict(K=2000, H=40, P=2, dt_us=10000, tile=128, lam=20.0),
+    "spline_elite_p6_cmp_t256": dict(K=5000, H=50, P=6, dt_us=10000, tile=256, method="elite", elite_count=50,
+                                      adaptive=True, compare_mppi=True),
+    "spline_mppi_p4_h128_t128": dict(K=700, H=128, P=4, dt_us=5000, tile=128),
 }
 
 
@@ -51,13 +60,14 @@ def test_plain_solves_pair_equals_single(name):
     import torch
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(CASES[name], seed=321)
-    if name == "mppi_terminal_fext_t128":
+    if name in ("mppi_terminal_fext_t128", "spline_mppi_p2_terminal_t128"):
         cfg["cost"] = dict(cfg["cost"], w_terminal=2.0)
     prob = W.problem(cfg)
     x0, xr, fe = _dev(prob["x0"]), _dev(prob["xref"]), _dev(prob["f_ext"])
     a, b = S.Controller(cfg), S.Controller(cfg)
     a.set_samples_per_thread(1)
     b.set_samples_per_thread(2)
+    assert a.samples_per_thread() == 1 and b.samples_per_thread() == 2
     for tick in range(3):
         g = dict(prob["gait"])
         g["phase0"] = (g["phase0"] + tick * cfg["q_init"] * cfg["dt_us"]) % W.PHASE_ONE
@@ -98,6 +108,46 @@ def test_batched_pair_equals_single(mode):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(res[1].cpu().numpy(), res[2].cpu().numpy())
         for i in range(n):  # a batched controller's costs stay in the batch's arena: compare its distribution
+            for which in (S.BUF_MEAN, S.BUF_VAR):
+                np.testing.assert_array_equal(sets[1][i].read(which).cpu().numpy(),
+                                              sets[2][i].read(which).cpu().numpy())
+    for b in batches.values():
+        b.close()
+
+
+@pytest.mark.parametrize("mode", [S.BATCH_GRID, S.BATCH_PERSISTENT])
+def test_batched_spline_pair_equals_single(mode):
+    # spline controllers of uneven K, H and method in one batch (4 knots, 128-sample
+    # tiles): the elite / Naive controllers' launch and the MPPI controllers'
+    import torch
+    rng = np.random.default_rng(11)
+    mix = []
+    for i in range(10):
+        cfg = W.config("plain_mppi_k512_h12")
+        cfg.update(K=int(rng.choice([256, 1000, 3000])), H=int(rng.choice([10, 25, 50])), P=4, dt_us=10000,
+                   tile=128, method=["mppi", "elite", "naive"][i % 3], adaptive=bool(i % 2), seed=100 + i,
+                   ctrl=i, lam=25.0)
+        if cfg["method"] == "elite":
+            cfg["elite_count"] = max(1, cfg["K"] // 20)
+        mix.append((cfg, W.problem(cfg)))
+    sets = {1: [S.Controller(c) for c, _ in mix], 2: [S.Controller(c) for c, _ in mix]}
+    tens = [(_dev(p["x0"]), _dev(p["xref"]), _dev(p["f_ext"])) for _, p in mix]
+    n = len(mix)
+    res, batches = {}, {}
+    for spt in (1, 2):
+        b = S.Batch(n, sum(c.workspace_bytes() + 256 for c in sets[spt]))
+        b.set_mode(mode)
+        b.set_samples_per_thread(spt)
+        batches[spt] = b
+        res[spt] = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(3):
+        for spt in (1, 2):
+            probs = [sets[spt][i].problem(tens[i][0], tens[i][1], mix[i][1]["gait"], tens[i][2],
+                                          0 if tick == 0 else 1) for i in range(n)]
+            batches[spt].solve(sets[spt], probs, res[spt])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(res[1].cpu().numpy(), res[2].cpu().numpy())
+        for i in range(n):
             for which in (S.BUF_MEAN, S.BUF_VAR):
                 np.testing.assert_array_equal(sets[1][i].read(which).cpu().numpy(),
                                               sets[2][i].read(which).cpu().numpy())

@@ -34,6 +34,9 @@ CASES = {
                                      compare_mppi=True),
     "elite_k40000_lanes1024": dict(K=40000, H=6, method="elite", elite_count=2500),
     "elite_spline_p4": dict(K=5000, H=30, P=4, dt_us=10000, method="elite", elite_count=50, adaptive=True),
+    "elite_spline_p4_pair": dict(K=5000, H=30, P=4, dt_us=10000, tile=256, method="elite", elite_count=50,
+                                 adaptive=True, spt=2),
+    "mppi_spline_p3_pair": dict(K=3000, H=25, P=3, dt_us=10000, tile=128, lam=30.0, spt=2),
     "naive_freqset": dict(K=3000, H=12, method="naive", q_init=1300, freq_set_mhz=(1300, 2000, 2400)),
     "mppi_worldfeet_friction": dict(K=2048, H=25, world_feet=True, friction_project=True, lam=30.0),
 }

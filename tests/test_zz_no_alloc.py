@@ -11,6 +11,8 @@ free memory unchanged.
 
 This file is collected last, so a run that stops at the first failure has
 already run every other test."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -56,12 +58,15 @@ def test_static_entry_equals_solve_on_two_calls(variant):
     results = [torch.empty(S.RESULT_BYTES, dtype=torch.uint8, device="cuda") for _ in range(2)]
     S.solve_mppi_static(cfg, x0, xref, gait1, fe, 0, state0, states[0], 0, results[0])
     torch.cuda.synchronize()
-    # the second call, warmed up: nothing is allocated on the device
+    # the second call, warmed up: nothing is allocated on the device (garbage of
+    # earlier tests collected first: a collection during the call could only lower
+    # the allocator's count)
+    gc.collect()
     free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
     S.solve_mppi_static(cfg, x0, xref, gait2, fe, 1, states[0], states[1], 1, results[1])
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.memory_allocated() <= alloc0
 
     for got_state, got_res, want_state, want_res in zip(states, results, ref_state, ref_res):
         np.testing.assert_array_equal(got_state.cpu().numpy(), want_state.cpu().numpy())
