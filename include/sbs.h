@@ -386,6 +386,17 @@ int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_p
 int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
                          sbs_result* results, void* stream);
 
+/* Inputs written in place for sbs_batch_solve_host: fills probs[i] (host_memory
+ * = 1) with pointers into the batch's pinned staging buffer, laid out as that
+ * call gathers these controllers in this order: x0 [12], xref [H][12], f_ext [3]
+ * when with_fext, feet [4][2] for ground-fixed feet.  A caller that writes its
+ * inputs there and passes these problems (same controllers, same order) saves
+ * the gather copy; the solve still copies the buffer to the device each tick.
+ * The pointers stay valid until a call with more or larger controllers grows
+ * the buffer, or sbs_batch_destroy.  Waits for the batch's ticks in flight.
+ * SBS_ERR_OOM if the buffer cannot grow. */
+int sbs_batch_host_inputs(sbs_batch* b, int n, sbs_handle* const* handles, int with_fext, sbs_problem* probs);
+
 /* Launch mode of a batch.  SBS_BATCH_GRID (default): one block per item, the
  * hardware block scheduler dispatching items in order, heaviest controllers
  * first.  SBS_BATCH_PERSISTENT: as many blocks as fit on the GPU pull items from

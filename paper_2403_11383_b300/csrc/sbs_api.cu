@@ -1192,21 +1192,18 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
 // pinned buffer and copied to the device in one transfer on the caller's stream,
 // the tick runs on the device copies, and the n results come back in one
 // transfer; the call returns when they are in `results`.
-extern "C" int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
-                                    sbs_result* results, void* stream)
+// Bytes of the host staging of one controller's inputs (16-byte aligned pieces):
+// x0 | xref | f_ext (when given) | feet (ground-fixed feet).
+static size_t staged_bytes(const sbs_handle* h, bool fext)
 {
-    if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    size_t need = 0;
-    for (int i = 0; i < n; ++i) {
-        const sbs_handle* h = handles[i];
-        const sbs_problem& p = probs[i];
-        if (!h || !p.x0 || !p.xref || p.host_memory != 1) return SBS_ERR_INVALID_ARG;
-        if (h->hP.world_feet && !p.feet) return SBS_ERR_INVALID_ARG;
-        need += align_up(12 * 4, 16) + align_up((size_t)12 * h->hP.H * 4, 16) + (p.f_ext ? 16 : 0) +
-                (h->hP.world_feet ? 32 : 0);
-    }
-    // wait for any earlier tick of this batch before its staging is rewritten
+    return align_up(12 * 4, 16) + align_up((size_t)12 * h->hP.H * 4, 16) + (fext ? 16 : 0) +
+           (h->hP.world_feet ? 32 : 0);
+}
+
+// Waits for the batch's ticks in flight, then grows the pinned input staging (and
+// its device twin) to at least `need` bytes.
+static int host_staging(sbs_batch* b, size_t need)
+{
     for (int k = 0; k < b->nslots; ++k)
         if (b->slot[k].used && cudaEventSynchronize(b->slot[k].done) != cudaSuccess) return SBS_ERR_CUDA;
     if (need > b->in_cap) {
@@ -1225,6 +1222,53 @@ extern "C" int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* hand
         }
         b->in_cap = cap;
     }
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_host_inputs(sbs_batch* b, int n, sbs_handle* const* handles, int with_fext,
+                                     sbs_problem* probs)
+{
+    if (!b || n < 1 || n > b->max_inst || !handles || !probs) return SBS_ERR_INVALID_ARG;
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!handles[i]) return SBS_ERR_INVALID_ARG;
+        need += staged_bytes(handles[i], with_fext != 0);
+    }
+    int st = host_staging(b, need);
+    if (st) return st;
+    size_t off = 0;
+    auto take = [&](size_t count) {
+        float* p = (float*)(b->h_in + off);
+        off += align_up(count * 4, 16);
+        return p;
+    };
+    for (int i = 0; i < n; ++i) {
+        sbs_problem& q = probs[i];
+        q.host_memory = 1;
+        q.x0 = take(12);
+        q.xref = take((size_t)12 * handles[i]->hP.H);
+        q.f_ext = with_fext ? take(3) : nullptr;
+        q.feet = handles[i]->hP.world_feet ? take(8) : nullptr;
+    }
+    return SBS_OK;
+}
+
+extern "C" int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* handles, const sbs_problem* probs,
+                                    sbs_result* results, void* stream)
+{
+    if (!b || n < 1 || n > b->max_inst || !handles || !probs || !results) return SBS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        const sbs_handle* h = handles[i];
+        const sbs_problem& p = probs[i];
+        if (!h || !p.x0 || !p.xref || p.host_memory != 1) return SBS_ERR_INVALID_ARG;
+        if (h->hP.world_feet && !p.feet) return SBS_ERR_INVALID_ARG;
+        need += staged_bytes(h, p.f_ext != nullptr);
+    }
+    // wait for any earlier tick of this batch before its staging is rewritten
+    int st0 = host_staging(b, need);
+    if (st0) return st0;
     if (n > b->res_cap) {
         if (b->h_res) cudaFreeHost(b->h_res);
         dev_free(&b->alloc, b->has_alloc, b->d_res);
@@ -1245,7 +1289,8 @@ extern "C" int sbs_batch_solve_host(sbs_batch* b, int n, sbs_handle* const* hand
     b->dprobs.resize(n);
     size_t off = 0;
     auto stage = [&](const float* src, size_t count) -> const float* {
-        std::memcpy(b->h_in + off, src, count * 4);
+        float* dst = (float*)(b->h_in + off);
+        if (src != dst) std::memcpy(dst, src, count * 4);  // inputs the caller wrote in place stay
         const float* d = (const float*)(b->d_in + off);
         off += align_up(count * 4, 16);
         return d;

@@ -143,6 +143,7 @@ ABI = {
     "sbs_batch_destroy": (None, [C.c_void_p]),
     "sbs_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sbs_batch_solve_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sbs_batch_host_inputs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     "sbs_status_str": (C.c_char_p, [C.c_int]),
     "sbs_solve_mppi_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                         C.c_void_p]),
@@ -552,6 +553,30 @@ class Batch:
             results.ctypes.data if hasattr(results, "ctypes") else C.addressof(results))
         check(lib().sbs_batch_solve_host(self._b, packed.n, packed.handles, packed.problems, C.c_void_p(ptr),
                                          _stream_ptr(stream)), "sbs_batch_solve_host")
+
+    def host_inputs(self, controllers, gaits, shift=1, with_fext=True):
+        """sbs_batch_host_inputs: host problems whose inputs live in the batch's
+        pinned staging buffer, packed for solve_host, and one dict of numpy views
+        per controller (x0 [12], xref [H, 12], f_ext [3] or None, feet [4, 2] or
+        None) to write that controller's inputs into; a solve_host of this Packed
+        then copies no input on the host."""
+        n = len(controllers)
+        hs = (C.c_void_p * n)(*[c.handle.value for c in controllers])
+        ps = (Problem * n)()
+        check(lib().sbs_batch_host_inputs(self._b, n, hs, 1 if with_fext else 0, ps), "sbs_batch_host_inputs")
+
+        def view(ptr, shape):
+            if not ptr:
+                return None
+            count = int(np.prod(shape))
+            return np.ctypeslib.as_array((C.c_float * count).from_address(ptr)).reshape(shape)
+        views = []
+        for i, c in enumerate(controllers):
+            ps[i].gait = make_gait(gaits[i])
+            ps[i].shift = shift
+            views.append({"x0": view(ps[i].x0, (12,)), "xref": view(ps[i].xref, (c.H, 12)),
+                          "f_ext": view(ps[i].f_ext, (3,)), "feet": view(ps[i].feet, (4, 2))})
+        return Packed(controllers, list(ps)), views
 
 
 class Packed:

@@ -527,3 +527,38 @@ def test_batch_host_memory_equals_device():
         bh.solve_host(S.Packed(host_c, pd), res_h)
     bd.close()
     bh.close()
+
+
+def test_host_inputs_in_place_equal_gathered():
+    # inputs written into the batch's pinned staging (sbs_batch_host_inputs) give the
+    # bits of the same inputs gathered from the caller's arrays, over warm ticks
+    import torch
+    mix = W.batch_mix(8, seed=41)
+    for c, _ in mix:
+        c["tile"] = 128
+    ta = [S.Controller(c) for c, _ in mix]
+    tb = [S.Controller(c) for c, _ in mix]
+    n = len(mix)
+    ba = S.Batch(n, sum(c.workspace_bytes() + 256 for c in ta))
+    bb = S.Batch(n, sum(c.workspace_bytes() + 256 for c in tb))
+    gaits = [p["gait"] for _, p in mix]
+    h = [tuple(np.ascontiguousarray(np.float32(p[k])) for k in ("x0", "xref", "f_ext")) for _, p in mix]
+    pb = S.Packed(tb, [tb[i].problem(h[i][0], h[i][1], gaits[i], h[i][2], 1, host=True) for i in range(n)])
+    pa, views = ba.host_inputs(ta, gaits, shift=1)
+    ra = np.zeros(n * S.RESULT_BYTES, dtype=np.uint8)
+    rb = np.zeros_like(ra)
+    rng = np.random.default_rng(5)
+    for tick in range(3):
+        for i in range(n):
+            x0 = (h[i][0] + np.float32(0.01) * rng.standard_normal(12).astype(np.float32)).astype(np.float32)
+            h[i][0][:] = x0  # the gathered side reads the caller's arrays
+            views[i]["x0"][:] = x0
+            views[i]["xref"][:] = h[i][1]
+            views[i]["f_ext"][:] = h[i][2]
+        ba.solve_host(pa, ra)
+        bb.solve_host(pb, rb)
+        np.testing.assert_array_equal(ra, rb)
+        for i in range(n):
+            np.testing.assert_array_equal(ta[i].read(S.BUF_MEAN).cpu().numpy(), tb[i].read(S.BUF_MEAN).cpu().numpy())
+    ba.close()
+    bb.close()
