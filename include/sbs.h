@@ -418,7 +418,14 @@ int sbs_batch_set_samples_per_thread(sbs_batch* b, int spt);
 int sbs_batch_get_samples_per_thread(const sbs_batch* b);
 
 /* The same choice for a handle's plain solves (sbs_solve); 0 (the default) is
- * one sample per thread. */
+ * one sample per thread.  Plain solves also take SBS_SPT_NOISE_WARPS: one
+ * sample per thread and a second thread per sample that draws the sample's
+ * normals one step ahead (2T threads per tile: the Philox and Box-Muller work
+ * runs on other warps than the model step), for controllers too small to fill
+ * the GPU, whose rollout is bound by each sample's chain of dependent
+ * instructions; same bits.  Controllers it does not apply to (spline policy,
+ * extended model features) take one sample per thread. */
+#define SBS_SPT_NOISE_WARPS 3
 int sbs_set_samples_per_thread(sbs_handle* h, int spt);
 
 /* Sampled deviations (Alg. 1 Sampling): the update needs sigma * eps of the
@@ -440,11 +447,12 @@ int sbs_batch_get_theta_mode(const sbs_batch* b);
 
 /* Autotuner of a handle's plain solves: times `ticks` solves of prob (after one
  * warm-up solve per setting; real solves, they advance the controller) at one
- * and, where the controller can take them, two samples per thread, storing and
- * regenerating the sampled deviations, and keeps the fastest setting.
- * ms_out[2 (spt - 1) + mode] gets the mean solve time in ms of each setting
- * (-1 where not measured).  Synchronises the stream. */
-int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int ticks, float ms_out[4],
+ * sample per thread, two where the controller can take them and the noise warps
+ * (SBS_SPT_NOISE_WARPS) where they apply, each storing and regenerating the
+ * sampled deviations, and keeps the fastest setting.  ms_out[2 (spt - 1) + mode]
+ * gets the mean solve time in ms of each setting (-1 where not measured).
+ * Synchronises the stream. */
+int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int ticks, float ms_out[6],
                  void* stream);
 
 /* Autotuner: runs `ticks` profiled ticks in each launch mode, with one and (where

@@ -467,7 +467,7 @@ int sbs_solve(sbs_handle* h, const sbs_problem* prob, sbs_result* result, void* 
         t.regen = h->regen;
         t.result = res;
         t.ws = h->ws;
-        st = launch_rollout(h->dP, P, t, stream, h->spt == 2 ? 2 : 1);
+        st = launch_rollout(h->dP, P, t, stream, h->spt > 0 ? h->spt : 1);
         if (st) return st;
         if (P.method != SBS_MPPI) {
             st = launch_select(h->dP, P, t, stream);
@@ -550,7 +550,7 @@ int sbs_shard_rollout(sbs_handle* h, const sbs_problem* prob, int rank, int worl
     t.ws.nfin = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(xbuf, 0, sbs_shard_exchange_bytes(h), s) != cudaSuccess) return SBS_ERR_CUDA;
-    st = launch_rollout(h->dP, P, t, stream, h->spt == 2 ? 2 : 1, end - begin);
+    st = launch_rollout(h->dP, P, t, stream, h->spt > 0 ? h->spt : 1, end - begin);
     if (st) return st;
     h->shard_t = t;
     h->shard_pending = true;
@@ -1379,13 +1379,14 @@ extern "C" int sbs_batch_autotune(sbs_batch* b, int n, sbs_handle* const* handle
     return SBS_OK;
 }
 
-extern "C" int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int ticks, float ms_out[4],
+extern "C" int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* result, int ticks, float ms_out[6],
                             void* stream)
 {
     if (!h || !prob || !result || ticks < 1 || !ms_out) return SBS_ERR_INVALID_ARG;
     const InstParams& P = h->hP;
     const bool ext = P.n_freq > 0 || P.world_feet || P.friction_project;
-    const int nspt = pair_capable(P.P, ext, P.T) && pair_fits(P.H, P.P, P.T, P.nb) ? 2 : 1;
+    const bool pair = pair_capable(P.P, ext, P.T) && pair_fits(P.H, P.P, P.T, P.nb);
+    const bool ws = ws_capable(P.P, ext, P.H, P.T, P.nb);
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -1395,8 +1396,9 @@ extern "C" int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* 
     }
     int st = SBS_OK, best_spt = 1, best_regen = 0;
     float best = 1e30f;
-    for (int i = 0; i < 4; ++i) ms_out[i] = -1.0f;
-    for (int sp = 1; sp <= nspt && st == SBS_OK; ++sp) {
+    for (int i = 0; i < 6; ++i) ms_out[i] = -1.0f;
+    for (int sp = 1; sp <= 3 && st == SBS_OK; ++sp) {
+        if ((sp == 2 && !pair) || (sp == SBS_SPT_NOISE_WARPS && !ws)) continue;
         for (int rg = 0; rg < 2 && st == SBS_OK; ++rg) {
             h->spt = sp;
             h->regen = rg;
@@ -1429,7 +1431,7 @@ extern "C" int sbs_autotune(sbs_handle* h, const sbs_problem* prob, sbs_result* 
     return SBS_OK;
 }
 
-extern "C" int sbs_get_samples_per_thread(const sbs_handle* h) { return h ? (h->spt == 2 ? 2 : 1) : SBS_ERR_INVALID_ARG; }
+extern "C" int sbs_get_samples_per_thread(const sbs_handle* h) { return h ? (h->spt > 0 ? h->spt : 1) : SBS_ERR_INVALID_ARG; }
 
 extern "C" int sbs_get_theta_mode(const sbs_handle* h)
 {
@@ -1466,7 +1468,7 @@ extern "C" int sbs_batch_get_samples_per_thread(const sbs_batch* b) { return b ?
 
 extern "C" int sbs_set_samples_per_thread(sbs_handle* h, int spt)
 {
-    if (!h || spt < 0 || spt > 2) return SBS_ERR_INVALID_ARG;
+    if (!h || spt < 0 || spt > SBS_SPT_NOISE_WARPS) return SBS_ERR_INVALID_ARG;
     h->spt = spt;
     return SBS_OK;
 }

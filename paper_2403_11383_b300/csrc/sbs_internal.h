@@ -112,7 +112,7 @@ static_assert(sizeof(InstParams) % 16 == 0, "InstParams must be a multiple of 16
 static_assert(sizeof(TickArgs) % 8 == 0, "TickArgs must be a multiple of 8 bytes");
 
 // Dynamic shared memory of one rollout item (bytes); nb force blocks.
-inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1, bool pair = false)
+__host__ __device__ inline size_t rollout_smem_bytes(int H, int P, int T, int nb = 1, bool pair = false)
 {
     int nt = P > 0 ? P : H;
     int nf = 12 * nt;
@@ -226,6 +226,15 @@ inline int rollout_variant(int P, bool ext, bool pair = false, bool regen = fals
 // Launches that can carry two samples per thread: the ordinary model (per-step or
 // spline policy), with tiles of a multiple of 64 samples (whole warps of pairs).
 inline bool pair_capable(int P, bool ext, int T) { (void)P; return !ext && T % 64 == 0; }
+// Dynamic shared memory of a warp-specialised tile: the per-step layout and a
+// double buffer of the normals of T samples.
+inline size_t ws_smem_bytes(int H, int T, int nb) { return rollout_smem_bytes(H, 0, T, nb) + 96 * (size_t)T; }
+// Plain launches that can take the noise warps: the per-step policy on the
+// ordinary model, whole warps of samples, 2T threads within the block limit.
+inline bool ws_capable(int P, bool ext, int H, int T, int nb)
+{
+    return P == 0 && !ext && T % 32 == 0 && 2 * T <= 2 * SBS_MAX_TILE && ws_smem_bytes(H, T, nb) <= kMaxDynamicSmem;
+}
 // ... and whose duplicated rows fit the shared memory of a block.
 inline bool pair_fits(int H, int P, int T, int nb) { return rollout_smem_bytes(H, P, T, nb, true) <= kMaxDynamicSmem; }
 

@@ -1409,6 +1409,272 @@ __device__ void rollout_tile_pair_spline(BlockShared& sh, float* dyn, int tile)
     if (t.partials == 1) tile_combine(sh, v, tile);
 }
 
+// ---------------------------------------------------------------------------
+// One tile of T samples on 2T threads (warp-specialised; the per-step policy on
+// the ordinary model), for controllers too small to fill the GPU, whose rollout
+// is bound by each sample's chain of dependent instructions: thread s < T
+// integrates sample s, thread T + s draws that sample's 12 normals one step
+// ahead into a double buffer in shared memory, so the Philox and Box-Muller
+// work runs on other warps than the model step.  The two halves meet at one
+// named barrier per step, which every thread passes H + 1 times.  The consumer
+// does the operations of rollout_tile<0, false> in the same order, and in the
+// tile's reductions the producers count as samples past K (weight zero, cost
+// +inf), which adds only zero terms: the results are bit-identical to the
+// one-sample launch on the same tile.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ws_barrier(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// The double buffer of normals after the per-step layout: [2][12][T] floats.
+__device__ __forceinline__ float* ws_ring(float* dyn, const InstParams& P, int T)
+{
+    return dyn + rollout_smem_bytes(P.H, 0, T, P.nb) / sizeof(float);
+}
+
+__device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
+{
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int NT = blockDim.x, T = NT >> 1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+    const bool producer = tid >= T;
+    const int s = producer ? tid - T : tid;  // the sample's place in the tile
+    const Views v = carve(dyn, P.H, 0, P.nf, T, P.nb);
+    float* ring = ws_ring(dyn, P, T);
+    stage(sh, v, 0);
+
+    const int K = P.K;
+    const uint32_t k = (uint32_t)tile * (uint32_t)T + (uint32_t)s;
+    const bool valid = !producer && k < (uint32_t)K;  // a producer carries no sample of its own
+    const uint32_t seed = P.seed, ctrl = P.ctrl;
+    const uint64_t iter = t.iter;
+    float* theta = t.ws.theta;
+    uint32_t q = P.q_init;
+    if (P.adaptive) q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
+
+    float J = kInf, Jc = 0.0f;
+    float x[12];
+    if (producer) {
+        const PhiloxPre pp = philox_pre(k, iter, seed, ctrl);
+        float e[12];
+        normals12(pp, 0, e);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) ring[c * T + s] = e[c];
+        ws_barrier(NT);
+        for (int j = 0; j < P.H; ++j) {
+            if (j + 1 < P.H) {
+                normals12(pp, j + 1, e);
+                float* r = ring + ((j + 1) & 1) * 12 * T;
+#pragma unroll
+                for (int c = 0; c < 12; ++c) r[c * T + s] = e[c];
+            }
+            ws_barrier(NT);
+        }
+    } else {
+        const float* mu = v.mu;
+        const float* sd = v.sd;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) x[c] = sh.x0[c];
+        const float fe[3] = {sh.fe[0], sh.fe[1], sh.fe[2]};
+        uint32_t ph[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t p0 = t.phase0 + t.offset[i];
+            ph[i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
+        }
+        const uint32_t step = q * P.dt_us;
+        const bool uniform_q = !P.adaptive;
+        const uint32_t duty = t.duty;
+        J = 0.0f;
+        ws_barrier(NT);  // step 0's normals
+        for (int j = 0; j < P.H; ++j) {
+            const float* r = ring + (j & 1) * 12 * T;
+            float e[12], G[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) e[c] = r[c * T + s];
+            const float4* m4 = reinterpret_cast<const float4*>(mu + 12 * j);
+            const float4* s4 = reinterpret_cast<const float4*>(sd + 12 * j);
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq) {
+                const float4 ma = m4[qq], sa = s4[qq];
+                const float mv[4] = {ma.x, ma.y, ma.z, ma.w}, sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) G[4 * qq + i] = __fmaf_rn(sv[i], e[4 * qq + i], mv[i]);
+            }
+            if (!t.regen) {
+#pragma unroll
+                for (int qq = 0; qq < 3; ++qq) {
+                    const float4 sa = s4[qq];
+                    const float sv[4] = {sa.x, sa.y, sa.z, sa.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) e[4 * qq + i] = __fmul_rn(sv[i], e[4 * qq + i]);
+                }
+                if (valid) {
+                    float4* o = reinterpret_cast<float4*>(theta + ((size_t)j * K + k) * 12);
+                    o[0] = make_float4(e[0], e[1], e[2], e[3]);
+                    o[1] = make_float4(e[4], e[5], e[6], e[7]);
+                    o[2] = make_float4(e[8], e[9], e[10], e[11]);
+                }
+            }
+            unsigned st, live, all;
+            if (uniform_q) {
+                st = live = all = sh.sched[j];
+            } else {
+                st = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) st |= (ph[i] < duty ? 1u : 0u) << i;
+                live = __reduce_or_sync(kFull, st);
+                all = __reduce_and_sync(kFull, st);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ph[i] += step;
+                    if (ph[i] >= kPhaseOne) ph[i] -= kPhaseOne;
+                }
+            }
+            if (live != all) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (!(st & (1u << i))) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
+            }
+            kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live, true));
+            srbd_step(P, x, G, fe, live);
+            ws_barrier(NT);
+        }
+        if (P.w_terminal > 0.0f) kahan_add(J, Jc, terminal_cost(P, x, v.xr + 12 * (P.H - 1)));
+        if (P.adaptive) kahan_add(J, Jc, freq_regulariser(P, q));
+        if (!isfinite(J)) J = kInf;
+        if (valid) {
+            t.ws.J[k] = J;
+            t.ws.q[k] = (int32_t)q;
+        }
+    }
+    if (t.ws.hist) {
+        // histograms of the top 16 and top 8 key bits for a large elite selection
+        const uint32_t bin = cost_key(J) >> 16;
+        const unsigned act = __ballot_sync(kFull, valid);
+        if (valid) {
+            const unsigned peers = __match_any_sync(act, bin);
+            if (lane == __ffs(peers) - 1) atomicAdd(t.ws.hist + bin, (unsigned)__popc(peers));
+            const unsigned peers8 = __match_any_sync(act, bin >> 8);
+            if (lane == __ffs(peers8) - 1) atomicAdd(t.ws.hist + kHistBins + (bin >> 8), (unsigned)__popc(peers8));
+        }
+    }
+    if (t.ws.best) {
+        // Naive: the best finite (cost, index) of the one force block
+        const bool fin = valid && J < kInf;
+        unsigned long long m = fin ? ~(((unsigned long long)cost_key(J) << 32) | k) : 0ull;
+        if (__any_sync(kFull, fin)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long xo = __shfl_xor_sync(kFull, m, o);
+                m = xo > m ? xo : m;
+            }
+            if (lane == 0) atomicMax(t.ws.best, m);
+        }
+        const unsigned nfw = __popc(__ballot_sync(kFull, fin));
+        if (lane == 0 && nfw) atomicAdd(t.ws.nfin, nfw);
+    }
+    if (!t.partials) return;
+
+    // ---- MPPI partial sums of this tile, shifted by the tile's best cost (the
+    // producers' warps add zero rows to the warp sums, after the consumers')
+    const bool fin = valid && J < kInf;
+    const float mt = block_min(sh, fin ? J : kInf);
+    const float w = (fin && mt < kInf) ? expf(-(J - mt) * P.inv_lambda) : 0.0f;
+    const float f = (float)q / 1000.0f;
+    {
+        const float s0 = warp_sum(w), s1 = warp_sum(w * w), s2 = warp_sum(w * f), s3 = warp_sum(fin ? 1.0f : 0.0f);
+        if (lane == 0) {
+            sh.red[warp][0] = s0;
+            sh.red[warp][1] = s1;
+            sh.red[warp][2] = s2;
+            sh.red[warp][3] = s3;
+        }
+    }
+    const int PS = P.part_stride;
+    float* row = t.ws.part + (size_t)tile * PS;
+    {
+        // the samples of nonzero weight listed in sample order; the consumers then
+        // sum one float4 column of the row each over a slice of the list (as in
+        // rollout_tile, with the tile's T samples)
+        float2* lst = reinterpret_cast<float2*>(v.acc);
+        const unsigned nzb = __ballot_sync(kFull, w != 0.0f);
+        if (lane == 0) sh.wtot[warp] = __popc(nzb);
+        __syncthreads();
+        int pos = 0, nnz = 0;
+        for (int g = 0; g < nw; ++g) {
+            const int c = sh.wtot[g];
+            pos += g < warp ? c : 0;
+            nnz += c;
+        }
+        if (w != 0.0f) lst[pos + __popc(nzb & ((1u << lane) - 1u))] = make_float2(w, __int_as_float(s));
+        __syncthreads();
+        const int ncol = 3 * P.H;
+        const int nsl = ncol < T ? T / ncol : 1;
+        float4* slice_sum = reinterpret_cast<float4*>(v.acc + 2 * T);  // [nsl][ncol] when nsl > 1
+        const float4* th4 = reinterpret_cast<const float4*>(theta) + (size_t)tile * T * 3;
+        float4* row4 = reinterpret_cast<float4*>(row + kPartHeader);
+        if (!producer) {
+            for (int it = tid; it < nsl * ncol; it += T) {
+                const int sl = it / ncol, c = it - sl * ncol, j = c / 3;
+                const float4* src = th4 + (size_t)j * K * 3 + (c - 3 * j);
+                const float4 sd4 = reinterpret_cast<const float4*>(v.sd + 12 * j)[c - 3 * j];
+                float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ac = a;
+                if (t.regen) {  // the listed samples' deviations regenerated from their draws
+#pragma unroll 1
+                    for (int e = sl; e < nnz; e += nsl) {
+                        const float2 we = lst[e];
+                        const float4 d = regen_quad((uint32_t)(tile * T + __float_as_int(we.y)), j, c - 3 * j,
+                                                    t.iter, P.seed, P.ctrl, sd4);
+                        kahan_wsum4(a, ac, we.x, d);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int e = sl; e < nnz; e += nsl) {
+                        const float2 we = lst[e];
+                        const float4 d = src[3 * __float_as_int(we.y)];
+                        kahan_wsum4(a, ac, we.x, d);
+                    }
+                }
+                if (nsl == 1) row4[c] = a;
+                else slice_sum[it] = a;
+            }
+        }
+        if (nsl > 1) {
+            __syncthreads();
+            if (!producer) {
+                for (int c = tid; c < ncol; c += T) {
+                    float4 a = slice_sum[c];
+                    for (int sl = 1; sl < nsl; ++sl) {
+                        const float4 b = slice_sum[sl * ncol + c];
+                        a.x += b.x;
+                        a.y += b.y;
+                        a.z += b.z;
+                        a.w += b.w;
+                    }
+                    row4[c] = a;
+                }
+            }
+        }
+    }
+    if (tid == 0) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int ww = 0; ww < nw; ++ww) {
+            a0 += sh.red[ww][0];
+            a1 += sh.red[ww][1];
+            a2 += sh.red[ww][2];
+            a3 += sh.red[ww][3];
+        }
+        row[0] = mt;
+        row[1] = a0;
+        row[2] = a1;
+        row[3] = a2;
+        row[4] = a3;
+    }
+    if (t.partials == 1) tile_combine(sh, v, tile);
+}
+
 // Cost of an order-preserving key (inverse of cost_key).
 __device__ __forceinline__ float key_cost(uint32_t u)
 {
@@ -2120,6 +2386,17 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 3) k_rollout_pair_spline(con
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
     rollout_tile_pair_spline<NP>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
+}
+
+// Warp-specialised one-sample rollout: 2T threads per tile of T samples.
+__global__ void __launch_bounds__(2 * SBS_MAX_TILE) k_rollout_ws(const InstParams* __restrict__ dP, TickArgs t)
+{
+    extern __shared__ float4 dyn4[];
+    __shared__ BlockShared sh;
+    load_params(dP, sh);
+    if (threadIdx.x == 0) sh.t = t;
+    __syncthreads();
+    rollout_tile_ws(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -2878,6 +3155,17 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
 {
     if (tiles < 0) tiles = hP.ntiles;
     if (tiles == 0) return SBS_OK;
+    if (spt == SBS_SPT_NOISE_WARPS) {
+        const bool ext0 = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
+        if (ws_capable(hP.P, ext0, hP.H, hP.T, hP.nb)) {
+            const size_t smem = ws_smem_bytes(hP.H, hP.T, hP.nb);
+            int st = ensure_smem_attr((const void*)k_rollout_ws, smem);
+            if (st) return st;
+            k_rollout_ws<<<tiles, 2 * hP.T, smem, (cudaStream_t)stream>>>(dP, t);
+            return status_of(cudaGetLastError());
+        }
+        spt = 1;
+    }
     const bool ext = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
     const bool pair = spt == 2 && pair_capable(hP.P, ext, hP.T) && pair_fits(hP.H, hP.P, hP.T, hP.nb);
     const size_t smem = rollout_smem_bytes(hP.H, hP.P, hP.T, hP.nb, pair);

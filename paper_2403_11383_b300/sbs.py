@@ -45,6 +45,7 @@ ERR_INVALID_ARG, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_DIVERGED = -1, 
 MPPI, ELITE, NAIVE = 0, 1, 2
 BUF_MEAN, BUF_VAR, BUF_COST, BUF_FREQ, BUF_ELITE, BUF_MPPI_MEAN = 0, 1, 2, 3, 4, 5
 THETA_STORE, THETA_REGENERATE = 0, 1
+SPT_NOISE_WARPS = 3  # plain solves: one sample per thread plus a thread drawing its noise one step ahead
 MAX_H, MAX_K, MAX_TILE, MAX_FREQ = 128, 1 << 24, 256, 8
 BATCH_PERSISTENT, BATCH_GRID = 0, 1
 
@@ -349,11 +350,11 @@ class Controller:
     def autotune(self, problem: "Problem", result, ticks: int = 5, stream=None):
         """sbs_autotune: time the plain-solve settings on this problem (real
         solves), keep the fastest; returns {(spt, theta_mode): ms}."""
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 6)()
         ptr = result.data_ptr() if hasattr(result, "data_ptr") else C.addressof(result)
         check(lib().sbs_autotune(self._h, C.byref(problem), C.c_void_p(ptr), ticks, ms, _stream_ptr(stream)),
               "sbs_autotune")
-        return {(1 + i // 2, i % 2): ms[i] for i in range(4) if ms[i] >= 0}
+        return {(1 + i // 2, i % 2): ms[i] for i in range(6) if ms[i] >= 0}
 
     def prepare(self):
         """Allocate the plain-solve workspace now."""

@@ -155,6 +155,41 @@ def test_batched_spline_pair_equals_single(mode):
         b.close()
 
 
+NOISE_WARP_CASES = [n for n in CASES if "spline" not in n and "fext" not in n] + ["mppi_terminal_fext_t128"]
+
+
+@pytest.mark.parametrize("theta", [S.THETA_STORE, S.THETA_REGENERATE])
+@pytest.mark.parametrize("name", NOISE_WARP_CASES)
+def test_plain_solves_noise_warps_equal_single(name, theta):
+    # one sample per thread with a producer thread drawing its normals one step
+    # ahead (2T threads per tile) against the one-sample launch
+    import torch
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(CASES[name], seed=322)
+    if name == "mppi_terminal_fext_t128":
+        cfg["cost"] = dict(cfg["cost"], w_terminal=2.0)
+    prob = W.problem(cfg)
+    x0, xr, fe = _dev(prob["x0"]), _dev(prob["xref"]), _dev(prob["f_ext"])
+    a, b = S.Controller(cfg), S.Controller(cfg)
+    for c in (a, b):
+        c.set_theta_mode(theta)
+    a.set_samples_per_thread(1)
+    b.set_samples_per_thread(S.SPT_NOISE_WARPS)
+    assert b.samples_per_thread() == S.SPT_NOISE_WARPS
+    for tick in range(3):
+        g = dict(prob["gait"])
+        g["phase0"] = (g["phase0"] + tick * cfg["q_init"] * cfg["dt_us"]) % W.PHASE_ONE
+        ra = a.solve(x0, xr, g, fe, 0 if tick == 0 else 1).clone()
+        rb = b.solve(x0, xr, g, fe, 0 if tick == 0 else 1).clone()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
+        oa, ob = _outputs(a, cfg), _outputs(b, cfg)
+        for key in oa:
+            np.testing.assert_array_equal(oa[key], ob[key], err_msg=f"{name} tick {tick} {key}")
+    a.close()
+    b.close()
+
+
 def test_autotune_keeps_results():
     # the autotuner may pick either sample count: the next tick equals a
     # one-sample-per-thread batch's
@@ -200,10 +235,11 @@ def test_plain_autotune_keeps_results():
     rb = torch.empty_like(ra)
     pa = a.problem(x0, xr, prob["gait"], fe, 1)
     ms = a.autotune(pa, ra, ticks=3)
-    assert set(ms) == {(1, 0), (1, 1), (2, 0), (2, 1)} and all(v > 0 for v in ms.values())
+    assert set(ms) == {(sp, rg) for sp in (1, 2, S.SPT_NOISE_WARPS) for rg in (0, 1)}
+    assert all(v > 0 for v in ms.values())
     best = min(ms, key=ms.get)
     assert (a.samples_per_thread(), a.theta_mode()) == best
-    for _ in range(4 * 4):
+    for _ in range(len(ms) * 4):
         b.solve(x0, xr, prob["gait"], fe, 1, rb)
     a.solve(x0, xr, prob["gait"], fe, 1, ra)
     b.solve(x0, xr, prob["gait"], fe, 1, rb)
