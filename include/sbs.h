@@ -423,8 +423,7 @@ int sbs_batch_get_samples_per_thread(const sbs_batch* b);
  * normals one step ahead (2T threads per tile: the Philox and Box-Muller work
  * runs on other warps than the model step), for controllers too small to fill
  * the GPU, whose rollout is bound by each sample's chain of dependent
- * instructions; same bits.  Controllers it does not apply to (spline policy,
- * extended model features) take one sample per thread. */
+ * instructions; same bits.  Spline controllers take one sample per thread. */
 #define SBS_SPT_NOISE_WARPS 3
 int sbs_set_samples_per_thread(sbs_handle* h, int spt);
 

@@ -229,11 +229,12 @@ inline bool pair_capable(int P, bool ext, int T) { (void)P; return !ext && T % 6
 // Dynamic shared memory of a warp-specialised tile: the per-step layout and a
 // double buffer of the normals of T samples.
 inline size_t ws_smem_bytes(int H, int T, int nb) { return rollout_smem_bytes(H, 0, T, nb) + 96 * (size_t)T; }
-// Plain launches that can take the noise warps: the per-step policy on the
-// ordinary model, whole warps of samples, 2T threads within the block limit.
+// Plain launches that can take the noise warps: the per-step policy (ordinary or
+// extended model), whole warps of samples, 2T threads within the block limit.
 inline bool ws_capable(int P, bool ext, int H, int T, int nb)
 {
-    return P == 0 && !ext && T % 32 == 0 && 2 * T <= 2 * SBS_MAX_TILE && ws_smem_bytes(H, T, nb) <= kMaxDynamicSmem;
+    (void)ext;
+    return P == 0 && T % 32 == 0 && 2 * T <= 2 * SBS_MAX_TILE && ws_smem_bytes(H, T, nb) <= kMaxDynamicSmem;
 }
 // ... and whose duplicated rows fit the shared memory of a block.
 inline bool pair_fits(int H, int P, int T, int nb) { return rollout_smem_bytes(H, P, T, nb, true) <= kMaxDynamicSmem; }

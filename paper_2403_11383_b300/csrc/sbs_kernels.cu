@@ -1410,14 +1410,14 @@ __device__ void rollout_tile_pair_spline(BlockShared& sh, float* dyn, int tile)
 }
 
 // ---------------------------------------------------------------------------
-// One tile of T samples on 2T threads (warp-specialised; the per-step policy on
-// the ordinary model), for controllers too small to fill the GPU, whose rollout
+// One tile of T samples on 2T threads (warp-specialised; the per-step policy;
+// EXT as in rollout_tile), for controllers too small to fill the GPU, whose rollout
 // is bound by each sample's chain of dependent instructions: thread s < T
 // integrates sample s, thread T + s draws that sample's 12 normals one step
 // ahead into a double buffer in shared memory, so the Philox and Box-Muller
 // work runs on other warps than the model step.  The two halves meet at one
 // named barrier per step, which every thread passes H + 1 times.  The consumer
-// does the operations of rollout_tile<0, false> in the same order, and in the
+// does the operations of rollout_tile<0, EXT> in the same order, and in the
 // tile's reductions the producers count as samples past K (weight zero, cost
 // +inf), which adds only zero terms: the results are bit-identical to the
 // one-sample launch on the same tile.
@@ -1433,6 +1433,7 @@ __device__ __forceinline__ float* ws_ring(float* dyn, const InstParams& P, int T
     return dyn + rollout_smem_bytes(P.H, 0, T, P.nb) / sizeof(float);
 }
 
+template <bool EXT>
 __device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
 {
     const InstParams& P = sh.P;
@@ -1451,7 +1452,15 @@ __device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
     const uint64_t iter = t.iter;
     float* theta = t.ws.theta;
     uint32_t q = P.q_init;
-    if (P.adaptive) q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
+    int blk = 0;  // force block: the sample's entry of a discrete frequency set
+    if (P.adaptive) {
+        q = sample_freq(k, iter, seed, ctrl, sh.mu_f, sh.sig_f, P.f_min, P.f_max);
+    } else if constexpr (EXT) {
+        if (P.n_freq > 0) {
+            blk = freq_block(k, iter, seed, ctrl, P.n_freq);
+            q = P.freq[blk];
+        }
+    }
 
     float J = kInf, Jc = 0.0f;
     float x[12];
@@ -1472,8 +1481,8 @@ __device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
             ws_barrier(NT);
         }
     } else {
-        const float* mu = v.mu;
-        const float* sd = v.sd;
+        const float* mu = v.mu + blk * P.nf;  // this sample's Gaussian
+        const float* sd = v.sd + blk * P.nf;
 #pragma unroll
         for (int c = 0; c < 12; ++c) x[c] = sh.x0[c];
         const float fe[3] = {sh.fe[0], sh.fe[1], sh.fe[2]};
@@ -1484,8 +1493,20 @@ __device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
             ph[i] = p0 >= kPhaseOne ? p0 - kPhaseOne : p0;
         }
         const uint32_t step = q * P.dt_us;
-        const bool uniform_q = !P.adaptive;
+        const bool uniform_q = !P.adaptive && P.n_freq == 0;
         const uint32_t duty = t.duty;
+        // world-fixed feet: ground positions, last step's stance flags, T_st / 2
+        float fx[4], fy[4];
+        unsigned prev = 0xfu;  // legs in stance at t_0 keep the given feet
+        float tsh = 0.0f;
+        if constexpr (EXT) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                fx[i] = sh.feet[2 * i];
+                fy[i] = sh.feet[2 * i + 1];
+            }
+            tsh = (0.5e-6f * (float)duty) / (float)q;
+        }
         J = 0.0f;
         ws_barrier(NT);  // step 0's normals
         for (int j = 0; j < P.H; ++j) {
@@ -1537,12 +1558,31 @@ __device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
                 for (int i = 0; i < 4; ++i)
                     if (!(st & (1u << i))) G[3 * i] = G[3 * i + 1] = G[3 * i + 2] = 0.0f;
             }
-            kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live, true));
-            srbd_step(P, x, G, fe, live);
+            bool penalty = true;
+            if constexpr (EXT) {
+                if (P.friction_project) {  // the policy output constrained to the cone (Sec. IV-B)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        cone_project(P.mu, P.inv_1pmu2, G[3 * i], G[3 * i + 1], G[3 * i + 2]);
+                    penalty = false;
+                }
+            }
+            kahan_add(J, Jc, stage_cost(P, x, v.xr + 12 * j, G, live, penalty));
+            if constexpr (EXT) {
+                if (P.world_feet) {
+                    const unsigned touch = st & ~prev;  // legs landing at this step
+                    prev = st;
+                    srbd_step_world(P, x, G, fe, live, fx, fy, touch, v.xr[12 * j + 6], v.xr[12 * j + 7], tsh);
+                } else {
+                    srbd_step(P, x, G, fe, live);
+                }
+            } else {
+                srbd_step(P, x, G, fe, live);
+            }
             ws_barrier(NT);
         }
         if (P.w_terminal > 0.0f) kahan_add(J, Jc, terminal_cost(P, x, v.xr + 12 * (P.H - 1)));
-        if (P.adaptive) kahan_add(J, Jc, freq_regulariser(P, q));
+        if (P.adaptive || P.n_freq > 0) kahan_add(J, Jc, freq_regulariser(P, q));
         if (!isfinite(J)) J = kInf;
         if (valid) {
             t.ws.J[k] = J;
@@ -1561,16 +1601,21 @@ __device__ void rollout_tile_ws(BlockShared& sh, float* dyn, int tile)
         }
     }
     if (t.ws.best) {
-        // Naive: the best finite (cost, index) of the one force block
+        // Naive: each force block's best finite (cost, index), kept as the maximum of
+        // the complemented 64-bit key; one atomic per warp and block present
         const bool fin = valid && J < kInf;
-        unsigned long long m = fin ? ~(((unsigned long long)cost_key(J) << 32) | k) : 0ull;
-        if (__any_sync(kFull, fin)) {
+        const unsigned long long key = fin ? ~(((unsigned long long)cost_key(J) << 32) | k) : 0ull;
+        unsigned todo = __reduce_or_sync(kFull, fin ? 1u << blk : 0u);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            unsigned long long m = blk == b ? key : 0ull;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long xo = __shfl_xor_sync(kFull, m, o);
                 m = xo > m ? xo : m;
             }
-            if (lane == 0) atomicMax(t.ws.best, m);
+            if (lane == 0) atomicMax(t.ws.best + b, m);
         }
         const unsigned nfw = __popc(__ballot_sync(kFull, fin));
         if (lane == 0 && nfw) atomicAdd(t.ws.nfin, nfw);
@@ -2389,6 +2434,7 @@ __global__ void __launch_bounds__(SBS_MAX_TILE / 2, 3) k_rollout_pair_spline(con
 }
 
 // Warp-specialised one-sample rollout: 2T threads per tile of T samples.
+template <bool EXT>
 __global__ void __launch_bounds__(2 * SBS_MAX_TILE) k_rollout_ws(const InstParams* __restrict__ dP, TickArgs t)
 {
     extern __shared__ float4 dyn4[];
@@ -2396,7 +2442,7 @@ __global__ void __launch_bounds__(2 * SBS_MAX_TILE) k_rollout_ws(const InstParam
     load_params(dP, sh);
     if (threadIdx.x == 0) sh.t = t;
     __syncthreads();
-    rollout_tile_ws(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
+    rollout_tile_ws<EXT>(sh, reinterpret_cast<float*>(dyn4), blockIdx.x + t.tile_base);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(const InstParams* __restrict__ dP, TickArgs t)
@@ -3159,9 +3205,11 @@ int launch_rollout(const InstParams* dP, const InstParams& hP, const TickArgs& t
         const bool ext0 = hP.n_freq > 0 || hP.world_feet || hP.friction_project;
         if (ws_capable(hP.P, ext0, hP.H, hP.T, hP.nb)) {
             const size_t smem = ws_smem_bytes(hP.H, hP.T, hP.nb);
-            int st = ensure_smem_attr((const void*)k_rollout_ws, smem);
+            const void* fn = ext0 ? (const void*)k_rollout_ws<true> : (const void*)k_rollout_ws<false>;
+            int st = ensure_smem_attr(fn, smem);
             if (st) return st;
-            k_rollout_ws<<<tiles, 2 * hP.T, smem, (cudaStream_t)stream>>>(dP, t);
+            if (ext0) k_rollout_ws<true><<<tiles, 2 * hP.T, smem, (cudaStream_t)stream>>>(dP, t);
+            else k_rollout_ws<false><<<tiles, 2 * hP.T, smem, (cudaStream_t)stream>>>(dP, t);
             return status_of(cudaGetLastError());
         }
         spt = 1;

@@ -155,7 +155,17 @@ def test_batched_spline_pair_equals_single(mode):
         b.close()
 
 
-NOISE_WARP_CASES = [n for n in CASES if "spline" not in n and "fext" not in n] + ["mppi_terminal_fext_t128"]
+NOISE_WARP_CASES = [n for n in CASES if "spline" not in n]
+# the extended model features (the frequency set, ground-fixed feet, friction projection)
+EXT_CASES = {
+    "naive_freqset_k10000": dict(K=10000, H=12, method="naive", q_init=1300, freq_set_mhz=(1300, 2000, 2400)),
+    "mppi_worldfeet_k2048": dict(K=2048, H=25, world_feet=True, lam=30.0),
+    "mppi_friction_adaptive_k3001": dict(K=3001, H=20, friction_project=True, adaptive=True, lam=30.0, tile=64),
+    "naive_freqset_k5000_t256": dict(K=5000, H=25, method="naive", q_init=2000, freq_set_mhz=(1500, 2000, 2500),
+                                     tile=256),
+}
+CASES.update({f"ext_{k}": v for k, v in EXT_CASES.items()})
+NOISE_WARP_CASES += [f"ext_{k}" for k in EXT_CASES]
 
 
 @pytest.mark.parametrize("theta", [S.THETA_STORE, S.THETA_REGENERATE])
@@ -170,6 +180,7 @@ def test_plain_solves_noise_warps_equal_single(name, theta):
         cfg["cost"] = dict(cfg["cost"], w_terminal=2.0)
     prob = W.problem(cfg)
     x0, xr, fe = _dev(prob["x0"]), _dev(prob["xref"]), _dev(prob["f_ext"])
+    feet = _dev(prob["feet"]) if "feet" in prob else None
     a, b = S.Controller(cfg), S.Controller(cfg)
     for c in (a, b):
         c.set_theta_mode(theta)
@@ -179,8 +190,8 @@ def test_plain_solves_noise_warps_equal_single(name, theta):
     for tick in range(3):
         g = dict(prob["gait"])
         g["phase0"] = (g["phase0"] + tick * cfg["q_init"] * cfg["dt_us"]) % W.PHASE_ONE
-        ra = a.solve(x0, xr, g, fe, 0 if tick == 0 else 1).clone()
-        rb = b.solve(x0, xr, g, fe, 0 if tick == 0 else 1).clone()
+        ra = a.solve(x0, xr, g, fe, 0 if tick == 0 else 1, feet=feet).clone()
+        rb = b.solve(x0, xr, g, fe, 0 if tick == 0 else 1, feet=feet).clone()
         torch.cuda.synchronize()
         np.testing.assert_array_equal(ra.cpu().numpy(), rb.cpu().numpy())
         oa, ob = _outputs(a, cfg), _outputs(b, cfg)
