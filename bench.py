@@ -96,8 +96,9 @@ def parse():
                     help="samples per block of the batched controllers; 0: timed at 128 and 256, fastest kept")
     ap.add_argument("--launch", default="auto", choices=["auto", "grid", "persistent"],
                     help="batched launch mode; auto: measured by the autotuner (with --spt and --theta)")
-    ap.add_argument("--spt", type=int, default=0, choices=[0, 1, 2],
-                    help="samples per thread of the batched rollout; 0: autotuned")
+    ap.add_argument("--spt", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="samples per thread of the rollout (3: one sample and a noise thread per sample, "
+                         "single-controller workloads only); 0: autotuned")
     ap.add_argument("--theta", default="auto", choices=["auto", "store", "regenerate"],
                     help="sampled deviations stored or regenerated; auto: autotuned")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and the parity record")
@@ -452,7 +453,14 @@ def run_single(args, world, rank, local):
     for w in range(max(args.warmup, 3)):
         ctl.solve(x0, xref, prob["gait"], fe, 0 if w == 0 else 1, res, feet=feet)
     p1 = ctl.problem(x0, xref, prob["gait"], fe, 1, feet=feet)  # built once, as a control loop would
-    tune = ctl.autotune(p1, res, ticks=5)  # samples per thread x stored or regenerated deviations
+    if args.spt or args.theta != "auto":  # fixed for a profiling capture, which would distort the tuner's timings
+        tune = {}
+        if args.spt:
+            ctl.set_samples_per_thread(args.spt)
+        if args.theta != "auto":
+            ctl.set_theta_mode(S.THETA_REGENERATE if args.theta == "regenerate" else S.THETA_STORE)
+    else:
+        tune = ctl.autotune(p1, res, ticks=5)  # samples per thread x stored or regenerated deviations
     flush = L2Flush(dev)
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -497,7 +505,9 @@ def run_single(args, world, rank, local):
                            "samples_per_thread": ctl.samples_per_thread(),
                            "sampled_deviations": "regenerate" if ctl.theta_mode() == S.THETA_REGENERATE else "store",
                            "autotune_ms_per_solve": {f"spt{k[0]}_{'regen' if k[1] else 'store'}": v
-                                                     for k, v in tune.items()},
+                                                     for k, v in tune.items()} or None,
+                           "fixed_by_flags": {k: v for k, v in (("spt", args.spt), ("theta", args.theta))
+                                              if v not in (0, "auto")} or None,
                            "l2": flush.describe(), "parallelism": f"replicas x{world}"},
                 "solves_per_s": world / (ms * 1e-3),
                 "roofline": {"kernel": "whole solve", "bound": "alu", "achieved": achieved, "peak": peak,

@@ -52,6 +52,15 @@ def test_single_workload_line(name):
     assert d["e2e"]["h2d_bytes_per_step"] == 4 * (12 + 3 + 12 * cfg["H"] + feet)
 
 
+def test_single_workload_fixed_setting():
+    # a profiling capture fixes the launch setting instead of timing the others
+    d = _run("--workload", "plain_mppi_k512_h12", "--spt", "3", "--theta", "regenerate")
+    _common(d)
+    c = d["config"]
+    assert c["samples_per_thread"] == 3 and c["sampled_deviations"] == "regenerate"
+    assert c["fixed_by_flags"] == {"spt": 3, "theta": "regenerate"} and c["autotune_ms_per_solve"] is None
+
+
 def test_small_batched_line():
     d = _run("--instances", "8", "--tile", "256", "--no-serving")
     _common(d)
