@@ -44,6 +44,11 @@ CASES = {
     "naive_k777_t64": dict(K=777, H=12, tile=64, method="naive"),
     "mppi_terminal_fext_t128": dict(K=2000, H=20, tile=128, gait="pace", f_ext=(5.0, -8.0, 0.0)),
     "mppi_h128_t256": dict(K=1500, H=128, dt_us=1000, tile=256),
+    # the shortest horizons and a single sample
+    "mppi_h1_k200_t64": dict(K=200, H=1, tile=64),
+    "elite_h1_adaptive_k1000": dict(K=1000, H=1, method="elite", elite_count=50, adaptive=True),
+    "naive_k1_h2": dict(K=1, H=2, method="naive"),
+    "spline_mppi_p4_h2_t64": dict(K=500, H=2, P=4, dt_us=10000, tile=64),
     # spline policy (every compiled knot count)
     "spline_mppi_p4_adaptive_t256": dict(K=3000, H=30, P=4, dt_us=10000, tile=256, lam=30.0, adaptive=True),
     "spline_elite_p3_t128": dict(K=4096, H=25, P=3, dt_us=10000, tile=128, method="elite", elite_count=100),

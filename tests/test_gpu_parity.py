@@ -112,11 +112,26 @@ def test_plain_mppi_single_solve(cuda):
 
 
 @pytest.mark.parametrize("K,H,gait,tile", [(1000, 7, "trot", 128), (77, 3, "pace", 64), (1, 5, "crawl", 128),
-                                           (3001, 20, "crawl", 256)])
+                                           (3001, 20, "crawl", 256), (150, 1, "trot", 64), (33, 2, "pace", 64)])
 def test_mppi_ragged_and_small(cuda, K, H, gait, tile):
     cfg = W.config("plain_mppi_k512_h12")
     cfg.update(K=K, H=H, gait=gait, tile=tile, seed=K)
     mppi_parity(cfg, W.problem(cfg), f"K{K}")
+
+
+@pytest.mark.parametrize("name,upd", [
+    ("elite_h1_adaptive", dict(K=1000, H=1, method="elite", elite_count=50, adaptive=True)),
+    ("elite_spline_p3_h2", dict(K=700, H=2, P=3, dt_us=10000, tile=64, method="elite", elite_count=35)),
+    ("spline_p4_h2", dict(K=500, H=2, P=4, dt_us=10000, tile=64)),
+])
+def test_shortest_horizons(cuda, name, upd):
+    # one step (the warm shift then re-initialises the whole mean) and the shortest
+    # spline horizon (four knots on two steps)
+    cfg = W.config("plain_mppi_k512_h12")
+    cfg.update(upd, seed=11)
+    prob = W.problem(cfg)
+    rep = (mppi_parity if cfg["method"] == "mppi" else elite_parity)(cfg, prob, name)
+    assert rep["gated"] >= 0.95 * cfg["K"], rep  # 98.6 % for the one-step adaptive elite solve
 
 
 @pytest.mark.parametrize("method", ["mppi", "elite"])
