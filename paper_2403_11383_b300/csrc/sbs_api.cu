@@ -928,7 +928,7 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
     void* args_b[] = {(void*)&recs, (void*)&counts_b, (void*)&heads};
     const void* fns[4] = {batch_rollout_fn(P, mode), batch_select_fn(mode),
                           batch_refit_fn(mode, (P & kRegenVariant) != 0), batch_rollout_fn(P, mode)};
-    const int threads[4] = {T, kSelectThreads, kBatchRefitThreads, T};
+    const int threads[4] = {T, mode == SBS_BATCH_GRID ? kBatchSelectThreads : kSelectThreads, kBatchRefitThreads, T};
     const size_t shm[4] = {smem, sel_smem, 0, smem};
     int least = 0, greatest = 0;
     if (split && cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) ok = false;
@@ -953,7 +953,10 @@ static int build_graph(sbs_batch* b, sbs_batch_slot& sl, int P, int mode, size_t
         if (k < 3) prev = sl.kernel_node[k];
     }
     cudaGraphExec_t ex = nullptr;
-    ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    // the update chain's priority holds only when the graph runs its nodes' own
+    // priorities; otherwise every node takes the launching stream's, and the
+    // selection queues behind all of the second rollout launch's blocks
+    ok = ok && cudaGraphInstantiateWithFlags(&ex, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         cudaGraphDestroy(g);

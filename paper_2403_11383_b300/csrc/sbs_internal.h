@@ -20,6 +20,10 @@ constexpr int kRefitLanesMax = 1024;     // virtual lanes of a refit with a larg
 __host__ __device__ inline int refit_lanes(int Ke) { return Ke > 2048 ? kRefitLanesMax : kRefitThreads; }
 constexpr int kBatchRefitThreads = 128;  // batched ticks: thousands of small refit items (8 blocks per SM)
 constexpr int kSelectThreads = 1024;
+// Selection blocks of a graph-replayed batched tick: the registers of two rollout
+// blocks, so a selection starts as soon as two rollout blocks of an SM finish and
+// runs beside the rest of the rollout (a 1024-thread block waits for a whole SM).
+constexpr int kBatchSelectThreads = 512;
 constexpr int kSelectSmemMaxK = 32768;       // costs staged in shared memory up to this K
 constexpr size_t kMaxDynamicSmem = 220 * 1024;  // dynamic shared memory one block may use (below the 227 KB
                                                  // opt-in limit, which also covers the static part)

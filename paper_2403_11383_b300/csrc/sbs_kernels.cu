@@ -3315,7 +3315,8 @@ int launch_batch(int P, int mode, const InstRec* dRecs, const int* dCounts, int*
     const void* fns[3] = {batch_rollout_fn(P, mode), batch_select_fn(mode),
                           batch_refit_fn(mode, (P & kRegenVariant) != 0)};
     if (!fns[0]) return SBS_ERR_INVALID_ARG;
-    const dim3 blocks[3] = {dim3(T), dim3(kSelectThreads), dim3(kBatchRefitThreads)};
+    const dim3 blocks[3] = {dim3(T), dim3(mode == SBS_BATCH_GRID ? kBatchSelectThreads : kSelectThreads),
+                            dim3(kBatchRefitThreads)};
     const size_t shm[3] = {smem, sel_smem, 0};
     const InstRec* r = dRecs;
     const int* c = dCounts;
