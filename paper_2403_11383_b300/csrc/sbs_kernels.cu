@@ -2240,14 +2240,19 @@ __device__ void refit_block(BlockShared& sh, int b)
             sh.dbar[tid - 32] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + (tid - 32));
         }
         __syncthreads();
-        if (REGEN && !diverged) {  // deviations not stored: regenerated from their draws
+        // deviations not stored: regenerated from their draws.  Each thread's first
+        // elite row (virtual lane tid of the first pass) is drawn before the shift is
+        // known; thread 0's row is the first elite's, the shift itself.
+        float d0[12];
+        if (REGEN && !diverged) {
             if (tid < 12) sh.sd12[tid] = sqrtf(sh.vr12[tid]);
             __syncthreads();
-            if (tid == 0) {
-                float d[12];
-                regen_row((uint32_t)__ldcg(elite), b, t.iter, P.seed, P.ctrl, sh.sd12, d);
+            if (tid < Ke) {
+                regen_row((uint32_t)__ldcg(elite + tid), b, t.iter, P.seed, P.ctrl, sh.sd12, d0);
+                if (tid == 0) {
 #pragma unroll
-                for (int c = 0; c < 12; ++c) sh.dbar[c] = d[c];
+                    for (int c = 0; c < 12; ++c) sh.dbar[c] = d0[c];
+                }
             }
             __syncthreads();
         }
@@ -2272,7 +2277,12 @@ __device__ void refit_block(BlockShared& sh, int b)
                 if (REGEN) {  // deviations regenerated from their draws
                     for (int e = vl; e < Ke; e += V) {
                         float d[12];
-                        regen_row((uint32_t)kb, b, t.iter, P.seed, P.ctrl, sh.sd12, d);
+                        if (e == tid) {  // drawn above
+#pragma unroll
+                            for (int c = 0; c < 12; ++c) d[c] = d0[c];
+                        } else {
+                            regen_row((uint32_t)kb, b, t.iter, P.seed, P.ctrl, sh.sd12, d);
+                        }
                         kb = e + V < Ke ? __ldcg(elite + e + V) : 0;
 #pragma unroll
                         for (int c = 0; c < 12; ++c) {
