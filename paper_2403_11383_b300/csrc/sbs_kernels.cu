@@ -2231,24 +2231,26 @@ __device__ void refit_block(BlockShared& sh, int b)
         return;
     }
     if (b < P.nt) {
+        // the thread's first elite index (virtual lane tid of the first pass), loaded
+        // alongside the distribution entries
+        const int kfirst = tid < Ke ? __ldcg(elite + tid) : 0;
         if (tid < 12) {
             float m, var;
             shifted_entry(P, t, sm, sv, 12 * b + tid, m, var);
             sh.mu12[tid] = m;
             sh.vr12[tid] = var;
+            if (REGEN) sh.sd12[tid] = sqrtf(var);
         } else if (tid >= 32 && tid < 44 && !diverged && !REGEN) {  // the first elite's deviation, alongside
             sh.dbar[tid - 32] = __ldcg(t.ws.theta + ((size_t)b * K + __ldcg(elite)) * 12 + (tid - 32));
         }
         __syncthreads();
         // deviations not stored: regenerated from their draws.  Each thread's first
-        // elite row (virtual lane tid of the first pass) is drawn before the shift is
-        // known; thread 0's row is the first elite's, the shift itself.
+        // elite row is drawn before the shift is known; thread 0's row is the first
+        // elite's, the shift itself.
         float d0[12];
         if (REGEN && !diverged) {
-            if (tid < 12) sh.sd12[tid] = sqrtf(sh.vr12[tid]);
-            __syncthreads();
             if (tid < Ke) {
-                regen_row((uint32_t)__ldcg(elite + tid), b, t.iter, P.seed, P.ctrl, sh.sd12, d0);
+                regen_row((uint32_t)kfirst, b, t.iter, P.seed, P.ctrl, sh.sd12, d0);
                 if (tid == 0) {
 #pragma unroll
                     for (int c = 0; c < 12; ++c) sh.dbar[c] = d0[c];
