@@ -1116,7 +1116,7 @@ extern "C" int sbs_batch_solve(sbs_batch* b, int n, sbs_handle* const* handles, 
         tile_begin += P.ntiles;
         if (P.method != SBS_MPPI) {
             select_begin += 1;
-            refit_begin += P.nt + P.adaptive;
+            refit_begin += refit_items(P.method, P.Ke, P.nt, P.adaptive);
             tiles_upd = tile_begin;  // these records come first
         }
     }

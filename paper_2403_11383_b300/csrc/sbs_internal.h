@@ -18,6 +18,23 @@ constexpr int kRefitLanesMax = 1024;     // virtual lanes of a refit with a larg
 // Virtual lanes of a refit (the order of its sums, the same for every block
 // size): more lanes for a large elite set shorten each lane's chain of loads.
 __host__ __device__ inline int refit_lanes(int Ke) { return Ke > 2048 ? kRefitLanesMax : kRefitThreads; }
+// Refit items of a batched controller.  An elite set of at most 2048 (one pass of
+// kRefitThreads virtual lanes per step) takes several consecutive steps per item,
+// about 4096 elite rows each, so one block's set-up serves them all; a larger set
+// and Naive take one step per item.  An adaptive controller's frequency entry is
+// one more item.  Each step's sums are formed in the same order either way.
+constexpr int kRefitChunk = 8;  // steps whose sums a multi-step refit block holds at once
+__host__ __device__ inline int refit_steps_per_item(int method, int Ke, int nt)
+{
+    if (method != SBS_ELITE || Ke > 2048) return 1;
+    const int s = 4096 / (Ke > 0 ? Ke : 1);
+    return s < 1 ? 1 : (s > nt ? nt : s);
+}
+__host__ __device__ inline int refit_items(int method, int Ke, int nt, int adaptive)
+{
+    const int s = refit_steps_per_item(method, Ke, nt);
+    return (nt + s - 1) / s + (adaptive ? 1 : 0);
+}
 constexpr int kBatchRefitThreads = 128;  // batched ticks: thousands of small refit items (8 blocks per SM)
 constexpr int kSelectThreads = 1024;
 // Selection blocks of a graph-replayed batched tick: the registers of two rollout

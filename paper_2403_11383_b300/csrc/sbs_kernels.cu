@@ -2390,6 +2390,141 @@ __device__ void refit_block(BlockShared& sh, int b)
     }
 }
 
+// Refit of steps b0 .. b1 - 1 of an elite controller whose set fits one pass of
+// kRefitThreads virtual lanes per step (Ke <= 2048): the steps' sums are those of
+// refit_block (the same virtual lanes, each step's sums about its first elite's
+// row), formed kRefitChunk steps at a time with one block barrier per chunk
+// instead of several per step, so one block's set-up serves many steps.  Warps
+// of virtual lanes past Ke hold exact zeros and skip their reductions.
+template <bool REGEN>
+__device__ void refit_steps(BlockShared& sh, int b0, int b1)
+{
+    constexpr int S = kRefitChunk, V = kRefitThreads, NW = V / 32;
+    __shared__ float cw[S][NW][12], cw2[S][NW][12];  // per-step totals of the virtual warps
+    __shared__ float cmu[S * 12], cvr[S * 12], csd[S * 12], cdb[S * 12];
+    const InstParams& P = sh.P;
+    const TickArgs& t = sh.t;
+    const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
+    const float* sm = P.state[t.src];
+    const float* sv = sm + P.D;
+    float* dm = P.state[1 - t.src];
+    float* dv = dm + P.D;
+    const int K = P.K, Ke = P.Ke;
+    const int32_t* elite = t.ws.elite;
+    sbs_result* r = t.result;
+    const bool diverged = __ldcg(&r->status) != SBS_OK;
+    const int e0 = __ldcg(elite);  // the first elite: each step's shift
+    for (int c0 = b0; c0 < b1; c0 += S) {
+        const int ns = min(S, b1 - c0);
+        for (int x = tid; x < 12 * ns; x += T) {
+            float m, var;
+            shifted_entry(P, t, sm, sv, 12 * c0 + x, m, var);
+            cmu[x] = m;
+            cvr[x] = var;
+            if (REGEN) csd[x] = sqrtf(var);
+            else if (!diverged) cdb[x] = __ldcg(t.ws.theta + ((size_t)(c0 + x / 12) * K + e0) * 12 + x % 12);
+        }
+        __syncthreads();
+        if (REGEN && !diverged) {
+            for (int jj = tid; jj < ns; jj += T) {
+                float d[12];
+                regen_row((uint32_t)e0, c0 + jj, t.iter, P.seed, P.ctrl, csd + 12 * jj, d);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) cdb[12 * jj + c] = d[c];
+            }
+            __syncthreads();
+        }
+        if (!diverged) {
+            for (int v0 = 0; v0 < V; v0 += T) {
+                const int vl = v0 + tid, vw = vl >> 5;
+                if (v0 + (tid & ~31) >= Ke) {  // no elite on this virtual warp: zero totals
+                    if (lane < 12)
+                        for (int jj = 0; jj < ns; ++jj) cw[jj][vw][lane] = cw2[jj][vw][lane] = 0.0f;
+                    continue;
+                }
+                for (int jj = 0; jj < ns; ++jj) {
+                    const int j = c0 + jj;
+                    const float* db = cdb + 12 * jj;
+                    float s[12], s2[12];
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) s[c] = s2[c] = 0.0f;
+                    for (int e = vl; e < Ke; e += V) {
+                        const int kb = __ldcg(elite + e);
+                        float d[12];
+                        if (REGEN) {
+                            regen_row((uint32_t)kb, j, t.iter, P.seed, P.ctrl, csd + 12 * jj, d);
+                        } else {
+                            const float4* src = reinterpret_cast<const float4*>(t.ws.theta + ((size_t)j * K + kb) * 12);
+                            const float4 a = __ldcg(src), bb = __ldcg(src + 1), cc = __ldcg(src + 2);
+                            d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+                            d[4] = bb.x; d[5] = bb.y; d[6] = bb.z; d[7] = bb.w;
+                            d[8] = cc.x; d[9] = cc.y; d[10] = cc.z; d[11] = cc.w;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 12; ++c) {
+                            const float q = d[c] - db[c];
+                            s[c] += q;
+                            s2[c] = fmaf(q, q, s2[c]);
+                        }
+                    }
+                    float o[3];
+                    int cc0 = warp_sum12(s, o);
+                    if ((lane & 7) == 0)
+                        for (int i = 0; i < 3; ++i) cw[jj][vw][cc0 + i] = o[i];
+                    cc0 = warp_sum12(s2, o);
+                    if ((lane & 7) == 0)
+                        for (int i = 0; i < 3; ++i) cw2[jj][vw][cc0 + i] = o[i];
+                }
+            }
+            __syncthreads();
+        }
+        for (int x = tid; x < 12 * ns; x += T) {
+            const int jj = x / 12, c = x - 12 * jj, j = c0 + jj;
+            float mean_c, var_c;
+            if (diverged) {
+                mean_c = cmu[x];
+                var_c = cvr[x];
+            } else {
+                float tot = 0.0f, tot2 = 0.0f;
+                for (int w = 0; w < NW; ++w) {
+                    tot += cw[jj][w][c];
+                    tot2 += cw2[jj][w][c];
+                }
+                const float m = tot / (float)Ke;
+                var_c = fmaxf(fmaf(-m, m, tot2 / (float)Ke), P.var_min);
+                mean_c = cmu[x] + (cdb[x] + m);
+            }
+            dm[12 * j + c] = mean_c;
+            dv[12 * j + c] = var_c;
+            if (j == 0) {
+                const uint32_t ph = (t.phase0 + t.offset[c / 3]) % kPhaseOne;
+                r->u0[c] = ph < t.duty ? mean_c : 0.0f;
+            }
+        }
+        if (c0 == 0 && tid == 0 && !P.adaptive) {
+            r->f_mean = P.q_init * 0.001f;
+            r->q_freq = (int32_t)P.q_init;
+        }
+        __syncthreads();
+    }
+}
+
+// Refit item q of a batched controller (refit_items of them).
+template <bool REGEN>
+__device__ void refit_item(BlockShared& sh, int q)
+{
+    const InstParams& P = sh.P;
+    const int spi = refit_steps_per_item(P.method, P.Ke, P.nt);
+    const int nq = (P.nt + spi - 1) / spi;
+    if (q >= nq) {
+        refit_block<REGEN>(sh, P.nt);  // the frequency entry
+    } else if (spi == 1) {
+        refit_block<REGEN>(sh, q);
+    } else {
+        refit_steps<REGEN>(sh, q * spi, min(q * spi + spi, P.nt));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -2785,7 +2920,7 @@ __global__ void __launch_bounds__(kBatchRefitThreads) k_grid_refit(const InstRec
     load_params(recs[i].dP, sh);
     load_tick(&recs[i].t, sh);
     __syncthreads();
-    refit_block<REGEN>(sh, it - recs[i].refit_begin);
+    refit_item<REGEN>(sh, it - recs[i].refit_begin);
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_batch_select(const InstRec* __restrict__ recs,
@@ -2823,7 +2958,7 @@ __global__ void __launch_bounds__(kBatchRefitThreads) k_batch_refit(const InstRe
         load_params(recs[i].dP, sh);
         load_tick(&recs[i].t, sh);
         __syncthreads();
-        refit_block<REGEN>(sh, it - recs[i].refit_begin);
+        refit_item<REGEN>(sh, it - recs[i].refit_begin);
         __syncthreads();
     }
 }
