@@ -11,14 +11,16 @@
 //              atomics instead.  <NP, EXT>: spline knots (0: one force per step);
 //              the extended model features (frequency set, ground-fixed feet,
 //              friction projection).
-//  k_select    one 1024-thread block per elite/naive controller: radix select of
+//  k_select    one block per elite/naive controller (1024 threads; 512 in a
+//              graph-replayed batched tick): radix select of
 //              the K_e lowest (cost, index) pairs and their ordered list (Alg. 1
 //              Sorting); Naive reads the per-block best keys.
 //  k_sel_*     the same selection spread over many blocks, for one controller
 //              with more costs than fit in shared memory (plain solves).
 //  k_refit     one block per step (or knot): elite mean and diagonal variance
 //              (Alg. 1 Update) or the best sample per force block (Alg. 3) from
-//              the stored deviations.
+//              the stored or regenerated deviations; batched ticks give an
+//              elite set of at most 2048 several steps per block.
 //  k_grid_* / k_batch_*  the same three stages for many controllers: one block
 //              per item, or persistent blocks pulling items from device queues.
 //  k_init      the initial distribution.
