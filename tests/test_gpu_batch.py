@@ -428,6 +428,56 @@ def test_large_elite_set_batch_equals_plain():
     b.close()
 
 
+@pytest.mark.parametrize("theta", [S.THETA_STORE, S.THETA_REGENERATE])
+@pytest.mark.parametrize("mode", [S.BATCH_GRID, S.BATCH_PERSISTENT])
+def test_multi_step_refit_items_equal_plain(mode, theta):
+    # batched refit items of several steps (elite sets up to 2048): one item of a
+    # whole 128-step horizon, items that end in a short one and a frequency item,
+    # two-step items at 2048 elites, and one step per item just above 2048 and at
+    # H = 1; beside an MPPI controller, so the grid-mode tick is split
+    import torch
+    base = W.config("plain_mppi_k512_h12")
+    specs = [dict(K=64, H=128, dt_us=1000, method="elite", elite_count=1),
+             dict(K=130, H=13, method="elite", elite_count=7),
+             dict(K=2000, H=128, dt_us=1000, method="elite", elite_count=100, adaptive=True),
+             dict(K=40960, H=6, method="elite", elite_count=2048),
+             dict(K=40980, H=3, method="elite", elite_count=2049, adaptive=True),
+             dict(K=6000, H=1, method="elite", elite_count=300),
+             dict(K=3000, H=20, method="mppi")]
+    mix = []
+    for i, sp in enumerate(specs):
+        c = dict(base)
+        c.update(sp)
+        c.update(seed=700 + i, ctrl=i)
+        mix.append((c, W.problem(c)))
+    plain = [S.Controller(c) for c, _ in mix]
+    batched = [S.Controller(c) for c, _ in mix]
+    for ctl in plain + batched:
+        ctl.set_theta_mode(theta)
+    tens = [_tensors(p) for _, p in mix]
+    n = len(mix)
+    # two selections over more than 32 768 costs: their counter words need a 2 GB arena
+    b = S.Batch(n, max(sum(c.workspace_bytes() + 256 for c in batched), 2 << 30))
+    b.set_mode(mode)
+    b.set_theta_mode(theta)
+    res = torch.empty(n * S.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for tick in range(3):
+        probs, want = [], []
+        for i, (c, p) in enumerate(mix):
+            x0, xr, fe, _ = tens[i]
+            g = _gait(p, tick, c)
+            want.append(plain[i].solve(x0, xr, g, fe, min(tick, 1)).clone())
+            probs.append(batched[i].problem(x0, xr, g, fe, min(tick, 1)))
+        b.solve(batched, probs, res)
+        torch.cuda.synchronize()
+        for i in range(n):
+            assert bytes(res[i * S.RESULT_BYTES:(i + 1) * S.RESULT_BYTES].cpu().numpy()) == \
+                bytes(want[i].cpu().numpy()), (i, tick)
+            np.testing.assert_array_equal(_state(batched[i])[0], _state(plain[i])[0])
+            np.testing.assert_array_equal(_state(batched[i])[1], _state(plain[i])[1])
+    b.close()
+
+
 def test_budget_admission_rejects_without_side_effects():
     import torch
     mix = _mix()[:3]
