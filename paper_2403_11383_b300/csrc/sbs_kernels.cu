@@ -50,6 +50,8 @@ struct __align__(16) BlockShared {
     int last;
     int hist[256];
     int wtot[32], wtot2[32];
+    unsigned selkmin[32];  // a selection's staging pass: per-warp best key and finite count
+    int selnf[32];
     int digit, below, count;
     unsigned char sched[SBS_MAX_H];  // stance legs of every step when all samples share the frequency
     float mu12[12], vr12[12], dbar[12], sd12[12];
@@ -1786,6 +1788,19 @@ __device__ void naive_select(BlockShared& sh)
 //    in global memory if the bin holds more keys than fit).
 // ---------------------------------------------------------------------------
 
+// The four staged keys i0 .. i0 + 3 from shared memory (the largest key at and
+// past end); i0 a multiple of 4.
+__device__ __forceinline__ void load4k(const uint32_t* k, int i0, int end, uint32_t c[4])
+{
+    if (i0 + 4 <= end) {
+        const uint4 q = *reinterpret_cast<const uint4*>(k + i0);
+        c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = i0 + u < end ? k[i0 + u] : 0xffffffffu;
+    }
+}
+
 // The four costs of keys i0 .. i0 + 3 (+inf at and past end); i0 a multiple of 4.
 __device__ __forceinline__ void load4(const float* J, int i0, int end, float c[4])
 {
@@ -2006,9 +2021,9 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total)
 // part of the best cost and of the number of finite costs.  R: rounds of 128
 // keys per warp whose loads are in flight together (more only pays when every
 // warp has that many rounds).
-template <int R>
+template <int R, bool KEYS = false>
 __device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int begin, int end, int out0,
-                              float* bmin_out, int* nf_out)
+                              float* bmin_out, int* nf_out, const uint32_t* skeys = nullptr)
 {
     const TickArgs& t = sh.t;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -2022,16 +2037,24 @@ __device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int be
     float bmin = kInf;
     for (int base = c0; base < c1; base += 128 * R) {
         float c[4 * R];
+        uint32_t kk[4 * R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) load4(J, base + 128 * r + 4 * lane, c1, c + 4 * r);
+        for (int r = 0; r < R; ++r) {
+            if constexpr (KEYS) load4k(skeys, base + 128 * r + 4 * lane, c1, kk + 4 * r);
+            else load4(J, base + 128 * r + 4 * lane, c1, c + 4 * r);
+        }
 #pragma unroll
         for (int u = 0; u < 4 * R; ++u) {
             if (base + 128 * (u / 4) + 4 * lane + (u & 3) < c1) {
-                const uint32_t key = cost_key(c[u]);
+                uint32_t key;
+                if constexpr (KEYS) key = kk[u];
+                else key = cost_key(c[u]);
                 lt += key < thr ? 1 : 0;
                 eq += key == thr ? 1 : 0;
-                bmin = fminf(bmin, c[u]);
-                nf += c[u] < kInf ? 1 : 0;
+                if constexpr (!KEYS) {
+                    bmin = fminf(bmin, c[u]);
+                    nf += c[u] < kInf ? 1 : 0;
+                }
             }
         }
     }
@@ -2052,8 +2075,12 @@ __device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int be
     int eq_seen = 0;
     for (int base0 = c0; base0 < c1; base0 += 128 * R) {
         float cr[4 * R];
+        uint32_t kr[4 * R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) load4(J, base0 + 128 * r + 4 * lane, c1, cr + 4 * r);
+        for (int r = 0; r < R; ++r) {
+            if constexpr (KEYS) load4k(skeys, base0 + 128 * r + 4 * lane, c1, kr + 4 * r);
+            else load4(J, base0 + 128 * r + 4 * lane, c1, cr + 4 * r);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i0 = base0 + 128 * r + 4 * lane;
@@ -2062,7 +2089,9 @@ __device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int be
             int ne = 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const uint32_t key = cost_key(c[u]);
+                uint32_t key;
+                if constexpr (KEYS) key = kr[4 * r + u];
+                else key = cost_key(c[u]);
                 is_lt[u] = i0 + u < c1 && key < thr;
                 is_eq[u] = i0 + u < c1 && key == thr;
                 ne += is_eq[u] ? 1 : 0;
@@ -2102,19 +2131,32 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
         naive_select(sh);
         return;
     }
-    const int tid = threadIdx.x, T = blockDim.x;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     const int K = P.K;
     const float* J = t.ws.J;
+    const bool staged = K <= kSelectSmemMaxK;
     uint32_t thr;
     int need_eq;
-    if (K <= kSelectSmemMaxK) {
-        // staging fused with the first pass's histogram (top 8 key bits)
+    if (staged) {
+        // staging fused with the first pass's histogram (top 8 key bits), the best
+        // key and the finite count (per warp, combined when the record is written)
         for (int i = tid; i < 256; i += T) sh.hist[i] = 0;
         __syncthreads();
+        const uint32_t kinf = cost_key(kInf);
+        uint32_t kmin = 0xffffffffu;
+        int nfk = 0;
         for (int i = tid; i < K; i += T) {
             const uint32_t key = cost_key(__ldcg(J + i));
             skeys[i] = key;
             atomicAdd(&sh.hist[key >> 24], 1);
+            kmin = min(kmin, key);
+            nfk += key < kinf ? 1 : 0;
+        }
+        kmin = __reduce_min_sync(kFull, kmin);
+        nfk = __reduce_add_sync(kFull, (unsigned)nfk);
+        if (lane == 0) {
+            sh.selkmin[warp] = kmin;
+            sh.selnf[warp] = nfk;
         }
         __syncthreads();
         int rank = P.Ke;
@@ -2135,13 +2177,24 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
         thr = prefix;
         need_eq = rank;
     }
-    float bm;
-    int nf;
-    if (K >= 16384) compact_range<4>(sh, thr, need_eq, 0, K, 0, &bm, &nf);
-    else compact_range<1>(sh, thr, need_eq, 0, K, 0, &bm, &nf);
-    const float beta = block_min(sh, bm);
-    int nfin;
-    block_scan(sh, nf, &nfin);
+    float bm, beta;
+    int nf, nfin;
+    if (staged) {  // the list from the staged keys; best cost and finite count from the staging pass
+        if (K >= 16384) compact_range<4, true>(sh, thr, need_eq, 0, K, 0, &bm, &nf, skeys);
+        else compact_range<1, true>(sh, thr, need_eq, 0, K, 0, &bm, &nf, skeys);
+        uint32_t kmin = 0xffffffffu;
+        nfin = 0;
+        for (int w = 0; w < nw; ++w) {
+            kmin = min(kmin, sh.selkmin[w]);
+            nfin += sh.selnf[w];
+        }
+        beta = key_cost(kmin);
+    } else {
+        if (K >= 16384) compact_range<4>(sh, thr, need_eq, 0, K, 0, &bm, &nf);
+        else compact_range<1>(sh, thr, need_eq, 0, K, 0, &bm, &nf);
+        beta = block_min(sh, bm);
+        block_scan(sh, nf, &nfin);
+    }
     if (tid == 0) {
         sbs_result* r = t.result;
         r->cost_min = beta;
