@@ -2182,11 +2182,13 @@ __device__ void select_block(BlockShared& sh, uint32_t* skeys)
     if (staged) {  // the list from the staged keys; best cost and finite count from the staging pass
         if (K >= 16384) compact_range<4, true>(sh, thr, need_eq, 0, K, 0, &bm, &nf, skeys);
         else compact_range<1, true>(sh, thr, need_eq, 0, K, 0, &bm, &nf, skeys);
+        // warp 0 combines the staging pass's per-warp best keys and finite counts
+        // (thread 0 writes the record)
         uint32_t kmin = 0xffffffffu;
         nfin = 0;
-        for (int w = 0; w < nw; ++w) {
-            kmin = min(kmin, sh.selkmin[w]);
-            nfin += sh.selnf[w];
+        if (warp == 0) {
+            kmin = __reduce_min_sync(kFull, lane < nw ? sh.selkmin[lane] : 0xffffffffu);
+            nfin = (int)__reduce_add_sync(kFull, lane < nw ? (unsigned)sh.selnf[lane] : 0u);
         }
         beta = key_cost(kmin);
     } else {
