@@ -2065,12 +2065,21 @@ __device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int be
         sh.wtot2[warp] = eq;
     }
     __syncthreads();
-    int off = out0, eqb = 0;
-    for (int w = 0; w < warp; ++w) {
-        const int e = sh.wtot2[w];
-        off += sh.wtot[w] + min(e, max(0, need_eq - eqb));
-        eqb += e;
+    // this warp's offset: the keys below thr in the warps before it, plus the ties
+    // those warps take (ties go to the lowest indices, so they take min(need_eq,
+    // their ties)); both counts are prefix sums over the warps, one scan per warp
+    const int lt_w = lane < nw ? sh.wtot[lane] : 0, eq_w = lane < nw ? sh.wtot2[lane] : 0;
+    int lt_in = lt_w, eq_in = eq_w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(kFull, lt_in, o), b = __shfl_up_sync(kFull, eq_in, o);
+        if (lane >= o) {
+            lt_in += a;
+            eq_in += b;
+        }
     }
+    const int eqb = __shfl_sync(kFull, eq_in - eq_w, warp);  // ties in the warps before this one
+    int off = out0 + __shfl_sync(kFull, lt_in - lt_w, warp) + max(0, min(need_eq, eqb));
     const int take_eq = min(eq, max(0, need_eq - eqb));  // this warp's ties, in index order
     int eq_seen = 0;
     for (int base0 = c0; base0 < c1; base0 += 128 * R) {
