@@ -2017,10 +2017,12 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total)
 // thr, by ascending index, into out from position out0 on (never past Ke).
 // begin is a multiple of 4.  Warp w owns a contiguous sub-range (a multiple of
 // 128 long, read as 16-byte loads); a first pass counts, the warps' offsets
-// follow in warp order, a second pass writes.  Each thread also returns its
-// part of the best cost and of the number of finite costs.  R: rounds of 128
-// keys per warp whose loads are in flight together (more only pays when every
-// warp has that many rounds).
+// follow from one scan over the warps' counts, a second pass writes.  Each
+// thread also returns its part of the best cost and of the number of finite
+// costs.  R: rounds of 128 keys per warp whose loads are in flight together
+// (more only pays when every warp has that many rounds).  KEYS: the keys come
+// from skeys, staged in shared memory, instead of the costs in global memory;
+// the best cost and finite count are then the caller's (from its staging pass).
 template <int R, bool KEYS = false>
 __device__ void compact_range(BlockShared& sh, uint32_t thr, int need_eq, int begin, int end, int out0,
                               float* bmin_out, int* nf_out, const uint32_t* skeys = nullptr)
